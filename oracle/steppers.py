@@ -1,0 +1,130 @@
+"""Oracle time steppers: Procedure 3 of Sec. 3.3 with the semi-discretisations
+of Sec. 3.1 (arXiv 2404.14864).
+
+Each time step solves one modified-Helmholtz Dirichlet problem
+Delta u - kappa u = -F in Omega, u = g on Gamma (Eq. 3.13 with f = -F) by
+the boundary integral equation of Eq. 3.17:
+
+  b = g - u+[phi = 0, f-tilde]          (Y f at the boundary nodes)
+  (1/2 I + W) phi = b                    (GMRES, phi_0 = previous phi)
+  U = interface solution for (f-tilde, phi), u^{n+1} = U on Omega nodes.
+
+The right-hand side F is carried as its own variable (Eqs. 3.4 and the
+unnumbered wave recurrence after Eq. 3.7), never by differencing u.
+
+Readings where the paper is silent (Procedure 3(a) only says "calculate
+F^1 by initial boundary condition"):
+
+* Heat (Crank-Nicolson, kappa = 2/tau): the caller gives u^0, Delta u^0 and
+  optional source sums; F^1 = (2/tau) u^0 + Delta u^0 + s^0 + s^1 and
+  F^{n+2} = (4/tau) u^{n+1} - F^{n+1} + s^{n+1} + s^{n+2} (Eq. 3.4 with a
+  source term added to u_t = Delta u + s).
+* Wave (theta-scheme, Eq. 3.5, kappa = 1/(theta tau^2), theta = 1/4 gives
+  4/tau^2): the caller gives u^0, u^1, Delta u^0, Delta u^1;
+  F^1 = kappa u^1 - Delta u^1,
+  F^2 = kappa (2 u^1 - u^0) + ((1 - 2 theta)/theta) Delta u^1 + Delta u^0,
+  F^{n+2} = (kappa/theta) u^{n+1} - ((1 - 2 theta)/theta) F^{n+1} - F^n
+  (for theta = 1/4: 16/tau^2, 2, 1 as printed).
+* Schroedinger (Strang, A = -i Delta as in Eq. 2.2, B = -i (v + w|u|^2)):
+  u* = u^n - i (tau/2) Delta u^n (Step 1); u** from the pointwise
+  Crank-Nicolson step of Eq. 3.10, closed form for w = 0; Step 3 (Eq. 3.12)
+  is Delta u - kappa u = -kappa u** with kappa = 2i/tau.  Delta u^{n+1} then
+  equals kappa (u^{n+1} - u**), so the next u* = 2 u^{n+1} - u**; the first
+  step uses the caller's Delta u^0.
+"""
+
+import numpy as np
+
+from .gmres import gmres
+from .interface import apply_operator, interface_solve
+
+
+class _Base:
+    def __init__(self, dom, tau, tol=1e-10, restart=50, maxit=2000):
+        self.dom, self.tau = dom, float(tau)
+        self.tol, self.restart, self.maxit = tol, restart, maxit
+        self.mask = dom.interior_inside()
+        self.phi = None
+        self.iters = []
+
+    def _solve(self, kappa, F, g):
+        """u^{n+1} on the grid for Delta u - kappa u = -F, u = g on Gamma."""
+        dom = self.dom
+        Ft = np.where(self.mask, -F, 0.0)
+        b = np.asarray(g) - apply_operator(dom, kappa, np.zeros(dom.nb, dtype=Ft.dtype), Ft)
+        x0 = self.phi if self.phi is not None else np.zeros(dom.nb, dtype=b.dtype)
+        phi, it, res, ok = gmres(lambda v: apply_operator(dom, kappa, v), b, x0,
+                                 self.tol, self.restart, self.maxit)
+        if not ok:
+            raise RuntimeError("GMRES did not converge (res %.3e)" % res)
+        self.phi = phi
+        self.iters.append(it)
+        _, U = interface_solve(dom, kappa, phi, Ft)
+        return U
+
+
+class HeatStepper(_Base):
+    """u_t = Delta u + s, Crank-Nicolson (Eqs. 3.1-3.4)."""
+
+    def init(self, u0, lap_u0, src_sum=None):
+        self.kappa = 2.0 / self.tau
+        self.F = (2.0 / self.tau) * np.asarray(u0) + np.asarray(lap_u0)
+        if src_sum is not None:
+            self.F = self.F + src_sum
+        self.u = np.array(u0, copy=True)
+
+    def step(self, g_next, src_sum_next=None):
+        """Advance one step; src_sum_next = s^{n+1} + s^{n+2} on the grid."""
+        U = self._solve(self.kappa, self.F, g_next)
+        self.u = U
+        self.F = (4.0 / self.tau) * U - self.F
+        if src_sum_next is not None:
+            self.F = self.F + src_sum_next
+        return U
+
+
+class WaveStepper(_Base):
+    """u_tt = Delta u, implicit theta-scheme (Eqs. 3.5-3.7)."""
+
+    def init(self, u0, lap_u0, u1, lap_u1, theta=0.25):
+        th = float(theta)
+        self.theta = th
+        self.kappa = 1.0 / (th * self.tau ** 2)
+        c = (1.0 - 2.0 * th) / th
+        self.F_prev = self.kappa * np.asarray(u1) - np.asarray(lap_u1)
+        self.F = self.kappa * (2.0 * np.asarray(u1) - np.asarray(u0)) + c * np.asarray(lap_u1) \
+            + np.asarray(lap_u0)
+        self.u = np.array(u1, copy=True)
+
+    def step(self, g_next):
+        U = self._solve(self.kappa, self.F, g_next)
+        self.u = U
+        c = (1.0 - 2.0 * self.theta) / self.theta
+        F_next = (self.kappa / self.theta) * U - c * self.F - self.F_prev
+        self.F_prev, self.F = self.F, F_next
+        return U
+
+
+class SchrodingerStepper(_Base):
+    """-i u_t + Delta u + v u + w |u|^2 u = 0 (Eq. 2.2), Strang splitting."""
+
+    def init(self, u0, lap_u0):
+        self.kappa = 2.0j / self.tau
+        u0 = np.asarray(u0, dtype=np.complex128)
+        self.ustar = u0 - 0.5j * self.tau * np.asarray(lap_u0, dtype=np.complex128)
+        self.u = u0.copy()
+
+    def b_step(self, ustar, v, w=0.0):
+        """Pointwise Crank-Nicolson step of Eq. 3.10 for iu_t = (v + w|u|^2) u."""
+        if w != 0.0:
+            raise NotImplementedError("w != 0 needs the pointwise Newton solve")
+        a = 0.5j * self.tau * np.asarray(v)
+        return (1.0 - a) / (1.0 + a) * ustar
+
+    def step(self, g_next, v, w=0.0):
+        uss = self.b_step(self.ustar, v, w)
+        # Step 3 (Eq. 3.12): Delta u - kappa u = -kappa u**, i.e. F = kappa u**.
+        U = self._solve(self.kappa, self.kappa * uss, g_next)
+        self.u = U
+        self.ustar = 2.0 * U - uss
+        return U
