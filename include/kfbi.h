@@ -1,0 +1,231 @@
+/*
+ * kfbi.h -- C ABI of the GB300 (sm_103a) KFBI operator-application library.
+ *
+ * The library implements the hot path of the GPU-accelerated kernel-free
+ * boundary integral (KFBI) method of Tan, Huang and Ying (arXiv 2404.14864):
+ * one application of the boundary-integral operator of the Dirichlet BIE
+ * (Eq. 3.17), i.e. Procedure 2 of Sec. 3.3 --
+ *   (a) jumps at the interface (Eq. 3.35 and the 3x3 system of Sec. 3.2.5)
+ *       and the corrected five-point right-hand side (Sec. 3.2.4),
+ *   (b) the box solve of Delta_h u - kappa u = R with u = 0 on the box
+ *       (Eq. 3.31) by DST-I transforms and an eigenvalue division
+ *       (Sec. 3.4.2),
+ *   (c) extraction of u+ at the boundary nodes (Eq. 3.36, Sec. 3.2.6) --
+ * and the time steppers of Sec. 3.1 / Procedure 3 that call it inside a
+ * GMRES solve of the BIE (the Krylov alternative named in Sec. 5).
+ *
+ * Conventions (all entry points):
+ *  - Plain C types only.  Device pointers are CUDA global-memory pointers
+ *    owned by the caller; the library never frees them.  Everything reached
+ *    through an opaque handle is owned by the library.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Calls enqueue work on it; kfbi_create_domain, the
+ *    kfbi_step_* calls and kfbi_destroy_* synchronise the stream before
+ *    returning (the step calls read GMRES convergence scalars on the host).
+ *  - Grid arrays exchanged with the caller are the (M-1) x (M-1) interior
+ *    nodes x_i = lo + i h, y_j = lo + j h, i, j = 1..M-1, h = (hi - lo)/M,
+ *    row-major with y slow: element (j-1)*(M-1) + (i-1).
+ *  - Boundary arrays have n_boundary entries, node k at curve parameter
+ *    2 pi k / n_boundary.
+ *  - Complex data are interleaved (re, im) pairs of doubles (complex128).
+ *    An operator call is complex iff kappa_im != 0.
+ *  - Every call returns a kfbi_status; the library never aborts or exits.
+ *    On failure the message is available from kfbi_last_error(dom) (or
+ *    kfbi_last_global_error() when no domain exists yet).
+ */
+#ifndef KFBI_H
+#define KFBI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  KFBI_OK = 0,
+  KFBI_ERR_ARG = 1,           /* invalid argument or size */
+  KFBI_ERR_GEOMETRY = 2,      /* interface too close to the box, bad stencil */
+  KFBI_ERR_OOM = 3,           /* device allocation failed or admission refused */
+  KFBI_ERR_NOT_CONVERGED = 4, /* GMRES reached gmres_maxit */
+  KFBI_ERR_NONFINITE = 5,     /* NaN/Inf in a residual */
+  KFBI_ERR_TIMEOUT = 6,       /* a bounded device-side wait gave up */
+  KFBI_ERR_CUDA = 7,          /* a CUDA runtime/driver call failed */
+  KFBI_ERR_UNSUPPORTED = 8    /* feature not available in this build */
+} kfbi_status;
+
+typedef enum {
+  KFBI_FP64 = 0,        /* plain path: every kernel in float64 */
+  KFBI_MIXED_TF32 = 1   /* DST on tcgen05 tensor cores, TF32 split in 3
+                           passes with FP32 accumulation; correction and
+                           extraction in FP32; GMRES in FP64 */
+} kfbi_precision;
+
+typedef enum {
+  KFBI_CURVE_POLAR = 0,  /* z(t) = c + r(t)(cos t, sin t),
+                            r(t) = params[0] + params[1] sin(params[2] t + params[3]) */
+  KFBI_CURVE_ELLIPSE = 1 /* z(t) = c + Rot(params[2]) (params[0] cos t, params[1] sin t) */
+} kfbi_curve_kind;
+
+typedef struct {
+  int M;               /* grid intervals per side (unknowns (M-1)^2), 8 <= M <= 4096 */
+  double box_lo;       /* box [box_lo, box_hi]^2 */
+  double box_hi;
+  int n_boundary;      /* boundary nodes, 16 <= n_boundary <= 16384 */
+  int curve_kind;      /* kfbi_curve_kind */
+  double cx, cy;       /* curve centre */
+  double params[6];    /* curve parameters (see kfbi_curve_kind) */
+  int precision;       /* kfbi_precision */
+  int gmres_restart;   /* GMRES restart length m, 1..64 */
+  double gmres_tol;    /* stop when ||r||_2 <= gmres_tol * ||b||_2 */
+  int gmres_maxit;     /* total GMRES iterations per solve */
+} kfbi_domain_desc;
+
+typedef struct {
+  int iters;           /* GMRES iterations (operator applications inside GMRES) */
+  double rel_residual; /* final rotated-residual estimate / ||b|| */
+  int converged;       /* 1 if rel_residual <= gmres_tol */
+  int applications;    /* operator applications in the step (GMRES + 2) */
+} kfbi_solve_info;
+
+typedef struct kfbi_domain kfbi_domain; /* opaque, library-owned */
+typedef struct kfbi_state kfbi_state;   /* opaque, library-owned time-level fields */
+typedef struct kfbi_plan kfbi_plan;     /* opaque, host-only setup tables */
+
+/* ---- setup (Procedure 1 of Sec. 3.3) ------------------------------------ */
+
+/* Build the geometry (boundary nodes, inside mask, irregular nodes, cut-edge
+ * intersections), the per-target coefficient tables and the DST tables on
+ * the host, upload them once to the current CUDA device and allocate the
+ * domain's work buffers.  Synchronous.  Errors: KFBI_ERR_ARG (sizes),
+ * KFBI_ERR_GEOMETRY (interface closer than 2h to the box, empty stencil),
+ * KFBI_ERR_OOM, KFBI_ERR_CUDA.  On error *out is NULL. */
+kfbi_status kfbi_create_domain(const kfbi_domain_desc* desc, void* stream, kfbi_domain** out);
+void kfbi_destroy_domain(kfbi_domain* dom);
+
+/* ---- the hot path (Procedure 2 of Sec. 3.3) ----------------------------- */
+
+/* out_dev[k] = u+(z_k): interior limit at boundary node k of the solution u
+ * of the interface problem (Eq. 3.30) Delta u - kappa u = f-tilde off Gamma,
+ * [u] = phi, [u_n] = 0 on Gamma, u = 0 on the box.
+ *   phi_dev : n_boundary doubles (complex128 if kappa_im != 0), device.
+ *   f_dev   : (M-1)^2 grid of f (same type as phi) or NULL for f = 0; values
+ *             at nodes outside Omega are ignored (f-tilde of Eq. 3.25).
+ *   out_dev : n_boundary doubles (complex128 if kappa_im != 0), device.
+ * kappa = kappa_re + i kappa_im; (lambda_a + lambda_b - kappa) must not
+ * vanish for any DST mode (true for kappa_re > 0 or kappa_im != 0).
+ * Asynchronous on `stream`; uses the domain's work buffers, so calls on one
+ * domain must not overlap. */
+kfbi_status kfbi_apply_operator(kfbi_domain* dom, double kappa_re, double kappa_im,
+                                const void* phi_dev, const void* f_dev, void* out_dev,
+                                void* stream);
+
+/* As kfbi_apply_operator, and also writes the grid solution u of Eq. 3.30 at
+ * all (M-1)^2 interior nodes (inside and outside Omega) to u_grid_dev (same
+ * element type).  u_plus_dev may be NULL. */
+kfbi_status kfbi_interface_solve(kfbi_domain* dom, double kappa_re, double kappa_im,
+                                 const void* phi_dev, const void* f_dev, void* u_grid_dev,
+                                 void* u_plus_dev, void* stream);
+
+/* Solve the Dirichlet BIE (Eq. 3.17) (1/2 I + W) phi = b by GMRES(m) with
+ * FP64 Arnoldi (CGS2), Givens rotations and the domain's operator;
+ * phi_dev holds the initial guess on entry and the solution on exit.
+ * Synchronous.  KFBI_ERR_NOT_CONVERGED if gmres_maxit is reached. */
+kfbi_status kfbi_solve_density(kfbi_domain* dom, double kappa_re, double kappa_im,
+                               const void* b_dev, void* phi_dev, kfbi_solve_info* info,
+                               void* stream);
+
+/* ---- time stepping (Sec. 3.1, Procedure 3) ------------------------------ */
+
+typedef enum { KFBI_HEAT = 0, KFBI_WAVE = 1, KFBI_SCHRODINGER = 2 } kfbi_equation;
+
+kfbi_status kfbi_state_create(kfbi_domain* dom, int equation, kfbi_state** out);
+void kfbi_state_destroy(kfbi_state* st);
+
+/* Heat u_t = Delta u + s, Crank-Nicolson (Eqs. 3.1-3.4), kappa = 2/dt:
+ * F^1 = (2/dt) u0 + lap_u0 + src_sum (src_sum = s^0 + s^1 or NULL). */
+kfbi_status kfbi_state_init_heat(kfbi_state* st, double dt, const double* u0_dev,
+                                 const double* lap_u0_dev, const double* src_sum_dev,
+                                 void* stream);
+/* Wave u_tt = Delta u, theta-scheme (Eq. 3.5), kappa = 1/(theta dt^2);
+ * the state starts at time level 1: u1 is the current field. */
+kfbi_status kfbi_state_init_wave(kfbi_state* st, double dt, double theta, const double* u0_dev,
+                                 const double* lap_u0_dev, const double* u1_dev,
+                                 const double* lap_u1_dev, void* stream);
+/* Schroedinger -i u_t + Delta u + v u + w|u|^2 u = 0 (Eq. 2.2), Strang
+ * splitting (Eqs. 3.8-3.12), kappa = 2i/dt; u0, lap_u0 complex128. */
+kfbi_status kfbi_state_init_schrodinger(kfbi_state* st, double dt, const void* u0_dev,
+                                        const void* lap_u0_dev, void* stream);
+
+/* One heat step: solve for u^{n+1} with Dirichlet data g_next_dev
+ * (n_boundary doubles at t^{n+1}), then F^{n+2} = (4/dt) u^{n+1} - F^{n+1}
+ * + src_sum_next (s^{n+1} + s^{n+2} on the grid, or NULL).  info may be NULL. */
+kfbi_status kfbi_step_heat(kfbi_domain* dom, kfbi_state* st, const double* g_next_dev,
+                           const double* src_sum_next_dev, kfbi_solve_info* info,
+                           void* stream);
+/* One wave step: u^{n+1} with data g_next_dev, then
+ * F^{n+2} = (kappa/theta) u^{n+1} - ((1-2theta)/theta) F^{n+1} - F^n. */
+kfbi_status kfbi_step_wave(kfbi_domain* dom, kfbi_state* st, const double* g_next_dev,
+                           kfbi_solve_info* info, void* stream);
+/* One Strang step: u** = ((1 - i dt v/2)/(1 + i dt v/2)) u* (Eq. 3.10 with
+ * w = 0; w != 0 returns KFBI_ERR_UNSUPPORTED), solve Eq. 3.12 for u^{n+1}
+ * with data g_next_dev (complex128), then u* = 2 u^{n+1} - u**.
+ * v_dev: (M-1)^2 doubles (the potential v). */
+kfbi_status kfbi_step_schrodinger(kfbi_domain* dom, kfbi_state* st, const double* v_dev,
+                                  double w, const void* g_next_dev, kfbi_solve_info* info,
+                                  void* stream);
+
+/* Copy the current field u^n (all (M-1)^2 nodes; values outside Omega are
+ * the exterior part of the interface solution) or the current density. */
+kfbi_status kfbi_state_get_u(kfbi_state* st, void* u_out_dev, void* stream);
+kfbi_status kfbi_state_get_phi(kfbi_state* st, void* phi_out_dev, void* stream);
+
+/* ---- inspection and diagnostics ----------------------------------------- */
+
+const char* kfbi_last_error(const kfbi_domain* dom);
+const char* kfbi_last_global_error(void);
+/* Number of CUDA kernels this library has launched since it was loaded. */
+long long kfbi_launch_count(void);
+/* Device bytes held by the domain (work buffers + tables). */
+long long kfbi_domain_device_bytes(const kfbi_domain* dom);
+
+/* Host-only plan: the geometry and coefficient tables kfbi_create_domain
+ * uploads, built without touching the GPU, for inspection and tests. */
+typedef enum {
+  KFBI_PLAN_N_EDGES = 0,     /* count: cut edges */
+  KFBI_PLAN_EDGE_I = 1,      /* int32[n_edges]: i of the lower/left endpoint */
+  KFBI_PLAN_EDGE_J = 2,      /* int32[n_edges]: j of the lower/left endpoint */
+  KFBI_PLAN_EDGE_DIR = 3,    /* int32[n_edges]: 0 along x, 1 along y */
+  KFBI_PLAN_EDGE_COORD = 4,  /* double[n_edges]: intersection coordinate on the edge's line */
+  KFBI_PLAN_EDGE_THETA = 5,  /* double[n_edges]: curve parameter of the intersection */
+  KFBI_PLAN_INSIDE = 6,      /* uint8[(M+1)^2]: inside mask, [j*(M+1)+i] */
+  KFBI_PLAN_N_IRREGULAR = 7, /* count: irregular nodes */
+  KFBI_PLAN_IRREGULAR = 8,   /* int32[n_irr]: interior index (j-1)*(M-1)+(i-1), ascending */
+  KFBI_PLAN_N_ARMS = 9,      /* count: correction arms (two per cut edge) */
+  KFBI_PLAN_ARM_NODE = 10,   /* int32[n_arms]: index into the irregular list */
+  KFBI_PLAN_ARM_K0 = 11,     /* int32[n_arms]: first density node of the 6-point stencil */
+  KFBI_PLAN_ARM_ALPHA = 12,  /* double[n_arms*6]: kappa-free density weights (scaled by s/h^2) */
+  KFBI_PLAN_ARM_BETA = 13,   /* double[n_arms*6]: density weights multiplying kappa */
+  KFBI_PLAN_ARM_FIDX = 14,   /* int32[n_arms*2]: interior indices of the f extrapolation */
+  KFBI_PLAN_ARM_FCOEF = 15,  /* double[n_arms*2]: their coefficients */
+  KFBI_PLAN_NODE_GIDX = 16,  /* int32[nb*6]: interior indices of the extraction stencil */
+  KFBI_PLAN_NODE_W = 17,     /* double[nb*6]: extraction weights on U */
+  KFBI_PLAN_NODE_A = 18,     /* double[nb*6]: kappa-free density weights, nodes k-2..k+3 */
+  KFBI_PLAN_NODE_B = 19,     /* double[nb*6]: density weights multiplying kappa */
+  KFBI_PLAN_NODE_FIDX = 20,  /* int32[nb]: interior index of f at the node */
+  KFBI_PLAN_NODE_FCOEF = 21  /* double[nb]: its coefficient */
+} kfbi_plan_field;
+
+kfbi_status kfbi_plan_create(const kfbi_domain_desc* desc, kfbi_plan** out);
+void kfbi_plan_destroy(kfbi_plan* plan);
+/* Element count of a field (or the value of a count field). */
+long long kfbi_plan_size(const kfbi_plan* plan, int field);
+/* Copy a field into host memory dst (kfbi_plan_size elements of its type). */
+kfbi_status kfbi_plan_export(const kfbi_plan* plan, int field, void* dst);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KFBI_H */

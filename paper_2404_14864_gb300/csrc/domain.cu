@@ -1,0 +1,637 @@
+// Domain setup upload and the float64 operator application (Procedure 2 of
+// Sec. 3.3, arXiv 2404.14864) on the GPU.
+//
+//   (a) k_correct: one thread per irregular node sums its cut arms' jump
+//       corrections (decoupled strategy of Sec. 3.4.2: the node owns its
+//       arms, no atomics) from the precomputed arm tables;
+//   (b) four passes of k_dgemm_t (out = (A S)^T, so two passes give S A S)
+//       with k_eigscale between forward and inverse transforms: the box
+//       solve of Eq. 3.31 by DST-I and the eigenvalue division;
+//   (c) k_extract: one thread per boundary node, Eq. 3.36 with the
+//       precomputed extraction weights and jump coefficients.
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "internal.h"
+
+namespace kfbi {
+
+std::atomic<long long> g_launches{0};
+static std::mutex g_err_mu;
+static std::string g_err;
+
+void set_global_error(const std::string& s) {
+  std::lock_guard<std::mutex> lk(g_err_mu);
+  g_err = s;
+}
+
+// ---------------------------------------------------------------------------
+// kernels
+// ---------------------------------------------------------------------------
+
+// Caller layout (n1 x n1, complex interleaved if C) -> padded planes, masked
+// to Omega (f-tilde of Eq. 3.25).  Padding is zero.
+template <bool C>
+__global__ void k_pad_mask(const double* __restrict__ src, const uint8_t* __restrict__ mask,
+                           double* __restrict__ dst, int n1, int Mp) {
+  const size_t plane = (size_t)Mp * Mp;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < plane;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    const int r = (int)(idx / Mp), c = (int)(idx % Mp);
+    double re = 0.0, im = 0.0;
+    if (r < n1 && c < n1 && mask[idx]) {
+      const size_t s = (size_t)r * n1 + c;
+      if (C) {
+        re = src[2 * s];
+        im = src[2 * s + 1];
+      } else {
+        re = src[s];
+      }
+    }
+    dst[idx] = re;
+    if (C) dst[plane + idx] = im;
+  }
+}
+
+// Padded planes -> caller layout (complex interleaved if C).
+template <bool C>
+__global__ void k_unpad(const double* __restrict__ src, double* __restrict__ dst, int n1, int Mp) {
+  const size_t plane = (size_t)Mp * Mp;
+  const size_t n = (size_t)n1 * n1;
+  for (size_t s = blockIdx.x * (size_t)blockDim.x + threadIdx.x; s < n;
+       s += (size_t)gridDim.x * blockDim.x) {
+    const int r = (int)(s / n1), c = (int)(s % n1);
+    const size_t p = (size_t)r * Mp + c;
+    if (C) {
+      dst[2 * s] = src[p];
+      dst[2 * s + 1] = src[plane + p];
+    } else {
+      dst[s] = src[p];
+    }
+  }
+}
+
+// (a) corrected right-hand side at the irregular nodes:
+// R(p) = f-tilde(p) + sum over arms of the jump correction (Sec. 3.2.4).
+// Arm a contributes sum_m (alpha_m + kappa beta_m) phi[k0+m] + sum_q c_q f[idx_q]
+// (weights already carry the sign and 1/h^2).
+template <bool C>
+__global__ void k_correct(double* __restrict__ R, size_t plane, const double* __restrict__ ft,
+                          const int* __restrict__ irr_off, const int* __restrict__ arm_start,
+                          const int* __restrict__ arm_k0, const double* __restrict__ alpha,
+                          const double* __restrict__ beta, const int* __restrict__ fidx,
+                          const double* __restrict__ fcoef, int n_irr, int n_arms, int nb,
+                          const double* __restrict__ phi, int ps, double kre, double kim) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= n_irr) return;
+  const int off = irr_off[n];
+  double sr = ft ? ft[off] : 0.0;
+  double si = (C && ft) ? ft[plane + off] : 0.0;
+  const int a1 = arm_start[n + 1];
+  for (int a = arm_start[n]; a < a1; ++a) {
+    int k = arm_k0[a];
+    double ar = 0.0, ai = 0.0, br = 0.0, bi = 0.0;
+#pragma unroll
+    for (int m = 0; m < 6; ++m) {
+      const double al = alpha[m * n_arms + a], be = beta[m * n_arms + a];
+      const double pr = phi[(size_t)k * ps];
+      ar = fma(al, pr, ar);
+      br = fma(be, pr, br);
+      if (C) {
+        const double pi = phi[(size_t)k * ps + 1];
+        ai = fma(al, pi, ai);
+        bi = fma(be, pi, bi);
+      }
+      k = (k + 1 == nb) ? 0 : k + 1;
+    }
+    sr += ar + kre * br;
+    if (C) {
+      sr -= kim * bi;
+      si += ai + kre * bi + kim * br;
+    }
+    if (ft) {
+      const int f0 = fidx[a], f1 = fidx[n_arms + a];
+      const double c0 = fcoef[a], c1 = fcoef[n_arms + a];
+      sr += c0 * ft[f0] + c1 * ft[f1];
+      if (C) si += c0 * ft[plane + f0] + c1 * ft[plane + f1];
+    }
+  }
+  R[off] = sr;
+  if (C) R[plane + off] = si;
+}
+
+// (b) one DST-I pass in float64: out[p][c][r] = sum_k A[p][r][k] S[k][c].
+// 64x64 output tile per block, 256 threads with 4x4 outputs each; the
+// transposed store is coalesced along r.
+__global__ void __launch_bounds__(256) k_dgemm_t(const double* __restrict__ A,
+                                                 const double* __restrict__ S,
+                                                 double* __restrict__ out, int Mp) {
+  __shared__ double As[16][65];
+  __shared__ double Bs[16][64];
+  const size_t plane = (size_t)Mp * Mp;
+  const double* Ap = A + blockIdx.z * plane;
+  double* Op = out + blockIdx.z * plane;
+  const int r0 = blockIdx.y * 64, c0 = blockIdx.x * 64;
+  const int tid = threadIdx.x, tr = tid & 15, tc = tid >> 4;
+  double acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+  for (int k0 = 0; k0 < Mp; k0 += 16) {
+#pragma unroll
+    for (int e = tid; e < 1024; e += 256) {
+      const int r = e >> 4, k = e & 15;
+      As[k][r] = Ap[(size_t)(r0 + r) * Mp + k0 + k];
+      const int kk = e >> 6, c = e & 63;
+      Bs[kk][c] = S[(size_t)(k0 + kk) * Mp + c0 + c];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      double a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[k][tr + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[k][tc + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int j = 0; j < 4; ++j)
+#pragma unroll
+    for (int i = 0; i < 4; ++i) Op[(size_t)(c0 + tc + 16 * j) * Mp + r0 + tr + 16 * i] = acc[i][j];
+}
+
+// (b) eigenvalue division of the transformed right-hand side:
+// U^_ab = R^_ab * (2/M)^2 / (lambda_a + lambda_b - kappa).
+__global__ void k_eigscale(double* __restrict__ T, size_t plane, int Mp, int n1,
+                           const double* __restrict__ lam, double kre, double kim, double scale,
+                           int cplx) {
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < plane;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    const int a = (int)(idx / Mp), b = (int)(idx % Mp);
+    if (a >= n1 || b >= n1) continue;
+    const double dr = lam[a] + lam[b] - kre;
+    if (!cplx) {
+      T[idx] *= scale / dr;
+    } else {
+      // (x + i y) * scale / (dr - i kim)
+      const double den = scale / (dr * dr + kim * kim);
+      const double x = T[idx], y = T[plane + idx];
+      T[idx] = (x * dr - y * kim) * den;
+      T[plane + idx] = (x * kim + y * dr) * den;
+    }
+  }
+}
+
+// (c) u+ at boundary node k (Eq. 3.36): sum_m w_m U(p_m) + jump terms.
+template <bool C>
+__global__ void k_extract(const double* __restrict__ U, size_t plane, const double* __restrict__ ft,
+                          const int* __restrict__ gidx, const double* __restrict__ w,
+                          const double* __restrict__ A, const double* __restrict__ B,
+                          const int* __restrict__ fidx, const double* __restrict__ fcoef, int nb,
+                          const double* __restrict__ phi, int ps, double kre, double kim,
+                          double* __restrict__ out, int os) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nb) return;
+  double sr = 0.0, si = 0.0;
+#pragma unroll
+  for (int m = 0; m < 6; ++m) {
+    const int g = gidx[m * nb + k];
+    const double wm = w[m * nb + k];
+    sr = fma(wm, U[g], sr);
+    if (C) si = fma(wm, U[plane + g], si);
+  }
+  double ar = 0.0, ai = 0.0, br = 0.0, bi = 0.0;
+  int kk = k - 2;
+  if (kk < 0) kk += nb;
+#pragma unroll
+  for (int j = 0; j < 6; ++j) {
+    const double a = A[j * nb + k], b = B[j * nb + k];
+    const double pr = phi[(size_t)kk * ps];
+    ar = fma(a, pr, ar);
+    br = fma(b, pr, br);
+    if (C) {
+      const double pi = phi[(size_t)kk * ps + 1];
+      ai = fma(a, pi, ai);
+      bi = fma(b, pi, bi);
+    }
+    kk = (kk + 1 == nb) ? 0 : kk + 1;
+  }
+  sr += ar + kre * br;
+  if (C) {
+    sr -= kim * bi;
+    si += ai + kre * bi + kim * br;
+  }
+  if (ft) {
+    const int g = fidx[k];
+    const double c = fcoef[k];
+    sr += c * ft[g];
+    if (C) si += c * ft[plane + g];
+  }
+  out[(size_t)k * os] = sr;
+  if (C)
+    out[(size_t)k * os + 1] = si;
+  else if (os == 2)
+    out[(size_t)k * os + 1] = 0.0;
+}
+
+// ---------------------------------------------------------------------------
+// host
+// ---------------------------------------------------------------------------
+
+int grid_for(size_t n, int block) {
+  size_t g = (n + block - 1) / block;
+  if (g > 152 * 32) g = 152 * 32;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+template <class T>
+static T* dev_upload(kfbi_domain* D, const std::vector<T>& v) {
+  T* p = nullptr;
+  const size_t bytes = std::max<size_t>(1, v.size()) * sizeof(T);
+  KFBI_CUDA(cudaMalloc(&p, bytes));
+  D->bytes += (long long)bytes;
+  if (!v.empty()) KFBI_CUDA(cudaMemcpy(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+  return p;
+}
+
+template <class T>
+static T* dev_alloc(kfbi_domain* D, size_t n) {
+  T* p = nullptr;
+  KFBI_CUDA(cudaMalloc(&p, std::max<size_t>(1, n) * sizeof(T)));
+  D->bytes += (long long)(std::max<size_t>(1, n) * sizeof(T));
+  return p;
+}
+
+static void free_domain(kfbi_domain* D) {
+  if (!D) return;
+  if (D->tc) tc_destroy(D->tc);
+  gmres_free(D);
+  void* ptrs[] = {D->d_mask, D->d_irr_off, D->d_arm_start, D->d_arm_k0, D->d_arm_alpha,
+                  D->d_arm_beta, D->d_arm_fidx, D->d_arm_fcoef, D->d_node_gidx, D->d_node_w,
+                  D->d_node_a, D->d_node_b, D->d_node_fidx, D->d_node_fcoef, D->d_arm_alpha32,
+                  D->d_arm_beta32, D->d_arm_fcoef32, D->d_node_w32, D->d_node_a32,
+                  D->d_node_b32, D->d_node_fcoef32, D->d_S, D->d_lam, D->d_R, D->d_T, D->d_U,
+                  D->d_fpad, D->d_zero_nb};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  delete D;
+}
+
+static std::vector<int> to_padded(const std::vector<int>& idx, int n1, int Mp) {
+  std::vector<int> o(idx.size());
+  for (size_t q = 0; q < idx.size(); ++q) o[q] = (idx[q] / n1) * Mp + (idx[q] % n1);
+  return o;
+}
+
+// [rows][cols] host table -> [cols][rows] device layout (SoA per column).
+template <class T>
+static std::vector<T> transpose(const std::vector<T>& v, int rows, int cols) {
+  std::vector<T> o(v.size());
+  for (int r = 0; r < rows; ++r)
+    for (int c = 0; c < cols; ++c) o[(size_t)c * rows + r] = v[(size_t)r * cols + c];
+  return o;
+}
+
+static std::vector<float> to_f32(const std::vector<double>& v) {
+  std::vector<float> o(v.size());
+  for (size_t q = 0; q < v.size(); ++q) o[q] = (float)v[q];
+  return o;
+}
+
+static void upload_domain(kfbi_domain* D, const Plan& P) {
+  const int n1 = D->n1, Mp = D->Mp, nb = D->nb, M = D->M;
+  const size_t plane = (size_t)Mp * Mp;
+  std::vector<uint8_t> mask(plane, 0);
+  for (int j = 1; j < M; ++j)
+    for (int i = 1; i < M; ++i) mask[(size_t)(j - 1) * Mp + (i - 1)] = P.in(i, j) ? 1 : 0;
+  D->d_mask = dev_upload(D, mask);
+  D->n_irr = P.n_irr();
+  D->n_arms = P.n_arms();
+  const int na = D->n_arms;
+  D->d_irr_off = dev_upload(D, to_padded(P.irr, n1, Mp));
+  D->d_arm_start = dev_upload(D, P.arm_start);
+  D->d_arm_k0 = dev_upload(D, P.arm_k0);
+  std::vector<double> alpha = transpose(P.arm_alpha, na, 6), beta = transpose(P.arm_beta, na, 6);
+  std::vector<double> fcoef = transpose(P.arm_fcoef, na, 2);
+  D->d_arm_alpha = dev_upload(D, alpha);
+  D->d_arm_beta = dev_upload(D, beta);
+  D->d_arm_fidx = dev_upload(D, transpose(to_padded(P.arm_fidx, n1, Mp), na, 2));
+  D->d_arm_fcoef = dev_upload(D, fcoef);
+  std::vector<double> nw = transpose(P.node_w, nb, 6), na_ = transpose(P.node_a, nb, 6),
+                      nb_ = transpose(P.node_b, nb, 6);
+  D->d_node_gidx = dev_upload(D, transpose(to_padded(P.node_gidx, n1, Mp), nb, 6));
+  D->d_node_w = dev_upload(D, nw);
+  D->d_node_a = dev_upload(D, na_);
+  D->d_node_b = dev_upload(D, nb_);
+  D->d_node_fidx = dev_upload(D, to_padded(P.node_fidx, n1, Mp));
+  D->d_node_fcoef = dev_upload(D, P.node_fcoef);
+  if (D->desc.precision == KFBI_MIXED_TF32) {
+    D->d_arm_alpha32 = dev_upload(D, to_f32(alpha));
+    D->d_arm_beta32 = dev_upload(D, to_f32(beta));
+    D->d_arm_fcoef32 = dev_upload(D, to_f32(fcoef));
+    D->d_node_w32 = dev_upload(D, to_f32(nw));
+    D->d_node_a32 = dev_upload(D, to_f32(na_));
+    D->d_node_b32 = dev_upload(D, to_f32(nb_));
+    D->d_node_fcoef32 = dev_upload(D, to_f32(P.node_fcoef));
+  }
+  // DST-I matrix S[a][i] = sin(pi a i / M), a*i reduced mod 2M; eigenvalues
+  // lambda_a = -(4/h^2) sin^2(pi a / 2M) of the 1-D second difference.
+  std::vector<double> S(plane, 0.0), lam(Mp, 0.0);
+  const double pi = 3.14159265358979323846264338327950288;
+  for (int a = 1; a <= n1; ++a) {
+    for (int i = 1; i <= n1; ++i) {
+      const long long ai = ((long long)a * i) % (2LL * M);
+      S[(size_t)(a - 1) * Mp + (i - 1)] = std::sin(pi * (double)ai / (double)M);
+    }
+    const double s = std::sin(pi * (double)a / (2.0 * M));
+    lam[a - 1] = -(4.0 / (D->h * D->h)) * s * s;
+  }
+  D->d_S = dev_upload(D, S);
+  D->d_lam = dev_upload(D, lam);
+  D->d_R = dev_alloc<double>(D, 2 * plane);
+  D->d_T = dev_alloc<double>(D, 2 * plane);
+  D->d_U = dev_alloc<double>(D, 2 * plane);
+  D->d_fpad = dev_alloc<double>(D, 2 * plane);
+  D->d_zero_nb = dev_alloc<double>(D, 2 * (size_t)nb);
+  KFBI_CUDA(cudaMemset(D->d_R, 0, 2 * plane * sizeof(double)));
+  KFBI_CUDA(cudaMemset(D->d_U, 0, 2 * plane * sizeof(double)));
+  KFBI_CUDA(cudaMemset(D->d_zero_nb, 0, 2 * (size_t)nb * sizeof(double)));
+  D->rhs_sparse_planes = 2;
+}
+
+void apply_internal(kfbi_domain* D, double kre, double kim, const double* phi, int ps,
+                    const double* ft, double* out, int os, bool want_grid, cudaStream_t st) {
+  if (D->tc) {
+    tc_apply(D, kre, kim, phi, ps, ft, out, os, want_grid, st);
+    return;
+  }
+  const bool C = kim != 0.0;
+  const int P = C ? 2 : 1;
+  const int Mp = D->Mp, n1 = D->n1;
+  const size_t plane = (size_t)Mp * Mp;
+  // base right-hand side: f-tilde everywhere, or zero off the irregular nodes
+  if (ft) {
+    KFBI_CUDA(cudaMemcpyAsync(D->d_R, ft, P * plane * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    D->rhs_sparse_planes = 0;
+  } else if (D->rhs_sparse_planes < P) {
+    KFBI_CUDA(cudaMemsetAsync(D->d_R, 0, 2 * plane * sizeof(double), st));
+    D->rhs_sparse_planes = 2;
+  }
+  if (D->n_irr > 0) {
+    if (C)
+      KFBI_LAUNCH(k_correct<true>, (D->n_irr + 127) / 128, 128, 0, st, D->d_R, plane, ft,
+                  D->d_irr_off, D->d_arm_start, D->d_arm_k0, D->d_arm_alpha, D->d_arm_beta,
+                  D->d_arm_fidx, D->d_arm_fcoef, D->n_irr, D->n_arms, D->nb, phi, ps, kre, kim);
+    else
+      KFBI_LAUNCH(k_correct<false>, (D->n_irr + 127) / 128, 128, 0, st, D->d_R, plane, ft,
+                  D->d_irr_off, D->d_arm_start, D->d_arm_k0, D->d_arm_alpha, D->d_arm_beta,
+                  D->d_arm_fidx, D->d_arm_fcoef, D->n_irr, D->n_arms, D->nb, phi, ps, kre, kim);
+  }
+  dim3 gg(Mp / 64, Mp / 64, P);
+  KFBI_LAUNCH(k_dgemm_t, gg, 256, 0, st, D->d_R, D->d_S, D->d_T, Mp);
+  KFBI_LAUNCH(k_dgemm_t, gg, 256, 0, st, D->d_T, D->d_S, D->d_U, Mp);
+  const double scale = (2.0 / D->M) * (2.0 / D->M);
+  KFBI_LAUNCH(k_eigscale, grid_for(plane, 256), 256, 0, st, D->d_U, plane, Mp, n1, D->d_lam, kre,
+              kim, scale, C ? 1 : 0);
+  KFBI_LAUNCH(k_dgemm_t, gg, 256, 0, st, D->d_U, D->d_S, D->d_T, Mp);
+  KFBI_LAUNCH(k_dgemm_t, gg, 256, 0, st, D->d_T, D->d_S, D->d_U, Mp);
+  if (out) {
+    if (C)
+      KFBI_LAUNCH(k_extract<true>, (D->nb + 127) / 128, 128, 0, st, D->d_U, plane, ft,
+                  D->d_node_gidx, D->d_node_w, D->d_node_a, D->d_node_b, D->d_node_fidx,
+                  D->d_node_fcoef, D->nb, phi, ps, kre, kim, out, os);
+    else
+      KFBI_LAUNCH(k_extract<false>, (D->nb + 127) / 128, 128, 0, st, D->d_U, plane, ft,
+                  D->d_node_gidx, D->d_node_w, D->d_node_a, D->d_node_b, D->d_node_fidx,
+                  D->d_node_fcoef, D->nb, phi, ps, kre, kim, out, os);
+  }
+  KFBI_CHECK_LAUNCH();
+}
+
+void pad_mask(kfbi_domain* D, const double* src, double* dst, bool C, cudaStream_t st) {
+  const size_t plane = (size_t)D->Mp * D->Mp;
+  if (C)
+    KFBI_LAUNCH(k_pad_mask<true>, grid_for(plane, 256), 256, 0, st, src, D->d_mask, dst, D->n1, D->Mp);
+  else
+    KFBI_LAUNCH(k_pad_mask<false>, grid_for(plane, 256), 256, 0, st, src, D->d_mask, dst, D->n1, D->Mp);
+  KFBI_CHECK_LAUNCH();
+}
+
+void unpad(kfbi_domain* D, const double* src, double* dst, bool C, cudaStream_t st) {
+  const size_t n = (size_t)D->n1 * D->n1;
+  if (C)
+    KFBI_LAUNCH(k_unpad<true>, grid_for(n, 256), 256, 0, st, src, dst, D->n1, D->Mp);
+  else
+    KFBI_LAUNCH(k_unpad<false>, grid_for(n, 256), 256, 0, st, src, dst, D->n1, D->Mp);
+  KFBI_CHECK_LAUNCH();
+}
+
+}  // namespace kfbi
+
+using namespace kfbi;
+
+extern "C" {
+
+kfbi_status kfbi_create_domain(const kfbi_domain_desc* desc, void* stream, kfbi_domain** out) {
+  if (!out) return KFBI_ERR_ARG;
+  *out = nullptr;
+  if (!desc) {
+    set_global_error("desc is NULL");
+    return KFBI_ERR_ARG;
+  }
+  if (desc->precision != KFBI_FP64 && desc->precision != KFBI_MIXED_TF32) {
+    set_global_error("unknown precision");
+    return KFBI_ERR_ARG;
+  }
+  if (desc->gmres_restart < 1 || desc->gmres_restart > 64 || desc->gmres_maxit < 1 ||
+      !(desc->gmres_tol > 0.0)) {
+    set_global_error("GMRES parameters out of range (1 <= restart <= 64, maxit >= 1, tol > 0)");
+    return KFBI_ERR_ARG;
+  }
+  Plan plan;
+  std::string err;
+  kfbi_status s = build_plan(*desc, plan, err);
+  if (s != KFBI_OK) {
+    set_global_error(err);
+    return s;
+  }
+  kfbi_domain* D = new (std::nothrow) kfbi_domain();
+  if (!D) return KFBI_ERR_OOM;
+  D->desc = *desc;
+  D->M = plan.M;
+  D->nb = plan.nb;
+  D->n1 = plan.n1;
+  D->Mp = ((plan.n1 + 127) / 128) * 128;
+  D->h = plan.h;
+  D->lo = plan.lo;
+  cudaStream_t st = (cudaStream_t)stream;
+  s = guarded(nullptr, [&]() -> kfbi_status {
+    KFBI_CUDA(cudaGetDevice(&D->device));
+    upload_domain(D, plan);
+    gmres_alloc(D);
+    if (desc->precision == KFBI_MIXED_TF32) D->tc = tc_create(D);
+    KFBI_CUDA(cudaStreamSynchronize(st));
+    return KFBI_OK;
+  });
+  if (s != KFBI_OK) {
+    free_domain(D);
+    return s;
+  }
+  *out = D;
+  return KFBI_OK;
+}
+
+void kfbi_destroy_domain(kfbi_domain* dom) {
+  if (!dom) return;
+  cudaDeviceSynchronize();
+  free_domain(dom);
+}
+
+kfbi_status kfbi_apply_operator(kfbi_domain* dom, double kappa_re, double kappa_im,
+                                const void* phi_dev, const void* f_dev, void* out_dev,
+                                void* stream) {
+  if (!dom) return KFBI_ERR_ARG;
+  if (!phi_dev || !out_dev) {
+    dom->err = "phi_dev and out_dev must be device pointers";
+    return KFBI_ERR_ARG;
+  }
+  return guarded(dom, [&]() -> kfbi_status {
+    cudaStream_t st = (cudaStream_t)stream;
+    const bool C = kappa_im != 0.0;
+    const double* ft = nullptr;
+    if (f_dev) {
+      pad_mask(dom, (const double*)f_dev, dom->d_fpad, C, st);
+      ft = dom->d_fpad;
+    }
+    apply_internal(dom, kappa_re, kappa_im, (const double*)phi_dev, C ? 2 : 1, ft,
+                   (double*)out_dev, C ? 2 : 1, false, st);
+    return KFBI_OK;
+  });
+}
+
+kfbi_status kfbi_interface_solve(kfbi_domain* dom, double kappa_re, double kappa_im,
+                                 const void* phi_dev, const void* f_dev, void* u_grid_dev,
+                                 void* u_plus_dev, void* stream) {
+  if (!dom) return KFBI_ERR_ARG;
+  if (!phi_dev || !u_grid_dev) {
+    dom->err = "phi_dev and u_grid_dev must be device pointers";
+    return KFBI_ERR_ARG;
+  }
+  return guarded(dom, [&]() -> kfbi_status {
+    cudaStream_t st = (cudaStream_t)stream;
+    const bool C = kappa_im != 0.0;
+    const double* ft = nullptr;
+    if (f_dev) {
+      pad_mask(dom, (const double*)f_dev, dom->d_fpad, C, st);
+      ft = dom->d_fpad;
+    }
+    apply_internal(dom, kappa_re, kappa_im, (const double*)phi_dev, C ? 2 : 1, ft,
+                   (double*)u_plus_dev, C ? 2 : 1, true, st);
+    unpad(dom, dom->d_U, (double*)u_grid_dev, C, st);
+    return KFBI_OK;
+  });
+}
+
+const char* kfbi_last_error(const kfbi_domain* dom) { return dom ? dom->err.c_str() : ""; }
+
+const char* kfbi_last_global_error(void) {
+  std::lock_guard<std::mutex> lk(g_err_mu);
+  static thread_local std::string copy;
+  copy = g_err;
+  return copy.c_str();
+}
+
+long long kfbi_launch_count(void) { return g_launches.load(); }
+
+long long kfbi_domain_device_bytes(const kfbi_domain* dom) {
+  if (!dom) return 0;
+  return dom->bytes + (dom->tc ? tc_bytes(dom->tc) : 0);
+}
+
+// ---- host-only plan ---------------------------------------------------------
+
+struct kfbi_plan {
+  Plan p;
+};
+
+kfbi_status kfbi_plan_create(const kfbi_domain_desc* desc, kfbi_plan** out) {
+  if (!out || !desc) return KFBI_ERR_ARG;
+  *out = nullptr;
+  kfbi_plan* pl = new (std::nothrow) kfbi_plan();
+  if (!pl) return KFBI_ERR_OOM;
+  std::string err;
+  kfbi_status s = build_plan(*desc, pl->p, err);
+  if (s != KFBI_OK) {
+    set_global_error(err);
+    delete pl;
+    return s;
+  }
+  *out = pl;
+  return KFBI_OK;
+}
+
+void kfbi_plan_destroy(kfbi_plan* plan) { delete plan; }
+
+long long kfbi_plan_size(const kfbi_plan* plan, int field) {
+  if (!plan) return -1;
+  const Plan& P = plan->p;
+  switch (field) {
+    case KFBI_PLAN_N_EDGES: return P.n_edges();
+    case KFBI_PLAN_EDGE_I: case KFBI_PLAN_EDGE_J: case KFBI_PLAN_EDGE_DIR:
+    case KFBI_PLAN_EDGE_COORD: case KFBI_PLAN_EDGE_THETA: return P.n_edges();
+    case KFBI_PLAN_INSIDE: return (long long)P.inside.size();
+    case KFBI_PLAN_N_IRREGULAR: return P.n_irr();
+    case KFBI_PLAN_IRREGULAR: return P.n_irr();
+    case KFBI_PLAN_N_ARMS: return P.n_arms();
+    case KFBI_PLAN_ARM_NODE: case KFBI_PLAN_ARM_K0: return P.n_arms();
+    case KFBI_PLAN_ARM_ALPHA: case KFBI_PLAN_ARM_BETA: return (long long)P.n_arms() * 6;
+    case KFBI_PLAN_ARM_FIDX: case KFBI_PLAN_ARM_FCOEF: return (long long)P.n_arms() * 2;
+    case KFBI_PLAN_NODE_GIDX: case KFBI_PLAN_NODE_W: case KFBI_PLAN_NODE_A:
+    case KFBI_PLAN_NODE_B: return (long long)P.nb * 6;
+    case KFBI_PLAN_NODE_FIDX: case KFBI_PLAN_NODE_FCOEF: return P.nb;
+    default: return -1;
+  }
+}
+
+kfbi_status kfbi_plan_export(const kfbi_plan* plan, int field, void* dst) {
+  if (!plan || !dst) return KFBI_ERR_ARG;
+  const Plan& P = plan->p;
+  auto cp = [&](const auto& v) {
+    std::memcpy(dst, v.data(), v.size() * sizeof(v[0]));
+    return KFBI_OK;
+  };
+  switch (field) {
+    case KFBI_PLAN_EDGE_I: return cp(P.e_i);
+    case KFBI_PLAN_EDGE_J: return cp(P.e_j);
+    case KFBI_PLAN_EDGE_DIR: return cp(P.e_dir);
+    case KFBI_PLAN_EDGE_COORD: return cp(P.e_coord);
+    case KFBI_PLAN_EDGE_THETA: return cp(P.e_theta);
+    case KFBI_PLAN_INSIDE: return cp(P.inside);
+    case KFBI_PLAN_IRREGULAR: return cp(P.irr);
+    case KFBI_PLAN_ARM_NODE: return cp(P.arm_node);
+    case KFBI_PLAN_ARM_K0: return cp(P.arm_k0);
+    case KFBI_PLAN_ARM_ALPHA: return cp(P.arm_alpha);
+    case KFBI_PLAN_ARM_BETA: return cp(P.arm_beta);
+    case KFBI_PLAN_ARM_FIDX: return cp(P.arm_fidx);
+    case KFBI_PLAN_ARM_FCOEF: return cp(P.arm_fcoef);
+    case KFBI_PLAN_NODE_GIDX: return cp(P.node_gidx);
+    case KFBI_PLAN_NODE_W: return cp(P.node_w);
+    case KFBI_PLAN_NODE_A: return cp(P.node_a);
+    case KFBI_PLAN_NODE_B: return cp(P.node_b);
+    case KFBI_PLAN_NODE_FIDX: return cp(P.node_fidx);
+    case KFBI_PLAN_NODE_FCOEF: return cp(P.node_fcoef);
+    default: return KFBI_ERR_ARG;
+  }
+}
+
+}  // extern "C"

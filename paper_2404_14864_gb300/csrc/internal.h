@@ -1,0 +1,201 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cstdint>
+#include <new>
+#include <stdexcept>
+#include <string>
+
+#include "kfbi.h"
+#include "plan.h"
+
+namespace kfbi {
+
+// Count of kernel launches issued by the library (kfbi_launch_count).
+extern std::atomic<long long> g_launches;
+// Message of the last failure not tied to a domain.
+void set_global_error(const std::string& s);
+
+// Launch a kernel and count it.
+#define KFBI_LAUNCH(kern, grid, block, smem, stream, ...)                              \
+  do {                                                                                  \
+    kern<<<(grid), (block), (smem), (stream)>>>(__VA_ARGS__);                           \
+    ::kfbi::g_launches.fetch_add(1, std::memory_order_relaxed);                         \
+  } while (0)
+
+struct CudaError {
+  cudaError_t code;
+  std::string where;
+};
+
+#define KFBI_CUDA(call)                                                                 \
+  do {                                                                                  \
+    cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess) throw ::kfbi::CudaError{e_, std::string(#call)};              \
+  } while (0)
+
+#define KFBI_CHECK_LAUNCH() KFBI_CUDA(cudaGetLastError())
+
+struct Status {
+  kfbi_status code;
+  std::string msg;
+};
+
+// Round to the nearest TF32 value (10 explicit mantissa bits), ties to even.
+__host__ __device__ inline float tf32_round(float x) {
+#ifdef __CUDA_ARCH__
+  uint32_t u = __float_as_uint(x);
+#else
+  uint32_t u;
+  __builtin_memcpy(&u, &x, 4);
+#endif
+  if ((u & 0x7f800000u) != 0x7f800000u) {
+    u += 0xfffu + ((u >> 13) & 1u);
+    u &= 0xffffe000u;
+  }
+#ifdef __CUDA_ARCH__
+  return __uint_as_float(u);
+#else
+  float r;
+  __builtin_memcpy(&r, &u, 4);
+  return r;
+#endif
+}
+
+struct TcDst;  // tensor-core DST engine (tc_dst.cu)
+
+}  // namespace kfbi
+
+// Device-resident domain: tables from the plan and work buffers.
+struct kfbi_domain {
+  kfbi_domain_desc desc{};
+  int M = 0, nb = 0, n1 = 0, Mp = 0;  // Mp: padded transform size (multiple of 128)
+  double h = 0, lo = 0;
+  int device = 0;
+  std::string err;
+  long long bytes = 0;
+
+  // tables (padded grid offsets row*Mp + col)
+  uint8_t* d_mask = nullptr;  // Mp*Mp, 1 = interior node inside Omega
+  int n_irr = 0, n_arms = 0;
+  int* d_irr_off = nullptr;
+  int* d_arm_start = nullptr;
+  int* d_arm_k0 = nullptr;
+  double* d_arm_alpha = nullptr;  // [m * n_arms + a]
+  double* d_arm_beta = nullptr;
+  int* d_arm_fidx = nullptr;      // [q * n_arms + a]
+  double* d_arm_fcoef = nullptr;
+  int* d_node_gidx = nullptr;     // [m * nb + k]
+  double* d_node_w = nullptr;
+  double* d_node_a = nullptr;
+  double* d_node_b = nullptr;
+  int* d_node_fidx = nullptr;
+  double* d_node_fcoef = nullptr;
+  float* d_arm_alpha32 = nullptr;  // FP32 copies for the mixed path
+  float* d_arm_beta32 = nullptr;
+  float* d_arm_fcoef32 = nullptr;
+  float* d_node_w32 = nullptr;
+  float* d_node_a32 = nullptr;
+  float* d_node_b32 = nullptr;
+  float* d_node_fcoef32 = nullptr;
+  double* d_S = nullptr;    // Mp*Mp DST-I matrix, zero padded
+  double* d_lam = nullptr;  // Mp eigenvalues (0 beyond n1)
+
+  // FP64 work buffers, two planes each (complex = re plane, im plane)
+  double* d_R = nullptr;
+  double* d_T = nullptr;
+  double* d_U = nullptr;
+  double* d_fpad = nullptr;  // caller's f converted to the padded masked layout
+  double* d_zero_nb = nullptr;  // 2*nb zeros (phi = 0)
+  int rhs_sparse_planes = 0; // planes of d_R known to be zero off the irregular nodes
+
+  // GMRES workspace (complex-interleaved vectors of length nb)
+  int restart = 0;
+  double* d_V = nullptr;    // (restart+1) * 2nb
+  double* d_W = nullptr;    // 2nb
+  double* d_X = nullptr;    // 2nb
+  double* d_B = nullptr;    // 2nb
+  double* d_H = nullptr;    // (restart+1)*restart complex, column-major
+  double* d_cs = nullptr;   // restart
+  double* d_sn = nullptr;   // restart complex
+  double* d_g = nullptr;    // restart+1 complex
+  double* d_scal = nullptr; // device scalars: [0] ||b||, [1] residual estimate, ...
+  double* h_scal = nullptr; // pinned mirror
+  cudaEvent_t ev_scal = nullptr;
+
+  kfbi::TcDst* tc = nullptr;  // mixed-precision engine (precision == KFBI_MIXED_TF32)
+};
+
+struct kfbi_state {
+  kfbi_domain* dom = nullptr;
+  int eq = 0;
+  int planes = 1;
+  double dt = 0, theta = 0.25, kre = 0, kim = 0;
+  bool initialised = false;
+  bool phi_zero = true;
+  double* d_u = nullptr;      // current field, padded planes
+  double* d_F = nullptr;      // F^{n+1} (heat, wave) or u* (Schroedinger)
+  double* d_Fprev = nullptr;  // F^n (wave)
+  double* d_ft = nullptr;     // masked f-tilde of the current solve
+  double* d_aux = nullptr;    // u** (Schroedinger)
+  double* d_phi = nullptr;    // density, complex interleaved 2nb
+  double* d_b = nullptr;      // BIE right-hand side, complex interleaved 2nb
+  double* d_ub = nullptr;     // u+ of the volume part
+};
+
+namespace kfbi {
+
+// domain.cu
+void apply_internal(kfbi_domain* D, double kre, double kim, const double* phi, int phi_stride,
+                    const double* ft, double* out, int out_stride, bool want_grid,
+                    cudaStream_t st);
+// Run f (returning kfbi_status); convert exceptions into a status and keep
+// the message on the domain (or globally when D is null).
+template <class F>
+kfbi_status guarded(kfbi_domain* D, F&& f) {
+  std::string msg;
+  kfbi_status code;
+  try {
+    return f();
+  } catch (const CudaError& e) {
+    msg = e.where + ": " + cudaGetErrorString(e.code);
+    code = (e.code == cudaErrorMemoryAllocation) ? KFBI_ERR_OOM : KFBI_ERR_CUDA;
+  } catch (const Status& s) {
+    msg = s.msg;
+    code = s.code;
+  } catch (const std::bad_alloc&) {
+    msg = "host allocation failed";
+    code = KFBI_ERR_OOM;
+  } catch (const std::exception& e) {
+    msg = e.what();
+    code = KFBI_ERR_ARG;
+  }
+  if (D)
+    D->err = msg;
+  else
+    set_global_error(msg);
+  return code;
+}
+
+// Caller layout <-> padded planes (domain.cu).
+void pad_mask(kfbi_domain* D, const double* src, double* dst, bool C, cudaStream_t st);
+void unpad(kfbi_domain* D, const double* src, double* dst, bool C, cudaStream_t st);
+int grid_for(size_t n, int block);
+
+// gmres.cu
+kfbi_status gmres_solve(kfbi_domain* D, double kre, double kim, const double* b, double* x,
+                        bool x_zero, kfbi_solve_info* info, cudaStream_t st);
+void gmres_alloc(kfbi_domain* D);
+void gmres_free(kfbi_domain* D);
+
+// tc_dst.cu (mixed path)
+TcDst* tc_create(kfbi_domain* D);
+void tc_destroy(TcDst* tc);
+void tc_apply(kfbi_domain* D, double kre, double kim, const double* phi, int phi_stride,
+              const double* ft, double* out, int out_stride, bool want_grid, cudaStream_t st);
+long long tc_bytes(const TcDst* tc);
+
+}  // namespace kfbi

@@ -1,0 +1,418 @@
+// Time steppers (Sec. 3.1 and Procedure 3 of Sec. 3.3, arXiv 2404.14864).
+//
+// Each step solves Delta u - kappa u = -F in Omega, u = g on Gamma through
+// the Dirichlet BIE: b = g - u+[0, f-tilde], GMRES for phi (initial guess
+// = previous phi), then one interface solve with (f-tilde, phi) whose grid
+// values in Omega are u^{n+1}.  The right-hand side F is carried as its own
+// variable (Eq. 3.4 for heat; the recurrence after Eq. 3.7 for the
+// theta-scheme; u* = 2u^{n+1} - u** for the Strang step, which is the
+// backward-Euler identity Delta u^{n+1} = kappa (u^{n+1} - u**)).
+// All grid kernels are elementwise over the padded planes, in float64.
+#include <cmath>
+
+#include "internal.h"
+
+namespace kfbi {
+namespace stp {
+
+// Grid kernels walk the padded plane; (r, c) inside [0, n1)^2 map to the
+// caller's (n1 x n1) index r*n1 + c.
+#define GRID_LOOP(Mp)                                                              \
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x;                 \
+       idx < (size_t)(Mp) * (Mp); idx += (size_t)gridDim.x * blockDim.x)
+
+__global__ void k_heat_init(double* F, double* u, const double* u0, const double* lap0,
+                            const double* src, int n1, int Mp, double two_dt) {
+  GRID_LOOP(Mp) {
+    const int r = (int)(idx / Mp), c = (int)(idx % Mp);
+    double f = 0.0, uu = 0.0;
+    if (r < n1 && c < n1) {
+      const size_t s = (size_t)r * n1 + c;
+      uu = u0[s];
+      f = two_dt * uu + lap0[s] + (src ? src[s] : 0.0);
+    }
+    F[idx] = f;
+    u[idx] = uu;
+  }
+}
+
+__global__ void k_wave_init(double* F, double* Fprev, double* u, const double* u0,
+                            const double* lap0, const double* u1, const double* lap1, int n1,
+                            int Mp, double kappa, double c1) {
+  GRID_LOOP(Mp) {
+    const int r = (int)(idx / Mp), c = (int)(idx % Mp);
+    double f = 0.0, fp = 0.0, uu = 0.0;
+    if (r < n1 && c < n1) {
+      const size_t s = (size_t)r * n1 + c;
+      uu = u1[s];
+      fp = kappa * u1[s] - lap1[s];
+      f = kappa * (2.0 * u1[s] - u0[s]) + c1 * lap1[s] + lap0[s];
+    }
+    F[idx] = f;
+    Fprev[idx] = fp;
+    u[idx] = uu;
+  }
+}
+
+// u* = u0 - i (dt/2) lap u0 (Step 1 of the Strang step), u = u0.
+__global__ void k_schr_init(double* ustar, double* u, const double* u0, const double* lap0,
+                            int n1, int Mp, double half_dt) {
+  const size_t plane = (size_t)Mp * Mp;
+  GRID_LOOP(Mp) {
+    const int r = (int)(idx / Mp), c = (int)(idx % Mp);
+    double ur = 0, ui = 0, sr = 0, si = 0;
+    if (r < n1 && c < n1) {
+      const size_t s = (size_t)r * n1 + c;
+      ur = u0[2 * s];
+      ui = u0[2 * s + 1];
+      // -i (dt/2) (lr + i li) = (dt/2) li - i (dt/2) lr
+      sr = ur + half_dt * lap0[2 * s + 1];
+      si = ui - half_dt * lap0[2 * s];
+    }
+    u[idx] = ur;
+    u[plane + idx] = ui;
+    ustar[idx] = sr;
+    ustar[plane + idx] = si;
+  }
+}
+
+// f-tilde = -F on Omega, 0 outside (Eq. 3.25 with f = -F).
+__global__ void k_make_ft(double* ft, const double* F, const uint8_t* mask, int Mp) {
+  GRID_LOOP(Mp) { ft[idx] = mask[idx] ? -F[idx] : 0.0; }
+}
+
+// Pointwise Crank-Nicolson step of Eq. 3.10 with w = 0:
+// u** = (1 - i a)/(1 + i a) u*, a = dt v / 2; and f-tilde = -kappa u** on
+// Omega with kappa = i kim (Eq. 3.12: Delta u - kappa u = -kappa u**).
+__global__ void k_schr_bstep(double* uss, double* ft, const double* ustar, const double* v,
+                             const uint8_t* mask, int n1, int Mp, double half_dt, double kim) {
+  const size_t plane = (size_t)Mp * Mp;
+  GRID_LOOP(Mp) {
+    const int r = (int)(idx / Mp), c = (int)(idx % Mp);
+    double xr = 0, xi = 0;
+    if (r < n1 && c < n1) {
+      const double a = half_dt * v[(size_t)r * n1 + c];
+      const double den = 1.0 / (1.0 + a * a);
+      const double pr = (1.0 - a * a) * den, pi = -2.0 * a * den;
+      const double sr = ustar[idx], si = ustar[plane + idx];
+      xr = pr * sr - pi * si;
+      xi = pr * si + pi * sr;
+    }
+    uss[idx] = xr;
+    uss[plane + idx] = xi;
+    // -kappa u** = -i kim (xr + i xi) = kim xi - i kim xr
+    const bool in = mask[idx] != 0;
+    ft[idx] = in ? kim * xi : 0.0;
+    ft[plane + idx] = in ? -kim * xr : 0.0;
+  }
+}
+
+// b = g - u+[0, f-tilde], complex interleaved; g is real unless C.
+__global__ void k_make_b(double* b, const double* g, const double* ub, int nb, int C) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nb) return;
+  const double gr = C ? g[2 * k] : g[k], gi = C ? g[2 * k + 1] : 0.0;
+  b[2 * k] = gr - ub[2 * k];
+  b[2 * k + 1] = gi - ub[2 * k + 1];
+}
+
+// Heat: u = U; F^{n+2} = (4/dt) U - F^{n+1} + src.
+__global__ void k_heat_update(double* u, double* F, const double* U, const double* src, int n1,
+                              int Mp, double four_dt) {
+  GRID_LOOP(Mp) {
+    const int r = (int)(idx / Mp), c = (int)(idx % Mp);
+    const double uu = U[idx];
+    double f = four_dt * uu - F[idx];
+    if (src && r < n1 && c < n1) f += src[(size_t)r * n1 + c];
+    u[idx] = uu;
+    F[idx] = f;
+  }
+}
+
+// Wave: F^{n+2} = (kappa/theta) U - ((1-2theta)/theta) F^{n+1} - F^n.
+__global__ void k_wave_update(double* u, double* F, double* Fprev, const double* U, int Mp,
+                              double k_theta, double c1) {
+  GRID_LOOP(Mp) {
+    const double uu = U[idx], f = F[idx];
+    const double fn = k_theta * uu - c1 * f - Fprev[idx];
+    Fprev[idx] = f;
+    F[idx] = fn;
+    u[idx] = uu;
+  }
+}
+
+// Strang: u = U; next u* = 2 U - u**.
+__global__ void k_schr_update(double* u, double* ustar, const double* U, const double* uss,
+                              int Mp) {
+  const size_t plane = (size_t)Mp * Mp;
+  GRID_LOOP(Mp) {
+    for (int p = 0; p < 2; ++p) {
+      const size_t q = p * plane + idx;
+      u[q] = U[q];
+      ustar[q] = 2.0 * U[q] - uss[q];
+    }
+  }
+}
+
+__global__ void k_copy_phi(const double* src, double* dst, int nb, int C) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nb) return;
+  if (C) {
+    dst[2 * k] = src[2 * k];
+    dst[2 * k + 1] = src[2 * k + 1];
+  } else {
+    dst[k] = src[2 * k];
+  }
+}
+
+}  // namespace stp
+
+using namespace stp;
+
+// One BIE solve of the step: b = g - u+[0, ft], GMRES for phi, then the grid
+// solution of Eq. 3.30 with (ft, phi) in D->d_U.
+static kfbi_status solve_step(kfbi_domain* D, kfbi_state* S, const double* g, bool gC,
+                              kfbi_solve_info* info, cudaStream_t st) {
+  const int nb = D->nb;
+  apply_internal(D, S->kre, S->kim, D->d_zero_nb, 2, S->d_ft, S->d_ub, 2, false, st);
+  KFBI_LAUNCH(k_make_b, (nb + 255) / 256, 256, 0, st, S->d_b, g, S->d_ub, nb, gC ? 1 : 0);
+  KFBI_CHECK_LAUNCH();
+  kfbi_solve_info loc{};
+  kfbi_status s = gmres_solve(D, S->kre, S->kim, S->d_b, S->d_phi, S->phi_zero, &loc, st);
+  S->phi_zero = false;
+  loc.applications += 2;
+  if (info) *info = loc;
+  if (s != KFBI_OK) return s;
+  apply_internal(D, S->kre, S->kim, S->d_phi, 2, S->d_ft, nullptr, 2, true, st);
+  return KFBI_OK;
+}
+
+}  // namespace kfbi
+
+using namespace kfbi;
+
+extern "C" {
+
+kfbi_status kfbi_state_create(kfbi_domain* dom, int equation, kfbi_state** out) {
+  if (!dom || !out) return KFBI_ERR_ARG;
+  *out = nullptr;
+  if (equation < KFBI_HEAT || equation > KFBI_SCHRODINGER) {
+    dom->err = "unknown equation";
+    return KFBI_ERR_ARG;
+  }
+  kfbi_state* S = new (std::nothrow) kfbi_state();
+  if (!S) return KFBI_ERR_OOM;
+  S->dom = dom;
+  S->eq = equation;
+  S->planes = equation == KFBI_SCHRODINGER ? 2 : 1;
+  kfbi_status s = guarded(dom, [&]() -> kfbi_status {
+    const size_t plane = (size_t)dom->Mp * dom->Mp * S->planes;
+    const size_t nb2 = 2 * (size_t)dom->nb;
+    KFBI_CUDA(cudaMalloc(&S->d_u, plane * sizeof(double)));
+    KFBI_CUDA(cudaMalloc(&S->d_F, plane * sizeof(double)));
+    KFBI_CUDA(cudaMalloc(&S->d_ft, plane * sizeof(double)));
+    if (equation == KFBI_WAVE) KFBI_CUDA(cudaMalloc(&S->d_Fprev, plane * sizeof(double)));
+    if (equation == KFBI_SCHRODINGER) KFBI_CUDA(cudaMalloc(&S->d_aux, plane * sizeof(double)));
+    KFBI_CUDA(cudaMalloc(&S->d_phi, nb2 * sizeof(double)));
+    KFBI_CUDA(cudaMalloc(&S->d_b, nb2 * sizeof(double)));
+    KFBI_CUDA(cudaMalloc(&S->d_ub, nb2 * sizeof(double)));
+    KFBI_CUDA(cudaMemset(S->d_phi, 0, nb2 * sizeof(double)));
+    return KFBI_OK;
+  });
+  if (s != KFBI_OK) {
+    kfbi_state_destroy(S);
+    return s;
+  }
+  *out = S;
+  return KFBI_OK;
+}
+
+void kfbi_state_destroy(kfbi_state* S) {
+  if (!S) return;
+  cudaDeviceSynchronize();
+  double* ptrs[] = {S->d_u, S->d_F, S->d_Fprev, S->d_ft, S->d_aux, S->d_phi, S->d_b, S->d_ub};
+  for (double* p : ptrs)
+    if (p) cudaFree(p);
+  delete S;
+}
+
+static kfbi_status check_state(kfbi_state* S, int eq) {
+  if (!S || !S->dom) return KFBI_ERR_ARG;
+  if (S->eq != eq) {
+    S->dom->err = "state was created for another equation";
+    return KFBI_ERR_ARG;
+  }
+  return KFBI_OK;
+}
+
+kfbi_status kfbi_state_init_heat(kfbi_state* S, double dt, const double* u0, const double* lap0,
+                                 const double* src, void* stream) {
+  kfbi_status c = check_state(S, KFBI_HEAT);
+  if (c != KFBI_OK) return c;
+  kfbi_domain* D = S->dom;
+  if (!(dt > 0.0) || !u0 || !lap0) {
+    D->err = "dt > 0 and u0, lap_u0 are required";
+    return KFBI_ERR_ARG;
+  }
+  return guarded(D, [&]() -> kfbi_status {
+    cudaStream_t st = (cudaStream_t)stream;
+    S->dt = dt;
+    S->kre = 2.0 / dt;
+    S->kim = 0.0;
+    const size_t plane = (size_t)D->Mp * D->Mp;
+    KFBI_LAUNCH(k_heat_init, grid_for(plane, 256), 256, 0, st, S->d_F, S->d_u, u0, lap0, src,
+                D->n1, D->Mp, 2.0 / dt);
+    KFBI_CHECK_LAUNCH();
+    KFBI_CUDA(cudaMemsetAsync(S->d_phi, 0, 2 * (size_t)D->nb * sizeof(double), st));
+    S->phi_zero = true;
+    S->initialised = true;
+    return KFBI_OK;
+  });
+}
+
+kfbi_status kfbi_state_init_wave(kfbi_state* S, double dt, double theta, const double* u0,
+                                 const double* lap0, const double* u1, const double* lap1,
+                                 void* stream) {
+  kfbi_status c = check_state(S, KFBI_WAVE);
+  if (c != KFBI_OK) return c;
+  kfbi_domain* D = S->dom;
+  if (!(dt > 0.0) || !(theta > 0.0) || !u0 || !lap0 || !u1 || !lap1) {
+    D->err = "dt > 0, theta > 0 and u0, lap_u0, u1, lap_u1 are required";
+    return KFBI_ERR_ARG;
+  }
+  return guarded(D, [&]() -> kfbi_status {
+    cudaStream_t st = (cudaStream_t)stream;
+    S->dt = dt;
+    S->theta = theta;
+    S->kre = 1.0 / (theta * dt * dt);
+    S->kim = 0.0;
+    const size_t plane = (size_t)D->Mp * D->Mp;
+    KFBI_LAUNCH(k_wave_init, grid_for(plane, 256), 256, 0, st, S->d_F, S->d_Fprev, S->d_u, u0,
+                lap0, u1, lap1, D->n1, D->Mp, S->kre, (1.0 - 2.0 * theta) / theta);
+    KFBI_CHECK_LAUNCH();
+    KFBI_CUDA(cudaMemsetAsync(S->d_phi, 0, 2 * (size_t)D->nb * sizeof(double), st));
+    S->phi_zero = true;
+    S->initialised = true;
+    return KFBI_OK;
+  });
+}
+
+kfbi_status kfbi_state_init_schrodinger(kfbi_state* S, double dt, const void* u0,
+                                        const void* lap0, void* stream) {
+  kfbi_status c = check_state(S, KFBI_SCHRODINGER);
+  if (c != KFBI_OK) return c;
+  kfbi_domain* D = S->dom;
+  if (!(dt > 0.0) || !u0 || !lap0) {
+    D->err = "dt > 0 and u0, lap_u0 are required";
+    return KFBI_ERR_ARG;
+  }
+  return guarded(D, [&]() -> kfbi_status {
+    cudaStream_t st = (cudaStream_t)stream;
+    S->dt = dt;
+    S->kre = 0.0;
+    S->kim = 2.0 / dt;
+    const size_t plane = (size_t)D->Mp * D->Mp;
+    KFBI_LAUNCH(k_schr_init, grid_for(plane, 256), 256, 0, st, S->d_F, S->d_u,
+                (const double*)u0, (const double*)lap0, D->n1, D->Mp, 0.5 * dt);
+    KFBI_CHECK_LAUNCH();
+    KFBI_CUDA(cudaMemsetAsync(S->d_phi, 0, 2 * (size_t)D->nb * sizeof(double), st));
+    S->phi_zero = true;
+    S->initialised = true;
+    return KFBI_OK;
+  });
+}
+
+kfbi_status kfbi_step_heat(kfbi_domain* dom, kfbi_state* S, const double* g_next,
+                           const double* src_sum_next, kfbi_solve_info* info, void* stream) {
+  kfbi_status c = check_state(S, KFBI_HEAT);
+  if (c != KFBI_OK) return c;
+  if (!dom || dom != S->dom || !g_next || !S->initialised) {
+    if (dom) dom->err = "step needs the state's domain, g_next and an initialised state";
+    return KFBI_ERR_ARG;
+  }
+  return guarded(dom, [&]() -> kfbi_status {
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t plane = (size_t)dom->Mp * dom->Mp;
+    KFBI_LAUNCH(k_make_ft, grid_for(plane, 256), 256, 0, st, S->d_ft, S->d_F, dom->d_mask, dom->Mp);
+    KFBI_CHECK_LAUNCH();
+    kfbi_status s = solve_step(dom, S, g_next, false, info, st);
+    if (s != KFBI_OK) return s;
+    KFBI_LAUNCH(k_heat_update, grid_for(plane, 256), 256, 0, st, S->d_u, S->d_F, dom->d_U,
+                src_sum_next, dom->n1, dom->Mp, 4.0 / S->dt);
+    KFBI_CHECK_LAUNCH();
+    KFBI_CUDA(cudaStreamSynchronize(st));
+    return KFBI_OK;
+  });
+}
+
+kfbi_status kfbi_step_wave(kfbi_domain* dom, kfbi_state* S, const double* g_next,
+                           kfbi_solve_info* info, void* stream) {
+  kfbi_status c = check_state(S, KFBI_WAVE);
+  if (c != KFBI_OK) return c;
+  if (!dom || dom != S->dom || !g_next || !S->initialised) {
+    if (dom) dom->err = "step needs the state's domain, g_next and an initialised state";
+    return KFBI_ERR_ARG;
+  }
+  return guarded(dom, [&]() -> kfbi_status {
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t plane = (size_t)dom->Mp * dom->Mp;
+    KFBI_LAUNCH(k_make_ft, grid_for(plane, 256), 256, 0, st, S->d_ft, S->d_F, dom->d_mask, dom->Mp);
+    KFBI_CHECK_LAUNCH();
+    kfbi_status s = solve_step(dom, S, g_next, false, info, st);
+    if (s != KFBI_OK) return s;
+    KFBI_LAUNCH(k_wave_update, grid_for(plane, 256), 256, 0, st, S->d_u, S->d_F, S->d_Fprev,
+                dom->d_U, dom->Mp, S->kre / S->theta, (1.0 - 2.0 * S->theta) / S->theta);
+    KFBI_CHECK_LAUNCH();
+    KFBI_CUDA(cudaStreamSynchronize(st));
+    return KFBI_OK;
+  });
+}
+
+kfbi_status kfbi_step_schrodinger(kfbi_domain* dom, kfbi_state* S, const double* v, double w,
+                                  const void* g_next, kfbi_solve_info* info, void* stream) {
+  kfbi_status c = check_state(S, KFBI_SCHRODINGER);
+  if (c != KFBI_OK) return c;
+  if (!dom || dom != S->dom || !g_next || !v || !S->initialised) {
+    if (dom) dom->err = "step needs the state's domain, v, g_next and an initialised state";
+    return KFBI_ERR_ARG;
+  }
+  if (w != 0.0) {
+    dom->err = "the nonlinear Strang B step (w != 0) is not built";
+    return KFBI_ERR_UNSUPPORTED;
+  }
+  return guarded(dom, [&]() -> kfbi_status {
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t plane = (size_t)dom->Mp * dom->Mp;
+    KFBI_LAUNCH(k_schr_bstep, grid_for(plane, 256), 256, 0, st, S->d_aux, S->d_ft, S->d_F, v,
+                dom->d_mask, dom->n1, dom->Mp, 0.5 * S->dt, S->kim);
+    KFBI_CHECK_LAUNCH();
+    kfbi_status s = solve_step(dom, S, (const double*)g_next, true, info, st);
+    if (s != KFBI_OK) return s;
+    KFBI_LAUNCH(k_schr_update, grid_for(plane, 256), 256, 0, st, S->d_u, S->d_F, dom->d_U,
+                S->d_aux, dom->Mp);
+    KFBI_CHECK_LAUNCH();
+    KFBI_CUDA(cudaStreamSynchronize(st));
+    return KFBI_OK;
+  });
+}
+
+kfbi_status kfbi_state_get_u(kfbi_state* S, void* u_out, void* stream) {
+  if (!S || !S->dom || !u_out) return KFBI_ERR_ARG;
+  return guarded(S->dom, [&]() -> kfbi_status {
+    unpad(S->dom, S->d_u, (double*)u_out, S->planes == 2, (cudaStream_t)stream);
+    return KFBI_OK;
+  });
+}
+
+kfbi_status kfbi_state_get_phi(kfbi_state* S, void* phi_out, void* stream) {
+  if (!S || !S->dom || !phi_out) return KFBI_ERR_ARG;
+  return guarded(S->dom, [&]() -> kfbi_status {
+    const int nb = S->dom->nb;
+    KFBI_LAUNCH(k_copy_phi, (nb + 255) / 256, 256, 0, (cudaStream_t)stream, S->d_phi,
+                (double*)phi_out, nb, S->planes == 2 ? 1 : 0);
+    KFBI_CHECK_LAUNCH();
+    return KFBI_OK;
+  });
+}
+
+}  // extern "C"

@@ -1,0 +1,347 @@
+"""Thin ctypes binding of the KFBI C ABI (``include/kfbi.h``).
+
+Argument marshalling only: every step of the operator application and of
+the time steppers runs in the library's CUDA kernels.  Device buffers are
+torch CUDA tensors (float64 or complex128, contiguous); streams are torch
+CUDA streams (default: the current stream).  The library must have been
+built (``paper_2404_14864_gb300.build.build()``); there is no fallback.
+"""
+
+import ctypes
+import math
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libkfbi.so")
+
+KFBI_OK = 0
+STATUS_NAMES = {0: "KFBI_OK", 1: "KFBI_ERR_ARG", 2: "KFBI_ERR_GEOMETRY", 3: "KFBI_ERR_OOM",
+                4: "KFBI_ERR_NOT_CONVERGED", 5: "KFBI_ERR_NONFINITE", 6: "KFBI_ERR_TIMEOUT",
+                7: "KFBI_ERR_CUDA", 8: "KFBI_ERR_UNSUPPORTED"}
+KFBI_FP64, KFBI_MIXED_TF32 = 0, 1
+KFBI_CURVE_POLAR, KFBI_CURVE_ELLIPSE = 0, 1
+KFBI_HEAT, KFBI_WAVE, KFBI_SCHRODINGER = 0, 1, 2
+
+PLAN_FIELDS = {
+    "edge_i": (1, np.int32), "edge_j": (2, np.int32), "edge_dir": (3, np.int32),
+    "edge_coord": (4, np.float64), "edge_theta": (5, np.float64), "inside": (6, np.uint8),
+    "irregular": (8, np.int32), "arm_node": (10, np.int32), "arm_k0": (11, np.int32),
+    "arm_alpha": (12, np.float64), "arm_beta": (13, np.float64), "arm_fidx": (14, np.int32),
+    "arm_fcoef": (15, np.float64), "node_gidx": (16, np.int32), "node_w": (17, np.float64),
+    "node_a": (18, np.float64), "node_b": (19, np.float64), "node_fidx": (20, np.int32),
+    "node_fcoef": (21, np.float64),
+}
+
+
+class KfbiError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), msg))
+        self.status = status
+
+
+class DomainDesc(ctypes.Structure):
+    _fields_ = [("M", ctypes.c_int), ("box_lo", ctypes.c_double), ("box_hi", ctypes.c_double),
+                ("n_boundary", ctypes.c_int), ("curve_kind", ctypes.c_int),
+                ("cx", ctypes.c_double), ("cy", ctypes.c_double),
+                ("params", ctypes.c_double * 6), ("precision", ctypes.c_int),
+                ("gmres_restart", ctypes.c_int), ("gmres_tol", ctypes.c_double),
+                ("gmres_maxit", ctypes.c_int)]
+
+
+class SolveInfo(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("rel_residual", ctypes.c_double),
+                ("converged", ctypes.c_int), ("applications", ctypes.c_int)]
+
+    def as_dict(self):
+        return {"iters": self.iters, "rel_residual": self.rel_residual,
+                "converged": bool(self.converged), "applications": self.applications}
+
+
+_lib = None
+_VP = ctypes.c_void_p
+
+
+def lib():
+    """Load libkfbi.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("libkfbi.so is not built (%s); run __graft_entry__.build()" % LIB_PATH)
+    L = ctypes.CDLL(LIB_PATH)
+    S = ctypes.c_int
+    sig = {
+        "kfbi_create_domain": (S, [ctypes.POINTER(DomainDesc), _VP, ctypes.POINTER(_VP)]),
+        "kfbi_destroy_domain": (None, [_VP]),
+        "kfbi_apply_operator": (S, [_VP, ctypes.c_double, ctypes.c_double, _VP, _VP, _VP, _VP]),
+        "kfbi_interface_solve": (S, [_VP, ctypes.c_double, ctypes.c_double, _VP, _VP, _VP, _VP, _VP]),
+        "kfbi_solve_density": (S, [_VP, ctypes.c_double, ctypes.c_double, _VP, _VP,
+                                   ctypes.POINTER(SolveInfo), _VP]),
+        "kfbi_state_create": (S, [_VP, ctypes.c_int, ctypes.POINTER(_VP)]),
+        "kfbi_state_destroy": (None, [_VP]),
+        "kfbi_state_init_heat": (S, [_VP, ctypes.c_double, _VP, _VP, _VP, _VP]),
+        "kfbi_state_init_wave": (S, [_VP, ctypes.c_double, ctypes.c_double, _VP, _VP, _VP, _VP, _VP]),
+        "kfbi_state_init_schrodinger": (S, [_VP, ctypes.c_double, _VP, _VP, _VP]),
+        "kfbi_step_heat": (S, [_VP, _VP, _VP, _VP, ctypes.POINTER(SolveInfo), _VP]),
+        "kfbi_step_wave": (S, [_VP, _VP, _VP, ctypes.POINTER(SolveInfo), _VP]),
+        "kfbi_step_schrodinger": (S, [_VP, _VP, _VP, ctypes.c_double, _VP,
+                                      ctypes.POINTER(SolveInfo), _VP]),
+        "kfbi_state_get_u": (S, [_VP, _VP, _VP]),
+        "kfbi_state_get_phi": (S, [_VP, _VP, _VP]),
+        "kfbi_last_error": (ctypes.c_char_p, [_VP]),
+        "kfbi_last_global_error": (ctypes.c_char_p, []),
+        "kfbi_launch_count": (ctypes.c_longlong, []),
+        "kfbi_domain_device_bytes": (ctypes.c_longlong, [_VP]),
+        "kfbi_plan_create": (S, [ctypes.POINTER(DomainDesc), ctypes.POINTER(_VP)]),
+        "kfbi_plan_destroy": (None, [_VP]),
+        "kfbi_plan_size": (ctypes.c_longlong, [_VP, ctypes.c_int]),
+        "kfbi_plan_export": (S, [_VP, ctypes.c_int, _VP]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def exported_symbols():
+    """Names of the entry points the binding declares (all must resolve)."""
+    lib()
+    return [n for n in dir(_lib) if n.startswith("kfbi_")]
+
+
+# ----------------------------------------------------------------------------
+# descriptors
+# ----------------------------------------------------------------------------
+
+
+def make_desc(d, precision=KFBI_FP64, restart=50, tol=1e-10, maxit=500):
+    """kfbi_domain_desc from a workload dict (see ``workloads.domain_desc``)."""
+    c = d["curve"]
+    p = (ctypes.c_double * 6)()
+    if c["kind"] == "polar":
+        kind = KFBI_CURVE_POLAR
+        vals = [c["r0"], c["eps"], c["k"], c.get("phase", 0.0)]
+    elif c["kind"] == "ellipse":
+        kind = KFBI_CURVE_ELLIPSE
+        vals = [c["a"], c["b"], c["alpha"]]
+    else:
+        raise ValueError("unknown curve kind")
+    for q, v in enumerate(vals):
+        p[q] = float(v)
+    return DomainDesc(int(d["M"]), float(d["lo"]), float(d["hi"]), int(d["nb"]), kind,
+                      float(c["cx"]), float(c["cy"]), p, int(precision), int(restart),
+                      float(tol), int(maxit))
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _check(status, dom=None):
+    if status != KFBI_OK:
+        L = lib()
+        msg = L.kfbi_last_error(dom) if dom else L.kfbi_last_global_error()
+        raise KfbiError(status, (msg or b"").decode())
+
+
+def launch_count():
+    return int(lib().kfbi_launch_count())
+
+
+# ----------------------------------------------------------------------------
+# C-ABI entry points with the same names
+# ----------------------------------------------------------------------------
+
+
+def kfbi_create_domain(desc, stream=None):
+    h = ctypes.c_void_p()
+    _check(lib().kfbi_create_domain(ctypes.byref(desc), _stream(stream), ctypes.byref(h)))
+    return h
+
+
+def kfbi_destroy_domain(h):
+    lib().kfbi_destroy_domain(h)
+
+
+def kfbi_apply_operator(h, kappa, phi, f, out, stream=None):
+    k = complex(kappa)
+    _check(lib().kfbi_apply_operator(h, k.real, k.imag, _ptr(phi), _ptr(f), _ptr(out),
+                                     _stream(stream)), h)
+
+
+def kfbi_interface_solve(h, kappa, phi, f, u_grid, u_plus=None, stream=None):
+    k = complex(kappa)
+    _check(lib().kfbi_interface_solve(h, k.real, k.imag, _ptr(phi), _ptr(f), _ptr(u_grid),
+                                      _ptr(u_plus), _stream(stream)), h)
+
+
+def kfbi_solve_density(h, kappa, b, phi, stream=None):
+    k = complex(kappa)
+    info = SolveInfo()
+    _check(lib().kfbi_solve_density(h, k.real, k.imag, _ptr(b), _ptr(phi), ctypes.byref(info),
+                                    _stream(stream)), h)
+    return info.as_dict()
+
+
+class Domain:
+    """Owning wrapper of a kfbi_domain."""
+
+    def __init__(self, desc_dict, precision=KFBI_FP64, restart=50, tol=1e-10, maxit=500,
+                 stream=None):
+        self.d = dict(desc_dict)
+        self.M, self.nb = int(desc_dict["M"]), int(desc_dict["nb"])
+        self.n1 = self.M - 1
+        self.precision = precision
+        self.h = kfbi_create_domain(make_desc(desc_dict, precision, restart, tol, maxit), stream)
+
+    def close(self):
+        if self.h:
+            kfbi_destroy_domain(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def device_bytes(self):
+        return int(lib().kfbi_domain_device_bytes(self.h))
+
+    def apply_operator(self, kappa, phi, f=None, out=None, stream=None):
+        import torch
+        if out is None:
+            out = torch.empty_like(phi)
+        kfbi_apply_operator(self.h, kappa, phi, f, out, stream)
+        return out
+
+    def interface_solve(self, kappa, phi, f=None, stream=None):
+        import torch
+        dt = phi.dtype
+        U = torch.empty(self.n1 * self.n1, dtype=dt, device=phi.device)
+        up = torch.empty_like(phi)
+        kfbi_interface_solve(self.h, kappa, phi, f, U, up, stream)
+        return up, U.view(self.n1, self.n1)
+
+    def solve_density(self, kappa, b, phi, stream=None):
+        return kfbi_solve_density(self.h, kappa, b, phi, stream)
+
+
+class State:
+    """Owning wrapper of a kfbi_state (time-level fields of one equation)."""
+
+    def __init__(self, dom, equation):
+        self.dom = dom
+        self.eq = equation
+        h = ctypes.c_void_p()
+        _check(lib().kfbi_state_create(dom.h, int(equation), ctypes.byref(h)), dom.h)
+        self.h = h
+
+    def close(self):
+        if self.h:
+            lib().kfbi_state_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def init_heat(self, dt, u0, lap_u0, src_sum=None, stream=None):
+        _check(lib().kfbi_state_init_heat(self.h, float(dt), _ptr(u0), _ptr(lap_u0),
+                                          _ptr(src_sum), _stream(stream)), self.dom.h)
+
+    def init_wave(self, dt, theta, u0, lap_u0, u1, lap_u1, stream=None):
+        _check(lib().kfbi_state_init_wave(self.h, float(dt), float(theta), _ptr(u0), _ptr(lap_u0),
+                                          _ptr(u1), _ptr(lap_u1), _stream(stream)), self.dom.h)
+
+    def init_schrodinger(self, dt, u0, lap_u0, stream=None):
+        _check(lib().kfbi_state_init_schrodinger(self.h, float(dt), _ptr(u0), _ptr(lap_u0),
+                                                 _stream(stream)), self.dom.h)
+
+    def step_heat(self, g_next, src_sum_next=None, stream=None):
+        info = SolveInfo()
+        _check(lib().kfbi_step_heat(self.dom.h, self.h, _ptr(g_next), _ptr(src_sum_next),
+                                    ctypes.byref(info), _stream(stream)), self.dom.h)
+        return info.as_dict()
+
+    def step_wave(self, g_next, stream=None):
+        info = SolveInfo()
+        _check(lib().kfbi_step_wave(self.dom.h, self.h, _ptr(g_next), ctypes.byref(info),
+                                    _stream(stream)), self.dom.h)
+        return info.as_dict()
+
+    def step_schrodinger(self, v, g_next, w=0.0, stream=None):
+        info = SolveInfo()
+        _check(lib().kfbi_step_schrodinger(self.dom.h, self.h, _ptr(v), float(w), _ptr(g_next),
+                                           ctypes.byref(info), _stream(stream)), self.dom.h)
+        return info.as_dict()
+
+    def get_u(self, out=None, stream=None):
+        import torch
+        n1 = self.dom.n1
+        if out is None:
+            dt = torch.complex128 if self.eq == KFBI_SCHRODINGER else torch.float64
+            out = torch.empty(n1 * n1, dtype=dt, device="cuda")
+        _check(lib().kfbi_state_get_u(self.h, _ptr(out), _stream(stream)), self.dom.h)
+        return out.view(n1, n1)
+
+    def get_phi(self, out=None, stream=None):
+        import torch
+        if out is None:
+            dt = torch.complex128 if self.eq == KFBI_SCHRODINGER else torch.float64
+            out = torch.empty(self.dom.nb, dtype=dt, device="cuda")
+        _check(lib().kfbi_state_get_phi(self.h, _ptr(out), _stream(stream)), self.dom.h)
+        return out
+
+
+# ----------------------------------------------------------------------------
+# host-only plan (no GPU needed)
+# ----------------------------------------------------------------------------
+
+
+class Plan:
+    """The geometry and coefficient tables kfbi_create_domain would upload."""
+
+    def __init__(self, desc_dict):
+        L = lib()
+        h = ctypes.c_void_p()
+        _check(L.kfbi_plan_create(ctypes.byref(make_desc(desc_dict)), ctypes.byref(h)))
+        self.h = h
+        self.n_edges = int(L.kfbi_plan_size(h, 0))
+        self.n_irregular = int(L.kfbi_plan_size(h, 7))
+        self.n_arms = int(L.kfbi_plan_size(h, 9))
+
+    def field(self, name):
+        L = lib()
+        fid, dt = PLAN_FIELDS[name]
+        n = int(L.kfbi_plan_size(self.h, fid))
+        a = np.zeros(max(n, 1), dtype=dt)
+        _check(L.kfbi_plan_export(self.h, fid, a.ctypes.data_as(ctypes.c_void_p)))
+        return a[:n]
+
+    def close(self):
+        if self.h:
+            lib().kfbi_plan_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

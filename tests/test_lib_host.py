@@ -1,0 +1,133 @@
+"""Host-side tests of the C-ABI library (no GPU): the shared library loads
+and exports every entry point of include/kfbi.h, and the host-built plan
+(geometry and coefficient tables) agrees with the oracle."""
+
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle.interface import edge_f_gamma, node_f_gamma
+from paper_2404_14864_gb300 import kfbi, workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+DOMAINS = [
+    W.domain_desc(64, W.star()),
+    W.domain_desc(48, W.ellipse(), nb=80),
+    W.domain_desc(96, W.flower(), nb=150),
+    W.domain_desc(40, W.star(0.45, 0.12, 3, 1.1, 0.05, -0.03)),
+]
+
+
+@pytest.fixture(scope="module")
+def built():
+    from paper_2404_14864_gb300 import build
+    build.build()
+    return kfbi.lib()
+
+
+def header_functions():
+    src = open(os.path.join(ROOT, "include", "kfbi.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(kfbi_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_library_exports_every_declared_entry_point(built):
+    names = header_functions()
+    assert len(names) >= 20
+    for n in names:
+        assert hasattr(built, n), n
+    # and the binding declares the same set
+    import ctypes
+    for n in names:
+        assert isinstance(getattr(built, n), ctypes._CFuncPtr)
+
+
+def test_create_domain_errors_without_touching_the_gpu(built):
+    bad = W.domain_desc(64, W.star(0.95, 0.1, 5, 0.0))  # touches the box
+    with pytest.raises(kfbi.KfbiError) as e:
+        kfbi.Plan(bad)
+    assert e.value.status == 2
+    d = kfbi.make_desc(W.domain_desc(64, W.star()))
+    d.M = 3
+    import ctypes
+    h = ctypes.c_void_p()
+    assert built.kfbi_create_domain(ctypes.byref(d), None, ctypes.byref(h)) == 1
+    assert not h.value
+    d = kfbi.make_desc(W.domain_desc(64, W.star()))
+    d.gmres_restart = 0
+    assert built.kfbi_create_domain(ctypes.byref(d), None, ctypes.byref(h)) == 1
+
+
+@pytest.mark.parametrize("desc", DOMAINS, ids=lambda d: "%s-%d" % (d["curve"]["kind"], d["M"]))
+def test_plan_geometry_matches_oracle(built, desc):
+    p = kfbi.Plan(desc)
+    d = oracle.make_domain(desc)
+    M = desc["M"]
+    assert np.array_equal(p.field("inside").reshape(M + 1, M + 1).astype(bool), d.inside)
+    irr = np.flatnonzero(d.irregular[1:-1, 1:-1].ravel())
+    assert np.array_equal(p.field("irregular"), irr)
+    assert p.n_edges == d.n_edges and p.n_arms == 2 * d.n_edges
+    assert np.array_equal(p.field("edge_i"), d.edge_i)
+    assert np.array_equal(p.field("edge_j"), d.edge_j)
+    assert np.array_equal(p.field("edge_dir"), d.edge_dir)
+    assert np.abs(p.field("edge_coord") - d.edge_coord).max() <= 1e-13
+    assert np.abs(p.field("edge_theta") - d.edge_theta).max() <= 1e-13
+
+
+def _plan_rhs(p, desc, phi, kappa, Ft):
+    """Apply the plan's arm tables as the correction kernel does (test-only)."""
+    nb = desc["nb"]
+    n1 = desc["M"] - 1
+    f = Ft.ravel()
+    R = f.astype(np.result_type(f, phi, kappa)).copy()
+    irr = p.field("irregular")
+    node = p.field("arm_node"); k0 = p.field("arm_k0")
+    al = p.field("arm_alpha").reshape(-1, 6); be = p.field("arm_beta").reshape(-1, 6)
+    fi = p.field("arm_fidx").reshape(-1, 2); fc = p.field("arm_fcoef").reshape(-1, 2)
+    idx = (k0[:, None] + np.arange(6)[None, :]) % nb
+    contrib = ((al + kappa * be) * phi[idx]).sum(axis=1) + (fc * f[fi]).sum(axis=1)
+    acc = np.zeros(len(irr), dtype=R.dtype)
+    np.add.at(acc, node, contrib)
+    R[irr] = f[irr] + acc
+    return R.reshape(n1, n1)
+
+
+def _plan_extract(p, desc, U, phi, kappa, Ft):
+    nb = desc["nb"]
+    u = U.ravel(); f = Ft.ravel()
+    g = p.field("node_gidx").reshape(nb, 6); w = p.field("node_w").reshape(nb, 6)
+    a = p.field("node_a").reshape(nb, 6); b = p.field("node_b").reshape(nb, 6)
+    idx = (np.arange(nb)[:, None] - 2 + np.arange(6)[None, :]) % nb
+    return (w * u[g]).sum(1) + ((a + kappa * b) * phi[idx]).sum(1) + \
+        p.field("node_fcoef") * f[p.field("node_fidx")]
+
+
+@pytest.mark.parametrize("desc", DOMAINS, ids=lambda d: "%s-%d" % (d["curve"]["kind"], d["M"]))
+@pytest.mark.parametrize("kappa", [17.0, 3.5e4, 40.0j])
+def test_plan_tables_reproduce_oracle_correction_and_extraction(built, desc, kappa):
+    p = kfbi.Plan(desc)
+    d = oracle.make_domain(desc)
+    rng = np.random.default_rng(21)
+    n1 = desc["M"] - 1
+    cplx = isinstance(kappa, complex)
+    phi = np.cos(3 * d.theta) + 0.3 * np.sin(7 * d.theta) + 0.1 * rng.standard_normal(d.nb)
+    X, Y = W.grid_xy(desc)
+    Ft = np.where(d.interior_inside(), np.sin(2 * X + 1) * np.cosh(Y) * 50.0, 0.0)
+    if cplx:
+        phi = phi + 1j * np.sin(2 * d.theta)
+        Ft = Ft * (1 - 0.5j)
+    ej = oracle.jumps_at(d, d.edge_theta, phi, edge_f_gamma(d, Ft), kappa)
+    R_or = oracle.correction_rhs(d, Ft, ej)
+    R_pl = _plan_rhs(p, desc, phi, kappa, Ft)
+    scale = np.abs(R_or).max()
+    assert np.abs(R_pl - R_or).max() <= 1e-12 * scale
+    U = rng.standard_normal((n1, n1)) + (1j * rng.standard_normal((n1, n1)) if cplx else 0)
+    nj = oracle.jumps_at(d, None, phi, node_f_gamma(d, Ft), kappa, node_k=np.arange(d.nb))
+    up_or = oracle.extraction(d, U, nj)
+    up_pl = _plan_extract(p, desc, U, phi, kappa, Ft)
+    assert np.abs(up_pl - up_or).max() <= 1e-11 * max(1.0, np.abs(up_or).max())
