@@ -1,0 +1,412 @@
+#!/usr/bin/env python
+"""Benchmark: KFBI wave time stepping at 1024^2 on one GB300 per rank.
+
+Workload (one "step" = one implicit time step = the whole hot path: the
+volume-source application, GMRES with one operator application per
+iteration, the final interface solve and the F recurrence):
+  wave equation u_tt = Delta u, theta-scheme theta = 1/4, ellipse a = 0.7,
+  b = 0.4 rotated 30 deg in [-1, 1]^2, M = 1024 (1023^2 unknowns),
+  2048 boundary nodes, dt = 4h, GMRES(50) tol 1e-10, manufactured solution
+  u = cos(sqrt(2) pi t) sin(pi x) sin(pi y) for the data.
+The metric is grid-point*steps/s = M^2 * steps / seconds.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Multi-GPU (torchrun): every rank runs an independent replica (the method
+has no exchange step); value = sum over ranks; timing = max over ranks.
+"""
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("grid-point·steps/s at 1024² vs plain FP64 GPU at fixed L∞ error; "
+          "p50/p99 latency")
+UNIT = "grid-point*steps/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--M", type=int, default=1024)
+    ap.add_argument("--precision", default="tf32", choices=["tf32", "fp64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64-compare", action="store_true")
+    ap.add_argument("--cpu-steps", type=int, default=2)
+    return ap.parse_args()
+
+
+def workload(M):
+    from paper_2404_14864_gb300 import workloads as W
+    desc = W.domain_desc(M, W.ellipse(0.7, 0.4, 30.0))
+    h = (desc["hi"] - desc["lo"]) / M
+    return desc, 4.0 * h, 0.25
+
+
+def config(M, desc, dt, precision):
+    return {"workload": "wave-theta0.25-ellipse-%d" % M, "M": M, "unknowns": (M - 1) ** 2,
+            "n_boundary": desc["nb"], "dt": "4h", "theta": 0.25, "gmres": "restart 50, tol 1e-10",
+            "precision": precision, "l2": "flushed between timed steps (256 MiB write)",
+            "box": [desc["lo"], desc["hi"]]}
+
+
+# ----------------------------------------------------------------------------
+# clocks during the timed region
+# ----------------------------------------------------------------------------
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        time.sleep(0.05)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax = float(p[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, p[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ----------------------------------------------------------------------------
+# our arm
+# ----------------------------------------------------------------------------
+
+
+def run_ours(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+
+    from paper_2404_14864_gb300 import build, kfbi, workloads as W
+
+    build.build()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    M = args.M
+    desc, dt, theta = workload(M)
+    ex = W.WaveExact()
+    X, Y = W.grid_xy(desc)
+    zx, zy = W.boundary_xy(desc)
+    n1 = M - 1
+    stream = torch.cuda.current_stream()
+
+    def cu(a):
+        return torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+
+    prec = kfbi.KFBI_MIXED_TF32 if args.precision == "tf32" else kfbi.KFBI_FP64
+    note = None
+    try:
+        dom = kfbi.Domain(desc, prec, restart=50, tol=1e-10, maxit=2000)
+    except kfbi.KfbiError as e:
+        if prec == kfbi.KFBI_FP64 or e.status != 8:
+            raise
+        note = "mixed path unavailable in this build (%s); fp64 path timed" % e
+        prec = kfbi.KFBI_FP64
+        dom = kfbi.Domain(desc, prec, restart=50, tol=1e-10, maxit=2000)
+    K, Wm = args.steps, args.warmup
+    n_total = Wm + K
+    # boundary data for every step, resident on the device before timing
+    g_all = [cu(ex.u(zx, zy, (k + 2) * dt)) for k in range(n_total)]
+
+    def new_state(domain):
+        st = kfbi.State(domain, kfbi.KFBI_WAVE)
+        st.init_wave(dt, theta, cu(ex.u(X, Y, 0.0)), cu(ex.lap(X, Y, 0.0)), cu(ex.u(X, Y, dt)),
+                     cu(ex.lap(X, Y, dt)))
+        return st
+
+    # inside mask for the error norm, from the library's host-side plan
+    ins = kfbi.Plan(desc).field("inside").reshape(M + 1, M + 1)[1:-1, 1:-1].astype(bool)
+    inside = torch.from_numpy(ins.copy()).to(dev)
+
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def run_steps(st, first, count, timed, lat):
+        iters = []
+        for k in range(first, first + count):
+            if timed:
+                flush.zero_()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+            info = st.step_wave(g_all[k])
+            iters.append(info["iters"])
+            if timed:
+                e1.record(stream)
+                e1.synchronize()
+                lat.append(e0.elapsed_time(e1))
+        return iters
+
+    st = new_state(dom)
+    run_steps(st, 0, Wm, False, [])
+    torch.cuda.synchronize()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk = ClockSampler(local_rank if "CUDA_VISIBLE_DEVICES" not in os.environ
+                       else os.environ["CUDA_VISIBLE_DEVICES"].split(",")[local_rank])
+    clk.start()
+    kfbi.kfbi_profile_reset()
+    kfbi.kfbi_profile_enable(True)
+    n_launch0 = kfbi.launch_count()
+    lat = []
+    t0 = time.perf_counter()
+    iters = run_steps(st, Wm, K, True, lat)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    n_launch = kfbi.launch_count() - n_launch0
+    kfbi.kfbi_profile_enable(False)
+    prof = {kfbi.PROF_NAMES[c]: kfbi.kfbi_profile_read(c) for c in range(5)}
+    clocks = clk.stop()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    t_dev = sum(lat) / 1e3
+    t_final = (Wm + K + 1) * dt
+    u = st.get_u()
+    err = float((u - torch.from_numpy(ex.u(X, Y, t_final)).to(dev)).abs()[inside].max())
+
+    # end to end through the public API with host buffers: H2D of the step's
+    # boundary data, the step, D2H of the solution grid
+    st2 = new_state(dom)
+    g_host = [torch.from_numpy(ex.u(zx, zy, (k + 2) * dt)).pin_memory() for k in range(K)]
+    u_host = torch.empty(n1 * n1, dtype=torch.float64).pin_memory()
+    g_dev = torch.empty(desc["nb"], dtype=torch.float64, device=dev)
+    u_dev = torch.empty(n1 * n1, dtype=torch.float64, device=dev)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(K):
+        g_dev.copy_(g_host[k], non_blocking=True)
+        st2.step_wave(g_dev)
+        st2.get_u(u_dev)
+        u_host.copy_(u_dev, non_blocking=True)
+        torch.cuda.synchronize()
+    t_e2e = time.perf_counter() - t0
+    st2.close()
+
+    # the plain FP64 GPU path on the same steps, for the fixed-error comparison
+    fp64 = None
+    if prec != kfbi.KFBI_FP64 and not args.no_fp64_compare:
+        dom64 = kfbi.Domain(desc, kfbi.KFBI_FP64, restart=50, tol=1e-10, maxit=2000)
+        st64 = new_state(dom64)
+        run_steps(st64, 0, Wm, False, [])
+        lat64 = []
+        run_steps(st64, Wm, K, True, lat64)
+        u64 = st64.get_u()
+        err64 = float((u64 - torch.from_numpy(ex.u(X, Y, t_final)).to(dev)).abs()[inside].max())
+        diff = float((u64 - u).abs()[inside].max())
+        fp64 = {"value": M * M * K / (sum(lat64) / 1e3), "unit": UNIT,
+                "ms_per_step": sum(lat64) / K, "linf_vs_exact": err64,
+                "linf_mixed_minus_fp64": diff}
+        st64.close()
+        dom64.close()
+
+    out = {"t_dev": t_dev, "t_e2e": t_e2e, "lat": lat, "iters": iters, "err": err,
+           "launches": n_launch, "prof": prof, "clocks": clocks, "prec": prec, "note": note,
+           "wall": wall, "fp64": fp64, "desc": desc, "dt": dt,
+           "h2d": desc["nb"] * 8, "d2h": n1 * n1 * 8}
+    st.close()
+    dom.close()
+    return out
+
+
+def roofline(res, M):
+    """Roofline of the dominant kernel class (the DST-I pass)."""
+    n, ms = res["prof"]["dst"]
+    if n == 0:
+        return None
+    avg_s = ms / n / 1e3
+    n1 = M - 1
+    from paper_2404_14864_gb300 import kfbi
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    if res["prec"] == kfbi.KFBI_FP64:
+        flops = 2.0 * n1 ** 3  # one dense pass: (n1 x n1) times (n1 x n1)
+        return {"bound": "alu", "achieved": flops / avg_s / 1e12, "peak": 1.25,
+                "unit": "TFLOP/s", "frac": flops / avg_s / 1e12 / 1.25, "traffic": None,
+                "kernel": "k_dgemm_t (float64 DST-I pass)",
+                "peak_source": "nominal GB300 FP64 rate (1.25 TFLOP/s, profiling recipe table)",
+                "avg_launch_us": avg_s * 1e6, "launches": n}
+    flops = 3 * 2.0 * n1 ** 3  # three TF32 products per split pass
+    bf16 = peaks.get("bf16_tflops_sustained", 1700.0)
+    peak = bf16 * (1.1 / 2.25)
+    return {"bound": "tensor", "achieved": flops / avg_s / 1e12, "peak": peak, "unit": "TFLOP/s",
+            "frac": flops / avg_s / 1e12 / peak, "traffic": None,
+            "kernel": "tcgen05 TF32x3 DST-I pass",
+            "peak_source": "measured bf16 sustained x nominal tf32/bf16 ratio (1.1/2.25)",
+            "avg_launch_us": avg_s * 1e6, "launches": n}
+
+
+# ----------------------------------------------------------------------------
+# oracle (CPU baseline / reference arm)
+# ----------------------------------------------------------------------------
+
+
+def run_oracle(M, steps, budget_s=150.0):
+    import numpy as np
+
+    import oracle
+    from paper_2404_14864_gb300 import workloads as W
+    desc, dt, theta = workload(M)
+    d = oracle.make_domain(desc)
+    ex = W.WaveExact()
+    X, Y = W.grid_xy(desc)
+    zx, zy = W.boundary_xy(desc)
+    st = oracle.WaveStepper(d, dt, 1e-10)
+    st.init(ex.u(X, Y, 0.0), ex.lap(X, Y, 0.0), ex.u(X, Y, dt), ex.lap(X, Y, dt))
+    done = 0
+    t0 = time.perf_counter()
+    for k in range(steps):
+        st.step(ex.u(zx, zy, (k + 2) * dt))
+        done += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    t = time.perf_counter() - t0
+    return done, t
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    M = args.M
+    desc, dt, theta = workload(M)
+
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        k = max(1, min(args.steps, 50))
+        run_oracle(M, 1, 1e9)  # one untimed warm-up step
+        done, t = run_oracle(M, k)
+        v = M * M * done / t
+        cores = os.cpu_count()
+        line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT,
+                "n_gpus": args.gpus, "steps": done, "warmup": 1, "ms_per_step": 1e3 * t / done,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic (manufactured solution)",
+                "config": config(M, desc, dt, "fp64 CPU oracle"),
+                "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                 "sample": "%d time steps of the %d^2 wave workload after one "
+                                           "untimed step (numpy float64 oracle)" % (done, M)},
+                "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return 0
+
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+
+    res = run_ours(args, rank, world, local_rank)
+    K = args.steps
+    t_dev, t_e2e = res["t_dev"], res["t_e2e"]
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        tt = torch.tensor([t_dev, t_e2e], dtype=torch.float64, device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_dev, t_e2e = float(tt[0]), float(tt[1])
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        done, t = run_oracle(M, args.cpu_steps)
+        cpu = {"value": M * M * done / t, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+               "sample": "%d time steps of the %d^2 wave workload (numpy float64 oracle, "
+                         "BLAS threads = host cores)" % (done, M)}
+
+    if rank == 0:
+        from paper_2404_14864_gb300 import kfbi
+        lat = sorted(res["lat"])
+        p = lambda q: lat[min(len(lat) - 1, int(math.ceil(q * len(lat))) - 1)]
+        line = {
+            "metric": METRIC, "value": world * M * M * K / t_dev, "unit": UNIT, "n_gpus": world,
+            "steps": K, "warmup": args.warmup, "ms_per_step": 1e3 * t_dev / K,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if res["prec"] == kfbi.KFBI_FP64 else "tf32x3-f32acc+f64",
+            "data": "synthetic (manufactured solution)",
+            "config": config(M, desc, dt, "fp64" if res["prec"] == kfbi.KFBI_FP64 else
+                             "mixed-tf32x3"),
+            "latency_ms": {"p50": p(0.5), "p99": p(0.99), "max": lat[-1]},
+            "linf_vs_exact": res["err"],
+            "gmres_iters_per_step": res["iters"],
+            "roofline": roofline(res, M),
+            "kernel_time_ms": {k: {"launches": v[0], "ms": v[1]} for k, v in res["prof"].items()},
+            "gpu_launches": res["launches"],
+            "clocks": res["clocks"],
+            "e2e": {"value": world * M * M * K / t_e2e, "unit": UNIT,
+                    "h2d_bytes_per_step": res["h2d"], "d2h_bytes_per_step": res["d2h"]},
+            "cpu_baseline": cpu,
+            "fp64_gpu": res["fp64"],
+            "wall_s_timed": res["wall"],
+        }
+        if res["note"]:
+            line["note"] = res["note"]
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

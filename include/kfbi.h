@@ -190,6 +190,22 @@ long long kfbi_launch_count(void);
 /* Device bytes held by the domain (work buffers + tables). */
 long long kfbi_domain_device_bytes(const kfbi_domain* dom);
 
+/* Kernel timing with CUDA events recorded on the launching stream around
+ * every launch of a kernel class (off by default; enabling it adds two
+ * event records per timed launch).  kfbi_profile_read synchronises the
+ * recorded events and returns the launch count and summed duration. */
+typedef enum {
+  KFBI_PROF_DST = 0,     /* one DST-I pass (GEMM) of the box solve */
+  KFBI_PROF_CORRECT = 1, /* corrected right-hand side */
+  KFBI_PROF_EXTRACT = 2, /* boundary extraction */
+  KFBI_PROF_KRYLOV = 3,  /* GMRES kernels */
+  KFBI_PROF_GRID = 4,    /* elementwise grid kernels (steppers, layout) */
+  KFBI_PROF_NCLASS = 5
+} kfbi_prof_class;
+void kfbi_profile_enable(int on);
+void kfbi_profile_reset(void);
+kfbi_status kfbi_profile_read(int cls, long long* launches, double* total_ms);
+
 /* Host-only plan: the geometry and coefficient tables kfbi_create_domain
  * uploads, built without touching the GPU, for inspection and tests. */
 typedef enum {

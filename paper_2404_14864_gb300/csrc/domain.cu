@@ -389,29 +389,29 @@ void apply_internal(kfbi_domain* D, double kre, double kim, const double* phi, i
   }
   if (D->n_irr > 0) {
     if (C)
-      KFBI_LAUNCH(k_correct<true>, (D->n_irr + 127) / 128, 128, 0, st, D->d_R, plane, ft,
+      KFBI_LAUNCH_P(KFBI_PROF_CORRECT, k_correct<true>, (D->n_irr + 127) / 128, 128, 0, st, D->d_R, plane, ft,
                   D->d_irr_off, D->d_arm_start, D->d_arm_k0, D->d_arm_alpha, D->d_arm_beta,
                   D->d_arm_fidx, D->d_arm_fcoef, D->n_irr, D->n_arms, D->nb, phi, ps, kre, kim);
     else
-      KFBI_LAUNCH(k_correct<false>, (D->n_irr + 127) / 128, 128, 0, st, D->d_R, plane, ft,
+      KFBI_LAUNCH_P(KFBI_PROF_CORRECT, k_correct<false>, (D->n_irr + 127) / 128, 128, 0, st, D->d_R, plane, ft,
                   D->d_irr_off, D->d_arm_start, D->d_arm_k0, D->d_arm_alpha, D->d_arm_beta,
                   D->d_arm_fidx, D->d_arm_fcoef, D->n_irr, D->n_arms, D->nb, phi, ps, kre, kim);
   }
   dim3 gg(Mp / 64, Mp / 64, P);
-  KFBI_LAUNCH(k_dgemm_t, gg, 256, 0, st, D->d_R, D->d_S, D->d_T, Mp);
-  KFBI_LAUNCH(k_dgemm_t, gg, 256, 0, st, D->d_T, D->d_S, D->d_U, Mp);
+  KFBI_LAUNCH_P(KFBI_PROF_DST, k_dgemm_t, gg, 256, 0, st, D->d_R, D->d_S, D->d_T, Mp);
+  KFBI_LAUNCH_P(KFBI_PROF_DST, k_dgemm_t, gg, 256, 0, st, D->d_T, D->d_S, D->d_U, Mp);
   const double scale = (2.0 / D->M) * (2.0 / D->M);
-  KFBI_LAUNCH(k_eigscale, grid_for(plane, 256), 256, 0, st, D->d_U, plane, Mp, n1, D->d_lam, kre,
+  KFBI_LAUNCH_P(KFBI_PROF_GRID, k_eigscale, grid_for(plane, 256), 256, 0, st, D->d_U, plane, Mp, n1, D->d_lam, kre,
               kim, scale, C ? 1 : 0);
-  KFBI_LAUNCH(k_dgemm_t, gg, 256, 0, st, D->d_U, D->d_S, D->d_T, Mp);
-  KFBI_LAUNCH(k_dgemm_t, gg, 256, 0, st, D->d_T, D->d_S, D->d_U, Mp);
+  KFBI_LAUNCH_P(KFBI_PROF_DST, k_dgemm_t, gg, 256, 0, st, D->d_U, D->d_S, D->d_T, Mp);
+  KFBI_LAUNCH_P(KFBI_PROF_DST, k_dgemm_t, gg, 256, 0, st, D->d_T, D->d_S, D->d_U, Mp);
   if (out) {
     if (C)
-      KFBI_LAUNCH(k_extract<true>, (D->nb + 127) / 128, 128, 0, st, D->d_U, plane, ft,
+      KFBI_LAUNCH_P(KFBI_PROF_EXTRACT, k_extract<true>, (D->nb + 127) / 128, 128, 0, st, D->d_U, plane, ft,
                   D->d_node_gidx, D->d_node_w, D->d_node_a, D->d_node_b, D->d_node_fidx,
                   D->d_node_fcoef, D->nb, phi, ps, kre, kim, out, os);
     else
-      KFBI_LAUNCH(k_extract<false>, (D->nb + 127) / 128, 128, 0, st, D->d_U, plane, ft,
+      KFBI_LAUNCH_P(KFBI_PROF_EXTRACT, k_extract<false>, (D->nb + 127) / 128, 128, 0, st, D->d_U, plane, ft,
                   D->d_node_gidx, D->d_node_w, D->d_node_a, D->d_node_b, D->d_node_fidx,
                   D->d_node_fcoef, D->nb, phi, ps, kre, kim, out, os);
   }

@@ -262,7 +262,7 @@ kfbi_status gmres_solve(kfbi_domain* D, double kre, double kim, const double* b,
   double2* H = (double2*)D->d_H;
   double2* g = (double2*)D->d_g;
   double2* sn = (double2*)D->d_sn;
-  KFBI_LAUNCH(k_bnorm, 1, kThreads, 0, st, (const double2*)b, nb, D->d_scal, tol);
+  KFBI_LAUNCH_P(KFBI_PROF_KRYLOV, k_bnorm, 1, kThreads, 0, st, (const double2*)b, nb, D->d_scal, tol);
   int it = 0;
   bool first = true;
   kfbi_status status = KFBI_OK;
@@ -270,7 +270,7 @@ kfbi_status gmres_solve(kfbi_domain* D, double kre, double kim, const double* b,
   for (;;) {
     const bool skip_ax = first && x_zero;
     if (!skip_ax) apply_internal(D, kre, kim, x, 2, nullptr, D->d_W, 2, false, st);
-    KFBI_LAUNCH(k_restart, 1, kThreads, 0, st, (const double2*)b, skip_ax ? nullptr : W, V, g, m,
+    KFBI_LAUNCH_P(KFBI_PROF_KRYLOV, k_restart, 1, kThreads, 0, st, (const double2*)b, skip_ax ? nullptr : W, V, g, m,
                 nb, D->d_scal);
     KFBI_CHECK_LAUNCH();
     read_scalars(D, st);
@@ -287,7 +287,7 @@ kfbi_status gmres_solve(kfbi_domain* D, double kre, double kim, const double* b,
     for (int j = 0; j < m; ++j) {
       apply_internal(D, kre, kim, (const double*)(V + (size_t)j * nb), 2, nullptr, D->d_W, 2,
                      false, st);
-      KFBI_LAUNCH(k_arnoldi, 1, kThreads, 0, st, V, nb, j, (const double2*)W, H, D->d_cs, sn, g, m,
+      KFBI_LAUNCH_P(KFBI_PROF_KRYLOV, k_arnoldi, 1, kThreads, 0, st, V, nb, j, (const double2*)W, H, D->d_cs, sn, g, m,
                   D->d_scal);
       KFBI_CHECK_LAUNCH();
       ++it;
@@ -295,7 +295,7 @@ kfbi_status gmres_solve(kfbi_domain* D, double kre, double kim, const double* b,
       read_scalars(D, st);
       if (D->h_scal[2] != 0.0 || it >= maxit) break;
     }
-    KFBI_LAUNCH(k_update, 1, kThreads, 0, st, V, nb, k, H, g, m, (double2*)x);
+    KFBI_LAUNCH_P(KFBI_PROF_KRYLOV, k_update, 1, kThreads, 0, st, V, nb, k, H, g, m, (double2*)x);
     KFBI_CHECK_LAUNCH();
     if (D->h_scal[2] != 0.0 || it >= maxit) break;
   }

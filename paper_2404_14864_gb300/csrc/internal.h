@@ -19,6 +19,20 @@ extern std::atomic<long long> g_launches;
 // Message of the last failure not tied to a domain.
 void set_global_error(const std::string& s);
 
+// Optional per-class event timing (prof.cpp).
+extern bool g_prof_on;
+void* prof_begin(int cls, cudaStream_t st);
+void prof_end(void* tok, cudaStream_t st);
+
+// Launch a kernel of a profiling class, count it and (if enabled) time it.
+#define KFBI_LAUNCH_P(cls, kern, grid, block, smem, stream, ...)                       \
+  do {                                                                                  \
+    void* tok_ = ::kfbi::g_prof_on ? ::kfbi::prof_begin((cls), (stream)) : nullptr;     \
+    kern<<<(grid), (block), (smem), (stream)>>>(__VA_ARGS__);                           \
+    if (tok_) ::kfbi::prof_end(tok_, (stream));                                         \
+    ::kfbi::g_launches.fetch_add(1, std::memory_order_relaxed);                         \
+  } while (0)
+
 // Launch a kernel and count it.
 #define KFBI_LAUNCH(kern, grid, block, smem, stream, ...)                              \
   do {                                                                                  \

@@ -175,7 +175,7 @@ static kfbi_status solve_step(kfbi_domain* D, kfbi_state* S, const double* g, bo
                               kfbi_solve_info* info, cudaStream_t st) {
   const int nb = D->nb;
   apply_internal(D, S->kre, S->kim, D->d_zero_nb, 2, S->d_ft, S->d_ub, 2, false, st);
-  KFBI_LAUNCH(k_make_b, (nb + 255) / 256, 256, 0, st, S->d_b, g, S->d_ub, nb, gC ? 1 : 0);
+  KFBI_LAUNCH_P(KFBI_PROF_GRID, k_make_b, (nb + 255) / 256, 256, 0, st, S->d_b, g, S->d_ub, nb, gC ? 1 : 0);
   KFBI_CHECK_LAUNCH();
   kfbi_solve_info loc{};
   kfbi_status s = gmres_solve(D, S->kre, S->kim, S->d_b, S->d_phi, S->phi_zero, &loc, st);
@@ -333,11 +333,11 @@ kfbi_status kfbi_step_heat(kfbi_domain* dom, kfbi_state* S, const double* g_next
   return guarded(dom, [&]() -> kfbi_status {
     cudaStream_t st = (cudaStream_t)stream;
     const size_t plane = (size_t)dom->Mp * dom->Mp;
-    KFBI_LAUNCH(k_make_ft, grid_for(plane, 256), 256, 0, st, S->d_ft, S->d_F, dom->d_mask, dom->Mp);
+    KFBI_LAUNCH_P(KFBI_PROF_GRID, k_make_ft, grid_for(plane, 256), 256, 0, st, S->d_ft, S->d_F, dom->d_mask, dom->Mp);
     KFBI_CHECK_LAUNCH();
     kfbi_status s = solve_step(dom, S, g_next, false, info, st);
     if (s != KFBI_OK) return s;
-    KFBI_LAUNCH(k_heat_update, grid_for(plane, 256), 256, 0, st, S->d_u, S->d_F, dom->d_U,
+    KFBI_LAUNCH_P(KFBI_PROF_GRID, k_heat_update, grid_for(plane, 256), 256, 0, st, S->d_u, S->d_F, dom->d_U,
                 src_sum_next, dom->n1, dom->Mp, 4.0 / S->dt);
     KFBI_CHECK_LAUNCH();
     KFBI_CUDA(cudaStreamSynchronize(st));
@@ -356,11 +356,11 @@ kfbi_status kfbi_step_wave(kfbi_domain* dom, kfbi_state* S, const double* g_next
   return guarded(dom, [&]() -> kfbi_status {
     cudaStream_t st = (cudaStream_t)stream;
     const size_t plane = (size_t)dom->Mp * dom->Mp;
-    KFBI_LAUNCH(k_make_ft, grid_for(plane, 256), 256, 0, st, S->d_ft, S->d_F, dom->d_mask, dom->Mp);
+    KFBI_LAUNCH_P(KFBI_PROF_GRID, k_make_ft, grid_for(plane, 256), 256, 0, st, S->d_ft, S->d_F, dom->d_mask, dom->Mp);
     KFBI_CHECK_LAUNCH();
     kfbi_status s = solve_step(dom, S, g_next, false, info, st);
     if (s != KFBI_OK) return s;
-    KFBI_LAUNCH(k_wave_update, grid_for(plane, 256), 256, 0, st, S->d_u, S->d_F, S->d_Fprev,
+    KFBI_LAUNCH_P(KFBI_PROF_GRID, k_wave_update, grid_for(plane, 256), 256, 0, st, S->d_u, S->d_F, S->d_Fprev,
                 dom->d_U, dom->Mp, S->kre / S->theta, (1.0 - 2.0 * S->theta) / S->theta);
     KFBI_CHECK_LAUNCH();
     KFBI_CUDA(cudaStreamSynchronize(st));
@@ -383,12 +383,12 @@ kfbi_status kfbi_step_schrodinger(kfbi_domain* dom, kfbi_state* S, const double*
   return guarded(dom, [&]() -> kfbi_status {
     cudaStream_t st = (cudaStream_t)stream;
     const size_t plane = (size_t)dom->Mp * dom->Mp;
-    KFBI_LAUNCH(k_schr_bstep, grid_for(plane, 256), 256, 0, st, S->d_aux, S->d_ft, S->d_F, v,
+    KFBI_LAUNCH_P(KFBI_PROF_GRID, k_schr_bstep, grid_for(plane, 256), 256, 0, st, S->d_aux, S->d_ft, S->d_F, v,
                 dom->d_mask, dom->n1, dom->Mp, 0.5 * S->dt, S->kim);
     KFBI_CHECK_LAUNCH();
     kfbi_status s = solve_step(dom, S, (const double*)g_next, true, info, st);
     if (s != KFBI_OK) return s;
-    KFBI_LAUNCH(k_schr_update, grid_for(plane, 256), 256, 0, st, S->d_u, S->d_F, dom->d_U,
+    KFBI_LAUNCH_P(KFBI_PROF_GRID, k_schr_update, grid_for(plane, 256), 256, 0, st, S->d_u, S->d_F, dom->d_U,
                 S->d_aux, dom->Mp);
     KFBI_CHECK_LAUNCH();
     KFBI_CUDA(cudaStreamSynchronize(st));

@@ -94,6 +94,10 @@ def lib():
         "kfbi_last_global_error": (ctypes.c_char_p, []),
         "kfbi_launch_count": (ctypes.c_longlong, []),
         "kfbi_domain_device_bytes": (ctypes.c_longlong, [_VP]),
+        "kfbi_profile_enable": (None, [ctypes.c_int]),
+        "kfbi_profile_reset": (None, []),
+        "kfbi_profile_read": (S, [ctypes.c_int, ctypes.POINTER(ctypes.c_longlong),
+                                  ctypes.POINTER(ctypes.c_double)]),
         "kfbi_plan_create": (S, [ctypes.POINTER(DomainDesc), ctypes.POINTER(_VP)]),
         "kfbi_plan_destroy": (None, [_VP]),
         "kfbi_plan_size": (ctypes.c_longlong, [_VP, ctypes.c_int]),
@@ -160,6 +164,26 @@ def _check(status, dom=None):
 
 def launch_count():
     return int(lib().kfbi_launch_count())
+
+
+PROF_DST, PROF_CORRECT, PROF_EXTRACT, PROF_KRYLOV, PROF_GRID = 0, 1, 2, 3, 4
+PROF_NAMES = {0: "dst", 1: "correct", 2: "extract", 3: "krylov", 4: "grid"}
+
+
+def kfbi_profile_enable(on=True):
+    lib().kfbi_profile_enable(1 if on else 0)
+
+
+def kfbi_profile_reset():
+    lib().kfbi_profile_reset()
+
+
+def kfbi_profile_read(cls):
+    """(launches, total_ms) of a kernel class since the last reset."""
+    n = ctypes.c_longlong()
+    ms = ctypes.c_double()
+    _check(lib().kfbi_profile_read(int(cls), ctypes.byref(n), ctypes.byref(ms)))
+    return int(n.value), float(ms.value)
 
 
 # ----------------------------------------------------------------------------
