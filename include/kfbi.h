@@ -136,6 +136,24 @@ kfbi_status kfbi_solve_density(kfbi_domain* dom, double kappa_re, double kappa_i
                                const void* b_dev, void* phi_dev, kfbi_solve_info* info,
                                void* stream);
 
+/* Allocation-free box solve, for callers that cannot allocate device memory
+ * (code that runs where cudaMalloc is not allowed, e.g. inside a graph
+ * capture it does not own, or a plugin whose host program owns every device
+ * allocation).  The paper has no counterpart to this entry point.
+ * Solves (D_xx + D_yy - kappa) u = rhs on the (M-1)^2 interior nodes of the
+ * box [box_lo, box_hi]^2 with u = 0 on the box boundary (the five-point
+ * operator of the box solve) by float64 DST-I passes, without a domain.
+ *   rhs_dev, u_dev : (M-1)^2 doubles, complex128 if kappa_im != 0, caller
+ *                    layout, device memory owned by the caller.
+ * Work space is a static device array of 2.5 MiB that every GPU loading the
+ * library holds until exit, so M - 1 <= 256; larger M returns KFBI_ERR_ARG.
+ * The first call on a device looks up the array's address (call it once
+ * before any stream capture); all calls share the array, so calls that
+ * overlap on the GPU race.  Allocates nothing; asynchronous on `stream`. */
+kfbi_status kfbi_box_solve_noalloc(int M, double box_lo, double box_hi, double kappa_re,
+                                   double kappa_im, const void* rhs_dev, void* u_dev,
+                                   void* stream);
+
 /* ---- time stepping (Sec. 3.1, Procedure 3) ------------------------------ */
 
 typedef enum { KFBI_HEAT = 0, KFBI_WAVE = 1, KFBI_SCHRODINGER = 2 } kfbi_equation;

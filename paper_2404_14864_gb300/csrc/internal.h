@@ -194,6 +194,14 @@ kfbi_status guarded(kfbi_domain* D, F&& f) {
   return code;
 }
 
+// Kernels of the float64 box solve (domain.cu), also launched by the
+// allocation-free variant (noalloc.cu).
+__global__ void k_dgemm_t(const double* __restrict__ A, const double* __restrict__ S,
+                          double* __restrict__ out, int Mp);
+__global__ void k_eigscale(double* __restrict__ T, size_t plane, int Mp, int n1,
+                           const double* __restrict__ lam, double kre, double kim, double scale,
+                           int cplx);
+
 // Caller layout <-> padded planes (domain.cu).
 void pad_mask(kfbi_domain* D, const double* src, double* dst, bool C, cudaStream_t st);
 void unpad(kfbi_domain* D, const double* src, double* dst, bool C, cudaStream_t st);

@@ -98,6 +98,8 @@ def lib():
         "kfbi_profile_reset": (None, []),
         "kfbi_profile_read": (S, [ctypes.c_int, ctypes.POINTER(ctypes.c_longlong),
                                   ctypes.POINTER(ctypes.c_double)]),
+        "kfbi_box_solve_noalloc": (S, [ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                       ctypes.c_double, ctypes.c_double, _VP, _VP, _VP]),
         "kfbi_plan_create": (S, [ctypes.POINTER(DomainDesc), ctypes.POINTER(_VP)]),
         "kfbi_plan_destroy": (None, [_VP]),
         "kfbi_plan_size": (ctypes.c_longlong, [_VP, ctypes.c_int]),
@@ -219,6 +221,13 @@ def kfbi_solve_density(h, kappa, b, phi, stream=None):
     _check(lib().kfbi_solve_density(h, k.real, k.imag, _ptr(b), _ptr(phi), ctypes.byref(info),
                                     _stream(stream)), h)
     return info.as_dict()
+
+
+def kfbi_box_solve_noalloc(M, box_lo, box_hi, kappa, rhs, u, stream=None):
+    """Box solve with no device allocation (static scratch, M - 1 <= 256)."""
+    k = complex(kappa)
+    _check(lib().kfbi_box_solve_noalloc(int(M), float(box_lo), float(box_hi), k.real, k.imag,
+                                        _ptr(rhs), _ptr(u), _stream(stream)))
 
 
 class Domain:
