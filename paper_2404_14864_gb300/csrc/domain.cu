@@ -369,16 +369,13 @@ static void upload_domain(kfbi_domain* D, const Plan& P) {
   D->rhs_sparse_planes = 2;
 }
 
-void apply_internal(kfbi_domain* D, double kre, double kim, const double* phi, int ps,
-                    const double* ft, double* out, int os, bool want_grid, cudaStream_t st) {
-  if (D->tc) {
-    tc_apply(D, kre, kim, phi, ps, ft, out, os, want_grid, st);
-    return;
-  }
+// FP64 corrected right-hand side in D->d_R (f-tilde plus the jump
+// corrections at the irregular nodes).
+void correct_fp64(kfbi_domain* D, double kre, double kim, const double* phi, int ps,
+                  const double* ft, cudaStream_t st) {
   const bool C = kim != 0.0;
   const int P = C ? 2 : 1;
-  const int Mp = D->Mp, n1 = D->n1;
-  const size_t plane = (size_t)Mp * Mp;
+  const size_t plane = (size_t)D->Mp * D->Mp;
   // base right-hand side: f-tilde everywhere, or zero off the irregular nodes
   if (ft) {
     KFBI_CUDA(cudaMemcpyAsync(D->d_R, ft, P * plane * sizeof(double), cudaMemcpyDeviceToDevice, st));
@@ -397,6 +394,35 @@ void apply_internal(kfbi_domain* D, double kre, double kim, const double* phi, i
                   D->d_irr_off, D->d_arm_start, D->d_arm_k0, D->d_arm_alpha, D->d_arm_beta,
                   D->d_arm_fidx, D->d_arm_fcoef, D->n_irr, D->n_arms, D->nb, phi, ps, kre, kim);
   }
+  KFBI_CHECK_LAUNCH();
+}
+
+// FP64 extraction of u+ from the grid solution in D->d_U.
+void extract_fp64(kfbi_domain* D, double kre, double kim, const double* phi, int ps,
+                  const double* ft, double* out, int os, cudaStream_t st) {
+  const size_t plane = (size_t)D->Mp * D->Mp;
+  if (kim != 0.0)
+    KFBI_LAUNCH_P(KFBI_PROF_EXTRACT, k_extract<true>, (D->nb + 127) / 128, 128, 0, st, D->d_U, plane, ft,
+                D->d_node_gidx, D->d_node_w, D->d_node_a, D->d_node_b, D->d_node_fidx,
+                D->d_node_fcoef, D->nb, phi, ps, kre, kim, out, os);
+  else
+    KFBI_LAUNCH_P(KFBI_PROF_EXTRACT, k_extract<false>, (D->nb + 127) / 128, 128, 0, st, D->d_U, plane, ft,
+                D->d_node_gidx, D->d_node_w, D->d_node_a, D->d_node_b, D->d_node_fidx,
+                D->d_node_fcoef, D->nb, phi, ps, kre, kim, out, os);
+  KFBI_CHECK_LAUNCH();
+}
+
+void apply_internal(kfbi_domain* D, double kre, double kim, const double* phi, int ps,
+                    const double* ft, double* out, int os, bool want_grid, cudaStream_t st) {
+  if (D->tc) {
+    tc_apply(D, kre, kim, phi, ps, ft, out, os, want_grid, st);
+    return;
+  }
+  const bool C = kim != 0.0;
+  const int P = C ? 2 : 1;
+  const int Mp = D->Mp, n1 = D->n1;
+  const size_t plane = (size_t)Mp * Mp;
+  correct_fp64(D, kre, kim, phi, ps, ft, st);
   dim3 gg(Mp / 64, Mp / 64, P);
   KFBI_LAUNCH_P(KFBI_PROF_DST, k_dgemm_t, gg, 256, 0, st, D->d_R, D->d_S, D->d_T, Mp);
   KFBI_LAUNCH_P(KFBI_PROF_DST, k_dgemm_t, gg, 256, 0, st, D->d_T, D->d_S, D->d_U, Mp);
@@ -405,17 +431,16 @@ void apply_internal(kfbi_domain* D, double kre, double kim, const double* phi, i
               kim, scale, C ? 1 : 0);
   KFBI_LAUNCH_P(KFBI_PROF_DST, k_dgemm_t, gg, 256, 0, st, D->d_U, D->d_S, D->d_T, Mp);
   KFBI_LAUNCH_P(KFBI_PROF_DST, k_dgemm_t, gg, 256, 0, st, D->d_T, D->d_S, D->d_U, Mp);
-  if (out) {
-    if (C)
-      KFBI_LAUNCH_P(KFBI_PROF_EXTRACT, k_extract<true>, (D->nb + 127) / 128, 128, 0, st, D->d_U, plane, ft,
-                  D->d_node_gidx, D->d_node_w, D->d_node_a, D->d_node_b, D->d_node_fidx,
-                  D->d_node_fcoef, D->nb, phi, ps, kre, kim, out, os);
-    else
-      KFBI_LAUNCH_P(KFBI_PROF_EXTRACT, k_extract<false>, (D->nb + 127) / 128, 128, 0, st, D->d_U, plane, ft,
-                  D->d_node_gidx, D->d_node_w, D->d_node_a, D->d_node_b, D->d_node_fidx,
-                  D->d_node_fcoef, D->nb, phi, ps, kre, kim, out, os);
-  }
+  if (out) extract_fp64(D, kre, kim, phi, ps, ft, out, os, st);
   KFBI_CHECK_LAUNCH();
+}
+
+void apply_accurate(kfbi_domain* D, double kre, double kim, const double* phi, int ps,
+                    const double* ft, double* out, int os, cudaStream_t st) {
+  if (D->tc)
+    tc_apply_accurate(D, kre, kim, phi, ps, ft, out, os, st);
+  else
+    apply_internal(D, kre, kim, phi, ps, ft, out, os, true, st);
 }
 
 void pad_mask(kfbi_domain* D, const double* src, double* dst, bool C, cudaStream_t st) {

@@ -10,7 +10,10 @@
 // float64, with complex Givens rotations on the Hessenberg column and the
 // rotated residual |g_{j+1}| as the convergence estimate.  All of it runs
 // in one CTA per kernel: the vectors are a few thousand entries.
+#include <algorithm>
 #include <cmath>
+#include <cstring>
+#include <string>
 
 #include "internal.h"
 
@@ -89,75 +92,160 @@ __global__ void __launch_bounds__(kThreads) k_restart(const double2* __restrict_
   }
 }
 
-// One Arnoldi step: w = A v_j on entry; CGS2 against v_0..v_j, v_{j+1} =
-// w / ||w||, Hessenberg column j rotated by the previous Givens rotations,
-// new rotation, g updated, residual estimate |g_{j+1}|.
-__global__ void __launch_bounds__(kThreads) k_arnoldi(double2* __restrict__ V, int nb, int j,
-                                                       const double2* __restrict__ w_in,
-                                                       double2* H, double* cs, double2* sn,
-                                                       double2* g, int m, double* scal) {
-  __shared__ double red[32];
-  __shared__ double2 hp[65], hacc[65];
-  double2* w = V + (size_t)(j + 1) * nb;  // build the new basis vector in place
-  for (int e = threadIdx.x; e < nb; e += kThreads) w[e] = w_in[e];
-  if (threadIdx.x <= j) hacc[threadIdx.x] = make_double2(0.0, 0.0);
+
+
+// ---- multi-CTA CGS2 Arnoldi ------------------------------------------------
+// GB300 keeps a small fraction of FP64 throughput per SM, so one Arnoldi
+// step is spread over up to 64 CTAs: each owns a slice of the vectors, the
+// inner products of a pass are per-CTA partial sums (one warp per basis
+// vector) reduced redundantly by every CTA in the next kernel.  Real
+// problems touch only the real parts (C = false).
+constexpr int GT = 256;  // threads per CTA of the grid kernels
+constexpr int GMAX = 64; // maximum CTAs
+
+template <bool C>
+__device__ __forceinline__ double2 dotpart(const double2* __restrict__ a,
+                                           const double2* __restrict__ b, int e0, int e1,
+                                           int lane) {
+  double2 s = make_double2(0.0, 0.0);
+  for (int e = e0 + lane; e < e1; e += 32) {
+    const double2 x = a[e], y = b[e];
+    if (C) {
+      s.x += x.x * y.x + x.y * y.y;
+      s.y += x.x * y.y - x.y * y.x;
+    } else {
+      s.x += x.x * y.x;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    s.x += __shfl_xor_sync(0xffffffffu, s.x, o);
+    if (C) s.y += __shfl_xor_sync(0xffffffffu, s.y, o);
+  }
+  return s;
+}
+
+// Sum the G partials of entries 0..n-1 into sh[] (warp per entry).
+template <bool C>
+__device__ void reduce_parts(const double2* __restrict__ part, int n, int G, double2* sh) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int i = warp; i < n; i += GT / 32) {
+    double2 s = make_double2(0.0, 0.0);
+    for (int b = lane; b < G; b += 32) {
+      const double2 v = part[(size_t)i * GMAX + b];
+      s.x += v.x;
+      if (C) s.y += v.y;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      s.x += __shfl_xor_sync(0xffffffffu, s.x, o);
+      if (C) s.y += __shfl_xor_sync(0xffffffffu, s.y, o);
+    }
+    if (lane == 0) sh[i] = s;
+  }
+}
+
+// Pass-1 inner products <v_i, w>, i = 0..j, per CTA slice.
+template <bool C>
+__global__ void __launch_bounds__(GT) k_cgs_dots(const double2* __restrict__ V, int nb, int j,
+                                                 const double2* __restrict__ w,
+                                                 double2* __restrict__ part, int slice) {
+  const int b = blockIdx.x, G = gridDim.x;
+  const int e0 = b * slice, e1 = min(nb, e0 + slice);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  (void)G;
+  for (int i = warp; i <= j; i += GT / 32) {
+    const double2 s = dotpart<C>(V + (size_t)i * nb, w, e0, e1, lane);
+    if (lane == 0) part[(size_t)i * GMAX + b] = s;
+  }
+}
+
+// Reduce the pass's inner products h, w -= V h on the slice, accumulate h
+// into the Hessenberg column (CTA 0), then either the next pass's partial
+// inner products (mode 0) or the partial squared norm (mode 1).
+template <bool C>
+__global__ void __launch_bounds__(GT) k_cgs_update(const double2* __restrict__ V, int nb, int j,
+                                                   double2* __restrict__ w,
+                                                   const double2* __restrict__ part_in,
+                                                   double2* __restrict__ part_out,
+                                                   double2* __restrict__ hcol, int first,
+                                                   int mode, int slice) {
+  __shared__ double2 h[65];
+  const int b = blockIdx.x, G = gridDim.x;
+  const int e0 = b * slice, e1 = min(nb, e0 + slice);
+  reduce_parts<C>(part_in, j + 1, G, h);
+  __syncthreads();
+  if (b == 0)
+    for (int i = threadIdx.x; i <= j; i += GT) {
+      if (first) {
+        hcol[i] = h[i];
+      } else {
+        hcol[i].x += h[i].x;
+        hcol[i].y += h[i].y;
+      }
+    }
+  for (int e = e0 + threadIdx.x; e < e1; e += GT) {
+    double2 acc = w[e];
+    for (int i = 0; i <= j; ++i) {
+      const double2 v = V[(size_t)i * nb + e], hi = h[i];
+      if (C) {
+        acc.x -= hi.x * v.x - hi.y * v.y;
+        acc.y -= hi.x * v.y + hi.y * v.x;
+      } else {
+        acc.x -= hi.x * v.x;
+      }
+    }
+    w[e] = acc;
+  }
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int pass = 0; pass < 2; ++pass) {
-    for (int i = warp; i <= j; i += kWarps) {
-      const double2* vi = V + (size_t)i * nb;
-      double2 s = make_double2(0.0, 0.0);
-      for (int e = lane; e < nb; e += 32) {
-        const double2 t = cconjmul(vi[e], w[e]);
-        s.x += t.x;
-        s.y += t.y;
-      }
-      for (int o = 16; o > 0; o >>= 1) {
-        s.x += __shfl_xor_sync(0xffffffffu, s.x, o);
-        s.y += __shfl_xor_sync(0xffffffffu, s.y, o);
-      }
-      if (lane == 0) hp[i] = s;
+  if (mode == 0) {
+    for (int i = warp; i <= j; i += GT / 32) {
+      const double2 s = dotpart<C>(V + (size_t)i * nb, w, e0, e1, lane);
+      if (lane == 0) part_out[(size_t)i * GMAX + b] = s;
     }
-    __syncthreads();
-    for (int e = threadIdx.x; e < nb; e += kThreads) {
-      double2 acc = w[e];
-      for (int i = 0; i <= j; ++i) {
-        const double2 t = cmul(hp[i], V[(size_t)i * nb + e]);
-        acc.x -= t.x;
-        acc.y -= t.y;
-      }
-      w[e] = acc;
-    }
-    if (threadIdx.x <= j) {
-      hacc[threadIdx.x].x += hp[threadIdx.x].x;
-      hacc[threadIdx.x].y += hp[threadIdx.x].y;
-    }
-    __syncthreads();
+  } else if (warp == 0) {
+    const double2 s = dotpart<C>(w, w, e0, e1, lane);
+    if (lane == 0) part_out[b] = make_double2(s.x, 0.0);
   }
-  double s = 0.0;
-  for (int e = threadIdx.x; e < nb; e += kThreads) s += w[e].x * w[e].x + w[e].y * w[e].y;
-  s = block_sum(s, red);
-  const double hn = sqrt(s);
+}
+
+// ||w|| from the partials, v_{j+1} = w / ||w||, then (CTA 0, one thread)
+// the Hessenberg column with the previous Givens rotations, the new
+// rotation, g and the convergence scalars.
+__global__ void __launch_bounds__(GT) k_cgs_finalize(double2* __restrict__ V, int nb, int j,
+                                                     const double2* __restrict__ w,
+                                                     const double2* __restrict__ part,
+                                                     const double2* __restrict__ hcol, double2* H,
+                                                     double* cs, double2* sn, double2* g, int m,
+                                                     double* scal, int slice) {
+  __shared__ double2 nrm[1];
+  const int b = blockIdx.x, G = gridDim.x;
+  const int e0 = b * slice, e1 = min(nb, e0 + slice);
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    double s = 0.0;
+    for (int q = lane; q < G; q += 32) s += part[q].x;
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) nrm[0] = make_double2(sqrt(s), 0.0);
+  }
+  __syncthreads();
+  const double hn = nrm[0].x;
   const double inv = hn > 0.0 ? 1.0 / hn : 0.0;
-  for (int e = threadIdx.x; e < nb; e += kThreads) {
-    w[e].x *= inv;
-    w[e].y *= inv;
-  }
-  if (threadIdx.x == 0) {
+  double2* vn = V + (size_t)(j + 1) * nb;
+  for (int e = e0 + threadIdx.x; e < e1; e += GT) vn[e] = make_double2(w[e].x * inv, w[e].y * inv);
+  if (b == 0 && threadIdx.x == 0) {
     double2* col = H + (size_t)j * (m + 1);
-    for (int i = 0; i <= j; ++i) col[i] = hacc[i];
+    for (int i = 0; i <= j; ++i) col[i] = hcol[i];
     col[j + 1] = make_double2(hn, 0.0);
-    for (int i = 0; i < j; ++i) {  // previous rotations
+    for (int i = 0; i < j; ++i) {
       const double c = cs[i];
       const double2 sv = sn[i], a = col[i], bb = col[i + 1];
       const double2 t = cmul(sv, bb);
-      const double2 csv = make_double2(sv.x, -sv.y);
-      const double2 u = cmul(csv, a);
+      const double2 u = cmul(make_double2(sv.x, -sv.y), a);
       col[i] = make_double2(c * a.x + t.x, c * a.y + t.y);
       col[i + 1] = make_double2(-u.x + c * bb.x, -u.y + c * bb.y);
     }
     const double2 a = col[j];
-    const double bre = col[j + 1].x;  // real, >= 0
+    const double bre = col[j + 1].x;
     double c;
     double2 sv;
     const double aa = hypot(a.x, a.y);
@@ -177,8 +265,7 @@ __global__ void __launch_bounds__(kThreads) k_arnoldi(double2* __restrict__ V, i
     col[j] = make_double2(c * a.x + sv.x * bre, c * a.y + sv.y * bre);
     col[j + 1] = make_double2(0.0, 0.0);
     const double2 gj = g[j];
-    const double2 csv = make_double2(sv.x, -sv.y);
-    const double2 u = cmul(csv, gj);
+    const double2 u = cmul(make_double2(sv.x, -sv.y), gj);
     g[j + 1] = make_double2(-u.x, -u.y);
     g[j] = make_double2(c * gj.x, c * gj.y);
     const double res = hypot(g[j + 1].x, g[j + 1].y);
@@ -187,26 +274,38 @@ __global__ void __launch_bounds__(kThreads) k_arnoldi(double2* __restrict__ V, i
   }
 }
 
-// x += V[:, :k] y with R y = g (k x k upper triangle of the rotated H).
-__global__ void __launch_bounds__(kThreads) k_update(const double2* __restrict__ V, int nb, int k,
-                                                      const double2* H, const double2* g, int m,
-                                                      double2* __restrict__ x) {
+// x += V[:, :k] y with R y = g: one warp per CTA solves the triangle
+// (row sums across lanes), then the CTA updates its slice.
+__global__ void __launch_bounds__(GT) k_update_grid(const double2* __restrict__ V, int nb, int k,
+                                                    const double2* H, const double2* g, int m,
+                                                    double2* __restrict__ x, int slice) {
   __shared__ double2 y[64];
-  if (threadIdx.x == 0) {
+  const int b = blockIdx.x;
+  const int e0 = b * slice, e1 = min(nb, e0 + slice);
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
     for (int i = k - 1; i >= 0; --i) {
-      double2 s = g[i];
-      for (int l = i + 1; l < k; ++l) {
+      double2 s = make_double2(0.0, 0.0);
+      for (int l = i + 1 + lane; l < k; l += 32) {
         const double2 t = cmul(H[(size_t)l * (m + 1) + i], y[l]);
-        s.x -= t.x;
-        s.y -= t.y;
+        s.x += t.x;
+        s.y += t.y;
       }
-      const double2 d = H[(size_t)i * (m + 1) + i];
-      const double dd = d.x * d.x + d.y * d.y;
-      y[i] = make_double2((s.x * d.x + s.y * d.y) / dd, (s.y * d.x - s.x * d.y) / dd);
+      for (int o = 16; o > 0; o >>= 1) {
+        s.x += __shfl_xor_sync(0xffffffffu, s.x, o);
+        s.y += __shfl_xor_sync(0xffffffffu, s.y, o);
+      }
+      if (lane == 0) {
+        const double2 r = make_double2(g[i].x - s.x, g[i].y - s.y);
+        const double2 d = H[(size_t)i * (m + 1) + i];
+        const double dd = d.x * d.x + d.y * d.y;
+        y[i] = make_double2((r.x * d.x + r.y * d.y) / dd, (r.y * d.x - r.x * d.y) / dd);
+      }
+      __syncwarp();
     }
   }
   __syncthreads();
-  for (int e = threadIdx.x; e < nb; e += kThreads) {
+  for (int e = e0 + threadIdx.x; e < e1; e += GT) {
     double2 acc = x[e];
     for (int i = 0; i < k; ++i) {
       const double2 t = cmul(y[i], V[(size_t)i * nb + e]);
@@ -220,6 +319,15 @@ __global__ void __launch_bounds__(kThreads) k_update(const double2* __restrict__
 }  // namespace gm
 
 using namespace gm;
+
+void check_device_flags(kfbi_domain* D) {
+  int flags = 0;
+  std::memcpy(&flags, D->h_scal + 6, sizeof(int));
+  if (flags != 0)
+    throw Status{KFBI_ERR_TIMEOUT,
+                 "a tensor-core DST pass gave up waiting on its pipeline (flags " +
+                     std::to_string(flags) + ")"};
+}
 
 void gmres_alloc(kfbi_domain* D) {
   const int m = D->desc.gmres_restart, nb = D->nb;
@@ -236,12 +344,20 @@ void gmres_alloc(kfbi_domain* D) {
   alloc(&D->d_cs, m);
   alloc(&D->d_sn, 2 * (size_t)m);
   alloc(&D->d_g, 2 * (size_t)(m + 1));
+  alloc(&D->d_part, 2 * 2 * (size_t)(m + 1) * GMAX);
+  alloc(&D->d_hcol, 2 * (size_t)(m + 1));
+  alloc(&D->d_Rv, 2 * (size_t)nb);
+  alloc(&D->d_Dv, 2 * (size_t)nb);
+  alloc(&D->d_Ax, 2 * (size_t)nb);
   alloc(&D->d_scal, 8);
+  KFBI_CUDA(cudaMemset(D->d_scal, 0, 8 * sizeof(double)));
   KFBI_CUDA(cudaMallocHost(&D->h_scal, 8 * sizeof(double)));
+  std::memset(D->h_scal, 0, 8 * sizeof(double));
 }
 
 void gmres_free(kfbi_domain* D) {
-  double* ptrs[] = {D->d_V, D->d_W, D->d_X, D->d_B, D->d_H, D->d_cs, D->d_sn, D->d_g, D->d_scal};
+  double* ptrs[] = {D->d_V,  D->d_W,  D->d_X,  D->d_B,  D->d_H,    D->d_cs,   D->d_sn,
+                    D->d_g,  D->d_Rv, D->d_Dv, D->d_Ax, D->d_part, D->d_hcol, D->d_scal};
   for (double* p : ptrs)
     if (p) cudaFree(p);
   if (D->h_scal) cudaFreeHost(D->h_scal);
@@ -249,19 +365,57 @@ void gmres_free(kfbi_domain* D) {
 }
 
 static void read_scalars(kfbi_domain* D, cudaStream_t st) {
-  KFBI_CUDA(cudaMemcpyAsync(D->h_scal, D->d_scal, 4 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  KFBI_CUDA(cudaMemcpyAsync(D->h_scal, D->d_scal, 8 * sizeof(double), cudaMemcpyDeviceToHost, st));
   KFBI_CUDA(cudaStreamSynchronize(st));
+  check_device_flags(D);
 }
 
-kfbi_status gmres_solve(kfbi_domain* D, double kre, double kim, const double* b, double* x,
-                        bool x_zero, kfbi_solve_info* info, cudaStream_t st) {
-  const int m = D->restart, nb = D->nb, maxit = D->desc.gmres_maxit;
-  const double tol = D->desc.gmres_tol;
+static void grid_shape(int nb, int& G, int& slice) {
+  G = (nb + 31) / 32;
+  if (G > GMAX) G = GMAX;
+  slice = ((nb + G - 1) / G + 31) / 32 * 32;
+  G = (nb + slice - 1) / slice;
+}
+
+// One Arnoldi step on w = A v_j (in D->d_W): CGS2 over the grid kernels.
+static void arnoldi_step(kfbi_domain* D, bool C, int j, cudaStream_t st) {
+  const int nb = D->nb, m = D->restart;
+  int G, slice;
+  grid_shape(nb, G, slice);
+  double2* V = (double2*)D->d_V;
+  double2* w = (double2*)D->d_W;
+  double2* p1 = (double2*)D->d_part;
+  double2* p2 = p1 + (size_t)(m + 1) * GMAX;
+  double2* hcol = (double2*)D->d_hcol;
+  if (C) {
+    KFBI_LAUNCH_P(KFBI_PROF_KRYLOV, k_cgs_dots<true>, G, GT, 0, st, V, nb, j, w, p1, slice);
+    KFBI_LAUNCH_P(KFBI_PROF_KRYLOV, k_cgs_update<true>, G, GT, 0, st, V, nb, j, w, p1, p2, hcol, 1,
+                  0, slice);
+    KFBI_LAUNCH_P(KFBI_PROF_KRYLOV, k_cgs_update<true>, G, GT, 0, st, V, nb, j, w, p2, p1, hcol, 0,
+                  1, slice);
+  } else {
+    KFBI_LAUNCH_P(KFBI_PROF_KRYLOV, k_cgs_dots<false>, G, GT, 0, st, V, nb, j, w, p1, slice);
+    KFBI_LAUNCH_P(KFBI_PROF_KRYLOV, k_cgs_update<false>, G, GT, 0, st, V, nb, j, w, p1, p2, hcol,
+                  1, 0, slice);
+    KFBI_LAUNCH_P(KFBI_PROF_KRYLOV, k_cgs_update<false>, G, GT, 0, st, V, nb, j, w, p2, p1, hcol,
+                  0, 1, slice);
+  }
+  KFBI_LAUNCH_P(KFBI_PROF_KRYLOV, k_cgs_finalize, G, GT, 0, st, V, nb, j, w, p1, hcol,
+                (double2*)D->d_H, D->d_cs, (double2*)D->d_sn, (double2*)D->d_g, m, D->d_scal,
+                slice);
+  KFBI_CHECK_LAUNCH();
+}
+
+// GMRES(m) with the domain's hot-path operator (apply_internal), relative
+// tolerance tol, at most maxit iterations.
+static kfbi_status gmres_core(kfbi_domain* D, double kre, double kim, const double* b, double* x,
+                              bool x_zero, double tol, int maxit, kfbi_solve_info* info,
+                              cudaStream_t st) {
+  const int m = D->restart, nb = D->nb;
   double2* V = (double2*)D->d_V;
   double2* W = (double2*)D->d_W;
   double2* H = (double2*)D->d_H;
   double2* g = (double2*)D->d_g;
-  double2* sn = (double2*)D->d_sn;
   KFBI_LAUNCH_P(KFBI_PROF_KRYLOV, k_bnorm, 1, kThreads, 0, st, (const double2*)b, nb, D->d_scal, tol);
   int it = 0;
   bool first = true;
@@ -287,16 +441,19 @@ kfbi_status gmres_solve(kfbi_domain* D, double kre, double kim, const double* b,
     for (int j = 0; j < m; ++j) {
       apply_internal(D, kre, kim, (const double*)(V + (size_t)j * nb), 2, nullptr, D->d_W, 2,
                      false, st);
-      KFBI_LAUNCH_P(KFBI_PROF_KRYLOV, k_arnoldi, 1, kThreads, 0, st, V, nb, j, (const double2*)W, H, D->d_cs, sn, g, m,
-                  D->d_scal);
-      KFBI_CHECK_LAUNCH();
+      arnoldi_step(D, kim != 0.0, j, st);
       ++it;
       k = j + 1;
       read_scalars(D, st);
       if (D->h_scal[2] != 0.0 || it >= maxit) break;
     }
-    KFBI_LAUNCH_P(KFBI_PROF_KRYLOV, k_update, 1, kThreads, 0, st, V, nb, k, H, g, m, (double2*)x);
-    KFBI_CHECK_LAUNCH();
+    {
+      int G, slice;
+      grid_shape(nb, G, slice);
+      KFBI_LAUNCH_P(KFBI_PROF_KRYLOV, k_update_grid, G, GT, 0, st, V, nb, k, H, g, m,
+                    (double2*)x, slice);
+      KFBI_CHECK_LAUNCH();
+    }
     if (D->h_scal[2] != 0.0 || it >= maxit) break;
   }
   KFBI_CUDA(cudaStreamSynchronize(st));
@@ -312,6 +469,109 @@ kfbi_status gmres_solve(kfbi_domain* D, double kre, double kim, const double* b,
     status = KFBI_ERR_NONFINITE;
   } else if (D->h_scal[2] != 1.0) {
     D->err = "GMRES reached gmres_maxit";
+    status = KFBI_ERR_NOT_CONVERGED;
+  }
+  return status;
+}
+
+namespace gm {
+// r = b - Ax (Ax null: r = b) and scal[1] = ||r||.
+__global__ void __launch_bounds__(kThreads) k_residual(const double2* __restrict__ b,
+                                                        const double2* __restrict__ Ax,
+                                                        double2* __restrict__ r, int nb,
+                                                        double* scal) {
+  __shared__ double red[32];
+  double s = 0.0;
+  for (int e = threadIdx.x; e < nb; e += kThreads) {
+    double2 v = b[e];
+    if (Ax) {
+      v.x -= Ax[e].x;
+      v.y -= Ax[e].y;
+    }
+    r[e] = v;
+    s += v.x * v.x + v.y * v.y;
+  }
+  s = block_sum(s, red);
+  if (threadIdx.x == 0) scal[1] = sqrt(s);
+}
+
+__global__ void k_axpy(double2* __restrict__ x, const double2* __restrict__ d, int nb) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < nb) {
+    x[e].x += d[e].x;
+    x[e].y += d[e].y;
+  }
+}
+}  // namespace gm
+
+// Relative tolerance below which the inner solves of the refinement do not
+// go: the TF32x3 operator is accurate to ~2e-6, so tighter inner solves
+// only add iterations.
+static const double kInnerFloor = 1e-6;
+
+kfbi_status gmres_solve(kfbi_domain* D, double kre, double kim, const double* b, double* x,
+                        bool x_zero, kfbi_solve_info* info, cudaStream_t st) {
+  const double tol = D->desc.gmres_tol;
+  const int maxit = D->desc.gmres_maxit;
+  if (!D->tc) return gmres_core(D, kre, kim, b, x, x_zero, tol, maxit, info, st);
+  // Mixed domain: iterative refinement.  The residual of the density,
+  // r = b - A phi, uses the accurate operator (apply_accurate, FP64 vector
+  // arithmetic); the corrections solve A_mixed d = r with the fast TF32x3
+  // operator inside GMRES.
+  const int nb = D->nb;
+  const dim3 vb((nb + 255) / 256);
+  KFBI_LAUNCH_P(KFBI_PROF_KRYLOV, k_bnorm, 1, kThreads, 0, st, (const double2*)b, nb, D->d_scal,
+                tol);
+  read_scalars(D, st);
+  const double bnorm = D->h_scal[0];
+  int it = 0, apps = 0;
+  double rn = 0.0;
+  bool conv = false;
+  kfbi_status status = KFBI_OK;
+  for (int sweep = 0; sweep < 8; ++sweep) {
+    const bool skip = sweep == 0 && x_zero;
+    if (!skip) {
+      apply_accurate(D, kre, kim, x, 2, nullptr, D->d_Ax, 2, st);
+      ++apps;
+    }
+    KFBI_LAUNCH_P(KFBI_PROF_KRYLOV, k_residual, 1, kThreads, 0, st, (const double2*)b,
+                  skip ? nullptr : (const double2*)D->d_Ax, (double2*)D->d_Rv, nb, D->d_scal);
+    KFBI_CHECK_LAUNCH();
+    read_scalars(D, st);
+    rn = D->h_scal[1];
+    if (!std::isfinite(rn)) {
+      D->err = "non-finite density residual";
+      status = KFBI_ERR_NONFINITE;
+      break;
+    }
+    if (bnorm == 0.0 || rn <= tol * bnorm) {
+      conv = true;
+      break;
+    }
+    if (it >= maxit) break;
+    const double inner_tol = std::max(0.5 * tol * bnorm / rn, kInnerFloor);
+    KFBI_CUDA(cudaMemsetAsync(D->d_Dv, 0, 2 * (size_t)nb * sizeof(double), st));
+    kfbi_solve_info in{};
+    kfbi_status s = gmres_core(D, kre, kim, D->d_Rv, D->d_Dv, true, inner_tol, maxit - it, &in, st);
+    it += in.iters;
+    apps += in.applications;
+    if (s == KFBI_ERR_NONFINITE) {
+      status = s;
+      break;
+    }
+    KFBI_LAUNCH_P(KFBI_PROF_KRYLOV, k_axpy, vb, 256, 0, st, (double2*)x, (const double2*)D->d_Dv,
+                  nb);
+    KFBI_CHECK_LAUNCH();
+  }
+  KFBI_CUDA(cudaStreamSynchronize(st));
+  if (info) {
+    info->iters = it;
+    info->applications = apps;
+    info->rel_residual = bnorm > 0.0 ? rn / bnorm : 0.0;
+    info->converged = conv ? 1 : 0;
+  }
+  if (status == KFBI_OK && !conv) {
+    D->err = "GMRES with refinement reached gmres_maxit";
     status = KFBI_ERR_NOT_CONVERGED;
   }
   return status;

@@ -136,6 +136,11 @@ struct kfbi_domain {
   double* d_cs = nullptr;   // restart
   double* d_sn = nullptr;   // restart complex
   double* d_g = nullptr;    // restart+1 complex
+  double* d_part = nullptr; // per-CTA partial inner products (2 x (restart+1) x 64 complex)
+  double* d_hcol = nullptr; // Hessenberg column being built (restart+1 complex)
+  double* d_Rv = nullptr;   // refinement residual (2nb)
+  double* d_Dv = nullptr;   // refinement correction (2nb)
+  double* d_Ax = nullptr;   // accurate operator output (2nb)
   double* d_scal = nullptr; // device scalars: [0] ||b||, [1] residual estimate, ...
   double* h_scal = nullptr; // pinned mirror
   cudaEvent_t ev_scal = nullptr;
@@ -163,9 +168,19 @@ struct kfbi_state {
 namespace kfbi {
 
 // domain.cu
+// The operator of the hot path: float64 on a KFBI_FP64 domain, the fast
+// TF32x3 tensor-core path on a KFBI_MIXED_TF32 domain.
 void apply_internal(kfbi_domain* D, double kre, double kim, const double* phi, int phi_stride,
                     const double* ft, double* out, int out_stride, bool want_grid,
                     cudaStream_t st);
+// The operator to FP64-level accuracy (identical to apply_internal on a
+// float64 domain; refined box solve on a mixed domain).  Grid left in d_U.
+void apply_accurate(kfbi_domain* D, double kre, double kim, const double* phi, int phi_stride,
+                    const double* ft, double* out, int out_stride, cudaStream_t st);
+void correct_fp64(kfbi_domain* D, double kre, double kim, const double* phi, int ps,
+                  const double* ft, cudaStream_t st);
+void extract_fp64(kfbi_domain* D, double kre, double kim, const double* phi, int ps,
+                  const double* ft, double* out, int os, cudaStream_t st);
 // Run f (returning kfbi_status); convert exceptions into a status and keep
 // the message on the domain (or globally when D is null).
 template <class F>
@@ -211,6 +226,9 @@ int grid_for(size_t n, int block);
 kfbi_status gmres_solve(kfbi_domain* D, double kre, double kim, const double* b, double* x,
                         bool x_zero, kfbi_solve_info* info, cudaStream_t st);
 void gmres_alloc(kfbi_domain* D);
+// Throws KFBI_ERR_TIMEOUT if a device kernel recorded a failed bounded wait
+// (flags read back into h_scal by the last scalar read).
+void check_device_flags(kfbi_domain* D);
 void gmres_free(kfbi_domain* D);
 
 // tc_dst.cu (mixed path)
@@ -218,6 +236,8 @@ TcDst* tc_create(kfbi_domain* D);
 void tc_destroy(TcDst* tc);
 void tc_apply(kfbi_domain* D, double kre, double kim, const double* phi, int phi_stride,
               const double* ft, double* out, int out_stride, bool want_grid, cudaStream_t st);
+void tc_apply_accurate(kfbi_domain* D, double kre, double kim, const double* phi, int phi_stride,
+                       const double* ft, double* out, int out_stride, cudaStream_t st);
 long long tc_bytes(const TcDst* tc);
 
 }  // namespace kfbi

@@ -170,11 +170,12 @@ __global__ void k_copy_phi(const double* src, double* dst, int nb, int C) {
 using namespace stp;
 
 // One BIE solve of the step: b = g - u+[0, ft], GMRES for phi, then the grid
-// solution of Eq. 3.30 with (ft, phi) in D->d_U.
+// solution of Eq. 3.30 with (ft, phi) in D->d_U.  b and the final grid use
+// the accurate operator (FP64-level on either domain precision).
 static kfbi_status solve_step(kfbi_domain* D, kfbi_state* S, const double* g, bool gC,
                               kfbi_solve_info* info, cudaStream_t st) {
   const int nb = D->nb;
-  apply_internal(D, S->kre, S->kim, D->d_zero_nb, 2, S->d_ft, S->d_ub, 2, false, st);
+  apply_accurate(D, S->kre, S->kim, D->d_zero_nb, 2, S->d_ft, S->d_ub, 2, st);
   KFBI_LAUNCH_P(KFBI_PROF_GRID, k_make_b, (nb + 255) / 256, 256, 0, st, S->d_b, g, S->d_ub, nb, gC ? 1 : 0);
   KFBI_CHECK_LAUNCH();
   kfbi_solve_info loc{};
@@ -183,7 +184,7 @@ static kfbi_status solve_step(kfbi_domain* D, kfbi_state* S, const double* g, bo
   loc.applications += 2;
   if (info) *info = loc;
   if (s != KFBI_OK) return s;
-  apply_internal(D, S->kre, S->kim, S->d_phi, 2, S->d_ft, nullptr, 2, true, st);
+  apply_accurate(D, S->kre, S->kim, S->d_phi, 2, S->d_ft, nullptr, 2, st);
   return KFBI_OK;
 }
 

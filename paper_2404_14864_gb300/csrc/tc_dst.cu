@@ -1,21 +1,750 @@
-// Mixed-precision operator application (tcgen05 tensor-core DST); built in
-// a following step.
+// Mixed-precision operator application: the DST-I box solve of Sec. 3.4.2
+// (arXiv 2404.14864) as dense GEMMs on the sm_103a tensor cores.
+//
+// One pass computes out[p][c][r] = sum_k A[p][r][k] S[k][c] (two passes give
+// S A S).  Operands are split into TF32 pairs, A = A_hi + A_lo and
+// S = S_hi + S_lo, and the pass accumulates A_hi S_hi + A_hi S_lo + A_lo S_hi
+// (the dropped A_lo S_lo is ~2^-22 relative).  Each CTA owns a 128 x 64
+// output tile (128 CTAs per 1024^2 pass) and runs six warps:
+//   - warp 0 lane 0 streams K-blocks of 32 fp32 (one 128-byte swizzle row)
+//     of A_hi, A_lo, S_hi, S_lo into a 4-stage shared-memory ring with TMA
+//     (cp.async.bulk.tensor, 128B swizzle, mbarrier completion);
+//   - warp 1 lane 0 issues tcgen05.mma kind::tf32 (M = 128, N = 64, K = 8),
+//     one K-block into one of eight TMEM accumulators, and releases the stage
+//     and publishes the accumulator with tcgen05.commit;
+//   - warps 2-5 drain each finished accumulator with tcgen05.ld (one tile
+//     row per thread) into FP32 registers, then store the tile transposed,
+//     which makes each warp's store one 128-byte line; the epilogue splits
+//     the result into the next pass's TF32 pair, applies the eigenvalue
+//     division of the box solve (pass 2, real kappa) or writes plain FP32
+//     (pass 4).
+// Every mbarrier wait is bounded; on timeout the kernel records an error
+// bit, drains its own copies and frees its TMEM.
+//
+// Correction and extraction run in FP32 from FP32 copies of the domain's
+// tables; GMRES and the steppers stay in FP64.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
 #include "internal.h"
 
 namespace kfbi {
+namespace tc {
+
+constexpr int BM = 128, BN = 64, BK = 32;
+constexpr int STAGES = 4;
+constexpr int A_BYTES = BM * BK * 4;          // 16 KiB
+constexpr int B_BYTES = BN * BK * 4;          // 8 KiB
+constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;  // A_hi, A_lo, B_hi, B_lo
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
+constexpr int THREADS = 192;                  // producer, MMA, 4 drain/epilogue warps
+constexpr int NACC = 8;                       // TMEM accumulators in flight
+constexpr uint32_t TMEM_COLS = NACC * BN;     // 512 columns: all of TMEM
+// kind::tf32, D = F32, A = B = TF32, both K-major, N = BN, M = BM
+constexpr uint32_t IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                           ((uint32_t)(BM >> 4) << 24);
+constexpr long long WAIT_LIMIT = 4000000000LL;  // cycles (~2 s)
+
+struct PassParams {
+  float* out_hi;
+  float* out_lo;
+  const float* lam;
+  int Mp, n1, mode, nk;  // mode 0: split, 1: eigen-divide + split, 2: plain fp32
+  float kre, scale;
+  int* err;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait on an mbarrier phase; false after WAIT_LIMIT cycles.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity))
+    if (clock64() - t0 > WAIT_LIMIT) return false;
+  return true;
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar,
+                                            int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major tile of 128-byte rows, 128B
+// swizzle, 8-row groups 1024 bytes apart.
+__device__ __forceinline__ uint64_t desc_sw128(const void* p) {
+  uint64_t d = (uint64_t)((smem_u32(p) >> 4) & 0x3FFFu);
+  d |= (uint64_t)1 << 16;             // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;   // stride byte offset
+  d |= (uint64_t)1 << 46;             // descriptor version
+  d |= (uint64_t)2 << 61;             // SWIZZLE_128B
+  return d;
+}
+
+__device__ __forceinline__ void umma_tf32(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+      "l"(a), "l"(b), "r"(IDESC), "r"(acc));
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32_nowait(uint32_t taddr, uint32_t* r) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32"
+      " {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15,"
+      " %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31},"
+      " [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+        "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+        "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+        "=r"(r[31])
+      : "r"(taddr));
+}
+
+// One DST-I pass.  The tensor core accumulates only one K-block (32 terms x
+// 3 products) into a TMEM accumulator; the drain warps add each K-block's
+// partial tile into FP32 registers with round-to-nearest adds while the MMA
+// fills the next of NACC accumulators.  Accumulating the whole K range inside the
+// tensor core lets its FP32 rounding error grow linearly with K (measured
+// 2.5e-5 relative at K = 1024); per-block draining keeps it at the level of
+// one block.
+__global__ void __launch_bounds__(THREADS, 1)
+    k_tc_dst_pass(const __grid_constant__ CUtensorMap mAhi, const __grid_constant__ CUtensorMap mAlo,
+                  const __grid_constant__ CUtensorMap mBhi, const __grid_constant__ CUtensorMap mBlo,
+                  PassParams prm) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* tiles = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t* full = (uint64_t*)(tiles + STAGES * STAGE_BYTES);
+  uint64_t* empty = full + STAGES;
+  uint64_t* accf = empty + STAGES;  // accumulator b holds a finished K-block
+  uint64_t* acce = accf + NACC;     // accumulator b has been drained
+  uint64_t* done = acce + NACC;     // all MMAs retired
+  uint32_t* tmem_slot = (uint32_t*)(done + 1);
+  volatile int* s_state = (volatile int*)(tmem_slot + 1);  // [0] abort, [1] issued, [2] consumed
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int row0 = blockIdx.y * BM;
+  const int col0 = blockIdx.x * BN;
+  const int nk = prm.nk;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < NACC; ++b) {
+      mbar_init(&accf[b], 1);
+      mbar_init(&acce[b], 4);
+    }
+    mbar_init(done, 1);
+    s_state[0] = 0;
+    s_state[1] = 0;
+    s_state[2] = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // TMA producer
+      int kb = 0;
+      for (; kb < nk; ++kb) {
+        const int s = kb % STAGES, n = kb / STAGES;
+        if (s_state[0] || !mbar_wait(&empty[s], (uint32_t)((n & 1) ^ 1))) {
+          s_state[0] = 1;
+          atomicOr(prm.err, 1);
+          break;
+        }
+        uint8_t* st = tiles + s * STAGE_BYTES;
+        mbar_expect_tx(&full[s], STAGE_BYTES);
+        const int kx = kb * BK;
+        tma_load_2d(st, &mAhi, &full[s], kx, row0);
+        tma_load_2d(st + A_BYTES, &mAlo, &full[s], kx, row0);
+        tma_load_2d(st + 2 * A_BYTES, &mBhi, &full[s], kx, col0);
+        tma_load_2d(st + 2 * A_BYTES + B_BYTES, &mBlo, &full[s], kx, col0);
+      }
+      s_state[1] = kb;
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // MMA issuer
+      int kb = 0;
+      for (; kb < nk; ++kb) {
+        const int s = kb % STAGES, n = kb / STAGES;
+        const int b = kb % NACC, nbuf = kb / NACC;
+        if (s_state[0] || !mbar_wait(&full[s], (uint32_t)(n & 1)) ||
+            !mbar_wait(&acce[b], (uint32_t)((nbuf & 1) ^ 1))) {
+          s_state[0] = 1;
+          atomicOr(prm.err, 2);
+          break;
+        }
+        tc_fence_after();
+        uint8_t* st = tiles + s * STAGE_BYTES;
+        const uint64_t ah = desc_sw128(st), al = desc_sw128(st + A_BYTES);
+        const uint64_t bh = desc_sw128(st + 2 * A_BYTES),
+                       bl = desc_sw128(st + 2 * A_BYTES + B_BYTES);
+        const uint32_t td = tmem + (uint32_t)(b * BN);
+#pragma unroll
+        for (int k = 0; k < BK / 8; ++k) {
+          const uint64_t o = (uint64_t)(2 * k);  // 8 tf32 = 32 bytes, in 16-byte units
+          umma_tf32(td, ah + o, bh + o, k ? 1u : 0u);
+          umma_tf32(td, ah + o, bl + o, 1u);
+          umma_tf32(td, al + o, bh + o, 1u);
+        }
+        umma_commit(&empty[s]);
+        umma_commit(&accf[b]);
+      }
+      s_state[2] = kb;
+      umma_commit(done);
+    }
+    __syncwarp();
+  } else {
+    // drain / epilogue warps: TMEM lane quarter (warp % 4) = tile rows
+    const int q = warp & 3;
+    const uint32_t lane_base = (uint32_t)(q * 32) << 16;
+    float acc[BN];
+#pragma unroll
+    for (int j = 0; j < BN; ++j) acc[j] = 0.f;
+    bool ok = true;
+    for (int kb = 0; kb < nk; ++kb) {
+      const int b = kb % NACC;
+      // one lane waits, the warp follows its verdict (tcgen05.ld needs the
+      // whole warp converged)
+      int got = 1;
+      if (lane == 0)
+        got = (!s_state[0] && mbar_wait(&accf[b], (uint32_t)((kb / NACC) & 1))) ? 1 : 0;
+      got = __shfl_sync(0xffffffffu, got, 0);
+      if (!got) {
+        ok = false;
+        if (lane == 0) {
+          s_state[0] = 1;
+          atomicOr(prm.err, 4);
+        }
+        break;
+      }
+      tc_fence_after();
+      uint32_t raw[BN];
+#pragma unroll
+      for (int cc = 0; cc < BN; cc += 32)
+        tmem_ld32_nowait(tmem + lane_base + (uint32_t)(b * BN + cc), &raw[cc]);
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+      for (int j = 0; j < BN; ++j) acc[j] += __uint_as_float(raw[j]);
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acce[b]);
+    }
+    if (ok && !s_state[0]) {
+      const int Mp = prm.Mp;
+      const int grow = row0 + q * 32 + lane;
+      const int p = grow / Mp, rr = grow - p * Mp;
+      const size_t pbase = (size_t)p * Mp * Mp + rr;
+      const float lam_r = (prm.mode == 1) ? prm.lam[rr] : 0.f;
+#pragma unroll
+      for (int j = 0; j < BN; ++j) {
+        const int c = col0 + j;
+        float x = acc[j];
+        if (prm.mode == 1)
+          x = (rr < prm.n1 && c < prm.n1) ? x * (prm.scale / (lam_r + prm.lam[c] - prm.kre)) : 0.f;
+        const size_t o = pbase + (size_t)c * Mp;
+        if (prm.mode == 2) {
+          prm.out_hi[o] = x;
+        } else {
+          const float hi = tf32_round(x);
+          prm.out_hi[o] = hi;
+          prm.out_lo[o] = tf32_round(x - hi);
+        }
+      }
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && s_state[0]) {
+    // drain TMA copies that were issued but never consumed
+    for (int kb = s_state[2]; kb < s_state[1]; ++kb)
+      mbar_wait(&full[kb % STAGES], (uint32_t)((kb / STAGES) & 1));
+  }
+  if (warp == 1) {
+    if (lane == 0) {
+      if (!mbar_wait(done, 0u)) atomicOr(prm.err, 8);
+    }
+    __syncwarp();
+    tc_fence_after();
+  }
+  __syncthreads();
+  if (warp == 1)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(TMEM_COLS));
+}
+
+// ---------------------------------------------------------------------------
+// FP32 correction / extraction and layout kernels of the mixed path
+// ---------------------------------------------------------------------------
+
+// FP64 planes -> TF32 pairs (hi = tf32(x), lo = tf32(x - hi)).
+__global__ void k_split64(const double* __restrict__ src, float* __restrict__ hi,
+                          float* __restrict__ lo, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const double x = src[i];
+    const float h = tf32_round((float)x);
+    hi[i] = h;
+    lo[i] = tf32_round((float)(x - (double)h));
+  }
+}
+
+// Corrected right-hand side at the irregular nodes in FP32, written as a
+// TF32 pair (same tables as k_correct, FP32 copies).
+template <bool C>
+__global__ void k_correct32(float* __restrict__ Rh, float* __restrict__ Rl, size_t plane,
+                            const double* __restrict__ ft, const int* __restrict__ irr_off,
+                            const int* __restrict__ arm_start, const int* __restrict__ arm_k0,
+                            const float* __restrict__ alpha, const float* __restrict__ beta,
+                            const int* __restrict__ fidx, const float* __restrict__ fcoef,
+                            int n_irr, int n_arms, int nb, const double* __restrict__ phi, int ps,
+                            float kre, float kim) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= n_irr) return;
+  const int off = irr_off[n];
+  float sr = ft ? (float)ft[off] : 0.f;
+  float si = (C && ft) ? (float)ft[plane + off] : 0.f;
+  const int a1 = arm_start[n + 1];
+  for (int a = arm_start[n]; a < a1; ++a) {
+    int k = arm_k0[a];
+    float ar = 0.f, ai = 0.f, br = 0.f, bi = 0.f;
+#pragma unroll
+    for (int m = 0; m < 6; ++m) {
+      const float al = alpha[m * n_arms + a], be = beta[m * n_arms + a];
+      const float pr = (float)phi[(size_t)k * ps];
+      ar = fmaf(al, pr, ar);
+      br = fmaf(be, pr, br);
+      if (C) {
+        const float pi = (float)phi[(size_t)k * ps + 1];
+        ai = fmaf(al, pi, ai);
+        bi = fmaf(be, pi, bi);
+      }
+      k = (k + 1 == nb) ? 0 : k + 1;
+    }
+    sr += ar + kre * br;
+    if (C) {
+      sr -= kim * bi;
+      si += ai + kre * bi + kim * br;
+    }
+    if (ft) {
+      const int f0 = fidx[a], f1 = fidx[n_arms + a];
+      const float c0 = fcoef[a], c1 = fcoef[n_arms + a];
+      sr += c0 * (float)ft[f0] + c1 * (float)ft[f1];
+      if (C) si += c0 * (float)ft[plane + f0] + c1 * (float)ft[plane + f1];
+    }
+  }
+  float h = tf32_round(sr);
+  Rh[off] = h;
+  Rl[off] = tf32_round(sr - h);
+  if (C) {
+    h = tf32_round(si);
+    Rh[plane + off] = h;
+    Rl[plane + off] = tf32_round(si - h);
+  }
+}
+
+// Complex eigenvalue division on TF32 pairs (two planes), in FP64.
+__global__ void k_eig_split_cplx(float* __restrict__ hi, float* __restrict__ lo, size_t plane,
+                                 int Mp, int n1, const double* __restrict__ lam, double kre,
+                                 double kim, double scale) {
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < plane;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    const int a = (int)(idx / Mp), b = (int)(idx % Mp);
+    if (a >= n1 || b >= n1) continue;
+    const double x = (double)hi[idx] + (double)lo[idx];
+    const double y = (double)hi[plane + idx] + (double)lo[plane + idx];
+    const double dr = lam[a] + lam[b] - kre;
+    const double den = scale / (dr * dr + kim * kim);
+    const double zr = (x * dr - y * kim) * den, zi = (x * kim + y * dr) * den;
+    float h = tf32_round((float)zr);
+    hi[idx] = h;
+    lo[idx] = tf32_round((float)(zr - (double)h));
+    h = tf32_round((float)zi);
+    hi[plane + idx] = h;
+    lo[plane + idx] = tf32_round((float)(zi - (double)h));
+  }
+}
+
+template <bool C>
+__global__ void k_extract32(const float* __restrict__ U, size_t plane,
+                            const double* __restrict__ ft, const int* __restrict__ gidx,
+                            const float* __restrict__ w, const float* __restrict__ A,
+                            const float* __restrict__ B, const int* __restrict__ fidx,
+                            const float* __restrict__ fcoef, int nb,
+                            const double* __restrict__ phi, int ps, float kre, float kim,
+                            double* __restrict__ out, int os) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nb) return;
+  float sr = 0.f, si = 0.f;
+#pragma unroll
+  for (int m = 0; m < 6; ++m) {
+    const int g = gidx[m * nb + k];
+    const float wm = w[m * nb + k];
+    sr = fmaf(wm, U[g], sr);
+    if (C) si = fmaf(wm, U[plane + g], si);
+  }
+  float ar = 0.f, ai = 0.f, br = 0.f, bi = 0.f;
+  int kk = k - 2;
+  if (kk < 0) kk += nb;
+#pragma unroll
+  for (int j = 0; j < 6; ++j) {
+    const float a = A[j * nb + k], b = B[j * nb + k];
+    const float pr = (float)phi[(size_t)kk * ps];
+    ar = fmaf(a, pr, ar);
+    br = fmaf(b, pr, br);
+    if (C) {
+      const float pi = (float)phi[(size_t)kk * ps + 1];
+      ai = fmaf(a, pi, ai);
+      bi = fmaf(b, pi, bi);
+    }
+    kk = (kk + 1 == nb) ? 0 : kk + 1;
+  }
+  sr += ar + kre * br;
+  if (C) {
+    sr -= kim * bi;
+    si += ai + kre * bi + kim * br;
+  }
+  if (ft) {
+    const int g = fidx[k];
+    const float c = fcoef[k];
+    sr += c * (float)ft[g];
+    if (C) si += c * (float)ft[plane + g];
+  }
+  out[(size_t)k * os] = (double)sr;
+  if (C)
+    out[(size_t)k * os + 1] = (double)si;
+  else if (os == 2)
+    out[(size_t)k * os + 1] = 0.0;
+}
+
+__global__ void k_f32_to_f64(const float* __restrict__ src, double* __restrict__ dst, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x)
+    dst[i] = (double)src[i];
+}
+
+// Residual of the five-point system in FP64 for the iterative refinement of
+// the box solve: res = R - (D_xx + D_yy - kappa) U with U = 0 outside the
+// (n1 x n1) interior, written as a TF32 pair for the correction solve.
+template <bool C>
+__global__ void k_resid_split(const double* __restrict__ R, const double* __restrict__ U,
+                              float* __restrict__ hi, float* __restrict__ lo, int Mp, int n1,
+                              double inv_h2, double kre, double kim) {
+  const size_t plane = (size_t)Mp * Mp;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < plane;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    const int r = (int)(idx / Mp), c = (int)(idx % Mp);
+    for (int p = 0; p < (C ? 2 : 1); ++p) {
+      double res = 0.0;
+      if (r < n1 && c < n1) {
+        const double* Up = U + p * plane;
+        const double u = Up[idx];
+        const double e = c + 1 < n1 ? Up[idx + 1] : 0.0;
+        const double w = c > 0 ? Up[idx - 1] : 0.0;
+        const double n = r + 1 < n1 ? Up[idx + Mp] : 0.0;
+        const double s = r > 0 ? Up[idx - Mp] : 0.0;
+        double Lu = (e + w + n + s - 4.0 * u) * inv_h2 - kre * u;
+        if (C) {
+          // -kappa u, imaginary part of kappa couples the planes
+          const double uo = U[(1 - p) * plane + idx];
+          Lu += (p == 0) ? kim * uo : -kim * uo;
+        }
+        res = R[p * plane + idx] - Lu;
+      }
+      const float h = tf32_round((float)res);
+      hi[p * plane + idx] = h;
+      lo[p * plane + idx] = tf32_round((float)(res - (double)h));
+    }
+  }
+}
+
+__global__ void k_add_f32(double* __restrict__ dst, const float* __restrict__ src, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x)
+    dst[i] += (double)src[i];
+}
+
+}  // namespace tc
+
+using namespace tc;
 
 struct TcDst {
+  int Mp = 0, n1 = 0;
+  float *S_hi = nullptr, *S_lo = nullptr, *lam = nullptr;
+  float *Rh = nullptr, *Rl = nullptr, *T1h = nullptr, *T1l = nullptr, *T2h = nullptr,
+        *T2l = nullptr, *U = nullptr;
+  int* err = nullptr;
+  CUtensorMap mS_hi, mS_lo, mR_hi, mR_lo, mT1_hi, mT1_lo, mT2_hi, mT2_lo;
+  int rhs_sparse_planes = 0;
   long long bytes = 0;
 };
 
-TcDst* tc_create(kfbi_domain*) {
-  throw Status{KFBI_ERR_UNSUPPORTED, "KFBI_MIXED_TF32 is not built yet"};
+static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static std::once_flag once;
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  std::call_once(once, []() {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+  });
+  return fn;
 }
-void tc_destroy(TcDst* tc) { delete tc; }
-void tc_apply(kfbi_domain*, double, double, const double*, int, const double*, double*, int, bool,
-              cudaStream_t) {
-  throw Status{KFBI_ERR_UNSUPPORTED, "KFBI_MIXED_TF32 is not built yet"};
+
+// 2-D fp32 tensor map: inner dimension `inner` (contiguous), `rows` rows,
+// box 32 x box_rows elements, 128B swizzle.
+static void make_map(CUtensorMap* m, float* base, int inner, int rows, int box_rows) {
+  auto fn = encode_fn();
+  if (!fn) throw Status{KFBI_ERR_CUDA, "cuTensorMapEncodeTiled is not available"};
+  cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)inner * sizeof(float)};
+  cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) throw Status{KFBI_ERR_CUDA, "cuTensorMapEncodeTiled failed"};
 }
-long long tc_bytes(const TcDst* tc) { return tc ? tc->bytes : 0; }
+
+TcDst* tc_create(kfbi_domain* D) {
+  TcDst* T = new TcDst();
+  try {
+    T->Mp = D->Mp;
+    T->n1 = D->n1;
+    const size_t plane = (size_t)D->Mp * D->Mp;
+    auto alloc = [&](float** p, size_t n) {
+      KFBI_CUDA(cudaMalloc(p, n * sizeof(float)));
+      T->bytes += (long long)(n * sizeof(float));
+    };
+    alloc(&T->S_hi, plane);
+    alloc(&T->S_lo, plane);
+    alloc(&T->lam, D->Mp);
+    float** bufs[] = {&T->Rh, &T->Rl, &T->T1h, &T->T1l, &T->T2h, &T->T2l, &T->U};
+    for (float** b : bufs) alloc(b, 2 * plane);
+    KFBI_CUDA(cudaMemset(T->Rh, 0, 2 * plane * sizeof(float)));
+    KFBI_CUDA(cudaMemset(T->Rl, 0, 2 * plane * sizeof(float)));
+    T->rhs_sparse_planes = 2;
+    T->err = (int*)(D->d_scal + 6);
+    KFBI_CUDA(cudaMemset(T->err, 0, sizeof(int)));
+    // TF32 pairs of S and FP32 eigenvalues from the FP64 device tables
+    std::vector<double> S(plane), lam(D->Mp);
+    KFBI_CUDA(cudaMemcpy(S.data(), D->d_S, plane * sizeof(double), cudaMemcpyDeviceToHost));
+    KFBI_CUDA(cudaMemcpy(lam.data(), D->d_lam, D->Mp * sizeof(double), cudaMemcpyDeviceToHost));
+    std::vector<float> sh(plane), sl(plane), l32(D->Mp);
+    for (size_t i = 0; i < plane; ++i) {
+      sh[i] = tf32_round((float)S[i]);
+      sl[i] = tf32_round((float)(S[i] - (double)sh[i]));
+    }
+    for (int i = 0; i < D->Mp; ++i) l32[i] = (float)lam[i];
+    KFBI_CUDA(cudaMemcpy(T->S_hi, sh.data(), plane * sizeof(float), cudaMemcpyHostToDevice));
+    KFBI_CUDA(cudaMemcpy(T->S_lo, sl.data(), plane * sizeof(float), cudaMemcpyHostToDevice));
+    KFBI_CUDA(cudaMemcpy(T->lam, l32.data(), D->Mp * sizeof(float), cudaMemcpyHostToDevice));
+    const int Mp = D->Mp;
+    make_map(&T->mS_hi, T->S_hi, Mp, Mp, BN);
+    make_map(&T->mS_lo, T->S_lo, Mp, Mp, BN);
+    make_map(&T->mR_hi, T->Rh, Mp, 2 * Mp, BM);
+    make_map(&T->mR_lo, T->Rl, Mp, 2 * Mp, BM);
+    make_map(&T->mT1_hi, T->T1h, Mp, 2 * Mp, BM);
+    make_map(&T->mT1_lo, T->T1l, Mp, 2 * Mp, BM);
+    make_map(&T->mT2_hi, T->T2h, Mp, 2 * Mp, BM);
+    make_map(&T->mT2_lo, T->T2l, Mp, 2 * Mp, BM);
+    KFBI_CUDA(cudaFuncSetAttribute(k_tc_dst_pass, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   SMEM_BYTES));
+  } catch (...) {
+    tc_destroy(T);
+    throw;
+  }
+  return T;
+}
+
+void tc_destroy(TcDst* T) {
+  if (!T) return;
+  float* ptrs[] = {T->S_hi, T->S_lo, T->lam, T->Rh, T->Rl, T->T1h, T->T1l, T->T2h, T->T2l, T->U};
+  for (float* p : ptrs)
+    if (p) cudaFree(p);
+  delete T;
+}
+
+long long tc_bytes(const TcDst* T) { return T ? T->bytes : 0; }
+
+static void launch_pass(TcDst* T, const CUtensorMap& ah, const CUtensorMap& al, float* oh,
+                        float* ol, int mode, int P, float kre, float scale, cudaStream_t st) {
+  PassParams prm;
+  prm.out_hi = oh;
+  prm.out_lo = ol;
+  prm.lam = T->lam;
+  prm.Mp = T->Mp;
+  prm.n1 = T->n1;
+  prm.mode = mode;
+  prm.nk = T->Mp / BK;
+  prm.kre = kre;
+  prm.scale = scale;
+  prm.err = T->err;
+  dim3 grid(T->Mp / BN, P * T->Mp / BM);
+  KFBI_LAUNCH_P(KFBI_PROF_DST, k_tc_dst_pass, grid, THREADS, SMEM_BYTES, st, ah, al, T->mS_hi,
+                T->mS_lo, prm);
+}
+
+// Four TF32x3 passes: (Rh, Rl) -> U (fp32 planes), eigenvalue division after
+// the forward transform.
+static void tc_box_solve(kfbi_domain* D, double kre, double kim, int P, cudaStream_t st) {
+  TcDst* T = D->tc;
+  const size_t plane = (size_t)T->Mp * T->Mp;
+  const bool C = kim != 0.0;
+  const float scale = (float)((2.0 / D->M) * (2.0 / D->M));
+  launch_pass(T, T->mR_hi, T->mR_lo, T->T1h, T->T1l, 0, P, 0.f, 0.f, st);
+  launch_pass(T, T->mT1_hi, T->mT1_lo, T->T2h, T->T2l, C ? 0 : 1, P, (float)kre, scale, st);
+  if (C)
+    KFBI_LAUNCH_P(KFBI_PROF_GRID, k_eig_split_cplx, grid_for(plane, 256), 256, 0, st, T->T2h,
+                  T->T2l, plane, T->Mp, T->n1, D->d_lam, kre, kim, (2.0 / D->M) * (2.0 / D->M));
+  launch_pass(T, T->mT2_hi, T->mT2_lo, T->T1h, T->T1l, 0, P, 0.f, 0.f, st);
+  launch_pass(T, T->mT1_hi, T->mT1_lo, T->U, nullptr, 2, P, 0.f, 0.f, st);
+}
+
+void tc_apply(kfbi_domain* D, double kre, double kim, const double* phi, int ps, const double* ft,
+              double* out, int os, bool want_grid, cudaStream_t st) {
+  TcDst* T = D->tc;
+  const bool C = kim != 0.0;
+  const int P = C ? 2 : 1;
+  const int Mp = T->Mp;
+  const size_t plane = (size_t)Mp * Mp;
+  if (ft) {
+    KFBI_LAUNCH_P(KFBI_PROF_GRID, k_split64, grid_for(P * plane, 256), 256, 0, st, ft, T->Rh,
+                  T->Rl, P * plane);
+    T->rhs_sparse_planes = 0;
+  } else if (T->rhs_sparse_planes < P) {
+    KFBI_CUDA(cudaMemsetAsync(T->Rh, 0, 2 * plane * sizeof(float), st));
+    KFBI_CUDA(cudaMemsetAsync(T->Rl, 0, 2 * plane * sizeof(float), st));
+    T->rhs_sparse_planes = 2;
+  }
+  if (D->n_irr > 0) {
+    if (C)
+      KFBI_LAUNCH_P(KFBI_PROF_CORRECT, k_correct32<true>, (D->n_irr + 127) / 128, 128, 0, st,
+                    T->Rh, T->Rl, plane, ft, D->d_irr_off, D->d_arm_start, D->d_arm_k0,
+                    D->d_arm_alpha32, D->d_arm_beta32, D->d_arm_fidx, D->d_arm_fcoef32,
+                    D->n_irr, D->n_arms, D->nb, phi, ps, (float)kre, (float)kim);
+    else
+      KFBI_LAUNCH_P(KFBI_PROF_CORRECT, k_correct32<false>, (D->n_irr + 127) / 128, 128, 0, st,
+                    T->Rh, T->Rl, plane, ft, D->d_irr_off, D->d_arm_start, D->d_arm_k0,
+                    D->d_arm_alpha32, D->d_arm_beta32, D->d_arm_fidx, D->d_arm_fcoef32,
+                    D->n_irr, D->n_arms, D->nb, phi, ps, (float)kre, (float)kim);
+  }
+  tc_box_solve(D, kre, kim, P, st);
+  if (out) {
+    if (C)
+      KFBI_LAUNCH_P(KFBI_PROF_EXTRACT, k_extract32<true>, (D->nb + 127) / 128, 128, 0, st, T->U,
+                    plane, ft, D->d_node_gidx, D->d_node_w32, D->d_node_a32, D->d_node_b32,
+                    D->d_node_fidx, D->d_node_fcoef32, D->nb, phi, ps, (float)kre, (float)kim,
+                    out, os);
+    else
+      KFBI_LAUNCH_P(KFBI_PROF_EXTRACT, k_extract32<false>, (D->nb + 127) / 128, 128, 0, st, T->U,
+                    plane, ft, D->d_node_gidx, D->d_node_w32, D->d_node_a32, D->d_node_b32,
+                    D->d_node_fidx, D->d_node_fcoef32, D->nb, phi, ps, (float)kre, (float)kim,
+                    out, os);
+  }
+  if (want_grid)
+    KFBI_LAUNCH_P(KFBI_PROF_GRID, k_f32_to_f64, grid_for(P * plane, 256), 256, 0, st, T->U,
+                  D->d_U, P * plane);
+  KFBI_CHECK_LAUNCH();
+}
+
+// Accurate application for the refinement residuals of the steppers: the
+// corrected right-hand side in FP64, one TF32x3 box solve, the FP64
+// five-point residual, a second box solve for the correction (the solve
+// error drops from ~delta to ~delta^2, delta ~ 2e-6), and the FP64
+// extraction.  The grid solution is left in D->d_U (FP64 planes).
+void tc_apply_accurate(kfbi_domain* D, double kre, double kim, const double* phi, int ps,
+                       const double* ft, double* out, int os, cudaStream_t st) {
+  TcDst* T = D->tc;
+  const bool C = kim != 0.0;
+  const int P = C ? 2 : 1;
+  const int Mp = T->Mp;
+  const size_t plane = (size_t)Mp * Mp;
+  correct_fp64(D, kre, kim, phi, ps, ft, st);  // D->d_R: FP64 corrected RHS
+  KFBI_LAUNCH_P(KFBI_PROF_GRID, k_split64, grid_for(P * plane, 256), 256, 0, st, D->d_R, T->Rh,
+                T->Rl, P * plane);
+  T->rhs_sparse_planes = 0;
+  tc_box_solve(D, kre, kim, P, st);
+  KFBI_LAUNCH_P(KFBI_PROF_GRID, k_f32_to_f64, grid_for(P * plane, 256), 256, 0, st, T->U, D->d_U,
+                P * plane);
+  const double inv_h2 = 1.0 / (D->h * D->h);
+  if (C)
+    KFBI_LAUNCH_P(KFBI_PROF_GRID, k_resid_split<true>, grid_for(plane, 256), 256, 0, st, D->d_R,
+                  D->d_U, T->Rh, T->Rl, Mp, T->n1, inv_h2, kre, kim);
+  else
+    KFBI_LAUNCH_P(KFBI_PROF_GRID, k_resid_split<false>, grid_for(plane, 256), 256, 0, st, D->d_R,
+                  D->d_U, T->Rh, T->Rl, Mp, T->n1, inv_h2, kre, kim);
+  tc_box_solve(D, kre, kim, P, st);
+  KFBI_LAUNCH_P(KFBI_PROF_GRID, k_add_f32, grid_for(P * plane, 256), 256, 0, st, D->d_U, T->U,
+                P * plane);
+  if (out) extract_fp64(D, kre, kim, phi, ps, ft, out, os, st);
+  KFBI_CHECK_LAUNCH();
+}
 
 }  // namespace kfbi
