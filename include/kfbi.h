@@ -209,9 +209,11 @@ long long kfbi_launch_count(void);
 long long kfbi_domain_device_bytes(const kfbi_domain* dom);
 
 /* Kernel timing with CUDA events recorded on the launching stream around
- * every launch of a kernel class (off by default; enabling it adds two
- * event records per timed launch).  kfbi_profile_read synchronises the
- * recorded events and returns the launch count and summed duration. */
+ * every launch of the enabled kernel classes (off by default).
+ * kfbi_profile_enable takes a bit mask of kfbi_prof_class bits (1 << cls;
+ * 0 disables); each timed launch adds two event records.
+ * kfbi_profile_read synchronises the recorded events and returns the launch
+ * count and summed duration of one class. */
 typedef enum {
   KFBI_PROF_DST = 0,     /* one DST-I pass (GEMM) of the box solve */
   KFBI_PROF_CORRECT = 1, /* corrected right-hand side */
@@ -220,7 +222,7 @@ typedef enum {
   KFBI_PROF_GRID = 4,    /* elementwise grid kernels (steppers, layout) */
   KFBI_PROF_NCLASS = 5
 } kfbi_prof_class;
-void kfbi_profile_enable(int on);
+void kfbi_profile_enable(int class_mask);
 void kfbi_profile_reset(void);
 kfbi_status kfbi_profile_read(int cls, long long* launches, double* total_ms);
 

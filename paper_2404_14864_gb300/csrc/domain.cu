@@ -504,7 +504,7 @@ kfbi_status kfbi_create_domain(const kfbi_domain_desc* desc, void* stream, kfbi_
     KFBI_CUDA(cudaGetDevice(&D->device));
     upload_domain(D, plan);
     gmres_alloc(D);
-    if (desc->precision == KFBI_MIXED_TF32) D->tc = tc_create(D);
+    if (desc->precision == KFBI_MIXED_TF32) D->tc = tc_create(D, plan);
     KFBI_CUDA(cudaStreamSynchronize(st));
     return KFBI_OK;
   });

@@ -21,6 +21,7 @@ void set_global_error(const std::string& s);
 
 // Optional per-class event timing (prof.cpp).
 extern bool g_prof_on;
+extern unsigned g_prof_mask;
 void* prof_begin(int cls, cudaStream_t st);
 void prof_end(void* tok, cudaStream_t st);
 
@@ -232,7 +233,7 @@ void check_device_flags(kfbi_domain* D);
 void gmres_free(kfbi_domain* D);
 
 // tc_dst.cu (mixed path)
-TcDst* tc_create(kfbi_domain* D);
+TcDst* tc_create(kfbi_domain* D, const Plan& P);
 void tc_destroy(TcDst* tc);
 void tc_apply(kfbi_domain* D, double kre, double kim, const double* phi, int phi_stride,
               const double* ft, double* out, int out_stride, bool want_grid, cudaStream_t st);

@@ -8,6 +8,7 @@
 namespace kfbi {
 
 bool g_prof_on = false;
+unsigned g_prof_mask = 0;
 
 namespace {
 struct Rec {
@@ -31,6 +32,7 @@ cudaEvent_t take() {
 }  // namespace
 
 void* prof_begin(int cls, cudaStream_t st) {
+  if (!((g_prof_mask >> cls) & 1u)) return nullptr;
   std::lock_guard<std::mutex> lk(mu);
   Rec r{cls, take(), take()};
   if (!r.a || !r.b) return nullptr;
@@ -52,7 +54,10 @@ using namespace kfbi;
 
 extern "C" {
 
-void kfbi_profile_enable(int on) { g_prof_on = on != 0; }
+void kfbi_profile_enable(int mask) {
+  g_prof_mask = (unsigned)mask;
+  g_prof_on = mask != 0;
+}
 
 void kfbi_profile_reset(void) {
   std::lock_guard<std::mutex> lk(mu);

@@ -26,6 +26,7 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -55,6 +56,8 @@ struct PassParams {
   float* out_lo;
   const float* lam;
   int Mp, n1, mode, nk;  // mode 0: split, 1: eigen-divide + split, 2: plain fp32
+  int kb0;               // first K-block (the pass covers K-blocks kb0 .. kb0 + nk - 1)
+  int ct0;               // first output column tile
   float kre, scale;
   int* err;
 };
@@ -175,7 +178,7 @@ __global__ void __launch_bounds__(THREADS, 1)
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int row0 = blockIdx.y * BM;
-  const int col0 = blockIdx.x * BN;
+  const int col0 = (prm.ct0 + blockIdx.x) * BN;
   const int nk = prm.nk;
 
   if (threadIdx.x == 0) {
@@ -217,7 +220,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         }
         uint8_t* st = tiles + s * STAGE_BYTES;
         mbar_expect_tx(&full[s], STAGE_BYTES);
-        const int kx = kb * BK;
+        const int kx = (prm.kb0 + kb) * BK;
         tma_load_2d(st, &mAhi, &full[s], kx, row0);
         tma_load_2d(st + A_BYTES, &mAlo, &full[s], kx, row0);
         tma_load_2d(st + 2 * A_BYTES, &mBhi, &full[s], kx, col0);
@@ -362,7 +365,7 @@ __global__ void k_correct32(float* __restrict__ Rh, float* __restrict__ Rl, size
                             const float* __restrict__ alpha, const float* __restrict__ beta,
                             const int* __restrict__ fidx, const float* __restrict__ fcoef,
                             int n_irr, int n_arms, int nb, const double* __restrict__ phi, int ps,
-                            float kre, float kim) {
+                            float kre, float kim, float* __restrict__ rv) {
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= n_irr) return;
   const int off = irr_off[n];
@@ -397,6 +400,11 @@ __global__ void k_correct32(float* __restrict__ Rh, float* __restrict__ Rl, size
       if (C) si += c0 * (float)ft[plane + f0] + c1 * (float)ft[plane + f1];
     }
   }
+  if (rv) {  // compact values for the sparse first pass
+    rv[n] = sr;
+    if (C) rv[n_irr + n] = si;
+    return;
+  }
   float h = tf32_round(sr);
   Rh[off] = h;
   Rl[off] = tf32_round(sr - h);
@@ -405,6 +413,121 @@ __global__ void k_correct32(float* __restrict__ Rh, float* __restrict__ Rl, size
     Rh[plane + off] = h;
     Rl[plane + off] = tf32_round(si - h);
   }
+}
+
+// Sparse first pass for a right-hand side supported on the irregular nodes
+// only (every GMRES application): T1[p][c][r] = sum over the irregular
+// nodes n of row r of v_n S[k_n][c], for the rows rmin .. rmin + nrows - 1
+// that hold irregular nodes, written as a TF32 pair.  Rows outside that
+// range are never written and stay zero.  32 x 32 tile per block, staged
+// through shared memory so both the S reads and the transposed writes are
+// coalesced.
+__global__ void __launch_bounds__(256) k_sparse_p1(const float* __restrict__ rv, int n_irr,
+                                                   const int* __restrict__ row_start,
+                                                   const int* __restrict__ node_col, int rmin,
+                                                   int nrows, const float* __restrict__ S32,
+                                                   float* __restrict__ Th, float* __restrict__ Tl,
+                                                   int Mp, int P) {
+  __shared__ float tile[2][32][33];
+  const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  for (int rr = ty; rr < 32; rr += 8) {
+    const int rl = r0 + rr;
+    float a0 = 0.f, a1 = 0.f;
+    if (rl < nrows) {
+      const int ne = row_start[rl + 1];
+      for (int n = row_start[rl]; n < ne; ++n) {
+        const float sv = S32[(size_t)node_col[n] * Mp + c0 + tx];
+        a0 = fmaf(rv[n], sv, a0);
+        if (P == 2) a1 = fmaf(rv[n_irr + n], sv, a1);
+      }
+    }
+    tile[0][rr][tx] = a0;
+    tile[1][rr][tx] = a1;
+  }
+  __syncthreads();
+  const size_t plane = (size_t)Mp * Mp;
+  for (int cc = ty; cc < 32; cc += 8) {
+    const int rl = r0 + tx;
+    if (rl >= nrows) continue;
+    const size_t o = (size_t)(c0 + cc) * Mp + (size_t)(rmin + rl);
+    for (int p = 0; p < P; ++p) {
+      const float x = tile[p][tx][cc];
+      const float h = tf32_round(x);
+      Th[p * plane + o] = h;
+      Tl[p * plane + o] = tf32_round(x - h);
+    }
+  }
+}
+
+// Last pass restricted to the extraction stencil, fused with Eq. 3.36:
+// U(j', i') = sum_a T3[i'][a] S[j'][a] for the six stencil points of node k
+// (one warp each, FP32 lane sums then a tree), then u+ as in k_extract32.
+template <bool C>
+__global__ void __launch_bounds__(192)
+    k_gather_extract(const float* __restrict__ T3, const float* __restrict__ S32, int Mp,
+                     size_t plane, const int* __restrict__ gidx, const float* __restrict__ w,
+                     const float* __restrict__ A, const float* __restrict__ B, int nb,
+                     const double* __restrict__ phi, int ps, float kre, float kim,
+                     double* __restrict__ out, int os) {
+  __shared__ float Ush[6][2];
+  const int k = blockIdx.x;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  {
+    const int off = gidx[warp * nb + k];
+    const int jr = off / Mp, ic = off - jr * Mp;
+    const float* t0 = T3 + (size_t)ic * Mp;
+    const float* sr = S32 + (size_t)jr * Mp;
+    float s0 = 0.f, s1 = 0.f;
+    for (int a = lane; a < Mp; a += 32) {
+      const float sv = sr[a];
+      s0 = fmaf(t0[a], sv, s0);
+      if (C) s1 = fmaf(t0[plane + a], sv, s1);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+      if (C) s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+    }
+    if (lane == 0) {
+      Ush[warp][0] = s0;
+      Ush[warp][1] = s1;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  float sr = 0.f, si = 0.f;
+#pragma unroll
+  for (int m = 0; m < 6; ++m) {
+    const float wm = w[m * nb + k];
+    sr = fmaf(wm, Ush[m][0], sr);
+    if (C) si = fmaf(wm, Ush[m][1], si);
+  }
+  float ar = 0.f, ai = 0.f, br = 0.f, bi = 0.f;
+  int kk = k - 2;
+  if (kk < 0) kk += nb;
+#pragma unroll
+  for (int j = 0; j < 6; ++j) {
+    const float a = A[j * nb + k], b = B[j * nb + k];
+    const float pr = (float)phi[(size_t)kk * ps];
+    ar = fmaf(a, pr, ar);
+    br = fmaf(b, pr, br);
+    if (C) {
+      const float pi = (float)phi[(size_t)kk * ps + 1];
+      ai = fmaf(a, pi, ai);
+      bi = fmaf(b, pi, bi);
+    }
+    kk = (kk + 1 == nb) ? 0 : kk + 1;
+  }
+  sr += ar + kre * br;
+  if (C) {
+    sr -= kim * bi;
+    si += ai + kre * bi + kim * br;
+  }
+  out[(size_t)k * os] = (double)sr;
+  if (C)
+    out[(size_t)k * os + 1] = (double)si;
+  else if (os == 2)
+    out[(size_t)k * os + 1] = 0.0;
 }
 
 // Complex eigenvalue division on TF32 pairs (two planes), in FP64.
@@ -534,7 +657,12 @@ using namespace tc;
 
 struct TcDst {
   int Mp = 0, n1 = 0;
-  float *S_hi = nullptr, *S_lo = nullptr, *lam = nullptr;
+  float *S_hi = nullptr, *S_lo = nullptr, *lam = nullptr, *S32 = nullptr;
+  // sparse route for right-hand sides supported on the irregular nodes
+  float *T1sh = nullptr, *T1sl = nullptr, *rv = nullptr;
+  int *row_start = nullptr, *node_col = nullptr;
+  int rmin = 0, nrows = 0, kb0 = 0, nk2 = 0, ct0 = 0, nt3 = 0;
+  CUtensorMap mT1s_hi, mT1s_lo;
   float *Rh = nullptr, *Rl = nullptr, *T1h = nullptr, *T1l = nullptr, *T2h = nullptr,
         *T2l = nullptr, *U = nullptr;
   int* err = nullptr;
@@ -572,7 +700,7 @@ static void make_map(CUtensorMap* m, float* base, int inner, int rows, int box_r
   if (r != CUDA_SUCCESS) throw Status{KFBI_ERR_CUDA, "cuTensorMapEncodeTiled failed"};
 }
 
-TcDst* tc_create(kfbi_domain* D) {
+TcDst* tc_create(kfbi_domain* D, const Plan& P) {
   TcDst* T = new TcDst();
   try {
     T->Mp = D->Mp;
@@ -584,7 +712,13 @@ TcDst* tc_create(kfbi_domain* D) {
     };
     alloc(&T->S_hi, plane);
     alloc(&T->S_lo, plane);
+    alloc(&T->S32, plane);
     alloc(&T->lam, D->Mp);
+    alloc(&T->T1sh, 2 * plane);
+    alloc(&T->T1sl, 2 * plane);
+    alloc(&T->rv, 2 * (size_t)std::max(1, D->n_irr));
+    KFBI_CUDA(cudaMemset(T->T1sh, 0, 2 * plane * sizeof(float)));
+    KFBI_CUDA(cudaMemset(T->T1sl, 0, 2 * plane * sizeof(float)));
     float** bufs[] = {&T->Rh, &T->Rl, &T->T1h, &T->T1l, &T->T2h, &T->T2l, &T->U};
     for (float** b : bufs) alloc(b, 2 * plane);
     KFBI_CUDA(cudaMemset(T->Rh, 0, 2 * plane * sizeof(float)));
@@ -596,10 +730,42 @@ TcDst* tc_create(kfbi_domain* D) {
     std::vector<double> S(plane), lam(D->Mp);
     KFBI_CUDA(cudaMemcpy(S.data(), D->d_S, plane * sizeof(double), cudaMemcpyDeviceToHost));
     KFBI_CUDA(cudaMemcpy(lam.data(), D->d_lam, D->Mp * sizeof(double), cudaMemcpyDeviceToHost));
-    std::vector<float> sh(plane), sl(plane), l32(D->Mp);
+    std::vector<float> sh(plane), sl(plane), l32(D->Mp), s32(plane);
     for (size_t i = 0; i < plane; ++i) {
       sh[i] = tf32_round((float)S[i]);
       sl[i] = tf32_round((float)(S[i] - (double)sh[i]));
+      s32[i] = (float)S[i];
+    }
+    KFBI_CUDA(cudaMemcpy(T->S32, s32.data(), plane * sizeof(float), cudaMemcpyHostToDevice));
+    // sparse route: rows of the right-hand side that hold irregular nodes
+    // (the irregular list is sorted by row), the K-blocks they span in the
+    // second pass and the output column tiles the extraction stencil reads
+    // in the third pass.
+    const int n1 = D->n1;
+    if (P.n_irr() > 0) {
+      T->rmin = P.irr.front() / n1;
+      const int rmax = P.irr.back() / n1;
+      T->nrows = rmax - T->rmin + 1;
+      std::vector<int> rs(T->nrows + 1, 0), col(P.n_irr());
+      for (int n = 0; n < P.n_irr(); ++n) {
+        rs[P.irr[n] / n1 - T->rmin + 1]++;
+        col[n] = P.irr[n] % n1;
+      }
+      for (int r = 0; r < T->nrows; ++r) rs[r + 1] += rs[r];
+      KFBI_CUDA(cudaMalloc(&T->row_start, rs.size() * sizeof(int)));
+      KFBI_CUDA(cudaMalloc(&T->node_col, col.size() * sizeof(int)));
+      T->bytes += (long long)((rs.size() + col.size()) * sizeof(int));
+      KFBI_CUDA(cudaMemcpy(T->row_start, rs.data(), rs.size() * sizeof(int), cudaMemcpyHostToDevice));
+      KFBI_CUDA(cudaMemcpy(T->node_col, col.data(), col.size() * sizeof(int), cudaMemcpyHostToDevice));
+      T->kb0 = T->rmin / BK;
+      T->nk2 = rmax / BK + 1 - T->kb0;
+      int imin = n1, imax = 0;
+      for (int v : P.node_gidx) {
+        imin = std::min(imin, v % n1);
+        imax = std::max(imax, v % n1);
+      }
+      T->ct0 = imin / BN;
+      T->nt3 = imax / BN + 1 - T->ct0;
     }
     for (int i = 0; i < D->Mp; ++i) l32[i] = (float)lam[i];
     KFBI_CUDA(cudaMemcpy(T->S_hi, sh.data(), plane * sizeof(float), cudaMemcpyHostToDevice));
@@ -614,6 +780,8 @@ TcDst* tc_create(kfbi_domain* D) {
     make_map(&T->mT1_lo, T->T1l, Mp, 2 * Mp, BM);
     make_map(&T->mT2_hi, T->T2h, Mp, 2 * Mp, BM);
     make_map(&T->mT2_lo, T->T2l, Mp, 2 * Mp, BM);
+    make_map(&T->mT1s_hi, T->T1sh, Mp, 2 * Mp, BM);
+    make_map(&T->mT1s_lo, T->T1sl, Mp, 2 * Mp, BM);
     KFBI_CUDA(cudaFuncSetAttribute(k_tc_dst_pass, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    SMEM_BYTES));
   } catch (...) {
@@ -625,16 +793,20 @@ TcDst* tc_create(kfbi_domain* D) {
 
 void tc_destroy(TcDst* T) {
   if (!T) return;
-  float* ptrs[] = {T->S_hi, T->S_lo, T->lam, T->Rh, T->Rl, T->T1h, T->T1l, T->T2h, T->T2l, T->U};
+  float* ptrs[] = {T->S_hi, T->S_lo, T->lam, T->S32, T->T1sh, T->T1sl, T->rv, T->Rh,
+                   T->Rl,   T->T1h,  T->T1l, T->T2h, T->T2l,  T->U};
   for (float* p : ptrs)
     if (p) cudaFree(p);
+  if (T->row_start) cudaFree(T->row_start);
+  if (T->node_col) cudaFree(T->node_col);
   delete T;
 }
 
 long long tc_bytes(const TcDst* T) { return T ? T->bytes : 0; }
 
 static void launch_pass(TcDst* T, const CUtensorMap& ah, const CUtensorMap& al, float* oh,
-                        float* ol, int mode, int P, float kre, float scale, cudaStream_t st) {
+                        float* ol, int mode, int P, float kre, float scale, cudaStream_t st,
+                        int kb0 = 0, int nk = -1, int ct0 = 0, int nct = -1) {
   PassParams prm;
   prm.out_hi = oh;
   prm.out_lo = ol;
@@ -642,11 +814,13 @@ static void launch_pass(TcDst* T, const CUtensorMap& ah, const CUtensorMap& al, 
   prm.Mp = T->Mp;
   prm.n1 = T->n1;
   prm.mode = mode;
-  prm.nk = T->Mp / BK;
+  prm.nk = nk < 0 ? T->Mp / BK : nk;
+  prm.kb0 = kb0;
+  prm.ct0 = ct0;
   prm.kre = kre;
   prm.scale = scale;
   prm.err = T->err;
-  dim3 grid(T->Mp / BN, P * T->Mp / BM);
+  dim3 grid(nct < 0 ? T->Mp / BN : nct, P * T->Mp / BM);
   KFBI_LAUNCH_P(KFBI_PROF_DST, k_tc_dst_pass, grid, THREADS, SMEM_BYTES, st, ah, al, T->mS_hi,
                 T->mS_lo, prm);
 }
@@ -667,9 +841,58 @@ static void tc_box_solve(kfbi_domain* D, double kre, double kim, int P, cudaStre
   launch_pass(T, T->mT1_hi, T->mT1_lo, T->U, nullptr, 2, P, 0.f, 0.f, st);
 }
 
+// GMRES application (no volume source, only u+ wanted): the right-hand
+// side lives on the irregular nodes and only the extraction stencil of the
+// grid solution is read, so the first pass is a sparse product on the CUDA
+// cores, the second pass runs over the K-blocks of the irregular rows only,
+// the third computes only the rows the stencil needs, and the last pass is a
+// gather fused with the extraction.  Same discrete operator as the dense
+// route; only zero terms and unread outputs are skipped.
+static void tc_apply_sparse(kfbi_domain* D, double kre, double kim, const double* phi, int ps,
+                            double* out, int os, cudaStream_t st) {
+  TcDst* T = D->tc;
+  const bool C = kim != 0.0;
+  const int P = C ? 2 : 1;
+  const int Mp = T->Mp;
+  const size_t plane = (size_t)Mp * Mp;
+  if (C)
+    KFBI_LAUNCH_P(KFBI_PROF_CORRECT, k_correct32<true>, (D->n_irr + 127) / 128, 128, 0, st, T->Rh,
+                  T->Rl, plane, nullptr, D->d_irr_off, D->d_arm_start, D->d_arm_k0,
+                  D->d_arm_alpha32, D->d_arm_beta32, D->d_arm_fidx, D->d_arm_fcoef32, D->n_irr,
+                  D->n_arms, D->nb, phi, ps, (float)kre, (float)kim, T->rv);
+  else
+    KFBI_LAUNCH_P(KFBI_PROF_CORRECT, k_correct32<false>, (D->n_irr + 127) / 128, 128, 0, st, T->Rh,
+                  T->Rl, plane, nullptr, D->d_irr_off, D->d_arm_start, D->d_arm_k0,
+                  D->d_arm_alpha32, D->d_arm_beta32, D->d_arm_fidx, D->d_arm_fcoef32, D->n_irr,
+                  D->n_arms, D->nb, phi, ps, (float)kre, (float)kim, T->rv);
+  KFBI_LAUNCH_P(KFBI_PROF_DST, k_sparse_p1, dim3(Mp / 32, (T->nrows + 31) / 32), dim3(32, 8), 0, st,
+                T->rv, D->n_irr, T->row_start, T->node_col, T->rmin, T->nrows, T->S32, T->T1sh,
+                T->T1sl, Mp, P);
+  const float scale = (float)((2.0 / D->M) * (2.0 / D->M));
+  launch_pass(T, T->mT1s_hi, T->mT1s_lo, T->T2h, T->T2l, C ? 0 : 1, P, (float)kre, scale, st,
+              T->kb0, T->nk2);
+  if (C)
+    KFBI_LAUNCH_P(KFBI_PROF_GRID, k_eig_split_cplx, grid_for(plane, 256), 256, 0, st, T->T2h,
+                  T->T2l, plane, Mp, T->n1, D->d_lam, kre, kim, (2.0 / D->M) * (2.0 / D->M));
+  launch_pass(T, T->mT2_hi, T->mT2_lo, T->U, nullptr, 2, P, 0.f, 0.f, st, 0, -1, T->ct0, T->nt3);
+  if (C)
+    KFBI_LAUNCH_P(KFBI_PROF_EXTRACT, k_gather_extract<true>, D->nb, 192, 0, st, T->U, T->S32, Mp,
+                  plane, D->d_node_gidx, D->d_node_w32, D->d_node_a32, D->d_node_b32, D->nb, phi,
+                  ps, (float)kre, (float)kim, out, os);
+  else
+    KFBI_LAUNCH_P(KFBI_PROF_EXTRACT, k_gather_extract<false>, D->nb, 192, 0, st, T->U, T->S32, Mp,
+                  plane, D->d_node_gidx, D->d_node_w32, D->d_node_a32, D->d_node_b32, D->nb, phi,
+                  ps, (float)kre, (float)kim, out, os);
+  KFBI_CHECK_LAUNCH();
+}
+
 void tc_apply(kfbi_domain* D, double kre, double kim, const double* phi, int ps, const double* ft,
               double* out, int os, bool want_grid, cudaStream_t st) {
   TcDst* T = D->tc;
+  if (!ft && !want_grid && out && D->n_irr > 0) {
+    tc_apply_sparse(D, kre, kim, phi, ps, out, os, st);
+    return;
+  }
   const bool C = kim != 0.0;
   const int P = C ? 2 : 1;
   const int Mp = T->Mp;
@@ -688,12 +911,12 @@ void tc_apply(kfbi_domain* D, double kre, double kim, const double* phi, int ps,
       KFBI_LAUNCH_P(KFBI_PROF_CORRECT, k_correct32<true>, (D->n_irr + 127) / 128, 128, 0, st,
                     T->Rh, T->Rl, plane, ft, D->d_irr_off, D->d_arm_start, D->d_arm_k0,
                     D->d_arm_alpha32, D->d_arm_beta32, D->d_arm_fidx, D->d_arm_fcoef32,
-                    D->n_irr, D->n_arms, D->nb, phi, ps, (float)kre, (float)kim);
+                    D->n_irr, D->n_arms, D->nb, phi, ps, (float)kre, (float)kim, nullptr);
     else
       KFBI_LAUNCH_P(KFBI_PROF_CORRECT, k_correct32<false>, (D->n_irr + 127) / 128, 128, 0, st,
                     T->Rh, T->Rl, plane, ft, D->d_irr_off, D->d_arm_start, D->d_arm_k0,
                     D->d_arm_alpha32, D->d_arm_beta32, D->d_arm_fidx, D->d_arm_fcoef32,
-                    D->n_irr, D->n_arms, D->nb, phi, ps, (float)kre, (float)kim);
+                    D->n_irr, D->n_arms, D->nb, phi, ps, (float)kre, (float)kim, nullptr);
   }
   tc_box_solve(D, kre, kim, P, st);
   if (out) {

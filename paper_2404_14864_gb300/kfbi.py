@@ -172,8 +172,18 @@ PROF_DST, PROF_CORRECT, PROF_EXTRACT, PROF_KRYLOV, PROF_GRID = 0, 1, 2, 3, 4
 PROF_NAMES = {0: "dst", 1: "correct", 2: "extract", 3: "krylov", 4: "grid"}
 
 
-def kfbi_profile_enable(on=True):
-    lib().kfbi_profile_enable(1 if on else 0)
+def kfbi_profile_enable(classes=True):
+    """Enable event timing for kernel classes: True = all, False = none, or
+    an iterable of class ids (PROF_*)."""
+    if classes is True:
+        mask = (1 << len(PROF_NAMES)) - 1
+    elif classes is False or classes is None:
+        mask = 0
+    else:
+        mask = 0
+        for c in classes:
+            mask |= 1 << int(c)
+    lib().kfbi_profile_enable(mask)
 
 
 def kfbi_profile_reset():
