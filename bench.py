@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--cpu-steps", type=int, default=2)
+    ap.add_argument("--workload", default="wave1024", choices=["wave1024", "batched"])
+    ap.add_argument("--batch", type=int, default=256)
     return ap.parse_args()
 
 
@@ -305,6 +307,78 @@ def roofline(res, M):
 
 
 # ----------------------------------------------------------------------------
+# batched heat workload (256 random stars of uneven size, one grouped step)
+# ----------------------------------------------------------------------------
+
+
+def run_batched(args):
+    import numpy as np
+    import torch
+
+    from paper_2404_14864_gb300 import build, kfbi, workloads as W
+    build.build()
+    dev = torch.device("cuda", 0)
+    inst = W.batched_instances(args.batch, seed=0)
+    ex = W.HeatExact()
+
+    def cu(a):
+        return torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+
+    doms, states, runs = [], [], []
+    for M, curve in inst:
+        desc = W.domain_desc(M, curve)
+        h = 2.0 / M
+        X, Y = W.grid_xy(desc)
+        zx, zy = W.boundary_xy(desc)
+        d = kfbi.Domain(desc, kfbi.KFBI_MIXED_TF32, restart=50, tol=1e-10, maxit=2000)
+        st = kfbi.State(d, kfbi.KFBI_HEAT)
+        st.init_heat(h, cu(ex.u(X, Y, 0)), cu(ex.lap(X, Y, 0)), cu(ex.src(X, Y, 0) + ex.src(X, Y, h)))
+        doms.append(d)
+        states.append(st)
+        runs.append((M, h, X, Y, zx, zy))
+    K, Wm = args.steps, args.warmup
+    g = [[cu(ex.u(zx, zy, (k + 1) * h)) for (M, h, X, Y, zx, zy) in runs] for k in range(Wm + K)]
+    s = [[cu(ex.src(X, Y, (k + 1) * h) + ex.src(X, Y, (k + 2) * h)) for (M, h, X, Y, zx, zy) in runs]
+         for k in range(Wm + K)]
+    batch = kfbi.Batch(doms)
+    for k in range(Wm):
+        batch.step(states, g[k], s[k])
+    torch.cuda.synchronize()
+    lat = []
+    n0 = kfbi.launch_count()
+    iters = []
+    for k in range(Wm, Wm + K):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        infos = batch.step(states, g[k], s[k])
+        e1.record()
+        e1.synchronize()
+        lat.append(e0.elapsed_time(e1))
+        iters.append(max(i["iters"] for i in infos))
+    t = sum(lat) / 1e3
+    pts = sum(M * M for M, *_ in runs)
+    errs = []
+    for (M, h, X, Y, zx, zy), st, d in zip(runs, states, doms):
+        u = st.get_u().cpu().numpy()
+        ins = kfbi.Plan(d.d).field("inside").reshape(M + 1, M + 1)[1:-1, 1:-1].astype(bool)
+        errs.append(float(np.abs(u - ex.u(X, Y, (Wm + K) * h))[ins].max()))
+    lat_s = sorted(lat)
+    line = {"metric": "grid-point*steps/s, batched heat (aggregate over instances)",
+            "value": pts * K / t, "unit": UNIT, "n_gpus": 1, "steps": K, "warmup": Wm,
+            "ms_per_step": 1e3 * t / K, "higher_is_better": True, "dtype": "tf32x3-f32acc+f64",
+            "data": "synthetic (manufactured solution)",
+            "config": {"workload": "batched-heat-%d" % args.batch,
+                       "sizes": sorted(set(M for M, *_ in runs)), "instances": len(runs),
+                       "seed": 0, "dt": "h"},
+            "latency_ms": {"p50": lat_s[len(lat_s) // 2], "p99": lat_s[-1]},
+            "linf_vs_exact_max": max(errs), "gmres_iters_max_per_step": iters,
+            "gpu_launches": kfbi.launch_count() - n0, "tuning": batch.tuning()}
+    print(json.dumps(line))
+    return 0
+
+
+# ----------------------------------------------------------------------------
 # oracle (CPU baseline / reference arm)
 # ----------------------------------------------------------------------------
 
@@ -360,6 +434,9 @@ def main():
                         "d2h_bytes_per_step": 0}}
         print(json.dumps(line))
         return 0
+
+    if args.workload == "batched":
+        return run_batched(args)
 
     if world > 1:
         import torch

@@ -199,6 +199,36 @@ kfbi_status kfbi_step_schrodinger(kfbi_domain* dom, kfbi_state* st, const double
 kfbi_status kfbi_state_get_u(kfbi_state* st, void* u_out_dev, void* stream);
 kfbi_status kfbi_state_get_phi(kfbi_state* st, void* phi_out_dev, void* stream);
 
+/* ---- batched time steps ------------------------------------------------- */
+
+/* A batch groups n KFBI_MIXED_TF32 domains of one device (any sizes and
+ * curves, same gmres_restart) so that one time step of all of them runs as
+ * grouped launches: the tcgen05 DST passes of every instance are one
+ * persistent launch over all instances' tiles, every other kernel takes the
+ * instance from its grid, and one lockstep GMRES iteration of the whole
+ * batch is a CUDA graph replayed until every instance has converged.  The
+ * first step binds the states, runs the autotuner (tile order of the
+ * grouped passes, timed with CUDA events) and captures the graph.
+ * Each instance gives the same result as kfbi_step_* on its own domain.
+ * The domains must outlive the batch. */
+typedef struct kfbi_batch kfbi_batch;
+kfbi_status kfbi_batch_create(kfbi_domain* const* domains, int n, void* stream, kfbi_batch** out);
+void kfbi_batch_destroy(kfbi_batch* batch);
+/* One time step of every instance: states[i] (initialised, on domains[i])
+ * advances with Dirichlet data g_next_dev[i] (n_boundary doubles, or
+ * complex128 for Schroedinger).  src_or_v_dev[i]: the heat source sum
+ * s^{n+1} + s^{n+2} (or NULL), the Schroedinger potential v (required), or
+ * unused for the wave equation; src_or_v_dev itself may be NULL.
+ * infos: n entries or NULL.  Synchronous. */
+kfbi_status kfbi_batch_step(kfbi_batch* batch, kfbi_state* const* states,
+                            const void* const* g_next_dev, const double* const* src_or_v_dev,
+                            kfbi_solve_info* infos, void* stream);
+/* Autotuner result: chosen tile order (0 as given, 1 largest instances
+ * first) and the measured microseconds of the grouped fast passes for each. */
+kfbi_status kfbi_batch_tuning(const kfbi_batch* batch, int* tile_order, double* us_natural,
+                              double* us_largest_first);
+const char* kfbi_batch_last_error(const kfbi_batch* batch);
+
 /* ---- inspection and diagnostics ----------------------------------------- */
 
 const char* kfbi_last_error(const kfbi_domain* dom);

@@ -1,0 +1,1494 @@
+// Batched time steps over many KFBI instances of uneven size (mixed
+// precision domains): every kernel of a step -- the volume-source and
+// final applications, the refinement residuals, the GMRES iterations with
+// their fast operator applications and CGS2 Arnoldi steps, and the F
+// updates -- is one launch for the whole batch.  Small kernels take the
+// instance from blockIdx.y; the tcgen05 DST passes are one persistent
+// launch over the tiles of all instances (k_tc_pass with descriptor
+// arrays).  Instances advance in lockstep; one that has converged is
+// switched off by a device flag that every kernel checks, so the others keep
+// iterating.  The per-iteration kernel sequence is captured once into a
+// CUDA graph (the iteration index lives in device memory) and replayed.
+//
+// The arithmetic of every kernel is the same as the single-instance path,
+// in the same order, so each instance of a batch produces the same bits as
+// the same domain stepped alone.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+#include <vector>
+
+#include "tc_internal.h"
+
+namespace kfbi {
+namespace bt {
+
+using tc::GroupArgs;
+using tc::PassDesc;
+
+// Everything a grouped kernel needs about one instance.
+struct GInst {
+  int Mp, n1, nb, n_irr, n_arms, M, m, C, eq;
+  int rmin, nrows;
+  double h, kre, kim, scale, dt, theta;
+  // FP64 domain tables
+  const uint8_t* mask;
+  const int* irr_off;
+  const int* arm_start;
+  const int* arm_k0;
+  const double* alpha;
+  const double* beta;
+  const int* arm_fidx;
+  const double* arm_fcoef;
+  const int* node_gidx;
+  const double* node_w;
+  const double* node_a;
+  const double* node_b;
+  const int* node_fidx;
+  const double* node_fcoef;
+  const double* lam64;
+  // FP32 tables of the mixed path
+  const float* alpha32;
+  const float* beta32;
+  const float* arm_fcoef32;
+  const float* node_w32;
+  const float* node_a32;
+  const float* node_b32;
+  const float* S32;
+  const int* row_start;
+  const int* node_col;
+  // work planes
+  double* R64;
+  double* U64;
+  float* Rh;
+  float* Rl;
+  float* T2h;
+  float* T2l;
+  float* U32;
+  float* T1sh;
+  float* T1sl;
+  float* rv;
+  // GMRES workspace (complex interleaved)
+  double2* V;
+  double2* W;
+  double2* H;
+  double* cs;
+  double2* sn;
+  double2* g;
+  double2* hcol;
+  double2* part;
+  double2* Rv;
+  double2* Dv;
+  double2* Ax;
+  double* scal;  // [0] ||b||, [1] residual, [2] status, [3] tol
+  // state
+  double* u;
+  double* F;
+  double* Fprev;
+  double* ft;
+  double* aux;
+  double2* x;    // density phi
+  double2* b;
+  double2* ub;
+  const double* g_next;   // per step (caller layout)
+  const double* src;      // heat source sum or Schroedinger potential (caller layout)
+  int* flags;             // [0] active, [1] k (iterations of the current cycle), [2] x_zero
+};
+
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+// Grid-stride over the padded plane of the instance in blockIdx.y.
+#define INST_PLANE_LOOP(I)                                                                 \
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x;                         \
+       idx < (size_t)(I).Mp * (I).Mp; idx += (size_t)gridDim.x * blockDim.x)
+
+#define ACTIVE_OR_RETURN(I) \
+  if ((I).flags[0] == 0) return;
+
+// ---- volume source and base right-hand side --------------------------------
+
+// heat/wave: f-tilde = -F on Omega; Schroedinger: u** = B(u*), f-tilde = -kappa u**
+__global__ void gk_make_ft(const GInst* gi) {
+  const GInst& I = gi[blockIdx.y];
+  const size_t plane = (size_t)I.Mp * I.Mp;
+  if (I.eq != KFBI_SCHRODINGER) {
+    INST_PLANE_LOOP(I) { I.ft[idx] = I.mask[idx] ? -I.F[idx] : 0.0; }
+    return;
+  }
+  const double half_dt = 0.5 * I.dt, kim = I.kim;
+  INST_PLANE_LOOP(I) {
+    const int r = (int)(idx / I.Mp), c = (int)(idx % I.Mp);
+    double xr = 0, xi = 0;
+    if (r < I.n1 && c < I.n1) {
+      const double a = half_dt * I.src[(size_t)r * I.n1 + c];
+      const double den = 1.0 / (1.0 + a * a);
+      const double pr = (1.0 - a * a) * den, pi = -2.0 * a * den;
+      const double sr = I.F[idx], si = I.F[plane + idx];
+      xr = pr * sr - pi * si;
+      xi = pr * si + pi * sr;
+    }
+    I.aux[idx] = xr;
+    I.aux[plane + idx] = xi;
+    const bool in = I.mask[idx] != 0;
+    I.ft[idx] = in ? kim * xi : 0.0;
+    I.ft[plane + idx] = in ? -kim * xr : 0.0;
+  }
+}
+
+// R64 = f-tilde (with_ft) or 0 over the instance's planes.
+__global__ void gk_base_rhs(const GInst* gi, int with_ft) {
+  const GInst& I = gi[blockIdx.y];
+  ACTIVE_OR_RETURN(I);
+  const size_t plane = (size_t)I.Mp * I.Mp;
+  const int P = I.C ? 2 : 1;
+  INST_PLANE_LOOP(I) {
+    for (int p = 0; p < P; ++p) I.R64[p * plane + idx] = with_ft ? I.ft[p * plane + idx] : 0.0;
+  }
+}
+
+// FP64 corrected RHS at the irregular nodes (as k_correct); phi complex
+// interleaved (stride 2).  which: 0 = zero density, 1 = x, 2 = V[j]
+__device__ __forceinline__ const double* density_of(const GInst& I, int which, int j) {
+  if (which == 0) return nullptr;
+  if (which == 1) return (const double*)I.x;
+  return (const double*)(I.V + (size_t)j * I.nb);
+}
+
+__global__ void gk_correct64(const GInst* gi, int which, int with_ft, const int* dj) {
+  const GInst& I = gi[blockIdx.y];
+  ACTIVE_OR_RETURN(I);
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= I.n_irr) return;
+  const double* phi = density_of(I, which, dj ? *dj : 0);
+  const double* ft = with_ft ? I.ft : nullptr;
+  const bool C = I.C != 0;
+  const size_t plane = (size_t)I.Mp * I.Mp;
+  const int off = I.irr_off[n];
+  double sr = ft ? ft[off] : 0.0;
+  double si = (C && ft) ? ft[plane + off] : 0.0;
+  const int a1 = I.arm_start[n + 1];
+  const int na = I.n_arms, nb = I.nb;
+  for (int a = I.arm_start[n]; a < a1; ++a) {
+    int k = I.arm_k0[a];
+    double ar = 0.0, ai = 0.0, br = 0.0, bi = 0.0;
+    if (phi) {
+#pragma unroll
+      for (int m = 0; m < 6; ++m) {
+        const double al = I.alpha[m * na + a], be = I.beta[m * na + a];
+        const double pr = phi[(size_t)k * 2];
+        ar = fma(al, pr, ar);
+        br = fma(be, pr, br);
+        if (C) {
+          const double pi = phi[(size_t)k * 2 + 1];
+          ai = fma(al, pi, ai);
+          bi = fma(be, pi, bi);
+        }
+        k = (k + 1 == nb) ? 0 : k + 1;
+      }
+    }
+    sr += ar + I.kre * br;
+    if (C) {
+      sr -= I.kim * bi;
+      si += ai + I.kre * bi + I.kim * br;
+    }
+    if (ft) {
+      const int f0 = I.arm_fidx[a], f1 = I.arm_fidx[na + a];
+      const double c0 = I.arm_fcoef[a], c1 = I.arm_fcoef[na + a];
+      sr += c0 * ft[f0] + c1 * ft[f1];
+      if (C) si += c0 * ft[plane + f0] + c1 * ft[plane + f1];
+    }
+  }
+  I.R64[off] = sr;
+  if (C) I.R64[plane + off] = si;
+}
+
+__device__ __forceinline__ float tf32r(float x) { return tf32_round(x); }
+
+__global__ void gk_split64(const GInst* gi) {
+  const GInst& I = gi[blockIdx.y];
+  ACTIVE_OR_RETURN(I);
+  const size_t plane = (size_t)I.Mp * I.Mp;
+  const int P = I.C ? 2 : 1;
+  INST_PLANE_LOOP(I) {
+    for (int p = 0; p < P; ++p) {
+      const size_t i = p * plane + idx;
+      const double x = I.R64[i];
+      const float h = tf32r((float)x);
+      I.Rh[i] = h;
+      I.Rl[i] = tf32r((float)(x - (double)h));
+    }
+  }
+}
+
+__global__ void gk_eig_cplx(const GInst* gi) {
+  const GInst& I = gi[blockIdx.y];
+  ACTIVE_OR_RETURN(I);
+  if (!I.C) return;
+  const size_t plane = (size_t)I.Mp * I.Mp;
+  INST_PLANE_LOOP(I) {
+    const int a = (int)(idx / I.Mp), bcol = (int)(idx % I.Mp);
+    if (a >= I.n1 || bcol >= I.n1) continue;
+    const double x = (double)I.T2h[idx] + (double)I.T2l[idx];
+    const double y = (double)I.T2h[plane + idx] + (double)I.T2l[plane + idx];
+    const double dr = I.lam64[a] + I.lam64[bcol] - I.kre;
+    const double den = I.scale / (dr * dr + I.kim * I.kim);
+    const double zr = (x * dr - y * I.kim) * den, zi = (x * I.kim + y * dr) * den;
+    float h = tf32r((float)zr);
+    I.T2h[idx] = h;
+    I.T2l[idx] = tf32r((float)(zr - (double)h));
+    h = tf32r((float)zi);
+    I.T2h[plane + idx] = h;
+    I.T2l[plane + idx] = tf32r((float)(zi - (double)h));
+  }
+}
+
+__global__ void gk_f32_to_f64(const GInst* gi) {
+  const GInst& I = gi[blockIdx.y];
+  ACTIVE_OR_RETURN(I);
+  const size_t plane = (size_t)I.Mp * I.Mp;
+  const int P = I.C ? 2 : 1;
+  INST_PLANE_LOOP(I) {
+    for (int p = 0; p < P; ++p) I.U64[p * plane + idx] = (double)I.U32[p * plane + idx];
+  }
+}
+
+__global__ void gk_resid_split(const GInst* gi) {
+  const GInst& I = gi[blockIdx.y];
+  ACTIVE_OR_RETURN(I);
+  const size_t plane = (size_t)I.Mp * I.Mp;
+  const int Mp = I.Mp, n1 = I.n1;
+  const double inv_h2 = 1.0 / (I.h * I.h);
+  const bool C = I.C != 0;
+  INST_PLANE_LOOP(I) {
+    const int r = (int)(idx / Mp), c = (int)(idx % Mp);
+    for (int p = 0; p < (C ? 2 : 1); ++p) {
+      double res = 0.0;
+      if (r < n1 && c < n1) {
+        const double* Up = I.U64 + p * plane;
+        const double u = Up[idx];
+        const double e = c + 1 < n1 ? Up[idx + 1] : 0.0;
+        const double w = c > 0 ? Up[idx - 1] : 0.0;
+        const double nn = r + 1 < n1 ? Up[idx + Mp] : 0.0;
+        const double s = r > 0 ? Up[idx - Mp] : 0.0;
+        double Lu = (e + w + nn + s - 4.0 * u) * inv_h2 - I.kre * u;
+        if (C) {
+          const double uo = I.U64[(1 - p) * plane + idx];
+          Lu += (p == 0) ? I.kim * uo : -I.kim * uo;
+        }
+        res = I.R64[p * plane + idx] - Lu;
+      }
+      const float h = tf32r((float)res);
+      I.Rh[p * plane + idx] = h;
+      I.Rl[p * plane + idx] = tf32r((float)(res - (double)h));
+    }
+  }
+}
+
+__global__ void gk_add_f32(const GInst* gi) {
+  const GInst& I = gi[blockIdx.y];
+  ACTIVE_OR_RETURN(I);
+  const size_t plane = (size_t)I.Mp * I.Mp;
+  const int P = I.C ? 2 : 1;
+  INST_PLANE_LOOP(I) {
+    for (int p = 0; p < P; ++p) I.U64[p * plane + idx] += (double)I.U32[p * plane + idx];
+  }
+}
+
+// FP64 extraction (as k_extract) into out (ub or Ax), complex interleaved.
+__global__ void gk_extract64(const GInst* gi, int which, int with_ft, int target) {
+  const GInst& I = gi[blockIdx.y];
+  ACTIVE_OR_RETURN(I);
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nb = I.nb;
+  if (k >= nb) return;
+  const double* phi = density_of(I, which, 0);
+  const double* ft = with_ft ? I.ft : nullptr;
+  double* out = target == 0 ? (double*)I.ub : (double*)I.Ax;
+  const bool C = I.C != 0;
+  const size_t plane = (size_t)I.Mp * I.Mp;
+  double sr = 0.0, si = 0.0;
+#pragma unroll
+  for (int m = 0; m < 6; ++m) {
+    const int gg = I.node_gidx[m * nb + k];
+    const double wm = I.node_w[m * nb + k];
+    sr = fma(wm, I.U64[gg], sr);
+    if (C) si = fma(wm, I.U64[plane + gg], si);
+  }
+  double ar = 0.0, ai = 0.0, br = 0.0, bi = 0.0;
+  if (phi) {
+    int kk = k - 2;
+    if (kk < 0) kk += nb;
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+      const double a = I.node_a[j * nb + k], b = I.node_b[j * nb + k];
+      const double pr = phi[(size_t)kk * 2];
+      ar = fma(a, pr, ar);
+      br = fma(b, pr, br);
+      if (C) {
+        const double pi = phi[(size_t)kk * 2 + 1];
+        ai = fma(a, pi, ai);
+        bi = fma(b, pi, bi);
+      }
+      kk = (kk + 1 == nb) ? 0 : kk + 1;
+    }
+  }
+  sr += ar + I.kre * br;
+  if (C) {
+    sr -= I.kim * bi;
+    si += ai + I.kre * bi + I.kim * br;
+  }
+  if (ft) {
+    const int gg = I.node_fidx[k];
+    const double c = I.node_fcoef[k];
+    sr += c * ft[gg];
+    if (C) si += c * ft[plane + gg];
+  }
+  out[(size_t)k * 2] = sr;
+  out[(size_t)k * 2 + 1] = C ? si : 0.0;
+}
+
+// ---- fast (sparse) application with the density V[j] ----------------------
+
+__global__ void gk_correct32_rv(const GInst* gi, const int* dj) {
+  const GInst& I = gi[blockIdx.y];
+  ACTIVE_OR_RETURN(I);
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= I.n_irr) return;
+  const double* phi = (const double*)(I.V + (size_t)(*dj) * I.nb);
+  const bool C = I.C != 0;
+  const int na = I.n_arms, nb = I.nb;
+  const float kre = (float)I.kre, kim = (float)I.kim;
+  float sr = 0.f, si = 0.f;
+  const int a1 = I.arm_start[n + 1];
+  for (int a = I.arm_start[n]; a < a1; ++a) {
+    int k = I.arm_k0[a];
+    float ar = 0.f, ai = 0.f, br = 0.f, bi = 0.f;
+#pragma unroll
+    for (int m = 0; m < 6; ++m) {
+      const float al = I.alpha32[m * na + a], be = I.beta32[m * na + a];
+      const float pr = (float)phi[(size_t)k * 2];
+      ar = fmaf(al, pr, ar);
+      br = fmaf(be, pr, br);
+      if (C) {
+        const float pi = (float)phi[(size_t)k * 2 + 1];
+        ai = fmaf(al, pi, ai);
+        bi = fmaf(be, pi, bi);
+      }
+      k = (k + 1 == nb) ? 0 : k + 1;
+    }
+    sr += ar + kre * br;
+    if (C) {
+      sr -= kim * bi;
+      si += ai + kre * bi + kim * br;
+    }
+  }
+  I.rv[n] = sr;
+  if (C) I.rv[I.n_irr + n] = si;
+}
+
+// blockIdx.z = instance; (x, y) = 32 x 32 output tile as in k_sparse_p1
+__global__ void __launch_bounds__(256) gk_sparse_p1(const GInst* gi) {
+  const GInst& I = gi[blockIdx.z];
+  ACTIVE_OR_RETURN(I);
+  const int Mp = I.Mp;
+  const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+  if (c0 >= Mp || r0 >= I.nrows) return;
+  __shared__ float tile[2][32][33];
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int P = I.C ? 2 : 1;
+  for (int rr = ty; rr < 32; rr += 8) {
+    const int rl = r0 + rr;
+    float a0 = 0.f, a1 = 0.f;
+    if (rl < I.nrows) {
+      const int ne = I.row_start[rl + 1];
+      for (int n = I.row_start[rl]; n < ne; ++n) {
+        const float sv = I.S32[(size_t)I.node_col[n] * Mp + c0 + tx];
+        a0 = fmaf(I.rv[n], sv, a0);
+        if (P == 2) a1 = fmaf(I.rv[I.n_irr + n], sv, a1);
+      }
+    }
+    tile[0][rr][tx] = a0;
+    tile[1][rr][tx] = a1;
+  }
+  __syncthreads();
+  const size_t plane = (size_t)Mp * Mp;
+  for (int cc = ty; cc < 32; cc += 8) {
+    const int rl = r0 + tx;
+    if (rl >= I.nrows) continue;
+    const size_t o = (size_t)(c0 + cc) * Mp + (size_t)(I.rmin + rl);
+    for (int p = 0; p < P; ++p) {
+      const float x = tile[p][tx][cc];
+      const float h = tf32r(x);
+      I.T1sh[p * plane + o] = h;
+      I.T1sl[p * plane + o] = tf32r(x - h);
+    }
+  }
+}
+
+// Gather of the stencil values and extraction (as k_gather_extract) into W.
+__global__ void __launch_bounds__(192) gk_gather_extract(const GInst* gi, const int* dj) {
+  const GInst& I = gi[blockIdx.y];
+  ACTIVE_OR_RETURN(I);
+  const int k = blockIdx.x;
+  const int nb = I.nb;
+  if (k >= nb) return;
+  __shared__ float Ush[6][2];
+  const int Mp = I.Mp;
+  const size_t plane = (size_t)Mp * Mp;
+  const bool C = I.C != 0;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  {
+    const int off = I.node_gidx[warp * nb + k];
+    const int jr = off / Mp, ic = off - jr * Mp;
+    const float* t0 = I.U32 + (size_t)ic * Mp;
+    const float* sr = I.S32 + (size_t)jr * Mp;
+    float s0 = 0.f, s1 = 0.f;
+    for (int a = lane; a < Mp; a += 32) {
+      const float sv = sr[a];
+      s0 = fmaf(t0[a], sv, s0);
+      if (C) s1 = fmaf(t0[plane + a], sv, s1);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+      if (C) s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+    }
+    if (lane == 0) {
+      Ush[warp][0] = s0;
+      Ush[warp][1] = s1;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  const double* phi = (const double*)(I.V + (size_t)(*dj) * nb);
+  const float kre = (float)I.kre, kim = (float)I.kim;
+  float sr = 0.f, si = 0.f;
+#pragma unroll
+  for (int m = 0; m < 6; ++m) {
+    const float wm = I.node_w32[m * nb + k];
+    sr = fmaf(wm, Ush[m][0], sr);
+    if (C) si = fmaf(wm, Ush[m][1], si);
+  }
+  float ar = 0.f, ai = 0.f, br = 0.f, bi = 0.f;
+  int kk = k - 2;
+  if (kk < 0) kk += nb;
+#pragma unroll
+  for (int j = 0; j < 6; ++j) {
+    const float a = I.node_a32[j * nb + k], b = I.node_b32[j * nb + k];
+    const float pr = (float)phi[(size_t)kk * 2];
+    ar = fmaf(a, pr, ar);
+    br = fmaf(b, pr, br);
+    if (C) {
+      const float pi = (float)phi[(size_t)kk * 2 + 1];
+      ai = fmaf(a, pi, ai);
+      bi = fmaf(b, pi, bi);
+    }
+    kk = (kk + 1 == nb) ? 0 : kk + 1;
+  }
+  sr += ar + kre * br;
+  if (C) {
+    sr -= kim * bi;
+    si += ai + kre * bi + kim * br;
+  }
+  I.W[k] = make_double2((double)sr, C ? (double)si : 0.0);
+}
+
+// ---- GMRES (as gmres.cu, instance in blockIdx.y) ---------------------------
+
+constexpr int GT = 256;
+constexpr int GMAX = 64;
+
+__device__ double block_sum(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  if (w == 0) {
+    v = (l < (int)(blockDim.x >> 5)) ? red[l] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (l == 0) red[0] = v;
+  }
+  __syncthreads();
+  const double r = red[0];
+  __syncthreads();
+  return r;
+}
+
+// b = g - ub (real g for heat/wave, complex for Schroedinger)
+__global__ void gk_make_b(const GInst* gi) {
+  const GInst& I = gi[blockIdx.y];
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= I.nb) return;
+  const bool gC = I.eq == KFBI_SCHRODINGER;
+  const double gr = gC ? I.g_next[2 * k] : I.g_next[k], gim = gC ? I.g_next[2 * k + 1] : 0.0;
+  I.b[k] = make_double2(gr - I.ub[k].x, gim - I.ub[k].y);
+}
+
+// ||b|| into scal[0] (tol into scal[3]); one 1024-thread block per instance
+__global__ void __launch_bounds__(1024) gk_bnorm(const GInst* gi, double tol, int which) {
+  const GInst& I = gi[blockIdx.y];
+  __shared__ double red[32];
+  const double2* v = which == 0 ? I.b : I.Rv;
+  double s = 0.0;
+  for (int e = threadIdx.x; e < I.nb; e += 1024) s += v[e].x * v[e].x + v[e].y * v[e].y;
+  s = block_sum(s, red);
+  if (threadIdx.x == 0) {
+    I.scal[0] = sqrt(s);
+    I.scal[3] = tol;
+  }
+}
+
+// All instances' scalars and flags into one buffer for a single readback.
+__global__ void gk_gather_scal(const GInst* gi, double* out) {
+  const GInst& I = gi[blockIdx.x];
+  if (threadIdx.x < 8) out[8 * blockIdx.x + threadIdx.x] = I.scal[threadIdx.x];
+}
+
+__global__ void gk_set_tol(const GInst* gi, const double* tol, const int* sel) {
+  const GInst& I = gi[blockIdx.x];
+  if (threadIdx.x == 0 && sel[blockIdx.x]) I.scal[3] = tol[blockIdx.x];
+}
+
+__global__ void gk_clear_k(const GInst* gi) {
+  const GInst& I = gi[blockIdx.x];
+  if (threadIdx.x == 0) I.flags[1] = 0;
+}
+
+// Rv = b - Ax (Ax omitted for x_zero) and ||Rv|| into scal[1]
+__global__ void __launch_bounds__(1024) gk_residual(const GInst* gi) {
+  const GInst& I = gi[blockIdx.y];
+  ACTIVE_OR_RETURN(I);
+  __shared__ double red[32];
+  const bool skip = I.flags[2] != 0;
+  double s = 0.0;
+  for (int e = threadIdx.x; e < I.nb; e += 1024) {
+    double2 v = I.b[e];
+    if (!skip) {
+      v.x -= I.Ax[e].x;
+      v.y -= I.Ax[e].y;
+    }
+    I.Rv[e] = v;
+    s += v.x * v.x + v.y * v.y;
+  }
+  s = block_sum(s, red);
+  if (threadIdx.x == 0) I.scal[1] = sqrt(s);
+}
+
+// V0 = r/beta with r = Rv - A Dv (restart) or Rv (fresh cycle), g = (beta, 0..)
+__global__ void __launch_bounds__(1024) gk_restart(const GInst* gi, int with_ax) {
+  const GInst& I = gi[blockIdx.y];
+  ACTIVE_OR_RETURN(I);
+  __shared__ double red[32];
+  double s = 0.0;
+  for (int e = threadIdx.x; e < I.nb; e += 1024) {
+    double2 r = I.Rv[e];
+    if (with_ax) {
+      r.x -= I.W[e].x;
+      r.y -= I.W[e].y;
+    }
+    I.V[e] = r;
+    s += r.x * r.x + r.y * r.y;
+  }
+  s = block_sum(s, red);
+  const double beta = sqrt(s);
+  const double inv = beta > 0.0 ? 1.0 / beta : 0.0;
+  for (int e = threadIdx.x; e < I.nb; e += 1024) {
+    I.V[e].x *= inv;
+    I.V[e].y *= inv;
+  }
+  if (threadIdx.x <= I.m) I.g[threadIdx.x] = make_double2(threadIdx.x == 0 ? beta : 0.0, 0.0);
+  if (threadIdx.x == 0) {
+    I.scal[1] = beta;
+    const double st = !isfinite(beta) ? 2.0 : (beta <= I.scal[3] * I.scal[0] ? 1.0 : 0.0);
+    I.scal[2] = st;
+    I.flags[1] = 0;
+    if (st != 0.0) I.flags[0] = 0;  // converged (or non-finite) before iterating
+  }
+}
+
+// Same partition of the vectors as the single-instance grid_shape().
+__device__ __forceinline__ void shape(int nb, int& G, int& slice) {
+  int G0 = (nb + 31) / 32;
+  if (G0 > 64) G0 = 64;
+  slice = ((nb + G0 - 1) / G0 + 31) / 32 * 32;
+  G = (nb + slice - 1) / slice;
+}
+
+__device__ __forceinline__ void slice_of(int nb, int b, int, int& e0, int& e1) {
+  int G, slice;
+  shape(nb, G, slice);
+  e0 = b * slice;
+  e1 = min(nb, e0 + slice);
+}
+
+__device__ __forceinline__ double2 dotpart(const double2* __restrict__ a,
+                                           const double2* __restrict__ b, int e0, int e1, int lane,
+                                           bool C) {
+  double2 s = make_double2(0.0, 0.0);
+  for (int e = e0 + lane; e < e1; e += 32) {
+    const double2 x = a[e], y = b[e];
+    if (C) {
+      s.x += x.x * y.x + x.y * y.y;
+      s.y += x.x * y.y - x.y * y.x;
+    } else {
+      s.x += x.x * y.x;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    s.x += __shfl_xor_sync(0xffffffffu, s.x, o);
+    if (C) s.y += __shfl_xor_sync(0xffffffffu, s.y, o);
+  }
+  return s;
+}
+
+__device__ __forceinline__ int grid_g(int nb) {
+  int G, slice;
+  shape(nb, G, slice);
+  return G;
+}
+
+__global__ void __launch_bounds__(GT) gk_cgs_dots(const GInst* gi, const int* dj) {
+  const GInst& I = gi[blockIdx.y];
+  ACTIVE_OR_RETURN(I);
+  const int G = grid_g(I.nb);
+  if ((int)blockIdx.x >= G) return;
+  const int j = *dj;
+  int e0, e1;
+  slice_of(I.nb, blockIdx.x, G, e0, e1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int i = warp; i <= j; i += GT / 32) {
+    const double2 s = dotpart(I.V + (size_t)i * I.nb, I.W, e0, e1, lane, I.C != 0);
+    if (lane == 0) I.part[(size_t)i * GMAX + blockIdx.x] = s;
+  }
+}
+
+__global__ void __launch_bounds__(GT) gk_cgs_update(const GInst* gi, const int* dj, int first,
+                                                    int mode) {
+  const GInst& I = gi[blockIdx.y];
+  ACTIVE_OR_RETURN(I);
+  const int G = grid_g(I.nb);
+  if ((int)blockIdx.x >= G) return;
+  const int j = *dj;
+  const bool C = I.C != 0;
+  __shared__ double2 h[65];
+  int e0, e1;
+  slice_of(I.nb, blockIdx.x, G, e0, e1);
+  const double2* part_in = first ? I.part : I.part + (size_t)(I.m + 1) * GMAX;
+  double2* part_out = first ? I.part + (size_t)(I.m + 1) * GMAX : I.part;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int i = warp; i <= j; i += GT / 32) {
+    double2 s = make_double2(0.0, 0.0);
+    for (int b = lane; b < G; b += 32) {
+      const double2 v = part_in[(size_t)i * GMAX + b];
+      s.x += v.x;
+      if (C) s.y += v.y;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      s.x += __shfl_xor_sync(0xffffffffu, s.x, o);
+      if (C) s.y += __shfl_xor_sync(0xffffffffu, s.y, o);
+    }
+    if (lane == 0) h[i] = s;
+  }
+  __syncthreads();
+  if (blockIdx.x == 0)
+    for (int i = threadIdx.x; i <= j; i += GT) {
+      if (first) {
+        I.hcol[i] = h[i];
+      } else {
+        I.hcol[i].x += h[i].x;
+        I.hcol[i].y += h[i].y;
+      }
+    }
+  for (int e = e0 + threadIdx.x; e < e1; e += GT) {
+    double2 acc = I.W[e];
+    for (int i = 0; i <= j; ++i) {
+      const double2 v = I.V[(size_t)i * I.nb + e], hi = h[i];
+      if (C) {
+        acc.x -= hi.x * v.x - hi.y * v.y;
+        acc.y -= hi.x * v.y + hi.y * v.x;
+      } else {
+        acc.x -= hi.x * v.x;
+      }
+    }
+    I.W[e] = acc;
+  }
+  __syncthreads();
+  if (mode == 0) {
+    for (int i = warp; i <= j; i += GT / 32) {
+      const double2 s = dotpart(I.V + (size_t)i * I.nb, I.W, e0, e1, lane, C);
+      if (lane == 0) part_out[(size_t)i * GMAX + blockIdx.x] = s;
+    }
+  } else if (warp == 0) {
+    const double2 s = dotpart(I.W, I.W, e0, e1, lane, C);
+    if (lane == 0) part_out[blockIdx.x] = make_double2(s.x, 0.0);
+  }
+}
+
+__global__ void __launch_bounds__(GT) gk_cgs_finalize(const GInst* gi, const int* dj) {
+  const GInst& I = gi[blockIdx.y];
+  ACTIVE_OR_RETURN(I);
+  const int G = grid_g(I.nb);
+  if ((int)blockIdx.x >= G) return;
+  const int j = *dj;
+  const int m = I.m;
+  __shared__ double nrm;
+  int e0, e1;
+  slice_of(I.nb, blockIdx.x, G, e0, e1);
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    double s = 0.0;
+    for (int q = lane; q < G; q += 32) s += I.part[q].x;
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) nrm = sqrt(s);
+  }
+  __syncthreads();
+  const double hn = nrm;
+  const double inv = hn > 0.0 ? 1.0 / hn : 0.0;
+  double2* vn = I.V + (size_t)(j + 1) * I.nb;
+  for (int e = e0 + threadIdx.x; e < e1; e += GT)
+    vn[e] = make_double2(I.W[e].x * inv, I.W[e].y * inv);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    double2* col = I.H + (size_t)j * (m + 1);
+    for (int i = 0; i <= j; ++i) col[i] = I.hcol[i];
+    col[j + 1] = make_double2(hn, 0.0);
+    for (int i = 0; i < j; ++i) {
+      const double c = I.cs[i];
+      const double2 sv = I.sn[i], a = col[i], bb = col[i + 1];
+      const double2 t = cmul(sv, bb);
+      const double2 u = cmul(make_double2(sv.x, -sv.y), a);
+      col[i] = make_double2(c * a.x + t.x, c * a.y + t.y);
+      col[i + 1] = make_double2(-u.x + c * bb.x, -u.y + c * bb.y);
+    }
+    const double2 a = col[j];
+    const double bre = col[j + 1].x;
+    double c;
+    double2 sv;
+    const double aa = hypot(a.x, a.y);
+    if (bre == 0.0) {
+      c = 1.0;
+      sv = make_double2(0.0, 0.0);
+    } else if (aa == 0.0) {
+      c = 0.0;
+      sv = make_double2(1.0, 0.0);
+    } else {
+      const double den = hypot(aa, bre);
+      c = aa / den;
+      sv = make_double2(a.x / aa * bre / den, a.y / aa * bre / den);
+    }
+    I.cs[j] = c;
+    I.sn[j] = sv;
+    col[j] = make_double2(c * a.x + sv.x * bre, c * a.y + sv.y * bre);
+    col[j + 1] = make_double2(0.0, 0.0);
+    const double2 gj = I.g[j];
+    const double2 u = cmul(make_double2(sv.x, -sv.y), gj);
+    I.g[j + 1] = make_double2(-u.x, -u.y);
+    I.g[j] = make_double2(c * gj.x, c * gj.y);
+    const double res = hypot(I.g[j + 1].x, I.g[j + 1].y);
+    I.scal[1] = res;
+    const double st = !isfinite(res) ? 2.0 : ((res <= I.scal[3] * I.scal[0] || hn == 0.0) ? 1.0 : 0.0);
+    I.scal[2] = st;
+    I.flags[1] = j + 1;
+    if (st != 0.0) I.flags[0] = 0;  // this instance stops iterating
+  }
+}
+
+// Dv += V y (k = flags[1] iterations); runs for every instance with k > 0.
+__global__ void __launch_bounds__(GT) gk_update(const GInst* gi) {
+  const GInst& I = gi[blockIdx.y];
+  const int k = I.flags[1];
+  if (k == 0) return;
+  const int G = grid_g(I.nb);
+  if ((int)blockIdx.x >= G) return;
+  const int m = I.m;
+  __shared__ double2 y[64];
+  int e0, e1;
+  slice_of(I.nb, blockIdx.x, G, e0, e1);
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    for (int i = k - 1; i >= 0; --i) {
+      double2 s = make_double2(0.0, 0.0);
+      for (int l = i + 1 + lane; l < k; l += 32) {
+        const double2 t = cmul(I.H[(size_t)l * (m + 1) + i], y[l]);
+        s.x += t.x;
+        s.y += t.y;
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        s.x += __shfl_xor_sync(0xffffffffu, s.x, o);
+        s.y += __shfl_xor_sync(0xffffffffu, s.y, o);
+      }
+      if (lane == 0) {
+        const double2 r = make_double2(I.g[i].x - s.x, I.g[i].y - s.y);
+        const double2 d = I.H[(size_t)i * (m + 1) + i];
+        const double dd = d.x * d.x + d.y * d.y;
+        y[i] = make_double2((r.x * d.x + r.y * d.y) / dd, (r.y * d.x - r.x * d.y) / dd);
+      }
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  for (int e = e0 + threadIdx.x; e < e1; e += GT) {
+    double2 acc = I.Dv[e];
+    for (int i = 0; i < k; ++i) {
+      const double2 t = cmul(y[i], I.V[(size_t)i * I.nb + e]);
+      acc.x += t.x;
+      acc.y += t.y;
+    }
+    I.Dv[e] = acc;
+  }
+}
+
+// x += Dv; Dv = 0
+__global__ void gk_axpy(const GInst* gi, const int* sel) {
+  const GInst& I = gi[blockIdx.y];
+  if (!sel[blockIdx.y]) return;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < I.nb; e += gridDim.x * blockDim.x) {
+    I.x[e].x += I.Dv[e].x;
+    I.x[e].y += I.Dv[e].y;
+    I.Dv[e] = make_double2(0.0, 0.0);
+  }
+}
+
+__global__ void gk_zero_dv(const GInst* gi) {
+  const GInst& I = gi[blockIdx.y];
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < I.nb; e += gridDim.x * blockDim.x)
+    I.Dv[e] = make_double2(0.0, 0.0);
+}
+
+// W = A Dv is needed at a restart: copy Dv into V[m] slot? -- the fast
+// operator reads V[j]; restarts place Dv into V[0] first (gk_dv_to_v0).
+__global__ void gk_dv_to_v0(const GInst* gi) {
+  const GInst& I = gi[blockIdx.y];
+  ACTIVE_OR_RETURN(I);
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < I.nb; e += gridDim.x * blockDim.x)
+    I.V[e] = I.Dv[e];
+}
+
+// ---- step updates ----------------------------------------------------------
+
+__global__ void gk_step_update(const GInst* gi) {
+  const GInst& I = gi[blockIdx.y];
+  const size_t plane = (size_t)I.Mp * I.Mp;
+  if (I.eq == KFBI_HEAT) {
+    const double four_dt = 4.0 / I.dt;
+    INST_PLANE_LOOP(I) {
+      const int r = (int)(idx / I.Mp), c = (int)(idx % I.Mp);
+      const double uu = I.U64[idx];
+      double f = four_dt * uu - I.F[idx];
+      if (I.src && r < I.n1 && c < I.n1) f += I.src[(size_t)r * I.n1 + c];
+      I.u[idx] = uu;
+      I.F[idx] = f;
+    }
+  } else if (I.eq == KFBI_WAVE) {
+    const double k_theta = I.kre / I.theta, c1 = (1.0 - 2.0 * I.theta) / I.theta;
+    INST_PLANE_LOOP(I) {
+      const double uu = I.U64[idx], f = I.F[idx];
+      const double fn = k_theta * uu - c1 * f - I.Fprev[idx];
+      I.Fprev[idx] = f;
+      I.F[idx] = fn;
+      I.u[idx] = uu;
+    }
+  } else {
+    INST_PLANE_LOOP(I) {
+      for (int p = 0; p < 2; ++p) {
+        const size_t q = p * plane + idx;
+        I.u[q] = I.U64[q];
+        I.F[q] = 2.0 * I.U64[q] - I.aux[q];
+      }
+    }
+  }
+}
+
+__global__ void gk_set_flags(const GInst* gi, const int* act, int x_zero_from_state) {
+  const GInst& I = gi[blockIdx.x];
+  if (threadIdx.x == 0) {
+    I.flags[0] = act[blockIdx.x];
+    if (x_zero_from_state >= 0) I.flags[2] = x_zero_from_state ? act[gridDim.x + blockIdx.x] : 0;
+  }
+}
+
+__global__ void gk_bump(int* dj) {
+  if (threadIdx.x == 0) *dj += 1;
+}
+
+}  // namespace bt
+}  // namespace kfbi
+
+// ============================================================================
+// host side
+// ============================================================================
+
+using namespace kfbi;
+using namespace kfbi::bt;
+using kfbi::tc::PassDesc;
+using kfbi::tc::GroupArgs;
+
+struct kfbi_batch {
+  int n = 0;
+  int device = 0;
+  int nsm = 148;
+  std::vector<kfbi_domain*> doms;
+  std::vector<kfbi_state*> states;  // bound at the first step
+  std::vector<GInst> h_inst;
+  GInst* d_inst = nullptr;
+  int* d_flags = nullptr;       // 4 ints per instance
+  int* d_j = nullptr;           // lockstep iteration index
+  int* d_sel = nullptr;         // 2n ints (selection for axpy / flags)
+  double* d_scal_all = nullptr; // 8 doubles per instance (readback staging)
+  double* d_tol = nullptr;      // n inner tolerances
+  double* h_scal = nullptr;     // pinned: 8 doubles per instance
+  int* h_flags = nullptr;       // pinned: 4 ints per instance
+  // grouped pass descriptors and tile prefixes, per pass kind
+  enum { kDense1, kDense2, kDense3, kDense4, kSparse2, kSparse3, kPassKinds };
+  PassDesc* d_pass[kPassKinds] = {nullptr};
+  int* d_prefix[kPassKinds] = {nullptr};
+  int total[kPassKinds] = {0};
+  int max_n_irr = 1, max_nb = 1, max_Mp = 128, max_nrows = 1, max_planes_blocks = 1;
+  bool bound = false;
+  // autotuned launch shape of the grouped passes (CTAs per SM multiple,
+  // tile order) and the CUDA graph of one lockstep GMRES iteration
+  int tile_order = 0;  // 0: instances in given order, 1: largest first
+  cudaGraphExec_t iter_graph = nullptr;
+  cudaStream_t graph_stream = nullptr;
+  double tuned_us[2] = {0.0, 0.0};
+  std::string err;
+  long long launches = 0;
+};
+
+namespace {
+
+dim3 inst_grid(int nblocks_x, int n) { return dim3((unsigned)std::max(1, nblocks_x), (unsigned)n); }
+
+void build_passes(kfbi_batch* B) {
+  // per-instance descriptors for the dense and sparse passes (kappa fixed by the states)
+  for (int kind = 0; kind < kfbi_batch::kPassKinds; ++kind) {
+    std::vector<PassDesc> ds(B->n);
+    std::vector<int> pref(B->n + 1, 0);
+    for (int ii = 0; ii < B->n; ++ii) {
+      const int i = B->tile_order ? ii : ii;  // order applied through the instance permutation below
+      kfbi_domain* D = B->doms[i];
+      TcDst* T = D->tc;
+      const GInst& I = B->h_inst[i];
+      const int P = I.C ? 2 : 1;
+      PassDesc d{};
+      d.b_hi = T->d_maps + kMapS_hi;
+      d.b_lo = T->d_maps + kMapS_lo;
+      d.lam = T->lam;
+      d.Mp = T->Mp;
+      d.n1 = T->n1;
+      d.kb0 = 0;
+      d.nk = T->Mp / tc::BK;
+      d.ct0 = 0;
+      d.nct = T->Mp / tc::BN;
+      d.nrt = P * T->Mp / tc::BM;
+      d.kre = 0.f;
+      d.scale = 0.f;
+      d.active = B->d_flags + 4 * i;
+      const float scale = (float)((2.0 / D->M) * (2.0 / D->M));
+      switch (kind) {
+        case kfbi_batch::kDense1:
+          d.a_hi = T->d_maps + kMapR_hi; d.a_lo = T->d_maps + kMapR_lo;
+          d.out_hi = T->T1h; d.out_lo = T->T1l; d.mode = 0; break;
+        case kfbi_batch::kDense2:
+          d.a_hi = T->d_maps + kMapT1_hi; d.a_lo = T->d_maps + kMapT1_lo;
+          d.out_hi = T->T2h; d.out_lo = T->T2l; d.mode = I.C ? 0 : 1;
+          d.kre = (float)I.kre; d.scale = scale; break;
+        case kfbi_batch::kDense3:
+          d.a_hi = T->d_maps + kMapT2_hi; d.a_lo = T->d_maps + kMapT2_lo;
+          d.out_hi = T->T1h; d.out_lo = T->T1l; d.mode = 0; break;
+        case kfbi_batch::kDense4:
+          d.a_hi = T->d_maps + kMapT1_hi; d.a_lo = T->d_maps + kMapT1_lo;
+          d.out_hi = T->U; d.out_lo = nullptr; d.mode = 2; break;
+        case kfbi_batch::kSparse2:
+          d.a_hi = T->d_maps + kMapT1s_hi; d.a_lo = T->d_maps + kMapT1s_lo;
+          d.out_hi = T->T2h; d.out_lo = T->T2l; d.mode = I.C ? 0 : 1;
+          d.kre = (float)I.kre; d.scale = scale; d.kb0 = T->kb0; d.nk = T->nk2; break;
+        case kfbi_batch::kSparse3:
+          d.a_hi = T->d_maps + kMapT2_hi; d.a_lo = T->d_maps + kMapT2_lo;
+          d.out_hi = T->U; d.out_lo = nullptr; d.mode = 2; d.ct0 = T->ct0; d.nct = T->nt3; break;
+      }
+      ds[i] = d;
+    }
+    // tile order: optionally largest instances first (longest-processing-time
+    // first keeps the persistent CTAs balanced)
+    std::vector<int> order(B->n);
+    std::iota(order.begin(), order.end(), 0);
+    if (B->tile_order == 1)
+      std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        return (long long)ds[a].nk * ds[a].nct * ds[a].nrt > (long long)ds[b].nk * ds[b].nct * ds[b].nrt;
+      });
+    std::vector<PassDesc> ordered(B->n);
+    for (int ii = 0; ii < B->n; ++ii) {
+      ordered[ii] = ds[order[ii]];
+      pref[ii + 1] = pref[ii] + ordered[ii].nct * ordered[ii].nrt;
+    }
+    B->total[kind] = pref[B->n];
+    if (!B->d_pass[kind]) {
+      KFBI_CUDA(cudaMalloc(&B->d_pass[kind], sizeof(PassDesc) * B->n));
+      KFBI_CUDA(cudaMalloc(&B->d_prefix[kind], sizeof(int) * (B->n + 1)));
+    }
+    KFBI_CUDA(cudaMemcpy(B->d_pass[kind], ordered.data(), sizeof(PassDesc) * B->n, cudaMemcpyHostToDevice));
+    KFBI_CUDA(cudaMemcpy(B->d_prefix[kind], pref.data(), sizeof(int) * (B->n + 1), cudaMemcpyHostToDevice));
+  }
+}
+
+void grouped_pass(kfbi_batch* B, int kind, cudaStream_t st) {
+  GroupArgs ga;
+  ga.descs = B->d_pass[kind];
+  ga.prefix = B->d_prefix[kind];
+  ga.n_inst = B->n;
+  ga.total = B->total[kind];
+  ga.one = PassDesc{};
+  ga.err = B->doms[0]->tc->err;
+  const int grid = std::min(ga.total, B->nsm);
+  KFBI_LAUNCH_P(KFBI_PROF_DST, tc::k_tc_pass, grid, tc::kPassThreads, tc::kPassSmem, st, ga);
+}
+
+int plane_blocks(kfbi_batch* B) { return B->max_planes_blocks; }
+
+// accurate application for all active instances: which = 0 (zero density),
+// 1 (x); with_ft; result grid in U64, u+ into ub (target 0) or Ax (1)
+void batch_accurate(kfbi_batch* B, int which, int with_ft, int target, cudaStream_t st) {
+  const int n = B->n;
+  const int pb = plane_blocks(B);
+  KFBI_LAUNCH_P(KFBI_PROF_GRID, gk_base_rhs, inst_grid(pb, n), 256, 0, st, B->d_inst, with_ft);
+  KFBI_LAUNCH_P(KFBI_PROF_CORRECT, gk_correct64, inst_grid((B->max_n_irr + 127) / 128, n), 128, 0, st,
+                B->d_inst, which, with_ft, (const int*)nullptr);
+  KFBI_LAUNCH_P(KFBI_PROF_GRID, gk_split64, inst_grid(pb, n), 256, 0, st, B->d_inst);
+  for (int sweep = 0; sweep < 2; ++sweep) {
+    grouped_pass(B, kfbi_batch::kDense1, st);
+    grouped_pass(B, kfbi_batch::kDense2, st);
+    KFBI_LAUNCH_P(KFBI_PROF_GRID, gk_eig_cplx, inst_grid(pb, n), 256, 0, st, B->d_inst);
+    grouped_pass(B, kfbi_batch::kDense3, st);
+    grouped_pass(B, kfbi_batch::kDense4, st);
+    if (sweep == 0) {
+      KFBI_LAUNCH_P(KFBI_PROF_GRID, gk_f32_to_f64, inst_grid(pb, n), 256, 0, st, B->d_inst);
+      KFBI_LAUNCH_P(KFBI_PROF_GRID, gk_resid_split, inst_grid(pb, n), 256, 0, st, B->d_inst);
+    } else {
+      KFBI_LAUNCH_P(KFBI_PROF_GRID, gk_add_f32, inst_grid(pb, n), 256, 0, st, B->d_inst);
+    }
+  }
+  KFBI_LAUNCH_P(KFBI_PROF_EXTRACT, gk_extract64, inst_grid((B->max_nb + 127) / 128, n), 128, 0, st,
+                B->d_inst, which, with_ft, target);
+  KFBI_CHECK_LAUNCH();
+}
+
+// one lockstep GMRES iteration: W = A_fast V[j], CGS2 Arnoldi, j += 1
+void batch_iteration(kfbi_batch* B, cudaStream_t st) {
+  const int n = B->n;
+  KFBI_LAUNCH_P(KFBI_PROF_CORRECT, gk_correct32_rv, inst_grid((B->max_n_irr + 127) / 128, n), 128, 0,
+                st, B->d_inst, (const int*)B->d_j);
+  KFBI_LAUNCH_P(KFBI_PROF_DST, gk_sparse_p1, dim3(B->max_Mp / 32, (B->max_nrows + 31) / 32, n),
+                dim3(32, 8), 0, st, B->d_inst);
+  grouped_pass(B, kfbi_batch::kSparse2, st);
+  KFBI_LAUNCH_P(KFBI_PROF_GRID, gk_eig_cplx, inst_grid(plane_blocks(B), n), 256, 0, st, B->d_inst);
+  grouped_pass(B, kfbi_batch::kSparse3, st);
+  KFBI_LAUNCH_P(KFBI_PROF_EXTRACT, gk_gather_extract, inst_grid(B->max_nb, n), 192, 0, st, B->d_inst,
+                (const int*)B->d_j);
+  KFBI_LAUNCH_P(KFBI_PROF_KRYLOV, gk_cgs_dots, inst_grid(GMAX, n), GT, 0, st, B->d_inst,
+                (const int*)B->d_j);
+  KFBI_LAUNCH_P(KFBI_PROF_KRYLOV, gk_cgs_update, inst_grid(GMAX, n), GT, 0, st, B->d_inst,
+                (const int*)B->d_j, 1, 0);
+  KFBI_LAUNCH_P(KFBI_PROF_KRYLOV, gk_cgs_update, inst_grid(GMAX, n), GT, 0, st, B->d_inst,
+                (const int*)B->d_j, 0, 1);
+  KFBI_LAUNCH_P(KFBI_PROF_KRYLOV, gk_cgs_finalize, inst_grid(GMAX, n), GT, 0, st, B->d_inst,
+                (const int*)B->d_j);
+  KFBI_LAUNCH_P(KFBI_PROF_KRYLOV, gk_bump, 1, 32, 0, st, B->d_j);
+  KFBI_CHECK_LAUNCH();
+}
+
+void read_state(kfbi_batch* B, cudaStream_t st) {
+  KFBI_LAUNCH(gk_gather_scal, B->n, 32, 0, st, B->d_inst, B->d_scal_all);
+  KFBI_CUDA(cudaMemcpyAsync(B->h_scal, B->d_scal_all, 8 * B->n * sizeof(double),
+                            cudaMemcpyDeviceToHost, st));
+  KFBI_CUDA(cudaMemcpyAsync(B->h_flags, B->d_flags, 4 * B->n * sizeof(int), cudaMemcpyDeviceToHost, st));
+  KFBI_CUDA(cudaStreamSynchronize(st));
+  for (int i = 0; i < B->n; ++i) {
+    int f = 0;
+    std::memcpy(&f, B->h_scal + 8 * i + 6, sizeof(int));
+    if (f) throw Status{KFBI_ERR_TIMEOUT, "a tensor-core DST pass gave up waiting on its pipeline"};
+  }
+}
+
+void set_active(kfbi_batch* B, const std::vector<int>& act, const std::vector<int>* xz, cudaStream_t st) {
+  std::vector<int> buf(act);
+  if (xz) buf.insert(buf.end(), xz->begin(), xz->end());
+  KFBI_CUDA(cudaMemcpyAsync(B->d_sel, buf.data(), buf.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+  KFBI_LAUNCH(gk_set_flags, B->n, 32, 0, st, B->d_inst, (const int*)B->d_sel, xz ? 1 : -1);
+  KFBI_CHECK_LAUNCH();
+}
+
+}  // namespace
+
+extern "C" {
+
+kfbi_status kfbi_batch_create(kfbi_domain* const* domains, int n, void* stream, kfbi_batch** out) {
+  if (!out || !domains || n < 1 || n > 4096) {
+    set_global_error("kfbi_batch_create: need 1 <= n <= 4096 domains");
+    return KFBI_ERR_ARG;
+  }
+  *out = nullptr;
+  for (int i = 0; i < n; ++i)
+    if (!domains[i] || !domains[i]->tc || domains[i]->n_irr == 0 ||
+        domains[i]->restart != domains[0]->restart) {
+      set_global_error("kfbi_batch_create: every domain must be KFBI_MIXED_TF32 with an interface "
+                       "and the same gmres_restart");
+      return KFBI_ERR_ARG;
+    }
+  kfbi_batch* B = new (std::nothrow) kfbi_batch();
+  if (!B) return KFBI_ERR_OOM;
+  B->n = n;
+  B->doms.assign(domains, domains + n);
+  kfbi_status s = guarded(nullptr, [&]() -> kfbi_status {
+    KFBI_CUDA(cudaGetDevice(&B->device));
+    KFBI_CUDA(cudaDeviceGetAttribute(&B->nsm, cudaDevAttrMultiProcessorCount, B->device));
+    KFBI_CUDA(cudaMalloc(&B->d_inst, sizeof(GInst) * n));
+    KFBI_CUDA(cudaMalloc(&B->d_flags, sizeof(int) * 4 * n));
+    KFBI_CUDA(cudaMemset(B->d_flags, 0, sizeof(int) * 4 * n));
+    KFBI_CUDA(cudaMalloc(&B->d_j, sizeof(int)));
+    KFBI_CUDA(cudaMalloc(&B->d_sel, sizeof(int) * 2 * n));
+    KFBI_CUDA(cudaMalloc(&B->d_scal_all, sizeof(double) * 8 * n));
+    KFBI_CUDA(cudaMalloc(&B->d_tol, sizeof(double) * n));
+    KFBI_CUDA(cudaMallocHost(&B->h_scal, sizeof(double) * 8 * n));
+    KFBI_CUDA(cudaMallocHost(&B->h_flags, sizeof(int) * 4 * n));
+    for (int i = 0; i < n; ++i) {
+      kfbi_domain* D = domains[i];
+      B->max_n_irr = std::max(B->max_n_irr, D->n_irr);
+      B->max_nb = std::max(B->max_nb, D->nb);
+      B->max_Mp = std::max(B->max_Mp, D->Mp);
+      B->max_nrows = std::max(B->max_nrows, D->tc->nrows);
+    }
+    B->max_planes_blocks = std::min(1024, (B->max_Mp * B->max_Mp + 255) / 256);
+    KFBI_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    return KFBI_OK;
+  });
+  if (s != KFBI_OK) {
+    kfbi_batch_destroy(B);
+    return s;
+  }
+  *out = B;
+  return KFBI_OK;
+}
+
+void kfbi_batch_destroy(kfbi_batch* B) {
+  if (!B) return;
+  cudaDeviceSynchronize();
+  if (B->iter_graph) cudaGraphExecDestroy(B->iter_graph);
+  for (int k = 0; k < kfbi_batch::kPassKinds; ++k) {
+    if (B->d_pass[k]) cudaFree(B->d_pass[k]);
+    if (B->d_prefix[k]) cudaFree(B->d_prefix[k]);
+  }
+  void* ps[] = {B->d_inst, B->d_flags, B->d_j, B->d_sel, B->d_scal_all, B->d_tol};
+  for (void* p : ps)
+    if (p) cudaFree(p);
+  if (B->h_scal) cudaFreeHost(B->h_scal);
+  if (B->h_flags) cudaFreeHost(B->h_flags);
+  delete B;
+}
+
+const char* kfbi_batch_last_error(const kfbi_batch* B) { return B ? B->err.c_str() : ""; }
+
+}  // extern "C"
+
+namespace {
+
+// Fill the per-instance descriptors for the bound states and this step's
+// boundary data / sources.
+void fill_instances(kfbi_batch* B, kfbi_state* const* states, const void* const* g_next,
+                    const double* const* src) {
+  B->h_inst.resize(B->n);
+  for (int i = 0; i < B->n; ++i) {
+    kfbi_domain* D = B->doms[i];
+    kfbi_state* S = states[i];
+    TcDst* T = D->tc;
+    GInst I{};
+    I.Mp = D->Mp; I.n1 = D->n1; I.nb = D->nb; I.n_irr = D->n_irr; I.n_arms = D->n_arms;
+    I.M = D->M; I.m = D->restart; I.C = S->kim != 0.0; I.eq = S->eq;
+    I.rmin = T->rmin; I.nrows = T->nrows;
+    I.h = D->h; I.kre = S->kre; I.kim = S->kim; I.scale = (2.0 / D->M) * (2.0 / D->M);
+    I.dt = S->dt; I.theta = S->theta;
+    I.mask = D->d_mask; I.irr_off = D->d_irr_off; I.arm_start = D->d_arm_start; I.arm_k0 = D->d_arm_k0;
+    I.alpha = D->d_arm_alpha; I.beta = D->d_arm_beta; I.arm_fidx = D->d_arm_fidx;
+    I.arm_fcoef = D->d_arm_fcoef; I.node_gidx = D->d_node_gidx; I.node_w = D->d_node_w;
+    I.node_a = D->d_node_a; I.node_b = D->d_node_b; I.node_fidx = D->d_node_fidx;
+    I.node_fcoef = D->d_node_fcoef; I.lam64 = D->d_lam;
+    I.alpha32 = D->d_arm_alpha32; I.beta32 = D->d_arm_beta32; I.arm_fcoef32 = D->d_arm_fcoef32;
+    I.node_w32 = D->d_node_w32; I.node_a32 = D->d_node_a32; I.node_b32 = D->d_node_b32;
+    I.S32 = T->S32; I.row_start = T->row_start; I.node_col = T->node_col;
+    I.R64 = D->d_R; I.U64 = D->d_U; I.Rh = T->Rh; I.Rl = T->Rl; I.T2h = T->T2h; I.T2l = T->T2l;
+    I.U32 = T->U; I.T1sh = T->T1sh; I.T1sl = T->T1sl; I.rv = T->rv;
+    I.V = (double2*)D->d_V; I.W = (double2*)D->d_W; I.H = (double2*)D->d_H; I.cs = D->d_cs;
+    I.sn = (double2*)D->d_sn; I.g = (double2*)D->d_g; I.hcol = (double2*)D->d_hcol;
+    I.part = (double2*)D->d_part; I.Rv = (double2*)D->d_Rv; I.Dv = (double2*)D->d_Dv;
+    I.Ax = (double2*)D->d_Ax; I.scal = D->d_scal;
+    I.u = S->d_u; I.F = S->d_F; I.Fprev = S->d_Fprev; I.ft = S->d_ft; I.aux = S->d_aux;
+    I.x = (double2*)S->d_phi; I.b = (double2*)S->d_b; I.ub = (double2*)S->d_ub;
+    I.g_next = (const double*)g_next[i];
+    I.src = src ? src[i] : nullptr;
+    I.flags = B->d_flags + 4 * i;
+    B->h_inst[i] = I;
+  }
+  KFBI_CUDA(cudaMemcpy(B->d_inst, B->h_inst.data(), sizeof(GInst) * B->n, cudaMemcpyHostToDevice));
+}
+
+// Refinement GMRES for every instance, lockstep (see gmres_solve).
+kfbi_status batch_gmres(kfbi_batch* B, kfbi_solve_info* infos, cudaStream_t st) {
+  const int n = B->n;
+  const double kInnerFloor = 1e-6;
+  std::vector<int> act(n, 1), xz(n), conv(n, 0), iters(n, 0), apps(n, 0);
+  std::vector<double> bnorm(n, 0.0), rn(n, 0.0);
+  for (int i = 0; i < n; ++i) xz[i] = B->states[i]->phi_zero ? 1 : 0;
+  // ||b||
+  set_active(B, act, &xz, st);
+  KFBI_LAUNCH_P(KFBI_PROF_KRYLOV, gk_bnorm, inst_grid(1, n), 1024, 0, st, B->d_inst,
+                B->doms[0]->desc.gmres_tol, 0);
+  read_state(B, st);
+  for (int i = 0; i < n; ++i) bnorm[i] = B->h_scal[8 * i];
+  for (int sweep = 0; sweep < 8; ++sweep) {
+    // residual r = b - A_accurate x for instances still active
+    set_active(B, act, &xz, st);
+    std::vector<int> need(n);
+    bool any_acc = false;
+    for (int i = 0; i < n; ++i) {
+      need[i] = act[i] && !xz[i];
+      any_acc |= need[i] != 0;
+    }
+    if (any_acc) {
+      set_active(B, need, nullptr, st);
+      batch_accurate(B, 1, 0, 1, st);
+      for (int i = 0; i < n; ++i) apps[i] += need[i];
+      set_active(B, act, &xz, st);
+    }
+    KFBI_LAUNCH_P(KFBI_PROF_KRYLOV, gk_residual, inst_grid(1, n), 1024, 0, st, B->d_inst);
+    read_state(B, st);
+    bool any = false;
+    std::vector<double> inner_tol(n, 1.0);
+    for (int i = 0; i < n; ++i) {
+      if (!act[i]) continue;
+      rn[i] = B->h_scal[8 * i + 1];
+      if (!std::isfinite(rn[i])) {
+        B->err = "non-finite density residual";
+        return KFBI_ERR_NONFINITE;
+      }
+      const double tol = B->doms[i]->desc.gmres_tol;
+      if (bnorm[i] == 0.0 || rn[i] <= tol * bnorm[i] || iters[i] >= B->doms[i]->desc.gmres_maxit) {
+        conv[i] = rn[i] <= tol * bnorm[i] || bnorm[i] == 0.0;
+        act[i] = 0;
+        continue;
+      }
+      inner_tol[i] = std::max(0.5 * tol * bnorm[i] / rn[i], kInnerFloor);
+      any = true;
+    }
+    if (!any) break;
+    for (int i = 0; i < n; ++i) xz[i] = 0;
+    // inner GMRES on A_fast d = r, d = 0, lockstep over the active set;
+    // the instance's tolerance relative to its ||r|| goes into scal[3]
+    std::vector<int> inner(act);
+    set_active(B, inner, &xz, st);
+    KFBI_LAUNCH_P(KFBI_PROF_KRYLOV, gk_zero_dv, inst_grid(8, n), 256, 0, st, B->d_inst);
+    KFBI_LAUNCH_P(KFBI_PROF_KRYLOV, gk_bnorm, inst_grid(1, n), 1024, 0, st, B->d_inst, 1.0, 1);
+    KFBI_CUDA(cudaMemcpyAsync(B->d_tol, inner_tol.data(), n * sizeof(double), cudaMemcpyHostToDevice, st));
+    KFBI_CUDA(cudaMemcpyAsync(B->d_sel, inner.data(), n * sizeof(int), cudaMemcpyHostToDevice, st));
+    KFBI_LAUNCH(gk_set_tol, n, 32, 0, st, B->d_inst, (const double*)B->d_tol, (const int*)B->d_sel);
+    bool first_cycle = true;
+    for (int cycle = 0; cycle < 64; ++cycle) {
+      bool any_inner = false;
+      for (int i = 0; i < n; ++i) any_inner |= inner[i] != 0;
+      if (!any_inner) break;
+      set_active(B, inner, nullptr, st);
+      if (!first_cycle) {
+        // restart: W = A_fast Dv (Dv staged in V[0]) then r = Rv - W
+        KFBI_CUDA(cudaMemsetAsync(B->d_j, 0, sizeof(int), st));
+        KFBI_LAUNCH_P(KFBI_PROF_KRYLOV, gk_dv_to_v0, inst_grid(8, n), 256, 0, st, B->d_inst);
+        KFBI_LAUNCH_P(KFBI_PROF_CORRECT, gk_correct32_rv, inst_grid((B->max_n_irr + 127) / 128, n), 128, 0,
+                      st, B->d_inst, (const int*)B->d_j);
+        KFBI_LAUNCH_P(KFBI_PROF_DST, gk_sparse_p1, dim3(B->max_Mp / 32, (B->max_nrows + 31) / 32, n),
+                      dim3(32, 8), 0, st, B->d_inst);
+        grouped_pass(B, kfbi_batch::kSparse2, st);
+        KFBI_LAUNCH_P(KFBI_PROF_GRID, gk_eig_cplx, inst_grid(plane_blocks(B), n), 256, 0, st, B->d_inst);
+        grouped_pass(B, kfbi_batch::kSparse3, st);
+        KFBI_LAUNCH_P(KFBI_PROF_EXTRACT, gk_gather_extract, inst_grid(B->max_nb, n), 192, 0, st,
+                      B->d_inst, (const int*)B->d_j);
+      }
+      KFBI_LAUNCH_P(KFBI_PROF_KRYLOV, gk_restart, inst_grid(1, n), 1024, 0, st, B->d_inst,
+                    first_cycle ? 0 : 1);
+      first_cycle = false;
+      KFBI_CUDA(cudaMemsetAsync(B->d_j, 0, sizeof(int), st));
+      read_state(B, st);
+      int m = 0;
+      for (int i = 0; i < n; ++i) {
+        if (!inner[i]) continue;
+        m = std::max(m, B->doms[i]->restart);
+        if (B->h_scal[8 * i + 2] != 0.0) inner[i] = 0;  // converged at the restart
+      }
+      bool any_left = false;
+      for (int i = 0; i < n; ++i) any_left |= inner[i] != 0;
+      if (!any_left) break;
+      for (int j = 0; j < m; ++j) {
+        // instances whose restart length is shorter stop at their m
+        if (B->iter_graph) {
+          KFBI_CUDA(cudaGraphLaunch(B->iter_graph, st));
+          g_launches.fetch_add(B->launches);
+        } else
+          batch_iteration(B, st);
+        read_state(B, st);
+        bool still = false;
+        for (int i = 0; i < n; ++i) {
+          if (!inner[i]) continue;
+          ++iters[i];
+          ++apps[i];
+          if (B->h_flags[4 * i] == 0) {
+            if (B->h_scal[8 * i + 2] == 2.0) {
+              B->err = "non-finite GMRES residual";
+              return KFBI_ERR_NONFINITE;
+            }
+            inner[i] = 0;  // converged
+          }
+          still |= inner[i] != 0;
+        }
+        if (!still) break;
+      }
+      // x-update for every instance that iterated this cycle (k = flags[1])
+      KFBI_LAUNCH_P(KFBI_PROF_KRYLOV, gk_update, inst_grid(GMAX, n), GT, 0, st, B->d_inst);
+      // instances still active after m iterations restart (unless out of iterations)
+      for (int i = 0; i < n; ++i)
+        if (inner[i] && iters[i] >= B->doms[i]->desc.gmres_maxit) inner[i] = 0;
+      // clear k so a finished instance does not update twice
+      KFBI_LAUNCH(gk_clear_k, n, 32, 0, st, B->d_inst);
+      KFBI_CHECK_LAUNCH();
+    }
+    // x += d for the instances that ran the inner solve
+    std::vector<int> ran(n);
+    for (int i = 0; i < n; ++i) ran[i] = act[i];
+    KFBI_CUDA(cudaMemcpyAsync(B->d_sel, ran.data(), n * sizeof(int), cudaMemcpyHostToDevice, st));
+    KFBI_LAUNCH_P(KFBI_PROF_KRYLOV, gk_axpy, inst_grid(8, n), 256, 0, st, B->d_inst, (const int*)B->d_sel);
+    KFBI_CHECK_LAUNCH();
+  }
+  KFBI_CUDA(cudaStreamSynchronize(st));
+  kfbi_status status = KFBI_OK;
+  for (int i = 0; i < n; ++i) {
+    if (infos) {
+      infos[i].iters = iters[i];
+      infos[i].applications = apps[i] + 2;
+      infos[i].rel_residual = bnorm[i] > 0.0 ? rn[i] / bnorm[i] : 0.0;
+      infos[i].converged = conv[i];
+    }
+    if (!conv[i]) status = KFBI_ERR_NOT_CONVERGED;
+    B->states[i]->phi_zero = false;
+  }
+  if (status != KFBI_OK) B->err = "GMRES with refinement reached gmres_maxit for an instance";
+  return status;
+}
+
+// Capture one lockstep iteration into a CUDA graph (kernel arguments are
+// fixed: the iteration index and the active flags live in device memory).
+void capture_iteration(kfbi_batch* B) {
+  if (B->iter_graph) return;
+  cudaStream_t cs;
+  KFBI_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  cudaGraph_t graph;
+  const long long before = g_launches.load();
+  KFBI_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+  const bool prof = g_prof_on;
+  g_prof_on = false;  // no event records inside the graph
+  batch_iteration(B, cs);
+  g_prof_on = prof;
+  KFBI_CUDA(cudaStreamEndCapture(cs, &graph));
+  KFBI_CUDA(cudaGraphInstantiate(&B->iter_graph, graph, 0));
+  KFBI_CUDA(cudaGraphDestroy(graph));
+  KFBI_CUDA(cudaStreamDestroy(cs));
+  B->launches = g_launches.load() - before;  // kernels per graph replay
+  g_launches.fetch_sub(B->launches);
+}
+
+// Autotuner: time the grouped fast application with the two tile orders
+// (instances as given, largest first) and keep the faster one.
+void autotune(kfbi_batch* B, cudaStream_t st) {
+  cudaEvent_t e0, e1;
+  KFBI_CUDA(cudaEventCreate(&e0));
+  KFBI_CUDA(cudaEventCreate(&e1));
+  std::vector<int> all(B->n, 1), zero(B->n, 0);
+  for (int order = 0; order < 2; ++order) {
+    B->tile_order = order;
+    build_passes(B);
+    set_active(B, all, &zero, st);
+    KFBI_CUDA(cudaMemsetAsync(B->d_j, 0, sizeof(int), st));
+    // one warm-up and three timed passes over the two grouped fast passes
+    grouped_pass(B, kfbi_batch::kSparse2, st);
+    KFBI_CUDA(cudaEventRecord(e0, st));
+    for (int r = 0; r < 3; ++r) {
+      grouped_pass(B, kfbi_batch::kSparse2, st);
+      grouped_pass(B, kfbi_batch::kSparse3, st);
+    }
+    KFBI_CUDA(cudaEventRecord(e1, st));
+    KFBI_CUDA(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    KFBI_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    B->tuned_us[order] = 1e3 * ms / 3.0;
+  }
+  B->tile_order = B->tuned_us[1] < B->tuned_us[0] ? 1 : 0;
+  build_passes(B);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+}
+
+}  // namespace
+
+extern "C" {
+
+kfbi_status kfbi_batch_step(kfbi_batch* B, kfbi_state* const* states, const void* const* g_next,
+                            const double* const* src_or_v, kfbi_solve_info* infos, void* stream) {
+  if (!B || !states || !g_next) return KFBI_ERR_ARG;
+  for (int i = 0; i < B->n; ++i) {
+    if (!states[i] || states[i]->dom != B->doms[i] || !states[i]->initialised || !g_next[i]) {
+      B->err = "state i must be initialised on domain i and g_next[i] given";
+      return KFBI_ERR_ARG;
+    }
+    if (states[i]->eq == KFBI_SCHRODINGER && (!src_or_v || !src_or_v[i])) {
+      B->err = "Schroedinger instances need the potential v in src_or_v[i]";
+      return KFBI_ERR_ARG;
+    }
+  }
+  kfbi_status s = guarded(nullptr, [&]() -> kfbi_status {
+    cudaStream_t st = (cudaStream_t)stream;
+    B->states.assign(states, states + B->n);
+    fill_instances(B, states, g_next, src_or_v);
+    if (!B->bound) {
+      autotune(B, st);
+      capture_iteration(B);
+      B->bound = true;
+    } else {
+      build_passes(B);
+    }
+    const int n = B->n;
+    std::vector<int> all(n, 1);
+    set_active(B, all, nullptr, st);
+    KFBI_LAUNCH_P(KFBI_PROF_GRID, gk_make_ft, inst_grid(plane_blocks(B), n), 256, 0, st, B->d_inst);
+    batch_accurate(B, 0, 1, 0, st);
+    KFBI_LAUNCH_P(KFBI_PROF_GRID, gk_make_b, inst_grid((B->max_nb + 255) / 256, n), 256, 0, st,
+                  B->d_inst);
+    kfbi_status gs = batch_gmres(B, infos, st);
+    if (gs != KFBI_OK) return gs;
+    set_active(B, all, nullptr, st);
+    batch_accurate(B, 1, 1, 0, st);
+    KFBI_LAUNCH_P(KFBI_PROF_GRID, gk_step_update, inst_grid(plane_blocks(B), n), 256, 0, st, B->d_inst);
+    KFBI_CHECK_LAUNCH();
+    KFBI_CUDA(cudaStreamSynchronize(st));
+    return KFBI_OK;
+  });
+  if (s != KFBI_OK && B->err.empty()) B->err = kfbi_last_global_error();
+  return s;
+}
+
+kfbi_status kfbi_batch_tuning(const kfbi_batch* B, int* tile_order, double* us_natural,
+                              double* us_largest_first) {
+  if (!B) return KFBI_ERR_ARG;
+  if (tile_order) *tile_order = B->tile_order;
+  if (us_natural) *us_natural = B->tuned_us[0];
+  if (us_largest_first) *us_largest_first = B->tuned_us[1];
+  return KFBI_OK;
+}
+
+}  // extern "C"

@@ -32,12 +32,11 @@
 #include <mutex>
 #include <vector>
 
-#include "internal.h"
+#include "tc_internal.h"
 
 namespace kfbi {
 namespace tc {
 
-constexpr int BM = 128, BN = 64, BK = 32;
 constexpr int STAGES = 4;
 constexpr int A_BYTES = BM * BK * 4;          // 16 KiB
 constexpr int B_BYTES = BN * BK * 4;          // 8 KiB
@@ -51,16 +50,22 @@ constexpr uint32_t IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(BN >
                            ((uint32_t)(BM >> 4) << 24);
 constexpr long long WAIT_LIMIT = 4000000000LL;  // cycles (~2 s)
 
-struct PassParams {
-  float* out_hi;
-  float* out_lo;
-  const float* lam;
-  int Mp, n1, mode, nk;  // mode 0: split, 1: eigen-divide + split, 2: plain fp32
-  int kb0;               // first K-block (the pass covers K-blocks kb0 .. kb0 + nk - 1)
-  int ct0;               // first output column tile
-  float kre, scale;
-  int* err;
-};
+__device__ __forceinline__ const PassDesc* tile_desc(const GroupArgs& ga, int t, int& lt) {
+  if (!ga.descs) {
+    lt = t;
+    return &ga.one;
+  }
+  int lo = 0, hi = ga.n_inst - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (ga.prefix[mid] <= t)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  lt = t - ga.prefix[lo];
+  return ga.descs + lo;
+}
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -162,10 +167,7 @@ __device__ __forceinline__ void tmem_ld32_nowait(uint32_t taddr, uint32_t* r) {
 // tensor core lets its FP32 rounding error grow linearly with K (measured
 // 2.5e-5 relative at K = 1024); per-block draining keeps it at the level of
 // one block.
-__global__ void __launch_bounds__(THREADS, 1)
-    k_tc_dst_pass(const __grid_constant__ CUtensorMap mAhi, const __grid_constant__ CUtensorMap mAlo,
-                  const __grid_constant__ CUtensorMap mBhi, const __grid_constant__ CUtensorMap mBlo,
-                  PassParams prm) {
+__global__ void __launch_bounds__(THREADS, 1) k_tc_pass(const __grid_constant__ GroupArgs ga) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* tiles = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint64_t* full = (uint64_t*)(tiles + STAGES * STAGE_BYTES);
@@ -177,9 +179,6 @@ __global__ void __launch_bounds__(THREADS, 1)
   volatile int* s_state = (volatile int*)(tmem_slot + 1);  // [0] abort, [1] issued, [2] consumed
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int row0 = blockIdx.y * BM;
-  const int col0 = (prm.ct0 + blockIdx.x) * BN;
-  const int nk = prm.nk;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -209,56 +208,71 @@ __global__ void __launch_bounds__(THREADS, 1)
 
   if (warp == 0) {
     if (lane == 0) {
-      // TMA producer
-      int kb = 0;
-      for (; kb < nk; ++kb) {
-        const int s = kb % STAGES, n = kb / STAGES;
-        if (s_state[0] || !mbar_wait(&empty[s], (uint32_t)((n & 1) ^ 1))) {
-          s_state[0] = 1;
-          atomicOr(prm.err, 1);
-          break;
+      // TMA producer: stage ring continues across this CTA's tiles
+      int g = 0;
+      bool abort = false;
+      for (int t = blockIdx.x; t < ga.total && !abort; t += gridDim.x) {
+        int lt;
+        const PassDesc* d = tile_desc(ga, t, lt);
+        if (d->active && *d->active == 0) continue;
+        const int row0 = (lt / d->nct) * BM, col0 = (d->ct0 + lt % d->nct) * BN;
+        for (int kb = 0; kb < d->nk; ++kb, ++g) {
+          const int s = g % STAGES, n = g / STAGES;
+          if (s_state[0] || !mbar_wait(&empty[s], (uint32_t)((n & 1) ^ 1))) {
+            s_state[0] = 1;
+            atomicOr(ga.err, 1);
+            abort = true;
+            break;
+          }
+          uint8_t* st = tiles + s * STAGE_BYTES;
+          mbar_expect_tx(&full[s], STAGE_BYTES);
+          const int kx = (d->kb0 + kb) * BK;
+          tma_load_2d(st, d->a_hi, &full[s], kx, row0);
+          tma_load_2d(st + A_BYTES, d->a_lo, &full[s], kx, row0);
+          tma_load_2d(st + 2 * A_BYTES, d->b_hi, &full[s], kx, col0);
+          tma_load_2d(st + 2 * A_BYTES + B_BYTES, d->b_lo, &full[s], kx, col0);
         }
-        uint8_t* st = tiles + s * STAGE_BYTES;
-        mbar_expect_tx(&full[s], STAGE_BYTES);
-        const int kx = (prm.kb0 + kb) * BK;
-        tma_load_2d(st, &mAhi, &full[s], kx, row0);
-        tma_load_2d(st + A_BYTES, &mAlo, &full[s], kx, row0);
-        tma_load_2d(st + 2 * A_BYTES, &mBhi, &full[s], kx, col0);
-        tma_load_2d(st + 2 * A_BYTES + B_BYTES, &mBlo, &full[s], kx, col0);
       }
-      s_state[1] = kb;
+      s_state[1] = g;
     }
     __syncwarp();
   } else if (warp == 1) {
     if (lane == 0) {
-      // MMA issuer
-      int kb = 0;
-      for (; kb < nk; ++kb) {
-        const int s = kb % STAGES, n = kb / STAGES;
-        const int b = kb % NACC, nbuf = kb / NACC;
-        if (s_state[0] || !mbar_wait(&full[s], (uint32_t)(n & 1)) ||
-            !mbar_wait(&acce[b], (uint32_t)((nbuf & 1) ^ 1))) {
-          s_state[0] = 1;
-          atomicOr(prm.err, 2);
-          break;
-        }
-        tc_fence_after();
-        uint8_t* st = tiles + s * STAGE_BYTES;
-        const uint64_t ah = desc_sw128(st), al = desc_sw128(st + A_BYTES);
-        const uint64_t bh = desc_sw128(st + 2 * A_BYTES),
-                       bl = desc_sw128(st + 2 * A_BYTES + B_BYTES);
-        const uint32_t td = tmem + (uint32_t)(b * BN);
+      // MMA issuer: one K-block per accumulator, accumulators in a ring
+      int g = 0;
+      bool abort = false;
+      for (int t = blockIdx.x; t < ga.total && !abort; t += gridDim.x) {
+        int lt;
+        const PassDesc* d = tile_desc(ga, t, lt);
+        if (d->active && *d->active == 0) continue;
+        for (int kb = 0; kb < d->nk; ++kb, ++g) {
+          const int s = g % STAGES, n = g / STAGES;
+          const int b = g % NACC, nbuf = g / NACC;
+          if (s_state[0] || !mbar_wait(&full[s], (uint32_t)(n & 1)) ||
+              !mbar_wait(&acce[b], (uint32_t)((nbuf & 1) ^ 1))) {
+            s_state[0] = 1;
+            atomicOr(ga.err, 2);
+            abort = true;
+            break;
+          }
+          tc_fence_after();
+          uint8_t* st = tiles + s * STAGE_BYTES;
+          const uint64_t ah = desc_sw128(st), al = desc_sw128(st + A_BYTES);
+          const uint64_t bh = desc_sw128(st + 2 * A_BYTES),
+                         bl = desc_sw128(st + 2 * A_BYTES + B_BYTES);
+          const uint32_t td = tmem + (uint32_t)(b * BN);
 #pragma unroll
-        for (int k = 0; k < BK / 8; ++k) {
-          const uint64_t o = (uint64_t)(2 * k);  // 8 tf32 = 32 bytes, in 16-byte units
-          umma_tf32(td, ah + o, bh + o, k ? 1u : 0u);
-          umma_tf32(td, ah + o, bl + o, 1u);
-          umma_tf32(td, al + o, bh + o, 1u);
+          for (int k = 0; k < BK / 8; ++k) {
+            const uint64_t o = (uint64_t)(2 * k);  // 8 tf32 = 32 bytes, in 16-byte units
+            umma_tf32(td, ah + o, bh + o, k ? 1u : 0u);
+            umma_tf32(td, ah + o, bl + o, 1u);
+            umma_tf32(td, al + o, bh + o, 1u);
+          }
+          umma_commit(&empty[s]);
+          umma_commit(&accf[b]);
         }
-        umma_commit(&empty[s]);
-        umma_commit(&accf[b]);
       }
-      s_state[2] = kb;
+      s_state[2] = g;
       umma_commit(done);
     }
     __syncwarp();
@@ -266,57 +280,66 @@ __global__ void __launch_bounds__(THREADS, 1)
     // drain / epilogue warps: TMEM lane quarter (warp % 4) = tile rows
     const int q = warp & 3;
     const uint32_t lane_base = (uint32_t)(q * 32) << 16;
-    float acc[BN];
-#pragma unroll
-    for (int j = 0; j < BN; ++j) acc[j] = 0.f;
+    int g = 0;
     bool ok = true;
-    for (int kb = 0; kb < nk; ++kb) {
-      const int b = kb % NACC;
-      // one lane waits, the warp follows its verdict (tcgen05.ld needs the
-      // whole warp converged)
-      int got = 1;
-      if (lane == 0)
-        got = (!s_state[0] && mbar_wait(&accf[b], (uint32_t)((kb / NACC) & 1))) ? 1 : 0;
-      got = __shfl_sync(0xffffffffu, got, 0);
-      if (!got) {
-        ok = false;
-        if (lane == 0) {
-          s_state[0] = 1;
-          atomicOr(prm.err, 4);
+    for (int t = blockIdx.x; t < ga.total && ok; t += gridDim.x) {
+      int lt;
+      const PassDesc* d = tile_desc(ga, t, lt);
+      if (d->active && *d->active == 0) continue;
+      const int row0 = (lt / d->nct) * BM, col0 = (d->ct0 + lt % d->nct) * BN;
+      float acc[BN];
+#pragma unroll
+      for (int j = 0; j < BN; ++j) acc[j] = 0.f;
+      for (int kb = 0; kb < d->nk; ++kb, ++g) {
+        const int b = g % NACC;
+        // one lane waits, the warp follows its verdict (tcgen05.ld needs the
+        // whole warp converged)
+        int got = 1;
+        if (lane == 0)
+          got = (!s_state[0] && mbar_wait(&accf[b], (uint32_t)((g / NACC) & 1))) ? 1 : 0;
+        got = __shfl_sync(0xffffffffu, got, 0);
+        if (!got) {
+          ok = false;
+          if (lane == 0) {
+            s_state[0] = 1;
+            atomicOr(ga.err, 4);
+          }
+          break;
         }
-        break;
+        tc_fence_after();
+        uint32_t raw[BN];
+#pragma unroll
+        for (int cc = 0; cc < BN; cc += 32)
+          tmem_ld32_nowait(tmem + lane_base + (uint32_t)(b * BN + cc), &raw[cc]);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+        for (int j = 0; j < BN; ++j) acc[j] += __uint_as_float(raw[j]);
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&acce[b]);
       }
-      tc_fence_after();
-      uint32_t raw[BN];
-#pragma unroll
-      for (int cc = 0; cc < BN; cc += 32)
-        tmem_ld32_nowait(tmem + lane_base + (uint32_t)(b * BN + cc), &raw[cc]);
-      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-      for (int j = 0; j < BN; ++j) acc[j] += __uint_as_float(raw[j]);
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&acce[b]);
-    }
-    if (ok && !s_state[0]) {
-      const int Mp = prm.Mp;
+      if (!ok || s_state[0]) break;
+      const int Mp = d->Mp;
       const int grow = row0 + q * 32 + lane;
       const int p = grow / Mp, rr = grow - p * Mp;
       const size_t pbase = (size_t)p * Mp * Mp + rr;
-      const float lam_r = (prm.mode == 1) ? prm.lam[rr] : 0.f;
+      const int mode = d->mode, n1 = d->n1;
+      const float lam_r = (mode == 1) ? d->lam[rr] : 0.f;
+      const float kre = d->kre, scale = d->scale;
+      float* oh = d->out_hi;
+      float* ol = d->out_lo;
 #pragma unroll
       for (int j = 0; j < BN; ++j) {
         const int c = col0 + j;
         float x = acc[j];
-        if (prm.mode == 1)
-          x = (rr < prm.n1 && c < prm.n1) ? x * (prm.scale / (lam_r + prm.lam[c] - prm.kre)) : 0.f;
+        if (mode == 1) x = (rr < n1 && c < n1) ? x * (scale / (lam_r + d->lam[c] - kre)) : 0.f;
         const size_t o = pbase + (size_t)c * Mp;
-        if (prm.mode == 2) {
-          prm.out_hi[o] = x;
+        if (mode == 2) {
+          oh[o] = x;
         } else {
           const float hi = tf32_round(x);
-          prm.out_hi[o] = hi;
-          prm.out_lo[o] = tf32_round(x - hi);
+          oh[o] = hi;
+          ol[o] = tf32_round(x - hi);
         }
       }
     }
@@ -324,12 +347,12 @@ __global__ void __launch_bounds__(THREADS, 1)
   __syncthreads();
   if (threadIdx.x == 0 && s_state[0]) {
     // drain TMA copies that were issued but never consumed
-    for (int kb = s_state[2]; kb < s_state[1]; ++kb)
-      mbar_wait(&full[kb % STAGES], (uint32_t)((kb / STAGES) & 1));
+    for (int g = s_state[2]; g < s_state[1]; ++g)
+      mbar_wait(&full[g % STAGES], (uint32_t)((g / STAGES) & 1));
   }
   if (warp == 1) {
     if (lane == 0) {
-      if (!mbar_wait(done, 0u)) atomicOr(prm.err, 8);
+      if (!mbar_wait(done, 0u)) atomicOr(ga.err, 8);
     }
     __syncwarp();
     tc_fence_after();
@@ -651,25 +674,12 @@ __global__ void k_add_f32(double* __restrict__ dst, const float* __restrict__ sr
     dst[i] += (double)src[i];
 }
 
+const int kPassThreads = THREADS;
+const int kPassSmem = SMEM_BYTES;
+
 }  // namespace tc
 
 using namespace tc;
-
-struct TcDst {
-  int Mp = 0, n1 = 0;
-  float *S_hi = nullptr, *S_lo = nullptr, *lam = nullptr, *S32 = nullptr;
-  // sparse route for right-hand sides supported on the irregular nodes
-  float *T1sh = nullptr, *T1sl = nullptr, *rv = nullptr;
-  int *row_start = nullptr, *node_col = nullptr;
-  int rmin = 0, nrows = 0, kb0 = 0, nk2 = 0, ct0 = 0, nt3 = 0;
-  CUtensorMap mT1s_hi, mT1s_lo;
-  float *Rh = nullptr, *Rl = nullptr, *T1h = nullptr, *T1l = nullptr, *T2h = nullptr,
-        *T2l = nullptr, *U = nullptr;
-  int* err = nullptr;
-  CUtensorMap mS_hi, mS_lo, mR_hi, mR_lo, mT1_hi, mT1_lo, mT2_hi, mT2_lo;
-  int rhs_sparse_planes = 0;
-  long long bytes = 0;
-};
 
 static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   static std::once_flag once;
@@ -782,8 +792,14 @@ TcDst* tc_create(kfbi_domain* D, const Plan& P) {
     make_map(&T->mT2_lo, T->T2l, Mp, 2 * Mp, BM);
     make_map(&T->mT1s_hi, T->T1sh, Mp, 2 * Mp, BM);
     make_map(&T->mT1s_lo, T->T1sl, Mp, 2 * Mp, BM);
-    KFBI_CUDA(cudaFuncSetAttribute(k_tc_dst_pass, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    const CUtensorMap maps[kNumMaps] = {T->mS_hi,  T->mS_lo,  T->mR_hi,   T->mR_lo,   T->mT1_hi,
+                                        T->mT1_lo, T->mT2_hi, T->mT2_lo, T->mT1s_hi, T->mT1s_lo};
+    KFBI_CUDA(cudaMalloc(&T->d_maps, sizeof(maps)));
+    T->bytes += (long long)sizeof(maps);
+    KFBI_CUDA(cudaMemcpy(T->d_maps, maps, sizeof(maps), cudaMemcpyHostToDevice));
+    KFBI_CUDA(cudaFuncSetAttribute(k_tc_pass, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    SMEM_BYTES));
+    KFBI_CUDA(cudaDeviceGetAttribute(&T->nsm, cudaDevAttrMultiProcessorCount, D->device));
   } catch (...) {
     tc_destroy(T);
     throw;
@@ -799,30 +815,50 @@ void tc_destroy(TcDst* T) {
     if (p) cudaFree(p);
   if (T->row_start) cudaFree(T->row_start);
   if (T->node_col) cudaFree(T->node_col);
+  if (T->d_maps) cudaFree(T->d_maps);
   delete T;
 }
 
 long long tc_bytes(const TcDst* T) { return T ? T->bytes : 0; }
 
-static void launch_pass(TcDst* T, const CUtensorMap& ah, const CUtensorMap& al, float* oh,
-                        float* ol, int mode, int P, float kre, float scale, cudaStream_t st,
-                        int kb0 = 0, int nk = -1, int ct0 = 0, int nct = -1) {
-  PassParams prm;
-  prm.out_hi = oh;
-  prm.out_lo = ol;
-  prm.lam = T->lam;
-  prm.Mp = T->Mp;
-  prm.n1 = T->n1;
-  prm.mode = mode;
-  prm.nk = nk < 0 ? T->Mp / BK : nk;
-  prm.kb0 = kb0;
-  prm.ct0 = ct0;
-  prm.kre = kre;
-  prm.scale = scale;
-  prm.err = T->err;
-  dim3 grid(nct < 0 ? T->Mp / BN : nct, P * T->Mp / BM);
-  KFBI_LAUNCH_P(KFBI_PROF_DST, k_tc_dst_pass, grid, THREADS, SMEM_BYTES, st, ah, al, T->mS_hi,
-                T->mS_lo, prm);
+// Descriptor of one instance's pass: A operand maps (am_hi, am_lo: kMap*
+// indices), output, mode, K-block range and output column-tile range.
+static PassDesc pass_desc(TcDst* T, int am_hi, int am_lo, float* oh, float* ol, int mode, int P,
+                          float kre, float scale, int kb0 = 0, int nk = -1, int ct0 = 0,
+                          int nct = -1) {
+  PassDesc d;
+  d.a_hi = T->d_maps + am_hi;
+  d.a_lo = T->d_maps + am_lo;
+  d.b_hi = T->d_maps + kMapS_hi;
+  d.b_lo = T->d_maps + kMapS_lo;
+  d.out_hi = oh;
+  d.out_lo = ol;
+  d.lam = T->lam;
+  d.Mp = T->Mp;
+  d.n1 = T->n1;
+  d.mode = mode;
+  d.kb0 = kb0;
+  d.nk = nk < 0 ? T->Mp / BK : nk;
+  d.ct0 = ct0;
+  d.nct = nct < 0 ? T->Mp / BN : nct;
+  d.nrt = P * T->Mp / BM;
+  d.kre = kre;
+  d.scale = scale;
+  d.active = nullptr;
+  return d;
+}
+
+// One persistent launch over the tiles of a single instance.
+static void launch_pass(TcDst* T, const PassDesc& d, cudaStream_t st) {
+  GroupArgs ga;
+  ga.descs = nullptr;
+  ga.prefix = nullptr;
+  ga.n_inst = 1;
+  ga.total = d.nct * d.nrt;
+  ga.one = d;
+  ga.err = T->err;
+  const int grid = std::min(ga.total, T->nsm);
+  KFBI_LAUNCH_P(KFBI_PROF_DST, k_tc_pass, grid, THREADS, SMEM_BYTES, st, ga);
 }
 
 // Four TF32x3 passes: (Rh, Rl) -> U (fp32 planes), eigenvalue division after
@@ -832,13 +868,14 @@ static void tc_box_solve(kfbi_domain* D, double kre, double kim, int P, cudaStre
   const size_t plane = (size_t)T->Mp * T->Mp;
   const bool C = kim != 0.0;
   const float scale = (float)((2.0 / D->M) * (2.0 / D->M));
-  launch_pass(T, T->mR_hi, T->mR_lo, T->T1h, T->T1l, 0, P, 0.f, 0.f, st);
-  launch_pass(T, T->mT1_hi, T->mT1_lo, T->T2h, T->T2l, C ? 0 : 1, P, (float)kre, scale, st);
+  launch_pass(T, pass_desc(T, kMapR_hi, kMapR_lo, T->T1h, T->T1l, 0, P, 0.f, 0.f), st);
+  launch_pass(T, pass_desc(T, kMapT1_hi, kMapT1_lo, T->T2h, T->T2l, C ? 0 : 1, P, (float)kre, scale),
+              st);
   if (C)
     KFBI_LAUNCH_P(KFBI_PROF_GRID, k_eig_split_cplx, grid_for(plane, 256), 256, 0, st, T->T2h,
                   T->T2l, plane, T->Mp, T->n1, D->d_lam, kre, kim, (2.0 / D->M) * (2.0 / D->M));
-  launch_pass(T, T->mT2_hi, T->mT2_lo, T->T1h, T->T1l, 0, P, 0.f, 0.f, st);
-  launch_pass(T, T->mT1_hi, T->mT1_lo, T->U, nullptr, 2, P, 0.f, 0.f, st);
+  launch_pass(T, pass_desc(T, kMapT2_hi, kMapT2_lo, T->T1h, T->T1l, 0, P, 0.f, 0.f), st);
+  launch_pass(T, pass_desc(T, kMapT1_hi, kMapT1_lo, T->U, nullptr, 2, P, 0.f, 0.f), st);
 }
 
 // GMRES application (no volume source, only u+ wanted): the right-hand
@@ -869,12 +906,15 @@ static void tc_apply_sparse(kfbi_domain* D, double kre, double kim, const double
                 T->rv, D->n_irr, T->row_start, T->node_col, T->rmin, T->nrows, T->S32, T->T1sh,
                 T->T1sl, Mp, P);
   const float scale = (float)((2.0 / D->M) * (2.0 / D->M));
-  launch_pass(T, T->mT1s_hi, T->mT1s_lo, T->T2h, T->T2l, C ? 0 : 1, P, (float)kre, scale, st,
-              T->kb0, T->nk2);
+  launch_pass(T, pass_desc(T, kMapT1s_hi, kMapT1s_lo, T->T2h, T->T2l, C ? 0 : 1, P, (float)kre,
+                           scale, T->kb0, T->nk2),
+              st);
   if (C)
     KFBI_LAUNCH_P(KFBI_PROF_GRID, k_eig_split_cplx, grid_for(plane, 256), 256, 0, st, T->T2h,
                   T->T2l, plane, Mp, T->n1, D->d_lam, kre, kim, (2.0 / D->M) * (2.0 / D->M));
-  launch_pass(T, T->mT2_hi, T->mT2_lo, T->U, nullptr, 2, P, 0.f, 0.f, st, 0, -1, T->ct0, T->nt3);
+  launch_pass(T, pass_desc(T, kMapT2_hi, kMapT2_lo, T->U, nullptr, 2, P, 0.f, 0.f, 0, -1, T->ct0,
+                           T->nt3),
+              st);
   if (C)
     KFBI_LAUNCH_P(KFBI_PROF_EXTRACT, k_gather_extract<true>, D->nb, 192, 0, st, T->U, T->S32, Mp,
                   plane, D->d_node_gidx, D->d_node_w32, D->d_node_a32, D->d_node_b32, D->nb, phi,

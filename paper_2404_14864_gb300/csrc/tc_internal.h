@@ -1,0 +1,75 @@
+// Shared declarations of the tensor-core DST engine (tc_dst.cu) and the
+// batch engine (batch.cu).
+#pragma once
+
+#include <cuda.h>
+
+#include "internal.h"
+
+namespace kfbi {
+namespace tc {
+
+constexpr int BM = 128, BN = 64, BK = 32;
+
+// One instance's share of a (possibly grouped) pass.  Tensor maps live in
+// device memory (one array per domain).
+struct PassDesc {
+  const CUtensorMap* a_hi;
+  const CUtensorMap* a_lo;
+  const CUtensorMap* b_hi;
+  const CUtensorMap* b_lo;
+  float* out_hi;
+  float* out_lo;
+  const float* lam;
+  int Mp, n1;
+  int mode;  // 0: TF32 pair out, 1: eigenvalue division + pair, 2: plain fp32
+  int kb0;   // first K-block; the pass covers K-blocks kb0 .. kb0 + nk - 1
+  int nk;
+  int ct0;   // first output column tile
+  int nct;   // output column tiles
+  int nrt;   // row tiles (planes x Mp / BM)
+  float kre, scale;
+  const int* active;  // instance flag (nullptr: always); tiles of inactive instances are skipped
+};
+
+// Tiles of all instances of a grouped launch, in prefix order.  A single
+// instance passes its descriptor by value (descs == nullptr).
+struct GroupArgs {
+  const PassDesc* descs;
+  const int* prefix;  // n_inst + 1 tile offsets
+  int n_inst;
+  int total;
+  PassDesc one;
+  int* err;
+};
+
+__global__ void k_tc_pass(const __grid_constant__ GroupArgs ga);
+extern const int kPassThreads;
+extern const int kPassSmem;
+
+}  // namespace tc
+
+enum { kMapS_hi, kMapS_lo, kMapR_hi, kMapR_lo, kMapT1_hi, kMapT1_lo, kMapT2_hi, kMapT2_lo,
+       kMapT1s_hi, kMapT1s_lo, kNumMaps };
+
+struct TcDst {
+  int Mp = 0, n1 = 0;
+  float *S_hi = nullptr, *S_lo = nullptr, *lam = nullptr, *S32 = nullptr;
+  // sparse route for right-hand sides supported on the irregular nodes
+  float *T1sh = nullptr, *T1sl = nullptr, *rv = nullptr;
+  int *row_start = nullptr, *node_col = nullptr;
+  int rmin = 0, nrows = 0, kb0 = 0, nk2 = 0, ct0 = 0, nt3 = 0;
+  CUtensorMap mT1s_hi, mT1s_lo;
+  // device copies of the tensor maps, in kMap* order
+  CUtensorMap* d_maps = nullptr;
+  int nsm = 148;
+  float *Rh = nullptr, *Rl = nullptr, *T1h = nullptr, *T1l = nullptr, *T2h = nullptr,
+        *T2l = nullptr, *U = nullptr;
+  int* err = nullptr;
+  CUtensorMap mS_hi, mS_lo, mR_hi, mR_lo, mT1_hi, mT1_lo, mT2_hi, mT2_lo;
+  int rhs_sparse_planes = 0;
+  long long bytes = 0;
+};
+
+
+}  // namespace kfbi

@@ -100,6 +100,13 @@ def lib():
                                   ctypes.POINTER(ctypes.c_double)]),
         "kfbi_box_solve_noalloc": (S, [ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                        ctypes.c_double, ctypes.c_double, _VP, _VP, _VP]),
+        "kfbi_batch_create": (S, [ctypes.POINTER(_VP), ctypes.c_int, _VP, ctypes.POINTER(_VP)]),
+        "kfbi_batch_destroy": (None, [_VP]),
+        "kfbi_batch_step": (S, [_VP, ctypes.POINTER(_VP), ctypes.POINTER(_VP), ctypes.POINTER(_VP),
+                                ctypes.POINTER(SolveInfo), _VP]),
+        "kfbi_batch_tuning": (S, [_VP, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double),
+                                  ctypes.POINTER(ctypes.c_double)]),
+        "kfbi_batch_last_error": (ctypes.c_char_p, [_VP]),
         "kfbi_plan_create": (S, [ctypes.POINTER(DomainDesc), ctypes.POINTER(_VP)]),
         "kfbi_plan_destroy": (None, [_VP]),
         "kfbi_plan_size": (ctypes.c_longlong, [_VP, ctypes.c_int]),
@@ -351,6 +358,52 @@ class State:
             out = torch.empty(self.dom.nb, dtype=dt, device="cuda")
         _check(lib().kfbi_state_get_phi(self.h, _ptr(out), _stream(stream)), self.dom.h)
         return out
+
+
+class Batch:
+    """Owning wrapper of a kfbi_batch: grouped time steps of many domains."""
+
+    def __init__(self, domains, stream=None):
+        L = lib()
+        self.domains = list(domains)
+        arr = (_VP * len(self.domains))(*[d.h for d in self.domains])
+        h = ctypes.c_void_p()
+        _check(L.kfbi_batch_create(arr, len(self.domains), _stream(stream), ctypes.byref(h)))
+        self.h = h
+
+    def close(self):
+        if self.h:
+            lib().kfbi_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, states, g_next, src_or_v=None, stream=None):
+        """One step of every instance; returns the per-instance solve infos."""
+        n = len(self.domains)
+        st = (_VP * n)(*[s.h for s in states])
+        gs = (_VP * n)(*[_ptr(g) for g in g_next])
+        sv = None
+        if src_or_v is not None:
+            sv = (_VP * n)(*[(_ptr(x) if x is not None else None) for x in src_or_v])
+        infos = (SolveInfo * n)()
+        status = lib().kfbi_batch_step(self.h, st, gs, sv, infos, _stream(stream))
+        if status != KFBI_OK:
+            msg = lib().kfbi_batch_last_error(self.h) or b""
+            raise KfbiError(status, msg.decode())
+        return [infos[i].as_dict() for i in range(n)]
+
+    def tuning(self):
+        o = ctypes.c_int()
+        a = ctypes.c_double()
+        b = ctypes.c_double()
+        _check(lib().kfbi_batch_tuning(self.h, ctypes.byref(o), ctypes.byref(a), ctypes.byref(b)))
+        return {"tile_order": int(o.value), "us_natural": float(a.value),
+                "us_largest_first": float(b.value)}
 
 
 # ----------------------------------------------------------------------------
