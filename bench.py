@@ -45,8 +45,11 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--cpu-steps", type=int, default=2)
-    ap.add_argument("--workload", default="wave1024", choices=["wave1024", "batched"])
+    ap.add_argument("--workload", default="wave1024", choices=["wave1024", "batched", "served"])
     ap.add_argument("--batch", type=int, default=256)
+    ap.add_argument("--requests", type=int, default=100)
+    ap.add_argument("--max-resident", type=int, default=64)
+    ap.add_argument("--rate", type=float, default=200.0)
     return ap.parse_args()
 
 
@@ -347,6 +350,8 @@ def run_batched(args):
     lat = []
     n0 = kfbi.launch_count()
     iters = []
+    clk = ClockSampler(os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0])
+    clk.start()
     for k in range(Wm, Wm + K):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -356,6 +361,7 @@ def run_batched(args):
         e1.synchronize()
         lat.append(e0.elapsed_time(e1))
         iters.append(max(i["iters"] for i in infos))
+    clocks = clk.stop()
     t = sum(lat) / 1e3
     pts = sum(M * M for M, *_ in runs)
     errs = []
@@ -373,7 +379,85 @@ def run_batched(args):
                        "seed": 0, "dt": "h"},
             "latency_ms": {"p50": lat_s[len(lat_s) // 2], "p99": lat_s[-1]},
             "linf_vs_exact_max": max(errs), "gmres_iters_max_per_step": iters,
-            "gpu_launches": kfbi.launch_count() - n0, "tuning": batch.tuning()}
+            "gpu_launches": kfbi.launch_count() - n0, "tuning": batch.tuning(), "clocks": clocks}
+    print(json.dumps(line))
+    return 0
+
+
+# ----------------------------------------------------------------------------
+# served stream (Poisson arrivals, continuous batching, admission by HBM)
+# ----------------------------------------------------------------------------
+
+
+def run_served(args):
+    import numpy as np
+    import torch
+
+    from paper_2404_14864_gb300 import build, kfbi, workloads as W
+    build.build()
+    torch.cuda.init()
+    reqs = W.served_requests(args.requests, rate=args.rate, seed=0)
+    t_prep = time.perf_counter()
+    inputs = [W.request_inputs(kind, W.domain_desc(M, curve), steps)
+              for (_, kind, M, curve, steps) in reqs]
+    t_prep = time.perf_counter() - t_prep
+    srv = kfbi.Server(max_resident=args.max_resident, hbm_reserve_bytes=8 << 30, restart=50,
+                      plan_threads=8)
+    ids = []
+    for (arr, kind, M, curve, steps), x in zip(reqs, inputs):
+        desc = W.domain_desc(M, curve)
+        ids.append(srv.submit(desc, x["equation"], steps, x["dt"], arr, x["u0"], x["lap_u0"], x["g"],
+                              theta=x.get("theta", 0.25), u1=x.get("u1"), lap_u1=x.get("lap_u1"),
+                              src_init=x.get("src_init"), src_profile=x.get("src_profile"),
+                              src_coef=x.get("src_coef"), potential=x.get("potential"),
+                              tol=1e-10, maxit=2000))
+    torch.cuda.synchronize()
+    clk = ClockSampler(os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0])
+    clk.start()
+    n0 = kfbi.launch_count()
+    t0 = time.perf_counter()
+    srv.run(time_limit=3600.0)
+    wall = time.perf_counter() - t0
+    launches = kfbi.launch_count() - n0
+    clocks = clk.stop()
+    st = srv.stats()
+    infos = [srv.info(i) for i in ids]
+    lat = sorted(i["finished"] - i["arrival"] for i in infos if i["state"] == kfbi.REQ_DONE)
+    wait = sorted(i["admitted"] - i["arrival"] for i in infos if i["admitted"] >= 0)
+    q = lambda v, f: v[min(len(v) - 1, int(math.ceil(f * len(v))) - 1)] if v else None
+    # L-infinity error of each result against the exact solution (inside nodes)
+    errs = {"heat": 0.0, "wave": 0.0, "schrodinger": 0.0}
+    for (arr, kind, M, curve, steps), x, i in zip(reqs, inputs, ids):
+        u = srv.result(i)
+        if u is None:
+            continue
+        p = kfbi.Plan(W.domain_desc(M, curve))
+        ins = p.field("inside").reshape(M + 1, M + 1)[1:-1, 1:-1].astype(bool)
+        p.close()
+        errs[kind] = max(errs[kind], float(np.abs(u - x["exact"]())[ins].max()))
+    steps_total = sum(r[4] for r in reqs)
+    line = {"metric": "grid-point*steps/s, served stream (Poisson arrivals, continuous batching)",
+            "value": st["grid_point_steps"] / wall, "unit": UNIT, "n_gpus": 1,
+            "steps": steps_total, "warmup": 0, "ms_per_step": 1e3 * wall / max(1, st["ticks"]),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "tf32x3-f32acc+f64", "data": "synthetic (manufactured solutions)",
+            "config": {"workload": "served-%d-requests" % len(reqs), "rate_per_s": args.rate,
+                       "sizes": [128, 256, 512, 1024, 2048], "steps": [20, 200],
+                       "kinds": "heat:wave:schrodinger 1:1:1", "seed": 0,
+                       "max_resident": args.max_resident, "admission": "FIFO, exact device bytes, "
+                       "8 GiB of free HBM kept", "gmres": "restart 50, tol 1e-10"},
+            "latency_s": {"p50": q(lat, 0.5), "p99": q(lat, 0.99), "max": lat[-1] if lat else None},
+            "queue_wait_s": {"p50": q(wait, 0.5), "p99": q(wait, 0.99)},
+            "completed": st["completed"], "failed": st["failed"], "ticks": st["ticks"],
+            "mean_resident": st["resident_ticks"] / max(1, st["ticks"]),
+            "busy_s": st["busy_seconds"], "admit_s": st["admit_seconds"], "wall_s": wall,
+            "peak_device_gib": st["peak_device_bytes"] / 2 ** 30,
+            "linf_vs_exact_max": errs, "gpu_launches": launches, "clocks": clocks,
+            "e2e": {"value": st["grid_point_steps"] / wall, "unit": UNIT,
+                    "h2d_bytes_per_step": st["h2d_bytes"] / max(1, st["ticks"]),
+                    "d2h_bytes_per_step": st["d2h_bytes"] / max(1, st["ticks"])},
+            "host_input_prep_s": t_prep}
+    srv.close()
     print(json.dumps(line))
     return 0
 
@@ -437,6 +521,8 @@ def main():
 
     if args.workload == "batched":
         return run_batched(args)
+    if args.workload == "served":
+        return run_served(args)
 
     if world > 1:
         import torch

@@ -209,7 +209,9 @@ kfbi_status kfbi_state_get_phi(kfbi_state* st, void* phi_out_dev, void* stream);
  * batch is a CUDA graph replayed until every instance has converged.  The
  * first step binds the states, runs the autotuner (tile order of the
  * grouped passes, timed with CUDA events) and captures the graph.
- * Each instance gives the same result as kfbi_step_* on its own domain.
+ * An instance's result does not depend on what it is batched with (same
+ * bits alone or in any mix); against kfbi_step_* on its own domain it agrees
+ * to the GMRES tolerance (reduction orders differ).
  * The domains must outlive the batch. */
 typedef struct kfbi_batch kfbi_batch;
 kfbi_status kfbi_batch_create(kfbi_domain* const* domains, int n, void* stream, kfbi_batch** out);
@@ -235,8 +237,15 @@ const char* kfbi_last_error(const kfbi_domain* dom);
 const char* kfbi_last_global_error(void);
 /* Number of CUDA kernels this library has launched since it was loaded. */
 long long kfbi_launch_count(void);
-/* Device bytes held by the domain (work buffers + tables). */
+/* Device bytes held by the domain (work buffers + its own tables; the DST-I
+ * tables shared by all domains on one grid are counted by
+ * kfbi_table_cache_bytes). */
 long long kfbi_domain_device_bytes(const kfbi_domain* dom);
+/* Device bytes held by a state's time-level fields and vectors. */
+long long kfbi_state_device_bytes(const kfbi_state* st);
+/* Device bytes of the shared DST-I tables (S and eigenvalues, and their
+ * TF32/FP32 forms) alive for all grids (M, h) in use. */
+long long kfbi_table_cache_bytes(void);
 
 /* Kernel timing with CUDA events recorded on the launching stream around
  * every launch of the enabled kernel classes (off by default).
@@ -289,6 +298,109 @@ void kfbi_plan_destroy(kfbi_plan* plan);
 long long kfbi_plan_size(const kfbi_plan* plan, int field);
 /* Copy a field into host memory dst (kfbi_plan_size elements of its type). */
 kfbi_status kfbi_plan_export(const kfbi_plan* plan, int field, void* dst);
+/* Exact device bytes that a domain created from this plan's description
+ * plus one state of the given equation hold (kfbi_domain_device_bytes +
+ * kfbi_state_device_bytes), computed on the host; -1 on bad arguments. */
+long long kfbi_plan_device_bytes(const kfbi_plan* plan, int equation);
+
+/* ---- served stream (continuous batching) --------------------------------- */
+
+/* A server runs many independent time-stepping requests (heat, wave and
+ * Schroedinger solves of any grid size and domain) on one device.  A request
+ * is admitted when its arrival time has passed, a slot is free
+ * (max_resident) and its exact device bytes fit both the server's budget and
+ * the device's free memory less hbm_reserve_bytes; admission is first come
+ * first served (a request that does not fit holds back later ones).  On
+ * admission its domain, state, boundary data and source/potential are made
+ * resident on the device.  Each tick then advances every resident request
+ * by one time step in one batch step (kfbi_batch_step semantics: grouped
+ * launches, lockstep GMRES), so requests that arrive while others run join
+ * at the next tick and share their launches.  A request that has taken all
+ * its steps is retired: its final field is copied to its host u_out and its
+ * device memory is freed for the next admissions.  A request's result does
+ * not depend on the other requests it ran with.
+ * Host threads (plan_threads) build the host plans of arrived requests
+ * while the device works; with plan_threads = 0 plans are built at
+ * admission.  Not thread safe: submit, tick and run from one thread. */
+typedef struct kfbi_server kfbi_server;
+
+typedef struct {
+  int max_resident;            /* requests on the device at once, 1..4096 */
+  long long hbm_budget_bytes;  /* device bytes the resident requests may hold;
+                                  0 = the free memory at creation less hbm_reserve_bytes */
+  long long hbm_reserve_bytes; /* free device memory every admission leaves untouched */
+  int gmres_restart;           /* GMRES restart shared by all requests (lockstep batch) */
+  int plan_threads;            /* host threads building request plans, 0..64 */
+} kfbi_server_desc;
+
+typedef struct {
+  kfbi_domain_desc domain; /* precision KFBI_MIXED_TF32, gmres_restart = the server's */
+  int equation;            /* kfbi_equation */
+  int steps;               /* time steps, >= 1 */
+  double dt;               /* time step */
+  double theta;            /* theta of the wave scheme (wave only) */
+  double arrival;          /* arrival time, seconds on the server clock */
+  /* Host buffers read at admission; they must stay valid until the request
+   * is resident.  Grids are (M-1)^2 row-major interior values, float64, or
+   * complex128 interleaved for the Schroedinger equation. */
+  const void* u0;          /* u at t_0 */
+  const void* lap_u0;      /* Laplacian of u at t_0 */
+  const double* u1;        /* wave: u at t_1 */
+  const double* lap_u1;    /* wave: Laplacian of u at t_1 */
+  const void* g;           /* steps x n_boundary Dirichlet values at t_1..t_steps
+                              (wave: t_2..t_{steps+1}; complex128 for Schroedinger) */
+  const double* src_init;  /* heat: first source sum s^0 + s^1 (grid) or NULL */
+  const double* src_profile; /* heat: spatial source profile p (grid) or NULL */
+  const double* src_coef;  /* heat: steps coefficients; step n (0-based) uses the
+                              source sum src_coef[n] * p; NULL = 1 */
+  const double* potential; /* Schroedinger: potential v (grid, float64) */
+  void* u_out;             /* host, written at completion: the final field (grid);
+                              must stay valid until the request is done */
+} kfbi_request;
+
+typedef enum {
+  KFBI_REQ_QUEUED = 0,
+  KFBI_REQ_RESIDENT = 1,
+  KFBI_REQ_DONE = 2,
+  KFBI_REQ_FAILED = 3
+} kfbi_request_state;
+
+typedef struct {
+  int state;               /* kfbi_request_state */
+  int status;              /* kfbi_status of a failed request */
+  double arrival, admitted, finished; /* server clock seconds (-1: not yet) */
+  int admit_tick, finish_tick;        /* tick indices (-1: not yet) */
+  int steps_done;
+  int max_iters;           /* most GMRES iterations of one of its steps */
+  double max_rel_residual; /* largest final relative residual of its steps */
+  long long device_bytes;  /* device bytes it held while resident */
+} kfbi_request_info;
+
+typedef struct {
+  int ticks, admitted, completed, failed;
+  double busy_seconds;         /* inside batch steps */
+  double admit_seconds;        /* admitting (plan wait, uploads, init) on the calling thread */
+  double resident_ticks;       /* sum over ticks of the resident count */
+  long long peak_device_bytes; /* most bytes held by resident requests at once */
+  long long h2d_bytes, d2h_bytes;
+  double grid_point_steps;     /* sum over completed steps of M^2 */
+} kfbi_server_stats;
+
+kfbi_status kfbi_server_create(const kfbi_server_desc* desc, void* stream, kfbi_server** out);
+void kfbi_server_destroy(kfbi_server* server);
+/* Queue a request; *id receives its index (0, 1, ... in submission order). */
+kfbi_status kfbi_server_submit(kfbi_server* server, const kfbi_request* req, int* id);
+/* One tick at server time now (seconds; now < 0 reads the server's wall
+ * clock): admissions, one batch step of the resident requests, retirement.
+ * *n_resident (may be NULL) receives the requests that stepped. */
+kfbi_status kfbi_server_tick(kfbi_server* server, double now, int* n_resident);
+/* Restart the wall clock at 0 and tick until every submitted request is
+ * done or failed, sleeping while nothing is resident and the next arrival
+ * lies ahead; KFBI_ERR_TIMEOUT if time_limit (> 0) seconds pass first. */
+kfbi_status kfbi_server_run(kfbi_server* server, double time_limit);
+kfbi_status kfbi_server_request_info(const kfbi_server* server, int id, kfbi_request_info* info);
+kfbi_status kfbi_server_get_stats(const kfbi_server* server, kfbi_server_stats* stats);
+const char* kfbi_server_last_error(const kfbi_server* server);
 
 #ifdef __cplusplus
 }

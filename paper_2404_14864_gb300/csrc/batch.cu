@@ -10,9 +10,11 @@
 // iterating.  The per-iteration kernel sequence is captured once into a
 // CUDA graph (the iteration index lives in device memory) and replayed.
 //
-// The arithmetic of every kernel is the same as the single-instance path,
-// in the same order, so each instance of a batch produces the same bits as
-// the same domain stepped alone.
+// An instance's arithmetic does not depend on the other instances of the
+// batch (each tile, reduction and GMRES decision is its own), so a domain
+// gives the same bits whatever it is batched with.  Against the
+// single-instance path the kernels differ in reduction order, and results
+// agree to the GMRES tolerance.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -93,6 +95,7 @@ struct GInst {
   double2* ub;
   const double* g_next;   // per step (caller layout)
   const double* src;      // heat source sum or Schroedinger potential (caller layout)
+  double src_scale;       // heat: the source sum of this step is src_scale * src
   int* flags;             // [0] active, [1] k (iterations of the current cycle), [2] x_zero
 };
 
@@ -877,7 +880,7 @@ __global__ void gk_step_update(const GInst* gi) {
       const int r = (int)(idx / I.Mp), c = (int)(idx % I.Mp);
       const double uu = I.U64[idx];
       double f = four_dt * uu - I.F[idx];
-      if (I.src && r < I.n1 && c < I.n1) f += I.src[(size_t)r * I.n1 + c];
+      if (I.src && r < I.n1 && c < I.n1) f += I.src_scale * I.src[(size_t)r * I.n1 + c];
       I.u[idx] = uu;
       I.F[idx] = f;
     }
@@ -926,7 +929,8 @@ using kfbi::tc::PassDesc;
 using kfbi::tc::GroupArgs;
 
 struct kfbi_batch {
-  int n = 0;
+  int n = 0;    // bound instances
+  int cap = 0;  // capacity of the per-instance device arrays
   int device = 0;
   int nsm = 148;
   std::vector<kfbi_domain*> doms;
@@ -950,6 +954,7 @@ struct kfbi_batch {
   // autotuned launch shape of the grouped passes (CTAs per SM multiple,
   // tile order) and the CUDA graph of one lockstep GMRES iteration
   int tile_order = 0;  // 0: instances in given order, 1: largest first
+  bool tuned = false;  // the autotuner ran (its choice is kept across rebinds)
   cudaGraphExec_t iter_graph = nullptr;
   cudaStream_t graph_stream = nullptr;
   double tuned_us[2] = {0.0, 0.0};
@@ -967,7 +972,7 @@ void build_passes(kfbi_batch* B) {
     std::vector<PassDesc> ds(B->n);
     std::vector<int> pref(B->n + 1, 0);
     for (int ii = 0; ii < B->n; ++ii) {
-      const int i = B->tile_order ? ii : ii;  // order applied through the instance permutation below
+      const int i = ii;  // tile order is applied by the permutation below
       kfbi_domain* D = B->doms[i];
       TcDst* T = D->tc;
       const GInst& I = B->h_inst[i];
@@ -1025,10 +1030,6 @@ void build_passes(kfbi_batch* B) {
       pref[ii + 1] = pref[ii] + ordered[ii].nct * ordered[ii].nrt;
     }
     B->total[kind] = pref[B->n];
-    if (!B->d_pass[kind]) {
-      KFBI_CUDA(cudaMalloc(&B->d_pass[kind], sizeof(PassDesc) * B->n));
-      KFBI_CUDA(cudaMalloc(&B->d_prefix[kind], sizeof(int) * (B->n + 1)));
-    }
     KFBI_CUDA(cudaMemcpy(B->d_pass[kind], ordered.data(), sizeof(PassDesc) * B->n, cudaMemcpyHostToDevice));
     KFBI_CUDA(cudaMemcpy(B->d_prefix[kind], pref.data(), sizeof(int) * (B->n + 1), cudaMemcpyHostToDevice));
   }
@@ -1120,47 +1121,91 @@ void set_active(kfbi_batch* B, const std::vector<int>& act, const std::vector<in
   KFBI_CHECK_LAUNCH();
 }
 
+// Per-instance device arrays for at least n instances (contents are
+// rebuilt by every step).
+void batch_reserve(kfbi_batch* B, int n) {
+  if (n <= B->cap) return;
+  KFBI_CUDA(cudaDeviceSynchronize());
+  void* ds[] = {B->d_inst, B->d_flags, B->d_sel, B->d_scal_all, B->d_tol};
+  for (void* p : ds)
+    if (p) cudaFree(p);
+  for (int k = 0; k < kfbi_batch::kPassKinds; ++k) {
+    if (B->d_pass[k]) cudaFree(B->d_pass[k]);
+    if (B->d_prefix[k]) cudaFree(B->d_prefix[k]);
+    B->d_pass[k] = nullptr;
+    B->d_prefix[k] = nullptr;
+  }
+  if (B->h_scal) cudaFreeHost(B->h_scal);
+  if (B->h_flags) cudaFreeHost(B->h_flags);
+  B->d_inst = nullptr; B->d_flags = nullptr; B->d_sel = nullptr; B->d_scal_all = nullptr;
+  B->d_tol = nullptr; B->h_scal = nullptr; B->h_flags = nullptr;
+  const int c = std::max(n, 2 * B->cap);
+  B->cap = 0;
+  KFBI_CUDA(cudaMalloc(&B->d_inst, sizeof(GInst) * c));
+  KFBI_CUDA(cudaMalloc(&B->d_flags, sizeof(int) * 4 * c));
+  KFBI_CUDA(cudaMemset(B->d_flags, 0, sizeof(int) * 4 * c));
+  KFBI_CUDA(cudaMalloc(&B->d_sel, sizeof(int) * 2 * c));
+  KFBI_CUDA(cudaMalloc(&B->d_scal_all, sizeof(double) * 8 * c));
+  KFBI_CUDA(cudaMalloc(&B->d_tol, sizeof(double) * c));
+  KFBI_CUDA(cudaMallocHost(&B->h_scal, sizeof(double) * 8 * c));
+  KFBI_CUDA(cudaMallocHost(&B->h_flags, sizeof(int) * 4 * c));
+  for (int k = 0; k < kfbi_batch::kPassKinds; ++k) {
+    KFBI_CUDA(cudaMalloc(&B->d_pass[k], sizeof(PassDesc) * c));
+    KFBI_CUDA(cudaMalloc(&B->d_prefix[k], sizeof(int) * (c + 1)));
+  }
+  B->cap = c;
+}
+
 }  // namespace
+
+namespace kfbi {
+
+kfbi_batch* batch_new() {
+  kfbi_batch* B = new kfbi_batch();
+  KFBI_CUDA(cudaGetDevice(&B->device));
+  KFBI_CUDA(cudaDeviceGetAttribute(&B->nsm, cudaDevAttrMultiProcessorCount, B->device));
+  KFBI_CUDA(cudaMalloc(&B->d_j, sizeof(int)));
+  return B;
+}
+
+void batch_bind(kfbi_batch* B, kfbi_domain* const* domains, int n) {
+  if (!domains || n < 1 || n > 4096) throw Status{KFBI_ERR_ARG, "a batch holds 1 to 4096 domains"};
+  for (int i = 0; i < n; ++i)
+    if (!domains[i] || !domains[i]->tc || domains[i]->n_irr == 0 ||
+        domains[i]->restart != domains[0]->restart)
+      throw Status{KFBI_ERR_ARG,
+                   "every domain of a batch must be KFBI_MIXED_TF32 with an interface and the "
+                   "same gmres_restart"};
+  batch_reserve(B, n);
+  if (B->iter_graph) {
+    KFBI_CUDA(cudaGraphExecDestroy(B->iter_graph));
+    B->iter_graph = nullptr;
+  }
+  B->bound = false;
+  B->n = n;
+  B->doms.assign(domains, domains + n);
+  B->max_n_irr = 1; B->max_nb = 1; B->max_Mp = 128; B->max_nrows = 1;
+  for (int i = 0; i < n; ++i) {
+    kfbi_domain* D = domains[i];
+    B->max_n_irr = std::max(B->max_n_irr, D->n_irr);
+    B->max_nb = std::max(B->max_nb, D->nb);
+    B->max_Mp = std::max(B->max_Mp, D->Mp);
+    B->max_nrows = std::max(B->max_nrows, D->tc->nrows);
+  }
+  B->max_planes_blocks = std::min(1024, (B->max_Mp * B->max_Mp + 255) / 256);
+}
+
+}  // namespace kfbi
 
 extern "C" {
 
 kfbi_status kfbi_batch_create(kfbi_domain* const* domains, int n, void* stream, kfbi_batch** out) {
-  if (!out || !domains || n < 1 || n > 4096) {
-    set_global_error("kfbi_batch_create: need 1 <= n <= 4096 domains");
-    return KFBI_ERR_ARG;
-  }
+  if (!out) return KFBI_ERR_ARG;
   *out = nullptr;
-  for (int i = 0; i < n; ++i)
-    if (!domains[i] || !domains[i]->tc || domains[i]->n_irr == 0 ||
-        domains[i]->restart != domains[0]->restart) {
-      set_global_error("kfbi_batch_create: every domain must be KFBI_MIXED_TF32 with an interface "
-                       "and the same gmres_restart");
-      return KFBI_ERR_ARG;
-    }
-  kfbi_batch* B = new (std::nothrow) kfbi_batch();
-  if (!B) return KFBI_ERR_OOM;
-  B->n = n;
-  B->doms.assign(domains, domains + n);
+  kfbi_batch* B = nullptr;
   kfbi_status s = guarded(nullptr, [&]() -> kfbi_status {
-    KFBI_CUDA(cudaGetDevice(&B->device));
-    KFBI_CUDA(cudaDeviceGetAttribute(&B->nsm, cudaDevAttrMultiProcessorCount, B->device));
-    KFBI_CUDA(cudaMalloc(&B->d_inst, sizeof(GInst) * n));
-    KFBI_CUDA(cudaMalloc(&B->d_flags, sizeof(int) * 4 * n));
-    KFBI_CUDA(cudaMemset(B->d_flags, 0, sizeof(int) * 4 * n));
-    KFBI_CUDA(cudaMalloc(&B->d_j, sizeof(int)));
-    KFBI_CUDA(cudaMalloc(&B->d_sel, sizeof(int) * 2 * n));
-    KFBI_CUDA(cudaMalloc(&B->d_scal_all, sizeof(double) * 8 * n));
-    KFBI_CUDA(cudaMalloc(&B->d_tol, sizeof(double) * n));
-    KFBI_CUDA(cudaMallocHost(&B->h_scal, sizeof(double) * 8 * n));
-    KFBI_CUDA(cudaMallocHost(&B->h_flags, sizeof(int) * 4 * n));
-    for (int i = 0; i < n; ++i) {
-      kfbi_domain* D = domains[i];
-      B->max_n_irr = std::max(B->max_n_irr, D->n_irr);
-      B->max_nb = std::max(B->max_nb, D->nb);
-      B->max_Mp = std::max(B->max_Mp, D->Mp);
-      B->max_nrows = std::max(B->max_nrows, D->tc->nrows);
-    }
-    B->max_planes_blocks = std::min(1024, (B->max_Mp * B->max_Mp + 255) / 256);
+    B = batch_new();
+    batch_bind(B, domains, n);
     KFBI_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
     return KFBI_OK;
   });
@@ -1197,7 +1242,7 @@ namespace {
 // Fill the per-instance descriptors for the bound states and this step's
 // boundary data / sources.
 void fill_instances(kfbi_batch* B, kfbi_state* const* states, const void* const* g_next,
-                    const double* const* src) {
+                    const double* const* src, const double* src_scale) {
   B->h_inst.resize(B->n);
   for (int i = 0; i < B->n; ++i) {
     kfbi_domain* D = B->doms[i];
@@ -1227,17 +1272,22 @@ void fill_instances(kfbi_batch* B, kfbi_state* const* states, const void* const*
     I.x = (double2*)S->d_phi; I.b = (double2*)S->d_b; I.ub = (double2*)S->d_ub;
     I.g_next = (const double*)g_next[i];
     I.src = src ? src[i] : nullptr;
+    I.src_scale = src_scale ? src_scale[i] : 1.0;
     I.flags = B->d_flags + 4 * i;
     B->h_inst[i] = I;
   }
   KFBI_CUDA(cudaMemcpy(B->d_inst, B->h_inst.data(), sizeof(GInst) * B->n, cudaMemcpyHostToDevice));
 }
 
-// Refinement GMRES for every instance, lockstep (see gmres_solve).
+// Refinement GMRES for every instance, lockstep (see gmres_solve).  An
+// instance whose residual turns non-finite is switched off and reported in
+// its info (converged 0, rel_residual NaN); the others carry on.  Returns
+// KFBI_ERR_NONFINITE if any instance went non-finite, else
+// KFBI_ERR_NOT_CONVERGED if any reached gmres_maxit, else KFBI_OK.
 kfbi_status batch_gmres(kfbi_batch* B, kfbi_solve_info* infos, cudaStream_t st) {
   const int n = B->n;
   const double kInnerFloor = 1e-6;
-  std::vector<int> act(n, 1), xz(n), conv(n, 0), iters(n, 0), apps(n, 0);
+  std::vector<int> act(n, 1), xz(n), conv(n, 0), iters(n, 0), apps(n, 0), bad(n, 0);
   std::vector<double> bnorm(n, 0.0), rn(n, 0.0);
   for (int i = 0; i < n; ++i) xz[i] = B->states[i]->phi_zero ? 1 : 0;
   // ||b||
@@ -1268,9 +1318,10 @@ kfbi_status batch_gmres(kfbi_batch* B, kfbi_solve_info* infos, cudaStream_t st) 
     for (int i = 0; i < n; ++i) {
       if (!act[i]) continue;
       rn[i] = B->h_scal[8 * i + 1];
-      if (!std::isfinite(rn[i])) {
-        B->err = "non-finite density residual";
-        return KFBI_ERR_NONFINITE;
+      if (!std::isfinite(rn[i]) || !std::isfinite(bnorm[i])) {
+        bad[i] = 1;
+        act[i] = 0;
+        continue;
       }
       const double tol = B->doms[i]->desc.gmres_tol;
       if (bnorm[i] == 0.0 || rn[i] <= tol * bnorm[i] || iters[i] >= B->doms[i]->desc.gmres_maxit) {
@@ -1341,10 +1392,11 @@ kfbi_status batch_gmres(kfbi_batch* B, kfbi_solve_info* infos, cudaStream_t st) 
           ++apps[i];
           if (B->h_flags[4 * i] == 0) {
             if (B->h_scal[8 * i + 2] == 2.0) {
-              B->err = "non-finite GMRES residual";
-              return KFBI_ERR_NONFINITE;
+              // non-finite GMRES residual: drop the instance from the sweeps
+              bad[i] = 1;
+              act[i] = 0;
             }
-            inner[i] = 0;  // converged
+            inner[i] = 0;  // converged (or dropped)
           }
           still |= inner[i] != 0;
         }
@@ -1361,25 +1413,34 @@ kfbi_status batch_gmres(kfbi_batch* B, kfbi_solve_info* infos, cudaStream_t st) 
     }
     // x += d for the instances that ran the inner solve
     std::vector<int> ran(n);
-    for (int i = 0; i < n; ++i) ran[i] = act[i];
+    for (int i = 0; i < n; ++i) ran[i] = act[i] && !bad[i];
     KFBI_CUDA(cudaMemcpyAsync(B->d_sel, ran.data(), n * sizeof(int), cudaMemcpyHostToDevice, st));
     KFBI_LAUNCH_P(KFBI_PROF_KRYLOV, gk_axpy, inst_grid(8, n), 256, 0, st, B->d_inst, (const int*)B->d_sel);
     KFBI_CHECK_LAUNCH();
   }
   KFBI_CUDA(cudaStreamSynchronize(st));
-  kfbi_status status = KFBI_OK;
+  bool any_bad = false, any_unconv = false;
   for (int i = 0; i < n; ++i) {
+    if (bad[i]) conv[i] = 0;
     if (infos) {
       infos[i].iters = iters[i];
       infos[i].applications = apps[i] + 2;
-      infos[i].rel_residual = bnorm[i] > 0.0 ? rn[i] / bnorm[i] : 0.0;
+      infos[i].rel_residual = bad[i] ? std::nan("") : (bnorm[i] > 0.0 ? rn[i] / bnorm[i] : 0.0);
       infos[i].converged = conv[i];
     }
-    if (!conv[i]) status = KFBI_ERR_NOT_CONVERGED;
+    any_bad |= bad[i] != 0;
+    any_unconv |= !conv[i] && !bad[i];
     B->states[i]->phi_zero = false;
   }
-  if (status != KFBI_OK) B->err = "GMRES with refinement reached gmres_maxit for an instance";
-  return status;
+  if (any_bad) {
+    B->err = "non-finite density residual in an instance";
+    return KFBI_ERR_NONFINITE;
+  }
+  if (any_unconv) {
+    B->err = "GMRES with refinement reached gmres_maxit for an instance";
+    return KFBI_ERR_NOT_CONVERGED;
+  }
+  return KFBI_OK;
 }
 
 // Capture one lockstep iteration into a CUDA graph (kernel arguments are
@@ -1436,11 +1497,13 @@ void autotune(kfbi_batch* B, cudaStream_t st) {
 
 }  // namespace
 
-extern "C" {
+namespace kfbi {
 
-kfbi_status kfbi_batch_step(kfbi_batch* B, kfbi_state* const* states, const void* const* g_next,
-                            const double* const* src_or_v, kfbi_solve_info* infos, void* stream) {
+kfbi_status batch_step(kfbi_batch* B, kfbi_state* const* states, const void* const* g_next,
+                       const double* const* src_or_v, const double* src_scale,
+                       kfbi_solve_info* infos, cudaStream_t st) {
   if (!B || !states || !g_next) return KFBI_ERR_ARG;
+  B->err.clear();
   for (int i = 0; i < B->n; ++i) {
     if (!states[i] || states[i]->dom != B->doms[i] || !states[i]->initialised || !g_next[i]) {
       B->err = "state i must be initialised on domain i and g_next[i] given";
@@ -1452,11 +1515,15 @@ kfbi_status kfbi_batch_step(kfbi_batch* B, kfbi_state* const* states, const void
     }
   }
   kfbi_status s = guarded(nullptr, [&]() -> kfbi_status {
-    cudaStream_t st = (cudaStream_t)stream;
     B->states.assign(states, states + B->n);
-    fill_instances(B, states, g_next, src_or_v);
+    fill_instances(B, states, g_next, src_or_v, src_scale);
     if (!B->bound) {
-      autotune(B, st);
+      if (!B->tuned) {
+        autotune(B, st);
+        B->tuned = true;
+      } else {
+        build_passes(B);
+      }
       capture_iteration(B);
       B->bound = true;
     } else {
@@ -1469,17 +1536,28 @@ kfbi_status kfbi_batch_step(kfbi_batch* B, kfbi_state* const* states, const void
     batch_accurate(B, 0, 1, 0, st);
     KFBI_LAUNCH_P(KFBI_PROF_GRID, gk_make_b, inst_grid((B->max_nb + 255) / 256, n), 256, 0, st,
                   B->d_inst);
+    // per-instance failures (non-finite, not converged) are reported in
+    // infos; every instance still completes its step so the batch stays
+    // consistent
     kfbi_status gs = batch_gmres(B, infos, st);
-    if (gs != KFBI_OK) return gs;
     set_active(B, all, nullptr, st);
     batch_accurate(B, 1, 1, 0, st);
     KFBI_LAUNCH_P(KFBI_PROF_GRID, gk_step_update, inst_grid(plane_blocks(B), n), 256, 0, st, B->d_inst);
     KFBI_CHECK_LAUNCH();
     KFBI_CUDA(cudaStreamSynchronize(st));
-    return KFBI_OK;
+    return gs;
   });
   if (s != KFBI_OK && B->err.empty()) B->err = kfbi_last_global_error();
   return s;
+}
+
+}  // namespace kfbi
+
+extern "C" {
+
+kfbi_status kfbi_batch_step(kfbi_batch* B, kfbi_state* const* states, const void* const* g_next,
+                            const double* const* src_or_v, kfbi_solve_info* infos, void* stream) {
+  return kfbi::batch_step(B, states, g_next, src_or_v, nullptr, infos, (cudaStream_t)stream);
 }
 
 kfbi_status kfbi_batch_tuning(const kfbi_batch* B, int* tile_order, double* us_natural,

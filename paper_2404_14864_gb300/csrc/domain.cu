@@ -280,7 +280,7 @@ static void free_domain(kfbi_domain* D) {
                   D->d_arm_beta, D->d_arm_fidx, D->d_arm_fcoef, D->d_node_gidx, D->d_node_w,
                   D->d_node_a, D->d_node_b, D->d_node_fidx, D->d_node_fcoef, D->d_arm_alpha32,
                   D->d_arm_beta32, D->d_arm_fcoef32, D->d_node_w32, D->d_node_a32,
-                  D->d_node_b32, D->d_node_fcoef32, D->d_S, D->d_lam, D->d_R, D->d_T, D->d_U,
+                  D->d_node_b32, D->d_node_fcoef32, D->d_R, D->d_T, D->d_U,
                   D->d_fpad, D->d_zero_nb};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -344,22 +344,12 @@ static void upload_domain(kfbi_domain* D, const Plan& P) {
     D->d_node_b32 = dev_upload(D, to_f32(nb_));
     D->d_node_fcoef32 = dev_upload(D, to_f32(P.node_fcoef));
   }
-  // DST-I matrix S[a][i] = sin(pi a i / M), a*i reduced mod 2M; eigenvalues
-  // lambda_a = -(4/h^2) sin^2(pi a / 2M) of the 1-D second difference.
-  std::vector<double> S(plane, 0.0), lam(Mp, 0.0);
-  const double pi = 3.14159265358979323846264338327950288;
-  for (int a = 1; a <= n1; ++a) {
-    for (int i = 1; i <= n1; ++i) {
-      const long long ai = ((long long)a * i) % (2LL * M);
-      S[(size_t)(a - 1) * Mp + (i - 1)] = std::sin(pi * (double)ai / (double)M);
-    }
-    const double s = std::sin(pi * (double)a / (2.0 * M));
-    lam[a - 1] = -(4.0 / (D->h * D->h)) * s * s;
-  }
-  D->d_S = dev_upload(D, S);
-  D->d_lam = dev_upload(D, lam);
+  // DST-I matrix and eigenvalues, shared with every domain on this grid
+  D->tables = dst_tables(M, Mp, D->h, D->desc.precision == KFBI_MIXED_TF32);
+  D->d_S = D->tables->S;
+  D->d_lam = D->tables->lam;
   D->d_R = dev_alloc<double>(D, 2 * plane);
-  D->d_T = dev_alloc<double>(D, 2 * plane);
+  if (D->desc.precision == KFBI_FP64) D->d_T = dev_alloc<double>(D, 2 * plane);
   D->d_U = dev_alloc<double>(D, 2 * plane);
   D->d_fpad = dev_alloc<double>(D, 2 * plane);
   D->d_zero_nb = dev_alloc<double>(D, 2 * (size_t)nb);
@@ -461,6 +451,48 @@ void unpad(kfbi_domain* D, const double* src, double* dst, bool C, cudaStream_t 
   KFBI_CHECK_LAUNCH();
 }
 
+kfbi_domain* domain_from_plan(const Plan& plan, cudaStream_t st) {
+  kfbi_domain* D = new kfbi_domain();
+  D->desc = plan.desc;
+  D->M = plan.M;
+  D->nb = plan.nb;
+  D->n1 = plan.n1;
+  D->Mp = ((plan.n1 + 127) / 128) * 128;
+  D->h = plan.h;
+  D->lo = plan.lo;
+  try {
+    KFBI_CUDA(cudaGetDevice(&D->device));
+    upload_domain(D, plan);
+    gmres_alloc(D);
+    if (plan.desc.precision == KFBI_MIXED_TF32) D->tc = tc_create(D, plan);
+    KFBI_CUDA(cudaStreamSynchronize(st));
+  } catch (...) {
+    free_domain(D);
+    throw;
+  }
+  return D;
+}
+
+// Mirrors upload_domain + gmres_alloc + tc_create (every table allocation
+// takes at least one element).
+long long domain_bytes_for(const Plan& P) {
+  auto n1 = [](size_t n) { return std::max<size_t>(1, n); };
+  const int Mp = ((P.n1 + 127) / 128) * 128;
+  const size_t plane = (size_t)Mp * Mp;
+  const bool mixed = P.desc.precision == KFBI_MIXED_TF32;
+  size_t b = n1(plane);                                                       // mask
+  b += sizeof(int) * (n1(P.irr.size()) + n1(P.arm_start.size()) + n1(P.arm_k0.size()) +
+                      n1(P.arm_fidx.size()) + n1(P.node_gidx.size()) + n1(P.node_fidx.size()));
+  const size_t dtab = 2 * n1(P.arm_alpha.size()) + n1(P.arm_fcoef.size()) +
+                      3 * n1(P.node_w.size()) + n1(P.node_fcoef.size());
+  b += sizeof(double) * dtab;
+  if (mixed) b += sizeof(float) * dtab;
+  b += sizeof(double) * (2 * plane * (mixed ? 3 : 4) + 2 * (size_t)P.nb);   // R, (T), U, fpad, zero_nb
+  long long total = (long long)b + gmres_bytes(P.desc.gmres_restart, P.nb);
+  if (mixed) total += tc_bytes_for(P, Mp);
+  return total;
+}
+
 }  // namespace kfbi
 
 using namespace kfbi;
@@ -490,28 +522,12 @@ kfbi_status kfbi_create_domain(const kfbi_domain_desc* desc, void* stream, kfbi_
     set_global_error(err);
     return s;
   }
-  kfbi_domain* D = new (std::nothrow) kfbi_domain();
-  if (!D) return KFBI_ERR_OOM;
-  D->desc = *desc;
-  D->M = plan.M;
-  D->nb = plan.nb;
-  D->n1 = plan.n1;
-  D->Mp = ((plan.n1 + 127) / 128) * 128;
-  D->h = plan.h;
-  D->lo = plan.lo;
-  cudaStream_t st = (cudaStream_t)stream;
+  kfbi_domain* D = nullptr;
   s = guarded(nullptr, [&]() -> kfbi_status {
-    KFBI_CUDA(cudaGetDevice(&D->device));
-    upload_domain(D, plan);
-    gmres_alloc(D);
-    if (desc->precision == KFBI_MIXED_TF32) D->tc = tc_create(D, plan);
-    KFBI_CUDA(cudaStreamSynchronize(st));
+    D = domain_from_plan(plan, (cudaStream_t)stream);
     return KFBI_OK;
   });
-  if (s != KFBI_OK) {
-    free_domain(D);
-    return s;
-  }
+  if (s != KFBI_OK) return s;
   *out = D;
   return KFBI_OK;
 }
@@ -606,6 +622,13 @@ kfbi_status kfbi_plan_create(const kfbi_domain_desc* desc, kfbi_plan** out) {
 }
 
 void kfbi_plan_destroy(kfbi_plan* plan) { delete plan; }
+
+long long kfbi_plan_device_bytes(const kfbi_plan* plan, int equation) {
+  if (!plan || equation < KFBI_HEAT || equation > KFBI_SCHRODINGER) return -1;
+  const Plan& P = plan->p;
+  const int Mp = ((P.n1 + 127) / 128) * 128;
+  return domain_bytes_for(P) + state_bytes_for(Mp, P.nb, equation);
+}
 
 long long kfbi_plan_size(const kfbi_plan* plan, int field) {
   if (!plan) return -1;

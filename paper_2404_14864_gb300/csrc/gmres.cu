@@ -329,6 +329,14 @@ void check_device_flags(kfbi_domain* D) {
                      std::to_string(flags) + ")"};
 }
 
+// Device bytes gmres_alloc takes for restart m and nb boundary nodes.
+long long gmres_bytes(int m, int nb) {
+  const size_t n = (size_t)(m + 1) * 2 * nb + 3 * 2 * (size_t)nb + (size_t)(m + 1) * m * 2 + m +
+                   2 * (size_t)m + 2 * (size_t)(m + 1) + 2 * 2 * (size_t)(m + 1) * GMAX +
+                   2 * (size_t)(m + 1) + 3 * 2 * (size_t)nb + 8;
+  return (long long)(n * sizeof(double));
+}
+
 void gmres_alloc(kfbi_domain* D) {
   const int m = D->desc.gmres_restart, nb = D->nb;
   D->restart = m;

@@ -7,6 +7,7 @@
 #include <cstdint>
 #include <new>
 #include <stdexcept>
+#include <memory>
 #include <string>
 
 #include "kfbi.h"
@@ -82,6 +83,23 @@ __host__ __device__ inline float tf32_round(float x) {
 
 struct TcDst;  // tensor-core DST engine (tc_dst.cu)
 
+// DST-I tables shared by every domain on the same grid (M, h), tables.cu:
+// S (Mp x Mp, zero padded) and the eigenvalues in FP64; for mixed domains
+// also the TF32 pair of S, an FP32 copy of S and FP32 eigenvalues.
+struct DstTables {
+  int M = 0, Mp = 0;
+  double h = 0;
+  double* S = nullptr;
+  double* lam = nullptr;
+  float* S_hi = nullptr;
+  float* S_lo = nullptr;
+  float* S32 = nullptr;
+  float* lam32 = nullptr;
+  long long bytes = 0;
+};
+std::shared_ptr<DstTables> dst_tables(int M, int Mp, double h, bool mixed);
+long long dst_tables_bytes();
+
 }  // namespace kfbi
 
 // Device-resident domain: tables from the plan and work buffers.
@@ -116,12 +134,13 @@ struct kfbi_domain {
   float* d_node_a32 = nullptr;
   float* d_node_b32 = nullptr;
   float* d_node_fcoef32 = nullptr;
-  double* d_S = nullptr;    // Mp*Mp DST-I matrix, zero padded
-  double* d_lam = nullptr;  // Mp eigenvalues (0 beyond n1)
+  std::shared_ptr<kfbi::DstTables> tables;  // shared per grid
+  double* d_S = nullptr;    // Mp*Mp DST-I matrix, zero padded (borrowed from tables)
+  double* d_lam = nullptr;  // Mp eigenvalues, 0 beyond n1 (borrowed from tables)
 
   // FP64 work buffers, two planes each (complex = re plane, im plane)
   double* d_R = nullptr;
-  double* d_T = nullptr;
+  double* d_T = nullptr;      // float64 domains only
   double* d_U = nullptr;
   double* d_fpad = nullptr;  // caller's f converted to the padded masked layout
   double* d_zero_nb = nullptr;  // 2*nb zeros (phi = 0)
@@ -164,6 +183,7 @@ struct kfbi_state {
   double* d_phi = nullptr;    // density, complex interleaved 2nb
   double* d_b = nullptr;      // BIE right-hand side, complex interleaved 2nb
   double* d_ub = nullptr;     // u+ of the volume part
+  long long bytes = 0;
 };
 
 namespace kfbi {
@@ -240,5 +260,25 @@ void tc_apply(kfbi_domain* D, double kre, double kim, const double* phi, int phi
 void tc_apply_accurate(kfbi_domain* D, double kre, double kim, const double* phi, int phi_stride,
                        const double* ft, double* out, int out_stride, cudaStream_t st);
 long long tc_bytes(const TcDst* tc);
+// Exact device bytes of what the allocation routines take for a plan: the
+// tensor-core buffers, the GMRES workspace, a whole domain (not counting the
+// shared DST tables) and one time-level state.
+long long tc_bytes_for(const Plan& P, int Mp);
+long long gmres_bytes(int m, int nb);
+long long domain_bytes_for(const Plan& P);
+long long state_bytes_for(int Mp, int nb, int equation);
+// A device domain from a built plan (throws Status); kfbi_create_domain
+// is build_plan followed by this.
+kfbi_domain* domain_from_plan(const Plan& plan, cudaStream_t st);
+
+// batch.cu, for the request server: a batch with no domains, (re)binding
+// it to a set of domains (keeps allocations that fit, drops the captured
+// graph; the autotuner's choice is kept), and a step whose heat source of
+// instance i is src_scale[i] * src[i] (src_scale NULL: 1).
+kfbi_batch* batch_new();
+void batch_bind(kfbi_batch* B, kfbi_domain* const* domains, int n);
+kfbi_status batch_step(kfbi_batch* B, kfbi_state* const* states, const void* const* g_next,
+                       const double* const* src_or_v, const double* src_scale,
+                       kfbi_solve_info* infos, cudaStream_t st);
 
 }  // namespace kfbi

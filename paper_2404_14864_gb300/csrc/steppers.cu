@@ -209,14 +209,18 @@ kfbi_status kfbi_state_create(kfbi_domain* dom, int equation, kfbi_state** out) 
   kfbi_status s = guarded(dom, [&]() -> kfbi_status {
     const size_t plane = (size_t)dom->Mp * dom->Mp * S->planes;
     const size_t nb2 = 2 * (size_t)dom->nb;
-    KFBI_CUDA(cudaMalloc(&S->d_u, plane * sizeof(double)));
-    KFBI_CUDA(cudaMalloc(&S->d_F, plane * sizeof(double)));
-    KFBI_CUDA(cudaMalloc(&S->d_ft, plane * sizeof(double)));
-    if (equation == KFBI_WAVE) KFBI_CUDA(cudaMalloc(&S->d_Fprev, plane * sizeof(double)));
-    if (equation == KFBI_SCHRODINGER) KFBI_CUDA(cudaMalloc(&S->d_aux, plane * sizeof(double)));
-    KFBI_CUDA(cudaMalloc(&S->d_phi, nb2 * sizeof(double)));
-    KFBI_CUDA(cudaMalloc(&S->d_b, nb2 * sizeof(double)));
-    KFBI_CUDA(cudaMalloc(&S->d_ub, nb2 * sizeof(double)));
+    auto alloc = [&](double** p, size_t n) {
+      KFBI_CUDA(cudaMalloc(p, n * sizeof(double)));
+      S->bytes += (long long)(n * sizeof(double));
+    };
+    alloc(&S->d_u, plane);
+    alloc(&S->d_F, plane);
+    alloc(&S->d_ft, plane);
+    if (equation == KFBI_WAVE) alloc(&S->d_Fprev, plane);
+    if (equation == KFBI_SCHRODINGER) alloc(&S->d_aux, plane);
+    alloc(&S->d_phi, nb2);
+    alloc(&S->d_b, nb2);
+    alloc(&S->d_ub, nb2);
     KFBI_CUDA(cudaMemset(S->d_phi, 0, nb2 * sizeof(double)));
     return KFBI_OK;
   });
@@ -227,6 +231,8 @@ kfbi_status kfbi_state_create(kfbi_domain* dom, int equation, kfbi_state** out) 
   *out = S;
   return KFBI_OK;
 }
+
+long long kfbi_state_device_bytes(const kfbi_state* st) { return st ? st->bytes : -1; }
 
 void kfbi_state_destroy(kfbi_state* S) {
   if (!S) return;
@@ -417,3 +423,14 @@ kfbi_status kfbi_state_get_phi(kfbi_state* S, void* phi_out, void* stream) {
 }
 
 }  // extern "C"
+
+namespace kfbi {
+
+long long state_bytes_for(int Mp, int nb, int equation) {
+  const int planes = equation == KFBI_SCHRODINGER ? 2 : 1;
+  const size_t plane = (size_t)Mp * Mp * planes;
+  const int fields = 3 + (equation != KFBI_HEAT ? 1 : 0);
+  return (long long)((fields * plane + 3 * 2 * (size_t)nb) * sizeof(double));
+}
+
+}  // namespace kfbi

@@ -720,10 +720,10 @@ TcDst* tc_create(kfbi_domain* D, const Plan& P) {
       KFBI_CUDA(cudaMalloc(p, n * sizeof(float)));
       T->bytes += (long long)(n * sizeof(float));
     };
-    alloc(&T->S_hi, plane);
-    alloc(&T->S_lo, plane);
-    alloc(&T->S32, plane);
-    alloc(&T->lam, D->Mp);
+    T->S_hi = D->tables->S_hi;  // borrowed, shared per grid
+    T->S_lo = D->tables->S_lo;
+    T->S32 = D->tables->S32;
+    T->lam = D->tables->lam32;
     alloc(&T->T1sh, 2 * plane);
     alloc(&T->T1sl, 2 * plane);
     alloc(&T->rv, 2 * (size_t)std::max(1, D->n_irr));
@@ -736,17 +736,6 @@ TcDst* tc_create(kfbi_domain* D, const Plan& P) {
     T->rhs_sparse_planes = 2;
     T->err = (int*)(D->d_scal + 6);
     KFBI_CUDA(cudaMemset(T->err, 0, sizeof(int)));
-    // TF32 pairs of S and FP32 eigenvalues from the FP64 device tables
-    std::vector<double> S(plane), lam(D->Mp);
-    KFBI_CUDA(cudaMemcpy(S.data(), D->d_S, plane * sizeof(double), cudaMemcpyDeviceToHost));
-    KFBI_CUDA(cudaMemcpy(lam.data(), D->d_lam, D->Mp * sizeof(double), cudaMemcpyDeviceToHost));
-    std::vector<float> sh(plane), sl(plane), l32(D->Mp), s32(plane);
-    for (size_t i = 0; i < plane; ++i) {
-      sh[i] = tf32_round((float)S[i]);
-      sl[i] = tf32_round((float)(S[i] - (double)sh[i]));
-      s32[i] = (float)S[i];
-    }
-    KFBI_CUDA(cudaMemcpy(T->S32, s32.data(), plane * sizeof(float), cudaMemcpyHostToDevice));
     // sparse route: rows of the right-hand side that hold irregular nodes
     // (the irregular list is sorted by row), the K-blocks they span in the
     // second pass and the output column tiles the extraction stencil reads
@@ -777,10 +766,6 @@ TcDst* tc_create(kfbi_domain* D, const Plan& P) {
       T->ct0 = imin / BN;
       T->nt3 = imax / BN + 1 - T->ct0;
     }
-    for (int i = 0; i < D->Mp; ++i) l32[i] = (float)lam[i];
-    KFBI_CUDA(cudaMemcpy(T->S_hi, sh.data(), plane * sizeof(float), cudaMemcpyHostToDevice));
-    KFBI_CUDA(cudaMemcpy(T->S_lo, sl.data(), plane * sizeof(float), cudaMemcpyHostToDevice));
-    KFBI_CUDA(cudaMemcpy(T->lam, l32.data(), D->Mp * sizeof(float), cudaMemcpyHostToDevice));
     const int Mp = D->Mp;
     make_map(&T->mS_hi, T->S_hi, Mp, Mp, BN);
     make_map(&T->mS_lo, T->S_lo, Mp, Mp, BN);
@@ -809,8 +794,7 @@ TcDst* tc_create(kfbi_domain* D, const Plan& P) {
 
 void tc_destroy(TcDst* T) {
   if (!T) return;
-  float* ptrs[] = {T->S_hi, T->S_lo, T->lam, T->S32, T->T1sh, T->T1sl, T->rv, T->Rh,
-                   T->Rl,   T->T1h,  T->T1l, T->T2h, T->T2l,  T->U};
+  float* ptrs[] = {T->T1sh, T->T1sl, T->rv, T->Rh, T->Rl, T->T1h, T->T1l, T->T2h, T->T2l, T->U};
   for (float* p : ptrs)
     if (p) cudaFree(p);
   if (T->row_start) cudaFree(T->row_start);
@@ -820,6 +804,18 @@ void tc_destroy(TcDst* T) {
 }
 
 long long tc_bytes(const TcDst* T) { return T ? T->bytes : 0; }
+
+// Device bytes tc_create takes for a plan on the padded size Mp.
+long long tc_bytes_for(const Plan& P, int Mp) {
+  const size_t plane = (size_t)Mp * Mp;
+  size_t n = 2 * 2 * plane + 2 * (size_t)std::max(1, P.n_irr()) + 7 * 2 * plane;
+  long long b = (long long)(n * sizeof(float));
+  if (P.n_irr() > 0) {
+    const int rows = P.irr.back() / P.n1 - P.irr.front() / P.n1 + 1;
+    b += (long long)((rows + 1 + P.n_irr()) * sizeof(int));
+  }
+  return b + (long long)(kNumMaps * sizeof(CUtensorMap));
+}
 
 // Descriptor of one instance's pass: A operand maps (am_hi, am_lo: kMap*
 // indices), output, mode, K-block range and output column-tile range.

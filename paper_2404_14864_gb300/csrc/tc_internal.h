@@ -54,6 +54,7 @@ enum { kMapS_hi, kMapS_lo, kMapR_hi, kMapR_lo, kMapT1_hi, kMapT1_lo, kMapT2_hi, 
 
 struct TcDst {
   int Mp = 0, n1 = 0;
+  // borrowed from the domain's shared DST tables
   float *S_hi = nullptr, *S_lo = nullptr, *lam = nullptr, *S32 = nullptr;
   // sparse route for right-hand sides supported on the irregular nodes
   float *T1sh = nullptr, *T1sl = nullptr, *rv = nullptr;

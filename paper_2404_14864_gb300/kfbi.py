@@ -59,6 +59,39 @@ class SolveInfo(ctypes.Structure):
                 "converged": bool(self.converged), "applications": self.applications}
 
 
+class ServerDesc(ctypes.Structure):
+    _fields_ = [("max_resident", ctypes.c_int), ("hbm_budget_bytes", ctypes.c_longlong),
+                ("hbm_reserve_bytes", ctypes.c_longlong), ("gmres_restart", ctypes.c_int),
+                ("plan_threads", ctypes.c_int)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("domain", DomainDesc), ("equation", ctypes.c_int), ("steps", ctypes.c_int),
+                ("dt", ctypes.c_double), ("theta", ctypes.c_double), ("arrival", ctypes.c_double),
+                ("u0", ctypes.c_void_p), ("lap_u0", ctypes.c_void_p), ("u1", ctypes.c_void_p),
+                ("lap_u1", ctypes.c_void_p), ("g", ctypes.c_void_p), ("src_init", ctypes.c_void_p),
+                ("src_profile", ctypes.c_void_p), ("src_coef", ctypes.c_void_p),
+                ("potential", ctypes.c_void_p), ("u_out", ctypes.c_void_p)]
+
+
+class RequestInfo(ctypes.Structure):
+    _fields_ = [("state", ctypes.c_int), ("status", ctypes.c_int), ("arrival", ctypes.c_double),
+                ("admitted", ctypes.c_double), ("finished", ctypes.c_double),
+                ("admit_tick", ctypes.c_int), ("finish_tick", ctypes.c_int),
+                ("steps_done", ctypes.c_int), ("max_iters", ctypes.c_int),
+                ("max_rel_residual", ctypes.c_double), ("device_bytes", ctypes.c_longlong)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("ticks", ctypes.c_int), ("admitted", ctypes.c_int), ("completed", ctypes.c_int),
+                ("failed", ctypes.c_int), ("busy_seconds", ctypes.c_double),
+                ("admit_seconds", ctypes.c_double), ("resident_ticks", ctypes.c_double),
+                ("peak_device_bytes", ctypes.c_longlong), ("h2d_bytes", ctypes.c_longlong),
+                ("d2h_bytes", ctypes.c_longlong), ("grid_point_steps", ctypes.c_double)]
+
+
+REQ_QUEUED, REQ_RESIDENT, REQ_DONE, REQ_FAILED = 0, 1, 2, 3
+
 _lib = None
 _VP = ctypes.c_void_p
 
@@ -94,6 +127,8 @@ def lib():
         "kfbi_last_global_error": (ctypes.c_char_p, []),
         "kfbi_launch_count": (ctypes.c_longlong, []),
         "kfbi_domain_device_bytes": (ctypes.c_longlong, [_VP]),
+        "kfbi_state_device_bytes": (ctypes.c_longlong, [_VP]),
+        "kfbi_table_cache_bytes": (ctypes.c_longlong, []),
         "kfbi_profile_enable": (None, [ctypes.c_int]),
         "kfbi_profile_reset": (None, []),
         "kfbi_profile_read": (S, [ctypes.c_int, ctypes.POINTER(ctypes.c_longlong),
@@ -111,6 +146,15 @@ def lib():
         "kfbi_plan_destroy": (None, [_VP]),
         "kfbi_plan_size": (ctypes.c_longlong, [_VP, ctypes.c_int]),
         "kfbi_plan_export": (S, [_VP, ctypes.c_int, _VP]),
+        "kfbi_plan_device_bytes": (ctypes.c_longlong, [_VP, ctypes.c_int]),
+        "kfbi_server_create": (S, [ctypes.POINTER(ServerDesc), _VP, ctypes.POINTER(_VP)]),
+        "kfbi_server_destroy": (None, [_VP]),
+        "kfbi_server_submit": (S, [_VP, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_int)]),
+        "kfbi_server_tick": (S, [_VP, ctypes.c_double, ctypes.POINTER(ctypes.c_int)]),
+        "kfbi_server_run": (S, [_VP, ctypes.c_double]),
+        "kfbi_server_request_info": (S, [_VP, ctypes.c_int, ctypes.POINTER(RequestInfo)]),
+        "kfbi_server_get_stats": (S, [_VP, ctypes.POINTER(ServerStats)]),
+        "kfbi_server_last_error": (ctypes.c_char_p, [_VP]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -291,6 +335,11 @@ class Domain:
         return kfbi_solve_density(self.h, kappa, b, phi, stream)
 
 
+def table_cache_bytes():
+    """Device bytes of the DST-I tables shared per grid."""
+    return int(lib().kfbi_table_cache_bytes())
+
+
 class State:
     """Owning wrapper of a kfbi_state (time-level fields of one equation)."""
 
@@ -351,6 +400,9 @@ class State:
         _check(lib().kfbi_state_get_u(self.h, _ptr(out), _stream(stream)), self.dom.h)
         return out.view(n1, n1)
 
+    def device_bytes(self):
+        return int(lib().kfbi_state_device_bytes(self.h))
+
     def get_phi(self, out=None, stream=None):
         import torch
         if out is None:
@@ -406,6 +458,107 @@ class Batch:
                 "us_largest_first": float(b.value)}
 
 
+class Server:
+    """Owning wrapper of a kfbi_server (continuous batching of requests).
+
+    Request data are host numpy arrays; the wrapper keeps them alive until
+    the request is done and returns the final field from ``result``."""
+
+    def __init__(self, max_resident=64, hbm_budget_bytes=0, hbm_reserve_bytes=4 << 30,
+                 restart=50, plan_threads=4, stream=None):
+        d = ServerDesc(int(max_resident), int(hbm_budget_bytes), int(hbm_reserve_bytes),
+                       int(restart), int(plan_threads))
+        h = ctypes.c_void_p()
+        _check(lib().kfbi_server_create(ctypes.byref(d), _stream(stream), ctypes.byref(h)))
+        self.h = h
+        self.restart = int(restart)
+        self._keep = {}
+        self._out = {}
+
+    def close(self):
+        if self.h:
+            lib().kfbi_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _raise(self, status):
+        msg = lib().kfbi_server_last_error(self.h) or b""
+        raise KfbiError(status, msg.decode())
+
+    def submit(self, desc_dict, equation, steps, dt, arrival, u0, lap_u0, g, theta=0.25, u1=None,
+               lap_u1=None, src_init=None, src_profile=None, src_coef=None, potential=None,
+               tol=1e-10, maxit=2000):
+        """Queue a request (grids (M-1, M-1); g (steps, nb)); returns its id."""
+        cplx = equation == KFBI_SCHRODINGER
+        gt = np.complex128 if cplx else np.float64
+
+        def arr(a, dt_=np.float64):
+            return None if a is None else np.ascontiguousarray(a, dtype=dt_)
+
+        keep = {"u0": arr(u0, gt), "lap_u0": arr(lap_u0, gt), "u1": arr(u1), "lap_u1": arr(lap_u1),
+                "g": arr(g, gt), "src_init": arr(src_init), "src_profile": arr(src_profile),
+                "src_coef": arr(src_coef), "potential": arr(potential)}
+        n1 = int(desc_dict["M"]) - 1
+        out = np.empty((n1, n1), dtype=gt)
+        if keep["g"].shape != (int(steps), int(desc_dict["nb"])):
+            raise ValueError("g must have shape (steps, nb)")
+
+        def p(a):
+            return None if a is None else ctypes.c_void_p(a.ctypes.data)
+
+        r = Request(make_desc(desc_dict, KFBI_MIXED_TF32, self.restart, tol, maxit), int(equation),
+                    int(steps), float(dt), float(theta), float(arrival), p(keep["u0"]),
+                    p(keep["lap_u0"]), p(keep["u1"]), p(keep["lap_u1"]), p(keep["g"]),
+                    p(keep["src_init"]), p(keep["src_profile"]), p(keep["src_coef"]),
+                    p(keep["potential"]), ctypes.c_void_p(out.ctypes.data))
+        i = ctypes.c_int()
+        status = lib().kfbi_server_submit(self.h, ctypes.byref(r), ctypes.byref(i))
+        if status != KFBI_OK:
+            self._raise(status)
+        self._keep[i.value] = keep
+        self._out[i.value] = out
+        return int(i.value)
+
+    def tick(self, now=-1.0):
+        """One tick at server time now (< 0: wall clock); returns how many stepped."""
+        n = ctypes.c_int()
+        status = lib().kfbi_server_tick(self.h, float(now), ctypes.byref(n))
+        if status != KFBI_OK:
+            self._raise(status)
+        return int(n.value)
+
+    def run(self, time_limit=0.0):
+        status = lib().kfbi_server_run(self.h, float(time_limit))
+        if status != KFBI_OK:
+            self._raise(status)
+
+    def info(self, i):
+        r = RequestInfo()
+        _check(lib().kfbi_server_request_info(self.h, int(i), ctypes.byref(r)))
+        d = {f: getattr(r, f) for f, _ in RequestInfo._fields_}
+        if d["state"] in (REQ_RESIDENT, REQ_DONE, REQ_FAILED):
+            k = self._keep.get(int(i))
+            if k is not None and d["state"] != REQ_RESIDENT:
+                self._keep.pop(int(i), None)
+        return d
+
+    def result(self, i):
+        """Final field of a completed request (None while it is not done)."""
+        if self.info(i)["state"] != REQ_DONE:
+            return None
+        return self._out[int(i)]
+
+    def stats(self):
+        st = ServerStats()
+        _check(lib().kfbi_server_get_stats(self.h, ctypes.byref(st)))
+        return {f: getattr(st, f) for f, _ in ServerStats._fields_}
+
+
 # ----------------------------------------------------------------------------
 # host-only plan (no GPU needed)
 # ----------------------------------------------------------------------------
@@ -414,10 +567,11 @@ class Batch:
 class Plan:
     """The geometry and coefficient tables kfbi_create_domain would upload."""
 
-    def __init__(self, desc_dict):
+    def __init__(self, desc_dict, precision=KFBI_FP64, restart=50):
         L = lib()
         h = ctypes.c_void_p()
-        _check(L.kfbi_plan_create(ctypes.byref(make_desc(desc_dict)), ctypes.byref(h)))
+        _check(L.kfbi_plan_create(ctypes.byref(make_desc(desc_dict, precision, restart)),
+                                  ctypes.byref(h)))
         self.h = h
         self.n_edges = int(L.kfbi_plan_size(h, 0))
         self.n_irregular = int(L.kfbi_plan_size(h, 7))
@@ -430,6 +584,10 @@ class Plan:
         a = np.zeros(max(n, 1), dtype=dt)
         _check(L.kfbi_plan_export(self.h, fid, a.ctypes.data_as(ctypes.c_void_p)))
         return a[:n]
+
+    def device_bytes(self, equation):
+        """Exact device bytes of a domain from this plan plus one state."""
+        return int(lib().kfbi_plan_device_bytes(self.h, int(equation)))
 
     def close(self):
         if self.h:

@@ -175,3 +175,52 @@ def served_requests(n=1000, rate=200.0, sizes=(128, 256, 512, 1024, 2048),
         st = int(rng.integers(steps[0], steps[1] + 1))
         out.append((t, kind, M, random_star(rng), st))
     return out
+
+
+# ----------------------------------------------------------------------------
+# Served requests: host inputs of one time-stepping request
+# ----------------------------------------------------------------------------
+
+KINDS = {"heat": 0, "wave": 1, "schrodinger": 2}   # kfbi_equation values
+STEP_OVER_H = {"heat": 1.0, "wave": 4.0, "schrodinger": 0.5}
+
+
+def request_inputs(kind, desc, steps, theta=0.5):
+    """Host inputs of a manufactured-solution request (the arguments of
+    ``kfbi.Server.submit`` besides the descriptor, arrival and tolerance).
+
+    heat: u = exp(-t) sin(pi x) cos(pi y) with its source, whose step sums
+    are src_coef[n] * profile (the source is exp(-t) times a profile);
+    wave: u = cos(sqrt 2 pi t) sin(pi x) sin(pi y), theta = 1/2 by default
+    (second order like 1/4, but its roots stay away from the double root
+    at -1 that makes theta = 1/4 grow on grids with a node very close to
+    the interface);
+    Schroedinger: plane wave k = (5, 0), V = 0.  "exact" gives the solution
+    at the request's final time on the interior grid."""
+    X, Y = grid_xy(desc)
+    zx, zy = boundary_xy(desc)
+    h = (desc["hi"] - desc["lo"]) / desc["M"]
+    dt = STEP_OVER_H[kind] * h
+    out = {"equation": KINDS[kind], "dt": dt, "steps": int(steps)}
+    if kind == "heat":
+        ex = HeatExact()
+        prof = ex.src(X, Y, 0.0)
+        out.update(u0=ex.u(X, Y, 0.0), lap_u0=ex.lap(X, Y, 0.0),
+                   src_init=ex.src(X, Y, 0.0) + ex.src(X, Y, dt), src_profile=prof,
+                   src_coef=np.array([math.exp(-(n + 1) * dt) + math.exp(-(n + 2) * dt)
+                                      for n in range(steps)]),
+                   g=np.stack([ex.u(zx, zy, (n + 1) * dt) for n in range(steps)]))
+        t_end = steps * dt
+    elif kind == "wave":
+        ex = WaveExact()
+        out.update(theta=float(theta), u0=ex.u(X, Y, 0.0), lap_u0=ex.lap(X, Y, 0.0), u1=ex.u(X, Y, dt),
+                   lap_u1=ex.lap(X, Y, dt),
+                   g=np.stack([ex.u(zx, zy, (n + 2) * dt) for n in range(steps)]))
+        t_end = (steps + 1) * dt
+    else:
+        ex = PlaneWaveExact(5.0, 0.0)
+        out.update(u0=ex.u(X, Y, 0.0), lap_u0=ex.lap(X, Y, 0.0), potential=np.zeros_like(X),
+                   g=np.stack([ex.u(zx, zy, (n + 1) * dt) for n in range(steps)]))
+        t_end = steps * dt
+    out["exact"] = lambda: ex.u(X, Y, t_end)
+    return out

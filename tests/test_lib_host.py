@@ -131,3 +131,71 @@ def test_plan_tables_reproduce_oracle_correction_and_extraction(built, desc, kap
     up_or = oracle.extraction(d, U, nj)
     up_pl = _plan_extract(p, desc, U, phi, kappa, Ft)
     assert np.abs(up_pl - up_or).max() <= 1e-11 * max(1.0, np.abs(up_or).max())
+
+
+def test_plan_device_bytes_on_the_host(built):
+    """The exact admission count is host-only: it grows with the padded grid
+    and the equation's fields, and rejects bad arguments."""
+    d = W.domain_desc(128, W.star())
+    p = kfbi.Plan(d, kfbi.KFBI_MIXED_TF32, 50)
+    heat, wave, schr = (p.device_bytes(e) for e in (kfbi.KFBI_HEAT, kfbi.KFBI_WAVE,
+                                                   kfbi.KFBI_SCHRODINGER))
+    Mp = 128
+    assert 0 < heat < wave < schr
+    assert wave - heat == Mp * Mp * 8           # F^n plane of the wave state
+    assert schr - heat == 5 * Mp * Mp * 8       # complex u, F, ft and u** planes
+    assert p.device_bytes(7) == -1
+    p.close()
+    p64 = kfbi.Plan(d, kfbi.KFBI_FP64, 50)
+    # the FP64 domain keeps a second FP64 work grid but no tensor-core planes
+    assert p64.device_bytes(kfbi.KFBI_HEAT) < heat
+    p64.close()
+    big = kfbi.Plan(W.domain_desc(512, W.star()), kfbi.KFBI_MIXED_TF32, 50)
+    ratio = big.device_bytes(kfbi.KFBI_HEAT) / heat
+    big.close()
+    assert 12.0 < ratio < 16.0                  # planes dominate: below (512/128)^2
+
+
+def test_served_request_stream_is_poisson_and_balanced():
+    reqs = W.served_requests(4000, rate=200.0, seed=0)
+    t = np.array([r[0] for r in reqs])
+    gaps = np.diff(np.concatenate([[0.0], t]))
+    assert np.all(gaps > 0)
+    assert abs(gaps.mean() - 1 / 200.0) < 0.1 / 200.0
+    assert abs(gaps.std() / gaps.mean() - 1.0) < 0.1   # exponential: cv = 1
+    kinds = [r[1] for r in reqs]
+    for k in ("heat", "wave", "schrodinger"):
+        assert abs(kinds.count(k) / len(kinds) - 1 / 3) < 0.04
+    assert set(r[2] for r in reqs) == {128, 256, 512, 1024, 2048}
+    steps = [r[4] for r in reqs]
+    assert min(steps) >= 20 and max(steps) <= 200
+    assert reqs[:3] == W.served_requests(3, rate=200.0, seed=0)  # seeded
+
+
+def test_request_inputs_shapes():
+    desc = W.domain_desc(64, W.star())
+    for kind in ("heat", "wave", "schrodinger"):
+        x = W.request_inputs(kind, desc, 5)
+        assert x["g"].shape == (5, 128)
+        assert x["u0"].shape == (63, 63)
+        assert x["exact"]().shape == (63, 63)
+    h = W.request_inputs("heat", desc, 5)
+    # the source sums are coefficient times profile (source = exp(-t) * profile)
+    ex = W.HeatExact()
+    X, Y = W.grid_xy(desc)
+    s2 = ex.src(X, Y, 2 * h["dt"]) + ex.src(X, Y, 3 * h["dt"])
+    assert np.allclose(h["src_coef"][1] * h["src_profile"], s2, rtol=1e-14, atol=1e-14)
+
+
+def test_binding_wrappers_expose_the_entry_points():
+    for cls, names in [(kfbi.Domain, ["apply_operator", "interface_solve", "solve_density",
+                                      "device_bytes"]),
+                       (kfbi.State, ["init_heat", "init_wave", "init_schrodinger", "step_heat",
+                                     "step_wave", "step_schrodinger", "get_u", "get_phi",
+                                     "device_bytes"]),
+                       (kfbi.Batch, ["step", "tuning"]),
+                       (kfbi.Server, ["submit", "tick", "run", "info", "result", "stats"]),
+                       (kfbi.Plan, ["field", "device_bytes"])]:
+        for n in names:
+            assert callable(getattr(cls, n, None)), (cls.__name__, n)
+    assert callable(kfbi.table_cache_bytes)
