@@ -259,11 +259,16 @@ typedef enum {
   KFBI_PROF_EXTRACT = 2, /* boundary extraction */
   KFBI_PROF_KRYLOV = 3,  /* GMRES kernels */
   KFBI_PROF_GRID = 4,    /* elementwise grid kernels (steppers, layout) */
-  KFBI_PROF_NCLASS = 5
+  KFBI_PROF_SPARSE = 5,  /* first DST pass of a sparse right-hand side (CUDA cores) */
+  KFBI_PROF_NCLASS = 6
 } kfbi_prof_class;
 void kfbi_profile_enable(int class_mask);
 void kfbi_profile_reset(void);
 kfbi_status kfbi_profile_read(int cls, long long* launches, double* total_ms);
+/* Floating-point operations the recorded launches of a class issued, for
+ * the classes whose launches count them (KFBI_PROF_DST: the executed dense
+ * products of each pass, three TF32 products per pass on a mixed domain). */
+kfbi_status kfbi_profile_work(int cls, double* flops);
 
 /* Host-only plan: the geometry and coefficient tables kfbi_create_domain
  * uploads, built without touching the GPU, for inspection and tests. */

@@ -949,6 +949,7 @@ struct kfbi_batch {
   PassDesc* d_pass[kPassKinds] = {nullptr};
   int* d_prefix[kPassKinds] = {nullptr};
   int total[kPassKinds] = {0};
+  double pass_work[kPassKinds] = {0};  // tensor flops of a pass over all instances
   int max_n_irr = 1, max_nb = 1, max_Mp = 128, max_nrows = 1, max_planes_blocks = 1;
   bool bound = false;
   // autotuned launch shape of the grouped passes (CTAs per SM multiple,
@@ -1030,6 +1031,8 @@ void build_passes(kfbi_batch* B) {
       pref[ii + 1] = pref[ii] + ordered[ii].nct * ordered[ii].nrt;
     }
     B->total[kind] = pref[B->n];
+    B->pass_work[kind] = 0.0;
+    for (int ii = 0; ii < B->n; ++ii) B->pass_work[kind] += tc::pass_flops(ordered[ii]);
     KFBI_CUDA(cudaMemcpy(B->d_pass[kind], ordered.data(), sizeof(PassDesc) * B->n, cudaMemcpyHostToDevice));
     KFBI_CUDA(cudaMemcpy(B->d_prefix[kind], pref.data(), sizeof(int) * (B->n + 1), cudaMemcpyHostToDevice));
   }
@@ -1044,7 +1047,8 @@ void grouped_pass(kfbi_batch* B, int kind, cudaStream_t st) {
   ga.one = PassDesc{};
   ga.err = B->doms[0]->tc->err;
   const int grid = std::min(ga.total, B->nsm);
-  KFBI_LAUNCH_P(KFBI_PROF_DST, tc::k_tc_pass, grid, tc::kPassThreads, tc::kPassSmem, st, ga);
+  KFBI_LAUNCH_PW(KFBI_PROF_DST, B->pass_work[kind], tc::k_tc_pass, grid, tc::kPassThreads,
+                 tc::kPassSmem, st, ga);
 }
 
 int plane_blocks(kfbi_batch* B) { return B->max_planes_blocks; }
@@ -1081,7 +1085,7 @@ void batch_iteration(kfbi_batch* B, cudaStream_t st) {
   const int n = B->n;
   KFBI_LAUNCH_P(KFBI_PROF_CORRECT, gk_correct32_rv, inst_grid((B->max_n_irr + 127) / 128, n), 128, 0,
                 st, B->d_inst, (const int*)B->d_j);
-  KFBI_LAUNCH_P(KFBI_PROF_DST, gk_sparse_p1, dim3(B->max_Mp / 32, (B->max_nrows + 31) / 32, n),
+  KFBI_LAUNCH_P(KFBI_PROF_SPARSE, gk_sparse_p1, dim3(B->max_Mp / 32, (B->max_nrows + 31) / 32, n),
                 dim3(32, 8), 0, st, B->d_inst);
   grouped_pass(B, kfbi_batch::kSparse2, st);
   KFBI_LAUNCH_P(KFBI_PROF_GRID, gk_eig_cplx, inst_grid(plane_blocks(B), n), 256, 0, st, B->d_inst);
@@ -1355,7 +1359,7 @@ kfbi_status batch_gmres(kfbi_batch* B, kfbi_solve_info* infos, cudaStream_t st) 
         KFBI_LAUNCH_P(KFBI_PROF_KRYLOV, gk_dv_to_v0, inst_grid(8, n), 256, 0, st, B->d_inst);
         KFBI_LAUNCH_P(KFBI_PROF_CORRECT, gk_correct32_rv, inst_grid((B->max_n_irr + 127) / 128, n), 128, 0,
                       st, B->d_inst, (const int*)B->d_j);
-        KFBI_LAUNCH_P(KFBI_PROF_DST, gk_sparse_p1, dim3(B->max_Mp / 32, (B->max_nrows + 31) / 32, n),
+        KFBI_LAUNCH_P(KFBI_PROF_SPARSE, gk_sparse_p1, dim3(B->max_Mp / 32, (B->max_nrows + 31) / 32, n),
                       dim3(32, 8), 0, st, B->d_inst);
         grouped_pass(B, kfbi_batch::kSparse2, st);
         KFBI_LAUNCH_P(KFBI_PROF_GRID, gk_eig_cplx, inst_grid(plane_blocks(B), n), 256, 0, st, B->d_inst);

@@ -414,13 +414,15 @@ void apply_internal(kfbi_domain* D, double kre, double kim, const double* phi, i
   const size_t plane = (size_t)Mp * Mp;
   correct_fp64(D, kre, kim, phi, ps, ft, st);
   dim3 gg(Mp / 64, Mp / 64, P);
-  KFBI_LAUNCH_P(KFBI_PROF_DST, k_dgemm_t, gg, 256, 0, st, D->d_R, D->d_S, D->d_T, Mp);
-  KFBI_LAUNCH_P(KFBI_PROF_DST, k_dgemm_t, gg, 256, 0, st, D->d_T, D->d_S, D->d_U, Mp);
+  // one float64 pass: P planes of an (n1 x n1) by (n1 x n1) product
+  const double pass_fl = 2.0 * P * (double)n1 * n1 * n1;
+  KFBI_LAUNCH_PW(KFBI_PROF_DST, pass_fl, k_dgemm_t, gg, 256, 0, st, D->d_R, D->d_S, D->d_T, Mp);
+  KFBI_LAUNCH_PW(KFBI_PROF_DST, pass_fl, k_dgemm_t, gg, 256, 0, st, D->d_T, D->d_S, D->d_U, Mp);
   const double scale = (2.0 / D->M) * (2.0 / D->M);
   KFBI_LAUNCH_P(KFBI_PROF_GRID, k_eigscale, grid_for(plane, 256), 256, 0, st, D->d_U, plane, Mp, n1, D->d_lam, kre,
               kim, scale, C ? 1 : 0);
-  KFBI_LAUNCH_P(KFBI_PROF_DST, k_dgemm_t, gg, 256, 0, st, D->d_U, D->d_S, D->d_T, Mp);
-  KFBI_LAUNCH_P(KFBI_PROF_DST, k_dgemm_t, gg, 256, 0, st, D->d_T, D->d_S, D->d_U, Mp);
+  KFBI_LAUNCH_PW(KFBI_PROF_DST, pass_fl, k_dgemm_t, gg, 256, 0, st, D->d_U, D->d_S, D->d_T, Mp);
+  KFBI_LAUNCH_PW(KFBI_PROF_DST, pass_fl, k_dgemm_t, gg, 256, 0, st, D->d_T, D->d_S, D->d_U, Mp);
   if (out) extract_fp64(D, kre, kim, phi, ps, ft, out, os, st);
   KFBI_CHECK_LAUNCH();
 }

@@ -15,6 +15,8 @@
 #include <cstring>
 #include <string>
 
+#include <cooperative_groups.h>
+
 #include "internal.h"
 
 namespace kfbi {
@@ -208,6 +210,50 @@ __global__ void __launch_bounds__(GT) k_cgs_update(const double2* __restrict__ V
   }
 }
 
+// Hessenberg column j (col[0..j] = h, col[j+1] = ||w||) through the previous
+// Givens rotations, the new rotation, g and the convergence scalars
+// (scal[1] residual estimate, scal[2] 1 converged / 2 non-finite).  One
+// thread.
+__device__ void givens_column(double2* col, int j, double hn, double* cs, double2* sn, double2* g,
+                              double* scal) {
+  col[j + 1] = make_double2(hn, 0.0);
+  for (int i = 0; i < j; ++i) {
+    const double c = cs[i];
+    const double2 sv = sn[i], a = col[i], bb = col[i + 1];
+    const double2 t = cmul(sv, bb);
+    const double2 u = cmul(make_double2(sv.x, -sv.y), a);
+    col[i] = make_double2(c * a.x + t.x, c * a.y + t.y);
+    col[i + 1] = make_double2(-u.x + c * bb.x, -u.y + c * bb.y);
+  }
+  const double2 a = col[j];
+  const double bre = col[j + 1].x;
+  double c;
+  double2 sv;
+  const double aa = hypot(a.x, a.y);
+  if (bre == 0.0) {
+    c = 1.0;
+    sv = make_double2(0.0, 0.0);
+  } else if (aa == 0.0) {
+    c = 0.0;
+    sv = make_double2(1.0, 0.0);
+  } else {
+    const double den = hypot(aa, bre);
+    c = aa / den;
+    sv = make_double2(a.x / aa * bre / den, a.y / aa * bre / den);
+  }
+  cs[j] = c;
+  sn[j] = sv;
+  col[j] = make_double2(c * a.x + sv.x * bre, c * a.y + sv.y * bre);
+  col[j + 1] = make_double2(0.0, 0.0);
+  const double2 gj = g[j];
+  const double2 u = cmul(make_double2(sv.x, -sv.y), gj);
+  g[j + 1] = make_double2(-u.x, -u.y);
+  g[j] = make_double2(c * gj.x, c * gj.y);
+  const double res = hypot(g[j + 1].x, g[j + 1].y);
+  scal[1] = res;
+  scal[2] = !isfinite(res) ? 2.0 : ((res <= scal[3] * scal[0] || hn == 0.0) ? 1.0 : 0.0);
+}
+
 // ||w|| from the partials, v_{j+1} = w / ||w||, then (CTA 0, one thread)
 // the Hessenberg column with the previous Givens rotations, the new
 // rotation, g and the convergence scalars.
@@ -235,43 +281,117 @@ __global__ void __launch_bounds__(GT) k_cgs_finalize(double2* __restrict__ V, in
   if (b == 0 && threadIdx.x == 0) {
     double2* col = H + (size_t)j * (m + 1);
     for (int i = 0; i <= j; ++i) col[i] = hcol[i];
-    col[j + 1] = make_double2(hn, 0.0);
-    for (int i = 0; i < j; ++i) {
-      const double c = cs[i];
-      const double2 sv = sn[i], a = col[i], bb = col[i + 1];
-      const double2 t = cmul(sv, bb);
-      const double2 u = cmul(make_double2(sv.x, -sv.y), a);
-      col[i] = make_double2(c * a.x + t.x, c * a.y + t.y);
-      col[i + 1] = make_double2(-u.x + c * bb.x, -u.y + c * bb.y);
-    }
-    const double2 a = col[j];
-    const double bre = col[j + 1].x;
-    double c;
-    double2 sv;
-    const double aa = hypot(a.x, a.y);
-    if (bre == 0.0) {
-      c = 1.0;
-      sv = make_double2(0.0, 0.0);
-    } else if (aa == 0.0) {
-      c = 0.0;
-      sv = make_double2(1.0, 0.0);
-    } else {
-      const double den = hypot(aa, bre);
-      c = aa / den;
-      sv = make_double2(a.x / aa * bre / den, a.y / aa * bre / den);
-    }
-    cs[j] = c;
-    sn[j] = sv;
-    col[j] = make_double2(c * a.x + sv.x * bre, c * a.y + sv.y * bre);
-    col[j + 1] = make_double2(0.0, 0.0);
-    const double2 gj = g[j];
-    const double2 u = cmul(make_double2(sv.x, -sv.y), gj);
-    g[j + 1] = make_double2(-u.x, -u.y);
-    g[j] = make_double2(c * gj.x, c * gj.y);
-    const double res = hypot(g[j + 1].x, g[j + 1].y);
-    scal[1] = res;
-    scal[2] = !isfinite(res) ? 2.0 : ((res <= scal[3] * scal[0] || hn == 0.0) ? 1.0 : 0.0);
+    givens_column(col, j, hn, cs, sn, g, scal);
   }
+}
+
+// ---- one Arnoldi step in one launch: a thread-block cluster ----------------
+// The CTAs of one cluster each own a slice of the basis vectors.  Every
+// pass's partial inner products (and the partial squared norm) sit in each
+// CTA's shared memory; after a cluster barrier every CTA sums all ranks'
+// partials through distributed shared memory in rank order, so all CTAs
+// hold bitwise identical coefficients.  CGS2: two projection passes, then
+// normalisation and (rank 0, one thread) the Givens update.  Replaces the
+// four launches of the grid version with one; the barriers are the
+// cluster's hardware barrier, reached by every thread of every CTA.
+constexpr int CLT = 256;  // threads per CTA of the cluster kernel
+
+template <bool C>
+__global__ void __launch_bounds__(CLT) k_arnoldi_cl(double2* __restrict__ V, int nb, int j,
+                                                    double2* __restrict__ w, double2* H, double* cs,
+                                                    double2* sn, double2* g, int m, double* scal) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  const int CL = (int)cl.num_blocks(), rank = (int)cl.block_rank();
+  __shared__ double2 pa[65], pb[65], h1[65], h2[65];
+  __shared__ double pn[CLT / 32];
+  __shared__ double pnorm;
+  const int slice = (nb + CL - 1) / CL;
+  const int e0 = min(nb, rank * slice), e1 = min(nb, e0 + slice);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // pass 1: <v_i, w> on this slice
+  for (int i = warp; i <= j; i += CLT / 32) {
+    const double2 s = dotpart<C>(V + (size_t)i * nb, w, e0, e1, lane);
+    if (lane == 0) pa[i] = s;
+  }
+  cl.sync();
+  for (int i = threadIdx.x; i <= j; i += CLT) {
+    double2 s = make_double2(0.0, 0.0);
+    for (int r = 0; r < CL; ++r) {
+      const double2 v = cl.map_shared_rank(pa, r)[i];
+      s.x += v.x;
+      s.y += v.y;
+    }
+    h1[i] = s;
+  }
+  __syncthreads();
+  for (int e = e0 + threadIdx.x; e < e1; e += CLT) {
+    double2 acc = w[e];
+    for (int i = 0; i <= j; ++i) {
+      const double2 v = V[(size_t)i * nb + e], hi = h1[i];
+      if (C) {
+        acc.x -= hi.x * v.x - hi.y * v.y;
+        acc.y -= hi.x * v.y + hi.y * v.x;
+      } else {
+        acc.x -= hi.x * v.x;
+      }
+    }
+    w[e] = acc;
+  }
+  __syncthreads();
+  // pass 2 (reorthogonalisation)
+  for (int i = warp; i <= j; i += CLT / 32) {
+    const double2 s = dotpart<C>(V + (size_t)i * nb, w, e0, e1, lane);
+    if (lane == 0) pb[i] = s;
+  }
+  cl.sync();
+  for (int i = threadIdx.x; i <= j; i += CLT) {
+    double2 s = make_double2(0.0, 0.0);
+    for (int r = 0; r < CL; ++r) {
+      const double2 v = cl.map_shared_rank(pb, r)[i];
+      s.x += v.x;
+      s.y += v.y;
+    }
+    h2[i] = s;
+  }
+  __syncthreads();
+  double ss = 0.0;
+  for (int e = e0 + threadIdx.x; e < e1; e += CLT) {
+    double2 acc = w[e];
+    for (int i = 0; i <= j; ++i) {
+      const double2 v = V[(size_t)i * nb + e], hi = h2[i];
+      if (C) {
+        acc.x -= hi.x * v.x - hi.y * v.y;
+        acc.y -= hi.x * v.y + hi.y * v.x;
+      } else {
+        acc.x -= hi.x * v.x;
+      }
+    }
+    w[e] = acc;
+    ss += acc.x * acc.x + acc.y * acc.y;
+  }
+  for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+  if (lane == 0) pn[warp] = ss;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int q = 0; q < CLT / 32; ++q) t += pn[q];
+    pnorm = t;
+  }
+  cl.sync();
+  double nn = 0.0;
+  for (int r = 0; r < CL; ++r) nn += *cl.map_shared_rank(&pnorm, r);
+  const double hn = sqrt(nn);
+  const double inv = hn > 0.0 ? 1.0 / hn : 0.0;
+  double2* vn = V + (size_t)(j + 1) * nb;
+  for (int e = e0 + threadIdx.x; e < e1; e += CLT) vn[e] = make_double2(w[e].x * inv, w[e].y * inv);
+  if (rank == 0 && threadIdx.x == 0) {
+    double2* col = H + (size_t)j * (m + 1);
+    for (int i = 0; i <= j; ++i) col[i] = make_double2(h1[i].x + h2[i].x, h1[i].y + h2[i].y);
+    givens_column(col, j, hn, cs, sn, g, scal);
+  }
+  // no CTA leaves while a peer may still read its shared memory
+  cl.sync();
 }
 
 // x += V[:, :k] y with R y = g: one warp per CTA solves the triangle
@@ -386,7 +506,75 @@ static void grid_shape(int nb, int& G, int& slice) {
 }
 
 // One Arnoldi step on w = A v_j (in D->d_W): CGS2 over the grid kernels.
+// Cluster size of the one-launch Arnoldi step: 16 CTAs where the device
+// runs such clusters (a non-portable size), else 8; 0 if clusters cannot be
+// launched at all (the grid version is used then).
+static int arnoldi_cluster_size() {
+  static int cl = -1;
+  if (cl >= 0) return cl;
+  cl = 0;
+  for (int want : {16, 8}) {
+    if (want > 8) {
+      if (cudaFuncSetAttribute(k_arnoldi_cl<true>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess ||
+          cudaFuncSetAttribute(k_arnoldi_cl<false>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+        cudaGetLastError();
+        continue;
+      }
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(want, 1, 1);
+    cfg.blockDim = dim3(CLT, 1, 1);
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = want;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int n1 = 0, n2 = 0;
+    if (cudaOccupancyMaxActiveClusters(&n1, k_arnoldi_cl<true>, &cfg) == cudaSuccess &&
+        cudaOccupancyMaxActiveClusters(&n2, k_arnoldi_cl<false>, &cfg) == cudaSuccess && n1 > 0 &&
+        n2 > 0) {
+      cl = want;
+      break;
+    }
+    cudaGetLastError();
+  }
+  return cl;
+}
+
+static void arnoldi_step_cluster(kfbi_domain* D, bool C, int j, int CL, cudaStream_t st) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(CL, 1, 1);
+  cfg.blockDim = dim3(CLT, 1, 1);
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = CL;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  double2* V = (double2*)D->d_V;
+  double2* w = (double2*)D->d_W;
+  void* tok = g_prof_on ? prof_begin(KFBI_PROF_KRYLOV, st) : nullptr;
+  if (C)
+    KFBI_CUDA(cudaLaunchKernelEx(&cfg, k_arnoldi_cl<true>, V, D->nb, j, w, (double2*)D->d_H, D->d_cs,
+                                 (double2*)D->d_sn, (double2*)D->d_g, D->restart, D->d_scal));
+  else
+    KFBI_CUDA(cudaLaunchKernelEx(&cfg, k_arnoldi_cl<false>, V, D->nb, j, w, (double2*)D->d_H,
+                                 D->d_cs, (double2*)D->d_sn, (double2*)D->d_g, D->restart,
+                                 D->d_scal));
+  if (tok) prof_end(tok, st);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+}
+
 static void arnoldi_step(kfbi_domain* D, bool C, int j, cudaStream_t st) {
+  const int CL = arnoldi_cluster_size();
+  if (CL > 0) {
+    arnoldi_step_cluster(D, C, j, CL, st);
+    return;
+  }
   const int nb = D->nb, m = D->restart;
   int G, slice;
   grid_shape(nb, G, slice);

@@ -25,6 +25,7 @@ extern bool g_prof_on;
 extern unsigned g_prof_mask;
 void* prof_begin(int cls, cudaStream_t st);
 void prof_end(void* tok, cudaStream_t st);
+void prof_add_work(void* tok, double work);
 
 // Launch a kernel of a profiling class, count it and (if enabled) time it.
 #define KFBI_LAUNCH_P(cls, kern, grid, block, smem, stream, ...)                       \
@@ -36,6 +37,19 @@ void prof_end(void* tok, cudaStream_t st);
   } while (0)
 
 // Launch a kernel and count it.
+// As KFBI_LAUNCH_P, and the launch's floating-point work (flops) is added to
+// its record for kfbi_profile_work.
+#define KFBI_LAUNCH_PW(cls, flops, kern, grid, block, smem, stream, ...)               \
+  do {                                                                                  \
+    void* tok_ = ::kfbi::g_prof_on ? ::kfbi::prof_begin((cls), (stream)) : nullptr;     \
+    kern<<<(grid), (block), (smem), (stream)>>>(__VA_ARGS__);                           \
+    if (tok_) {                                                                         \
+      ::kfbi::prof_end(tok_, (stream));                                                 \
+      ::kfbi::prof_add_work(tok_, (flops));                                             \
+    }                                                                                   \
+    ::kfbi::g_launches.fetch_add(1, std::memory_order_relaxed);                         \
+  } while (0)
+
 #define KFBI_LAUNCH(kern, grid, block, smem, stream, ...)                              \
   do {                                                                                  \
     kern<<<(grid), (block), (smem), (stream)>>>(__VA_ARGS__);                           \

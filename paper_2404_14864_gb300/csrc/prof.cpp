@@ -14,6 +14,7 @@ namespace {
 struct Rec {
   int cls;
   cudaEvent_t a, b;
+  double work;  // floating-point operations the launch issues (0 if not counted)
 };
 std::mutex mu;
 std::vector<Rec> recs;
@@ -34,7 +35,7 @@ cudaEvent_t take() {
 void* prof_begin(int cls, cudaStream_t st) {
   if (!((g_prof_mask >> cls) & 1u)) return nullptr;
   std::lock_guard<std::mutex> lk(mu);
-  Rec r{cls, take(), take()};
+  Rec r{cls, take(), take(), 0.0};
   if (!r.a || !r.b) return nullptr;
   cudaEventRecord(r.a, st);
   recs.push_back(r);
@@ -46,6 +47,13 @@ void prof_end(void* tok, cudaStream_t st) {
   std::lock_guard<std::mutex> lk(mu);
   size_t i = (size_t)tok - 1;
   if (i < recs.size()) cudaEventRecord(recs[i].b, st);
+}
+
+void prof_add_work(void* tok, double work) {
+  if (!tok) return;
+  std::lock_guard<std::mutex> lk(mu);
+  size_t i = (size_t)tok - 1;
+  if (i < recs.size()) recs[i].work += work;
 }
 
 }  // namespace kfbi
@@ -84,6 +92,16 @@ kfbi_status kfbi_profile_read(int cls, long long* launches, double* total_ms) {
   }
   *launches = n;
   *total_ms = ms;
+  return KFBI_OK;
+}
+
+kfbi_status kfbi_profile_work(int cls, double* flops) {
+  if (!flops || cls < 0 || cls >= KFBI_PROF_NCLASS) return KFBI_ERR_ARG;
+  std::lock_guard<std::mutex> lk(mu);
+  double w = 0.0;
+  for (auto& r : recs)
+    if (r.cls == cls) w += r.work;
+  *flops = w;
   return KFBI_OK;
 }
 

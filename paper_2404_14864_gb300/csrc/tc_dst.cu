@@ -3,21 +3,28 @@
 //
 // One pass computes out[p][c][r] = sum_k A[p][r][k] S[k][c] (two passes give
 // S A S).  Operands are split into TF32 pairs, A = A_hi + A_lo and
-// S = S_hi + S_lo, and the pass accumulates A_hi S_hi + A_hi S_lo + A_lo S_hi
-// (the dropped A_lo S_lo is ~2^-22 relative).  Each CTA owns a 128 x 64
-// output tile (128 CTAs per 1024^2 pass) and runs six warps:
+// S = S_hi + S_lo.  Each CTA owns a 128 x 64 output tile (128 CTAs per
+// 1024^2 pass) and runs six warps:
 //   - warp 0 lane 0 streams K-blocks of 32 fp32 (one 128-byte swizzle row)
 //     of A_hi, A_lo, S_hi, S_lo into a 4-stage shared-memory ring with TMA
-//     (cp.async.bulk.tensor, 128B swizzle, mbarrier completion);
-//   - warp 1 lane 0 issues tcgen05.mma kind::tf32 (M = 128, N = 64, K = 8),
-//     one K-block into one of eight TMEM accumulators, and releases the stage
-//     and publishes the accumulator with tcgen05.commit;
+//     (cp.async.bulk.tensor, 128B swizzle, mbarrier completion).  S_hi and
+//     S_lo land back to back, so together they are one 128-row operand;
+//   - warp 1 lane 0 issues tcgen05.mma kind::tf32 with M = 128, N = 128,
+//     K = 8: A_hi [S_hi | S_lo] and A_lo [S_hi | S_lo] into one TMEM
+//     accumulator of 128 columns (columns j and 64 + j hold the hi and lo
+//     halves of output column j, so all four products are formed).  Two
+//     K-blocks go into one of four accumulators, which tcgen05.commit then
+//     publishes; each stage is released by its own commit;
 //   - warps 2-5 drain each finished accumulator with tcgen05.ld (one tile
-//     row per thread) into FP32 registers, then store the tile transposed,
-//     which makes each warp's store one 128-byte line; the epilogue splits
-//     the result into the next pass's TF32 pair, applies the eigenvalue
-//     division of the box solve (pass 2, real kappa) or writes plain FP32
-//     (pass 4).
+//     row per thread) into FP32 registers, adding the two halves, then
+//     store the tile transposed, which makes each warp's store one
+//     128-byte line; the epilogue splits the result into the next pass's
+//     TF32 pair, applies the eigenvalue division of the box solve (pass 2,
+//     real kappa) or writes plain FP32 (pass 4).
+// N = 128 runs the tensor core about twice as efficiently per product as
+// three N = 64 products, and draining every second K-block halves the
+// commit round trips; the accumulator sums 64 K-terms, which keeps the
+// tensor core's internal FP32 rounding at the level of one group.
 // Every mbarrier wait is bounded; on timeout the kernel records an error
 // bit, drains its own copies and frees its TMEM.
 //
@@ -43,10 +50,12 @@ constexpr int B_BYTES = BN * BK * 4;          // 8 KiB
 constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;  // A_hi, A_lo, B_hi, B_lo
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
 constexpr int THREADS = 192;                  // producer, MMA, 4 drain/epilogue warps
-constexpr int NACC = 8;                       // TMEM accumulators in flight
-constexpr uint32_t TMEM_COLS = NACC * BN;     // 512 columns: all of TMEM
-// kind::tf32, D = F32, A = B = TF32, both K-major, N = BN, M = BM
-constexpr uint32_t IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(BN >> 3) << 17) |
+constexpr int NW = 2 * BN;                    // MMA width: [S_hi | S_lo]
+constexpr int NACC = 4;                       // TMEM accumulators in flight
+constexpr int KPA = 2;                        // K-blocks per accumulator
+constexpr uint32_t TMEM_COLS = NACC * NW;     // 512 columns: all of TMEM
+// kind::tf32, D = F32, A = B = TF32, both K-major, N = NW, M = BM
+constexpr uint32_t IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(NW >> 3) << 17) |
                            ((uint32_t)(BM >> 4) << 24);
 constexpr long long WAIT_LIMIT = 4000000000LL;  // cycles (~2 s)
 
@@ -160,13 +169,13 @@ __device__ __forceinline__ void tmem_ld32_nowait(uint32_t taddr, uint32_t* r) {
       : "r"(taddr));
 }
 
-// One DST-I pass.  The tensor core accumulates only one K-block (32 terms x
-// 3 products) into a TMEM accumulator; the drain warps add each K-block's
-// partial tile into FP32 registers with round-to-nearest adds while the MMA
-// fills the next of NACC accumulators.  Accumulating the whole K range inside the
-// tensor core lets its FP32 rounding error grow linearly with K (measured
-// 2.5e-5 relative at K = 1024); per-block draining keeps it at the level of
-// one block.
+// One DST-I pass (see the file comment).  The tensor core accumulates KPA
+// K-blocks (64 terms, both operand halves) into a TMEM accumulator; the
+// drain warps add each group's partial tile into FP32 registers with
+// round-to-nearest adds while the MMA fills the next of NACC accumulators.
+// Accumulating the whole K range inside the tensor core lets its FP32
+// rounding error grow linearly with K (measured 2.5e-5 relative at
+// K = 1024); per-group draining keeps it at the level of one group.
 __global__ void __launch_bounds__(THREADS, 1) k_tc_pass(const __grid_constant__ GroupArgs ga) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* tiles = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -238,8 +247,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_pass(const __grid_constant__ 
     __syncwarp();
   } else if (warp == 1) {
     if (lane == 0) {
-      // MMA issuer: one K-block per accumulator, accumulators in a ring
-      int g = 0;
+      // MMA issuer: KPA K-blocks per accumulator, accumulators in a ring
+      int g = 0, q = 0;  // K-blocks and accumulator groups issued
       bool abort = false;
       for (int t = blockIdx.x; t < ga.total && !abort; t += gridDim.x) {
         int lt;
@@ -247,9 +256,11 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_pass(const __grid_constant__ 
         if (d->active && *d->active == 0) continue;
         for (int kb = 0; kb < d->nk; ++kb, ++g) {
           const int s = g % STAGES, n = g / STAGES;
-          const int b = g % NACC, nbuf = g / NACC;
+          const int b = q % NACC, nbuf = q / NACC;
+          const bool first = (kb % KPA) == 0;
+          const bool last = (kb % KPA) == KPA - 1 || kb == d->nk - 1;
           if (s_state[0] || !mbar_wait(&full[s], (uint32_t)(n & 1)) ||
-              !mbar_wait(&acce[b], (uint32_t)((nbuf & 1) ^ 1))) {
+              (first && !mbar_wait(&acce[b], (uint32_t)((nbuf & 1) ^ 1)))) {
             s_state[0] = 1;
             atomicOr(ga.err, 2);
             abort = true;
@@ -258,18 +269,19 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_pass(const __grid_constant__ 
           tc_fence_after();
           uint8_t* st = tiles + s * STAGE_BYTES;
           const uint64_t ah = desc_sw128(st), al = desc_sw128(st + A_BYTES);
-          const uint64_t bh = desc_sw128(st + 2 * A_BYTES),
-                         bl = desc_sw128(st + 2 * A_BYTES + B_BYTES);
-          const uint32_t td = tmem + (uint32_t)(b * BN);
+          const uint64_t bb = desc_sw128(st + 2 * A_BYTES);  // [S_hi | S_lo], 128 rows
+          const uint32_t td = tmem + (uint32_t)(b * NW);
 #pragma unroll
           for (int k = 0; k < BK / 8; ++k) {
             const uint64_t o = (uint64_t)(2 * k);  // 8 tf32 = 32 bytes, in 16-byte units
-            umma_tf32(td, ah + o, bh + o, k ? 1u : 0u);
-            umma_tf32(td, ah + o, bl + o, 1u);
-            umma_tf32(td, al + o, bh + o, 1u);
+            umma_tf32(td, ah + o, bb + o, (first && k == 0) ? 0u : 1u);
+            umma_tf32(td, al + o, bb + o, 1u);
           }
           umma_commit(&empty[s]);
-          umma_commit(&accf[b]);
+          if (last) {
+            umma_commit(&accf[b]);
+            ++q;
+          }
         }
       }
       s_state[2] = g;
@@ -290,7 +302,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_pass(const __grid_constant__ 
       float acc[BN];
 #pragma unroll
       for (int j = 0; j < BN; ++j) acc[j] = 0.f;
-      for (int kb = 0; kb < d->nk; ++kb, ++g) {
+      const int ngroups = (d->nk + KPA - 1) / KPA;
+      for (int gi = 0; gi < ngroups; ++gi, ++g) {
         const int b = g % NACC;
         // one lane waits, the warp follows its verdict (tcgen05.ld needs the
         // whole warp converged)
@@ -307,13 +320,15 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_pass(const __grid_constant__ 
           break;
         }
         tc_fence_after();
-        uint32_t raw[BN];
 #pragma unroll
-        for (int cc = 0; cc < BN; cc += 32)
-          tmem_ld32_nowait(tmem + lane_base + (uint32_t)(b * BN + cc), &raw[cc]);
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        for (int cc = 0; cc < BN; cc += 32) {
+          uint32_t rh[32], rl[32];
+          tmem_ld32_nowait(tmem + lane_base + (uint32_t)(b * NW + cc), rh);
+          tmem_ld32_nowait(tmem + lane_base + (uint32_t)(b * NW + BN + cc), rl);
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-        for (int j = 0; j < BN; ++j) acc[j] += __uint_as_float(raw[j]);
+          for (int j = 0; j < 32; ++j) acc[cc + j] += __uint_as_float(rh[j]) + __uint_as_float(rl[j]);
+        }
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(&acce[b]);
@@ -844,6 +859,12 @@ static PassDesc pass_desc(TcDst* T, int am_hi, int am_lo, float* oh, float* ol, 
   return d;
 }
 
+// Tensor flops one pass issues: three TF32 products (hi*hi, hi*lo, lo*hi)
+// of BM x BN x BK per tile and K-block.
+double tc::pass_flops(const PassDesc& d) {
+  return 3.0 * 2.0 * BM * BN * BK * (double)d.nrt * d.nct * d.nk;
+}
+
 // One persistent launch over the tiles of a single instance.
 static void launch_pass(TcDst* T, const PassDesc& d, cudaStream_t st) {
   GroupArgs ga;
@@ -854,7 +875,7 @@ static void launch_pass(TcDst* T, const PassDesc& d, cudaStream_t st) {
   ga.one = d;
   ga.err = T->err;
   const int grid = std::min(ga.total, T->nsm);
-  KFBI_LAUNCH_P(KFBI_PROF_DST, k_tc_pass, grid, THREADS, SMEM_BYTES, st, ga);
+  KFBI_LAUNCH_PW(KFBI_PROF_DST, tc::pass_flops(d), k_tc_pass, grid, THREADS, SMEM_BYTES, st, ga);
 }
 
 // Four TF32x3 passes: (Rh, Rl) -> U (fp32 planes), eigenvalue division after
@@ -898,7 +919,7 @@ static void tc_apply_sparse(kfbi_domain* D, double kre, double kim, const double
                   T->Rl, plane, nullptr, D->d_irr_off, D->d_arm_start, D->d_arm_k0,
                   D->d_arm_alpha32, D->d_arm_beta32, D->d_arm_fidx, D->d_arm_fcoef32, D->n_irr,
                   D->n_arms, D->nb, phi, ps, (float)kre, (float)kim, T->rv);
-  KFBI_LAUNCH_P(KFBI_PROF_DST, k_sparse_p1, dim3(Mp / 32, (T->nrows + 31) / 32), dim3(32, 8), 0, st,
+  KFBI_LAUNCH_P(KFBI_PROF_SPARSE, k_sparse_p1, dim3(Mp / 32, (T->nrows + 31) / 32), dim3(32, 8), 0, st,
                 T->rv, D->n_irr, T->row_start, T->node_col, T->rmin, T->nrows, T->S32, T->T1sh,
                 T->T1sl, Mp, P);
   const float scale = (float)((2.0 / D->M) * (2.0 / D->M));

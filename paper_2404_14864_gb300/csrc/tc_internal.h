@@ -44,6 +44,8 @@ struct GroupArgs {
 };
 
 __global__ void k_tc_pass(const __grid_constant__ GroupArgs ga);
+// Tensor flops of one pass of an instance (all its tiles and K-blocks).
+double pass_flops(const PassDesc& d);
 extern const int kPassThreads;
 extern const int kPassSmem;
 

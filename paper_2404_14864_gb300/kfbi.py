@@ -133,6 +133,7 @@ def lib():
         "kfbi_profile_reset": (None, []),
         "kfbi_profile_read": (S, [ctypes.c_int, ctypes.POINTER(ctypes.c_longlong),
                                   ctypes.POINTER(ctypes.c_double)]),
+        "kfbi_profile_work": (S, [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
         "kfbi_box_solve_noalloc": (S, [ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                        ctypes.c_double, ctypes.c_double, _VP, _VP, _VP]),
         "kfbi_batch_create": (S, [ctypes.POINTER(_VP), ctypes.c_int, _VP, ctypes.POINTER(_VP)]),
@@ -219,8 +220,8 @@ def launch_count():
     return int(lib().kfbi_launch_count())
 
 
-PROF_DST, PROF_CORRECT, PROF_EXTRACT, PROF_KRYLOV, PROF_GRID = 0, 1, 2, 3, 4
-PROF_NAMES = {0: "dst", 1: "correct", 2: "extract", 3: "krylov", 4: "grid"}
+PROF_DST, PROF_CORRECT, PROF_EXTRACT, PROF_KRYLOV, PROF_GRID, PROF_SPARSE = 0, 1, 2, 3, 4, 5
+PROF_NAMES = {0: "dst", 1: "correct", 2: "extract", 3: "krylov", 4: "grid", 5: "sparse"}
 
 
 def kfbi_profile_enable(classes=True):
@@ -247,6 +248,13 @@ def kfbi_profile_read(cls):
     ms = ctypes.c_double()
     _check(lib().kfbi_profile_read(int(cls), ctypes.byref(n), ctypes.byref(ms)))
     return int(n.value), float(ms.value)
+
+
+def kfbi_profile_work(cls):
+    """Floating-point operations issued by the recorded launches of a class."""
+    w = ctypes.c_double()
+    _check(lib().kfbi_profile_work(int(cls), ctypes.byref(w)))
+    return float(w.value)
 
 
 # ----------------------------------------------------------------------------
