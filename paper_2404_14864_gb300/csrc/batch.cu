@@ -955,6 +955,7 @@ struct kfbi_batch {
   // autotuned launch shape of the grouped passes (CTAs per SM multiple,
   // tile order) and the CUDA graph of one lockstep GMRES iteration
   int tile_order = 0;  // 0: instances in given order, 1: largest first
+  int splitk = 0;      // grouped passes: 0 from the tile count, 1, or 2 (CTA pairs)
   bool tuned = false;  // the autotuner ran (its choice is kept across rebinds)
   cudaGraphExec_t iter_graph = nullptr;
   cudaStream_t graph_stream = nullptr;
@@ -987,8 +988,8 @@ void build_passes(kfbi_batch* B) {
       d.kb0 = 0;
       d.nk = T->Mp / tc::BK;
       d.ct0 = 0;
-      d.nct = T->Mp / tc::BN;
-      d.nrt = P * T->Mp / tc::BM;
+      d.nct = T->Mp / tc::BC;
+      d.nrt = P * T->Mp / tc::BR;
       d.kre = 0.f;
       d.scale = 0.f;
       d.active = B->d_flags + 4 * i;
@@ -1046,9 +1047,8 @@ void grouped_pass(kfbi_batch* B, int kind, cudaStream_t st) {
   ga.total = B->total[kind];
   ga.one = PassDesc{};
   ga.err = B->doms[0]->tc->err;
-  const int grid = std::min(ga.total, B->nsm);
-  KFBI_LAUNCH_PW(KFBI_PROF_DST, B->pass_work[kind], tc::k_tc_pass, grid, tc::kPassThreads,
-                 tc::kPassSmem, st, ga);
+  ga.splitk = B->splitk;
+  tc::launch_tc_pass(ga, B->nsm, B->pass_work[kind], st);
 }
 
 int plane_blocks(kfbi_batch* B) { return B->max_planes_blocks; }

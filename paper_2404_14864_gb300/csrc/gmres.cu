@@ -254,6 +254,42 @@ __device__ void givens_column(double2* col, int j, double hn, double* cs, double
   scal[2] = !isfinite(res) ? 2.0 : ((res <= scal[3] * scal[0] || hn == 0.0) ? 1.0 : 0.0);
 }
 
+// The same for a real problem (every h, sn and g real): real arithmetic
+// only, which halves the dependent FP64 chain of each rotation.
+__device__ void givens_column_real(double2* col, int j, double hn, double* cs, double2* sn,
+                                   double2* g, double* scal) {
+  double carry = col[0].x;
+  for (int i = 0; i < j; ++i) {
+    const double c = cs[i], sv = sn[i].x, b = col[i + 1].x;
+    col[i] = make_double2(c * carry + sv * b, 0.0);
+    carry = -sv * carry + c * b;
+  }
+  const double a = carry, bre = hn;
+  double c, sv;
+  const double aa = fabs(a);
+  if (bre == 0.0) {
+    c = 1.0;
+    sv = 0.0;
+  } else if (aa == 0.0) {
+    c = 0.0;
+    sv = 1.0;
+  } else {
+    const double den = hypot(aa, bre);
+    c = aa / den;
+    sv = (a < 0.0 ? -1.0 : 1.0) * bre / den;
+  }
+  cs[j] = c;
+  sn[j] = make_double2(sv, 0.0);
+  col[j] = make_double2(c * a + sv * bre, 0.0);
+  col[j + 1] = make_double2(0.0, 0.0);
+  const double gj = g[j].x;
+  g[j + 1] = make_double2(-sv * gj, 0.0);
+  g[j] = make_double2(c * gj, 0.0);
+  const double res = fabs(sv * gj);
+  scal[1] = res;
+  scal[2] = !isfinite(res) ? 2.0 : ((res <= scal[3] * scal[0] || hn == 0.0) ? 1.0 : 0.0);
+}
+
 // ||w|| from the partials, v_{j+1} = w / ||w||, then (CTA 0, one thread)
 // the Hessenberg column with the previous Givens rotations, the new
 // rotation, g and the convergence scalars.
@@ -286,7 +322,8 @@ __global__ void __launch_bounds__(GT) k_cgs_finalize(double2* __restrict__ V, in
 }
 
 // ---- one Arnoldi step in one launch: a thread-block cluster ----------------
-// The CTAs of one cluster each own a slice of the basis vectors.  Every
+// The CTAs of one cluster each own a slice of the basis vectors, staged once
+// into shared memory (when it fits) because every phase reads it.  Every
 // pass's partial inner products (and the partial squared norm) sit in each
 // CTA's shared memory; after a cluster barrier every CTA sums all ranks'
 // partials through distributed shared memory in rank order, so all CTAs
@@ -294,101 +331,246 @@ __global__ void __launch_bounds__(GT) k_cgs_finalize(double2* __restrict__ V, in
 // normalisation and (rank 0, one thread) the Givens update.  Replaces the
 // four launches of the grid version with one; the barriers are the
 // cluster's hardware barrier, reached by every thread of every CTA.
-constexpr int CLT = 256;  // threads per CTA of the cluster kernel
+constexpr int CLT = 256;                 // threads per CTA of the cluster kernel
+constexpr int CL_MAX = 16;               // largest cluster
+constexpr int VS_CAP = 200 * 1024;       // shared-memory cap of the staged basis slice
+
+// Partial inner products <v_i, w>, i = 0..j, on a slice.  GB300 issues
+// few FP64 instructions per clock, so the layout minimises them: groups of
+// 8 lanes own one inner product (four per warp), each lane sums every 8th
+// element with two accumulators, and three shuffle steps finish the group.
+template <bool C>
+__device__ __forceinline__ void slice_dots(const double2* __restrict__ Vb, int ld,
+                                           const double2* __restrict__ ws, int ns, int j,
+                                           double2* out, int warp, int lane) {
+  constexpr int NWARP = CLT / 32;
+  const int grp = lane >> 3, sub = lane & 7;
+  for (int base = warp * 4; base <= j; base += NWARP * 4) {
+    const int i = base + grp;
+    const bool live = i <= j;
+    double2 s0 = make_double2(0.0, 0.0), s1 = make_double2(0.0, 0.0);
+    if (live) {
+      const double2* vr = Vb + (size_t)i * ld;
+      int q = sub;
+      for (; q + 8 < ns; q += 16) {
+        const double2 x0 = vr[q], y0 = ws[q], x1 = vr[q + 8], y1 = ws[q + 8];
+        if (C) {
+          s0.x += x0.x * y0.x + x0.y * y0.y;
+          s0.y += x0.x * y0.y - x0.y * y0.x;
+          s1.x += x1.x * y1.x + x1.y * y1.y;
+          s1.y += x1.x * y1.y - x1.y * y1.x;
+        } else {
+          s0.x += x0.x * y0.x;
+          s1.x += x1.x * y1.x;
+        }
+      }
+      if (q < ns) {
+        const double2 x0 = vr[q], y0 = ws[q];
+        if (C) {
+          s0.x += x0.x * y0.x + x0.y * y0.y;
+          s0.y += x0.x * y0.y - x0.y * y0.x;
+        } else {
+          s0.x += x0.x * y0.x;
+        }
+      }
+      s0.x += s1.x;
+      if (C) s0.y += s1.y;
+    }
+#pragma unroll
+    for (int o = 4; o > 0; o >>= 1) {
+      s0.x += __shfl_xor_sync(0xffffffffu, s0.x, o);
+      if (C) s0.y += __shfl_xor_sync(0xffffffffu, s0.y, o);
+    }
+    if (live && sub == 0) out[i] = s0;
+  }
+}
+
+// Sum of entry i over the cluster's ranks, as a fixed pairwise tree (the
+// same value in every CTA).
+template <bool C>
+__device__ __forceinline__ double2 cl_sum(cooperative_groups::cluster_group& cl, double2* buf,
+                                          int i, int CL) {
+  double2 v[CL_MAX];
+#pragma unroll
+  for (int r = 0; r < CL_MAX; ++r)
+    v[r] = r < CL ? cl.map_shared_rank(buf, r)[i] : make_double2(0.0, 0.0);
+#pragma unroll
+  for (int w = 1; w < CL_MAX; w <<= 1)
+#pragma unroll
+    for (int r = 0; r + w < CL_MAX; r += 2 * w) {
+      v[r].x += v[r + w].x;
+      if (C) v[r].y += v[r + w].y;
+    }
+  return v[0];
+}
+
+// Sum over i in {i0, i0 + step, ...} <= j of h_i V[i][e] with two
+// accumulators (i0, i0 + 2 step, ... and i0 + step, i0 + 3 step, ...)
+// added at the end.
+template <bool C>
+__device__ __forceinline__ double2 hv_sum(const double2* __restrict__ Vb, int ld, int e, int j,
+                                          const double2* h, int i0, int step) {
+  double2 a0 = make_double2(0.0, 0.0), a1 = make_double2(0.0, 0.0);
+  int i = i0;
+  for (; i + step <= j; i += 2 * step) {
+    const double2 v0 = Vb[(size_t)i * ld + e], g0 = h[i];
+    const double2 v1 = Vb[(size_t)(i + step) * ld + e], g1 = h[i + step];
+    if (C) {
+      a0.x += g0.x * v0.x - g0.y * v0.y;
+      a0.y += g0.x * v0.y + g0.y * v0.x;
+      a1.x += g1.x * v1.x - g1.y * v1.y;
+      a1.y += g1.x * v1.y + g1.y * v1.x;
+    } else {
+      a0.x += g0.x * v0.x;
+      a1.x += g1.x * v1.x;
+    }
+  }
+  if (i <= j) {
+    const double2 v0 = Vb[(size_t)i * ld + e], g0 = h[i];
+    if (C) {
+      a0.x += g0.x * v0.x - g0.y * v0.y;
+      a0.y += g0.x * v0.y + g0.y * v0.x;
+    } else {
+      a0.x += g0.x * v0.x;
+    }
+  }
+  return make_double2(a0.x + a1.x, a0.y + a1.y);
+}
+
+// w -= V h on a slice.  When the slice has at most CLT / 2 elements two
+// threads share an element (even and odd i), combined in a fixed order;
+// every thread of the CTA reaches both barriers.
+template <bool C>
+__device__ __forceinline__ void slice_update(const double2* __restrict__ Vb, int ld,
+                                             double2* __restrict__ ws, int ns, int j,
+                                             const double2* h, double2* tmp) {
+  const int t = threadIdx.x;
+  if (2 * ns <= CLT) {
+    const int par = t < ns ? 0 : 1;
+    const int e = par ? t - ns : t;
+    const bool mine = t < 2 * ns;
+    double2 a = make_double2(0.0, 0.0);
+    if (mine) a = hv_sum<C>(Vb, ld, e, j, h, par, 2);
+    if (mine && par == 1) tmp[e] = a;
+    __syncthreads();
+    if (mine && par == 0) {
+      const double2 o = tmp[e];
+      ws[e] = make_double2(ws[e].x - (a.x + o.x), ws[e].y - (a.y + o.y));
+    }
+    __syncthreads();
+  } else {
+    for (int e = t; e < ns; e += CLT) {
+      const double2 a = hv_sum<C>(Vb, ld, e, j, h, 0, 1);
+      ws[e] = make_double2(ws[e].x - a.x, ws[e].y - a.y);
+    }
+    __syncthreads();
+  }
+}
 
 template <bool C>
 __global__ void __launch_bounds__(CLT) k_arnoldi_cl(double2* __restrict__ V, int nb, int j,
                                                     double2* __restrict__ w, double2* H, double* cs,
-                                                    double2* sn, double2* g, int m, double* scal) {
+                                                    double2* sn, double2* g, int m, double* scal,
+                                                    int cached) {
   namespace cg = cooperative_groups;
   cg::cluster_group cl = cg::this_cluster();
+  extern __shared__ double2 vs[];  // staged basis slice, [i][e - e0]
   const int CL = (int)cl.num_blocks(), rank = (int)cl.block_rank();
-  __shared__ double2 pa[65], pb[65], h1[65], h2[65];
+  __shared__ double2 pa[65], pb[65], h1[65], h2[65], tmp[CLT], gcol[66], gsn[65], gg[66];
+  __shared__ double gcs[65];
   __shared__ double pn[CLT / 32];
   __shared__ double pnorm;
   const int slice = (nb + CL - 1) / CL;
-  const int e0 = min(nb, rank * slice), e1 = min(nb, e0 + slice);
+  const int e0 = min(nb, rank * slice), e1 = min(nb, e0 + slice), ns = e1 - e0;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const double2* Vb;  // row i of this slice at Vb + i * ld
+  int ld;
+  if (cached) {
+    for (int q = threadIdx.x; q < (j + 1) * ns; q += CLT) {
+      const int i = q / ns, e = q - i * ns;
+      vs[i * slice + e] = V[(size_t)i * nb + e0 + e];
+    }
+    __syncthreads();
+    Vb = vs;
+    ld = slice;
+  } else {
+    Vb = V + e0;
+    ld = nb;
+  }
+  double2* ws = w + e0;
   // pass 1: <v_i, w> on this slice
-  for (int i = warp; i <= j; i += CLT / 32) {
-    const double2 s = dotpart<C>(V + (size_t)i * nb, w, e0, e1, lane);
-    if (lane == 0) pa[i] = s;
-  }
+  slice_dots<C>(Vb, ld, ws, ns, j, pa, warp, lane);
   cl.sync();
-  for (int i = threadIdx.x; i <= j; i += CLT) {
-    double2 s = make_double2(0.0, 0.0);
-    for (int r = 0; r < CL; ++r) {
-      const double2 v = cl.map_shared_rank(pa, r)[i];
-      s.x += v.x;
-      s.y += v.y;
-    }
-    h1[i] = s;
-  }
+  for (int i = threadIdx.x; i <= j; i += CLT) h1[i] = cl_sum<C>(cl, pa, i, CL);
   __syncthreads();
-  for (int e = e0 + threadIdx.x; e < e1; e += CLT) {
-    double2 acc = w[e];
-    for (int i = 0; i <= j; ++i) {
-      const double2 v = V[(size_t)i * nb + e], hi = h1[i];
-      if (C) {
-        acc.x -= hi.x * v.x - hi.y * v.y;
-        acc.y -= hi.x * v.y + hi.y * v.x;
-      } else {
-        acc.x -= hi.x * v.x;
-      }
-    }
-    w[e] = acc;
-  }
+  slice_update<C>(Vb, ld, ws, ns, j, h1, tmp);
   __syncthreads();
   // pass 2 (reorthogonalisation)
-  for (int i = warp; i <= j; i += CLT / 32) {
-    const double2 s = dotpart<C>(V + (size_t)i * nb, w, e0, e1, lane);
-    if (lane == 0) pb[i] = s;
-  }
+  slice_dots<C>(Vb, ld, ws, ns, j, pb, warp, lane);
   cl.sync();
-  for (int i = threadIdx.x; i <= j; i += CLT) {
-    double2 s = make_double2(0.0, 0.0);
-    for (int r = 0; r < CL; ++r) {
-      const double2 v = cl.map_shared_rank(pb, r)[i];
-      s.x += v.x;
-      s.y += v.y;
-    }
-    h2[i] = s;
-  }
+  for (int i = threadIdx.x; i <= j; i += CLT) h2[i] = cl_sum<C>(cl, pb, i, CL);
+  __syncthreads();
+  slice_update<C>(Vb, ld, ws, ns, j, h2, tmp);
   __syncthreads();
   double ss = 0.0;
-  for (int e = e0 + threadIdx.x; e < e1; e += CLT) {
-    double2 acc = w[e];
-    for (int i = 0; i <= j; ++i) {
-      const double2 v = V[(size_t)i * nb + e], hi = h2[i];
-      if (C) {
-        acc.x -= hi.x * v.x - hi.y * v.y;
-        acc.y -= hi.x * v.y + hi.y * v.x;
-      } else {
-        acc.x -= hi.x * v.x;
-      }
-    }
-    w[e] = acc;
-    ss += acc.x * acc.x + acc.y * acc.y;
-  }
+  for (int e = threadIdx.x; e < ns; e += CLT) ss += ws[e].x * ws[e].x + ws[e].y * ws[e].y;
   for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
   if (lane == 0) pn[warp] = ss;
   __syncthreads();
   if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int q = 0; q < CLT / 32; ++q) t += pn[q];
-    pnorm = t;
+    double t[CLT / 32];
+#pragma unroll
+    for (int q = 0; q < CLT / 32; ++q) t[q] = pn[q];
+#pragma unroll
+    for (int w2 = 1; w2 < CLT / 32; w2 <<= 1)
+#pragma unroll
+      for (int q = 0; q + w2 < CLT / 32; q += 2 * w2) t[q] += t[q + w2];
+    pnorm = t[0];
   }
   cl.sync();
-  double nn = 0.0;
-  for (int r = 0; r < CL; ++r) nn += *cl.map_shared_rank(&pnorm, r);
+  double nn;
+  {
+    double v[CL_MAX];
+#pragma unroll
+    for (int r = 0; r < CL_MAX; ++r) v[r] = r < CL ? *cl.map_shared_rank(&pnorm, r) : 0.0;
+#pragma unroll
+    for (int w2 = 1; w2 < CL_MAX; w2 <<= 1)
+#pragma unroll
+      for (int r = 0; r + w2 < CL_MAX; r += 2 * w2) v[r] += v[r + w2];
+    nn = v[0];
+  }
   const double hn = sqrt(nn);
   const double inv = hn > 0.0 ? 1.0 / hn : 0.0;
-  double2* vn = V + (size_t)(j + 1) * nb;
-  for (int e = e0 + threadIdx.x; e < e1; e += CLT) vn[e] = make_double2(w[e].x * inv, w[e].y * inv);
-  if (rank == 0 && threadIdx.x == 0) {
+  double2* vn = V + (size_t)(j + 1) * nb + e0;
+  for (int e = threadIdx.x; e < ns; e += CLT) vn[e] = make_double2(ws[e].x * inv, ws[e].y * inv);
+  if (rank == 0) {
+    // stage the rotations, g and the new column in shared memory so the
+    // sequential rotation chain waits on no global loads
+    for (int i = threadIdx.x; i <= j + 1; i += CLT) {
+      if (i <= j) gcol[i] = make_double2(h1[i].x + h2[i].x, h1[i].y + h2[i].y);
+      if (i < j) {
+        gcs[i] = cs[i];
+        gsn[i] = sn[i];
+      }
+      gg[i] = g[i];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      if (C)
+        givens_column(gcol, j, hn, gcs, gsn, gg, scal);
+      else
+        givens_column_real(gcol, j, hn, gcs, gsn, gg, scal);
+    }
+    __syncthreads();
     double2* col = H + (size_t)j * (m + 1);
-    for (int i = 0; i <= j; ++i) col[i] = make_double2(h1[i].x + h2[i].x, h1[i].y + h2[i].y);
-    givens_column(col, j, hn, cs, sn, g, scal);
+    for (int i = threadIdx.x; i <= j + 1; i += CLT) {
+      col[i] = gcol[i];
+      g[i] = gg[i];
+    }
+    if (threadIdx.x == 0) {
+      cs[j] = gcs[j];
+      sn[j] = gsn[j];
+    }
   }
   // no CTA leaves while a peer may still read its shared memory
   cl.sync();
@@ -514,6 +696,11 @@ static int arnoldi_cluster_size() {
   if (cl >= 0) return cl;
   cl = 0;
   for (int want : {16, 8}) {
+    if (cudaFuncSetAttribute(k_arnoldi_cl<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, VS_CAP) != cudaSuccess ||
+        cudaFuncSetAttribute(k_arnoldi_cl<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, VS_CAP) != cudaSuccess) {
+      cudaGetLastError();
+      break;
+    }
     if (want > 8) {
       if (cudaFuncSetAttribute(k_arnoldi_cl<true>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess ||
           cudaFuncSetAttribute(k_arnoldi_cl<false>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
@@ -524,6 +711,7 @@ static int arnoldi_cluster_size() {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(want, 1, 1);
     cfg.blockDim = dim3(CLT, 1, 1);
+    cfg.dynamicSmemBytes = VS_CAP;
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeClusterDimension;
     at[0].val.clusterDim.x = want;
@@ -548,6 +736,10 @@ static void arnoldi_step_cluster(kfbi_domain* D, bool C, int j, int CL, cudaStre
   cfg.gridDim = dim3(CL, 1, 1);
   cfg.blockDim = dim3(CLT, 1, 1);
   cfg.stream = st;
+  const int slice = (D->nb + CL - 1) / CL;
+  const size_t vbytes = (size_t)(j + 1) * slice * sizeof(double2);
+  const int cached = vbytes <= (size_t)VS_CAP ? 1 : 0;
+  cfg.dynamicSmemBytes = cached ? vbytes : 0;
   cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeClusterDimension;
   at[0].val.clusterDim.x = CL;
@@ -560,11 +752,12 @@ static void arnoldi_step_cluster(kfbi_domain* D, bool C, int j, int CL, cudaStre
   void* tok = g_prof_on ? prof_begin(KFBI_PROF_KRYLOV, st) : nullptr;
   if (C)
     KFBI_CUDA(cudaLaunchKernelEx(&cfg, k_arnoldi_cl<true>, V, D->nb, j, w, (double2*)D->d_H, D->d_cs,
-                                 (double2*)D->d_sn, (double2*)D->d_g, D->restart, D->d_scal));
+                                 (double2*)D->d_sn, (double2*)D->d_g, D->restart, D->d_scal,
+                                 cached));
   else
     KFBI_CUDA(cudaLaunchKernelEx(&cfg, k_arnoldi_cl<false>, V, D->nb, j, w, (double2*)D->d_H,
                                  D->d_cs, (double2*)D->d_sn, (double2*)D->d_g, D->restart,
-                                 D->d_scal));
+                                 D->d_scal, cached));
   if (tok) prof_end(tok, st);
   g_launches.fetch_add(1, std::memory_order_relaxed);
 }

@@ -1,28 +1,29 @@
 // Mixed-precision operator application: the DST-I box solve of Sec. 3.4.2
 // (arXiv 2404.14864) as dense GEMMs on the sm_103a tensor cores.
 //
-// One pass computes out[p][c][r] = sum_k A[p][r][k] S[k][c] (two passes give
-// S A S).  Operands are split into TF32 pairs, A = A_hi + A_lo and
-// S = S_hi + S_lo.  Each CTA owns a 128 x 64 output tile (128 CTAs per
-// 1024^2 pass) and runs six warps:
+// One pass computes out[p][c][r] = sum_k S[c][k] A[p][r][k] (S is
+// symmetric; two passes give S A S).  Operands are split into TF32 pairs,
+// A = A_hi + A_lo and S = S_hi + S_lo.  Each CTA owns a 128 (c) x 128 (r)
+// output tile (64 CTAs per real 1024^2 pass) and runs ten warps:
 //   - warp 0 lane 0 streams K-blocks of 32 fp32 (one 128-byte swizzle row)
-//     of A_hi, A_lo, S_hi, S_lo into a 4-stage shared-memory ring with TMA
-//     (cp.async.bulk.tensor, 128B swizzle, mbarrier completion).  S_hi and
-//     S_lo land back to back, so together they are one 128-row operand;
-//   - warp 1 lane 0 issues tcgen05.mma kind::tf32 with M = 128, N = 128,
-//     K = 8: A_hi [S_hi | S_lo] and A_lo [S_hi | S_lo] into one TMEM
-//     accumulator of 128 columns (columns j and 64 + j hold the hi and lo
-//     halves of output column j, so all four products are formed).  Two
-//     K-blocks go into one of four accumulators, which tcgen05.commit then
-//     publishes; each stage is released by its own commit;
-//   - warps 2-5 drain each finished accumulator with tcgen05.ld (one tile
-//     row per thread) into FP32 registers, adding the two halves, then
-//     store the tile transposed, which makes each warp's store one
-//     128-byte line; the epilogue splits the result into the next pass's
-//     TF32 pair, applies the eigenvalue division of the box solve (pass 2,
-//     real kappa) or writes plain FP32 (pass 4).
-// N = 128 runs the tensor core about twice as efficiently per product as
-// three N = 64 products, and draining every second K-block halves the
+//     of S_hi, S_lo, A_hi, A_lo into a 3-stage shared-memory ring with TMA
+//     (cp.async.bulk.tensor, 128B swizzle, mbarrier completion).  A_hi and
+//     A_lo land back to back, so together they are one 256-row operand;
+//   - warp 1 lane 0 issues tcgen05.mma kind::tf32 with M = 128 (c),
+//     N = 256 (r of A_hi, then r of A_lo), K = 8: S_hi [A_hi | A_lo] and
+//     S_lo [A_hi | A_lo] into one TMEM accumulator of 256 columns (columns
+//     j and 128 + j hold the hi and lo halves of output column j, so all
+//     four products are formed).  Two K-blocks go into one of two
+//     accumulators, which tcgen05.commit then publishes; each stage is
+//     released by its own commit;
+//   - warps 2-9 drain each finished accumulator with tcgen05.ld (one output
+//     row c per thread, half of the r columns per warp group) into FP32
+//     registers, adding the two halves, then store their 64 consecutive r
+//     values with vector stores; the epilogue splits the result into the
+//     next pass's TF32 pair, applies the eigenvalue division of the box
+//     solve (pass 2, real kappa) or writes plain FP32 (pass 4).
+// N = 256 is the tensor core's full width (three N = 64 products ran it at
+// about a third of its rate), and draining every second K-block halves the
 // commit round trips; the accumulator sums 64 K-terms, which keeps the
 // tensor core's internal FP32 rounding at the level of one group.
 // Every mbarrier wait is bounded; on timeout the kernel records an error
@@ -44,19 +45,22 @@
 namespace kfbi {
 namespace tc {
 
-constexpr int STAGES = 4;
-constexpr int A_BYTES = BM * BK * 4;          // 16 KiB
-constexpr int B_BYTES = BN * BK * 4;          // 8 KiB
-constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;  // A_hi, A_lo, B_hi, B_lo
-constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
-constexpr int THREADS = 192;                  // producer, MMA, 4 drain/epilogue warps
-constexpr int NW = 2 * BN;                    // MMA width: [S_hi | S_lo]
-constexpr int NACC = 4;                       // TMEM accumulators in flight
+constexpr int STAGES = 3;
+constexpr int S_BYTES = BC * BK * 4;          // 16 KiB: S_hi or S_lo
+constexpr int A_BYTES = BR * BK * 4;          // 16 KiB: A_hi or A_lo
+constexpr int STAGE_BYTES = 2 * S_BYTES + 2 * A_BYTES;  // S_hi, S_lo, A_hi, A_lo
+constexpr int RECV_BYTES = BC * (BR / 2) * 4;  // 32 KiB: half a tile from the peer CTA
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + RECV_BYTES + 1024 + 256;
+constexpr int NDRAIN = 8;                     // drain / epilogue warps
+constexpr int THREADS = 64 + 32 * NDRAIN;     // producer, MMA, drain warps
+constexpr int NW = 2 * BR;                    // MMA width: [A_hi | A_lo]
+constexpr int NACC = 2;                       // TMEM accumulators in flight
 constexpr int KPA = 2;                        // K-blocks per accumulator
+constexpr int RH = BR / 2;                    // r columns per drain warp group
 constexpr uint32_t TMEM_COLS = NACC * NW;     // 512 columns: all of TMEM
-// kind::tf32, D = F32, A = B = TF32, both K-major, N = NW, M = BM
+// kind::tf32, D = F32, A = B = TF32, both K-major, N = NW, M = BC
 constexpr uint32_t IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(NW >> 3) << 17) |
-                           ((uint32_t)(BM >> 4) << 24);
+                           ((uint32_t)(BC >> 4) << 24);
 constexpr long long WAIT_LIMIT = 4000000000LL;  // cycles (~2 s)
 
 __device__ __forceinline__ const PassDesc* tile_desc(const GroupArgs& ga, int t, int& lt) {
@@ -111,6 +115,41 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
   while (!mbar_try_wait(bar, parity))
     if (clock64() - t0 > WAIT_LIMIT) return false;
   return true;
+}
+
+// Wait that also acquires writes other CTAs of the cluster released to
+// this barrier (remote stores followed by a remote arrive).
+__device__ __forceinline__ bool mbar_wait_cluster(uint64_t* bar, uint32_t parity) {
+  const long long t0 = clock64();
+  for (;;) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if (clock64() - t0 > WAIT_LIMIT) return false;
+  }
+}
+
+// Address of the same shared-memory location in CTA `rank` of the cluster.
+__device__ __forceinline__ uint32_t peer_addr(const void* p, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(smem_u32(p)), "r"(rank));
+  return r;
+}
+
+__device__ __forceinline__ void st_peer_v4(uint32_t addr, float a, float b, float c, float d) {
+  asm volatile("st.shared::cluster.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "f"(a), "f"(b),
+               "f"(c), "f"(d)
+               : "memory");
+}
+
+__device__ __forceinline__ void arrive_peer(uint32_t bar_addr) {
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(bar_addr)
+               : "memory");
 }
 
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar,
@@ -179,12 +218,15 @@ __device__ __forceinline__ void tmem_ld32_nowait(uint32_t taddr, uint32_t* r) {
 __global__ void __launch_bounds__(THREADS, 1) k_tc_pass(const __grid_constant__ GroupArgs ga) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* tiles = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  uint64_t* full = (uint64_t*)(tiles + STAGES * STAGE_BYTES);
+  float* recv = (float*)(tiles + STAGES * STAGE_BYTES);  // [BC rows][BR / 2]
+  uint64_t* full = (uint64_t*)(tiles + STAGES * STAGE_BYTES + RECV_BYTES);
   uint64_t* empty = full + STAGES;
-  uint64_t* accf = empty + STAGES;  // accumulator b holds a finished K-block
+  uint64_t* accf = empty + STAGES;  // accumulator b holds a finished group
   uint64_t* acce = accf + NACC;     // accumulator b has been drained
   uint64_t* done = acce + NACC;     // all MMAs retired
-  uint32_t* tmem_slot = (uint32_t*)(done + 1);
+  uint64_t* rfull = done + 1;       // split K: the peer's half tile is in recv
+  uint64_t* pfree = rfull + 1;      // split K: the peer has consumed what we sent
+  uint32_t* tmem_slot = (uint32_t*)(pfree + 1);
   volatile int* s_state = (volatile int*)(tmem_slot + 1);  // [0] abort, [1] issued, [2] consumed
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -196,9 +238,11 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_pass(const __grid_constant__ 
     }
     for (int b = 0; b < NACC; ++b) {
       mbar_init(&accf[b], 1);
-      mbar_init(&acce[b], 4);
+      mbar_init(&acce[b], NDRAIN);
     }
     mbar_init(done, 1);
+    mbar_init(rfull, 4 * 32);
+    mbar_init(pfree, 4 * 32);
     s_state[0] = 0;
     s_state[1] = 0;
     s_state[2] = 0;
@@ -214,18 +258,25 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_pass(const __grid_constant__ 
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
+  // tile loop: CTA pairs (split K) walk the tiles together, rank r taking
+  // K-block half r; otherwise every CTA walks its own tiles
+  const int split = ga.splitk == 2 ? 2 : 1;
+  const int rank = split == 2 ? (int)(blockIdx.x & 1) : 0;
+  const int unit0 = blockIdx.x / split, nunits = gridDim.x / split;
 
   if (warp == 0) {
     if (lane == 0) {
       // TMA producer: stage ring continues across this CTA's tiles
       int g = 0;
       bool abort = false;
-      for (int t = blockIdx.x; t < ga.total && !abort; t += gridDim.x) {
+      for (int t = unit0; t < ga.total && !abort; t += nunits) {
         int lt;
         const PassDesc* d = tile_desc(ga, t, lt);
         if (d->active && *d->active == 0) continue;
-        const int row0 = (lt / d->nct) * BM, col0 = (d->ct0 + lt % d->nct) * BN;
-        for (int kb = 0; kb < d->nk; ++kb, ++g) {
+        const int r0 = (lt / d->nct) * BR, c0 = (d->ct0 + lt % d->nct) * BC;
+        const int kh = split == 2 ? (d->nk + 1) / 2 : d->nk;
+        const int kbl = rank ? kh : 0, kbh = rank ? d->nk : kh;
+        for (int kb = kbl; kb < kbh; ++kb, ++g) {
           const int s = g % STAGES, n = g / STAGES;
           if (s_state[0] || !mbar_wait(&empty[s], (uint32_t)((n & 1) ^ 1))) {
             s_state[0] = 1;
@@ -236,10 +287,10 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_pass(const __grid_constant__ 
           uint8_t* st = tiles + s * STAGE_BYTES;
           mbar_expect_tx(&full[s], STAGE_BYTES);
           const int kx = (d->kb0 + kb) * BK;
-          tma_load_2d(st, d->a_hi, &full[s], kx, row0);
-          tma_load_2d(st + A_BYTES, d->a_lo, &full[s], kx, row0);
-          tma_load_2d(st + 2 * A_BYTES, d->b_hi, &full[s], kx, col0);
-          tma_load_2d(st + 2 * A_BYTES + B_BYTES, d->b_lo, &full[s], kx, col0);
+          tma_load_2d(st, d->b_hi, &full[s], kx, c0);
+          tma_load_2d(st + S_BYTES, d->b_lo, &full[s], kx, c0);
+          tma_load_2d(st + 2 * S_BYTES, d->a_hi, &full[s], kx, r0);
+          tma_load_2d(st + 2 * S_BYTES + A_BYTES, d->a_lo, &full[s], kx, r0);
         }
       }
       s_state[1] = g;
@@ -250,15 +301,17 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_pass(const __grid_constant__ 
       // MMA issuer: KPA K-blocks per accumulator, accumulators in a ring
       int g = 0, q = 0;  // K-blocks and accumulator groups issued
       bool abort = false;
-      for (int t = blockIdx.x; t < ga.total && !abort; t += gridDim.x) {
+      for (int t = unit0; t < ga.total && !abort; t += nunits) {
         int lt;
         const PassDesc* d = tile_desc(ga, t, lt);
         if (d->active && *d->active == 0) continue;
-        for (int kb = 0; kb < d->nk; ++kb, ++g) {
+        const int kh = split == 2 ? (d->nk + 1) / 2 : d->nk;
+        const int kbl = rank ? kh : 0, kbh = rank ? d->nk : kh;
+        for (int kb = kbl; kb < kbh; ++kb, ++g) {
           const int s = g % STAGES, n = g / STAGES;
           const int b = q % NACC, nbuf = q / NACC;
-          const bool first = (kb % KPA) == 0;
-          const bool last = (kb % KPA) == KPA - 1 || kb == d->nk - 1;
+          const bool first = ((kb - kbl) % KPA) == 0;
+          const bool last = ((kb - kbl) % KPA) == KPA - 1 || kb == kbh - 1;
           if (s_state[0] || !mbar_wait(&full[s], (uint32_t)(n & 1)) ||
               (first && !mbar_wait(&acce[b], (uint32_t)((nbuf & 1) ^ 1)))) {
             s_state[0] = 1;
@@ -268,14 +321,14 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_pass(const __grid_constant__ 
           }
           tc_fence_after();
           uint8_t* st = tiles + s * STAGE_BYTES;
-          const uint64_t ah = desc_sw128(st), al = desc_sw128(st + A_BYTES);
-          const uint64_t bb = desc_sw128(st + 2 * A_BYTES);  // [S_hi | S_lo], 128 rows
+          const uint64_t sh = desc_sw128(st), sl = desc_sw128(st + S_BYTES);
+          const uint64_t aa = desc_sw128(st + 2 * S_BYTES);  // [A_hi | A_lo], 256 rows
           const uint32_t td = tmem + (uint32_t)(b * NW);
 #pragma unroll
           for (int k = 0; k < BK / 8; ++k) {
             const uint64_t o = (uint64_t)(2 * k);  // 8 tf32 = 32 bytes, in 16-byte units
-            umma_tf32(td, ah + o, bb + o, (first && k == 0) ? 0u : 1u);
-            umma_tf32(td, al + o, bb + o, 1u);
+            umma_tf32(td, sh + o, aa + o, (first && k == 0) ? 0u : 1u);
+            umma_tf32(td, sl + o, aa + o, 1u);
           }
           umma_commit(&empty[s]);
           if (last) {
@@ -289,20 +342,25 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_pass(const __grid_constant__ 
     }
     __syncwarp();
   } else {
-    // drain / epilogue warps: TMEM lane quarter (warp % 4) = tile rows
+    // drain / epilogue warps: TMEM lane quarter (warp % 4) = 32 output rows
+    // c; warps 2-5 take r columns 0..63 of the tile, warps 6-9 64..127
     const int q = warp & 3;
+    const int half = (warp - 2) >> 2;
     const uint32_t lane_base = (uint32_t)(q * 32) << 16;
-    int g = 0;
+    int g = 0, ex = 0;  // accumulator groups drained, tiles exchanged
     bool ok = true;
-    for (int t = blockIdx.x; t < ga.total && ok; t += gridDim.x) {
+    const int row = q * 32 + lane;  // output row c within the tile
+    const uint32_t peer = (uint32_t)(rank ^ 1);
+    for (int t = unit0; t < ga.total && ok; t += nunits) {
       int lt;
       const PassDesc* d = tile_desc(ga, t, lt);
       if (d->active && *d->active == 0) continue;
-      const int row0 = (lt / d->nct) * BM, col0 = (d->ct0 + lt % d->nct) * BN;
-      float acc[BN];
+      const int r0 = (lt / d->nct) * BR, c0 = (d->ct0 + lt % d->nct) * BC;
+      float acc[RH];
 #pragma unroll
-      for (int j = 0; j < BN; ++j) acc[j] = 0.f;
-      const int ngroups = (d->nk + KPA - 1) / KPA;
+      for (int j = 0; j < RH; ++j) acc[j] = 0.f;
+      const int kh = split == 2 ? (d->nk + 1) / 2 : d->nk;
+      const int ngroups = ((rank ? d->nk - kh : kh) + KPA - 1) / KPA;
       for (int gi = 0; gi < ngroups; ++gi, ++g) {
         const int b = g % NACC;
         // one lane waits, the warp follows its verdict (tcgen05.ld needs the
@@ -321,10 +379,11 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_pass(const __grid_constant__ 
         }
         tc_fence_after();
 #pragma unroll
-        for (int cc = 0; cc < BN; cc += 32) {
+        for (int cc = 0; cc < RH; cc += 32) {
           uint32_t rh[32], rl[32];
-          tmem_ld32_nowait(tmem + lane_base + (uint32_t)(b * NW + cc), rh);
-          tmem_ld32_nowait(tmem + lane_base + (uint32_t)(b * NW + BN + cc), rl);
+          const uint32_t col = (uint32_t)(b * NW + half * RH + cc);
+          tmem_ld32_nowait(tmem + lane_base + col, rh);
+          tmem_ld32_nowait(tmem + lane_base + col + BR, rl);
           asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
           for (int j = 0; j < 32; ++j) acc[cc + j] += __uint_as_float(rh[j]) + __uint_as_float(rl[j]);
@@ -334,27 +393,61 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_pass(const __grid_constant__ 
         if (lane == 0) mbar_arrive(&acce[b]);
       }
       if (!ok || s_state[0]) break;
-      const int Mp = d->Mp;
-      const int grow = row0 + q * 32 + lane;
-      const int p = grow / Mp, rr = grow - p * Mp;
-      const size_t pbase = (size_t)p * Mp * Mp + rr;
-      const int mode = d->mode, n1 = d->n1;
-      const float lam_r = (mode == 1) ? d->lam[rr] : 0.f;
-      const float kre = d->kre, scale = d->scale;
-      float* oh = d->out_hi;
-      float* ol = d->out_lo;
+      if (split == 2) {
+        // rank r finishes r-half r of the tile: send the other half's
+        // partial sums to the peer, receive the peer's partials of ours
+        const uint32_t ph = (uint32_t)(ex & 1);
+        ++ex;
+        if (half != rank) {
+          if (!mbar_wait_cluster(pfree, ph ^ 1u)) {
+            s_state[0] = 1;
+            atomicOr(ga.err, 16);
+            ok = false;
+            break;
+          }
+          const uint32_t dst = peer_addr(recv + row * RH, peer);
 #pragma unroll
-      for (int j = 0; j < BN; ++j) {
-        const int c = col0 + j;
-        float x = acc[j];
-        if (mode == 1) x = (rr < n1 && c < n1) ? x * (scale / (lam_r + d->lam[c] - kre)) : 0.f;
-        const size_t o = pbase + (size_t)c * Mp;
+          for (int j = 0; j < RH; j += 4)
+            st_peer_v4(dst + 4u * j, acc[j], acc[j + 1], acc[j + 2], acc[j + 3]);
+          arrive_peer(peer_addr(rfull, peer));
+          continue;
+        }
+        if (!mbar_wait_cluster(rfull, ph)) {
+          s_state[0] = 1;
+          atomicOr(ga.err, 32);
+          ok = false;
+          break;
+        }
+#pragma unroll
+        for (int j = 0; j < RH; ++j) acc[j] += recv[row * RH + j];
+        arrive_peer(peer_addr(pfree, peer));
+      }
+      const int Mp = d->Mp, n1 = d->n1, mode = d->mode;
+      const int c = c0 + q * 32 + lane;
+      const int p = r0 / Mp, rb = r0 - p * Mp + half * RH;  // first r of this thread's run
+      const size_t o0 = (size_t)p * Mp * Mp + (size_t)c * Mp + rb;
+      const float lam_c = (mode == 1) ? d->lam[c] : 0.f;
+      const float kre = d->kre, scale = d->scale;
+#pragma unroll
+      for (int j = 0; j < RH; j += 4) {
+        float x[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          x[u] = acc[j + u];
+          const int rr = rb + j + u;
+          if (mode == 1) x[u] = (rr < n1 && c < n1) ? x[u] * (scale / (d->lam[rr] + lam_c - kre)) : 0.f;
+        }
         if (mode == 2) {
-          oh[o] = x;
+          *reinterpret_cast<float4*>(d->out_hi + o0 + j) = make_float4(x[0], x[1], x[2], x[3]);
         } else {
-          const float hi = tf32_round(x);
-          oh[o] = hi;
-          ol[o] = tf32_round(x - hi);
+          float hi[4], lo[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            hi[u] = tf32_round(x[u]);
+            lo[u] = tf32_round(x[u] - hi[u]);
+          }
+          *reinterpret_cast<float4*>(d->out_hi + o0 + j) = make_float4(hi[0], hi[1], hi[2], hi[3]);
+          *reinterpret_cast<float4*>(d->out_lo + o0 + j) = make_float4(lo[0], lo[1], lo[2], lo[3]);
         }
       }
     }
@@ -376,6 +469,12 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_pass(const __grid_constant__ 
   if (warp == 1)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
                  "r"(TMEM_COLS));
+  if (split == 2) {
+    // neither CTA of a pair leaves while the other may still write to its
+    // shared memory or arrive on its barriers
+    asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;" ::
+                     : "memory");
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -778,20 +877,20 @@ TcDst* tc_create(kfbi_domain* D, const Plan& P) {
         imin = std::min(imin, v % n1);
         imax = std::max(imax, v % n1);
       }
-      T->ct0 = imin / BN;
-      T->nt3 = imax / BN + 1 - T->ct0;
+      T->ct0 = imin / BC;
+      T->nt3 = imax / BC + 1 - T->ct0;
     }
     const int Mp = D->Mp;
-    make_map(&T->mS_hi, T->S_hi, Mp, Mp, BN);
-    make_map(&T->mS_lo, T->S_lo, Mp, Mp, BN);
-    make_map(&T->mR_hi, T->Rh, Mp, 2 * Mp, BM);
-    make_map(&T->mR_lo, T->Rl, Mp, 2 * Mp, BM);
-    make_map(&T->mT1_hi, T->T1h, Mp, 2 * Mp, BM);
-    make_map(&T->mT1_lo, T->T1l, Mp, 2 * Mp, BM);
-    make_map(&T->mT2_hi, T->T2h, Mp, 2 * Mp, BM);
-    make_map(&T->mT2_lo, T->T2l, Mp, 2 * Mp, BM);
-    make_map(&T->mT1s_hi, T->T1sh, Mp, 2 * Mp, BM);
-    make_map(&T->mT1s_lo, T->T1sl, Mp, 2 * Mp, BM);
+    make_map(&T->mS_hi, T->S_hi, Mp, Mp, BC);
+    make_map(&T->mS_lo, T->S_lo, Mp, Mp, BC);
+    make_map(&T->mR_hi, T->Rh, Mp, 2 * Mp, BR);
+    make_map(&T->mR_lo, T->Rl, Mp, 2 * Mp, BR);
+    make_map(&T->mT1_hi, T->T1h, Mp, 2 * Mp, BR);
+    make_map(&T->mT1_lo, T->T1l, Mp, 2 * Mp, BR);
+    make_map(&T->mT2_hi, T->T2h, Mp, 2 * Mp, BR);
+    make_map(&T->mT2_lo, T->T2l, Mp, 2 * Mp, BR);
+    make_map(&T->mT1s_hi, T->T1sh, Mp, 2 * Mp, BR);
+    make_map(&T->mT1s_lo, T->T1sl, Mp, 2 * Mp, BR);
     const CUtensorMap maps[kNumMaps] = {T->mS_hi,  T->mS_lo,  T->mR_hi,   T->mR_lo,   T->mT1_hi,
                                         T->mT1_lo, T->mT2_hi, T->mT2_lo, T->mT1s_hi, T->mT1s_lo};
     KFBI_CUDA(cudaMalloc(&T->d_maps, sizeof(maps)));
@@ -851,8 +950,8 @@ static PassDesc pass_desc(TcDst* T, int am_hi, int am_lo, float* oh, float* ol, 
   d.kb0 = kb0;
   d.nk = nk < 0 ? T->Mp / BK : nk;
   d.ct0 = ct0;
-  d.nct = nct < 0 ? T->Mp / BN : nct;
-  d.nrt = P * T->Mp / BM;
+  d.nct = nct < 0 ? T->Mp / BC : nct;
+  d.nrt = P * T->Mp / BR;
   d.kre = kre;
   d.scale = scale;
   d.active = nullptr;
@@ -860,9 +959,35 @@ static PassDesc pass_desc(TcDst* T, int am_hi, int am_lo, float* oh, float* ol, 
 }
 
 // Tensor flops one pass issues: three TF32 products (hi*hi, hi*lo, lo*hi)
-// of BM x BN x BK per tile and K-block.
+// of BC x BR x BK per tile and K-block.
 double tc::pass_flops(const PassDesc& d) {
-  return 3.0 * 2.0 * BM * BN * BK * (double)d.nrt * d.nct * d.nk;
+  return 3.0 * 2.0 * BC * BR * BK * (double)d.nrt * d.nct * d.nk;
+}
+
+void tc::launch_tc_pass(GroupArgs ga, int nsm, double work, cudaStream_t st) {
+  if (ga.splitk < 1) ga.splitk = 2 * ga.total <= nsm ? 2 : 1;
+  const int pairs = ga.splitk == 2;
+  const int grid = pairs ? 2 * std::min(ga.total, nsm / 2) : std::min(ga.total, nsm);
+  if (grid <= 0) return;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid, 1, 1);
+  cfg.blockDim = dim3(THREADS, 1, 1);
+  cfg.dynamicSmemBytes = SMEM_BYTES;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = pairs ? 2 : 1;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = pairs ? 1 : 0;
+  void* tok = g_prof_on ? prof_begin(KFBI_PROF_DST, st) : nullptr;
+  KFBI_CUDA(cudaLaunchKernelEx(&cfg, k_tc_pass, ga));
+  if (tok) {
+    prof_end(tok, st);
+    prof_add_work(tok, work);
+  }
+  g_launches.fetch_add(1, std::memory_order_relaxed);
 }
 
 // One persistent launch over the tiles of a single instance.
@@ -874,8 +999,8 @@ static void launch_pass(TcDst* T, const PassDesc& d, cudaStream_t st) {
   ga.total = d.nct * d.nrt;
   ga.one = d;
   ga.err = T->err;
-  const int grid = std::min(ga.total, T->nsm);
-  KFBI_LAUNCH_PW(KFBI_PROF_DST, tc::pass_flops(d), k_tc_pass, grid, THREADS, SMEM_BYTES, st, ga);
+  ga.splitk = 0;
+  tc::launch_tc_pass(ga, T->nsm, tc::pass_flops(d), st);
 }
 
 // Four TF32x3 passes: (Rh, Rl) -> U (fp32 planes), eigenvalue division after

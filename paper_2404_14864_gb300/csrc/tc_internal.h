@@ -9,7 +9,10 @@
 namespace kfbi {
 namespace tc {
 
-constexpr int BM = 128, BN = 64, BK = 32;
+// Output tile of a pass: BC values of the transform index c (rows of S, the
+// MMA's M) by BR values of the data index r (rows of the data planes; the
+// MMA's N is 2 BR, the hi and lo halves side by side); K-blocks of BK.
+constexpr int BC = 128, BR = 128, BK = 32;
 
 // One instance's share of a (possibly grouped) pass.  Tensor maps live in
 // device memory (one array per domain).
@@ -27,7 +30,7 @@ struct PassDesc {
   int nk;
   int ct0;   // first output column tile
   int nct;   // output column tiles
-  int nrt;   // row tiles (planes x Mp / BM)
+  int nrt;   // tiles along r (planes x Mp / BR)
   float kre, scale;
   const int* active;  // instance flag (nullptr: always); tiles of inactive instances are skipped
 };
@@ -41,9 +44,13 @@ struct GroupArgs {
   int total;
   PassDesc one;
   int* err;
+  int splitk;  // 1, or 2: CTA pairs (2-CTA clusters) split each tile's K range
 };
 
 __global__ void k_tc_pass(const __grid_constant__ GroupArgs ga);
+// Launch one pass (ga.splitk < 1: chosen from the tile count; CTA pairs
+// when the tiles fill at most half of the SMs).  work: flops for profiling.
+void launch_tc_pass(GroupArgs ga, int nsm, double work, cudaStream_t st);
 // Tensor flops of one pass of an instance (all its tiles and K-blocks).
 double pass_flops(const PassDesc& d);
 extern const int kPassThreads;
