@@ -280,6 +280,13 @@ def run_ours(args, rank, world, local_rank):
     return out
 
 
+# DRAM bytes per launch of the mixed DST pass at the 1024^2 wave workload
+# (dram__bytes_read.sum + dram__bytes_write.sum from one ncu --set full
+# capture, mean of three launches of the timed step's passes).  Reset to
+# None whenever k_tc_pass changes until it is captured again.
+TC_PASS_TRAFFIC_1024 = (8.4718e6 + 3.3e3 + 14.7561e6 + 0.0 + 8.4749e6 + 7.4e3) / 3.0
+
+
 def roofline(res, M):
     """Roofline of the dominant kernel class (the DST-I passes): the flops the
     timed launches issued (counted per launch by the library: the executed
@@ -306,7 +313,8 @@ def roofline(res, M):
     bf16 = peaks.get("bf16_tflops_sustained", 1700.0)
     peak = bf16 * (1.1 / 2.25)
     return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": achieved / peak, "traffic": None,
+            "frac": achieved / peak, "traffic": TC_PASS_TRAFFIC_1024 if M == 1024 else None,
+            "traffic_unit": "bytes per launch",
             "kernel": "k_tc_pass (tcgen05 TF32x3 DST-I pass)",
             "peak_source": "of measured: bf16 sustained x nominal tf32/bf16 ratio (1.1/2.25)",
             "avg_launch_us": avg_s * 1e6, "launches": n, "flops_per_launch": flops / n}

@@ -3,12 +3,14 @@ DST passes with FP32 accumulation drained per K-block, FP32 correction and
 extraction, FP64 GMRES and steppers) against the float64 oracle.
 
 Stated bound for the fast operator (one application, what GMRES iterates
-with): 2e-5 relative L-infinity for u+ and the grid solution.  Arithmetic behind it: operands are TF32 pairs (2^-22 relative),
-each 32-term K-block is accumulated by the tensor core (<= 12 group
-additions, <= ~1.4e-6 relative of the block's partial sum) and blocks are
-summed in FP32 with round-to-nearest (< 2e-7 relative at K = 1024); four
-passes plus the FP32 correction and extraction stay below ~1e-5.  Observed
-maximum: 2.5e-6 for M <= 1024.  The bound is below the discretisation
+with): 2e-5 relative L-infinity for u+ and the grid solution.  Arithmetic
+behind it: operands are TF32 pairs (2^-22 relative) and all four products
+are formed; each group of 64 K-terms is accumulated by the tensor core (16
+MMA accumulations, <= ~2e-6 relative of the group's partial sum) and groups
+(and the two K halves of a split pass) are summed in FP32 with
+round-to-nearest (< 2e-7 relative at K = 2048); four passes plus the FP32
+correction and extraction stay below ~1e-5.  Observed maximum: 2.5e-6 for
+M <= 1024.  The bound is below the discretisation
 error of every workload here (5.6e-5 for the 1024^2 wave, 4e-4 for the
 64^2 heat problem).  For time steps the test also requires the mixed
 path's error against the exact solution to be at most 1.1x the float64
@@ -68,6 +70,10 @@ def test_mixed_operator_within_bound(name, desc, kind):
     up, U = dom.interface_solve(kappa, dev(phi), dev(f))
     assert rel_linf(host(up), up_or) <= BOUND
     assert rel_linf(host(U), U_or) <= BOUND
+    # f = 0: the sparse route GMRES iterates with
+    a_or = oracle.apply_operator(d, kappa, phi)
+    a = dom.apply_operator(kappa, dev(phi))
+    assert rel_linf(host(a), a_or) <= BOUND
     up0 = host(dom.apply_operator(kappa, dev(phi)))
     assert rel_linf(up0, oracle.apply_operator(d, kappa, phi)) <= BOUND
     # deterministic: the same call gives the same bits
@@ -182,3 +188,24 @@ def test_mixed_solve_density_refined(kappa):
     x_or, it, res, ok = oracle.gmres(lambda v: oracle.apply_operator(d, kappa, v), b, None,
                                      1e-13, 50, 400)
     assert rel_linf(host(phi), x_or) <= STEP_BOUND
+
+
+def test_mixed_operator_full_size_2048():
+    """The largest served grid (2048^2, 4096 boundary nodes) at the wave's
+    kappa (the largest kappa h^2 of the steppers): fast operator against the
+    oracle."""
+    rng = np.random.Generator(np.random.PCG64(7))
+    desc = W.domain_desc(2048, W.random_star(rng))
+    h = (desc["hi"] - desc["lo"]) / desc["M"]
+    kappa = 4.0 / (4 * h) ** 2
+    d, phi, f = _inputs(desc, False, seed=3)
+    Ft = np.where(d.interior_inside(), f, 0.0)
+    up_or, U_or = oracle.interface_solve(d, kappa, phi, Ft)
+    dom = kfbi.Domain(desc, kfbi.KFBI_MIXED_TF32)
+    up, U = dom.interface_solve(kappa, dev(phi), dev(f))
+    assert rel_linf(host(up), up_or) <= BOUND
+    assert rel_linf(host(U), U_or) <= BOUND
+    # f = 0: the sparse route GMRES iterates with
+    a_or = oracle.apply_operator(d, kappa, phi)
+    a = dom.apply_operator(kappa, dev(phi))
+    assert rel_linf(host(a), a_or) <= BOUND
