@@ -50,6 +50,7 @@ def parse():
     ap.add_argument("--requests", type=int, default=100)
     ap.add_argument("--max-resident", type=int, default=64)
     ap.add_argument("--rate", type=float, default=200.0)
+    ap.add_argument("--lanes", type=int, default=3)
     return ap.parse_args()
 
 
@@ -413,7 +414,7 @@ def run_served(args):
               for (_, kind, M, curve, steps) in reqs]
     t_prep = time.perf_counter() - t_prep
     srv = kfbi.Server(max_resident=args.max_resident, hbm_reserve_bytes=8 << 30, restart=50,
-                      plan_threads=8)
+                      plan_threads=8, lanes=args.lanes)
     ids = []
     for (arr, kind, M, curve, steps), x in zip(reqs, inputs):
         desc = W.domain_desc(M, curve)
@@ -455,8 +456,9 @@ def run_served(args):
             "config": {"workload": "served-%d-requests" % len(reqs), "rate_per_s": args.rate,
                        "sizes": [128, 256, 512, 1024, 2048], "steps": [20, 200],
                        "kinds": "heat:wave:schrodinger 1:1:1", "seed": 0,
-                       "max_resident": args.max_resident, "admission": "FIFO, exact device bytes, "
-                       "8 GiB of free HBM kept", "gmres": "restart 50, tol 1e-10"},
+                       "max_resident": args.max_resident, "lanes": args.lanes,
+                       "admission": "FIFO per size lane, exact device bytes, 8 GiB of free HBM "
+                       "kept", "gmres": "restart 50, tol 1e-10"},
             "latency_s": {"p50": q(lat, 0.5), "p99": q(lat, 0.99), "max": lat[-1] if lat else None},
             "queue_wait_s": {"p50": q(wait, 0.5), "p99": q(wait, 0.99)},
             "completed": st["completed"], "failed": st["failed"], "ticks": st["ticks"],

@@ -324,9 +324,16 @@ long long kfbi_plan_device_bytes(const kfbi_plan* plan, int equation);
  * its steps is retired: its final field is copied to its host u_out and its
  * device memory is freed for the next admissions.  A request's result does
  * not depend on the other requests it ran with.
+ * Lanes: with lanes > 1 requests are split by padded grid size (up to 512,
+ * up to 1024, larger; lane = min(class, lanes - 1)), each lane with its own
+ * batch, stream and admission queue under the shared slot and byte limits.
+ * kfbi_server_run drives every lane from its own host thread, so small
+ * requests are not held to the pace of the largest grid; kfbi_server_tick
+ * steps the lanes one after another.  Tick indices in kfbi_request_info
+ * count the request's lane's ticks.
  * Host threads (plan_threads) build the host plans of arrived requests
  * while the device works; with plan_threads = 0 plans are built at
- * admission.  Not thread safe: submit, tick and run from one thread. */
+ * admission.  Submit, tick and run are called from one thread. */
 typedef struct kfbi_server kfbi_server;
 
 typedef struct {
@@ -336,6 +343,8 @@ typedef struct {
   long long hbm_reserve_bytes; /* free device memory every admission leaves untouched */
   int gmres_restart;           /* GMRES restart shared by all requests (lockstep batch) */
   int plan_threads;            /* host threads building request plans, 0..64 */
+  int lanes;                   /* size lanes, 0..3 (0 and 1: one lane on the given stream;
+                                  more: one stream and host thread per lane) */
 } kfbi_server_desc;
 
 typedef struct {
@@ -382,8 +391,8 @@ typedef struct {
 } kfbi_request_info;
 
 typedef struct {
-  int ticks, admitted, completed, failed;
-  double busy_seconds;         /* inside batch steps */
+  int ticks, admitted, completed, failed; /* ticks summed over lanes */
+  double busy_seconds;         /* inside batch steps, summed over lanes */
   double admit_seconds;        /* admitting (plan wait, uploads, init) on the calling thread */
   double resident_ticks;       /* sum over ticks of the resident count */
   long long peak_device_bytes; /* most bytes held by resident requests at once */

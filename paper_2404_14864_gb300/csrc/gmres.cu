@@ -691,10 +691,8 @@ static void grid_shape(int nb, int& G, int& slice) {
 // Cluster size of the one-launch Arnoldi step: 16 CTAs where the device
 // runs such clusters (a non-portable size), else 8; 0 if clusters cannot be
 // launched at all (the grid version is used then).
-static int arnoldi_cluster_size() {
-  static int cl = -1;
-  if (cl >= 0) return cl;
-  cl = 0;
+static int probe_cluster_size() {
+  int cl = 0;
   for (int want : {16, 8}) {
     if (cudaFuncSetAttribute(k_arnoldi_cl<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, VS_CAP) != cudaSuccess ||
         cudaFuncSetAttribute(k_arnoldi_cl<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, VS_CAP) != cudaSuccess) {
@@ -728,6 +726,11 @@ static int arnoldi_cluster_size() {
     }
     cudaGetLastError();
   }
+  return cl;
+}
+
+static int arnoldi_cluster_size() {
+  static const int cl = probe_cluster_size();  // thread-safe one-time probe
   return cl;
 }
 

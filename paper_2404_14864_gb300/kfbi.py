@@ -62,7 +62,7 @@ class SolveInfo(ctypes.Structure):
 class ServerDesc(ctypes.Structure):
     _fields_ = [("max_resident", ctypes.c_int), ("hbm_budget_bytes", ctypes.c_longlong),
                 ("hbm_reserve_bytes", ctypes.c_longlong), ("gmres_restart", ctypes.c_int),
-                ("plan_threads", ctypes.c_int)]
+                ("plan_threads", ctypes.c_int), ("lanes", ctypes.c_int)]
 
 
 class Request(ctypes.Structure):
@@ -473,9 +473,9 @@ class Server:
     the request is done and returns the final field from ``result``."""
 
     def __init__(self, max_resident=64, hbm_budget_bytes=0, hbm_reserve_bytes=4 << 30,
-                 restart=50, plan_threads=4, stream=None):
+                 restart=50, plan_threads=4, lanes=1, stream=None):
         d = ServerDesc(int(max_resident), int(hbm_budget_bytes), int(hbm_reserve_bytes),
-                       int(restart), int(plan_threads))
+                       int(restart), int(plan_threads), int(lanes))
         h = ctypes.c_void_p()
         _check(lib().kfbi_server_create(ctypes.byref(d), _stream(stream), ctypes.byref(h)))
         self.h = h

@@ -39,9 +39,10 @@ def ellipse(a=0.7, b=0.4, alpha_deg=30.0, cx=0.0, cy=0.0):
 
 
 def domain_desc(M, curve, nb=None, lo=-1.0, hi=1.0):
-    """Grid label M (intervals per side), nb boundary nodes (default 2M)."""
+    """Grid label M (intervals per side), nb boundary nodes (default M, the
+    paper's choice; the 64^2 heat configuration states 128)."""
     return {"M": int(M), "lo": float(lo), "hi": float(hi),
-            "nb": int(nb if nb is not None else 2 * M), "curve": dict(curve)}
+            "nb": int(nb if nb is not None else M), "curve": dict(curve)}
 
 
 def grid_xy(desc):

@@ -260,3 +260,32 @@ def test_a_diverging_request_fails_alone():
         assert np.array_equal(alone.result(j), srv.result(ids[n]))
         alone.close()
     srv.close()
+
+
+def test_lanes_run_concurrently_with_identical_results():
+    """Three size lanes driven by their own host threads (kfbi_server_run):
+    every request gives the same bits as alone, and a small request
+    finishes before the large one that arrived with it."""
+    rng = np.random.Generator(np.random.PCG64(31))
+    mix = [
+        ("heat", W.domain_desc(128, W.random_star(rng)), 4, 0.000),
+        ("schrodinger", W.domain_desc(256, W.random_star(rng)), 3, 0.001),
+        ("wave", W.domain_desc(640, W.random_star(rng)), 3, 0.001),
+        ("heat", W.domain_desc(1100, W.random_star(rng)), 3, 0.000),
+        ("heat", W.domain_desc(96, W.random_star(rng)), 2, 0.002),
+    ]
+    srv = kfbi.Server(max_resident=8, plan_threads=2, restart=50, lanes=3)
+    ids = [_submit(srv, k, d, s, a) for k, d, s, a in mix]
+    srv.run(time_limit=300.0)
+    infos = [srv.info(i) for i in ids]
+    err = (kfbi.lib().kfbi_server_last_error(srv.h) or b"").decode()
+    assert all(i["state"] == kfbi.REQ_DONE for i in infos), (
+        [(i["state"], i["status"], i["steps_done"]) for i in infos], err)
+    assert infos[0]["finished"] < infos[3]["finished"]
+    for i, (k, d, s, a) in zip(ids, mix):
+        ref = kfbi.Server(max_resident=1, plan_threads=0, restart=50)
+        j = _submit(ref, k, d, s, 0.0)
+        _drain(ref, 1)
+        assert np.array_equal(ref.result(j), srv.result(i)), (k, d["M"])
+        ref.close()
+    srv.close()

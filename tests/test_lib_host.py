@@ -176,7 +176,7 @@ def test_request_inputs_shapes():
     desc = W.domain_desc(64, W.star())
     for kind in ("heat", "wave", "schrodinger"):
         x = W.request_inputs(kind, desc, 5)
-        assert x["g"].shape == (5, 128)
+        assert x["g"].shape == (5, 64)
         assert x["u0"].shape == (63, 63)
         assert x["exact"]().shape == (63, 63)
     h = W.request_inputs("heat", desc, 5)

@@ -30,7 +30,8 @@ def _paper_orders():
 
 
 def _heat_err(M, T=0.125):
-    desc = W.domain_desc(M, W.star())
+    # the 64^2 heat configuration's node density: 128 boundary nodes at 64^2
+    desc = W.domain_desc(M, W.star(), nb=2 * M)
     d = oracle.make_domain(desc)
     ex = W.HeatExact()
     X, Y = W.grid_xy(desc)
