@@ -47,7 +47,7 @@ def parse():
     ap.add_argument("--cpu-steps", type=int, default=2)
     ap.add_argument("--workload", default="wave1024", choices=["wave1024", "batched", "served"])
     ap.add_argument("--batch", type=int, default=256)
-    ap.add_argument("--requests", type=int, default=100)
+    ap.add_argument("--requests", type=int, default=200)
     ap.add_argument("--max-resident", type=int, default=64)
     ap.add_argument("--rate", type=float, default=200.0)
     ap.add_argument("--lanes", type=int, default=3)

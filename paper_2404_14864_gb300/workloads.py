@@ -193,9 +193,8 @@ def request_inputs(kind, desc, steps, theta=0.5):
     heat: u = exp(-t) sin(pi x) cos(pi y) with its source, whose step sums
     are src_coef[n] * profile (the source is exp(-t) times a profile);
     wave: u = cos(sqrt 2 pi t) sin(pi x) sin(pi y), theta = 1/2 by default
-    (second order like 1/4, but its roots stay away from the double root
-    at -1 that makes theta = 1/4 grow on grids with a node very close to
-    the interface);
+    (second order like 1/4; its roots stay away from the double root at -1
+    where theta = 1/4 lets a few random-star domains grow over 20-200 steps);
     Schroedinger: plane wave k = (5, 0), V = 0.  "exact" gives the solution
     at the request's final time on the interior grid."""
     X, Y = grid_xy(desc)
