@@ -208,6 +208,25 @@ __device__ __forceinline__ void tmem_ld32_nowait(uint32_t taddr, uint32_t* r) {
       : "r"(taddr));
 }
 
+// TF32 value of x, rounded to nearest (ties away from zero) by the
+// conversion instruction.  The split x = hi + lo only needs hi to carry at
+// most 10 mantissa bits; lo = x - hi is exact in FP32 either way.
+__device__ __forceinline__ float tf32_rna(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+__device__ __forceinline__ void tmem_ld16_nowait(uint32_t taddr, uint32_t* r) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32"
+      " {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+}
+
 // One DST-I pass (see the file comment).  The tensor core accumulates KPA
 // K-blocks (64 terms, both operand halves) into a TMEM accumulator; the
 // drain warps add each group's partial tile into FP32 registers with
@@ -379,14 +398,14 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_pass(const __grid_constant__ 
         }
         tc_fence_after();
 #pragma unroll
-        for (int cc = 0; cc < RH; cc += 32) {
-          uint32_t rh[32], rl[32];
+        for (int cc = 0; cc < RH; cc += 16) {
+          uint32_t rh[16], rl[16];
           const uint32_t col = (uint32_t)(b * NW + half * RH + cc);
-          tmem_ld32_nowait(tmem + lane_base + col, rh);
-          tmem_ld32_nowait(tmem + lane_base + col + BR, rl);
+          tmem_ld16_nowait(tmem + lane_base + col, rh);
+          tmem_ld16_nowait(tmem + lane_base + col + BR, rl);
           asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-          for (int j = 0; j < 32; ++j) acc[cc + j] += __uint_as_float(rh[j]) + __uint_as_float(rl[j]);
+          for (int j = 0; j < 16; ++j) acc[cc + j] += __uint_as_float(rh[j]) + __uint_as_float(rl[j]);
         }
         tc_fence_before();
         __syncwarp();
@@ -419,15 +438,25 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_pass(const __grid_constant__ 
           break;
         }
 #pragma unroll
-        for (int j = 0; j < RH; ++j) acc[j] += recv[row * RH + j];
+        for (int j = 0; j < RH; j += 4) {
+          const float4 v = *reinterpret_cast<const float4*>(recv + row * RH + j);
+          acc[j] += v.x;
+          acc[j + 1] += v.y;
+          acc[j + 2] += v.z;
+          acc[j + 3] += v.w;
+        }
         arrive_peer(peer_addr(pfree, peer));
       }
+      // Epilogue: each thread owns output row c and stores its 64 r values
+      // (contiguous in memory) as 16-byte vectors.
       const int Mp = d->Mp, n1 = d->n1, mode = d->mode;
       const int c = c0 + q * 32 + lane;
       const int p = r0 / Mp, rb = r0 - p * Mp + half * RH;  // first r of this thread's run
       const size_t o0 = (size_t)p * Mp * Mp + (size_t)c * Mp + rb;
       const float lam_c = (mode == 1) ? d->lam[c] : 0.f;
       const float kre = d->kre, scale = d->scale;
+      float* oh = d->out_hi;
+      float* ol = d->out_lo;
 #pragma unroll
       for (int j = 0; j < RH; j += 4) {
         float x[4];
@@ -438,16 +467,16 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_pass(const __grid_constant__ 
           if (mode == 1) x[u] = (rr < n1 && c < n1) ? x[u] * (scale / (d->lam[rr] + lam_c - kre)) : 0.f;
         }
         if (mode == 2) {
-          *reinterpret_cast<float4*>(d->out_hi + o0 + j) = make_float4(x[0], x[1], x[2], x[3]);
+          *reinterpret_cast<float4*>(oh + o0 + j) = make_float4(x[0], x[1], x[2], x[3]);
         } else {
           float hi[4], lo[4];
 #pragma unroll
           for (int u = 0; u < 4; ++u) {
-            hi[u] = tf32_round(x[u]);
-            lo[u] = tf32_round(x[u] - hi[u]);
+            hi[u] = tf32_rna(x[u]);
+            lo[u] = tf32_rna(x[u] - hi[u]);
           }
-          *reinterpret_cast<float4*>(d->out_hi + o0 + j) = make_float4(hi[0], hi[1], hi[2], hi[3]);
-          *reinterpret_cast<float4*>(d->out_lo + o0 + j) = make_float4(lo[0], lo[1], lo[2], lo[3]);
+          *reinterpret_cast<float4*>(oh + o0 + j) = make_float4(hi[0], hi[1], hi[2], hi[3]);
+          *reinterpret_cast<float4*>(ol + o0 + j) = make_float4(lo[0], lo[1], lo[2], lo[3]);
         }
       }
     }
