@@ -629,7 +629,8 @@ long long kfbi_plan_device_bytes(const kfbi_plan* plan, int equation) {
   if (!plan || equation < KFBI_HEAT || equation > KFBI_SCHRODINGER) return -1;
   const Plan& P = plan->p;
   const int Mp = ((P.n1 + 127) / 128) * 128;
-  return domain_bytes_for(P) + state_bytes_for(Mp, P.nb, equation);
+  return domain_bytes_for(P) +
+         state_bytes_for(Mp, P.nb, equation, P.desc.precision == KFBI_MIXED_TF32);
 }
 
 long long kfbi_plan_size(const kfbi_plan* plan, int field) {

@@ -902,9 +902,11 @@ __global__ void k_axpy(double2* __restrict__ x, const double2* __restrict__ d, i
 static const double kInnerFloor = 1e-6;
 
 kfbi_status gmres_solve(kfbi_domain* D, double kre, double kim, const double* b, double* x,
-                        bool x_zero, kfbi_solve_info* info, cudaStream_t st) {
+                        bool x_zero, kfbi_solve_info* info, cudaStream_t st, const double* ax0,
+                        double* ax_out, bool* grid_wx) {
   const double tol = D->desc.gmres_tol;
   const int maxit = D->desc.gmres_maxit;
+  if (grid_wx) *grid_wx = false;
   if (!D->tc) return gmres_core(D, kre, kim, b, x, x_zero, tol, maxit, info, st);
   // Mixed domain: iterative refinement.  The residual of the density,
   // r = b - A phi, uses the accurate operator (apply_accurate, FP64 vector
@@ -920,14 +922,22 @@ kfbi_status gmres_solve(kfbi_domain* D, double kre, double kim, const double* b,
   double rn = 0.0;
   bool conv = false;
   kfbi_status status = KFBI_OK;
+  bool fresh = false;  // D->d_Ax and D->d_U come from an application at the current x
   for (int sweep = 0; sweep < 8; ++sweep) {
     const bool skip = sweep == 0 && x_zero;
+    const double* ax = skip ? nullptr : D->d_Ax;
+    fresh = false;
     if (!skip) {
-      apply_accurate(D, kre, kim, x, 2, nullptr, D->d_Ax, 2, st);
-      ++apps;
+      if (sweep == 0 && ax0) {
+        ax = ax0;  // A x of the incoming x, kept by the caller (superposition)
+      } else {
+        apply_accurate(D, kre, kim, x, 2, nullptr, D->d_Ax, 2, st);
+        ++apps;
+        fresh = true;
+      }
     }
     KFBI_LAUNCH_P(KFBI_PROF_KRYLOV, k_residual, 1, kThreads, 0, st, (const double2*)b,
-                  skip ? nullptr : (const double2*)D->d_Ax, (double2*)D->d_Rv, nb, D->d_scal);
+                  (const double2*)ax, (double2*)D->d_Rv, nb, D->d_scal);
     KFBI_CHECK_LAUNCH();
     read_scalars(D, st);
     rn = D->h_scal[1];
@@ -954,6 +964,11 @@ kfbi_status gmres_solve(kfbi_domain* D, double kre, double kim, const double* b,
     KFBI_LAUNCH_P(KFBI_PROF_KRYLOV, k_axpy, vb, 256, 0, st, (double2*)x, (const double2*)D->d_Dv,
                   nb);
     KFBI_CHECK_LAUNCH();
+  }
+  if (conv && fresh && ax_out) {
+    KFBI_CUDA(cudaMemcpyAsync(ax_out, D->d_Ax, 2 * (size_t)nb * sizeof(double),
+                              cudaMemcpyDeviceToDevice, st));
+    if (grid_wx) *grid_wx = true;
   }
   KFBI_CUDA(cudaStreamSynchronize(st));
   if (info) {

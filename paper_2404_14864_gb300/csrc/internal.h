@@ -197,6 +197,10 @@ struct kfbi_state {
   double* d_phi = nullptr;    // density, complex interleaved 2nb
   double* d_b = nullptr;      // BIE right-hand side, complex interleaved 2nb
   double* d_ub = nullptr;     // u+ of the volume part
+  // mixed domains: superposition caches of the refined solve
+  double* d_uf = nullptr;     // grid of the volume part, Y f-tilde (planes x Mp^2)
+  double* d_ax = nullptr;     // A phi at the current phi (complex interleaved 2nb)
+  bool ax_valid = false;
   long long bytes = 0;
 };
 
@@ -258,8 +262,15 @@ void unpad(kfbi_domain* D, const double* src, double* dst, bool C, cudaStream_t 
 int grid_for(size_t n, int block);
 
 // gmres.cu
+// GMRES for A x = b (refined on a mixed domain).  ax0 (optional, mixed
+// only): A x for the incoming x, reused for the first residual instead of an
+// application.  ax_out (optional): receives A x at the returned x when the
+// last residual was a fresh accurate application at it; *grid_wx is then
+// true and D->d_U holds that application's grid, W x (no volume source).
 kfbi_status gmres_solve(kfbi_domain* D, double kre, double kim, const double* b, double* x,
-                        bool x_zero, kfbi_solve_info* info, cudaStream_t st);
+                        bool x_zero, kfbi_solve_info* info, cudaStream_t st,
+                        const double* ax0 = nullptr, double* ax_out = nullptr,
+                        bool* grid_wx = nullptr);
 void gmres_alloc(kfbi_domain* D);
 // Throws KFBI_ERR_TIMEOUT if a device kernel recorded a failed bounded wait
 // (flags read back into h_scal by the last scalar read).
@@ -280,7 +291,7 @@ long long tc_bytes(const TcDst* tc);
 long long tc_bytes_for(const Plan& P, int Mp);
 long long gmres_bytes(int m, int nb);
 long long domain_bytes_for(const Plan& P);
-long long state_bytes_for(int Mp, int nb, int equation);
+long long state_bytes_for(int Mp, int nb, int equation, bool mixed);
 // A device domain from a built plan (throws Status); kfbi_create_domain
 // is build_plan followed by this.
 kfbi_domain* domain_from_plan(const Plan& plan, cudaStream_t st);

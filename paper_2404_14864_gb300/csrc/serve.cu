@@ -276,7 +276,8 @@ void admit(kfbi_server* S, Lane& L, double now) {
       if (q.job->status == KFBI_OK) {
         const Plan& P = q.job->plan;
         need = kfbi::domain_bytes_for(P) +
-               state_bytes_for(((P.n1 + 127) / 128) * 128, P.nb, q.r.equation) + data_bytes(q.r, P);
+               state_bytes_for(((P.n1 + 127) / 128) * 128, P.nb, q.r.equation, true) +
+               data_bytes(q.r, P);
         if (need <= S->budget) {
           size_t free_b = 0, total_b = 0;
           if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) free_b = 0;

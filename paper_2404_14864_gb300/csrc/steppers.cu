@@ -172,19 +172,41 @@ using namespace stp;
 // One BIE solve of the step: b = g - u+[0, ft], GMRES for phi, then the grid
 // solution of Eq. 3.30 with (ft, phi) in D->d_U.  b and the final grid use
 // the accurate operator (FP64-level on either domain precision).
+// Superposition of the refined solve: U = W phi (in U) + Y f-tilde.
+__global__ void k_add_grid(double* __restrict__ U, const double* __restrict__ uf, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x)
+    U[i] += uf[i];
+}
+
 static kfbi_status solve_step(kfbi_domain* D, kfbi_state* S, const double* g, bool gC,
                               kfbi_solve_info* info, cudaStream_t st) {
   const int nb = D->nb;
+  const size_t pl = (size_t)S->planes * D->Mp * D->Mp;
   apply_accurate(D, S->kre, S->kim, D->d_zero_nb, 2, S->d_ft, S->d_ub, 2, st);
+  // mixed domains keep Y f-tilde so that the final grid is a sum (the
+  // discrete solution is linear in (f-tilde, phi))
+  if (S->d_uf)
+    KFBI_CUDA(cudaMemcpyAsync(S->d_uf, D->d_U, pl * sizeof(double), cudaMemcpyDeviceToDevice, st));
   KFBI_LAUNCH_P(KFBI_PROF_GRID, k_make_b, (nb + 255) / 256, 256, 0, st, S->d_b, g, S->d_ub, nb, gC ? 1 : 0);
   KFBI_CHECK_LAUNCH();
   kfbi_solve_info loc{};
-  kfbi_status s = gmres_solve(D, S->kre, S->kim, S->d_b, S->d_phi, S->phi_zero, &loc, st);
+  bool grid_wx = false;
+  const bool have_ax = S->d_ax && S->ax_valid && !S->phi_zero;
+  S->ax_valid = false;
+  kfbi_status s = gmres_solve(D, S->kre, S->kim, S->d_b, S->d_phi, S->phi_zero, &loc, st,
+                              have_ax ? S->d_ax : nullptr, S->d_ax, &grid_wx);
   S->phi_zero = false;
-  loc.applications += 2;
+  S->ax_valid = grid_wx;
+  loc.applications += grid_wx ? 1 : 2;
   if (info) *info = loc;
   if (s != KFBI_OK) return s;
-  apply_accurate(D, S->kre, S->kim, S->d_phi, 2, S->d_ft, nullptr, 2, st);
+  if (grid_wx) {
+    KFBI_LAUNCH_P(KFBI_PROF_GRID, k_add_grid, grid_for(pl, 256), 256, 0, st, D->d_U, S->d_uf, pl);
+    KFBI_CHECK_LAUNCH();
+  } else {
+    apply_accurate(D, S->kre, S->kim, S->d_phi, 2, S->d_ft, nullptr, 2, st);
+  }
   return KFBI_OK;
 }
 
@@ -221,6 +243,10 @@ kfbi_status kfbi_state_create(kfbi_domain* dom, int equation, kfbi_state** out) 
     alloc(&S->d_phi, nb2);
     alloc(&S->d_b, nb2);
     alloc(&S->d_ub, nb2);
+    if (dom->tc) {
+      alloc(&S->d_uf, plane);
+      alloc(&S->d_ax, nb2);
+    }
     KFBI_CUDA(cudaMemset(S->d_phi, 0, nb2 * sizeof(double)));
     return KFBI_OK;
   });
@@ -237,7 +263,8 @@ long long kfbi_state_device_bytes(const kfbi_state* st) { return st ? st->bytes 
 void kfbi_state_destroy(kfbi_state* S) {
   if (!S) return;
   cudaDeviceSynchronize();
-  double* ptrs[] = {S->d_u, S->d_F, S->d_Fprev, S->d_ft, S->d_aux, S->d_phi, S->d_b, S->d_ub};
+  double* ptrs[] = {S->d_u,   S->d_F, S->d_Fprev, S->d_ft, S->d_aux,
+                    S->d_phi, S->d_b, S->d_ub,    S->d_uf, S->d_ax};
   for (double* p : ptrs)
     if (p) cudaFree(p);
   delete S;
@@ -272,6 +299,7 @@ kfbi_status kfbi_state_init_heat(kfbi_state* S, double dt, const double* u0, con
     KFBI_CHECK_LAUNCH();
     KFBI_CUDA(cudaMemsetAsync(S->d_phi, 0, 2 * (size_t)D->nb * sizeof(double), st));
     S->phi_zero = true;
+    S->ax_valid = false;
     S->initialised = true;
     return KFBI_OK;
   });
@@ -299,6 +327,7 @@ kfbi_status kfbi_state_init_wave(kfbi_state* S, double dt, double theta, const d
     KFBI_CHECK_LAUNCH();
     KFBI_CUDA(cudaMemsetAsync(S->d_phi, 0, 2 * (size_t)D->nb * sizeof(double), st));
     S->phi_zero = true;
+    S->ax_valid = false;
     S->initialised = true;
     return KFBI_OK;
   });
@@ -324,6 +353,7 @@ kfbi_status kfbi_state_init_schrodinger(kfbi_state* S, double dt, const void* u0
     KFBI_CHECK_LAUNCH();
     KFBI_CUDA(cudaMemsetAsync(S->d_phi, 0, 2 * (size_t)D->nb * sizeof(double), st));
     S->phi_zero = true;
+    S->ax_valid = false;
     S->initialised = true;
     return KFBI_OK;
   });
@@ -426,11 +456,12 @@ kfbi_status kfbi_state_get_phi(kfbi_state* S, void* phi_out, void* stream) {
 
 namespace kfbi {
 
-long long state_bytes_for(int Mp, int nb, int equation) {
+long long state_bytes_for(int Mp, int nb, int equation, bool mixed) {
   const int planes = equation == KFBI_SCHRODINGER ? 2 : 1;
   const size_t plane = (size_t)Mp * Mp * planes;
-  const int fields = 3 + (equation != KFBI_HEAT ? 1 : 0);
-  return (long long)((fields * plane + 3 * 2 * (size_t)nb) * sizeof(double));
+  const int fields = 3 + (equation != KFBI_HEAT ? 1 : 0) + (mixed ? 1 : 0);
+  const int vectors = 3 + (mixed ? 1 : 0);
+  return (long long)((fields * plane + vectors * 2 * (size_t)nb) * sizeof(double));
 }
 
 }  // namespace kfbi

@@ -143,7 +143,8 @@ def test_plan_device_bytes_on_the_host(built):
     Mp = 128
     assert 0 < heat < wave < schr
     assert wave - heat == Mp * Mp * 8           # F^n plane of the wave state
-    assert schr - heat == 5 * Mp * Mp * 8       # complex u, F, ft and u** planes
+    # complex u, F, ft, u** and Y f-tilde (10 planes) against real u, F, ft, Y f-tilde (4)
+    assert schr - heat == 6 * Mp * Mp * 8
     assert p.device_bytes(7) == -1
     p.close()
     p64 = kfbi.Plan(d, kfbi.KFBI_FP64, 50)
