@@ -93,6 +93,8 @@ struct GInst {
   double2* x;    // density phi
   double2* b;
   double2* ub;
+  double* uf;             // Y f-tilde grid kept from the b computation (superposition)
+  double2* axc;           // A phi at the state's phi (superposition cache)
   const double* g_next;   // per step (caller layout)
   const double* src;      // heat source sum or Schroedinger potential (caller layout)
   double src_scale;       // heat: the source sum of this step is src_scale * src
@@ -580,6 +582,42 @@ __global__ void __launch_bounds__(1024) gk_residual(const GInst* gi) {
   if (threadIdx.x == 0) I.scal[1] = sqrt(s);
 }
 
+// Superposition of the refined step (as the single-instance path): the
+// discrete solution is Y f-tilde + W phi, so the grid of the b computation
+// is kept, and A phi of a converged residual check is reused by the next
+// step's first residual.
+__global__ void gk_keep_uf(const GInst* gi) {
+  const GInst& I = gi[blockIdx.y];
+  ACTIVE_OR_RETURN(I);
+  const size_t plane = (size_t)I.Mp * I.Mp;
+  const int P = I.C ? 2 : 1;
+  INST_PLANE_LOOP(I) {
+    for (int p = 0; p < P; ++p) I.uf[p * plane + idx] = I.U64[p * plane + idx];
+  }
+}
+
+__global__ void gk_add_uf(const GInst* gi) {
+  const GInst& I = gi[blockIdx.y];
+  ACTIVE_OR_RETURN(I);
+  const size_t plane = (size_t)I.Mp * I.Mp;
+  const int P = I.C ? 2 : 1;
+  INST_PLANE_LOOP(I) {
+    for (int p = 0; p < P; ++p) I.U64[p * plane + idx] += I.uf[p * plane + idx];
+  }
+}
+
+// direction 0: Ax = cached A phi; 1: cache = Ax
+__global__ void gk_ax_cache(const GInst* gi, int direction) {
+  const GInst& I = gi[blockIdx.y];
+  ACTIVE_OR_RETURN(I);
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < I.nb; k += gridDim.x * blockDim.x) {
+    if (direction == 0)
+      I.Ax[k] = I.axc[k];
+    else
+      I.axc[k] = I.Ax[k];
+  }
+}
+
 // V0 = r/beta with r = Rv - A Dv (restart) or Rv (fresh cycle), g = (beta, 0..)
 __global__ void __launch_bounds__(1024) gk_restart(const GInst* gi, int with_ax) {
   const GInst& I = gi[blockIdx.y];
@@ -960,6 +998,7 @@ struct kfbi_batch {
   cudaGraphExec_t iter_graph = nullptr;
   cudaStream_t graph_stream = nullptr;
   double tuned_us[2] = {0.0, 0.0};
+  std::vector<int> grid_wx;  // last step: instance's U64 holds W phi at its final phi
   std::string err;
   long long launches = 0;
 };
@@ -1273,6 +1312,7 @@ void fill_instances(kfbi_batch* B, kfbi_state* const* states, const void* const*
     I.part = (double2*)D->d_part; I.Rv = (double2*)D->d_Rv; I.Dv = (double2*)D->d_Dv;
     I.Ax = (double2*)D->d_Ax; I.scal = D->d_scal;
     I.u = S->d_u; I.F = S->d_F; I.Fprev = S->d_Fprev; I.ft = S->d_ft; I.aux = S->d_aux;
+    I.uf = S->d_uf; I.axc = (double2*)S->d_ax;
     I.x = (double2*)S->d_phi; I.b = (double2*)S->d_b; I.ub = (double2*)S->d_ub;
     I.g_next = (const double*)g_next[i];
     I.src = src ? src[i] : nullptr;
@@ -1292,8 +1332,14 @@ kfbi_status batch_gmres(kfbi_batch* B, kfbi_solve_info* infos, cudaStream_t st) 
   const int n = B->n;
   const double kInnerFloor = 1e-6;
   std::vector<int> act(n, 1), xz(n), conv(n, 0), iters(n, 0), apps(n, 0), bad(n, 0);
+  std::vector<int> ax_ok(n), fresh(n, 0);
   std::vector<double> bnorm(n, 0.0), rn(n, 0.0);
-  for (int i = 0; i < n; ++i) xz[i] = B->states[i]->phi_zero ? 1 : 0;
+  B->grid_wx.assign(n, 0);
+  for (int i = 0; i < n; ++i) {
+    xz[i] = B->states[i]->phi_zero ? 1 : 0;
+    ax_ok[i] = !xz[i] && B->states[i]->ax_valid && B->states[i]->d_ax ? 1 : 0;
+    B->states[i]->ax_valid = false;
+  }
   // ||b||
   set_active(B, act, &xz, st);
   KFBI_LAUNCH_P(KFBI_PROF_KRYLOV, gk_bnorm, inst_grid(1, n), 1024, 0, st, B->d_inst,
@@ -1301,20 +1347,31 @@ kfbi_status batch_gmres(kfbi_batch* B, kfbi_solve_info* infos, cudaStream_t st) 
   read_state(B, st);
   for (int i = 0; i < n; ++i) bnorm[i] = B->h_scal[8 * i];
   for (int sweep = 0; sweep < 8; ++sweep) {
-    // residual r = b - A_accurate x for instances still active
+    // residual r = b - A_accurate x for instances still active; at the
+    // first sweep an instance whose A phi is cached (its phi is the
+    // previous step's converged phi) copies it instead
     set_active(B, act, &xz, st);
-    std::vector<int> need(n);
-    bool any_acc = false;
+    std::vector<int> need(n), cached(n);
+    bool any_acc = false, any_cached = false;
     for (int i = 0; i < n; ++i) {
-      need[i] = act[i] && !xz[i];
+      const bool has = act[i] && !xz[i];
+      cached[i] = has && sweep == 0 && ax_ok[i];
+      need[i] = has && !cached[i];
+      fresh[i] = need[i];
       any_acc |= need[i] != 0;
+      any_cached |= cached[i] != 0;
+    }
+    if (any_cached) {
+      set_active(B, cached, nullptr, st);
+      KFBI_LAUNCH_P(KFBI_PROF_KRYLOV, gk_ax_cache, inst_grid((B->max_nb + 255) / 256, n), 256, 0, st,
+                    B->d_inst, 0);
     }
     if (any_acc) {
       set_active(B, need, nullptr, st);
       batch_accurate(B, 1, 0, 1, st);
       for (int i = 0; i < n; ++i) apps[i] += need[i];
-      set_active(B, act, &xz, st);
     }
+    if (any_cached || any_acc) set_active(B, act, &xz, st);
     KFBI_LAUNCH_P(KFBI_PROF_KRYLOV, gk_residual, inst_grid(1, n), 1024, 0, st, B->d_inst);
     read_state(B, st);
     bool any = false;
@@ -1330,6 +1387,7 @@ kfbi_status batch_gmres(kfbi_batch* B, kfbi_solve_info* infos, cudaStream_t st) 
       const double tol = B->doms[i]->desc.gmres_tol;
       if (bnorm[i] == 0.0 || rn[i] <= tol * bnorm[i] || iters[i] >= B->doms[i]->desc.gmres_maxit) {
         conv[i] = rn[i] <= tol * bnorm[i] || bnorm[i] == 0.0;
+        B->grid_wx[i] = conv[i] && fresh[i];
         act[i] = 0;
         continue;
       }
@@ -1422,13 +1480,21 @@ kfbi_status batch_gmres(kfbi_batch* B, kfbi_solve_info* infos, cudaStream_t st) 
     KFBI_LAUNCH_P(KFBI_PROF_KRYLOV, gk_axpy, inst_grid(8, n), 256, 0, st, B->d_inst, (const int*)B->d_sel);
     KFBI_CHECK_LAUNCH();
   }
+  bool any_wx = false;
+  for (int i = 0; i < n; ++i) any_wx |= B->grid_wx[i] != 0;
+  if (any_wx) {
+    set_active(B, B->grid_wx, nullptr, st);
+    KFBI_LAUNCH_P(KFBI_PROF_KRYLOV, gk_ax_cache, inst_grid((B->max_nb + 255) / 256, n), 256, 0, st,
+                  B->d_inst, 1);
+  }
+  for (int i = 0; i < n; ++i) B->states[i]->ax_valid = B->grid_wx[i] != 0;
   KFBI_CUDA(cudaStreamSynchronize(st));
   bool any_bad = false, any_unconv = false;
   for (int i = 0; i < n; ++i) {
     if (bad[i]) conv[i] = 0;
     if (infos) {
       infos[i].iters = iters[i];
-      infos[i].applications = apps[i] + 2;
+      infos[i].applications = apps[i] + (B->grid_wx[i] ? 1 : 2);
       infos[i].rel_residual = bad[i] ? std::nan("") : (bnorm[i] > 0.0 ? rn[i] / bnorm[i] : 0.0);
       infos[i].converged = conv[i];
     }
@@ -1538,14 +1604,32 @@ kfbi_status batch_step(kfbi_batch* B, kfbi_state* const* states, const void* con
     set_active(B, all, nullptr, st);
     KFBI_LAUNCH_P(KFBI_PROF_GRID, gk_make_ft, inst_grid(plane_blocks(B), n), 256, 0, st, B->d_inst);
     batch_accurate(B, 0, 1, 0, st);
+    KFBI_LAUNCH_P(KFBI_PROF_GRID, gk_keep_uf, inst_grid(plane_blocks(B), n), 256, 0, st, B->d_inst);
     KFBI_LAUNCH_P(KFBI_PROF_GRID, gk_make_b, inst_grid((B->max_nb + 255) / 256, n), 256, 0, st,
                   B->d_inst);
     // per-instance failures (non-finite, not converged) are reported in
     // infos; every instance still completes its step so the batch stays
     // consistent
     kfbi_status gs = batch_gmres(B, infos, st);
+    // final grid: W phi (left by the converged residual check) + Y f-tilde,
+    // else a refined application with (f-tilde, phi)
+    std::vector<int> sum_set(n), full_set(n);
+    bool any_sum = false, any_full = false;
+    for (int i = 0; i < n; ++i) {
+      sum_set[i] = B->grid_wx[i];
+      full_set[i] = !B->grid_wx[i];
+      any_sum |= sum_set[i] != 0;
+      any_full |= full_set[i] != 0;
+    }
+    if (any_sum) {
+      set_active(B, sum_set, nullptr, st);
+      KFBI_LAUNCH_P(KFBI_PROF_GRID, gk_add_uf, inst_grid(plane_blocks(B), n), 256, 0, st, B->d_inst);
+    }
+    if (any_full) {
+      set_active(B, full_set, nullptr, st);
+      batch_accurate(B, 1, 1, 0, st);
+    }
     set_active(B, all, nullptr, st);
-    batch_accurate(B, 1, 1, 0, st);
     KFBI_LAUNCH_P(KFBI_PROF_GRID, gk_step_update, inst_grid(plane_blocks(B), n), 256, 0, st, B->d_inst);
     KFBI_CHECK_LAUNCH();
     KFBI_CUDA(cudaStreamSynchronize(st));
