@@ -34,6 +34,26 @@ METRIC = ("grid-point·steps/s at 1024² vs plain FP64 GPU at fixed L∞ error; 
 UNIT = "grid-point*steps/s"
 
 
+def max_over_ranks(values, world, device=None):
+    """The slowest rank's times: an all-reduce (max) of a few floats over the
+    default process group (the timing barrier is the only collective of the
+    replica runs).  device: where the reduction tensor lives ("cuda" under
+    NCCL, None for a CPU group)."""
+    if world <= 1:
+        return [float(v) for v in values]
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.cpu()]
+
+
+def replica_value(world, work_per_rank, seconds):
+    """Whole-job throughput of independent replicas: all ranks' work over the
+    slowest rank's time (weak scaling)."""
+    return world * work_per_rank / seconds
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -283,9 +303,9 @@ def run_ours(args, rank, world, local_rank):
 
 # DRAM bytes per launch of the mixed DST pass at the 1024^2 wave workload
 # (dram__bytes_read.sum + dram__bytes_write.sum from one ncu --set full
-# capture, mean of three launches of the timed step's passes).  Reset to
-# None whenever k_tc_pass changes until it is captured again.
-TC_PASS_TRAFFIC_1024 = (8.4718e6 + 3.3e3 + 14.7561e6 + 0.0 + 8.4749e6 + 7.4e3) / 3.0
+# capture of three dense passes of the timed step, mean).  Reset to None
+# whenever k_tc_pass changes until it is captured again.
+TC_PASS_TRAFFIC_1024 = (16.845568e6 + 256 + 16.849920e6 + 768 + 16.845568e6 + 256) / 3.0
 
 
 def roofline(res, M):
@@ -545,13 +565,7 @@ def main():
 
     res = run_ours(args, rank, world, local_rank)
     K = args.steps
-    t_dev, t_e2e = res["t_dev"], res["t_e2e"]
-    if world > 1:
-        import torch
-        import torch.distributed as dist
-        tt = torch.tensor([t_dev, t_e2e], dtype=torch.float64, device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_dev, t_e2e = float(tt[0]), float(tt[1])
+    t_dev, t_e2e = max_over_ranks([res["t_dev"], res["t_e2e"]], world, "cuda")
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -565,7 +579,8 @@ def main():
         lat = sorted(res["lat"])
         p = lambda q: lat[min(len(lat) - 1, int(math.ceil(q * len(lat))) - 1)]
         line = {
-            "metric": METRIC, "value": world * M * M * K / t_dev, "unit": UNIT, "n_gpus": world,
+            "metric": METRIC, "value": replica_value(world, M * M * K, t_dev), "unit": UNIT,
+            "n_gpus": world,
             "steps": K, "warmup": args.warmup, "ms_per_step": 1e3 * t_dev / K,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64" if res["prec"] == kfbi.KFBI_FP64 else "tf32x3-f32acc+f64",
@@ -580,7 +595,7 @@ def main():
                                         for k, v in res["breakdown"].items()},
             "gpu_launches": res["launches"],
             "clocks": res["clocks"],
-            "e2e": {"value": world * M * M * K / t_e2e, "unit": UNIT,
+            "e2e": {"value": replica_value(world, M * M * K, t_e2e), "unit": UNIT,
                     "h2d_bytes_per_step": res["h2d"], "d2h_bytes_per_step": res["d2h"]},
             "cpu_baseline": cpu,
             "fp64_gpu": res["fp64"],
