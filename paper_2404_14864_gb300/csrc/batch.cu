@@ -117,6 +117,7 @@ __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
 
 // heat/wave: f-tilde = -F on Omega; Schroedinger: u** = B(u*), f-tilde = -kappa u**
 __global__ void gk_make_ft(const GInst* gi) {
+  KFBI_PDL_ENTRY();
   const GInst& I = gi[blockIdx.y];
   const size_t plane = (size_t)I.Mp * I.Mp;
   if (I.eq != KFBI_SCHRODINGER) {
@@ -145,6 +146,7 @@ __global__ void gk_make_ft(const GInst* gi) {
 
 // R64 = f-tilde (with_ft) or 0 over the instance's planes.
 __global__ void gk_base_rhs(const GInst* gi, int with_ft) {
+  KFBI_PDL_ENTRY();
   const GInst& I = gi[blockIdx.y];
   ACTIVE_OR_RETURN(I);
   const size_t plane = (size_t)I.Mp * I.Mp;
@@ -163,6 +165,7 @@ __device__ __forceinline__ const double* density_of(const GInst& I, int which, i
 }
 
 __global__ void gk_correct64(const GInst* gi, int which, int with_ft, const int* dj) {
+  KFBI_PDL_ENTRY();
   const GInst& I = gi[blockIdx.y];
   ACTIVE_OR_RETURN(I);
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
@@ -213,6 +216,7 @@ __global__ void gk_correct64(const GInst* gi, int which, int with_ft, const int*
 __device__ __forceinline__ float tf32r(float x) { return tf32_round(x); }
 
 __global__ void gk_split64(const GInst* gi) {
+  KFBI_PDL_ENTRY();
   const GInst& I = gi[blockIdx.y];
   ACTIVE_OR_RETURN(I);
   const size_t plane = (size_t)I.Mp * I.Mp;
@@ -229,6 +233,7 @@ __global__ void gk_split64(const GInst* gi) {
 }
 
 __global__ void gk_eig_cplx(const GInst* gi) {
+  KFBI_PDL_ENTRY();
   const GInst& I = gi[blockIdx.y];
   ACTIVE_OR_RETURN(I);
   if (!I.C) return;
@@ -251,6 +256,7 @@ __global__ void gk_eig_cplx(const GInst* gi) {
 }
 
 __global__ void gk_f32_to_f64(const GInst* gi) {
+  KFBI_PDL_ENTRY();
   const GInst& I = gi[blockIdx.y];
   ACTIVE_OR_RETURN(I);
   const size_t plane = (size_t)I.Mp * I.Mp;
@@ -261,6 +267,7 @@ __global__ void gk_f32_to_f64(const GInst* gi) {
 }
 
 __global__ void gk_resid_split(const GInst* gi) {
+  KFBI_PDL_ENTRY();
   const GInst& I = gi[blockIdx.y];
   ACTIVE_OR_RETURN(I);
   const size_t plane = (size_t)I.Mp * I.Mp;
@@ -293,6 +300,7 @@ __global__ void gk_resid_split(const GInst* gi) {
 }
 
 __global__ void gk_add_f32(const GInst* gi) {
+  KFBI_PDL_ENTRY();
   const GInst& I = gi[blockIdx.y];
   ACTIVE_OR_RETURN(I);
   const size_t plane = (size_t)I.Mp * I.Mp;
@@ -304,6 +312,7 @@ __global__ void gk_add_f32(const GInst* gi) {
 
 // FP64 extraction (as k_extract) into out (ub or Ax), complex interleaved.
 __global__ void gk_extract64(const GInst* gi, int which, int with_ft, int target) {
+  KFBI_PDL_ENTRY();
   const GInst& I = gi[blockIdx.y];
   ACTIVE_OR_RETURN(I);
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -358,6 +367,7 @@ __global__ void gk_extract64(const GInst* gi, int which, int with_ft, int target
 // ---- fast (sparse) application with the density V[j] ----------------------
 
 __global__ void gk_correct32_rv(const GInst* gi, const int* dj) {
+  KFBI_PDL_ENTRY();
   const GInst& I = gi[blockIdx.y];
   ACTIVE_OR_RETURN(I);
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
@@ -396,6 +406,7 @@ __global__ void gk_correct32_rv(const GInst* gi, const int* dj) {
 
 // blockIdx.z = instance; (x, y) = 32 x 32 output tile as in k_sparse_p1
 __global__ void __launch_bounds__(256) gk_sparse_p1(const GInst* gi) {
+  KFBI_PDL_ENTRY();
   const GInst& I = gi[blockIdx.z];
   ACTIVE_OR_RETURN(I);
   const int Mp = I.Mp;
@@ -435,6 +446,7 @@ __global__ void __launch_bounds__(256) gk_sparse_p1(const GInst* gi) {
 
 // Gather of the stencil values and extraction (as k_gather_extract) into W.
 __global__ void __launch_bounds__(192) gk_gather_extract(const GInst* gi, const int* dj) {
+  KFBI_PDL_ENTRY();
   const GInst& I = gi[blockIdx.y];
   ACTIVE_OR_RETURN(I);
   const int k = blockIdx.x;
@@ -524,6 +536,7 @@ __device__ double block_sum(double v, double* red) {
 
 // b = g - ub (real g for heat/wave, complex for Schroedinger)
 __global__ void gk_make_b(const GInst* gi) {
+  KFBI_PDL_ENTRY();
   const GInst& I = gi[blockIdx.y];
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= I.nb) return;
@@ -534,6 +547,7 @@ __global__ void gk_make_b(const GInst* gi) {
 
 // ||b|| into scal[0] (tol into scal[3]); one 1024-thread block per instance
 __global__ void __launch_bounds__(1024) gk_bnorm(const GInst* gi, double tol, int which) {
+  KFBI_PDL_ENTRY();
   const GInst& I = gi[blockIdx.y];
   __shared__ double red[32];
   const double2* v = which == 0 ? I.b : I.Rv;
@@ -548,22 +562,26 @@ __global__ void __launch_bounds__(1024) gk_bnorm(const GInst* gi, double tol, in
 
 // All instances' scalars and flags into one buffer for a single readback.
 __global__ void gk_gather_scal(const GInst* gi, double* out) {
+  KFBI_PDL_ENTRY();
   const GInst& I = gi[blockIdx.x];
   if (threadIdx.x < 8) out[8 * blockIdx.x + threadIdx.x] = I.scal[threadIdx.x];
 }
 
 __global__ void gk_set_tol(const GInst* gi, const double* tol, const int* sel) {
+  KFBI_PDL_ENTRY();
   const GInst& I = gi[blockIdx.x];
   if (threadIdx.x == 0 && sel[blockIdx.x]) I.scal[3] = tol[blockIdx.x];
 }
 
 __global__ void gk_clear_k(const GInst* gi) {
+  KFBI_PDL_ENTRY();
   const GInst& I = gi[blockIdx.x];
   if (threadIdx.x == 0) I.flags[1] = 0;
 }
 
 // Rv = b - Ax (Ax omitted for x_zero) and ||Rv|| into scal[1]
 __global__ void __launch_bounds__(1024) gk_residual(const GInst* gi) {
+  KFBI_PDL_ENTRY();
   const GInst& I = gi[blockIdx.y];
   ACTIVE_OR_RETURN(I);
   __shared__ double red[32];
@@ -587,6 +605,7 @@ __global__ void __launch_bounds__(1024) gk_residual(const GInst* gi) {
 // is kept, and A phi of a converged residual check is reused by the next
 // step's first residual.
 __global__ void gk_keep_uf(const GInst* gi) {
+  KFBI_PDL_ENTRY();
   const GInst& I = gi[blockIdx.y];
   ACTIVE_OR_RETURN(I);
   const size_t plane = (size_t)I.Mp * I.Mp;
@@ -597,6 +616,7 @@ __global__ void gk_keep_uf(const GInst* gi) {
 }
 
 __global__ void gk_add_uf(const GInst* gi) {
+  KFBI_PDL_ENTRY();
   const GInst& I = gi[blockIdx.y];
   ACTIVE_OR_RETURN(I);
   const size_t plane = (size_t)I.Mp * I.Mp;
@@ -608,6 +628,7 @@ __global__ void gk_add_uf(const GInst* gi) {
 
 // direction 0: Ax = cached A phi; 1: cache = Ax
 __global__ void gk_ax_cache(const GInst* gi, int direction) {
+  KFBI_PDL_ENTRY();
   const GInst& I = gi[blockIdx.y];
   ACTIVE_OR_RETURN(I);
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < I.nb; k += gridDim.x * blockDim.x) {
@@ -620,6 +641,7 @@ __global__ void gk_ax_cache(const GInst* gi, int direction) {
 
 // V0 = r/beta with r = Rv - A Dv (restart) or Rv (fresh cycle), g = (beta, 0..)
 __global__ void __launch_bounds__(1024) gk_restart(const GInst* gi, int with_ax) {
+  KFBI_PDL_ENTRY();
   const GInst& I = gi[blockIdx.y];
   ACTIVE_OR_RETURN(I);
   __shared__ double red[32];
@@ -692,6 +714,7 @@ __device__ __forceinline__ int grid_g(int nb) {
 }
 
 __global__ void __launch_bounds__(GT) gk_cgs_dots(const GInst* gi, const int* dj) {
+  KFBI_PDL_ENTRY();
   const GInst& I = gi[blockIdx.y];
   ACTIVE_OR_RETURN(I);
   const int G = grid_g(I.nb);
@@ -708,6 +731,7 @@ __global__ void __launch_bounds__(GT) gk_cgs_dots(const GInst* gi, const int* dj
 
 __global__ void __launch_bounds__(GT) gk_cgs_update(const GInst* gi, const int* dj, int first,
                                                     int mode) {
+  KFBI_PDL_ENTRY();
   const GInst& I = gi[blockIdx.y];
   ACTIVE_OR_RETURN(I);
   const int G = grid_g(I.nb);
@@ -769,6 +793,7 @@ __global__ void __launch_bounds__(GT) gk_cgs_update(const GInst* gi, const int* 
 }
 
 __global__ void __launch_bounds__(GT) gk_cgs_finalize(const GInst* gi, const int* dj) {
+  KFBI_PDL_ENTRY();
   const GInst& I = gi[blockIdx.y];
   ACTIVE_OR_RETURN(I);
   const int G = grid_g(I.nb);
@@ -838,6 +863,7 @@ __global__ void __launch_bounds__(GT) gk_cgs_finalize(const GInst* gi, const int
 
 // Dv += V y (k = flags[1] iterations); runs for every instance with k > 0.
 __global__ void __launch_bounds__(GT) gk_update(const GInst* gi) {
+  KFBI_PDL_ENTRY();
   const GInst& I = gi[blockIdx.y];
   const int k = I.flags[1];
   if (k == 0) return;
@@ -883,6 +909,7 @@ __global__ void __launch_bounds__(GT) gk_update(const GInst* gi) {
 
 // x += Dv; Dv = 0
 __global__ void gk_axpy(const GInst* gi, const int* sel) {
+  KFBI_PDL_ENTRY();
   const GInst& I = gi[blockIdx.y];
   if (!sel[blockIdx.y]) return;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < I.nb; e += gridDim.x * blockDim.x) {
@@ -893,6 +920,7 @@ __global__ void gk_axpy(const GInst* gi, const int* sel) {
 }
 
 __global__ void gk_zero_dv(const GInst* gi) {
+  KFBI_PDL_ENTRY();
   const GInst& I = gi[blockIdx.y];
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < I.nb; e += gridDim.x * blockDim.x)
     I.Dv[e] = make_double2(0.0, 0.0);
@@ -901,6 +929,7 @@ __global__ void gk_zero_dv(const GInst* gi) {
 // W = A Dv is needed at a restart: copy Dv into V[m] slot? -- the fast
 // operator reads V[j]; restarts place Dv into V[0] first (gk_dv_to_v0).
 __global__ void gk_dv_to_v0(const GInst* gi) {
+  KFBI_PDL_ENTRY();
   const GInst& I = gi[blockIdx.y];
   ACTIVE_OR_RETURN(I);
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < I.nb; e += gridDim.x * blockDim.x)
@@ -910,6 +939,7 @@ __global__ void gk_dv_to_v0(const GInst* gi) {
 // ---- step updates ----------------------------------------------------------
 
 __global__ void gk_step_update(const GInst* gi) {
+  KFBI_PDL_ENTRY();
   const GInst& I = gi[blockIdx.y];
   const size_t plane = (size_t)I.Mp * I.Mp;
   if (I.eq == KFBI_HEAT) {
@@ -943,6 +973,7 @@ __global__ void gk_step_update(const GInst* gi) {
 }
 
 __global__ void gk_set_flags(const GInst* gi, const int* act, int x_zero_from_state) {
+  KFBI_PDL_ENTRY();
   const GInst& I = gi[blockIdx.x];
   if (threadIdx.x == 0) {
     I.flags[0] = act[blockIdx.x];
@@ -951,6 +982,7 @@ __global__ void gk_set_flags(const GInst* gi, const int* act, int x_zero_from_st
 }
 
 __global__ void gk_bump(int* dj) {
+  KFBI_PDL_ENTRY();
   if (threadIdx.x == 0) *dj += 1;
 }
 
@@ -1055,6 +1087,8 @@ void build_passes(kfbi_batch* B) {
           d.a_hi = T->d_maps + kMapT2_hi; d.a_lo = T->d_maps + kMapT2_lo;
           d.out_hi = T->U; d.out_lo = nullptr; d.mode = 2; d.ct0 = T->ct0; d.nct = T->nt3; break;
       }
+      d.o_hi = tc_out_map(T, d.out_hi);
+      d.o_lo = d.out_lo ? tc_out_map(T, d.out_lo) : nullptr;
       ds[i] = d;
     }
     // tile order: optionally largest instances first (longest-processing-time

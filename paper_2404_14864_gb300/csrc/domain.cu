@@ -36,6 +36,7 @@ void set_global_error(const std::string& s) {
 template <bool C>
 __global__ void k_pad_mask(const double* __restrict__ src, const uint8_t* __restrict__ mask,
                            double* __restrict__ dst, int n1, int Mp) {
+  KFBI_PDL_ENTRY();
   const size_t plane = (size_t)Mp * Mp;
   for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < plane;
        idx += (size_t)gridDim.x * blockDim.x) {
@@ -58,6 +59,7 @@ __global__ void k_pad_mask(const double* __restrict__ src, const uint8_t* __rest
 // Padded planes -> caller layout (complex interleaved if C).
 template <bool C>
 __global__ void k_unpad(const double* __restrict__ src, double* __restrict__ dst, int n1, int Mp) {
+  KFBI_PDL_ENTRY();
   const size_t plane = (size_t)Mp * Mp;
   const size_t n = (size_t)n1 * n1;
   for (size_t s = blockIdx.x * (size_t)blockDim.x + threadIdx.x; s < n;
@@ -84,6 +86,7 @@ __global__ void k_correct(double* __restrict__ R, size_t plane, const double* __
                           const double* __restrict__ beta, const int* __restrict__ fidx,
                           const double* __restrict__ fcoef, int n_irr, int n_arms, int nb,
                           const double* __restrict__ phi, int ps, double kre, double kim) {
+  KFBI_PDL_ENTRY();
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= n_irr) return;
   const int off = irr_off[n];
@@ -128,6 +131,7 @@ __global__ void k_correct(double* __restrict__ R, size_t plane, const double* __
 __global__ void __launch_bounds__(256) k_dgemm_t(const double* __restrict__ A,
                                                  const double* __restrict__ S,
                                                  double* __restrict__ out, int Mp) {
+  KFBI_PDL_ENTRY();
   __shared__ double As[16][65];
   __shared__ double Bs[16][64];
   const size_t plane = (size_t)Mp * Mp;
@@ -174,6 +178,7 @@ __global__ void __launch_bounds__(256) k_dgemm_t(const double* __restrict__ A,
 __global__ void k_eigscale(double* __restrict__ T, size_t plane, int Mp, int n1,
                            const double* __restrict__ lam, double kre, double kim, double scale,
                            int cplx) {
+  KFBI_PDL_ENTRY();
   for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < plane;
        idx += (size_t)gridDim.x * blockDim.x) {
     const int a = (int)(idx / Mp), b = (int)(idx % Mp);
@@ -199,6 +204,7 @@ __global__ void k_extract(const double* __restrict__ U, size_t plane, const doub
                           const int* __restrict__ fidx, const double* __restrict__ fcoef, int nb,
                           const double* __restrict__ phi, int ps, double kre, double kim,
                           double* __restrict__ out, int os) {
+  KFBI_PDL_ENTRY();
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= nb) return;
   double sr = 0.0, si = 0.0;

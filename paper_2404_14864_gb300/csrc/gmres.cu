@@ -54,6 +54,7 @@ __device__ double block_sum(double v, double* red) {
 // 2 non-finite), [3] tol
 __global__ void __launch_bounds__(kThreads) k_bnorm(const double2* __restrict__ b, int nb,
                                                      double* scal, double tol) {
+  KFBI_PDL_ENTRY();
   __shared__ double red[32];
   double s = 0.0;
   for (int e = threadIdx.x; e < nb; e += kThreads) s += b[e].x * b[e].x + b[e].y * b[e].y;
@@ -69,6 +70,7 @@ __global__ void __launch_bounds__(kThreads) k_restart(const double2* __restrict_
                                                        const double2* __restrict__ Ax,
                                                        double2* __restrict__ V0, double2* g,
                                                        int m, int nb, double* scal) {
+  KFBI_PDL_ENTRY();
   __shared__ double red[32];
   double s = 0.0;
   for (int e = threadIdx.x; e < nb; e += kThreads) {
@@ -150,6 +152,7 @@ template <bool C>
 __global__ void __launch_bounds__(GT) k_cgs_dots(const double2* __restrict__ V, int nb, int j,
                                                  const double2* __restrict__ w,
                                                  double2* __restrict__ part, int slice) {
+  KFBI_PDL_ENTRY();
   const int b = blockIdx.x, G = gridDim.x;
   const int e0 = b * slice, e1 = min(nb, e0 + slice);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -170,6 +173,7 @@ __global__ void __launch_bounds__(GT) k_cgs_update(const double2* __restrict__ V
                                                    double2* __restrict__ part_out,
                                                    double2* __restrict__ hcol, int first,
                                                    int mode, int slice) {
+  KFBI_PDL_ENTRY();
   __shared__ double2 h[65];
   const int b = blockIdx.x, G = gridDim.x;
   const int e0 = b * slice, e1 = min(nb, e0 + slice);
@@ -299,6 +303,7 @@ __global__ void __launch_bounds__(GT) k_cgs_finalize(double2* __restrict__ V, in
                                                      const double2* __restrict__ hcol, double2* H,
                                                      double* cs, double2* sn, double2* g, int m,
                                                      double* scal, int slice) {
+  KFBI_PDL_ENTRY();
   __shared__ double2 nrm[1];
   const int b = blockIdx.x, G = gridDim.x;
   const int e0 = b * slice, e1 = min(nb, e0 + slice);
@@ -472,6 +477,7 @@ __global__ void __launch_bounds__(CLT) k_arnoldi_cl(double2* __restrict__ V, int
                                                     double2* __restrict__ w, double2* H, double* cs,
                                                     double2* sn, double2* g, int m, double* scal,
                                                     int cached) {
+  KFBI_PDL_ENTRY();
   namespace cg = cooperative_groups;
   cg::cluster_group cl = cg::this_cluster();
   extern __shared__ double2 vs[];  // staged basis slice, [i][e - e0]
@@ -581,6 +587,7 @@ __global__ void __launch_bounds__(CLT) k_arnoldi_cl(double2* __restrict__ V, int
 __global__ void __launch_bounds__(GT) k_update_grid(const double2* __restrict__ V, int nb, int k,
                                                     const double2* H, const double2* g, int m,
                                                     double2* __restrict__ x, int slice) {
+  KFBI_PDL_ENTRY();
   __shared__ double2 y[64];
   const int b = blockIdx.x;
   const int e0 = b * slice, e1 = min(nb, e0 + slice);
@@ -743,13 +750,14 @@ static void arnoldi_step_cluster(kfbi_domain* D, bool C, int j, int CL, cudaStre
   const size_t vbytes = (size_t)(j + 1) * slice * sizeof(double2);
   const int cached = vbytes <= (size_t)VS_CAP ? 1 : 0;
   cfg.dynamicSmemBytes = cached ? vbytes : 0;
-  cudaLaunchAttribute at[1];
+  cudaLaunchAttribute at[2];
   at[0].id = cudaLaunchAttributeClusterDimension;
   at[0].val.clusterDim.x = CL;
   at[0].val.clusterDim.y = 1;
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
+  add_pdl_attr(cfg, at);
   double2* V = (double2*)D->d_V;
   double2* w = (double2*)D->d_W;
   void* tok = g_prof_on ? prof_begin(KFBI_PROF_KRYLOV, st) : nullptr;
@@ -872,6 +880,7 @@ __global__ void __launch_bounds__(kThreads) k_residual(const double2* __restrict
                                                         const double2* __restrict__ Ax,
                                                         double2* __restrict__ r, int nb,
                                                         double* scal) {
+  KFBI_PDL_ENTRY();
   __shared__ double red[32];
   double s = 0.0;
   for (int e = threadIdx.x; e < nb; e += kThreads) {
@@ -888,6 +897,7 @@ __global__ void __launch_bounds__(kThreads) k_residual(const double2* __restrict
 }
 
 __global__ void k_axpy(double2* __restrict__ x, const double2* __restrict__ d, int nb) {
+  KFBI_PDL_ENTRY();
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e < nb) {
     x[e].x += d[e].x;
@@ -990,12 +1000,14 @@ using namespace kfbi;
 
 namespace kfbi_cv {
 __global__ void k_to_cplx(const double* __restrict__ src, double* __restrict__ dst, int n, int C) {
+  KFBI_PDL_ENTRY();
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n) return;
   dst[2 * k] = C ? src[2 * k] : src[k];
   dst[2 * k + 1] = C ? src[2 * k + 1] : 0.0;
 }
 __global__ void k_from_cplx(const double* __restrict__ src, double* __restrict__ dst, int n, int C) {
+  KFBI_PDL_ENTRY();
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n) return;
   if (C) {

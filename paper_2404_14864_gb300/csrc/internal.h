@@ -9,6 +9,7 @@
 #include <stdexcept>
 #include <memory>
 #include <string>
+#include <utility>
 
 #include "kfbi.h"
 #include "plan.h"
@@ -27,11 +28,49 @@ void* prof_begin(int cls, cudaStream_t st);
 void prof_end(void* tok, cudaStream_t st);
 void prof_add_work(void* tok, double work);
 
+// Programmatic dependent launch.  Every library kernel is launched with
+// programmatic stream serialization (unless KFBI_PDL=0), so it can be
+// scheduled while the previous kernel of its stream drains; its first
+// statement, KFBI_PDL_ENTRY, waits for that kernel's completion and memory
+// before any global access and then lets the next kernel launch.  Stream
+// order is kept; what overlaps is the launch and block scheduling.  For a
+// kernel not launched as a dependent both instructions return at once.
+extern bool g_pdl;
+#define KFBI_PDL_ENTRY() \
+  asm volatile("griddepcontrol.wait;\n\tgriddepcontrol.launch_dependents;" ::: "memory")
+
+// Sets the programmatic-serialization attribute on a launch configuration
+// whose attrs array has room for one more entry.
+inline void add_pdl_attr(cudaLaunchConfig_t& cfg, cudaLaunchAttribute* at) {
+  if (!g_pdl) return;
+  at[cfg.numAttrs].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[cfg.numAttrs].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  ++cfg.numAttrs;
+}
+
+struct CudaError;
+[[noreturn]] void throw_launch_error(cudaError_t e);
+
+template <typename... P, typename... A>
+inline void launch_kernel(void (*kern)(P...), dim3 grid, dim3 block, size_t smem,
+                          cudaStream_t st, A&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  add_pdl_attr(cfg, at);
+  const cudaError_t e = cudaLaunchKernelEx(&cfg, kern, std::forward<A>(args)...);
+  if (e != cudaSuccess) throw_launch_error(e);
+}
+
 // Launch a kernel of a profiling class, count it and (if enabled) time it.
 #define KFBI_LAUNCH_P(cls, kern, grid, block, smem, stream, ...)                       \
   do {                                                                                  \
     void* tok_ = ::kfbi::g_prof_on ? ::kfbi::prof_begin((cls), (stream)) : nullptr;     \
-    kern<<<(grid), (block), (smem), (stream)>>>(__VA_ARGS__);                           \
+    ::kfbi::launch_kernel(kern, (grid), (block), (smem), (stream), __VA_ARGS__);        \
     if (tok_) ::kfbi::prof_end(tok_, (stream));                                         \
     ::kfbi::g_launches.fetch_add(1, std::memory_order_relaxed);                         \
   } while (0)
@@ -42,7 +81,7 @@ void prof_add_work(void* tok, double work);
 #define KFBI_LAUNCH_PW(cls, flops, kern, grid, block, smem, stream, ...)               \
   do {                                                                                  \
     void* tok_ = ::kfbi::g_prof_on ? ::kfbi::prof_begin((cls), (stream)) : nullptr;     \
-    kern<<<(grid), (block), (smem), (stream)>>>(__VA_ARGS__);                           \
+    ::kfbi::launch_kernel(kern, (grid), (block), (smem), (stream), __VA_ARGS__);        \
     if (tok_) {                                                                         \
       ::kfbi::prof_end(tok_, (stream));                                                 \
       ::kfbi::prof_add_work(tok_, (flops));                                             \
@@ -52,7 +91,7 @@ void prof_add_work(void* tok, double work);
 
 #define KFBI_LAUNCH(kern, grid, block, smem, stream, ...)                              \
   do {                                                                                  \
-    kern<<<(grid), (block), (smem), (stream)>>>(__VA_ARGS__);                           \
+    ::kfbi::launch_kernel(kern, (grid), (block), (smem), (stream), __VA_ARGS__);        \
     ::kfbi::g_launches.fetch_add(1, std::memory_order_relaxed);                         \
   } while (0)
 

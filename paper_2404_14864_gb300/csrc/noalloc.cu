@@ -38,6 +38,7 @@ static double* g_addr[kMaxDevices] = {nullptr};
 
 // S[a][i] = sin(pi a i / M) (a*i reduced mod 2M), zero padded; lambda_a.
 __global__ void k_na_tables(double* S, double* lam, int M, int Mp, double h) {
+  KFBI_PDL_ENTRY();
   const size_t plane = (size_t)Mp * Mp;
   const double pi = 3.14159265358979323846264338327950288;
   for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < plane;
@@ -62,6 +63,7 @@ __global__ void k_na_tables(double* S, double* lam, int M, int Mp, double h) {
 
 // caller layout (n1 x n1, interleaved if C) -> padded planes, zero padding
 __global__ void k_na_pad(const double* src, double* dst, int n1, int Mp, int C) {
+  KFBI_PDL_ENTRY();
   const size_t plane = (size_t)Mp * Mp;
   for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < plane;
        idx += (size_t)gridDim.x * blockDim.x) {
@@ -78,6 +80,7 @@ __global__ void k_na_pad(const double* src, double* dst, int n1, int Mp, int C) 
 }
 
 __global__ void k_na_unpad(const double* src, double* dst, int n1, int Mp, int C) {
+  KFBI_PDL_ENTRY();
   const size_t plane = (size_t)Mp * Mp;
   const size_t n = (size_t)n1 * n1;
   for (size_t s = blockIdx.x * (size_t)blockDim.x + threadIdx.x; s < n;

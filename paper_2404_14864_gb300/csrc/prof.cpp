@@ -1,5 +1,6 @@
 // Kernel-class timing with CUDA events (kfbi_profile_*).  Each timed launch
 // records an event pair on its stream; reading synchronises and sums them.
+#include <cstdlib>
 #include <mutex>
 #include <vector>
 
@@ -8,6 +9,12 @@
 namespace kfbi {
 
 bool g_prof_on = false;
+bool g_pdl = [] {
+  const char* e = std::getenv("KFBI_PDL");
+  return !(e && e[0] == '0');
+}();
+
+void throw_launch_error(cudaError_t e) { throw CudaError{e, "kernel launch"}; }
 unsigned g_prof_mask = 0;
 
 namespace {

@@ -23,6 +23,7 @@ namespace stp {
 
 __global__ void k_heat_init(double* F, double* u, const double* u0, const double* lap0,
                             const double* src, int n1, int Mp, double two_dt) {
+  KFBI_PDL_ENTRY();
   GRID_LOOP(Mp) {
     const int r = (int)(idx / Mp), c = (int)(idx % Mp);
     double f = 0.0, uu = 0.0;
@@ -39,6 +40,7 @@ __global__ void k_heat_init(double* F, double* u, const double* u0, const double
 __global__ void k_wave_init(double* F, double* Fprev, double* u, const double* u0,
                             const double* lap0, const double* u1, const double* lap1, int n1,
                             int Mp, double kappa, double c1) {
+  KFBI_PDL_ENTRY();
   GRID_LOOP(Mp) {
     const int r = (int)(idx / Mp), c = (int)(idx % Mp);
     double f = 0.0, fp = 0.0, uu = 0.0;
@@ -57,6 +59,7 @@ __global__ void k_wave_init(double* F, double* Fprev, double* u, const double* u
 // u* = u0 - i (dt/2) lap u0 (Step 1 of the Strang step), u = u0.
 __global__ void k_schr_init(double* ustar, double* u, const double* u0, const double* lap0,
                             int n1, int Mp, double half_dt) {
+  KFBI_PDL_ENTRY();
   const size_t plane = (size_t)Mp * Mp;
   GRID_LOOP(Mp) {
     const int r = (int)(idx / Mp), c = (int)(idx % Mp);
@@ -78,6 +81,7 @@ __global__ void k_schr_init(double* ustar, double* u, const double* u0, const do
 
 // f-tilde = -F on Omega, 0 outside (Eq. 3.25 with f = -F).
 __global__ void k_make_ft(double* ft, const double* F, const uint8_t* mask, int Mp) {
+  KFBI_PDL_ENTRY();
   GRID_LOOP(Mp) { ft[idx] = mask[idx] ? -F[idx] : 0.0; }
 }
 
@@ -86,6 +90,7 @@ __global__ void k_make_ft(double* ft, const double* F, const uint8_t* mask, int 
 // Omega with kappa = i kim (Eq. 3.12: Delta u - kappa u = -kappa u**).
 __global__ void k_schr_bstep(double* uss, double* ft, const double* ustar, const double* v,
                              const uint8_t* mask, int n1, int Mp, double half_dt, double kim) {
+  KFBI_PDL_ENTRY();
   const size_t plane = (size_t)Mp * Mp;
   GRID_LOOP(Mp) {
     const int r = (int)(idx / Mp), c = (int)(idx % Mp);
@@ -109,6 +114,7 @@ __global__ void k_schr_bstep(double* uss, double* ft, const double* ustar, const
 
 // b = g - u+[0, f-tilde], complex interleaved; g is real unless C.
 __global__ void k_make_b(double* b, const double* g, const double* ub, int nb, int C) {
+  KFBI_PDL_ENTRY();
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= nb) return;
   const double gr = C ? g[2 * k] : g[k], gi = C ? g[2 * k + 1] : 0.0;
@@ -119,6 +125,7 @@ __global__ void k_make_b(double* b, const double* g, const double* ub, int nb, i
 // Heat: u = U; F^{n+2} = (4/dt) U - F^{n+1} + src.
 __global__ void k_heat_update(double* u, double* F, const double* U, const double* src, int n1,
                               int Mp, double four_dt) {
+  KFBI_PDL_ENTRY();
   GRID_LOOP(Mp) {
     const int r = (int)(idx / Mp), c = (int)(idx % Mp);
     const double uu = U[idx];
@@ -132,6 +139,7 @@ __global__ void k_heat_update(double* u, double* F, const double* U, const doubl
 // Wave: F^{n+2} = (kappa/theta) U - ((1-2theta)/theta) F^{n+1} - F^n.
 __global__ void k_wave_update(double* u, double* F, double* Fprev, const double* U, int Mp,
                               double k_theta, double c1) {
+  KFBI_PDL_ENTRY();
   GRID_LOOP(Mp) {
     const double uu = U[idx], f = F[idx];
     const double fn = k_theta * uu - c1 * f - Fprev[idx];
@@ -144,6 +152,7 @@ __global__ void k_wave_update(double* u, double* F, double* Fprev, const double*
 // Strang: u = U; next u* = 2 U - u**.
 __global__ void k_schr_update(double* u, double* ustar, const double* U, const double* uss,
                               int Mp) {
+  KFBI_PDL_ENTRY();
   const size_t plane = (size_t)Mp * Mp;
   GRID_LOOP(Mp) {
     for (int p = 0; p < 2; ++p) {
@@ -155,6 +164,7 @@ __global__ void k_schr_update(double* u, double* ustar, const double* U, const d
 }
 
 __global__ void k_copy_phi(const double* src, double* dst, int nb, int C) {
+  KFBI_PDL_ENTRY();
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= nb) return;
   if (C) {
@@ -174,6 +184,7 @@ using namespace stp;
 // the accurate operator (FP64-level on either domain precision).
 // Superposition of the refined solve: U = W phi (in U) + Y f-tilde.
 __global__ void k_add_grid(double* __restrict__ U, const double* __restrict__ uf, size_t n) {
+  KFBI_PDL_ENTRY();
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
        i += (size_t)gridDim.x * blockDim.x)
     U[i] += uf[i];

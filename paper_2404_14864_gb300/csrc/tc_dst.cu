@@ -18,10 +18,14 @@
 //     released by its own commit;
 //   - warps 2-9 drain each finished accumulator with tcgen05.ld (one output
 //     row c per thread, half of the r columns per warp group) into FP32
-//     registers, adding the two halves, then store their 64 consecutive r
-//     values with vector stores; the epilogue splits the result into the
-//     next pass's TF32 pair, applies the eigenvalue division of the box
-//     solve (pass 2, real kappa) or writes plain FP32 (pass 4).
+//     registers, adding the two halves.  The epilogue splits the result
+//     into the next pass's TF32 pair, applies the eigenvalue division of
+//     the box solve (pass 2, real kappa) or keeps plain FP32 (pass 4), and
+//     writes it through shared memory: each warp group stages 32-column
+//     boxes in the 128B-swizzled layout of the output's tensor map and one
+//     thread stores them with TMA (cp.async.bulk.tensor, global <- shared).
+//     Row-per-thread global stores touched 32 lines per instruction and
+//     took longer than the whole K loop.
 // N = 256 is the tensor core's full width (three N = 64 products ran it at
 // about a third of its rate), and draining every second K-block halves the
 // commit round trips; the accumulator sums 64 K-terms, which keeps the
@@ -50,6 +54,7 @@ constexpr int S_BYTES = BC * BK * 4;          // 16 KiB: S_hi or S_lo
 constexpr int A_BYTES = BR * BK * 4;          // 16 KiB: A_hi or A_lo
 constexpr int STAGE_BYTES = 2 * S_BYTES + 2 * A_BYTES;  // S_hi, S_lo, A_hi, A_lo
 constexpr int RECV_BYTES = BC * (BR / 2) * 4;  // 32 KiB: half a tile from the peer CTA
+constexpr int BOX_FLOATS = BC * 32;            // one staged output box: 128 rows x 32 r (16 KiB)
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + RECV_BYTES + 1024 + 256;
 constexpr int NDRAIN = 8;                     // drain / epilogue warps
 constexpr int THREADS = 64 + 32 * NDRAIN;     // producer, MMA, drain warps
@@ -152,6 +157,57 @@ __device__ __forceinline__ void arrive_peer(uint32_t bar_addr) {
                : "memory");
 }
 
+__device__ __forceinline__ void st_shared_v4(uint32_t addr, float a, float b, float c, float d) {
+  asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "f"(a), "f"(b), "f"(c),
+               "f"(d)
+               : "memory");
+}
+
+// Byte offset of 16-byte chunk k of row `row` in a buffer of 128-byte-
+// aligned rows whose chunk index is XORed with row & 7: the 128B swizzle of
+// the tensor maps, and conflict-free for a quarter warp on consecutive rows.
+__device__ __forceinline__ uint32_t swz(int row, int row_bytes, int k) {
+  return (uint32_t)(row * row_bytes + ((k ^ (row & 7)) << 4));
+}
+
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, const void* src, int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
+          reinterpret_cast<uint64_t>(map)),
+      "r"(x), "r"(y), "r"(smem_u32(src))
+      : "memory");
+}
+
+__device__ __forceinline__ void bulk_commit() {
+  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+
+// The shared-memory source of every committed bulk store has been read.
+__device__ __forceinline__ void bulk_wait_read() {
+  asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
+
+// Every committed bulk store is complete.
+__device__ __forceinline__ void bulk_wait_all() {
+  asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+}
+
+// Barrier of the four warps of one drain half on an mbarrier of count 4:
+// bounded like every other wait, so a warp whose partners aborted returns
+// false instead of hanging.  n counts this thread's crossings.
+__device__ __forceinline__ bool half_sync(uint64_t* bar, int& n, int lane) {
+  __syncwarp();
+  if (lane == 0) mbar_arrive(bar);
+  const bool ok = mbar_wait(bar, (uint32_t)(n & 1));
+  ++n;
+  __syncwarp();
+  return ok;
+}
+
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar,
                                             int x, int y) {
   asm volatile(
@@ -245,7 +301,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_pass(const __grid_constant__ 
   uint64_t* done = acce + NACC;     // all MMAs retired
   uint64_t* rfull = done + 1;       // split K: the peer's half tile is in recv
   uint64_t* pfree = rfull + 1;      // split K: the peer has consumed what we sent
-  uint32_t* tmem_slot = (uint32_t*)(pfree + 1);
+  uint64_t* stb = pfree + 1;        // [2]: staging barrier of drain half 0 / 1
+  uint32_t* tmem_slot = (uint32_t*)(stb + 2);
   volatile int* s_state = (volatile int*)(tmem_slot + 1);  // [0] abort, [1] issued, [2] consumed
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -262,6 +319,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_pass(const __grid_constant__ 
     mbar_init(done, 1);
     mbar_init(rfull, 4 * 32);
     mbar_init(pfree, 4 * 32);
+    mbar_init(&stb[0], 4);
+    mbar_init(&stb[1], 4);
     s_state[0] = 0;
     s_state[1] = 0;
     s_state[2] = 0;
@@ -277,6 +336,9 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_pass(const __grid_constant__ 
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
+  // programmatic dependent launch: the set-up above touches no global
+  // memory; wait for the previous kernel here, then let the next one launch
+  KFBI_PDL_ENTRY();
   // tile loop: CTA pairs (split K) walk the tiles together, rank r taking
   // K-block half r; otherwise every CTA walks its own tiles
   const int split = ga.splitk == 2 ? 2 : 1;
@@ -366,10 +428,15 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_pass(const __grid_constant__ 
     const int q = warp & 3;
     const int half = (warp - 2) >> 2;
     const uint32_t lane_base = (uint32_t)(q * 32) << 16;
-    int g = 0, ex = 0;  // accumulator groups drained, tiles exchanged
+    int g = 0, ex = 0, nsb = 0;  // groups drained, tiles exchanged, staging barrier crossings
     bool ok = true;
     const int row = q * 32 + lane;  // output row c within the tile
     const uint32_t peer = (uint32_t)(rank ^ 1);
+    const bool elected = ((warp - 2) & 3) == 0 && lane == 0;  // issues this half's bulk stores
+    // staging: split K, the finishing half owns all of recv (two boxes);
+    // otherwise each half owns one box of it
+    float* stg = split == 2 ? recv : recv + half * BOX_FLOATS;
+    const int boxes = split == 2 ? 2 : 1;
     for (int t = unit0; t < ga.total && ok; t += nunits) {
       int lt;
       const PassDesc* d = tile_desc(ga, t, lt);
@@ -414,7 +481,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_pass(const __grid_constant__ 
       if (!ok || s_state[0]) break;
       if (split == 2) {
         // rank r finishes r-half r of the tile: send the other half's
-        // partial sums to the peer, receive the peer's partials of ours
+        // partial sums to the peer, receive the peer's partials of ours.
+        // recv rows are 256 bytes with the chunk index swizzled by row.
         const uint32_t ph = (uint32_t)(ex & 1);
         ++ex;
         if (half != rank) {
@@ -424,10 +492,11 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_pass(const __grid_constant__ 
             ok = false;
             break;
           }
-          const uint32_t dst = peer_addr(recv + row * RH, peer);
+          const uint32_t dst = peer_addr(recv, peer);
 #pragma unroll
-          for (int j = 0; j < RH; j += 4)
-            st_peer_v4(dst + 4u * j, acc[j], acc[j + 1], acc[j + 2], acc[j + 3]);
+          for (int k = 0; k < RH / 4; ++k)
+            st_peer_v4(dst + swz(row, RH * 4, k), acc[4 * k], acc[4 * k + 1], acc[4 * k + 2],
+                       acc[4 * k + 3]);
           arrive_peer(peer_addr(rfull, peer));
           continue;
         }
@@ -438,48 +507,97 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_pass(const __grid_constant__ 
           break;
         }
 #pragma unroll
-        for (int j = 0; j < RH; j += 4) {
-          const float4 v = *reinterpret_cast<const float4*>(recv + row * RH + j);
-          acc[j] += v.x;
-          acc[j + 1] += v.y;
-          acc[j + 2] += v.z;
-          acc[j + 3] += v.w;
+        for (int k = 0; k < RH / 4; ++k) {
+          const float4 v = *reinterpret_cast<const float4*>(
+              reinterpret_cast<const uint8_t*>(recv) + swz(row, RH * 4, k));
+          acc[4 * k] += v.x;
+          acc[4 * k + 1] += v.y;
+          acc[4 * k + 2] += v.z;
+          acc[4 * k + 3] += v.w;
+        }
+      }
+      // Epilogue: scale (pass 2), then per output array (hi, lo; or the
+      // plain FP32 plane) stage `boxes` boxes of 128 rows x 32 r and store
+      // them with TMA.  Box (y = p Mp + c0, x = first r) of the output's
+      // 2-D map [P Mp rows][Mp].
+      const int Mp = d->Mp, mode = d->mode;
+      const int p = r0 / Mp, rb = r0 - p * Mp + half * RH;  // first r of this half
+      if (mode == 1) {
+        const int c = c0 + row, n1 = d->n1;
+        const float lam_c = d->lam[c], kre = d->kre, scale = d->scale;
+#pragma unroll
+        for (int j = 0; j < RH; ++j) {
+          const int rr = rb + j;
+          acc[j] = (rr < n1 && c < n1) ? acc[j] * (scale / (d->lam[rr] + lam_c - kre)) : 0.f;
+        }
+      }
+      const uint32_t stg_base = smem_u32(stg);
+      const int narr = mode == 2 ? 1 : 2;
+      for (int a = 0; a < narr && ok; ++a) {
+        const CUtensorMap* om = a ? d->o_lo : d->o_hi;
+#pragma unroll
+        for (int bx = 0; bx < RH / 32; ++bx) {
+          const int slot = boxes == 2 ? bx : 0;
+          if (slot == 0) {
+            // a round starts: the staging buffer is free once the previous
+            // bulk store has read it (and, split K, every thread of the
+            // half has read the peer's partials)
+            if (elected) bulk_wait_read();
+            if (!half_sync(&stb[half], nsb, lane)) {
+              ok = false;
+              break;
+            }
+          }
+#pragma unroll
+          for (int k = 0; k < 8; ++k) {
+            float v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              const float x = acc[bx * 32 + 4 * k + u];
+              const float h = tf32_rna(x);
+              v[u] = mode == 2 ? x : (a == 0 ? h : tf32_rna(x - h));
+            }
+            st_shared_v4(stg_base + (uint32_t)(slot * BOX_FLOATS * 4) + swz(row, 128, k), v[0],
+                         v[1], v[2], v[3]);
+          }
+          if (slot == boxes - 1) {
+            // the round's boxes are staged: hand them to the TMA unit
+            fence_proxy_async();
+            if (!half_sync(&stb[half], nsb, lane)) {
+              ok = false;
+              break;
+            }
+            if (elected) {
+              for (int i = 0; i < boxes; ++i)
+                tma_store_2d(om, stg + i * BOX_FLOATS, rb + (bx - boxes + 1 + i) * 32, p * Mp + c0);
+              bulk_commit();
+            }
+          }
+        }
+      }
+      if (!ok) {
+        if (lane == 0) {
+          s_state[0] = 1;
+          atomicOr(ga.err, 64);
+        }
+        break;
+      }
+      if (split == 2) {
+        // recv may take the peer's next half tile once the stores have read it
+        if (elected) bulk_wait_read();
+        if (!half_sync(&stb[half], nsb, lane)) {
+          if (lane == 0) {
+            s_state[0] = 1;
+            atomicOr(ga.err, 64);
+          }
+          ok = false;
+          break;
         }
         arrive_peer(peer_addr(pfree, peer));
       }
-      // Epilogue: each thread owns output row c and stores its 64 r values
-      // (contiguous in memory) as 16-byte vectors.
-      const int Mp = d->Mp, n1 = d->n1, mode = d->mode;
-      const int c = c0 + q * 32 + lane;
-      const int p = r0 / Mp, rb = r0 - p * Mp + half * RH;  // first r of this thread's run
-      const size_t o0 = (size_t)p * Mp * Mp + (size_t)c * Mp + rb;
-      const float lam_c = (mode == 1) ? d->lam[c] : 0.f;
-      const float kre = d->kre, scale = d->scale;
-      float* oh = d->out_hi;
-      float* ol = d->out_lo;
-#pragma unroll
-      for (int j = 0; j < RH; j += 4) {
-        float x[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          x[u] = acc[j + u];
-          const int rr = rb + j + u;
-          if (mode == 1) x[u] = (rr < n1 && c < n1) ? x[u] * (scale / (d->lam[rr] + lam_c - kre)) : 0.f;
-        }
-        if (mode == 2) {
-          *reinterpret_cast<float4*>(oh + o0 + j) = make_float4(x[0], x[1], x[2], x[3]);
-        } else {
-          float hi[4], lo[4];
-#pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            hi[u] = tf32_rna(x[u]);
-            lo[u] = tf32_rna(x[u] - hi[u]);
-          }
-          *reinterpret_cast<float4*>(oh + o0 + j) = make_float4(hi[0], hi[1], hi[2], hi[3]);
-          *reinterpret_cast<float4*>(ol + o0 + j) = make_float4(lo[0], lo[1], lo[2], lo[3]);
-        }
-      }
     }
+    // bulk stores complete before the CTA releases its shared memory
+    if (elected) bulk_wait_all();
   }
   __syncthreads();
   if (threadIdx.x == 0 && s_state[0]) {
@@ -513,6 +631,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_pass(const __grid_constant__ 
 // FP64 planes -> TF32 pairs (hi = tf32(x), lo = tf32(x - hi)).
 __global__ void k_split64(const double* __restrict__ src, float* __restrict__ hi,
                           float* __restrict__ lo, size_t n) {
+  KFBI_PDL_ENTRY();
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
        i += (size_t)gridDim.x * blockDim.x) {
     const double x = src[i];
@@ -532,6 +651,7 @@ __global__ void k_correct32(float* __restrict__ Rh, float* __restrict__ Rl, size
                             const int* __restrict__ fidx, const float* __restrict__ fcoef,
                             int n_irr, int n_arms, int nb, const double* __restrict__ phi, int ps,
                             float kre, float kim, float* __restrict__ rv) {
+  KFBI_PDL_ENTRY();
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= n_irr) return;
   const int off = irr_off[n];
@@ -594,6 +714,7 @@ __global__ void __launch_bounds__(256) k_sparse_p1(const float* __restrict__ rv,
                                                    int nrows, const float* __restrict__ S32,
                                                    float* __restrict__ Th, float* __restrict__ Tl,
                                                    int Mp, int P) {
+  KFBI_PDL_ENTRY();
   __shared__ float tile[2][32][33];
   const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
   const int tx = threadIdx.x, ty = threadIdx.y;
@@ -636,6 +757,7 @@ __global__ void __launch_bounds__(192)
                      const float* __restrict__ A, const float* __restrict__ B, int nb,
                      const double* __restrict__ phi, int ps, float kre, float kim,
                      double* __restrict__ out, int os) {
+  KFBI_PDL_ENTRY();
   __shared__ float Ush[6][2];
   const int k = blockIdx.x;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -700,6 +822,7 @@ __global__ void __launch_bounds__(192)
 __global__ void k_eig_split_cplx(float* __restrict__ hi, float* __restrict__ lo, size_t plane,
                                  int Mp, int n1, const double* __restrict__ lam, double kre,
                                  double kim, double scale) {
+  KFBI_PDL_ENTRY();
   for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < plane;
        idx += (size_t)gridDim.x * blockDim.x) {
     const int a = (int)(idx / Mp), b = (int)(idx % Mp);
@@ -726,6 +849,7 @@ __global__ void k_extract32(const float* __restrict__ U, size_t plane,
                             const float* __restrict__ fcoef, int nb,
                             const double* __restrict__ phi, int ps, float kre, float kim,
                             double* __restrict__ out, int os) {
+  KFBI_PDL_ENTRY();
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= nb) return;
   float sr = 0.f, si = 0.f;
@@ -771,6 +895,7 @@ __global__ void k_extract32(const float* __restrict__ U, size_t plane,
 }
 
 __global__ void k_f32_to_f64(const float* __restrict__ src, double* __restrict__ dst, size_t n) {
+  KFBI_PDL_ENTRY();
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
        i += (size_t)gridDim.x * blockDim.x)
     dst[i] = (double)src[i];
@@ -783,6 +908,7 @@ template <bool C>
 __global__ void k_resid_split(const double* __restrict__ R, const double* __restrict__ U,
                               float* __restrict__ hi, float* __restrict__ lo, int Mp, int n1,
                               double inv_h2, double kre, double kim) {
+  KFBI_PDL_ENTRY();
   const size_t plane = (size_t)Mp * Mp;
   for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < plane;
        idx += (size_t)gridDim.x * blockDim.x) {
@@ -812,6 +938,7 @@ __global__ void k_resid_split(const double* __restrict__ R, const double* __rest
 }
 
 __global__ void k_add_f32(double* __restrict__ dst, const float* __restrict__ src, size_t n) {
+  KFBI_PDL_ENTRY();
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
        i += (size_t)gridDim.x * blockDim.x)
     dst[i] += (double)src[i];
@@ -920,8 +1047,10 @@ TcDst* tc_create(kfbi_domain* D, const Plan& P) {
     make_map(&T->mT2_lo, T->T2l, Mp, 2 * Mp, BR);
     make_map(&T->mT1s_hi, T->T1sh, Mp, 2 * Mp, BR);
     make_map(&T->mT1s_lo, T->T1sl, Mp, 2 * Mp, BR);
-    const CUtensorMap maps[kNumMaps] = {T->mS_hi,  T->mS_lo,  T->mR_hi,   T->mR_lo,   T->mT1_hi,
-                                        T->mT1_lo, T->mT2_hi, T->mT2_lo, T->mT1s_hi, T->mT1s_lo};
+    make_map(&T->mU, T->U, Mp, 2 * Mp, BC);
+    const CUtensorMap maps[kNumMaps] = {T->mS_hi,  T->mS_lo,  T->mR_hi,   T->mR_lo,
+                                        T->mT1_hi, T->mT1_lo, T->mT2_hi,  T->mT2_lo,
+                                        T->mT1s_hi, T->mT1s_lo, T->mU};
     KFBI_CUDA(cudaMalloc(&T->d_maps, sizeof(maps)));
     T->bytes += (long long)sizeof(maps);
     KFBI_CUDA(cudaMemcpy(T->d_maps, maps, sizeof(maps), cudaMemcpyHostToDevice));
@@ -960,6 +1089,15 @@ long long tc_bytes_for(const Plan& P, int Mp) {
   return b + (long long)(kNumMaps * sizeof(CUtensorMap));
 }
 
+const CUtensorMap* tc_out_map(const TcDst* T, const float* out) {
+  if (out == T->T1h) return T->d_maps + kMapT1_hi;
+  if (out == T->T1l) return T->d_maps + kMapT1_lo;
+  if (out == T->T2h) return T->d_maps + kMapT2_hi;
+  if (out == T->T2l) return T->d_maps + kMapT2_lo;
+  if (out == T->U) return T->d_maps + kMapU;
+  throw Status{KFBI_ERR_ARG, "pass output is not one of the domain's planes"};
+}
+
 // Descriptor of one instance's pass: A operand maps (am_hi, am_lo: kMap*
 // indices), output, mode, K-block range and output column-tile range.
 static PassDesc pass_desc(TcDst* T, int am_hi, int am_lo, float* oh, float* ol, int mode, int P,
@@ -972,6 +1110,8 @@ static PassDesc pass_desc(TcDst* T, int am_hi, int am_lo, float* oh, float* ol, 
   d.b_lo = T->d_maps + kMapS_lo;
   d.out_hi = oh;
   d.out_lo = ol;
+  d.o_hi = tc_out_map(T, oh);
+  d.o_lo = ol ? tc_out_map(T, ol) : nullptr;
   d.lam = T->lam;
   d.Mp = T->Mp;
   d.n1 = T->n1;
@@ -1003,13 +1143,14 @@ void tc::launch_tc_pass(GroupArgs ga, int nsm, double work, cudaStream_t st) {
   cfg.blockDim = dim3(THREADS, 1, 1);
   cfg.dynamicSmemBytes = SMEM_BYTES;
   cfg.stream = st;
-  cudaLaunchAttribute at[1];
+  cudaLaunchAttribute at[2];
   at[0].id = cudaLaunchAttributeClusterDimension;
   at[0].val.clusterDim.x = pairs ? 2 : 1;
   at[0].val.clusterDim.y = 1;
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
   cfg.numAttrs = pairs ? 1 : 0;
+  add_pdl_attr(cfg, at);
   void* tok = g_prof_on ? prof_begin(KFBI_PROF_DST, st) : nullptr;
   KFBI_CUDA(cudaLaunchKernelEx(&cfg, k_tc_pass, ga));
   if (tok) {

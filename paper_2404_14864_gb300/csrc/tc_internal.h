@@ -23,6 +23,8 @@ struct PassDesc {
   const CUtensorMap* b_lo;
   float* out_hi;
   float* out_lo;
+  const CUtensorMap* o_hi;  // maps of out_hi / out_lo ([P Mp rows][Mp], box 32 x 128),
+  const CUtensorMap* o_lo;  // written by TMA stores; o_lo unused in mode 2
   const float* lam;
   int Mp, n1;
   int mode;  // 0: TF32 pair out, 1: eigenvalue division + pair, 2: plain fp32
@@ -59,7 +61,7 @@ extern const int kPassSmem;
 }  // namespace tc
 
 enum { kMapS_hi, kMapS_lo, kMapR_hi, kMapR_lo, kMapT1_hi, kMapT1_lo, kMapT2_hi, kMapT2_lo,
-       kMapT1s_hi, kMapT1s_lo, kNumMaps };
+       kMapT1s_hi, kMapT1s_lo, kMapU, kNumMaps };
 
 struct TcDst {
   int Mp = 0, n1 = 0;
@@ -76,10 +78,14 @@ struct TcDst {
   float *Rh = nullptr, *Rl = nullptr, *T1h = nullptr, *T1l = nullptr, *T2h = nullptr,
         *T2l = nullptr, *U = nullptr;
   int* err = nullptr;
-  CUtensorMap mS_hi, mS_lo, mR_hi, mR_lo, mT1_hi, mT1_lo, mT2_hi, mT2_lo;
+  CUtensorMap mS_hi, mS_lo, mR_hi, mR_lo, mT1_hi, mT1_lo, mT2_hi, mT2_lo, mU;
   int rhs_sparse_planes = 0;
   long long bytes = 0;
 };
 
+
+// Device tensor map of one of the domain's pass output planes (T1, T2 pairs
+// or U); throws for any other pointer.
+const CUtensorMap* tc_out_map(const TcDst* T, const float* out);
 
 }  // namespace kfbi
