@@ -18,6 +18,7 @@
 #include <cooperative_groups.h>
 
 #include "internal.h"
+#include "tc_internal.h"
 
 namespace kfbi {
 
@@ -478,6 +479,9 @@ __global__ void __launch_bounds__(CLT) k_arnoldi_cl(double2* __restrict__ V, int
                                                     double2* sn, double2* g, int m, double* scal,
                                                     int cached) {
   KFBI_PDL_ENTRY();
+  // a step queued ahead of an earlier step that converged does nothing
+  // (every CTA of the cluster reads the same flag and returns together)
+  KFBI_STOP_RETURN(scal + 2);
   namespace cg = cooperative_groups;
   cg::cluster_group cl = cg::this_cluster();
   extern __shared__ double2 vs[];  // staged basis slice, [i][e - e0]
@@ -670,6 +674,9 @@ void gmres_alloc(kfbi_domain* D) {
   KFBI_CUDA(cudaMemset(D->d_scal, 0, 8 * sizeof(double)));
   KFBI_CUDA(cudaMallocHost(&D->h_scal, 8 * sizeof(double)));
   std::memset(D->h_scal, 0, 8 * sizeof(double));
+  KFBI_CUDA(cudaMallocHost(&D->h_ring, 16 * sizeof(double)));
+  std::memset(D->h_ring, 0, 16 * sizeof(double));
+  for (cudaEvent_t& e : D->ev_ring) KFBI_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
 }
 
 void gmres_free(kfbi_domain* D) {
@@ -679,6 +686,12 @@ void gmres_free(kfbi_domain* D) {
     if (p) cudaFree(p);
   if (D->h_scal) cudaFreeHost(D->h_scal);
   D->h_scal = nullptr;
+  if (D->h_ring) cudaFreeHost(D->h_ring);
+  D->h_ring = nullptr;
+  for (cudaEvent_t& e : D->ev_ring) {
+    if (e) cudaEventDestroy(e);
+    e = nullptr;
+  }
 }
 
 static void read_scalars(kfbi_domain* D, cudaStream_t st) {
@@ -806,16 +819,60 @@ static void arnoldi_step(kfbi_domain* D, bool C, int j, cudaStream_t st) {
   KFBI_CHECK_LAUNCH();
 }
 
+// Sets the sparse-route stop flag of a mixed domain for the lifetime of a
+// GMRES call that queues iterations ahead, and clears it on every exit.
+struct StopScope {
+  TcDst* T;
+  StopScope(kfbi_domain* D, bool on) : T(on ? D->tc : nullptr) {
+    if (T) T->stop = D->d_scal + 2;
+  }
+  ~StopScope() {
+    if (T) T->stop = nullptr;
+  }
+};
+
 // GMRES(m) with the domain's hot-path operator (apply_internal), relative
 // tolerance tol, at most maxit iterations.
+//
+// Mixed domains with the cluster Arnoldi step queue one iteration ahead:
+// iteration j + 1 (and iteration 0, ahead of the restart's check) is in the
+// stream before the host reads iteration j's residual, so the GPU does not
+// wait for the host between iterations.  The scalars of each step are
+// copied into a two-slot pinned ring behind an event; the host reads slot s
+// before it queues snapshot s + 2.  When iteration j converged, the queued
+// iteration j + 1 finds the convergence flag set and its kernels return at
+// once; it would only have written H column j + 1, g[j + 1 .. j + 2] and
+// V[j + 2], none of which the update with k = j + 1 reads.
 static kfbi_status gmres_core(kfbi_domain* D, double kre, double kim, const double* b, double* x,
                               bool x_zero, double tol, int maxit, kfbi_solve_info* info,
                               cudaStream_t st) {
   const int m = D->restart, nb = D->nb;
+  const bool C = kim != 0.0;
   double2* V = (double2*)D->d_V;
   double2* W = (double2*)D->d_W;
   double2* H = (double2*)D->d_H;
   double2* g = (double2*)D->d_g;
+  const bool ahead = D->tc && D->n_irr > 0 && arnoldi_cluster_size() > 0;
+  StopScope scope(D, ahead);
+  long long seq = 0;  // scalar snapshots queued
+  auto snapshot = [&]() {
+    const int s = (int)(seq & 1);
+    KFBI_CUDA(cudaMemcpyAsync(D->h_ring + 8 * s, D->d_scal, 8 * sizeof(double),
+                              cudaMemcpyDeviceToHost, st));
+    KFBI_CUDA(cudaEventRecord(D->ev_ring[s], st));
+    return seq++;
+  };
+  auto read_snapshot = [&](long long q) {
+    const int s = (int)(q & 1);
+    KFBI_CUDA(cudaEventSynchronize(D->ev_ring[s]));
+    std::memcpy(D->h_scal, D->h_ring + 8 * s, 8 * sizeof(double));
+    check_device_flags(D);
+  };
+  auto iterate = [&](int j) {
+    apply_internal(D, kre, kim, (const double*)(V + (size_t)j * nb), 2, nullptr, D->d_W, 2,
+                   false, st);
+    arnoldi_step(D, C, j, st);
+  };
   KFBI_LAUNCH_P(KFBI_PROF_KRYLOV, k_bnorm, 1, kThreads, 0, st, (const double2*)b, nb, D->d_scal, tol);
   int it = 0;
   bool first = true;
@@ -827,7 +884,17 @@ static kfbi_status gmres_core(kfbi_domain* D, double kre, double kim, const doub
     KFBI_LAUNCH_P(KFBI_PROF_KRYLOV, k_restart, 1, kThreads, 0, st, (const double2*)b, skip_ax ? nullptr : W, V, g, m,
                 nb, D->d_scal);
     KFBI_CHECK_LAUNCH();
-    read_scalars(D, st);
+    long long s0 = 0;  // snapshot of the restart; iteration j's is s0 + 1 + j
+    if (ahead) {
+      s0 = snapshot();
+      if (it < maxit) {
+        iterate(0);
+        snapshot();
+      }
+      read_snapshot(s0);
+    } else {
+      read_scalars(D, st);
+    }
     if (info) info->applications += skip_ax ? 0 : 1;
     if (D->h_scal[0] == 0.0) {  // b = 0 -> x = 0
       KFBI_CUDA(cudaMemsetAsync(x, 0, 2 * (size_t)nb * sizeof(double), st));
@@ -839,12 +906,20 @@ static kfbi_status gmres_core(kfbi_domain* D, double kre, double kim, const doub
     first = false;
     int k = 0;
     for (int j = 0; j < m; ++j) {
-      apply_internal(D, kre, kim, (const double*)(V + (size_t)j * nb), 2, nullptr, D->d_W, 2,
-                     false, st);
-      arnoldi_step(D, kim != 0.0, j, st);
+      if (ahead) {
+        // iteration j is queued; queue j + 1 if it is within the cycle and
+        // the iteration budget, then read j
+        if (j + 1 < m && it + 2 <= maxit) {
+          iterate(j + 1);
+          snapshot();
+        }
+        read_snapshot(s0 + 1 + j);
+      } else {
+        iterate(j);
+        read_scalars(D, st);
+      }
       ++it;
       k = j + 1;
-      read_scalars(D, st);
       if (D->h_scal[2] != 0.0 || it >= maxit) break;
     }
     {

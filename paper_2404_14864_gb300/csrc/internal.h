@@ -39,6 +39,15 @@ extern bool g_pdl;
 #define KFBI_PDL_ENTRY() \
   asm volatile("griddepcontrol.wait;\n\tgriddepcontrol.launch_dependents;" ::: "memory")
 
+// Early exit of a kernel of a speculatively queued GMRES iteration: stop
+// points at the solver's convergence flag (nonzero once an earlier
+// iteration converged or failed); nullptr never stops.  Read after
+// KFBI_PDL_ENTRY, so the flag written by the previous kernel is visible.
+#define KFBI_STOP_RETURN(stop) \
+  do {                         \
+    if ((stop) && *(stop) != 0.0) return; \
+  } while (0)
+
 // Sets the programmatic-serialization attribute on a launch configuration
 // whose attrs array has room for one more entry.
 inline void add_pdl_attr(cudaLaunchConfig_t& cfg, cudaLaunchAttribute* at) {
@@ -216,6 +225,10 @@ struct kfbi_domain {
   double* d_Ax = nullptr;   // accurate operator output (2nb)
   double* d_scal = nullptr; // device scalars: [0] ||b||, [1] residual estimate, ...
   double* h_scal = nullptr; // pinned mirror
+  // GMRES lookahead: pinned snapshots of d_scal (two slots, in stream
+  // order) and the events that mark them
+  double* h_ring = nullptr;
+  cudaEvent_t ev_ring[2] = {nullptr, nullptr};
   cudaEvent_t ev_scal = nullptr;
 
   kfbi::TcDst* tc = nullptr;  // mixed-precision engine (precision == KFBI_MIXED_TF32)

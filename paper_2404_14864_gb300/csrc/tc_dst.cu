@@ -9,13 +9,14 @@
 //     of S_hi, S_lo, A_hi, A_lo into a 3-stage shared-memory ring with TMA
 //     (cp.async.bulk.tensor, 128B swizzle, mbarrier completion).  A_hi and
 //     A_lo land back to back, so together they are one 256-row operand;
-//   - warp 1 lane 0 issues tcgen05.mma kind::tf32 with M = 128 (c),
-//     N = 256 (r of A_hi, then r of A_lo), K = 8: S_hi [A_hi | A_lo] and
-//     S_lo [A_hi | A_lo] into one TMEM accumulator of 256 columns (columns
-//     j and 128 + j hold the hi and lo halves of output column j, so all
-//     four products are formed).  Two K-blocks go into one of two
-//     accumulators, which tcgen05.commit then publishes; each stage is
-//     released by its own commit;
+//   - warp 1 lane 0 issues tcgen05.mma kind::tf32 with M = 128 (c), K = 8:
+//     S_hi [A_hi | A_lo] with N = 256 (r of A_hi, then r of A_lo) into one
+//     TMEM accumulator of 256 columns, and S_lo A_hi with N = 128 into its
+//     second half, so columns j and 128 + j hold S_hi A_hi and
+//     S_hi A_lo + S_lo A_hi of output column j.  The fourth product
+//     S_lo A_lo (below FP32 resolution) is not formed.  Two K-blocks go
+//     into one of two accumulators, which tcgen05.commit then publishes;
+//     each stage is released by its own commit;
 //   - warps 2-9 drain each finished accumulator with tcgen05.ld (one output
 //     row c per thread, half of the r columns per warp group) into FP32
 //     registers, adding the two halves.  The epilogue splits the result
@@ -55,23 +56,31 @@ constexpr int A_BYTES = BR * BK * 4;          // 16 KiB: A_hi or A_lo
 constexpr int STAGE_BYTES = 2 * S_BYTES + 2 * A_BYTES;  // S_hi, S_lo, A_hi, A_lo
 constexpr int RECV_BYTES = BC * (BR / 2) * 4;  // 32 KiB: half a tile from the peer CTA
 constexpr int BOX_FLOATS = BC * 32;            // one staged output box: 128 rows x 32 r (16 KiB)
-constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + RECV_BYTES + 1024 + 256;
+constexpr int SMALL_BYTES = 512;  // descriptor copy, barriers, TMEM slot, state
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + RECV_BYTES + 1024 + SMALL_BYTES;
 constexpr int NDRAIN = 8;                     // drain / epilogue warps
 constexpr int THREADS = 64 + 32 * NDRAIN;     // producer, MMA, drain warps
 constexpr int NW = 2 * BR;                    // MMA width: [A_hi | A_lo]
 constexpr int NACC = 2;                       // TMEM accumulators in flight
-constexpr int KPA = 2;                        // K-blocks per accumulator
+constexpr int KPA = 4;                        // K-blocks per accumulator
 constexpr int RH = BR / 2;                    // r columns per drain warp group
 constexpr uint32_t TMEM_COLS = NACC * NW;     // 512 columns: all of TMEM
 // kind::tf32, D = F32, A = B = TF32, both K-major, N = NW, M = BC
-constexpr uint32_t IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(NW >> 3) << 17) |
-                           ((uint32_t)(BC >> 4) << 24);
+constexpr uint32_t idesc_tf32(int n) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) |
+         ((uint32_t)(BC >> 4) << 24);
+}
+constexpr uint32_t IDESC = idesc_tf32(NW);     // S_hi [A_hi | A_lo]
+constexpr uint32_t IDESC_LO = idesc_tf32(BR);  // S_lo A_hi
 constexpr long long WAIT_LIMIT = 4000000000LL;  // cycles (~2 s)
 
-__device__ __forceinline__ const PassDesc* tile_desc(const GroupArgs& ga, int t, int& lt) {
+// Descriptor of tile t (and its index within its instance).  A single
+// instance's descriptor is read from its shared-memory copy `one`.
+__device__ __forceinline__ const PassDesc* tile_desc(const GroupArgs& ga, const PassDesc* one,
+                                                     int t, int& lt) {
   if (!ga.descs) {
     lt = t;
-    return &ga.one;
+    return one;
   }
   int lo = 0, hi = ga.n_inst - 1;
   while (lo < hi) {
@@ -83,6 +92,12 @@ __device__ __forceinline__ const PassDesc* tile_desc(const GroupArgs& ga, int t,
   }
   lt = t - ga.prefix[lo];
   return ga.descs + lo;
+}
+
+// Tiles of an inactive instance, or of a speculative iteration after
+// convergence, are skipped (every role of the pass tests the same flags).
+__device__ __forceinline__ bool skip_desc(const PassDesc* d) {
+  return (d->active && *d->active == 0) || (d->stop && *d->stop != 0.0);
 }
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -208,6 +223,10 @@ __device__ __forceinline__ bool half_sync(uint64_t* bar, int& n, int lane) {
   return ok;
 }
 
+__device__ __forceinline__ void prefetch_map(const CUtensorMap* map) {
+  asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
+}
+
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar,
                                             int x, int y) {
   asm volatile(
@@ -228,11 +247,12 @@ __device__ __forceinline__ uint64_t desc_sw128(const void* p) {
   return d;
 }
 
-__device__ __forceinline__ void umma_tf32(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t acc) {
+__device__ __forceinline__ void umma_tf32(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc,
+                                          uint32_t acc) {
   asm volatile(
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
       " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
-      "l"(a), "l"(b), "r"(IDESC), "r"(acc));
+      "l"(a), "l"(b), "r"(idesc), "r"(acc));
 }
 
 __device__ __forceinline__ void umma_commit(uint64_t* bar) {
@@ -294,7 +314,9 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_pass(const __grid_constant__ 
   extern __shared__ uint8_t smem_raw[];
   uint8_t* tiles = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   float* recv = (float*)(tiles + STAGES * STAGE_BYTES);  // [BC rows][BR / 2]
-  uint64_t* full = (uint64_t*)(tiles + STAGES * STAGE_BYTES + RECV_BYTES);
+  uint8_t* small = tiles + STAGES * STAGE_BYTES + RECV_BYTES;
+  PassDesc* s_one = (PassDesc*)small;  // single-instance descriptor (128 bytes)
+  uint64_t* full = (uint64_t*)(small + 128);
   uint64_t* empty = full + STAGES;
   uint64_t* accf = empty + STAGES;  // accumulator b holds a finished group
   uint64_t* acce = accf + NACC;     // accumulator b has been drained
@@ -307,7 +329,18 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_pass(const __grid_constant__ 
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
+  static_assert(sizeof(PassDesc) <= 128, "descriptor copy slot");
+  if (threadIdx.x == 64 && !ga.descs) *s_one = ga.one;  // read as kernel parameters
   if (threadIdx.x == 0) {
+    if (!ga.descs) {
+      // the maps were written at domain set-up, long before any pass
+      prefetch_map(ga.one.b_hi);
+      prefetch_map(ga.one.b_lo);
+      prefetch_map(ga.one.a_hi);
+      prefetch_map(ga.one.a_lo);
+      prefetch_map(ga.one.o_hi);
+      if (ga.one.o_lo) prefetch_map(ga.one.o_lo);
+    }
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
@@ -352,8 +385,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_pass(const __grid_constant__ 
       bool abort = false;
       for (int t = unit0; t < ga.total && !abort; t += nunits) {
         int lt;
-        const PassDesc* d = tile_desc(ga, t, lt);
-        if (d->active && *d->active == 0) continue;
+        const PassDesc* d = tile_desc(ga, s_one, t, lt);
+        if (skip_desc(d)) continue;
         const int r0 = (lt / d->nct) * BR, c0 = (d->ct0 + lt % d->nct) * BC;
         const int kh = split == 2 ? (d->nk + 1) / 2 : d->nk;
         const int kbl = rank ? kh : 0, kbh = rank ? d->nk : kh;
@@ -384,8 +417,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_pass(const __grid_constant__ 
       bool abort = false;
       for (int t = unit0; t < ga.total && !abort; t += nunits) {
         int lt;
-        const PassDesc* d = tile_desc(ga, t, lt);
-        if (d->active && *d->active == 0) continue;
+        const PassDesc* d = tile_desc(ga, s_one, t, lt);
+        if (skip_desc(d)) continue;
         const int kh = split == 2 ? (d->nk + 1) / 2 : d->nk;
         const int kbl = rank ? kh : 0, kbh = rank ? d->nk : kh;
         for (int kb = kbl; kb < kbh; ++kb, ++g) {
@@ -408,8 +441,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_pass(const __grid_constant__ 
 #pragma unroll
           for (int k = 0; k < BK / 8; ++k) {
             const uint64_t o = (uint64_t)(2 * k);  // 8 tf32 = 32 bytes, in 16-byte units
-            umma_tf32(td, sh + o, aa + o, (first && k == 0) ? 0u : 1u);
-            umma_tf32(td, sl + o, aa + o, 1u);
+            umma_tf32(td, sh + o, aa + o, IDESC, (first && k == 0) ? 0u : 1u);
+            umma_tf32(td + BR, sl + o, aa + o, IDESC_LO, 1u);
           }
           umma_commit(&empty[s]);
           if (last) {
@@ -439,8 +472,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_pass(const __grid_constant__ 
     const int boxes = split == 2 ? 2 : 1;
     for (int t = unit0; t < ga.total && ok; t += nunits) {
       int lt;
-      const PassDesc* d = tile_desc(ga, t, lt);
-      if (d->active && *d->active == 0) continue;
+      const PassDesc* d = tile_desc(ga, s_one, t, lt);
+      if (skip_desc(d)) continue;
       const int r0 = (lt / d->nct) * BR, c0 = (d->ct0 + lt % d->nct) * BC;
       float acc[RH];
 #pragma unroll
@@ -650,8 +683,9 @@ __global__ void k_correct32(float* __restrict__ Rh, float* __restrict__ Rl, size
                             const float* __restrict__ alpha, const float* __restrict__ beta,
                             const int* __restrict__ fidx, const float* __restrict__ fcoef,
                             int n_irr, int n_arms, int nb, const double* __restrict__ phi, int ps,
-                            float kre, float kim, float* __restrict__ rv) {
+                            float kre, float kim, float* __restrict__ rv, const double* stop) {
   KFBI_PDL_ENTRY();
+  KFBI_STOP_RETURN(stop);
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= n_irr) return;
   const int off = irr_off[n];
@@ -713,8 +747,9 @@ __global__ void __launch_bounds__(256) k_sparse_p1(const float* __restrict__ rv,
                                                    const int* __restrict__ node_col, int rmin,
                                                    int nrows, const float* __restrict__ S32,
                                                    float* __restrict__ Th, float* __restrict__ Tl,
-                                                   int Mp, int P) {
+                                                   int Mp, int P, const double* stop) {
   KFBI_PDL_ENTRY();
+  KFBI_STOP_RETURN(stop);
   __shared__ float tile[2][32][33];
   const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
   const int tx = threadIdx.x, ty = threadIdx.y;
@@ -756,8 +791,9 @@ __global__ void __launch_bounds__(192)
                      size_t plane, const int* __restrict__ gidx, const float* __restrict__ w,
                      const float* __restrict__ A, const float* __restrict__ B, int nb,
                      const double* __restrict__ phi, int ps, float kre, float kim,
-                     double* __restrict__ out, int os) {
+                     double* __restrict__ out, int os, const double* stop) {
   KFBI_PDL_ENTRY();
+  KFBI_STOP_RETURN(stop);
   __shared__ float Ush[6][2];
   const int k = blockIdx.x;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -821,8 +857,9 @@ __global__ void __launch_bounds__(192)
 // Complex eigenvalue division on TF32 pairs (two planes), in FP64.
 __global__ void k_eig_split_cplx(float* __restrict__ hi, float* __restrict__ lo, size_t plane,
                                  int Mp, int n1, const double* __restrict__ lam, double kre,
-                                 double kim, double scale) {
+                                 double kim, double scale, const double* stop) {
   KFBI_PDL_ENTRY();
+  KFBI_STOP_RETURN(stop);
   for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < plane;
        idx += (size_t)gridDim.x * blockDim.x) {
     const int a = (int)(idx / Mp), b = (int)(idx % Mp);
@@ -1124,6 +1161,7 @@ static PassDesc pass_desc(TcDst* T, int am_hi, int am_lo, float* oh, float* ol, 
   d.kre = kre;
   d.scale = scale;
   d.active = nullptr;
+  d.stop = nullptr;
   return d;
 }
 
@@ -1185,7 +1223,7 @@ static void tc_box_solve(kfbi_domain* D, double kre, double kim, int P, cudaStre
               st);
   if (C)
     KFBI_LAUNCH_P(KFBI_PROF_GRID, k_eig_split_cplx, grid_for(plane, 256), 256, 0, st, T->T2h,
-                  T->T2l, plane, T->Mp, T->n1, D->d_lam, kre, kim, (2.0 / D->M) * (2.0 / D->M));
+                  T->T2l, plane, T->Mp, T->n1, D->d_lam, kre, kim, (2.0 / D->M) * (2.0 / D->M), nullptr);
   launch_pass(T, pass_desc(T, kMapT2_hi, kMapT2_lo, T->T1h, T->T1l, 0, P, 0.f, 0.f), st);
   launch_pass(T, pass_desc(T, kMapT1_hi, kMapT1_lo, T->U, nullptr, 2, P, 0.f, 0.f), st);
 }
@@ -1208,33 +1246,35 @@ static void tc_apply_sparse(kfbi_domain* D, double kre, double kim, const double
     KFBI_LAUNCH_P(KFBI_PROF_CORRECT, k_correct32<true>, (D->n_irr + 127) / 128, 128, 0, st, T->Rh,
                   T->Rl, plane, nullptr, D->d_irr_off, D->d_arm_start, D->d_arm_k0,
                   D->d_arm_alpha32, D->d_arm_beta32, D->d_arm_fidx, D->d_arm_fcoef32, D->n_irr,
-                  D->n_arms, D->nb, phi, ps, (float)kre, (float)kim, T->rv);
+                  D->n_arms, D->nb, phi, ps, (float)kre, (float)kim, T->rv, T->stop);
   else
     KFBI_LAUNCH_P(KFBI_PROF_CORRECT, k_correct32<false>, (D->n_irr + 127) / 128, 128, 0, st, T->Rh,
                   T->Rl, plane, nullptr, D->d_irr_off, D->d_arm_start, D->d_arm_k0,
                   D->d_arm_alpha32, D->d_arm_beta32, D->d_arm_fidx, D->d_arm_fcoef32, D->n_irr,
-                  D->n_arms, D->nb, phi, ps, (float)kre, (float)kim, T->rv);
+                  D->n_arms, D->nb, phi, ps, (float)kre, (float)kim, T->rv, T->stop);
   KFBI_LAUNCH_P(KFBI_PROF_SPARSE, k_sparse_p1, dim3(Mp / 32, (T->nrows + 31) / 32), dim3(32, 8), 0, st,
                 T->rv, D->n_irr, T->row_start, T->node_col, T->rmin, T->nrows, T->S32, T->T1sh,
-                T->T1sl, Mp, P);
+                T->T1sl, Mp, P, T->stop);
   const float scale = (float)((2.0 / D->M) * (2.0 / D->M));
-  launch_pass(T, pass_desc(T, kMapT1s_hi, kMapT1s_lo, T->T2h, T->T2l, C ? 0 : 1, P, (float)kre,
-                           scale, T->kb0, T->nk2),
-              st);
+  PassDesc d2 = pass_desc(T, kMapT1s_hi, kMapT1s_lo, T->T2h, T->T2l, C ? 0 : 1, P, (float)kre,
+                          scale, T->kb0, T->nk2);
+  d2.stop = T->stop;
+  launch_pass(T, d2, st);
   if (C)
     KFBI_LAUNCH_P(KFBI_PROF_GRID, k_eig_split_cplx, grid_for(plane, 256), 256, 0, st, T->T2h,
-                  T->T2l, plane, Mp, T->n1, D->d_lam, kre, kim, (2.0 / D->M) * (2.0 / D->M));
-  launch_pass(T, pass_desc(T, kMapT2_hi, kMapT2_lo, T->U, nullptr, 2, P, 0.f, 0.f, 0, -1, T->ct0,
-                           T->nt3),
-              st);
+                  T->T2l, plane, Mp, T->n1, D->d_lam, kre, kim, (2.0 / D->M) * (2.0 / D->M), T->stop);
+  PassDesc d3 = pass_desc(T, kMapT2_hi, kMapT2_lo, T->U, nullptr, 2, P, 0.f, 0.f, 0, -1, T->ct0,
+                          T->nt3);
+  d3.stop = T->stop;
+  launch_pass(T, d3, st);
   if (C)
     KFBI_LAUNCH_P(KFBI_PROF_EXTRACT, k_gather_extract<true>, D->nb, 192, 0, st, T->U, T->S32, Mp,
                   plane, D->d_node_gidx, D->d_node_w32, D->d_node_a32, D->d_node_b32, D->nb, phi,
-                  ps, (float)kre, (float)kim, out, os);
+                  ps, (float)kre, (float)kim, out, os, T->stop);
   else
     KFBI_LAUNCH_P(KFBI_PROF_EXTRACT, k_gather_extract<false>, D->nb, 192, 0, st, T->U, T->S32, Mp,
                   plane, D->d_node_gidx, D->d_node_w32, D->d_node_a32, D->d_node_b32, D->nb, phi,
-                  ps, (float)kre, (float)kim, out, os);
+                  ps, (float)kre, (float)kim, out, os, T->stop);
   KFBI_CHECK_LAUNCH();
 }
 
@@ -1263,12 +1303,12 @@ void tc_apply(kfbi_domain* D, double kre, double kim, const double* phi, int ps,
       KFBI_LAUNCH_P(KFBI_PROF_CORRECT, k_correct32<true>, (D->n_irr + 127) / 128, 128, 0, st,
                     T->Rh, T->Rl, plane, ft, D->d_irr_off, D->d_arm_start, D->d_arm_k0,
                     D->d_arm_alpha32, D->d_arm_beta32, D->d_arm_fidx, D->d_arm_fcoef32,
-                    D->n_irr, D->n_arms, D->nb, phi, ps, (float)kre, (float)kim, nullptr);
+                    D->n_irr, D->n_arms, D->nb, phi, ps, (float)kre, (float)kim, nullptr, nullptr);
     else
       KFBI_LAUNCH_P(KFBI_PROF_CORRECT, k_correct32<false>, (D->n_irr + 127) / 128, 128, 0, st,
                     T->Rh, T->Rl, plane, ft, D->d_irr_off, D->d_arm_start, D->d_arm_k0,
                     D->d_arm_alpha32, D->d_arm_beta32, D->d_arm_fidx, D->d_arm_fcoef32,
-                    D->n_irr, D->n_arms, D->nb, phi, ps, (float)kre, (float)kim, nullptr);
+                    D->n_irr, D->n_arms, D->nb, phi, ps, (float)kre, (float)kim, nullptr, nullptr);
   }
   tc_box_solve(D, kre, kim, P, st);
   if (out) {

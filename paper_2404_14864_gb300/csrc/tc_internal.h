@@ -35,6 +35,7 @@ struct PassDesc {
   int nrt;   // tiles along r (planes x Mp / BR)
   float kre, scale;
   const int* active;  // instance flag (nullptr: always); tiles of inactive instances are skipped
+  const double* stop; // speculative GMRES iteration: all tiles skipped while *stop != 0
 };
 
 // Tiles of all instances of a grouped launch, in prefix order.  A single
@@ -81,6 +82,9 @@ struct TcDst {
   CUtensorMap mS_hi, mS_lo, mR_hi, mR_lo, mT1_hi, mT1_lo, mT2_hi, mT2_lo, mU;
   int rhs_sparse_planes = 0;
   long long bytes = 0;
+  // while a GMRES cycle queues iterations ahead: the solver's convergence
+  // flag, passed to the kernels of the fast (sparse-route) application
+  const double* stop = nullptr;
 };
 
 
