@@ -55,7 +55,6 @@ constexpr int S_BYTES = BC * BK * 4;          // 16 KiB: S_hi or S_lo
 constexpr int A_BYTES = BR * BK * 4;          // 16 KiB: A_hi or A_lo
 constexpr int STAGE_BYTES = 2 * S_BYTES + 2 * A_BYTES;  // S_hi, S_lo, A_hi, A_lo
 constexpr int RECV_BYTES = BC * (BR / 2) * 4;  // 32 KiB: half a tile from the peer CTA
-constexpr int BOX_FLOATS = BC * 32;            // one staged output box: 128 rows x 32 r (16 KiB)
 constexpr int SMALL_BYTES = 512;  // descriptor copy, barriers, TMEM slot, state
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + RECV_BYTES + 1024 + SMALL_BYTES;
 constexpr int NDRAIN = 8;                     // drain / epilogue warps
@@ -161,12 +160,6 @@ __device__ __forceinline__ uint32_t peer_addr(const void* p, uint32_t rank) {
   return r;
 }
 
-__device__ __forceinline__ void st_peer_v4(uint32_t addr, float a, float b, float c, float d) {
-  asm volatile("st.shared::cluster.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "f"(a), "f"(b),
-               "f"(c), "f"(d)
-               : "memory");
-}
-
 __device__ __forceinline__ void arrive_peer(uint32_t bar_addr) {
   asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(bar_addr)
                : "memory");
@@ -197,6 +190,15 @@ __device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, const void*
       : "memory");
 }
 
+__device__ __forceinline__ void tma_store_2d_addr(const CUtensorMap* map, uint32_t src, int x,
+                                                  int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
+          reinterpret_cast<uint64_t>(map)),
+      "r"(x), "r"(y), "r"(src)
+      : "memory");
+}
+
 __device__ __forceinline__ void bulk_commit() {
   asm volatile("cp.async.bulk.commit_group;" ::: "memory");
 }
@@ -206,21 +208,26 @@ __device__ __forceinline__ void bulk_wait_read() {
   asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
 }
 
+// All but the most recent committed bulk group have read their source.
+__device__ __forceinline__ void bulk_wait_read1() {
+  asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+}
+
 // Every committed bulk store is complete.
 __device__ __forceinline__ void bulk_wait_all() {
   asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
 }
 
-// Barrier of the four warps of one drain half on an mbarrier of count 4:
-// bounded like every other wait, so a warp whose partners aborted returns
-// false instead of hanging.  n counts this thread's crossings.
-__device__ __forceinline__ bool half_sync(uint64_t* bar, int& n, int lane) {
-  __syncwarp();
-  if (lane == 0) mbar_arrive(bar);
-  const bool ok = mbar_wait(bar, (uint32_t)(n & 1));
-  ++n;
-  __syncwarp();
-  return ok;
+// Bulk copy of `bytes` from this CTA's shared memory to shared memory of a
+// CTA of the cluster (peer addresses from mapa), completing `bytes` of
+// transaction count on the peer's mbarrier.
+__device__ __forceinline__ void bulk_copy_to_peer(uint32_t dst, const void* src, uint32_t bytes,
+                                                  uint32_t peer_bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.shared::cta.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          dst),
+      "r"(smem_u32(src)), "r"(bytes), "r"(peer_bar)
+      : "memory");
 }
 
 __device__ __forceinline__ void prefetch_map(const CUtensorMap* map) {
@@ -323,8 +330,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_pass(const __grid_constant__ 
   uint64_t* done = acce + NACC;     // all MMAs retired
   uint64_t* rfull = done + 1;       // split K: the peer's half tile is in recv
   uint64_t* pfree = rfull + 1;      // split K: the peer has consumed what we sent
-  uint64_t* stb = pfree + 1;        // [2]: staging barrier of drain half 0 / 1
-  uint32_t* tmem_slot = (uint32_t*)(stb + 2);
+  uint32_t* tmem_slot = (uint32_t*)(pfree + 1);
   volatile int* s_state = (volatile int*)(tmem_slot + 1);  // [0] abort, [1] issued, [2] consumed
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -350,10 +356,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_pass(const __grid_constant__ 
       mbar_init(&acce[b], NDRAIN);
     }
     mbar_init(done, 1);
-    mbar_init(rfull, 4 * 32);
+    mbar_init(rfull, 1);  // the receiver's expect_tx; the peer's bulk copy completes the bytes
     mbar_init(pfree, 4 * 32);
-    mbar_init(&stb[0], 4);
-    mbar_init(&stb[1], 4);
     s_state[0] = 0;
     s_state[1] = 0;
     s_state[2] = 0;
@@ -461,20 +465,29 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_pass(const __grid_constant__ 
     const int q = warp & 3;
     const int half = (warp - 2) >> 2;
     const uint32_t lane_base = (uint32_t)(q * 32) << 16;
-    int g = 0, ex = 0, nsb = 0;  // groups drained, tiles exchanged, staging barrier crossings
+    int g = 0, ex = 0, nst = 0;  // groups drained, tiles exchanged, bulk stores of this warp
     bool ok = true;
     const int row = q * 32 + lane;  // output row c within the tile
     const uint32_t peer = (uint32_t)(rank ^ 1);
-    const bool elected = ((warp - 2) & 3) == 0 && lane == 0;  // issues this half's bulk stores
-    // staging: split K, the finishing half owns all of recv (two boxes);
-    // otherwise each half owns one box of it
-    float* stg = split == 2 ? recv : recv + half * BOX_FLOATS;
-    const int boxes = split == 2 ? 2 : 1;
+    const bool elected = ((warp - 2) & 3) == 0 && lane == 0;  // arms this half's receive barrier
+    // output staging: split K, two 4 KiB slots in this warp's 8 KiB of recv;
+    // otherwise one 4 KiB slot per drain warp
+    const int nslot = split == 2 ? 2 : 1;
+    const uint32_t wslot = smem_u32(recv) + (uint32_t)(split == 2 ? q * 8192 : (warp - 2) * 4096);
     for (int t = unit0; t < ga.total && ok; t += nunits) {
       int lt;
       const PassDesc* d = tile_desc(ga, s_one, t, lt);
       if (skip_desc(d)) continue;
       const int r0 = (lt / d->nct) * BR, c0 = (d->ct0 + lt % d->nct) * BC;
+      // eigenvalues of this tile's rows and columns (pass 2), loaded before
+      // the accumulation so their latency is hidden behind it
+      float lam_c = 0.f, lam_r0 = 0.f, lam_r1 = 0.f;
+      if (d->mode == 1) {
+        const int rb0 = r0 % d->Mp + half * RH;
+        lam_c = d->lam[c0 + row];
+        lam_r0 = d->lam[rb0 + lane];
+        lam_r1 = d->lam[rb0 + 32 + lane];
+      }
       float acc[RH];
 #pragma unroll
       for (int j = 0; j < RH; ++j) acc[j] = 0.f;
@@ -516,6 +529,10 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_pass(const __grid_constant__ 
         // rank r finishes r-half r of the tile: send the other half's
         // partial sums to the peer, receive the peer's partials of ours.
         // recv rows are 256 bytes with the chunk index swizzled by row.
+        // The sending half stages its partials in stage 0 of its own ring
+        // (a CTA pair owns exactly one tile, so the ring is idle once the
+        // last group is drained) and one thread moves the 32 KiB to the
+        // peer's recv with a bulk copy that completes on the peer's rfull.
         const uint32_t ph = (uint32_t)(ex & 1);
         ++ex;
         if (half != rank) {
@@ -525,14 +542,22 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_pass(const __grid_constant__ 
             ok = false;
             break;
           }
-          const uint32_t dst = peer_addr(recv, peer);
+          // this warp's 32 rows: 8 KiB at the same offset here and in recv
+          uint8_t* sreg = tiles + q * (RECV_BYTES / 4);
 #pragma unroll
           for (int k = 0; k < RH / 4; ++k)
-            st_peer_v4(dst + swz(row, RH * 4, k), acc[4 * k], acc[4 * k + 1], acc[4 * k + 2],
-                       acc[4 * k + 3]);
-          arrive_peer(peer_addr(rfull, peer));
+            st_shared_v4(smem_u32(tiles) + swz(row, RH * 4, k), acc[4 * k], acc[4 * k + 1],
+                         acc[4 * k + 2], acc[4 * k + 3]);
+          fence_proxy_async();
+          __syncwarp();
+          if (lane == 0) {
+            bulk_copy_to_peer(peer_addr(recv, peer) + (uint32_t)(q * (RECV_BYTES / 4)), sreg,
+                              (uint32_t)(RECV_BYTES / 4), peer_addr(rfull, peer));
+            bulk_commit();
+          }
           continue;
         }
+        if (elected) mbar_expect_tx(rfull, (uint32_t)RECV_BYTES);
         if (!mbar_wait_cluster(rfull, ph)) {
           s_state[0] = 1;
           atomicOr(ga.err, 32);
@@ -548,39 +573,51 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_pass(const __grid_constant__ 
           acc[4 * k + 2] += v.z;
           acc[4 * k + 3] += v.w;
         }
+        __syncwarp();  // every lane has read its rows before the warp stages over them
       }
       // Epilogue: scale (pass 2), then per output array (hi, lo; or the
-      // plain FP32 plane) stage `boxes` boxes of 128 rows x 32 r and store
-      // them with TMA.  Box (y = p Mp + c0, x = first r) of the output's
-      // 2-D map [P Mp rows][Mp].
+      // plain FP32 plane) and 32-column box, each warp stages its 32 rows
+      // (4 KiB, 128B-swizzled) and its lane 0 stores them with TMA: box
+      // (x = first r, y = p Mp + c0 + 32 q) of the output's 2-D store map
+      // [P Mp rows][Mp].  Warps never wait on one another: the staging
+      // slots lie in the warp's own rows of recv (split K: two slots, after
+      // the peer's partials there have been read) or its own 4 KiB of it.
       const int Mp = d->Mp, mode = d->mode;
       const int p = r0 / Mp, rb = r0 - p * Mp + half * RH;  // first r of this half
-      if (mode == 1) {
-        const int c = c0 + row, n1 = d->n1;
-        const float lam_c = d->lam[c], kre = d->kre, scale = d->scale;
-#pragma unroll
-        for (int j = 0; j < RH; ++j) {
-          const int rr = rb + j;
-          acc[j] = (rr < n1 && c < n1) ? acc[j] * (scale / (d->lam[rr] + lam_c - kre)) : 0.f;
-        }
-      }
-      const uint32_t stg_base = smem_u32(stg);
       const int narr = mode == 2 ? 1 : 2;
-      for (int a = 0; a < narr && ok; ++a) {
-        const CUtensorMap* om = a ? d->o_lo : d->o_hi;
+      const int y = p * Mp + c0 + q * 32;
+      const int c = c0 + row, n1 = d->n1;
+      const float kre = d->kre, scale = d->scale;
 #pragma unroll
-        for (int bx = 0; bx < RH / 32; ++bx) {
-          const int slot = boxes == 2 ? bx : 0;
-          if (slot == 0) {
-            // a round starts: the staging buffer is free once the previous
-            // bulk store has read it (and, split K, every thread of the
-            // half has read the peer's partials)
-            if (elected) bulk_wait_read();
-            if (!half_sync(&stb[half], nsb, lane)) {
-              ok = false;
-              break;
-            }
+      for (int bx = 0; bx < RH / 32; ++bx) {
+        if (mode == 1) {
+          // eigenvalue division of the box solve: lam[r] is the same for every
+          // row, so each lane loads one and the warp shares them
+          const int r_lane = rb + bx * 32 + lane;
+          const float lam_r = bx ? lam_r1 : lam_r0;
+          // padded rows and columns (index n1 and beyond) are zero
+          const float cs = c < n1 ? scale : 0.f;
+          const unsigned valid = __ballot_sync(0xffffffffu, r_lane < n1);
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const float den = __shfl_sync(0xffffffffu, lam_r, j) + lam_c - kre;
+            acc[bx * 32 + j] *= ((valid >> j) & 1u) ? __fdividef(cs, den) : 0.f;
           }
+        }
+        for (int a = 0; a < narr; ++a) {
+          const CUtensorMap* om = a ? d->o_lo : d->o_hi;
+          const int slot = nslot == 2 ? (nst & 1) : 0;
+          if (nst >= nslot) {
+            // the slot's previous store has read it
+            if (lane == 0) {
+              if (nslot == 2)
+                bulk_wait_read1();
+              else
+                bulk_wait_read();
+            }
+            __syncwarp();
+          }
+          const uint32_t sb = wslot + (uint32_t)(slot * 4096);
 #pragma unroll
           for (int k = 0; k < 8; ++k) {
             float v[4];
@@ -590,47 +627,26 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_pass(const __grid_constant__ 
               const float h = tf32_rna(x);
               v[u] = mode == 2 ? x : (a == 0 ? h : tf32_rna(x - h));
             }
-            st_shared_v4(stg_base + (uint32_t)(slot * BOX_FLOATS * 4) + swz(row, 128, k), v[0],
-                         v[1], v[2], v[3]);
+            st_shared_v4(sb + swz(lane, 128, k), v[0], v[1], v[2], v[3]);
           }
-          if (slot == boxes - 1) {
-            // the round's boxes are staged: hand them to the TMA unit
-            fence_proxy_async();
-            if (!half_sync(&stb[half], nsb, lane)) {
-              ok = false;
-              break;
-            }
-            if (elected) {
-              for (int i = 0; i < boxes; ++i)
-                tma_store_2d(om, stg + i * BOX_FLOATS, rb + (bx - boxes + 1 + i) * 32, p * Mp + c0);
-              bulk_commit();
-            }
+          fence_proxy_async();
+          __syncwarp();
+          if (lane == 0) {
+            tma_store_2d_addr(om, sb, rb + bx * 32, y);
+            bulk_commit();
           }
+          ++nst;
         }
-      }
-      if (!ok) {
-        if (lane == 0) {
-          s_state[0] = 1;
-          atomicOr(ga.err, 64);
-        }
-        break;
       }
       if (split == 2) {
         // recv may take the peer's next half tile once the stores have read it
-        if (elected) bulk_wait_read();
-        if (!half_sync(&stb[half], nsb, lane)) {
-          if (lane == 0) {
-            s_state[0] = 1;
-            atomicOr(ga.err, 64);
-          }
-          ok = false;
-          break;
-        }
+        if (lane == 0) bulk_wait_read();
+        __syncwarp();
         arrive_peer(peer_addr(pfree, peer));
       }
     }
-    // bulk stores complete before the CTA releases its shared memory
-    if (elected) bulk_wait_all();
+    // bulk stores and copies complete before the CTA releases its shared memory
+    if (lane == 0) bulk_wait_all();
   }
   __syncthreads();
   if (threadIdx.x == 0 && s_state[0]) {
@@ -1084,10 +1100,15 @@ TcDst* tc_create(kfbi_domain* D, const Plan& P) {
     make_map(&T->mT2_lo, T->T2l, Mp, 2 * Mp, BR);
     make_map(&T->mT1s_hi, T->T1sh, Mp, 2 * Mp, BR);
     make_map(&T->mT1s_lo, T->T1sl, Mp, 2 * Mp, BR);
-    make_map(&T->mU, T->U, Mp, 2 * Mp, BC);
+    make_map(&T->sT1_hi, T->T1h, Mp, 2 * Mp, 32);
+    make_map(&T->sT1_lo, T->T1l, Mp, 2 * Mp, 32);
+    make_map(&T->sT2_hi, T->T2h, Mp, 2 * Mp, 32);
+    make_map(&T->sT2_lo, T->T2l, Mp, 2 * Mp, 32);
+    make_map(&T->sU, T->U, Mp, 2 * Mp, 32);
     const CUtensorMap maps[kNumMaps] = {T->mS_hi,  T->mS_lo,  T->mR_hi,   T->mR_lo,
                                         T->mT1_hi, T->mT1_lo, T->mT2_hi,  T->mT2_lo,
-                                        T->mT1s_hi, T->mT1s_lo, T->mU};
+                                        T->mT1s_hi, T->mT1s_lo, T->sT1_hi, T->sT1_lo,
+                                        T->sT2_hi, T->sT2_lo, T->sU};
     KFBI_CUDA(cudaMalloc(&T->d_maps, sizeof(maps)));
     T->bytes += (long long)sizeof(maps);
     KFBI_CUDA(cudaMemcpy(T->d_maps, maps, sizeof(maps), cudaMemcpyHostToDevice));
@@ -1127,11 +1148,11 @@ long long tc_bytes_for(const Plan& P, int Mp) {
 }
 
 const CUtensorMap* tc_out_map(const TcDst* T, const float* out) {
-  if (out == T->T1h) return T->d_maps + kMapT1_hi;
-  if (out == T->T1l) return T->d_maps + kMapT1_lo;
-  if (out == T->T2h) return T->d_maps + kMapT2_hi;
-  if (out == T->T2l) return T->d_maps + kMapT2_lo;
-  if (out == T->U) return T->d_maps + kMapU;
+  if (out == T->T1h) return T->d_maps + kStT1_hi;
+  if (out == T->T1l) return T->d_maps + kStT1_lo;
+  if (out == T->T2h) return T->d_maps + kStT2_hi;
+  if (out == T->T2l) return T->d_maps + kStT2_lo;
+  if (out == T->U) return T->d_maps + kStU;
   throw Status{KFBI_ERR_ARG, "pass output is not one of the domain's planes"};
 }
 
@@ -1172,7 +1193,9 @@ double tc::pass_flops(const PassDesc& d) {
 }
 
 void tc::launch_tc_pass(GroupArgs ga, int nsm, double work, cudaStream_t st) {
-  if (ga.splitk < 1) ga.splitk = 2 * ga.total <= nsm ? 2 : 1;
+  // CTA pairs only when every pair owns exactly one tile (the pair
+  // exchange reuses the idle stage ring)
+  if (ga.splitk < 1 || (ga.splitk == 2 && 2 * ga.total > nsm)) ga.splitk = 2 * ga.total <= nsm ? 2 : 1;
   const int pairs = ga.splitk == 2;
   const int grid = pairs ? 2 * std::min(ga.total, nsm / 2) : std::min(ga.total, nsm);
   if (grid <= 0) return;

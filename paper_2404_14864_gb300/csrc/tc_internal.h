@@ -23,7 +23,7 @@ struct PassDesc {
   const CUtensorMap* b_lo;
   float* out_hi;
   float* out_lo;
-  const CUtensorMap* o_hi;  // maps of out_hi / out_lo ([P Mp rows][Mp], box 32 x 128),
+  const CUtensorMap* o_hi;  // store maps of out_hi / out_lo ([P Mp rows][Mp], box 32 x 32),
   const CUtensorMap* o_lo;  // written by TMA stores; o_lo unused in mode 2
   const float* lam;
   int Mp, n1;
@@ -61,8 +61,10 @@ extern const int kPassSmem;
 
 }  // namespace tc
 
+// Load maps (box 32 x 128 rows) and, for the pass outputs, store maps
+// (box 32 x 32 rows: one drain warp's rows).
 enum { kMapS_hi, kMapS_lo, kMapR_hi, kMapR_lo, kMapT1_hi, kMapT1_lo, kMapT2_hi, kMapT2_lo,
-       kMapT1s_hi, kMapT1s_lo, kMapU, kNumMaps };
+       kMapT1s_hi, kMapT1s_lo, kStT1_hi, kStT1_lo, kStT2_hi, kStT2_lo, kStU, kNumMaps };
 
 struct TcDst {
   int Mp = 0, n1 = 0;
@@ -79,7 +81,8 @@ struct TcDst {
   float *Rh = nullptr, *Rl = nullptr, *T1h = nullptr, *T1l = nullptr, *T2h = nullptr,
         *T2l = nullptr, *U = nullptr;
   int* err = nullptr;
-  CUtensorMap mS_hi, mS_lo, mR_hi, mR_lo, mT1_hi, mT1_lo, mT2_hi, mT2_lo, mU;
+  CUtensorMap mS_hi, mS_lo, mR_hi, mR_lo, mT1_hi, mT1_lo, mT2_hi, mT2_lo;
+  CUtensorMap sT1_hi, sT1_lo, sT2_hi, sT2_lo, sU;  // store maps
   int rhs_sparse_planes = 0;
   long long bytes = 0;
   // while a GMRES cycle queues iterations ahead: the solver's convergence
