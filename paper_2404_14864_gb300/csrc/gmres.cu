@@ -837,7 +837,9 @@ struct StopScope {
 // Mixed domains with the cluster Arnoldi step queue one iteration ahead:
 // iteration j + 1 (and iteration 0, ahead of the restart's check) is in the
 // stream before the host reads iteration j's residual, so the GPU does not
-// wait for the host between iterations.  The scalars of each step are
+// wait for the host between iterations; the exception is an iteration that
+// the residual history predicts to be the last one (the previous residual
+// times the previous reduction ratio within 3x of the target).  The scalars of each step are
 // copied into a two-slot pinned ring behind an event; the host reads slot s
 // before it queues snapshot s + 2.  When iteration j converged, the queued
 // iteration j + 1 finds the convergence flag set and its kernels return at
@@ -905,15 +907,29 @@ static kfbi_status gmres_core(kfbi_domain* D, double kre, double kim, const doub
     if (D->h_scal[2] != 0.0 || it >= maxit) break;
     first = false;
     int k = 0;
+    int queued = ahead && it < maxit ? 0 : -1;  // last iteration of this cycle in the stream
+    double res1 = D->h_scal[1], res2 = 0.0;      // residual estimates after j - 1 and j - 2
     for (int j = 0; j < m; ++j) {
       if (ahead) {
-        // iteration j is queued; queue j + 1 if it is within the cycle and
-        // the iteration budget, then read j
-        if (j + 1 < m && it + 2 <= maxit) {
+        if (queued < j) {
+          iterate(j);
+          snapshot();
+          queued = j;
+        }
+        // queue j + 1 before reading j, unless j is expected to converge:
+        // GMRES residuals fall at a fairly steady rate, and a queued
+        // iteration after convergence still costs its (early-exiting)
+        // launches
+        const double target = D->h_scal[3] * D->h_scal[0];
+        const bool likely_last = res2 > 0.0 && res1 * (res1 / res2) <= 3.0 * target;
+        if (j + 1 < m && it + 2 <= maxit && !likely_last) {
           iterate(j + 1);
           snapshot();
+          queued = j + 1;
         }
         read_snapshot(s0 + 1 + j);
+        res2 = res1;
+        res1 = D->h_scal[1];
       } else {
         iterate(j);
         read_scalars(D, st);
