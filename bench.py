@@ -302,10 +302,10 @@ def run_ours(args, rank, world, local_rank):
 
 
 # DRAM bytes per launch of the mixed DST pass at the 1024^2 wave workload
-# (dram__bytes_read.sum + dram__bytes_write.sum from one ncu --set full
-# capture of three dense passes of the timed step, mean).  Reset to None
-# whenever k_tc_pass changes until it is captured again.
-TC_PASS_TRAFFIC_1024 = (16.845568e6 + 256 + 16.849920e6 + 768 + 16.845568e6 + 256) / 3.0
+# (dram__bytes_read.sum + dram__bytes_write.sum of a dense pass, from one
+# ncu --set full capture of the timed step).  Reset to None whenever
+# k_tc_pass changes until it is captured again.
+TC_PASS_TRAFFIC_1024 = 16.845824e6 + 0.0
 
 
 def roofline(res, M):
