@@ -57,9 +57,15 @@ typedef enum {
 
 typedef enum {
   KFBI_FP64 = 0,        /* plain path: every kernel in float64 */
-  KFBI_MIXED_TF32 = 1   /* DST on tcgen05 tensor cores, TF32 split in 3
+  KFBI_MIXED_TF32 = 1,  /* DST on tcgen05 tensor cores, TF32 split in 3
                            passes with FP32 accumulation; correction and
                            extraction in FP32; GMRES in FP64 */
+  KFBI_MIXED_FFT32 = 2  /* DST-I by FP32 FFT on the CUDA cores (M a power
+                           of two, 64 <= M <= 1024; otherwise
+                           KFBI_ERR_UNSUPPORTED at creation); correction,
+                           extraction, GMRES and refinement as
+                           KFBI_MIXED_TF32.  Single domains only: batches and
+                           the server take KFBI_MIXED_TF32 domains */
 } kfbi_precision;
 
 typedef enum {

@@ -341,7 +341,7 @@ static void upload_domain(kfbi_domain* D, const Plan& P) {
   D->d_node_b = dev_upload(D, nb_);
   D->d_node_fidx = dev_upload(D, to_padded(P.node_fidx, n1, Mp));
   D->d_node_fcoef = dev_upload(D, P.node_fcoef);
-  if (D->desc.precision == KFBI_MIXED_TF32) {
+  if (is_mixed(D->desc.precision)) {
     D->d_arm_alpha32 = dev_upload(D, to_f32(alpha));
     D->d_arm_beta32 = dev_upload(D, to_f32(beta));
     D->d_arm_fcoef32 = dev_upload(D, to_f32(fcoef));
@@ -351,7 +351,7 @@ static void upload_domain(kfbi_domain* D, const Plan& P) {
     D->d_node_fcoef32 = dev_upload(D, to_f32(P.node_fcoef));
   }
   // DST-I matrix and eigenvalues, shared with every domain on this grid
-  D->tables = dst_tables(M, Mp, D->h, D->desc.precision == KFBI_MIXED_TF32);
+  D->tables = dst_tables(M, Mp, D->h, is_mixed(D->desc.precision));
   D->d_S = D->tables->S;
   D->d_lam = D->tables->lam;
   D->d_R = dev_alloc<double>(D, 2 * plane);
@@ -472,7 +472,7 @@ kfbi_domain* domain_from_plan(const Plan& plan, cudaStream_t st) {
     KFBI_CUDA(cudaGetDevice(&D->device));
     upload_domain(D, plan);
     gmres_alloc(D);
-    if (plan.desc.precision == KFBI_MIXED_TF32) D->tc = tc_create(D, plan);
+    if (is_mixed(plan.desc.precision)) D->tc = tc_create(D, plan);
     KFBI_CUDA(cudaStreamSynchronize(st));
   } catch (...) {
     free_domain(D);
@@ -487,7 +487,7 @@ long long domain_bytes_for(const Plan& P) {
   auto n1 = [](size_t n) { return std::max<size_t>(1, n); };
   const int Mp = ((P.n1 + 127) / 128) * 128;
   const size_t plane = (size_t)Mp * Mp;
-  const bool mixed = P.desc.precision == KFBI_MIXED_TF32;
+  const bool mixed = is_mixed(P.desc.precision);
   size_t b = n1(plane);                                                       // mask
   b += sizeof(int) * (n1(P.irr.size()) + n1(P.arm_start.size()) + n1(P.arm_k0.size()) +
                       n1(P.arm_fidx.size()) + n1(P.node_gidx.size()) + n1(P.node_fidx.size()));
@@ -514,7 +514,7 @@ kfbi_status kfbi_create_domain(const kfbi_domain_desc* desc, void* stream, kfbi_
     set_global_error("desc is NULL");
     return KFBI_ERR_ARG;
   }
-  if (desc->precision != KFBI_FP64 && desc->precision != KFBI_MIXED_TF32) {
+  if (desc->precision != KFBI_FP64 && !is_mixed(desc->precision)) {
     set_global_error("unknown precision");
     return KFBI_ERR_ARG;
   }
@@ -636,7 +636,7 @@ long long kfbi_plan_device_bytes(const kfbi_plan* plan, int equation) {
   const Plan& P = plan->p;
   const int Mp = ((P.n1 + 127) / 128) * 128;
   return domain_bytes_for(P) +
-         state_bytes_for(Mp, P.nb, equation, P.desc.precision == KFBI_MIXED_TF32);
+         state_bytes_for(Mp, P.nb, equation, is_mixed(P.desc.precision));
 }
 
 long long kfbi_plan_size(const kfbi_plan* plan, int field) {

@@ -1,0 +1,247 @@
+// Fast DST-I passes for KFBI_MIXED_FFT32 domains: the box solve of
+// Sec. 3.4.2 (arXiv 2404.14864) with each one-dimensional sine transform
+// computed by an FP32 FFT on the CUDA cores instead of a dense product.
+//
+// One pass transforms every row of an Mp x Mp plane and writes the result
+// transposed, like a dense pass: out[p][c][r] = sum_n sin(pi (c+1) n / M)
+// in[p][r][n-1], c = 0 .. M-2 (rows c >= M-1 of the output are never
+// written and stay zero).  Two passes give S A S.
+//
+// DST-I through a complex FFT of length M.  With x_n = in[r][n-1]
+// (n = 1 .. M-1), let y be the odd extension of length 2M (y_0 = y_M = 0,
+// y_n = x_n, y_{2M-n} = -x_n).  Its DFT is -2i times the DST, so
+// DST_k = -Im(Y_k)/2.  Y comes from one complex FFT of length M of the
+// packing z_m = y_{2m} + i y_{2m+1}: with Z = FFT_M(z), the even and odd
+// parts are E_k = (Z_k + conj Z_{M-k})/2 and O_k = (Z_k - conj Z_{M-k})/(2i),
+// and Y_k = E_k + exp(-i pi k/M) O_k.
+//
+// FFT_M, M = 32 N1 (four-step factorisation n = 32 n1 + n2, k = k1 + N1 k2):
+// lane n2 holds z_{32 n1 + n2} for all n1 and does an N1-point DFT in
+// registers; the result is multiplied by W_M^{n2 k1} and transposed through
+// shared memory; lane k1 then does the 32-point DFT over n2 and holds
+// Z_{k1 + N1 k2}.  In-register DFTs are radix-2 with twiddles from a shared
+// table of W_M^j (exact powers computed on the host in float64).
+//
+// One warp per row, RPB rows per block; the block stages its rows' results
+// and writes the transposed output as RPB-float runs.  Pass 2 of a box solve
+// (real kappa) applies the eigenvalue division as it stages.
+#include <cstdint>
+
+#include "tc_internal.h"
+
+namespace kfbi {
+namespace ff {
+
+constexpr int RPB = 8;  // rows (warps) per block
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+__host__ __device__ constexpr int bitrev(int i, int bits) {
+  int r = 0;
+  for (int b = 0; b < bits; ++b) r |= ((i >> b) & 1) << (bits - 1 - b);
+  return r;
+}
+
+__host__ __device__ constexpr int log2i(int n) { return n <= 1 ? 0 : 1 + log2i(n >> 1); }
+
+// t[i] = a[bitrev(i)] with every index a compile-time constant (a loop
+// would leave the permutation to the optimiser and the arrays in memory).
+template <int N, int I = 0>
+__device__ __forceinline__ void bitrev_copy(float2 (&t)[N], const float2 (&a)[N]) {
+  if constexpr (I < N) {
+    constexpr int J = bitrev(I, log2i(N));
+    t[I] = a[J];
+    bitrev_copy<N, I + 1>(t, a);
+  }
+}
+
+// Butterflies of stage LEN (LEN / 2 apart), then the next stage; one
+// template instance per stage keeps every register index a constant.
+template <int N, int LEN>
+__device__ __forceinline__ void dft_stages(float2 (&t)[N], const float2* tw, int stride) {
+  if constexpr (LEN <= N) {
+#pragma unroll
+    for (int i = 0; i < N; i += LEN) {
+#pragma unroll
+      for (int j = 0; j < LEN / 2; ++j) {
+        const float2 u = t[i + j];
+        const float2 v =
+            j == 0 ? t[i + j + LEN / 2] : cmul(t[i + j + LEN / 2], tw[j * (N / LEN) * stride]);
+        t[i + j] = make_float2(u.x + v.x, u.y + v.y);
+        t[i + j + LEN / 2] = make_float2(u.x - v.x, u.y - v.y);
+      }
+    }
+    dft_stages<N, LEN * 2>(t, tw, stride);
+  }
+}
+
+// In-place radix-2 decimation-in-time DFT of N values in registers;
+// tw[j * stride] = exp(-2 pi i j / (N * stride)), so W_len^j is
+// tw[j * (N / len) * stride].
+template <int N>
+__device__ __forceinline__ void dft_reg(float2 (&a)[N], const float2* tw, int stride) {
+  float2 t[N];
+  bitrev_copy<N>(t, a);
+  dft_stages<N, 2>(t, tw, stride);
+#pragma unroll
+  for (int i = 0; i < N; ++i) a[i] = t[i];
+}
+
+// Element y_n of the odd extension of row xr (x_n at xr[n-1]).
+__device__ __forceinline__ float yodd(const float* xr, int n, int M) {
+  if (n == 0 || n == M) return 0.f;
+  return n < M ? xr[n - 1] : -xr[2 * M - n - 1];
+}
+
+// Shared memory of one block (floats): twiddles 2M, W_2M table 2M,
+// eigenvalues M, staged output (M - 1) x (RPB + 1), input rows RPB x M,
+// transposes RPB x N1 x 33 complex.
+constexpr size_t smem_bytes(int M) {
+  return sizeof(float) * ((size_t)2 * M + 2 * M + M + (size_t)M * (RPB + 1) + (size_t)RPB * M +
+                          (size_t)RPB * (M / 32) * 33 * 2);
+}
+
+// mode 0: plain transform; mode 1: eigenvalue division of the box solve,
+// out *= scale / (lam[r] + lam[c] - kre) for r < n1, 0 for padded rows r.
+template <int N1>
+__global__ void __launch_bounds__(32 * RPB) k_dst_fft(const float* __restrict__ in,
+                                                      float* __restrict__ out, int Mp, int n1,
+                                                      const float2* __restrict__ twM,
+                                                      const float2* __restrict__ tw2M, int mode,
+                                                      const float* __restrict__ lam, float kre,
+                                                      float scale, const double* stop) {
+  constexpr int M = 32 * N1;
+  extern __shared__ float4 smem4[];
+  float2* s_tw = reinterpret_cast<float2*>(smem4);  // [M]
+  float2* s_tw2 = s_tw + M;                         // [M]
+  float* s_lam = reinterpret_cast<float*>(s_tw2 + M);  // [M]
+  float* s_out = s_lam + M;                         // [M - 1][RPB + 1]
+  float* s_rows = s_out + (size_t)M * (RPB + 1);    // [RPB][M]
+  float2* s_ex = reinterpret_cast<float2*>(s_rows + RPB * M);  // [RPB][N1][33]
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // the twiddle and eigenvalue tables are written once at domain set-up:
+  // load them before waiting for the previous kernel
+  for (int i = threadIdx.x; i < M; i += 32 * RPB) {
+    s_tw[i] = twM[i];
+    s_tw2[i] = tw2M[i];
+    s_lam[i] = mode == 1 && i < n1 ? lam[i] : 0.f;
+  }
+  KFBI_PDL_ENTRY();
+  KFBI_STOP_RETURN(stop);
+  const int row0 = blockIdx.x * RPB;  // first row over all planes
+  const int p = row0 / Mp, rr0 = row0 - p * Mp;
+  const float* src = in + (size_t)row0 * Mp;
+  for (int i = threadIdx.x; i < RPB * (M / 4); i += 32 * RPB) {
+    const int rw = i / (M / 4), cq = i - rw * (M / 4);
+    *reinterpret_cast<float4*>(s_rows + rw * M + 4 * cq) =
+        *reinterpret_cast<const float4*>(src + (size_t)rw * Mp + 4 * cq);
+  }
+  __syncthreads();
+  const float* xr = s_rows + warp * M;
+  // step 1: N1-point DFTs over n1 of z_{32 n1 + lane}, then W_M^{lane k1}
+  float2 a[N1];
+#pragma unroll
+  for (int q = 0; q < N1; ++q) {
+    const int m = 32 * q + lane;
+    a[q] = make_float2(yodd(xr, 2 * m, M), yodd(xr, 2 * m + 1, M));
+  }
+  dft_reg<N1>(a, s_tw, 32);
+  float2* ex = s_ex + (size_t)warp * N1 * 33;
+#pragma unroll
+  for (int k1 = 0; k1 < N1; ++k1) ex[k1 * 33 + lane] = cmul(a[k1], s_tw[(lane * k1) & (M - 1)]);
+  __syncwarp();
+  // step 3: lane k1 < N1 does the 32-point DFT over n2
+  float2 b[32];
+  if (lane < N1) {
+#pragma unroll
+    for (int n2 = 0; n2 < 32; ++n2) b[n2] = ex[lane * 33 + n2];
+    dft_reg<32>(b, s_tw, N1);
+  }
+  __syncwarp();
+  float2* Z = ex;  // Z_k at Z[k], k < M (fits in the N1 x 33 transpose buffer)
+  if (lane < N1) {
+#pragma unroll
+    for (int k2 = 0; k2 < 32; ++k2) Z[lane + N1 * k2] = b[k2];
+  }
+  __syncwarp();
+  // DST_k = -Im(E_k + exp(-i pi k / M) O_k) / 2, k = 1 .. M-1; output row c = k - 1
+  const int r = rr0 + warp;  // data row within the plane
+  const float lam_r = r < n1 ? s_lam[r] : 0.f;
+#pragma unroll
+  for (int t = 0; t < N1; ++t) {
+    const int k = lane + 32 * t;
+    if (k == 0) continue;
+    const float2 zk = Z[k], zc = Z[M - k];
+    const float ey = 0.5f * (zk.y - zc.y);
+    const float ox = 0.5f * (zk.y + zc.y), oy = -0.5f * (zk.x - zc.x);
+    const float2 w = s_tw2[k];
+    float v = -0.5f * (ey + w.x * oy + w.y * ox);
+    const int c = k - 1;
+    if (mode == 1) v = r < n1 ? v * __fdividef(scale, lam_r + s_lam[c] - kre) : 0.f;
+    s_out[c * (RPB + 1) + warp] = v;
+  }
+  __syncthreads();
+  float* dst = out + (size_t)p * Mp * Mp + rr0;
+  for (int i = threadIdx.x; i < (M - 1) * (RPB / 4); i += 32 * RPB) {
+    const int c = i / (RPB / 4), h = i - c * (RPB / 4);
+    const float* sv = s_out + c * (RPB + 1) + 4 * h;
+    *reinterpret_cast<float4*>(dst + (size_t)c * Mp + 4 * h) = make_float4(sv[0], sv[1], sv[2], sv[3]);
+  }
+}
+
+template <int N1>
+static void set_smem_attr() {
+  KFBI_CUDA(cudaFuncSetAttribute(k_dst_fft<N1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem_bytes(32 * N1)));
+}
+
+template <int N1>
+static void launch_n1(const float* in, float* out, int Mp, int n1, const float2* twM,
+                      const float2* tw2M, int mode, const float* lam, float kre, float scale,
+                      int P, const double* stop, cudaStream_t st) {
+  const int blocks = P * Mp / RPB;
+  KFBI_LAUNCH_PW(KFBI_PROF_DST, fft_pass_flops(32 * N1, P * Mp), k_dst_fft<N1>, blocks, 32 * RPB,
+                 smem_bytes(32 * N1), st, in, out, Mp, n1, twM, tw2M, mode, lam, kre, scale, stop);
+}
+
+}  // namespace ff
+
+// Flops of one pass as executed: per row one complex FFT of length M
+// (5 M log2 M) and the O(M) untangling (about 10 M).
+double fft_pass_flops(int M, int rows) {
+  int lg = 0;
+  while ((1 << lg) < M) ++lg;
+  return (double)rows * (5.0 * M * lg + 10.0 * M);
+}
+
+bool fft_supported(int M) { return M >= 64 && M <= 1024 && (M & (M - 1)) == 0; }
+
+size_t fft_smem_bytes(int M) { return ff::smem_bytes(M); }
+
+void fft_prepare(int M) {
+  switch (M) {
+    case 64: ff::set_smem_attr<2>(); break;
+    case 128: ff::set_smem_attr<4>(); break;
+    case 256: ff::set_smem_attr<8>(); break;
+    case 512: ff::set_smem_attr<16>(); break;
+    case 1024: ff::set_smem_attr<32>(); break;
+    default: throw Status{KFBI_ERR_UNSUPPORTED, "FFT passes need M = 64 .. 1024, a power of two"};
+  }
+}
+
+void fft_pass(const TcDst* T, const float* in, float* out, int mode, float kre, float scale, int P,
+              const double* stop, cudaStream_t st) {
+  const int M = T->n1 + 1;
+  switch (M) {
+    case 64: ff::launch_n1<2>(in, out, T->Mp, T->n1, T->twM, T->tw2M, mode, T->lam, kre, scale, P, stop, st); break;
+    case 128: ff::launch_n1<4>(in, out, T->Mp, T->n1, T->twM, T->tw2M, mode, T->lam, kre, scale, P, stop, st); break;
+    case 256: ff::launch_n1<8>(in, out, T->Mp, T->n1, T->twM, T->tw2M, mode, T->lam, kre, scale, P, stop, st); break;
+    case 512: ff::launch_n1<16>(in, out, T->Mp, T->n1, T->twM, T->tw2M, mode, T->lam, kre, scale, P, stop, st); break;
+    case 1024: ff::launch_n1<32>(in, out, T->Mp, T->n1, T->twM, T->tw2M, mode, T->lam, kre, scale, P, stop, st); break;
+    default: throw Status{KFBI_ERR_UNSUPPORTED, "FFT passes need M = 64 .. 1024, a power of two"};
+  }
+}
+
+}  // namespace kfbi

@@ -61,6 +61,12 @@ inline void add_pdl_attr(cudaLaunchConfig_t& cfg, cudaLaunchAttribute* at) {
 struct CudaError;
 [[noreturn]] void throw_launch_error(cudaError_t e);
 
+// Precisions that run the mixed engine (FP32 correction and extraction,
+// FP32 box solves with FP64 refinement).
+inline bool is_mixed(int precision) {
+  return precision == KFBI_MIXED_TF32 || precision == KFBI_MIXED_FFT32;
+}
+
 template <typename... P, typename... A>
 inline void launch_kernel(void (*kern)(P...), dim3 grid, dim3 block, size_t smem,
                           cudaStream_t st, A&&... args) {
@@ -231,7 +237,7 @@ struct kfbi_domain {
   cudaEvent_t ev_ring[2] = {nullptr, nullptr};
   cudaEvent_t ev_scal = nullptr;
 
-  kfbi::TcDst* tc = nullptr;  // mixed-precision engine (precision == KFBI_MIXED_TF32)
+  kfbi::TcDst* tc = nullptr;  // mixed-precision engine (KFBI_MIXED_TF32 or KFBI_MIXED_FFT32)
 };
 
 struct kfbi_state {

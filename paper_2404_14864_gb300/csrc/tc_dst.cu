@@ -684,6 +684,10 @@ __global__ void k_split64(const double* __restrict__ src, float* __restrict__ hi
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
        i += (size_t)gridDim.x * blockDim.x) {
     const double x = src[i];
+    if (!lo) {  // single FP32 plane (FFT passes)
+      hi[i] = (float)x;
+      continue;
+    }
     const float h = tf32_round((float)x);
     hi[i] = h;
     lo[i] = tf32_round((float)(x - (double)h));
@@ -739,6 +743,11 @@ __global__ void k_correct32(float* __restrict__ Rh, float* __restrict__ Rl, size
   if (rv) {  // compact values for the sparse first pass
     rv[n] = sr;
     if (C) rv[n_irr + n] = si;
+    return;
+  }
+  if (!Rl) {  // single FP32 plane (FFT passes)
+    Rh[off] = sr;
+    if (C) Rh[plane + off] = si;
     return;
   }
   float h = tf32_round(sr);
@@ -880,11 +889,16 @@ __global__ void k_eig_split_cplx(float* __restrict__ hi, float* __restrict__ lo,
        idx += (size_t)gridDim.x * blockDim.x) {
     const int a = (int)(idx / Mp), b = (int)(idx % Mp);
     if (a >= n1 || b >= n1) continue;
-    const double x = (double)hi[idx] + (double)lo[idx];
-    const double y = (double)hi[plane + idx] + (double)lo[plane + idx];
+    const double x = (double)hi[idx] + (lo ? (double)lo[idx] : 0.0);
+    const double y = (double)hi[plane + idx] + (lo ? (double)lo[plane + idx] : 0.0);
     const double dr = lam[a] + lam[b] - kre;
     const double den = scale / (dr * dr + kim * kim);
     const double zr = (x * dr - y * kim) * den, zi = (x * kim + y * dr) * den;
+    if (!lo) {  // single FP32 planes (FFT passes)
+      hi[idx] = (float)zr;
+      hi[plane + idx] = (float)zi;
+      continue;
+    }
     float h = tf32_round((float)zr);
     hi[idx] = h;
     lo[idx] = tf32_round((float)(zr - (double)h));
@@ -982,6 +996,10 @@ __global__ void k_resid_split(const double* __restrict__ R, const double* __rest
           Lu += (p == 0) ? kim * uo : -kim * uo;
         }
         res = R[p * plane + idx] - Lu;
+      }
+      if (!lo) {  // single FP32 plane (FFT passes)
+        hi[p * plane + idx] = (float)res;
+        continue;
       }
       const float h = tf32_round((float)res);
       hi[p * plane + idx] = h;
@@ -1114,6 +1132,24 @@ TcDst* tc_create(kfbi_domain* D, const Plan& P) {
     KFBI_CUDA(cudaMemcpy(T->d_maps, maps, sizeof(maps), cudaMemcpyHostToDevice));
     KFBI_CUDA(cudaFuncSetAttribute(k_tc_pass, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    SMEM_BYTES));
+    if (D->desc.precision == KFBI_MIXED_FFT32) {
+      const int M = D->M;
+      if (!fft_supported(M)) throw Status{KFBI_ERR_UNSUPPORTED, "FFT passes need M = 64 .. 1024, a power of two"};
+      // W_M^j and exp(-i pi j / M), j < M, in float64 then rounded
+      std::vector<float2> tw(M), tw2(M);
+      for (int j = 0; j < M; ++j) {
+        const double a = -2.0 * M_PI * j / M, b = -M_PI * j / M;
+        tw[j] = make_float2((float)std::cos(a), (float)std::sin(a));
+        tw2[j] = make_float2((float)std::cos(b), (float)std::sin(b));
+      }
+      KFBI_CUDA(cudaMalloc(&T->twM, M * sizeof(float2)));
+      KFBI_CUDA(cudaMalloc(&T->tw2M, M * sizeof(float2)));
+      T->bytes += 2LL * M * (long long)sizeof(float2);
+      KFBI_CUDA(cudaMemcpy(T->twM, tw.data(), M * sizeof(float2), cudaMemcpyHostToDevice));
+      KFBI_CUDA(cudaMemcpy(T->tw2M, tw2.data(), M * sizeof(float2), cudaMemcpyHostToDevice));
+      fft_prepare(M);
+      T->fft = true;
+    }
     KFBI_CUDA(cudaDeviceGetAttribute(&T->nsm, cudaDevAttrMultiProcessorCount, D->device));
   } catch (...) {
     tc_destroy(T);
@@ -1130,6 +1166,8 @@ void tc_destroy(TcDst* T) {
   if (T->row_start) cudaFree(T->row_start);
   if (T->node_col) cudaFree(T->node_col);
   if (T->d_maps) cudaFree(T->d_maps);
+  if (T->twM) cudaFree(T->twM);
+  if (T->tw2M) cudaFree(T->tw2M);
   delete T;
 }
 
@@ -1144,6 +1182,7 @@ long long tc_bytes_for(const Plan& P, int Mp) {
     const int rows = P.irr.back() / P.n1 - P.irr.front() / P.n1 + 1;
     b += (long long)((rows + 1 + P.n_irr()) * sizeof(int));
   }
+  if (P.desc.precision == KFBI_MIXED_FFT32) b += 2LL * P.M * (long long)sizeof(float2);
   return b + (long long)(kNumMaps * sizeof(CUtensorMap));
 }
 
@@ -1241,6 +1280,17 @@ static void tc_box_solve(kfbi_domain* D, double kre, double kim, int P, cudaStre
   const size_t plane = (size_t)T->Mp * T->Mp;
   const bool C = kim != 0.0;
   const float scale = (float)((2.0 / D->M) * (2.0 / D->M));
+  if (T->fft) {
+    fft_pass(T, T->Rh, T->T1h, 0, 0.f, 0.f, P, nullptr, st);
+    fft_pass(T, T->T1h, T->T2h, C ? 0 : 1, (float)kre, scale, P, nullptr, st);
+    if (C)
+      KFBI_LAUNCH_P(KFBI_PROF_GRID, k_eig_split_cplx, grid_for(plane, 256), 256, 0, st, T->T2h,
+                    nullptr, plane, T->Mp, T->n1, D->d_lam, kre, kim, (2.0 / D->M) * (2.0 / D->M),
+                    nullptr);
+    fft_pass(T, T->T2h, T->T1h, 0, 0.f, 0.f, P, nullptr, st);
+    fft_pass(T, T->T1h, T->U, 0, 0.f, 0.f, P, nullptr, st);
+    return;
+  }
   launch_pass(T, pass_desc(T, kMapR_hi, kMapR_lo, T->T1h, T->T1l, 0, P, 0.f, 0.f), st);
   launch_pass(T, pass_desc(T, kMapT1_hi, kMapT1_lo, T->T2h, T->T2l, C ? 0 : 1, P, (float)kre, scale),
               st);
@@ -1265,6 +1315,43 @@ static void tc_apply_sparse(kfbi_domain* D, double kre, double kim, const double
   const int P = C ? 2 : 1;
   const int Mp = T->Mp;
   const size_t plane = (size_t)Mp * Mp;
+  if (T->fft) {
+    // FFT passes cost the same for any right-hand side: correct into the
+    // dense FP32 plane (zero away from the irregular nodes), three full
+    // passes, and the last pass evaluated at the stencil points only
+    if (T->rhs_sparse_planes < P) {
+      KFBI_CUDA(cudaMemsetAsync(T->Rh, 0, 2 * plane * sizeof(float), st));
+      T->rhs_sparse_planes = 2;
+    }
+    if (C)
+      KFBI_LAUNCH_P(KFBI_PROF_CORRECT, k_correct32<true>, (D->n_irr + 127) / 128, 128, 0, st, T->Rh,
+                    nullptr, plane, nullptr, D->d_irr_off, D->d_arm_start, D->d_arm_k0,
+                    D->d_arm_alpha32, D->d_arm_beta32, D->d_arm_fidx, D->d_arm_fcoef32, D->n_irr,
+                    D->n_arms, D->nb, phi, ps, (float)kre, (float)kim, nullptr, T->stop);
+    else
+      KFBI_LAUNCH_P(KFBI_PROF_CORRECT, k_correct32<false>, (D->n_irr + 127) / 128, 128, 0, st,
+                    T->Rh, nullptr, plane, nullptr, D->d_irr_off, D->d_arm_start, D->d_arm_k0,
+                    D->d_arm_alpha32, D->d_arm_beta32, D->d_arm_fidx, D->d_arm_fcoef32, D->n_irr,
+                    D->n_arms, D->nb, phi, ps, (float)kre, (float)kim, nullptr, T->stop);
+    const float scale = (float)((2.0 / D->M) * (2.0 / D->M));
+    fft_pass(T, T->Rh, T->T1h, 0, 0.f, 0.f, P, T->stop, st);
+    fft_pass(T, T->T1h, T->T2h, C ? 0 : 1, (float)kre, scale, P, T->stop, st);
+    if (C)
+      KFBI_LAUNCH_P(KFBI_PROF_GRID, k_eig_split_cplx, grid_for(plane, 256), 256, 0, st, T->T2h,
+                    nullptr, plane, Mp, T->n1, D->d_lam, kre, kim, (2.0 / D->M) * (2.0 / D->M),
+                    T->stop);
+    fft_pass(T, T->T2h, T->U, 0, 0.f, 0.f, P, T->stop, st);
+    if (C)
+      KFBI_LAUNCH_P(KFBI_PROF_EXTRACT, k_gather_extract<true>, D->nb, 192, 0, st, T->U, T->S32, Mp,
+                    plane, D->d_node_gidx, D->d_node_w32, D->d_node_a32, D->d_node_b32, D->nb, phi,
+                    ps, (float)kre, (float)kim, out, os, T->stop);
+    else
+      KFBI_LAUNCH_P(KFBI_PROF_EXTRACT, k_gather_extract<false>, D->nb, 192, 0, st, T->U, T->S32, Mp,
+                    plane, D->d_node_gidx, D->d_node_w32, D->d_node_a32, D->d_node_b32, D->nb, phi,
+                    ps, (float)kre, (float)kim, out, os, T->stop);
+    KFBI_CHECK_LAUNCH();
+    return;
+  }
   if (C)
     KFBI_LAUNCH_P(KFBI_PROF_CORRECT, k_correct32<true>, (D->n_irr + 127) / 128, 128, 0, st, T->Rh,
                   T->Rl, plane, nullptr, D->d_irr_off, D->d_arm_start, D->d_arm_k0,
@@ -1314,7 +1401,7 @@ void tc_apply(kfbi_domain* D, double kre, double kim, const double* phi, int ps,
   const size_t plane = (size_t)Mp * Mp;
   if (ft) {
     KFBI_LAUNCH_P(KFBI_PROF_GRID, k_split64, grid_for(P * plane, 256), 256, 0, st, ft, T->Rh,
-                  T->Rl, P * plane);
+                  T->fft ? nullptr : T->Rl, P * plane);
     T->rhs_sparse_planes = 0;
   } else if (T->rhs_sparse_planes < P) {
     KFBI_CUDA(cudaMemsetAsync(T->Rh, 0, 2 * plane * sizeof(float), st));
@@ -1324,12 +1411,12 @@ void tc_apply(kfbi_domain* D, double kre, double kim, const double* phi, int ps,
   if (D->n_irr > 0) {
     if (C)
       KFBI_LAUNCH_P(KFBI_PROF_CORRECT, k_correct32<true>, (D->n_irr + 127) / 128, 128, 0, st,
-                    T->Rh, T->Rl, plane, ft, D->d_irr_off, D->d_arm_start, D->d_arm_k0,
+                    T->Rh, T->fft ? nullptr : T->Rl, plane, ft, D->d_irr_off, D->d_arm_start, D->d_arm_k0,
                     D->d_arm_alpha32, D->d_arm_beta32, D->d_arm_fidx, D->d_arm_fcoef32,
                     D->n_irr, D->n_arms, D->nb, phi, ps, (float)kre, (float)kim, nullptr, nullptr);
     else
       KFBI_LAUNCH_P(KFBI_PROF_CORRECT, k_correct32<false>, (D->n_irr + 127) / 128, 128, 0, st,
-                    T->Rh, T->Rl, plane, ft, D->d_irr_off, D->d_arm_start, D->d_arm_k0,
+                    T->Rh, T->fft ? nullptr : T->Rl, plane, ft, D->d_irr_off, D->d_arm_start, D->d_arm_k0,
                     D->d_arm_alpha32, D->d_arm_beta32, D->d_arm_fidx, D->d_arm_fcoef32,
                     D->n_irr, D->n_arms, D->nb, phi, ps, (float)kre, (float)kim, nullptr, nullptr);
   }
@@ -1366,7 +1453,7 @@ void tc_apply_accurate(kfbi_domain* D, double kre, double kim, const double* phi
   const size_t plane = (size_t)Mp * Mp;
   correct_fp64(D, kre, kim, phi, ps, ft, st);  // D->d_R: FP64 corrected RHS
   KFBI_LAUNCH_P(KFBI_PROF_GRID, k_split64, grid_for(P * plane, 256), 256, 0, st, D->d_R, T->Rh,
-                T->Rl, P * plane);
+                T->fft ? nullptr : T->Rl, P * plane);
   T->rhs_sparse_planes = 0;
   tc_box_solve(D, kre, kim, P, st);
   KFBI_LAUNCH_P(KFBI_PROF_GRID, k_f32_to_f64, grid_for(P * plane, 256), 256, 0, st, T->U, D->d_U,
@@ -1374,10 +1461,10 @@ void tc_apply_accurate(kfbi_domain* D, double kre, double kim, const double* phi
   const double inv_h2 = 1.0 / (D->h * D->h);
   if (C)
     KFBI_LAUNCH_P(KFBI_PROF_GRID, k_resid_split<true>, grid_for(plane, 256), 256, 0, st, D->d_R,
-                  D->d_U, T->Rh, T->Rl, Mp, T->n1, inv_h2, kre, kim);
+                  D->d_U, T->Rh, T->fft ? nullptr : T->Rl, Mp, T->n1, inv_h2, kre, kim);
   else
     KFBI_LAUNCH_P(KFBI_PROF_GRID, k_resid_split<false>, grid_for(plane, 256), 256, 0, st, D->d_R,
-                  D->d_U, T->Rh, T->Rl, Mp, T->n1, inv_h2, kre, kim);
+                  D->d_U, T->Rh, T->fft ? nullptr : T->Rl, Mp, T->n1, inv_h2, kre, kim);
   tc_box_solve(D, kre, kim, P, st);
   KFBI_LAUNCH_P(KFBI_PROF_GRID, k_add_f32, grid_for(P * plane, 256), 256, 0, st, D->d_U, T->U,
                 P * plane);

@@ -88,8 +88,24 @@ struct TcDst {
   // while a GMRES cycle queues iterations ahead: the solver's convergence
   // flag, passed to the kernels of the fast (sparse-route) application
   const double* stop = nullptr;
+  // KFBI_MIXED_FFT32: passes by FP32 FFT (fft_dst.cu) on single FP32 planes
+  // (Rh, T1h, T2h, U; the lo planes stay unused); twiddles W_M^j and
+  // exp(-i pi j / M), j < M
+  bool fft = false;
+  float2* twM = nullptr;
+  float2* tw2M = nullptr;
 };
 
+
+// FP32 FFT passes (fft_dst.cu).  fft_pass transforms every row of P planes
+// of `in` and writes out transposed (mode 1: eigenvalue division of the box
+// solve); stop as KFBI_STOP_RETURN.
+bool fft_supported(int M);
+size_t fft_smem_bytes(int M);
+void fft_prepare(int M);
+double fft_pass_flops(int M, int rows);
+void fft_pass(const TcDst* T, const float* in, float* out, int mode, float kre, float scale, int P,
+              const double* stop, cudaStream_t st);
 
 // Device tensor map of one of the domain's pass output planes (T1, T2 pairs
 // or U); throws for any other pointer.

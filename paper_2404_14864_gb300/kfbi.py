@@ -20,7 +20,7 @@ KFBI_OK = 0
 STATUS_NAMES = {0: "KFBI_OK", 1: "KFBI_ERR_ARG", 2: "KFBI_ERR_GEOMETRY", 3: "KFBI_ERR_OOM",
                 4: "KFBI_ERR_NOT_CONVERGED", 5: "KFBI_ERR_NONFINITE", 6: "KFBI_ERR_TIMEOUT",
                 7: "KFBI_ERR_CUDA", 8: "KFBI_ERR_UNSUPPORTED"}
-KFBI_FP64, KFBI_MIXED_TF32 = 0, 1
+KFBI_FP64, KFBI_MIXED_TF32, KFBI_MIXED_FFT32 = 0, 1, 2
 KFBI_CURVE_POLAR, KFBI_CURVE_ELLIPSE = 0, 1
 KFBI_HEAT, KFBI_WAVE, KFBI_SCHRODINGER = 0, 1, 2
 
