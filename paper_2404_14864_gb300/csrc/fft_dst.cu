@@ -67,8 +67,11 @@ __device__ __forceinline__ void dft_stages(float2 (&t)[N], const float2* tw, int
 #pragma unroll
       for (int j = 0; j < LEN / 2; ++j) {
         const float2 u = t[i + j];
-        const float2 v =
-            j == 0 ? t[i + j + LEN / 2] : cmul(t[i + j + LEN / 2], tw[j * (N / LEN) * stride]);
+        const float2 x = t[i + j + LEN / 2];
+        // W^0 = 1 and W_LEN^{LEN/4} = -i need no multiplication
+        const float2 v = j == 0 ? x
+                         : (4 * j == LEN ? make_float2(x.y, -x.x)
+                                         : cmul(x, tw[j * (N / LEN) * stride]));
         t[i + j] = make_float2(u.x + v.x, u.y + v.y);
         t[i + j + LEN / 2] = make_float2(u.x - v.x, u.y - v.y);
       }
@@ -95,13 +98,15 @@ __device__ __forceinline__ float yodd(const float* xr, int n, int M) {
   return n < M ? xr[n - 1] : -xr[2 * M - n - 1];
 }
 
-// Shared memory of one block (floats): twiddles 2M, W_2M table 2M,
-// eigenvalues M, staged output (M - 1) x (RPB + 1), input rows RPB x M,
-// transposes RPB x N1 x 33 complex.
+// Shared memory of one block (floats): twiddle tables W_M^j, W_M^{n2 k1}
+// by [k1][n2], exp(-i pi k/M) (2M each), eigenvalues M, and per warp an
+// N1 x 33 complex transpose buffer that first holds the warp's input row;
+// once every warp has finished its transposes the buffers hold the staged
+// output, (M - 1) x (RPB + 1) floats.
 constexpr size_t smem_bytes(int M) {
-  return sizeof(float) * ((size_t)2 * M + 2 * M + M + (size_t)M * (RPB + 1) + (size_t)RPB * M +
-                          (size_t)RPB * (M / 32) * 33 * 2);
+  return sizeof(float) * ((size_t)6 * M + M + (size_t)RPB * (M / 32) * 33 * 2);
 }
+static_assert((1024 - 1) * (RPB + 1) <= RPB * 32 * 33 * 2, "staged output fits the transposes");
 
 // mode 0: plain transform; mode 1: eigenvalue division of the box solve,
 // out *= scale / (lam[r] + lam[c] - kre) for r < n1, 0 for padded rows r.
@@ -109,37 +114,78 @@ template <int N1>
 __global__ void __launch_bounds__(32 * RPB) k_dst_fft(const float* __restrict__ in,
                                                       float* __restrict__ out, int Mp, int n1,
                                                       const float2* __restrict__ twM,
+                                                      const float2* __restrict__ twB,
                                                       const float2* __restrict__ tw2M, int mode,
                                                       const float* __restrict__ lam, float kre,
                                                       float scale, const double* stop) {
   constexpr int M = 32 * N1;
+  constexpr int T = 32 * RPB;  // threads
   extern __shared__ float4 smem4[];
-  float2* s_tw = reinterpret_cast<float2*>(smem4);  // [M]
-  float2* s_tw2 = s_tw + M;                         // [M]
+  float2* s_tw = reinterpret_cast<float2*>(smem4);  // [M] W_M^j
+  float2* s_twb = s_tw + M;                         // [N1][32] W_M^{n2 k1}
+  float2* s_tw2 = s_twb + M;                        // [M] exp(-i pi k / M)
   float* s_lam = reinterpret_cast<float*>(s_tw2 + M);  // [M]
-  float* s_out = s_lam + M;                         // [M - 1][RPB + 1]
-  float* s_rows = s_out + (size_t)M * (RPB + 1);    // [RPB][M]
-  float2* s_ex = reinterpret_cast<float2*>(s_rows + RPB * M);  // [RPB][N1][33]
+  float2* s_ex = reinterpret_cast<float2*>(s_lam + M);   // [RPB][N1][33]
+  float* s_out = reinterpret_cast<float*>(s_ex);         // [M - 1][RPB + 1], after the transposes
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  // the twiddle and eigenvalue tables are written once at domain set-up:
-  // load them before waiting for the previous kernel
-  for (int i = threadIdx.x; i < M; i += 32 * RPB) {
-    s_tw[i] = twM[i];
-    s_tw2[i] = tw2M[i];
-    s_lam[i] = mode == 1 && i < n1 ? lam[i] : 0.f;
+  // the tables are written once at domain set-up: load them before waiting
+  // for the previous kernel (every load issued before any is used)
+  {
+    constexpr int NT = (M + T - 1) / T;
+    float2 v0[NT], v1[NT], v2[NT];
+    float v3[NT];
+#pragma unroll
+    for (int q = 0; q < NT; ++q) {
+      const int i = threadIdx.x + q * T;
+      if (i < M) {
+        v0[q] = twM[i];
+        v1[q] = twB[i];
+        v2[q] = tw2M[i];
+        v3[q] = mode == 1 && i < n1 ? lam[i] : 0.f;
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < NT; ++q) {
+      const int i = threadIdx.x + q * T;
+      if (i < M) {
+        s_tw[i] = v0[q];
+        s_twb[i] = v1[q];
+        s_tw2[i] = v2[q];
+        s_lam[i] = v3[q];
+      }
+    }
   }
   KFBI_PDL_ENTRY();
   KFBI_STOP_RETURN(stop);
   const int row0 = blockIdx.x * RPB;  // first row over all planes
   const int p = row0 / Mp, rr0 = row0 - p * Mp;
-  const float* src = in + (size_t)row0 * Mp;
-  for (int i = threadIdx.x; i < RPB * (M / 4); i += 32 * RPB) {
-    const int rw = i / (M / 4), cq = i - rw * (M / 4);
-    *reinterpret_cast<float4*>(s_rows + rw * M + 4 * cq) =
-        *reinterpret_cast<const float4*>(src + (size_t)rw * Mp + 4 * cq);
+  // the block's RPB input rows (M floats each) into the warps' transpose
+  // buffers: all loads first, then all stores
+  {
+    const float* src = in + (size_t)row0 * Mp;
+    constexpr int NV = RPB * (M / 4) / T;  // float4 per thread (M >= 128)
+    constexpr int NVQ = NV > 0 ? NV : 1;
+    float4 v[NVQ];
+#pragma unroll
+    for (int q = 0; q < NVQ; ++q) {
+      const int i = threadIdx.x + q * T;
+      if (i < RPB * (M / 4)) {
+        const int rw = i / (M / 4), cq = i - rw * (M / 4);
+        v[q] = *reinterpret_cast<const float4*>(src + (size_t)rw * Mp + 4 * cq);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < NVQ; ++q) {
+      const int i = threadIdx.x + q * T;
+      if (i < RPB * (M / 4)) {
+        const int rw = i / (M / 4), cq = i - rw * (M / 4);
+        *reinterpret_cast<float4*>(reinterpret_cast<float*>(s_ex + (size_t)rw * N1 * 33) + 4 * cq) = v[q];
+      }
+    }
   }
   __syncthreads();
-  const float* xr = s_rows + warp * M;
+  float2* ex = s_ex + (size_t)warp * N1 * 33;
+  const float* xr = reinterpret_cast<const float*>(ex);
   // step 1: N1-point DFTs over n1 of z_{32 n1 + lane}, then W_M^{lane k1}
   float2 a[N1];
 #pragma unroll
@@ -148,9 +194,9 @@ __global__ void __launch_bounds__(32 * RPB) k_dst_fft(const float* __restrict__ 
     a[q] = make_float2(yodd(xr, 2 * m, M), yodd(xr, 2 * m + 1, M));
   }
   dft_reg<N1>(a, s_tw, 32);
-  float2* ex = s_ex + (size_t)warp * N1 * 33;
+  __syncwarp();  // every lane has read its part of the row before the transpose overwrites it
 #pragma unroll
-  for (int k1 = 0; k1 < N1; ++k1) ex[k1 * 33 + lane] = cmul(a[k1], s_tw[(lane * k1) & (M - 1)]);
+  for (int k1 = 0; k1 < N1; ++k1) ex[k1 * 33 + lane] = cmul(a[k1], s_twb[k1 * 32 + lane]);
   __syncwarp();
   // step 3: lane k1 < N1 does the 32-point DFT over n2
   float2 b[32];
@@ -158,36 +204,48 @@ __global__ void __launch_bounds__(32 * RPB) k_dst_fft(const float* __restrict__ 
 #pragma unroll
     for (int n2 = 0; n2 < 32; ++n2) b[n2] = ex[lane * 33 + n2];
     dft_reg<32>(b, s_tw, N1);
-  }
-  __syncwarp();
-  float2* Z = ex;  // Z_k at Z[k], k < M (fits in the N1 x 33 transpose buffer)
-  if (lane < N1) {
+  } else {
 #pragma unroll
-    for (int k2 = 0; k2 < 32; ++k2) Z[lane + N1 * k2] = b[k2];
+    for (int n2 = 0; n2 < 32; ++n2) b[n2] = make_float2(0.f, 0.f);
   }
-  __syncwarp();
-  // DST_k = -Im(E_k + exp(-i pi k / M) O_k) / 2, k = 1 .. M-1; output row c = k - 1
+  // every warp is done with its transpose buffer: the staged output may
+  // overwrite them
+  __syncthreads();
+  // DST_k = -Im(E_k + exp(-i pi k / M) O_k) / 2 for k = lane + N1 k2
+  // (lanes < N1 hold Z_k in b[k2]); Z_{M-k} is b[31 - k2] of lane N1 - lane,
+  // or, for lane 0, its own b[(32 - k2) % 32].  Output row c = k - 1.
   const int r = rr0 + warp;  // data row within the plane
   const float lam_r = r < n1 ? s_lam[r] : 0.f;
+  const int partner = lane == 0 ? 0 : N1 - lane;
 #pragma unroll
-  for (int t = 0; t < N1; ++t) {
-    const int k = lane + 32 * t;
-    if (k == 0) continue;
-    const float2 zk = Z[k], zc = Z[M - k];
+  for (int k2 = 0; k2 < 32; ++k2) {
+    float2 zc;
+    zc.x = __shfl_sync(0xffffffffu, b[31 - k2].x, partner);
+    zc.y = __shfl_sync(0xffffffffu, b[31 - k2].y, partner);
+    if (lane == 0) zc = b[(32 - k2) & 31];
+    // straight-line body (only the store is predicated) so the unrolled
+    // iterations overlap
+    const int k = (lane + N1 * k2) & (M - 1);
+    const float2 zk = b[k2];
     const float ey = 0.5f * (zk.y - zc.y);
     const float ox = 0.5f * (zk.y + zc.y), oy = -0.5f * (zk.x - zc.x);
     const float2 w = s_tw2[k];
     float v = -0.5f * (ey + w.x * oy + w.y * ox);
     const int c = k - 1;
-    if (mode == 1) v = r < n1 ? v * __fdividef(scale, lam_r + s_lam[c] - kre) : 0.f;
-    s_out[c * (RPB + 1) + warp] = v;
+    if (mode == 1) v = r < n1 ? v * __fdividef(scale, lam_r + s_lam[c < 0 ? 0 : c] - kre) : 0.f;
+    if (lane < N1 && k != 0) s_out[c * (RPB + 1) + warp] = v;
   }
   __syncthreads();
   float* dst = out + (size_t)p * Mp * Mp + rr0;
-  for (int i = threadIdx.x; i < (M - 1) * (RPB / 4); i += 32 * RPB) {
-    const int c = i / (RPB / 4), h = i - c * (RPB / 4);
-    const float* sv = s_out + c * (RPB + 1) + 4 * h;
-    *reinterpret_cast<float4*>(dst + (size_t)c * Mp + 4 * h) = make_float4(sv[0], sv[1], sv[2], sv[3]);
+  constexpr int NW = ((M - 1) * (RPB / 4) + T - 1) / T;
+#pragma unroll
+  for (int q = 0; q < NW; ++q) {
+    const int i = threadIdx.x + q * T;
+    if (i < (M - 1) * (RPB / 4)) {
+      const int c = i / (RPB / 4), h = i - c * (RPB / 4);
+      const float* sv = s_out + c * (RPB + 1) + 4 * h;
+      *reinterpret_cast<float4*>(dst + (size_t)c * Mp + 4 * h) = make_float4(sv[0], sv[1], sv[2], sv[3]);
+    }
   }
 }
 
@@ -199,11 +257,11 @@ static void set_smem_attr() {
 
 template <int N1>
 static void launch_n1(const float* in, float* out, int Mp, int n1, const float2* twM,
-                      const float2* tw2M, int mode, const float* lam, float kre, float scale,
+                      const float2* twB, const float2* tw2M, int mode, const float* lam, float kre, float scale,
                       int P, const double* stop, cudaStream_t st) {
   const int blocks = P * Mp / RPB;
   KFBI_LAUNCH_PW(KFBI_PROF_DST, fft_pass_flops(32 * N1, P * Mp), k_dst_fft<N1>, blocks, 32 * RPB,
-                 smem_bytes(32 * N1), st, in, out, Mp, n1, twM, tw2M, mode, lam, kre, scale, stop);
+                 smem_bytes(32 * N1), st, in, out, Mp, n1, twM, twB, tw2M, mode, lam, kre, scale, stop);
 }
 
 }  // namespace ff
@@ -235,11 +293,11 @@ void fft_pass(const TcDst* T, const float* in, float* out, int mode, float kre, 
               const double* stop, cudaStream_t st) {
   const int M = T->n1 + 1;
   switch (M) {
-    case 64: ff::launch_n1<2>(in, out, T->Mp, T->n1, T->twM, T->tw2M, mode, T->lam, kre, scale, P, stop, st); break;
-    case 128: ff::launch_n1<4>(in, out, T->Mp, T->n1, T->twM, T->tw2M, mode, T->lam, kre, scale, P, stop, st); break;
-    case 256: ff::launch_n1<8>(in, out, T->Mp, T->n1, T->twM, T->tw2M, mode, T->lam, kre, scale, P, stop, st); break;
-    case 512: ff::launch_n1<16>(in, out, T->Mp, T->n1, T->twM, T->tw2M, mode, T->lam, kre, scale, P, stop, st); break;
-    case 1024: ff::launch_n1<32>(in, out, T->Mp, T->n1, T->twM, T->tw2M, mode, T->lam, kre, scale, P, stop, st); break;
+    case 64: ff::launch_n1<2>(in, out, T->Mp, T->n1, T->twM, T->twB, T->tw2M, mode, T->lam, kre, scale, P, stop, st); break;
+    case 128: ff::launch_n1<4>(in, out, T->Mp, T->n1, T->twM, T->twB, T->tw2M, mode, T->lam, kre, scale, P, stop, st); break;
+    case 256: ff::launch_n1<8>(in, out, T->Mp, T->n1, T->twM, T->twB, T->tw2M, mode, T->lam, kre, scale, P, stop, st); break;
+    case 512: ff::launch_n1<16>(in, out, T->Mp, T->n1, T->twM, T->twB, T->tw2M, mode, T->lam, kre, scale, P, stop, st); break;
+    case 1024: ff::launch_n1<32>(in, out, T->Mp, T->n1, T->twM, T->twB, T->tw2M, mode, T->lam, kre, scale, P, stop, st); break;
     default: throw Status{KFBI_ERR_UNSUPPORTED, "FFT passes need M = 64 .. 1024, a power of two"};
   }
 }

@@ -508,6 +508,17 @@ __global__ void __launch_bounds__(CLT) k_arnoldi_cl(double2* __restrict__ V, int
     ld = nb;
   }
   double2* ws = w + e0;
+  if (rank == 0) {
+    // the stored rotations and g: written by earlier steps, read only at the
+    // end; loading them now overlaps their latency with the inner products
+    for (int i = threadIdx.x; i <= j + 1; i += CLT) {
+      if (i < j) {
+        gcs[i] = cs[i];
+        gsn[i] = sn[i];
+      }
+      gg[i] = g[i];
+    }
+  }
   // pass 1: <v_i, w> on this slice
   slice_dots<C>(Vb, ld, ws, ns, j, pa, warp, lane);
   cl.sync();
@@ -554,16 +565,10 @@ __global__ void __launch_bounds__(CLT) k_arnoldi_cl(double2* __restrict__ V, int
   double2* vn = V + (size_t)(j + 1) * nb + e0;
   for (int e = threadIdx.x; e < ns; e += CLT) vn[e] = make_double2(ws[e].x * inv, ws[e].y * inv);
   if (rank == 0) {
-    // stage the rotations, g and the new column in shared memory so the
+    // the new column joins the rotations and g staged at the start, so the
     // sequential rotation chain waits on no global loads
-    for (int i = threadIdx.x; i <= j + 1; i += CLT) {
-      if (i <= j) gcol[i] = make_double2(h1[i].x + h2[i].x, h1[i].y + h2[i].y);
-      if (i < j) {
-        gcs[i] = cs[i];
-        gsn[i] = sn[i];
-      }
-      gg[i] = g[i];
-    }
+    for (int i = threadIdx.x; i <= j; i += CLT)
+      gcol[i] = make_double2(h1[i].x + h2[i].x, h1[i].y + h2[i].y);
     __syncthreads();
     if (threadIdx.x == 0) {
       if (C)
@@ -1015,10 +1020,11 @@ kfbi_status gmres_solve(kfbi_domain* D, double kre, double kim, const double* b,
   // operator inside GMRES.
   const int nb = D->nb;
   const dim3 vb((nb + 255) / 256);
+  // ||b|| goes to scal[0]; it is read with the first residual (one host
+  // round trip instead of two), before the inner solves reuse the slot
   KFBI_LAUNCH_P(KFBI_PROF_KRYLOV, k_bnorm, 1, kThreads, 0, st, (const double2*)b, nb, D->d_scal,
                 tol);
-  read_scalars(D, st);
-  const double bnorm = D->h_scal[0];
+  double bnorm = 0.0;
   int it = 0, apps = 0;
   double rn = 0.0;
   bool conv = false;
@@ -1041,6 +1047,7 @@ kfbi_status gmres_solve(kfbi_domain* D, double kre, double kim, const double* b,
                   (const double2*)ax, (double2*)D->d_Rv, nb, D->d_scal);
     KFBI_CHECK_LAUNCH();
     read_scalars(D, st);
+    if (sweep == 0) bnorm = D->h_scal[0];
     rn = D->h_scal[1];
     if (!std::isfinite(rn)) {
       D->err = "non-finite density residual";

@@ -1136,16 +1136,23 @@ TcDst* tc_create(kfbi_domain* D, const Plan& P) {
       const int M = D->M;
       if (!fft_supported(M)) throw Status{KFBI_ERR_UNSUPPORTED, "FFT passes need M = 64 .. 1024, a power of two"};
       // W_M^j and exp(-i pi j / M), j < M, in float64 then rounded
-      std::vector<float2> tw(M), tw2(M);
+      // (the exponent n2 k1 is reduced mod M before the angle is formed)
+      std::vector<float2> tw(M), twb(M), tw2(M);
+      auto w = [M](long long j) {
+        const double a = -2.0 * M_PI * (double)(j % M) / M;
+        return make_float2((float)std::cos(a), (float)std::sin(a));
+      };
       for (int j = 0; j < M; ++j) {
-        const double a = -2.0 * M_PI * j / M, b = -M_PI * j / M;
-        tw[j] = make_float2((float)std::cos(a), (float)std::sin(a));
+        tw[j] = w(j);
+        const double b = -M_PI * j / M;
         tw2[j] = make_float2((float)std::cos(b), (float)std::sin(b));
       }
-      KFBI_CUDA(cudaMalloc(&T->twM, M * sizeof(float2)));
-      KFBI_CUDA(cudaMalloc(&T->tw2M, M * sizeof(float2)));
-      T->bytes += 2LL * M * (long long)sizeof(float2);
+      for (int k1 = 0; k1 < M / 32; ++k1)
+        for (int n2 = 0; n2 < 32; ++n2) twb[k1 * 32 + n2] = w((long long)n2 * k1);
+      for (float2** pp : {&T->twM, &T->twB, &T->tw2M}) KFBI_CUDA(cudaMalloc(pp, M * sizeof(float2)));
+      T->bytes += 3LL * M * (long long)sizeof(float2);
       KFBI_CUDA(cudaMemcpy(T->twM, tw.data(), M * sizeof(float2), cudaMemcpyHostToDevice));
+      KFBI_CUDA(cudaMemcpy(T->twB, twb.data(), M * sizeof(float2), cudaMemcpyHostToDevice));
       KFBI_CUDA(cudaMemcpy(T->tw2M, tw2.data(), M * sizeof(float2), cudaMemcpyHostToDevice));
       fft_prepare(M);
       T->fft = true;
@@ -1167,6 +1174,7 @@ void tc_destroy(TcDst* T) {
   if (T->node_col) cudaFree(T->node_col);
   if (T->d_maps) cudaFree(T->d_maps);
   if (T->twM) cudaFree(T->twM);
+  if (T->twB) cudaFree(T->twB);
   if (T->tw2M) cudaFree(T->tw2M);
   delete T;
 }
@@ -1182,7 +1190,7 @@ long long tc_bytes_for(const Plan& P, int Mp) {
     const int rows = P.irr.back() / P.n1 - P.irr.front() / P.n1 + 1;
     b += (long long)((rows + 1 + P.n_irr()) * sizeof(int));
   }
-  if (P.desc.precision == KFBI_MIXED_FFT32) b += 2LL * P.M * (long long)sizeof(float2);
+  if (P.desc.precision == KFBI_MIXED_FFT32) b += 3LL * P.M * (long long)sizeof(float2);
   return b + (long long)(kNumMaps * sizeof(CUtensorMap));
 }
 

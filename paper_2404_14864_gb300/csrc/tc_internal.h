@@ -89,10 +89,11 @@ struct TcDst {
   // flag, passed to the kernels of the fast (sparse-route) application
   const double* stop = nullptr;
   // KFBI_MIXED_FFT32: passes by FP32 FFT (fft_dst.cu) on single FP32 planes
-  // (Rh, T1h, T2h, U; the lo planes stay unused); twiddles W_M^j and
-  // exp(-i pi j / M), j < M
+  // (Rh, T1h, T2h, U; the lo planes stay unused); twiddles W_M^j,
+  // W_M^{n2 k1} at [k1][n2] (n2 < 32) and exp(-i pi j / M), j < M
   bool fft = false;
   float2* twM = nullptr;
+  float2* twB = nullptr;
   float2* tw2M = nullptr;
 };
 
