@@ -61,7 +61,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--M", type=int, default=1024)
-    ap.add_argument("--precision", default="tf32", choices=["tf32", "fft32", "fp64"])
+    ap.add_argument("--precision", default="fft32", choices=["tf32", "fft32", "fp64"])
+    ap.add_argument("--no-alt-path", action="store_true",
+                    help="skip the second (TF32 tensor-core) measurement of the default run")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--cpu-steps", type=int, default=2)
@@ -226,10 +228,8 @@ def run_ours(args, rank, world, local_rank):
     clk = ClockSampler(local_rank if "CUDA_VISIBLE_DEVICES" not in os.environ
                        else os.environ["CUDA_VISIBLE_DEVICES"].split(",")[local_rank])
     clk.start()
-    kfbi.kfbi_profile_reset()
-    # time only the dominant kernel class live (two event records per DST
-    # launch); the other classes are timed in a separate untimed step below
-    kfbi.kfbi_profile_enable([kfbi.PROF_DST])
+    # timed region: per-step CUDA events only (an event between two kernels
+    # would serialise the programmatic-dependent launches it measures)
     n_launch0 = kfbi.launch_count()
     lat = []
     t0 = time.perf_counter()
@@ -237,13 +237,26 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0
     n_launch = kfbi.launch_count() - n_launch0
-    kfbi.kfbi_profile_enable(False)
-    prof = {"dst": kfbi.kfbi_profile_read(kfbi.PROF_DST),
-            "dst_flops": kfbi.kfbi_profile_work(kfbi.PROF_DST)}
     clocks = clk.stop()
     if world > 1:
         import torch.distributed as dist
         dist.barrier()
+    # second timed pass over the same steps with an event pair around every
+    # launch of the dominant kernel class: its average launch duration and
+    # the flops those launches issued, for the roofline
+    st_r = new_state(dom)
+    run_steps(st_r, 0, Wm, False, [])
+    torch.cuda.synchronize()
+    kfbi.kfbi_profile_reset()
+    kfbi.kfbi_profile_enable([kfbi.PROF_DST])
+    lat_r = []
+    run_steps(st_r, Wm, K, True, lat_r)
+    torch.cuda.synchronize()
+    kfbi.kfbi_profile_enable(False)
+    prof = {"dst": kfbi.kfbi_profile_read(kfbi.PROF_DST),
+            "dst_flops": kfbi.kfbi_profile_work(kfbi.PROF_DST),
+            "ms_per_step_instrumented": sum(lat_r) / K}
+    st_r.close()
     t_dev = sum(lat) / 1e3
     t_final = (Wm + K + 1) * dt
     u = st.get_u()
@@ -318,6 +331,8 @@ def roofline(res, M):
     flops = res["prof"]["dst_flops"]
     if n == 0 or ms <= 0:
         return None
+    how = ("CUDA event pair around every DST launch, on its stream, in a second timed pass "
+           "of the same steps (%.3f ms/step with those events)" % res["prof"]["ms_per_step_instrumented"])
     avg_s = ms / n / 1e3
     from paper_2404_14864_gb300 import kfbi
     peaks = {}
@@ -331,7 +346,8 @@ def roofline(res, M):
                 "frac": achieved / 1.25, "traffic": None,
                 "kernel": "k_dgemm_t (float64 DST-I pass)",
                 "peak_source": "nominal GB300 FP64 rate (1.25 TFLOP/s, profiling recipe table)",
-                "avg_launch_us": avg_s * 1e6, "launches": n, "flops_per_launch": flops / n}
+                "avg_launch_us": avg_s * 1e6, "launches": n, "flops_per_launch": flops / n,
+                "timing": how}
     if res["prec"] == kfbi.KFBI_MIXED_FFT32:
         # one pass reads every row of an FP32 plane and writes it transposed
         # (the wave workload is real: one plane)
@@ -343,7 +359,7 @@ def roofline(res, M):
                 "kernel": "k_dst_fft (FP32 FFT DST-I pass)",
                 "peak_source": "of measured: STREAM-style copy (hbm_gbs)",
                 "algorithmic_bytes_per_launch": nbytes, "avg_launch_us": avg_s * 1e6,
-                "launches": n, "flops_per_launch": flops / n}
+                "launches": n, "flops_per_launch": flops / n, "timing": how}
     bf16 = peaks.get("bf16_tflops_sustained", 1700.0)
     peak = bf16 * (1.1 / 2.25)
     return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
@@ -351,7 +367,8 @@ def roofline(res, M):
             "traffic_unit": "bytes per launch",
             "kernel": "k_tc_pass (tcgen05 TF32x3 DST-I pass)",
             "peak_source": "of measured: bf16 sustained x nominal tf32/bf16 ratio (1.1/2.25)",
-            "avg_launch_us": avg_s * 1e6, "launches": n, "flops_per_launch": flops / n}
+            "avg_launch_us": avg_s * 1e6, "launches": n, "flops_per_launch": flops / n,
+            "timing": how}
 
 
 # ----------------------------------------------------------------------------
@@ -577,6 +594,17 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
 
     res = run_ours(args, rank, world, local_rank)
+    alt = None
+    if world == 1 and args.precision == "fft32" and not args.no_alt_path:
+        # the same workload with the TF32 tensor-core DST passes
+        import copy
+        a2 = copy.copy(args)
+        a2.precision, a2.no_fp64_compare = "tf32", True
+        r2 = run_ours(a2, rank, world, local_rank)
+        alt = {"value": M * M * args.steps / r2["t_dev"], "unit": UNIT,
+               "ms_per_step": 1e3 * r2["t_dev"] / args.steps, "linf_vs_exact": r2["err"],
+               "roofline": roofline(r2, M),
+               "e2e": {"value": M * M * args.steps / r2["t_e2e"], "unit": UNIT}}
     K = args.steps
     t_dev, t_e2e = max_over_ranks([res["t_dev"], res["t_e2e"]], world, "cuda")
 
@@ -596,10 +624,12 @@ def main():
             "n_gpus": world,
             "steps": K, "warmup": args.warmup, "ms_per_step": 1e3 * t_dev / K,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64" if res["prec"] == kfbi.KFBI_FP64 else "tf32x3-f32acc+f64",
+            "dtype": {kfbi.KFBI_FP64: "f64", kfbi.KFBI_MIXED_TF32: "tf32x3-f32acc+f64",
+                      kfbi.KFBI_MIXED_FFT32: "fp32-fft+f64"}[res["prec"]],
             "data": "synthetic (manufactured solution)",
-            "config": config(M, desc, dt, "fp64" if res["prec"] == kfbi.KFBI_FP64 else
-                             "mixed-tf32x3"),
+            "config": config(M, desc, dt, {kfbi.KFBI_FP64: "fp64",
+                                           kfbi.KFBI_MIXED_TF32: "mixed-tf32x3",
+                                           kfbi.KFBI_MIXED_FFT32: "mixed-fp32-fft"}[res["prec"]]),
             "latency_ms": {"p50": p(0.5), "p99": p(0.99), "max": lat[-1]},
             "linf_vs_exact": res["err"],
             "gmres_iters_per_step": res["iters"],
@@ -614,6 +644,8 @@ def main():
             "fp64_gpu": res["fp64"],
             "wall_s_timed": res["wall"],
         }
+        if alt:
+            line["tf32_tensor_path"] = alt
         if res["note"]:
             line["note"] = res["note"]
         print(json.dumps(line))

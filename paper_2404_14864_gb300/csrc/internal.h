@@ -32,12 +32,14 @@ void prof_add_work(void* tok, double work);
 // programmatic stream serialization (unless KFBI_PDL=0), so it can be
 // scheduled while the previous kernel of its stream drains; its first
 // statement, KFBI_PDL_ENTRY, waits for that kernel's completion and memory
-// before any global access and then lets the next kernel launch.  Stream
-// order is kept; what overlaps is the launch and block scheduling.  For a
-// kernel not launched as a dependent both instructions return at once.
+// before any global access.  Stream order is kept; what overlaps is the
+// launch and block scheduling.  No kernel triggers its dependents early:
+// blocks of the next kernel launched at the start of the current one sat
+// waiting on its SMs and slowed it (a float64 DGEMM pass by a third, the
+// FFT passes by a quarter), so the dependents launch as its blocks exit.
+// For a kernel not launched as a dependent the wait returns at once.
 extern bool g_pdl;
-#define KFBI_PDL_ENTRY() \
-  asm volatile("griddepcontrol.wait;\n\tgriddepcontrol.launch_dependents;" ::: "memory")
+#define KFBI_PDL_ENTRY() asm volatile("griddepcontrol.wait;" ::: "memory")
 
 // Early exit of a kernel of a speculatively queued GMRES iteration: stop
 // points at the solver's convergence flag (nonzero once an earlier

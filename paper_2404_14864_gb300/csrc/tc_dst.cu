@@ -374,7 +374,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_pass(const __grid_constant__ 
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
   // programmatic dependent launch: the set-up above touches no global
-  // memory; wait for the previous kernel here, then let the next one launch
+  // memory; wait for the previous kernel here
   KFBI_PDL_ENTRY();
   // tile loop: CTA pairs (split K) walk the tiles together, rank r taking
   // K-block half r; otherwise every CTA walks its own tiles
