@@ -222,14 +222,31 @@ __global__ void __launch_bounds__(GT) k_cgs_update(const double2* __restrict__ V
 __device__ void givens_column(double2* col, int j, double hn, double* cs, double2* sn, double2* g,
                               double* scal) {
   col[j + 1] = make_double2(hn, 0.0);
+  // rotation i mixes the carried entry with the original col[i + 1]; the
+  // operands of rotation i + 1 are loaded during rotation i, so the chain
+  // is the arithmetic alone
+  double2 carry = col[0];
+  double c_n = 0.0;
+  double2 s_n = make_double2(0.0, 0.0), b_n = make_double2(0.0, 0.0);
+  if (j > 0) {
+    c_n = cs[0];
+    s_n = sn[0];
+    b_n = col[1];
+  }
   for (int i = 0; i < j; ++i) {
-    const double c = cs[i];
-    const double2 sv = sn[i], a = col[i], bb = col[i + 1];
+    const double c = c_n;
+    const double2 sv = s_n, bb = b_n, a = carry;
+    if (i + 1 < j) {
+      c_n = cs[i + 1];
+      s_n = sn[i + 1];
+      b_n = col[i + 2];
+    }
     const double2 t = cmul(sv, bb);
     const double2 u = cmul(make_double2(sv.x, -sv.y), a);
     col[i] = make_double2(c * a.x + t.x, c * a.y + t.y);
-    col[i + 1] = make_double2(-u.x + c * bb.x, -u.y + c * bb.y);
+    carry = make_double2(-u.x + c * bb.x, -u.y + c * bb.y);
   }
+  col[j] = carry;
   const double2 a = col[j];
   const double bre = col[j + 1].x;
   double c;
@@ -263,9 +280,21 @@ __device__ void givens_column(double2* col, int j, double hn, double* cs, double
 // only, which halves the dependent FP64 chain of each rotation.
 __device__ void givens_column_real(double2* col, int j, double hn, double* cs, double2* sn,
                                    double2* g, double* scal) {
+  // operands of rotation i + 1 are loaded during rotation i (see givens_column)
   double carry = col[0].x;
+  double c_n = 0.0, s_n = 0.0, b_n = 0.0;
+  if (j > 0) {
+    c_n = cs[0];
+    s_n = sn[0].x;
+    b_n = col[1].x;
+  }
   for (int i = 0; i < j; ++i) {
-    const double c = cs[i], sv = sn[i].x, b = col[i + 1].x;
+    const double c = c_n, sv = s_n, b = b_n;
+    if (i + 1 < j) {
+      c_n = cs[i + 1];
+      s_n = sn[i + 1].x;
+      b_n = col[i + 2].x;
+    }
     col[i] = make_double2(c * carry + sv * b, 0.0);
     carry = -sv * carry + c * b;
   }
@@ -489,7 +518,7 @@ __global__ void __launch_bounds__(CLT) k_arnoldi_cl(double2* __restrict__ V, int
   __shared__ double2 pa[65], pb[65], h1[65], h2[65], tmp[CLT], gcol[66], gsn[65], gg[66];
   __shared__ double gcs[65];
   __shared__ double pn[CLT / 32];
-  __shared__ double pnorm;
+  __shared__ double pnorm, s_hn;
   const int slice = (nb + CL - 1) / CL;
   const int e0 = min(nb, rank * slice), e1 = min(nb, e0 + slice), ns = e1 - e0;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -549,8 +578,9 @@ __global__ void __launch_bounds__(CLT) k_arnoldi_cl(double2* __restrict__ V, int
     pnorm = t[0];
   }
   cl.sync();
-  double nn;
-  {
+  if (threadIdx.x == 0) {
+    // one thread reads the CL partial norms (every thread of the cluster
+    // reading them all piled 4096 remote loads per CTA on 16 words)
     double v[CL_MAX];
 #pragma unroll
     for (int r = 0; r < CL_MAX; ++r) v[r] = r < CL ? *cl.map_shared_rank(&pnorm, r) : 0.0;
@@ -558,9 +588,13 @@ __global__ void __launch_bounds__(CLT) k_arnoldi_cl(double2* __restrict__ V, int
     for (int w2 = 1; w2 < CL_MAX; w2 <<= 1)
 #pragma unroll
       for (int r = 0; r + w2 < CL_MAX; r += 2 * w2) v[r] += v[r + w2];
-    nn = v[0];
+    s_hn = sqrt(v[0]);
   }
-  const double hn = sqrt(nn);
+  __syncthreads();
+  // that was the last read of a peer's shared memory: arrive on the
+  // cluster barrier now, wait for the peers only before leaving
+  asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+  const double hn = s_hn;
   const double inv = hn > 0.0 ? 1.0 / hn : 0.0;
   double2* vn = V + (size_t)(j + 1) * nb + e0;
   for (int e = threadIdx.x; e < ns; e += CLT) vn[e] = make_double2(ws[e].x * inv, ws[e].y * inv);
@@ -588,7 +622,7 @@ __global__ void __launch_bounds__(CLT) k_arnoldi_cl(double2* __restrict__ V, int
     }
   }
   // no CTA leaves while a peer may still read its shared memory
-  cl.sync();
+  asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 
 // x += V[:, :k] y with R y = g: one warp per CTA solves the triangle
