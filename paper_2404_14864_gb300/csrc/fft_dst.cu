@@ -31,6 +31,7 @@
 
 namespace kfbi {
 namespace ff {
+using kfbi::FftSparseRhs;
 
 constexpr int RPB = 8;  // rows (warps) per block
 
@@ -110,14 +111,18 @@ static_assert((1024 - 1) * (RPB + 1) <= RPB * 32 * 33 * 2, "staged output fits t
 
 // mode 0: plain transform; mode 1: eigenvalue division of the box solve,
 // out *= scale / (lam[r] + lam[c] - kre) for r < n1, 0 for padded rows r.
-template <int N1>
+// SPARSE: the input plane is not read; each warp builds its row from the
+// corrected values of the row's irregular nodes (the right-hand side of a
+// fast application is zero elsewhere), with the arithmetic of k_correct32.
+template <int N1, bool SPARSE>
 __global__ void __launch_bounds__(32 * RPB) k_dst_fft(const float* __restrict__ in,
                                                       float* __restrict__ out, int Mp, int n1,
                                                       const float2* __restrict__ twM,
                                                       const float2* __restrict__ twB,
                                                       const float2* __restrict__ tw2M, int mode,
                                                       const float* __restrict__ lam, float kre,
-                                                      float scale, const double* stop) {
+                                                      float scale, const double* stop,
+                                                      const FftSparseRhs sp) {
   constexpr int M = 32 * N1;
   constexpr int T = 32 * RPB;  // threads
   extern __shared__ float4 smem4[];
@@ -159,6 +164,43 @@ __global__ void __launch_bounds__(32 * RPB) k_dst_fft(const float* __restrict__ 
   KFBI_STOP_RETURN(stop);
   const int row0 = blockIdx.x * RPB;  // first row over all planes
   const int p = row0 / Mp, rr0 = row0 - p * Mp;
+  if constexpr (SPARSE) {
+    float* xrow = reinterpret_cast<float*>(s_ex + (size_t)warp * N1 * 33);
+#pragma unroll
+    for (int q = 0; q < M / 32; ++q) xrow[lane + 32 * q] = 0.f;
+    __syncwarp();
+    const int rl = rr0 + warp - sp.rmin;  // row within the irregular rows
+    if (rl >= 0 && rl < sp.nrows) {
+      const int ne = sp.row_start[rl + 1];
+      for (int n = sp.row_start[rl] + lane; n < ne; n += 32) {
+        float sr = 0.f, si = 0.f;
+        const int a1 = sp.arm_start[n + 1];
+        for (int a = sp.arm_start[n]; a < a1; ++a) {
+          int k = sp.arm_k0[a];
+          float ar = 0.f, ai = 0.f, br = 0.f, bi = 0.f;
+#pragma unroll
+          for (int m = 0; m < 6; ++m) {
+            const float al = sp.alpha[m * sp.n_arms + a], be = sp.beta[m * sp.n_arms + a];
+            const float pr = (float)sp.phi[(size_t)k * sp.ps];
+            ar = fmaf(al, pr, ar);
+            br = fmaf(be, pr, br);
+            if (sp.cplx) {
+              const float pi = (float)sp.phi[(size_t)k * sp.ps + 1];
+              ai = fmaf(al, pi, ai);
+              bi = fmaf(be, pi, bi);
+            }
+            k = (k + 1 == sp.nb) ? 0 : k + 1;
+          }
+          sr += ar + sp.kre * br;
+          if (sp.cplx) {
+            sr -= sp.kim * bi;
+            si += ai + sp.kre * bi + sp.kim * br;
+          }
+        }
+        xrow[sp.node_col[n]] = p == 0 ? sr : si;
+      }
+    }
+  } else
   // the block's RPB input rows (M floats each) into the warps' transpose
   // buffers: all loads first, then all stores
   {
@@ -251,17 +293,25 @@ __global__ void __launch_bounds__(32 * RPB) k_dst_fft(const float* __restrict__ 
 
 template <int N1>
 static void set_smem_attr() {
-  KFBI_CUDA(cudaFuncSetAttribute(k_dst_fft<N1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  KFBI_CUDA(cudaFuncSetAttribute(k_dst_fft<N1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem_bytes(32 * N1)));
+  KFBI_CUDA(cudaFuncSetAttribute(k_dst_fft<N1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem_bytes(32 * N1)));
 }
 
 template <int N1>
 static void launch_n1(const float* in, float* out, int Mp, int n1, const float2* twM,
-                      const float2* twB, const float2* tw2M, int mode, const float* lam, float kre, float scale,
-                      int P, const double* stop, cudaStream_t st) {
+                      const float2* twB, const float2* tw2M, int mode, const float* lam, float kre,
+                      float scale, int P, const double* stop, cudaStream_t st,
+                      const FftSparseRhs* sp) {
   const int blocks = P * Mp / RPB;
-  KFBI_LAUNCH_PW(KFBI_PROF_DST, fft_pass_flops(32 * N1, P * Mp), k_dst_fft<N1>, blocks, 32 * RPB,
-                 smem_bytes(32 * N1), st, in, out, Mp, n1, twM, twB, tw2M, mode, lam, kre, scale, stop);
+  const double fl = fft_pass_flops(32 * N1, P * Mp);
+  if (sp)
+    KFBI_LAUNCH_PW(KFBI_PROF_DST, fl, (k_dst_fft<N1, true>), blocks, 32 * RPB, smem_bytes(32 * N1),
+                   st, in, out, Mp, n1, twM, twB, tw2M, mode, lam, kre, scale, stop, *sp);
+  else
+    KFBI_LAUNCH_PW(KFBI_PROF_DST, fl, (k_dst_fft<N1, false>), blocks, 32 * RPB, smem_bytes(32 * N1),
+                   st, in, out, Mp, n1, twM, twB, tw2M, mode, lam, kre, scale, stop, FftSparseRhs{});
 }
 
 }  // namespace ff
@@ -290,14 +340,14 @@ void fft_prepare(int M) {
 }
 
 void fft_pass(const TcDst* T, const float* in, float* out, int mode, float kre, float scale, int P,
-              const double* stop, cudaStream_t st) {
+              const double* stop, cudaStream_t st, const FftSparseRhs* sp) {
   const int M = T->n1 + 1;
   switch (M) {
-    case 64: ff::launch_n1<2>(in, out, T->Mp, T->n1, T->twM, T->twB, T->tw2M, mode, T->lam, kre, scale, P, stop, st); break;
-    case 128: ff::launch_n1<4>(in, out, T->Mp, T->n1, T->twM, T->twB, T->tw2M, mode, T->lam, kre, scale, P, stop, st); break;
-    case 256: ff::launch_n1<8>(in, out, T->Mp, T->n1, T->twM, T->twB, T->tw2M, mode, T->lam, kre, scale, P, stop, st); break;
-    case 512: ff::launch_n1<16>(in, out, T->Mp, T->n1, T->twM, T->twB, T->tw2M, mode, T->lam, kre, scale, P, stop, st); break;
-    case 1024: ff::launch_n1<32>(in, out, T->Mp, T->n1, T->twM, T->twB, T->tw2M, mode, T->lam, kre, scale, P, stop, st); break;
+    case 64: ff::launch_n1<2>(in, out, T->Mp, T->n1, T->twM, T->twB, T->tw2M, mode, T->lam, kre, scale, P, stop, st, sp); break;
+    case 128: ff::launch_n1<4>(in, out, T->Mp, T->n1, T->twM, T->twB, T->tw2M, mode, T->lam, kre, scale, P, stop, st, sp); break;
+    case 256: ff::launch_n1<8>(in, out, T->Mp, T->n1, T->twM, T->twB, T->tw2M, mode, T->lam, kre, scale, P, stop, st, sp); break;
+    case 512: ff::launch_n1<16>(in, out, T->Mp, T->n1, T->twM, T->twB, T->tw2M, mode, T->lam, kre, scale, P, stop, st, sp); break;
+    case 1024: ff::launch_n1<32>(in, out, T->Mp, T->n1, T->twM, T->twB, T->tw2M, mode, T->lam, kre, scale, P, stop, st, sp); break;
     default: throw Status{KFBI_ERR_UNSUPPORTED, "FFT passes need M = 64 .. 1024, a power of two"};
   }
 }

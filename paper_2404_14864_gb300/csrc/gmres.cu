@@ -356,6 +356,126 @@ __global__ void __launch_bounds__(GT) k_cgs_finalize(double2* __restrict__ V, in
   }
 }
 
+// Rotations 0 .. j-1 of the Givens sequence applied to a new Hessenberg
+// column col[0 .. j] by one warp (j <= 64).  Rotation i maps the carried
+// entry x (col[i] after rotation i-1) and the untouched col[i+1] to
+// col[i] = c_i x + s_i col[i+1] and the next carry -conj(s_i) x +
+// c_i col[i+1]: the carries follow x_{i+1} = al_i x_i + be_i with al_i =
+// -conj(s_i), be_i = c_i col[i+1], a first-order linear recurrence, so they
+// are a prefix composition of affine maps.  Each lane composes the maps of
+// rotations 2 lane and 2 lane + 1, a five-level scan over the lanes gives
+// every lane the composition of all earlier maps, and each lane then forms
+// its two outputs.  The chain is about ten dependent float64 operations
+// instead of j (a float64 operation waits ~100+ cycles on this part).
+// Leaves the rotated entries in col[0 .. j-1] and the last carry in col[j].
+template <bool C>
+__device__ void rotate_column_warp(double2* col, int j, const double* cs, const double2* sn,
+                                   int lane) {
+  auto mul = [](double2 a, double2 b) {
+    return C ? make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x)
+             : make_double2(a.x * b.x, 0.0);
+  };
+  auto add = [](double2 a, double2 b) { return make_double2(a.x + b.x, C ? a.y + b.y : 0.0); };
+  const int i0 = 2 * lane, i1 = 2 * lane + 1;
+  double2 al[2], be[2], sv[2], bv[2];
+  double cv[2];
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    const int i = 2 * lane + q;
+    if (i < j) {
+      cv[q] = cs[i];
+      sv[q] = sn[i];
+      bv[q] = col[i + 1];
+      al[q] = make_double2(-sv[q].x, C ? sv[q].y : 0.0);
+      be[q] = make_double2(cv[q] * bv[q].x, C ? cv[q] * bv[q].y : 0.0);
+    } else {  // identity map
+      cv[q] = 1.0;
+      sv[q] = make_double2(0.0, 0.0);
+      bv[q] = make_double2(0.0, 0.0);
+      al[q] = make_double2(1.0, 0.0);
+      be[q] = make_double2(0.0, 0.0);
+    }
+  }
+  const double2 x0 = col[0];
+  // this lane's composition f_i1 o f_i0, then the inclusive scan
+  double2 A = mul(al[1], al[0]), B = add(mul(al[1], be[0]), be[1]);
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    double2 Ap, Bp;
+    Ap.x = __shfl_up_sync(0xffffffffu, A.x, d);
+    Ap.y = __shfl_up_sync(0xffffffffu, A.y, d);
+    Bp.x = __shfl_up_sync(0xffffffffu, B.x, d);
+    Bp.y = __shfl_up_sync(0xffffffffu, B.y, d);
+    if (lane >= d) {
+      B = add(mul(A, Bp), B);
+      A = mul(A, Ap);
+    }
+  }
+  // composition of the maps of all earlier lanes applied to col[0]
+  double2 Ae, Be;
+  Ae.x = __shfl_up_sync(0xffffffffu, A.x, 1);
+  Ae.y = __shfl_up_sync(0xffffffffu, A.y, 1);
+  Be.x = __shfl_up_sync(0xffffffffu, B.x, 1);
+  Be.y = __shfl_up_sync(0xffffffffu, B.y, 1);
+  if (lane == 0) {
+    Ae = make_double2(1.0, 0.0);
+    Be = make_double2(0.0, 0.0);
+  }
+  const double2 x_0 = add(mul(Ae, x0), Be);          // carry entering rotation i0
+  const double2 x_1 = add(mul(al[0], x_0), be[0]);   // carry entering rotation i1
+  const double2 x_2 = add(mul(al[1], x_1), be[1]);   // carry after rotation i1
+  __syncwarp();  // every lane has read its inputs before the column is overwritten
+  if (i0 < j) col[i0] = add(make_double2(cv[0] * x_0.x, C ? cv[0] * x_0.y : 0.0), mul(sv[0], bv[0]));
+  if (i1 < j) col[i1] = add(make_double2(cv[1] * x_1.x, C ? cv[1] * x_1.y : 0.0), mul(sv[1], bv[1]));
+  if (i0 == j - 1) col[j] = x_1;
+  if (i1 == j - 1) col[j] = x_2;
+  __syncwarp();
+}
+
+// The new rotation of an Arnoldi step: zeroes hn below the rotated entry
+// a = col[j], stores (c, s), updates col and g and the residual estimate
+// (scal[1]) and convergence flag (scal[2]).
+template <bool C>
+__device__ void givens_new(double2* col, int j, double hn, double* cs, double2* sn, double2* g,
+                           double* scal) {
+  const double2 a = col[j];
+  const double bre = hn;
+  double c;
+  double2 sv;
+  // one reciprocal square root per quantity (Hessenberg entries are far
+  // from the overflow range); division and hypot are long chains of
+  // dependent float64 operations on this part
+  const double a2 = C ? a.x * a.x + a.y * a.y : a.x * a.x;
+  if (bre == 0.0) {
+    c = 1.0;
+    sv = make_double2(0.0, 0.0);
+  } else if (a2 == 0.0) {
+    c = 0.0;
+    sv = make_double2(1.0, 0.0);
+  } else {
+    const double inv_den = rsqrt(a2 + bre * bre);
+    const double inv_aa = rsqrt(a2);
+    const double aa = a2 * inv_aa;
+    c = aa * inv_den;
+    const double sb = bre * inv_den;
+    if (C)
+      sv = make_double2(a.x * inv_aa * sb, a.y * inv_aa * sb);
+    else
+      sv = make_double2((a.x < 0.0 ? -1.0 : 1.0) * sb, 0.0);
+  }
+  cs[j] = c;
+  sn[j] = sv;
+  col[j] = make_double2(c * a.x + sv.x * bre, C ? c * a.y + sv.y * bre : 0.0);
+  col[j + 1] = make_double2(0.0, 0.0);
+  const double2 gj = g[j];
+  const double2 u = C ? cmul(make_double2(sv.x, -sv.y), gj) : make_double2(sv.x * gj.x, 0.0);
+  g[j + 1] = make_double2(-u.x, -u.y);
+  g[j] = make_double2(c * gj.x, C ? c * gj.y : 0.0);
+  const double res = C ? hypot(g[j + 1].x, g[j + 1].y) : fabs(sv.x * gj.x);
+  scal[1] = res;
+  scal[2] = !isfinite(res) ? 2.0 : ((res <= scal[3] * scal[0] || hn == 0.0) ? 1.0 : 0.0);
+}
+
 // ---- one Arnoldi step in one launch: a thread-block cluster ----------------
 // The CTAs of one cluster each own a slice of the basis vectors, staged once
 // into shared memory (when it fits) because every phase reads it.  Every
@@ -578,17 +698,17 @@ __global__ void __launch_bounds__(CLT) k_arnoldi_cl(double2* __restrict__ V, int
     pnorm = t[0];
   }
   cl.sync();
-  if (threadIdx.x == 0) {
-    // one thread reads the CL partial norms (every thread of the cluster
-    // reading them all piled 4096 remote loads per CTA on 16 words)
-    double v[CL_MAX];
+  if (threadIdx.x < 32) {
+    // lane r < CL reads rank r's partial norm (every thread of the cluster
+    // reading them all piled 4096 remote loads per CTA on 16 words); the
+    // pairwise tree by shuffles adds in the same fixed order on every CTA
+    double v = lane < CL ? *cl.map_shared_rank(&pnorm, lane) : 0.0;
 #pragma unroll
-    for (int r = 0; r < CL_MAX; ++r) v[r] = r < CL ? *cl.map_shared_rank(&pnorm, r) : 0.0;
-#pragma unroll
-    for (int w2 = 1; w2 < CL_MAX; w2 <<= 1)
-#pragma unroll
-      for (int r = 0; r + w2 < CL_MAX; r += 2 * w2) v[r] += v[r + w2];
-    s_hn = sqrt(v[0]);
+    for (int w2 = 1; w2 < CL_MAX; w2 <<= 1) {
+      const double o = __shfl_down_sync(0xffffffffu, v, w2);
+      if ((lane & (2 * w2 - 1)) == 0) v += o;
+    }
+    if (lane == 0) s_hn = sqrt(v);
   }
   __syncthreads();
   // that was the last read of a peer's shared memory: arrive on the
@@ -604,12 +724,8 @@ __global__ void __launch_bounds__(CLT) k_arnoldi_cl(double2* __restrict__ V, int
     for (int i = threadIdx.x; i <= j; i += CLT)
       gcol[i] = make_double2(h1[i].x + h2[i].x, h1[i].y + h2[i].y);
     __syncthreads();
-    if (threadIdx.x == 0) {
-      if (C)
-        givens_column(gcol, j, hn, gcs, gsn, gg, scal);
-      else
-        givens_column_real(gcol, j, hn, gcs, gsn, gg, scal);
-    }
+    if (threadIdx.x < 32) rotate_column_warp<C>(gcol, j, gcs, gsn, threadIdx.x);
+    if (threadIdx.x == 0) givens_new<C>(gcol, j, hn, gcs, gsn, gg, scal);
     __syncthreads();
     double2* col = H + (size_t)j * (m + 1);
     for (int i = threadIdx.x; i <= j + 1; i += CLT) {

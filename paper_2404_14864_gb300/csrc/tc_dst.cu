@@ -1324,25 +1324,27 @@ static void tc_apply_sparse(kfbi_domain* D, double kre, double kim, const double
   const int Mp = T->Mp;
   const size_t plane = (size_t)Mp * Mp;
   if (T->fft) {
-    // FFT passes cost the same for any right-hand side: correct into the
-    // dense FP32 plane (zero away from the irregular nodes), three full
-    // passes, and the last pass evaluated at the stencil points only
-    if (T->rhs_sparse_planes < P) {
-      KFBI_CUDA(cudaMemsetAsync(T->Rh, 0, 2 * plane * sizeof(float), st));
-      T->rhs_sparse_planes = 2;
-    }
-    if (C)
-      KFBI_LAUNCH_P(KFBI_PROF_CORRECT, k_correct32<true>, (D->n_irr + 127) / 128, 128, 0, st, T->Rh,
-                    nullptr, plane, nullptr, D->d_irr_off, D->d_arm_start, D->d_arm_k0,
-                    D->d_arm_alpha32, D->d_arm_beta32, D->d_arm_fidx, D->d_arm_fcoef32, D->n_irr,
-                    D->n_arms, D->nb, phi, ps, (float)kre, (float)kim, nullptr, T->stop);
-    else
-      KFBI_LAUNCH_P(KFBI_PROF_CORRECT, k_correct32<false>, (D->n_irr + 127) / 128, 128, 0, st,
-                    T->Rh, nullptr, plane, nullptr, D->d_irr_off, D->d_arm_start, D->d_arm_k0,
-                    D->d_arm_alpha32, D->d_arm_beta32, D->d_arm_fidx, D->d_arm_fcoef32, D->n_irr,
-                    D->n_arms, D->nb, phi, ps, (float)kre, (float)kim, nullptr, T->stop);
+    // FFT passes cost the same for any right-hand side: the first pass
+    // builds its rows from the corrected irregular nodes (no plane is read),
+    // then two full passes and the last pass at the stencil points only
+    FftSparseRhs sp;
+    sp.row_start = T->row_start;
+    sp.node_col = T->node_col;
+    sp.rmin = T->rmin;
+    sp.nrows = T->nrows;
+    sp.arm_start = D->d_arm_start;
+    sp.arm_k0 = D->d_arm_k0;
+    sp.alpha = D->d_arm_alpha32;
+    sp.beta = D->d_arm_beta32;
+    sp.n_arms = D->n_arms;
+    sp.nb = D->nb;
+    sp.phi = phi;
+    sp.ps = ps;
+    sp.kre = (float)kre;
+    sp.kim = (float)kim;
+    sp.cplx = C ? 1 : 0;
     const float scale = (float)((2.0 / D->M) * (2.0 / D->M));
-    fft_pass(T, T->Rh, T->T1h, 0, 0.f, 0.f, P, T->stop, st);
+    fft_pass(T, nullptr, T->T1h, 0, 0.f, 0.f, P, T->stop, st, &sp);
     fft_pass(T, T->T1h, T->T2h, C ? 0 : 1, (float)kre, scale, P, T->stop, st);
     if (C)
       KFBI_LAUNCH_P(KFBI_PROF_GRID, k_eig_split_cplx, grid_for(plane, 256), 256, 0, st, T->T2h,

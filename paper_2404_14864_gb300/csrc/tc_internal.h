@@ -98,15 +98,34 @@ struct TcDst {
 };
 
 
+// Right-hand side of a fast application for the FFT first pass: the
+// irregular nodes by row (CSR from row rmin, in the order of the correction
+// tables) and what the correction of each needs.
+struct FftSparseRhs {
+  const int* row_start;
+  const int* node_col;
+  int rmin, nrows;
+  const int* arm_start;
+  const int* arm_k0;
+  const float* alpha;
+  const float* beta;
+  int n_arms, nb;
+  const double* phi;
+  int ps;
+  float kre, kim;
+  int cplx;
+};
+
 // FP32 FFT passes (fft_dst.cu).  fft_pass transforms every row of P planes
 // of `in` and writes out transposed (mode 1: eigenvalue division of the box
-// solve); stop as KFBI_STOP_RETURN.
+// solve); with sp the rows are built from the corrected irregular nodes
+// instead of read from `in`; stop as KFBI_STOP_RETURN.
 bool fft_supported(int M);
 size_t fft_smem_bytes(int M);
 void fft_prepare(int M);
 double fft_pass_flops(int M, int rows);
 void fft_pass(const TcDst* T, const float* in, float* out, int mode, float kre, float scale, int P,
-              const double* stop, cudaStream_t st);
+              const double* stop, cudaStream_t st, const FftSparseRhs* sp = nullptr);
 
 // Device tensor map of one of the domain's pass output planes (T1, T2 pairs
 // or U); throws for any other pointer.
