@@ -808,10 +808,17 @@ __global__ void __launch_bounds__(256) k_sparse_p1(const float* __restrict__ rv,
 }
 
 // Last pass restricted to the extraction stencil, fused with Eq. 3.36:
-// U(j', i') = sum_a T3[i'][a] S[j'][a] for the six stencil points of node k
-// (one warp each, FP32 lane sums then a tree), then u+ as in k_extract32.
+// U(j', i') = sum_a T3[i'][a] S[j'][a] at the six stencil points of node k,
+// then u+ as in k_extract32.  One block of GE_WARPS warps per node: the six
+// points lie in a 3 x 3 window of grid rows j and columns i, so the block
+// streams three rows of T3 and three rows of S (float4, each warp a
+// quarter of them) and forms all nine window sums, reduced over lanes and
+// warps; the six it needs are picked from shared memory.  (Six warps per
+// node with a full dot product each read twice the rows, 48 MB per
+// application at 1024^2; one warp per node left too few warps in flight.)
+constexpr int GE_WARPS = 4;
 template <bool C>
-__global__ void __launch_bounds__(192)
+__global__ void __launch_bounds__(32 * GE_WARPS)
     k_gather_extract(const float* __restrict__ T3, const float* __restrict__ S32, int Mp,
                      size_t plane, const int* __restrict__ gidx, const float* __restrict__ w,
                      const float* __restrict__ A, const float* __restrict__ B, int nb,
@@ -819,38 +826,87 @@ __global__ void __launch_bounds__(192)
                      double* __restrict__ out, int os, const double* stop) {
   KFBI_PDL_ENTRY();
   KFBI_STOP_RETURN(stop);
-  __shared__ float Ush[6][2];
-  const int k = blockIdx.x;
+  constexpr int NP = C ? 2 : 1;
+  __shared__ float win[GE_WARPS][NP][3][3];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  {
-    const int off = gidx[warp * nb + k];
-    const int jr = off / Mp, ic = off - jr * Mp;
-    const float* t0 = T3 + (size_t)ic * Mp;
-    const float* sr = S32 + (size_t)jr * Mp;
-    float s0 = 0.f, s1 = 0.f;
-    for (int a = lane; a < Mp; a += 32) {
-      const float sv = sr[a];
-      s0 = fmaf(t0[a], sv, s0);
-      if (C) s1 = fmaf(t0[plane + a], sv, s1);
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-      s0 += __shfl_xor_sync(0xffffffffu, s0, o);
-      if (C) s1 += __shfl_xor_sync(0xffffffffu, s1, o);
-    }
-    if (lane == 0) {
-      Ush[warp][0] = s0;
-      Ush[warp][1] = s1;
-    }
+  const int k = blockIdx.x;
+  int jm[6], im[6];
+  int jlo = Mp, ilo = Mp;
+#pragma unroll
+  for (int m = 0; m < 6; ++m) {
+    const int off = gidx[m * nb + k];
+    jm[m] = off / Mp;
+    im[m] = off - jm[m] * Mp;
+    jlo = min(jlo, jm[m]);
+    ilo = min(ilo, im[m]);
   }
+  const float4* tr[NP][3];
+  const float4* srow[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    // rows past the plane are clamped; their sums are never picked
+    const int ii = min(ilo + d, Mp - 1), jj = min(jlo + d, Mp - 1);
+#pragma unroll
+    for (int q = 0; q < NP; ++q)
+      tr[q][d] = reinterpret_cast<const float4*>(T3 + q * plane + (size_t)ii * Mp);
+    srow[d] = reinterpret_cast<const float4*>(S32 + (size_t)jj * Mp);
+  }
+  float acc[NP][3][3];
+#pragma unroll
+  for (int q = 0; q < NP; ++q)
+#pragma unroll
+    for (int dj = 0; dj < 3; ++dj)
+#pragma unroll
+      for (int di = 0; di < 3; ++di) acc[q][dj][di] = 0.f;
+  for (int a4 = threadIdx.x; a4 < Mp / 4; a4 += 32 * GE_WARPS) {
+    float4 t[NP][3], sv[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+#pragma unroll
+      for (int q = 0; q < NP; ++q) t[q][d] = tr[q][d][a4];
+      sv[d] = srow[d][a4];
+    }
+#pragma unroll
+    for (int q = 0; q < NP; ++q)
+#pragma unroll
+      for (int dj = 0; dj < 3; ++dj)
+#pragma unroll
+        for (int di = 0; di < 3; ++di) {
+          float x = acc[q][dj][di];
+          x = fmaf(t[q][di].x, sv[dj].x, x);
+          x = fmaf(t[q][di].y, sv[dj].y, x);
+          x = fmaf(t[q][di].z, sv[dj].z, x);
+          x = fmaf(t[q][di].w, sv[dj].w, x);
+          acc[q][dj][di] = x;
+        }
+  }
+#pragma unroll
+  for (int q = 0; q < NP; ++q)
+#pragma unroll
+    for (int dj = 0; dj < 3; ++dj)
+#pragma unroll
+      for (int di = 0; di < 3; ++di) {
+        float x = acc[q][dj][di];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        if (lane == 0) win[warp][q][dj][di] = x;
+      }
   __syncthreads();
   if (threadIdx.x != 0) return;
-  float sr = 0.f, si = 0.f;
+  float sr_ = 0.f, si = 0.f;
 #pragma unroll
   for (int m = 0; m < 6; ++m) {
     const float wm = w[m * nb + k];
-    sr = fmaf(wm, Ush[m][0], sr);
-    if (C) si = fmaf(wm, Ush[m][1], si);
+    float ur = 0.f, ui = 0.f;
+#pragma unroll
+    for (int v = 0; v < GE_WARPS; ++v) {
+      ur += win[v][0][jm[m] - jlo][im[m] - ilo];
+      if (C) ui += win[v][NP - 1][jm[m] - jlo][im[m] - ilo];
+    }
+    sr_ = fmaf(wm, ur, sr_);
+    if (C) si = fmaf(wm, ui, si);
   }
+  float sr = sr_;
   float ar = 0.f, ai = 0.f, br = 0.f, bi = 0.f;
   int kk = k - 2;
   if (kk < 0) kk += nb;
@@ -1107,6 +1163,24 @@ TcDst* tc_create(kfbi_domain* D, const Plan& P) {
       T->ct0 = imin / BC;
       T->nt3 = imax / BC + 1 - T->ct0;
     }
+    {
+      // k_gather_extract reads each node's six stencil points from a 3 x 3
+      // window of grid rows and columns
+      const int nb = D->nb, n1s = D->n1;
+      for (int k = 0; k < nb; ++k) {
+        int jlo = 1 << 30, jhi = -1, ilo = 1 << 30, ihi = -1;
+        for (int m = 0; m < 6; ++m) {
+          const int v = P.node_gidx[(size_t)k * 6 + m];
+          const int jj = v / n1s, ii = v % n1s;
+          jlo = std::min(jlo, jj);
+          jhi = std::max(jhi, jj);
+          ilo = std::min(ilo, ii);
+          ihi = std::max(ihi, ii);
+        }
+        if (jhi - jlo > 2 || ihi - ilo > 2)
+          throw Status{KFBI_ERR_GEOMETRY, "an extraction stencil spans more than 3 x 3 grid points"};
+      }
+    }
     const int Mp = D->Mp;
     make_map(&T->mS_hi, T->S_hi, Mp, Mp, BC);
     make_map(&T->mS_lo, T->S_lo, Mp, Mp, BC);
@@ -1352,11 +1426,11 @@ static void tc_apply_sparse(kfbi_domain* D, double kre, double kim, const double
                     T->stop);
     fft_pass(T, T->T2h, T->U, 0, 0.f, 0.f, P, T->stop, st);
     if (C)
-      KFBI_LAUNCH_P(KFBI_PROF_EXTRACT, k_gather_extract<true>, D->nb, 192, 0, st, T->U, T->S32, Mp,
+      KFBI_LAUNCH_P(KFBI_PROF_EXTRACT, k_gather_extract<true>, D->nb, 32 * GE_WARPS, 0, st, T->U, T->S32, Mp,
                     plane, D->d_node_gidx, D->d_node_w32, D->d_node_a32, D->d_node_b32, D->nb, phi,
                     ps, (float)kre, (float)kim, out, os, T->stop);
     else
-      KFBI_LAUNCH_P(KFBI_PROF_EXTRACT, k_gather_extract<false>, D->nb, 192, 0, st, T->U, T->S32, Mp,
+      KFBI_LAUNCH_P(KFBI_PROF_EXTRACT, k_gather_extract<false>, D->nb, 32 * GE_WARPS, 0, st, T->U, T->S32, Mp,
                     plane, D->d_node_gidx, D->d_node_w32, D->d_node_a32, D->d_node_b32, D->nb, phi,
                     ps, (float)kre, (float)kim, out, os, T->stop);
     KFBI_CHECK_LAUNCH();
@@ -1388,11 +1462,11 @@ static void tc_apply_sparse(kfbi_domain* D, double kre, double kim, const double
   d3.stop = T->stop;
   launch_pass(T, d3, st);
   if (C)
-    KFBI_LAUNCH_P(KFBI_PROF_EXTRACT, k_gather_extract<true>, D->nb, 192, 0, st, T->U, T->S32, Mp,
+    KFBI_LAUNCH_P(KFBI_PROF_EXTRACT, k_gather_extract<true>, D->nb, 32 * GE_WARPS, 0, st, T->U, T->S32, Mp,
                   plane, D->d_node_gidx, D->d_node_w32, D->d_node_a32, D->d_node_b32, D->nb, phi,
                   ps, (float)kre, (float)kim, out, os, T->stop);
   else
-    KFBI_LAUNCH_P(KFBI_PROF_EXTRACT, k_gather_extract<false>, D->nb, 192, 0, st, T->U, T->S32, Mp,
+    KFBI_LAUNCH_P(KFBI_PROF_EXTRACT, k_gather_extract<false>, D->nb, 32 * GE_WARPS, 0, st, T->U, T->S32, Mp,
                   plane, D->d_node_gidx, D->d_node_w32, D->d_node_a32, D->d_node_b32, D->nb, phi,
                   ps, (float)kre, (float)kim, out, os, T->stop);
   KFBI_CHECK_LAUNCH();
