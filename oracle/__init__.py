@@ -18,6 +18,7 @@ for the heat, wave and Schroedinger equations on irregular domains"):
   (Eq. 3.36).  ``apply_operator`` chains them: it evaluates the interior
   limit u+ at the boundary nodes of the solution of the interface problem
   (Eq. 3.30) with Phi = phi, Psi = psi, F = f-tilde.
+* ``richardson`` -- the Richardson iteration of Eq. 3.21
 * ``gmres``     -- restarted GMRES with modified Gram-Schmidt and Givens
   rotations for the Dirichlet BIE (Eq. 3.17) (Sec. 5 names GMRES as the
   Krylov alternative to the Richardson iteration of Eq. 3.21).
@@ -49,7 +50,7 @@ from .interface import (
     apply_operator,
     interface_solve,
 )
-from .gmres import gmres
+from .gmres import gmres, richardson
 from .steppers import HeatStepper, WaveStepper, SchrodingerStepper
 
 __all__ = [
@@ -57,5 +58,5 @@ __all__ = [
     "box_solve", "dst_matrix", "eigenvalues", "lagrange6_weights",
     "density_derivatives", "jumps_at", "jump_matrix3", "correction_rhs",
     "extraction", "extraction_stencil", "apply_operator", "interface_solve",
-    "gmres", "HeatStepper", "WaveStepper", "SchrodingerStepper",
+    "gmres", "richardson", "HeatStepper", "WaveStepper", "SchrodingerStepper",
 ]

@@ -78,3 +78,34 @@ def gmres(apply_A, b, x0=None, tol=1e-10, restart=50, maxit=1000):
         x = x + V[:k].T @ y
         if done:
             return x, it, abs(g[k]) / bnorm, True
+
+
+def richardson(apply_A, b, x0=None, gamma=0.9, tol=1e-10, maxit=10000):
+    """The Richardson iteration of Eq. 3.21 for Eq. 3.17.
+
+    With A = 1/2 I + W and b = g_D - Y f, Eq. 3.21 reads
+    phi_{k+1} = (1 - gamma/2) phi_k + gamma (g_D - Y f - W phi_k)
+              = phi_k + gamma (b - A phi_k),
+    gamma in (0, 1) in the paper.  Stops when ||b - A phi_k||_2 <= tol
+    ||b||_2: Sec. 4 leaves the convergence norm open, and the relative
+    2-norm of the residual (gamma^-1 times the change of phi) is the
+    reading taken here, the same test GMRES uses.
+    Returns (x, iterations, relative residual, converged flag): iterations
+    counts the updates made, i.e. operator applications minus one for the
+    final check."""
+    b = np.asarray(b)
+    dt = np.result_type(b, np.float64) if x0 is None else np.result_type(b, x0, np.float64)
+    x = np.zeros(len(b), dtype=dt) if x0 is None else np.array(x0, dtype=dt, copy=True)
+    bnorm = np.linalg.norm(b)
+    if bnorm == 0.0:
+        return np.zeros_like(x), 0, 0.0, True
+    it = 0
+    while True:
+        r = b - apply_A(x)
+        rel = np.linalg.norm(r) / bnorm
+        if rel <= tol:
+            return x, it, rel, True
+        if it >= maxit or not np.isfinite(rel):
+            return x, it, rel, False
+        x = x + gamma * r
+        it += 1
