@@ -62,6 +62,9 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--M", type=int, default=1024)
     ap.add_argument("--precision", default="fft32", choices=["tf32", "fft32", "fp64"])
+    ap.add_argument("--solver", default="gmres", choices=["gmres", "richardson"],
+                    help="density solver: GMRES(50) or the Richardson iteration of Eq. 3.21")
+    ap.add_argument("--gamma", type=float, default=0.5, help="Richardson step")
     ap.add_argument("--no-alt-path", action="store_true",
                     help="skip the second (TF32 tensor-core) measurement of the default run")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -83,9 +86,11 @@ def workload(M):
     return desc, 4.0 * h, 0.25
 
 
-def config(M, desc, dt, precision):
+def config(M, desc, dt, precision, solver="gmres", gamma=0.5):
+    sv = ("gmres restart 50, tol 1e-10" if solver == "gmres"
+          else "richardson gamma %g, tol 1e-10" % gamma)
     return {"workload": "wave-theta0.25-ellipse-%d" % M, "M": M, "unknowns": (M - 1) ** 2,
-            "n_boundary": desc["nb"], "dt": "4h", "theta": 0.25, "gmres": "restart 50, tol 1e-10",
+            "n_boundary": desc["nb"], "dt": "4h", "theta": 0.25, "solver": sv,
             "precision": precision, "l2": "flushed between timed steps (256 MiB write)",
             "box": [desc["lo"], desc["hi"]]}
 
@@ -177,14 +182,16 @@ def run_ours(args, rank, world, local_rank):
     prec = {"tf32": kfbi.KFBI_MIXED_TF32, "fft32": kfbi.KFBI_MIXED_FFT32,
             "fp64": kfbi.KFBI_FP64}[args.precision]
     note = None
+    sv = {"solver": kfbi.KFBI_RICHARDSON if args.solver == "richardson" else kfbi.KFBI_GMRES,
+          "gamma": args.gamma}
     try:
-        dom = kfbi.Domain(desc, prec, restart=50, tol=1e-10, maxit=2000)
+        dom = kfbi.Domain(desc, prec, restart=50, tol=1e-10, maxit=2000, **sv)
     except kfbi.KfbiError as e:
         if prec == kfbi.KFBI_FP64 or e.status != 8:
             raise
         note = "mixed path unavailable in this build (%s); fp64 path timed" % e
         prec = kfbi.KFBI_FP64
-        dom = kfbi.Domain(desc, prec, restart=50, tol=1e-10, maxit=2000)
+        dom = kfbi.Domain(desc, prec, restart=50, tol=1e-10, maxit=2000, **sv)
     K, Wm = args.steps, args.warmup
     n_total = Wm + K
     # boundary data for every step, resident on the device before timing
@@ -291,7 +298,7 @@ def run_ours(args, rank, world, local_rank):
     # the plain FP64 GPU path on the same steps, for the fixed-error comparison
     fp64 = None
     if prec != kfbi.KFBI_FP64 and not args.no_fp64_compare:
-        dom64 = kfbi.Domain(desc, kfbi.KFBI_FP64, restart=50, tol=1e-10, maxit=2000)
+        dom64 = kfbi.Domain(desc, kfbi.KFBI_FP64, restart=50, tol=1e-10, maxit=2000, **sv)
         st64 = new_state(dom64)
         run_steps(st64, 0, Wm, False, [])
         lat64 = []
@@ -629,10 +636,11 @@ def main():
             "data": "synthetic (manufactured solution)",
             "config": config(M, desc, dt, {kfbi.KFBI_FP64: "fp64",
                                            kfbi.KFBI_MIXED_TF32: "mixed-tf32x3",
-                                           kfbi.KFBI_MIXED_FFT32: "mixed-fp32-fft"}[res["prec"]]),
+                                           kfbi.KFBI_MIXED_FFT32: "mixed-fp32-fft"}[res["prec"]],
+                             args.solver, args.gamma),
             "latency_ms": {"p50": p(0.5), "p99": p(0.99), "max": lat[-1]},
             "linf_vs_exact": res["err"],
-            "gmres_iters_per_step": res["iters"],
+            "%s_iters_per_step" % args.solver: res["iters"],
             "roofline": roofline(res, M),
             "kernel_time_ms_one_step": {k: {"launches": v[0], "ms": v[1]}
                                         for k, v in res["breakdown"].items()},

@@ -86,10 +86,27 @@ typedef struct {
   int gmres_restart;   /* GMRES restart length m, 1..64 */
   double gmres_tol;    /* stop when ||r||_2 <= gmres_tol * ||b||_2 */
   int gmres_maxit;     /* total GMRES iterations per solve */
+  int solver;          /* kfbi_solver: how the density equation is solved;
+                          0 (a zero-initialised description) = GMRES */
+  double richardson_gamma; /* KFBI_RICHARDSON step gamma, 0 < gamma < 2 */
 } kfbi_domain_desc;
 
+/* Iterative solver of the density equation (Eq. 3.17) behind
+ * kfbi_solve_density and the time steppers of one domain.  gmres_tol and
+ * gmres_maxit bound both (for Richardson, maxit counts its updates).
+ *   KFBI_GMRES      restarted GMRES(gmres_restart), CGS2 Arnoldi in FP64.
+ *   KFBI_RICHARDSON the Richardson iteration of Eq. 3.21,
+ *                   phi <- phi + gamma (b - A phi), one operator application
+ *                   and one fused residual/update kernel per iteration.  The
+ *                   paper takes gamma in (0, 1); it converges whenever
+ *                   |1 - gamma lambda| < 1 on the spectrum of A = 1/2 I + W,
+ *                   so 0 < gamma < 2 is accepted.  Single domains only:
+ *                   batches and the server refuse such domains. */
+typedef enum { KFBI_GMRES = 0, KFBI_RICHARDSON = 1 } kfbi_solver;
+
 typedef struct {
-  int iters;           /* GMRES iterations (operator applications inside GMRES) */
+  int iters;           /* solver iterations (GMRES: operator applications inside
+                          GMRES; Richardson: updates of phi) */
   double rel_residual; /* final rotated-residual estimate / ||b|| */
   int converged;       /* 1 if rel_residual <= gmres_tol */
   int applications;    /* operator applications in the step (GMRES + 2) */
@@ -134,8 +151,9 @@ kfbi_status kfbi_interface_solve(kfbi_domain* dom, double kappa_re, double kappa
                                  const void* phi_dev, const void* f_dev, void* u_grid_dev,
                                  void* u_plus_dev, void* stream);
 
-/* Solve the Dirichlet BIE (Eq. 3.17) (1/2 I + W) phi = b by GMRES(m) with
- * FP64 Arnoldi (CGS2), Givens rotations and the domain's operator;
+/* Solve the Dirichlet BIE (Eq. 3.17) (1/2 I + W) phi = b with the domain's
+ * solver (kfbi_solver: GMRES(m) with FP64 Arnoldi (CGS2) and Givens
+ * rotations, or the Richardson iteration of Eq. 3.21) and operator;
  * phi_dev holds the initial guess on entry and the solution on exit.
  * Synchronous.  KFBI_ERR_NOT_CONVERGED if gmres_maxit is reached. */
 kfbi_status kfbi_solve_density(kfbi_domain* dom, double kappa_re, double kappa_im,

@@ -80,13 +80,14 @@ def gmres(apply_A, b, x0=None, tol=1e-10, restart=50, maxit=1000):
             return x, it, abs(g[k]) / bnorm, True
 
 
-def richardson(apply_A, b, x0=None, gamma=0.9, tol=1e-10, maxit=10000):
+def richardson(apply_A, b, x0=None, gamma=0.5, tol=1e-10, maxit=10000):
     """The Richardson iteration of Eq. 3.21 for Eq. 3.17.
 
     With A = 1/2 I + W and b = g_D - Y f, Eq. 3.21 reads
     phi_{k+1} = (1 - gamma/2) phi_k + gamma (g_D - Y f - W phi_k)
               = phi_k + gamma (b - A phi_k),
-    gamma in (0, 1) in the paper.  Stops when ||b - A phi_k||_2 <= tol
+    gamma in (0, 1) in the paper, which gives no value: 0.5 is the default
+    read here.  Stops when ||b - A phi_k||_2 <= tol
     ||b||_2: Sec. 4 leaves the convergence norm open, and the relative
     2-norm of the residual (gamma^-1 times the change of phi) is the
     reading taken here, the same test GMRES uses.

@@ -6,7 +6,8 @@ Delta u - kappa u = -F in Omega, u = g on Gamma (Eq. 3.13 with f = -F) by
 the boundary integral equation of Eq. 3.17:
 
   b = g - u+[phi = 0, f-tilde]          (Y f at the boundary nodes)
-  (1/2 I + W) phi = b                    (GMRES, phi_0 = previous phi)
+  (1/2 I + W) phi = b                    (GMRES, or the Richardson iteration
+                                          of Eq. 3.21; phi_0 = previous phi)
   U = interface solution for (f-tilde, phi), u^{n+1} = U on Omega nodes.
 
 The right-hand side F is carried as its own variable (Eqs. 3.4 and the
@@ -35,14 +36,15 @@ F^1 by initial boundary condition"):
 
 import numpy as np
 
-from .gmres import gmres
+from .gmres import gmres, richardson
 from .interface import apply_operator, interface_solve
 
 
 class _Base:
-    def __init__(self, dom, tau, tol=1e-10, restart=50, maxit=2000):
+    def __init__(self, dom, tau, tol=1e-10, restart=50, maxit=2000, solver="gmres", gamma=0.5):
         self.dom, self.tau = dom, float(tau)
         self.tol, self.restart, self.maxit = tol, restart, maxit
+        self.solver, self.gamma = solver, gamma
         self.mask = dom.interior_inside()
         self.phi = None
         self.iters = []
@@ -53,10 +55,13 @@ class _Base:
         Ft = np.where(self.mask, -F, 0.0)
         b = np.asarray(g) - apply_operator(dom, kappa, np.zeros(dom.nb, dtype=Ft.dtype), Ft)
         x0 = self.phi if self.phi is not None else np.zeros(dom.nb, dtype=b.dtype)
-        phi, it, res, ok = gmres(lambda v: apply_operator(dom, kappa, v), b, x0,
-                                 self.tol, self.restart, self.maxit)
+        A = lambda v: apply_operator(dom, kappa, v)
+        if self.solver == "richardson":
+            phi, it, res, ok = richardson(A, b, x0, self.gamma, self.tol, self.maxit)
+        else:
+            phi, it, res, ok = gmres(A, b, x0, self.tol, self.restart, self.maxit)
         if not ok:
-            raise RuntimeError("GMRES did not converge (res %.3e)" % res)
+            raise RuntimeError("%s did not converge (res %.3e)" % (self.solver, res))
         self.phi = phi
         self.iters.append(it)
         _, U = interface_solve(dom, kappa, phi, Ft)

@@ -1249,10 +1249,10 @@ void batch_bind(kfbi_batch* B, kfbi_domain* const* domains, int n) {
   if (!domains || n < 1 || n > 4096) throw Status{KFBI_ERR_ARG, "a batch holds 1 to 4096 domains"};
   for (int i = 0; i < n; ++i)
     if (!domains[i] || !domains[i]->tc || domains[i]->n_irr == 0 ||
-        domains[i]->restart != domains[0]->restart)
+        domains[i]->restart != domains[0]->restart || domains[i]->desc.solver != KFBI_GMRES)
       throw Status{KFBI_ERR_ARG,
-                   "every domain of a batch must be KFBI_MIXED_TF32 with an interface and the "
-                   "same gmres_restart"};
+                   "every domain of a batch must be KFBI_MIXED_TF32 with an interface, the "
+                   "GMRES solver and the same gmres_restart"};
   batch_reserve(B, n);
   if (B->iter_graph) {
     KFBI_CUDA(cudaGraphExecDestroy(B->iter_graph));

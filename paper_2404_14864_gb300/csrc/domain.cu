@@ -523,6 +523,15 @@ kfbi_status kfbi_create_domain(const kfbi_domain_desc* desc, void* stream, kfbi_
     set_global_error("GMRES parameters out of range (1 <= restart <= 64, maxit >= 1, tol > 0)");
     return KFBI_ERR_ARG;
   }
+  if (desc->solver != KFBI_GMRES && desc->solver != KFBI_RICHARDSON) {
+    set_global_error("unknown solver");
+    return KFBI_ERR_ARG;
+  }
+  if (desc->solver == KFBI_RICHARDSON &&
+      !(desc->richardson_gamma > 0.0 && desc->richardson_gamma < 2.0)) {
+    set_global_error("Richardson step gamma must lie in (0, 2)");
+    return KFBI_ERR_ARG;
+  }
   Plan plan;
   std::string err;
   kfbi_status s = build_plan(*desc, plan, err);

@@ -1152,6 +1152,182 @@ __global__ void k_axpy(double2* __restrict__ x, const double2* __restrict__ d, i
 }
 }  // namespace gm
 
+namespace gm {
+// Richardson scalars (scal): [0] ||b||, [1] ||r|| of the last step, [2] status
+// (0 running, 1 converged, 2 non-finite, 3 maxit updates made), [3] tol,
+// [4] updates made, [5] ||r|| of the step before the last.
+__global__ void __launch_bounds__(kThreads) k_richardson_init(const double2* __restrict__ b,
+                                                              int nb, double* scal, double tol) {
+  KFBI_PDL_ENTRY();
+  __shared__ double red[32];
+  double s = 0.0;
+  for (int e = threadIdx.x; e < nb; e += kThreads) s += b[e].x * b[e].x + b[e].y * b[e].y;
+  s = block_sum(s, red);
+  if (threadIdx.x == 0) {
+    scal[0] = sqrt(s);
+    scal[1] = 0.0;
+    scal[2] = 0.0;
+    scal[3] = tol;
+    scal[4] = 0.0;
+    scal[5] = 0.0;
+  }
+}
+
+// One step of Eq. 3.21 after the application Ax = A x (Ax null: x = 0):
+// r = b - Ax and its 2-norm, then, in this order,
+//   ||b|| = 0                 -> x = 0, converged;
+//   ||r|| <= tol ||b||        -> converged, x kept;
+//   ||r|| not finite          -> status 2;
+//   maxit updates already made -> status 3, x kept;
+//   otherwise x += gamma r and one more update counted.
+// A step queued behind one that set the status returns at once, so steps
+// may be queued ahead of the host's convergence check.
+__global__ void __launch_bounds__(kThreads) k_richardson_step(const double2* __restrict__ b,
+                                                              const double2* __restrict__ Ax,
+                                                              double2* __restrict__ x, int nb,
+                                                              double gamma, int maxit,
+                                                              double* scal) {
+  KFBI_PDL_ENTRY();
+  KFBI_STOP_RETURN(scal + 2);
+  __shared__ double red[32];
+  // every thread reads the scalars before the block_sum barriers; thread 0
+  // writes them only after
+  const double bn = scal[0], tol = scal[3], made = scal[4], last = scal[1];
+  double s = 0.0;
+  for (int e = threadIdx.x; e < nb; e += kThreads) {
+    double2 r = b[e];
+    if (Ax) {
+      r.x -= Ax[e].x;
+      r.y -= Ax[e].y;
+    }
+    s += r.x * r.x + r.y * r.y;
+  }
+  s = block_sum(s, red);
+  const double rn = sqrt(s);
+  int status = 0;
+  if (bn == 0.0)
+    status = 1;
+  else if (rn <= tol * bn)
+    status = 1;
+  else if (!isfinite(rn))
+    status = 2;
+  else if (made >= (double)maxit)
+    status = 3;
+  if (status == 0 || bn == 0.0) {
+    for (int e = threadIdx.x; e < nb; e += kThreads) {
+      double2 v = make_double2(0.0, 0.0);
+      if (bn != 0.0) {
+        double2 r = b[e];
+        if (Ax) {
+          r.x -= Ax[e].x;
+          r.y -= Ax[e].y;
+        }
+        v = x[e];
+        v.x += gamma * r.x;
+        v.y += gamma * r.y;
+      }
+      x[e] = v;
+    }
+  }
+  if (threadIdx.x == 0) {
+    scal[5] = last;
+    scal[1] = bn == 0.0 ? 0.0 : rn;
+    scal[2] = (double)status;
+    if (status == 0) scal[4] = made + 1.0;
+  }
+}
+}  // namespace gm
+
+// The Richardson iteration of Eq. 3.21, phi <- phi + gamma (b - A phi), with
+// the domain's hot-path operator (apply_internal), relative tolerance tol and
+// at most maxit updates.  Each step is one application and one
+// k_richardson_step; steps are queued in runs whose length the host
+// predicts from the residual reduction it has seen (the residual of a
+// Richardson iteration falls by a nearly constant factor, the spectral
+// radius of I - gamma A), and the host reads the scalars once per run.  Steps
+// queued past convergence do nothing: the step kernel returns at once and,
+// on a mixed domain with irregular nodes, so do the kernels of the
+// application (the sparse route's stop flag).
+static kfbi_status richardson_core(kfbi_domain* D, double kre, double kim, const double* b,
+                                   double* x, bool x_zero, double tol, int maxit,
+                                   kfbi_solve_info* info, cudaStream_t st) {
+  const int nb = D->nb;
+  const double gamma = D->desc.richardson_gamma;
+  const bool cheap_tail = D->tc && D->n_irr > 0;
+  StopScope scope(D, cheap_tail);
+  KFBI_LAUNCH_P(KFBI_PROF_KRYLOV, k_richardson_init, 1, kThreads, 0, st, (const double2*)b, nb,
+                D->d_scal, tol);
+  KFBI_CHECK_LAUNCH();
+  if (info) *info = kfbi_solve_info{0, 0.0, 0, 0};
+  const long long cap = (long long)maxit + 1;  // steps that can still act
+  long long queued = 0;
+  int run = 8;
+  double res_prev = 0.0;
+  long long q_prev = 0;
+  for (;;) {
+    const long long n = std::min<long long>(run, cap - queued);
+    for (long long i = 0; i < n; ++i, ++queued) {
+      const bool skip = queued == 0 && x_zero;
+      if (!skip) apply_internal(D, kre, kim, x, 2, nullptr, D->d_W, 2, false, st);
+      KFBI_LAUNCH_P(KFBI_PROF_KRYLOV, k_richardson_step, 1, kThreads, 0, st, (const double2*)b,
+                    skip ? nullptr : (const double2*)D->d_W, (double2*)x, nb, gamma, maxit,
+                    D->d_scal);
+      KFBI_CHECK_LAUNCH();
+    }
+    read_scalars(D, st);
+    if (D->h_scal[2] != 0.0 || queued >= cap) break;
+    // reduction per step: over the steps since the last read, else over the
+    // last step alone
+    const double res = D->h_scal[1];
+    double rate = 0.0;
+    if (res_prev > 0.0 && queued > q_prev)
+      rate = std::pow(res / res_prev, 1.0 / (double)(queued - q_prev));
+    else if (D->h_scal[5] > 0.0)
+      rate = res / D->h_scal[5];
+    res_prev = res;
+    q_prev = queued;
+    const double target = tol * D->h_scal[0];
+    if (rate > 0.0 && rate < 0.999 && res > target) {
+      // steps until the residual of a step falls below the target: the
+      // last one read is r_(queued-1), the next step computes r_queued
+      const double need = std::ceil(std::log(target / res) / std::log(rate));
+      run = (int)std::min(std::max(need + (cheap_tail ? 1.0 : 0.0), 1.0), 256.0);
+    } else {
+      run = std::min(2 * run, 256);
+    }
+  }
+  const int made = (int)D->h_scal[4];
+  const int status = (int)D->h_scal[2];
+  if (info) {
+    info->iters = made;
+    // applications whose residual the iteration used: every step that did
+    // not return at once, less a first step on x = 0 (steps queued past
+    // the stop are not counted)
+    const int active = made + (status != 0 ? 1 : 0);
+    info->applications = active - (x_zero && active > 0 ? 1 : 0);
+    info->rel_residual = D->h_scal[0] > 0.0 ? D->h_scal[1] / D->h_scal[0] : 0.0;
+    info->converged = status == 1;
+  }
+  if (status == 2) {
+    D->err = "non-finite Richardson residual";
+    return KFBI_ERR_NONFINITE;
+  }
+  if (status != 1) {
+    D->err = "Richardson iteration reached gmres_maxit";
+    return KFBI_ERR_NOT_CONVERGED;
+  }
+  return KFBI_OK;
+}
+
+// Inner solver of the domain (kfbi_solver).
+static kfbi_status inner_solve(kfbi_domain* D, double kre, double kim, const double* b, double* x,
+                               bool x_zero, double tol, int maxit, kfbi_solve_info* info,
+                               cudaStream_t st) {
+  if (D->desc.solver == KFBI_RICHARDSON)
+    return richardson_core(D, kre, kim, b, x, x_zero, tol, maxit, info, st);
+  return gmres_core(D, kre, kim, b, x, x_zero, tol, maxit, info, st);
+}
+
 // Relative tolerance below which the inner solves of the refinement do not
 // go: the TF32x3 operator is accurate to ~2e-6, so tighter inner solves
 // only add iterations.
@@ -1163,7 +1339,7 @@ kfbi_status gmres_solve(kfbi_domain* D, double kre, double kim, const double* b,
   const double tol = D->desc.gmres_tol;
   const int maxit = D->desc.gmres_maxit;
   if (grid_wx) *grid_wx = false;
-  if (!D->tc) return gmres_core(D, kre, kim, b, x, x_zero, tol, maxit, info, st);
+  if (!D->tc) return inner_solve(D, kre, kim, b, x, x_zero, tol, maxit, info, st);
   // Mixed domain: iterative refinement.  The residual of the density,
   // r = b - A phi, uses the accurate operator (apply_accurate, FP64 vector
   // arithmetic); the corrections solve A_mixed d = r with the fast TF32x3
@@ -1212,7 +1388,8 @@ kfbi_status gmres_solve(kfbi_domain* D, double kre, double kim, const double* b,
     const double inner_tol = std::max(0.5 * tol * bnorm / rn, kInnerFloor);
     KFBI_CUDA(cudaMemsetAsync(D->d_Dv, 0, 2 * (size_t)nb * sizeof(double), st));
     kfbi_solve_info in{};
-    kfbi_status s = gmres_core(D, kre, kim, D->d_Rv, D->d_Dv, true, inner_tol, maxit - it, &in, st);
+    kfbi_status s =
+        inner_solve(D, kre, kim, D->d_Rv, D->d_Dv, true, inner_tol, maxit - it, &in, st);
     it += in.iters;
     apps += in.applications;
     if (s == KFBI_ERR_NONFINITE) {

@@ -506,6 +506,8 @@ kfbi_status check_request(const kfbi_server* S, const kfbi_request* r, std::stri
     return why = "the request's gmres_restart must equal the server's", KFBI_ERR_ARG;
   if (r->domain.gmres_maxit < 1 || !(r->domain.gmres_tol > 0.0))
     return why = "GMRES parameters out of range", KFBI_ERR_ARG;
+  if (r->domain.solver != KFBI_GMRES)
+    return why = "served requests are solved by GMRES", KFBI_ERR_ARG;
   if (r->equation < KFBI_HEAT || r->equation > KFBI_SCHRODINGER)
     return why = "unknown equation", KFBI_ERR_ARG;
   if (r->steps < 1 || !(r->dt > 0.0) || !(r->arrival >= 0.0))

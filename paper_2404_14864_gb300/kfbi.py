@@ -21,6 +21,7 @@ STATUS_NAMES = {0: "KFBI_OK", 1: "KFBI_ERR_ARG", 2: "KFBI_ERR_GEOMETRY", 3: "KFB
                 4: "KFBI_ERR_NOT_CONVERGED", 5: "KFBI_ERR_NONFINITE", 6: "KFBI_ERR_TIMEOUT",
                 7: "KFBI_ERR_CUDA", 8: "KFBI_ERR_UNSUPPORTED"}
 KFBI_FP64, KFBI_MIXED_TF32, KFBI_MIXED_FFT32 = 0, 1, 2
+KFBI_GMRES, KFBI_RICHARDSON = 0, 1
 KFBI_CURVE_POLAR, KFBI_CURVE_ELLIPSE = 0, 1
 KFBI_HEAT, KFBI_WAVE, KFBI_SCHRODINGER = 0, 1, 2
 
@@ -47,7 +48,8 @@ class DomainDesc(ctypes.Structure):
                 ("cx", ctypes.c_double), ("cy", ctypes.c_double),
                 ("params", ctypes.c_double * 6), ("precision", ctypes.c_int),
                 ("gmres_restart", ctypes.c_int), ("gmres_tol", ctypes.c_double),
-                ("gmres_maxit", ctypes.c_int)]
+                ("gmres_maxit", ctypes.c_int), ("solver", ctypes.c_int),
+                ("richardson_gamma", ctypes.c_double)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -176,7 +178,7 @@ def exported_symbols():
 # ----------------------------------------------------------------------------
 
 
-def make_desc(d, precision=KFBI_FP64, restart=50, tol=1e-10, maxit=500):
+def make_desc(d, precision=KFBI_FP64, restart=50, tol=1e-10, maxit=500, solver=None, gamma=0.5):
     """kfbi_domain_desc from a workload dict (see ``workloads.domain_desc``)."""
     c = d["curve"]
     p = (ctypes.c_double * 6)()
@@ -192,7 +194,8 @@ def make_desc(d, precision=KFBI_FP64, restart=50, tol=1e-10, maxit=500):
         p[q] = float(v)
     return DomainDesc(int(d["M"]), float(d["lo"]), float(d["hi"]), int(d["nb"]), kind,
                       float(c["cx"]), float(c["cy"]), p, int(precision), int(restart),
-                      float(tol), int(maxit))
+                      float(tol), int(maxit), KFBI_GMRES if solver is None else int(solver),
+                      float(gamma))
 
 
 def _ptr(t):
@@ -303,12 +306,14 @@ class Domain:
     """Owning wrapper of a kfbi_domain."""
 
     def __init__(self, desc_dict, precision=KFBI_FP64, restart=50, tol=1e-10, maxit=500,
-                 stream=None):
+                 stream=None, solver=None, gamma=0.5):
         self.d = dict(desc_dict)
         self.M, self.nb = int(desc_dict["M"]), int(desc_dict["nb"])
         self.n1 = self.M - 1
         self.precision = precision
-        self.h = kfbi_create_domain(make_desc(desc_dict, precision, restart, tol, maxit), stream)
+        self.solver = KFBI_GMRES if solver is None else int(solver)
+        self.h = kfbi_create_domain(make_desc(desc_dict, precision, restart, tol, maxit,
+                                              self.solver, gamma), stream)
 
     def close(self):
         if self.h:

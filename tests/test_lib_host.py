@@ -61,6 +61,13 @@ def test_create_domain_errors_without_touching_the_gpu(built):
     d = kfbi.make_desc(W.domain_desc(64, W.star()))
     d.gmres_restart = 0
     assert built.kfbi_create_domain(ctypes.byref(d), None, ctypes.byref(h)) == 1
+    # solver: unknown kinds and Richardson steps outside (0, 2) are refused
+    # before any device work
+    for solver, gamma in ((2, 0.9), (-1, 0.9), (kfbi.KFBI_RICHARDSON, 0.0),
+                          (kfbi.KFBI_RICHARDSON, 2.0), (kfbi.KFBI_RICHARDSON, float("nan"))):
+        d = kfbi.make_desc(W.domain_desc(64, W.star()), solver=solver, gamma=gamma)
+        assert built.kfbi_create_domain(ctypes.byref(d), None, ctypes.byref(h)) == 1
+        assert not h.value
 
 
 @pytest.mark.parametrize("desc", DOMAINS, ids=lambda d: "%s-%d" % (d["curve"]["kind"], d["M"]))

@@ -80,3 +80,27 @@ def test_richardson_zero_rhs_and_divergence():
     # gamma beyond 2 / lam_max diverges: the iteration stops unconverged
     x, it, rel, ok = oracle.richardson(lambda v: A @ v, np.ones(2), gamma=1.9, tol=1e-10, maxit=200)
     assert not ok and it == 200
+
+
+def test_richardson_stepper_matches_gmres_stepper():
+    # heat steps on a circle: either solver of the density equation gives the
+    # same fields (to the solver tolerance), and the Richardson counts follow
+    # the spectral radius (more iterations for smaller gamma)
+    desc = W.domain_desc(32, W.star(1.0, 0.0, 1), lo=-1.5, hi=1.5)
+    d = oracle.make_domain(desc)
+    ex = W.HeatExact()
+    X, Y = W.grid_xy(desc)
+    zx, zy = W.boundary_xy(desc)
+    out = {}
+    for solver, gamma in (("gmres", 0.0), ("richardson", 0.5), ("richardson", 1.5)):
+        orc = oracle.HeatStepper(d, d.h, 1e-12, solver=solver, gamma=gamma, maxit=5000)
+        orc.init(ex.u(X, Y, 0), ex.lap(X, Y, 0), ex.src(X, Y, 0) + ex.src(X, Y, d.h))
+        for k in range(3):
+            t1 = (k + 1) * d.h
+            U = orc.step(ex.u(zx, zy, t1), ex.src(X, Y, t1) + ex.src(X, Y, t1 + d.h))
+        out[(solver, gamma)] = (U, orc.iters)
+    m = d.interior_inside()
+    Ug = out[("gmres", 0.0)][0]
+    for key in (("richardson", 0.5), ("richardson", 1.5)):
+        assert np.abs(out[key][0] - Ug)[m].max() <= 1e-9 * np.abs(Ug[m]).max()
+    assert all(a > b for a, b in zip(out[("richardson", 0.5)][1], out[("richardson", 1.5)][1]))
