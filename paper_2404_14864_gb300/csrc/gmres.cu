@@ -1261,8 +1261,17 @@ static kfbi_status richardson_core(kfbi_domain* D, double kre, double kim, const
   if (info) *info = kfbi_solve_info{0, 0.0, 0, 0};
   const long long cap = (long long)maxit + 1;  // steps that can still act
   long long queued = 0;
-  int run = 8;
-  double res_prev = 0.0;
+  // first run: on x = 0 (r_0 = b) with the rate of an earlier solve at the
+  // same kappa, the steps until rate^k <= tol plus the step that sees it;
+  // otherwise a short run to measure the rate on
+  int run = cheap_tail ? 8 : 2;
+  const bool known = D->rich_rate > 0.0 && D->rich_rate < 0.999 && D->rich_kre == kre &&
+                     D->rich_kim == kim;
+  if (x_zero && known) {
+    const double k = std::ceil(std::log(tol) / std::log(D->rich_rate));
+    run = (int)std::min(std::max(k + 1.0 + (cheap_tail ? 1.0 : 0.0), 1.0), 256.0);
+  }
+  double res_prev = 0.0, rate = 0.0;
   long long q_prev = 0;
   for (;;) {
     const long long n = std::min<long long>(run, cap - queued);
@@ -1279,7 +1288,7 @@ static kfbi_status richardson_core(kfbi_domain* D, double kre, double kim, const
     // reduction per step: over the steps since the last read, else over the
     // last step alone
     const double res = D->h_scal[1];
-    double rate = 0.0;
+    rate = 0.0;
     if (res_prev > 0.0 && queued > q_prev)
       rate = std::pow(res / res_prev, 1.0 / (double)(queued - q_prev));
     else if (D->h_scal[5] > 0.0)
@@ -1298,6 +1307,13 @@ static kfbi_status richardson_core(kfbi_domain* D, double kre, double kim, const
   }
   const int made = (int)D->h_scal[4];
   const int status = (int)D->h_scal[2];
+  if (status == 1 && x_zero && made >= 2 && D->h_scal[0] > 0.0 && D->h_scal[1] > 0.0)
+    rate = std::pow(D->h_scal[1] / D->h_scal[0], 1.0 / made);  // r_0 = b
+  if (status == 1 && rate > 0.0 && rate < 0.999) {
+    D->rich_rate = rate;
+    D->rich_kre = kre;
+    D->rich_kim = kim;
+  }
   if (info) {
     info->iters = made;
     // applications whose residual the iteration used: every step that did

@@ -237,6 +237,9 @@ struct kfbi_domain {
   // order) and the events that mark them
   double* h_ring = nullptr;
   cudaEvent_t ev_ring[2] = {nullptr, nullptr};
+  // residual reduction per Richardson step seen at kappa = (rich_kre,
+  // rich_kim) in the last solve (0: none yet); sizes the first run of steps
+  double rich_rate = 0.0, rich_kre = 0.0, rich_kim = 0.0;
   cudaEvent_t ev_scal = nullptr;
 
   kfbi::TcDst* tc = nullptr;  // mixed-precision engine (KFBI_MIXED_TF32 or KFBI_MIXED_FFT32)
