@@ -70,7 +70,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--cpu-steps", type=int, default=2)
-    ap.add_argument("--workload", default="wave1024", choices=["wave1024", "batched", "served"])
+    ap.add_argument("--workload", default="wave1024",
+                    choices=["wave1024", "nls1024", "batched", "served"],
+                    help="wave1024: theta = 1/4 wave (headline); nls1024: the paper's nonlinear "
+                         "Schroedinger example (w = 1) at --M; batched, served: configs 4, 5")
     ap.add_argument("--batch", type=int, default=256)
     ap.add_argument("--requests", type=int, default=200)
     ap.add_argument("--max-resident", type=int, default=64)
@@ -84,6 +87,113 @@ def workload(M):
     desc = W.domain_desc(M, W.ellipse(0.7, 0.4, 30.0))
     h = (desc["hi"] - desc["lo"]) / M
     return desc, 4.0 * h, 0.25
+
+
+class WaveProblem:
+    """The headline workload: theta = 1/4 wave on the rotated ellipse,
+    u = cos(sqrt2 pi t) sin(pi x) sin(pi y), dt = 4h."""
+
+    kind = "wave"
+
+    def __init__(self, M):
+        from paper_2404_14864_gb300 import workloads as W
+        self.M = M
+        self.desc, self.dt, self.theta = workload(M)
+        self.ex = W.WaveExact()
+        self.X, self.Y = W.grid_xy(self.desc)
+        self.zx, self.zy = W.boundary_xy(self.desc)
+        self.cplx = False
+
+    def equation(self, kfbi):
+        return kfbi.KFBI_WAVE
+
+    def g(self, k):
+        """Dirichlet data of step k (0-based): u at (k + 2) dt."""
+        return self.ex.u(self.zx, self.zy, (k + 2) * self.dt)
+
+    def exact(self, n):
+        """u after n steps."""
+        return self.ex.u(self.X, self.Y, (n + 1) * self.dt)
+
+    def init(self, st, cu):
+        ex, X, Y, dt = self.ex, self.X, self.Y, self.dt
+        st.init_wave(dt, self.theta, cu(ex.u(X, Y, 0.0)), cu(ex.lap(X, Y, 0.0)),
+                     cu(ex.u(X, Y, dt)), cu(ex.lap(X, Y, dt)))
+
+    def step(self, st, g_dev):
+        return st.step_wave(g_dev)
+
+    def oracle_stepper(self, oracle, d):
+        ex, X, Y, dt = self.ex, self.X, self.Y, self.dt
+        st = oracle.WaveStepper(d, dt, 1e-10)
+        st.init(ex.u(X, Y, 0.0), ex.lap(X, Y, 0.0), ex.u(X, Y, dt), ex.lap(X, Y, dt))
+        return st
+
+    def oracle_step(self, st, k):
+        st.step(self.g(k))
+
+    def config(self, precision, solver="gmres", gamma=0.5):
+        return config(self.M, self.desc, self.dt, precision, solver, gamma)
+
+
+class NlsProblem:
+    """The paper's nonlinear Schroedinger example (Sec. 4, Ex. 5) at grid M:
+    w = 1, v = 1 - cos^2 x cos^2 y, u = exp(i t) cos x cos y, star
+    r = 1.5 (0.8 + 0.2 cos 3 theta), box [-pi, pi]^2, N_b = M, dt = 8 / M
+    (the time steps of its Table 4)."""
+
+    kind = "nls"
+
+    def __init__(self, M):
+        from paper_2404_14864_gb300 import workloads as W
+        self.M = M
+        self.desc = W.domain_desc(M, W.ex5_star(0.2), lo=-math.pi, hi=math.pi)
+        self.dt = 8.0 / M
+        self.ex = W.NonlinearSchrodingerExact()
+        self.X, self.Y = W.grid_xy(self.desc)
+        self.zx, self.zy = W.boundary_xy(self.desc)
+        self.V = self.ex.v(self.X, self.Y)
+        self.cplx = True
+        self.Vd = None
+
+    def equation(self, kfbi):
+        return kfbi.KFBI_SCHRODINGER
+
+    def g(self, k):
+        return self.ex.u(self.zx, self.zy, (k + 1) * self.dt)
+
+    def exact(self, n):
+        return self.ex.u(self.X, self.Y, n * self.dt)
+
+    def init(self, st, cu):
+        if self.Vd is None:
+            self.Vd = cu(self.V)
+        st.init_schrodinger(self.dt, cu(self.ex.u(self.X, self.Y, 0.0)),
+                            cu(self.ex.lap(self.X, self.Y, 0.0)))
+
+    def step(self, st, g_dev):
+        return st.step_schrodinger(self.Vd, g_dev, w=self.ex.w)
+
+    def oracle_stepper(self, oracle, d):
+        st = oracle.SchrodingerStepper(d, self.dt, 1e-10)
+        st.init(self.ex.u(self.X, self.Y, 0.0), self.ex.lap(self.X, self.Y, 0.0))
+        return st
+
+    def oracle_step(self, st, k):
+        st.step(self.g(k), self.V, self.ex.w)
+
+    def config(self, precision, solver="gmres", gamma=0.5):
+        sv = ("gmres restart 50, tol 1e-10" if solver == "gmres"
+              else "richardson gamma %g, tol 1e-10" % gamma)
+        return {"workload": "nonlinear-schrodinger-w1-star-%d" % self.M, "M": self.M,
+                "unknowns": (self.M - 1) ** 2, "n_boundary": self.desc["nb"], "dt": "8/M",
+                "w": 1.0, "solver": sv, "precision": precision,
+                "l2": "flushed between timed steps (256 MiB write)",
+                "box": [self.desc["lo"], self.desc["hi"]]}
+
+
+def make_problem(args):
+    return NlsProblem(args.M) if args.workload == "nls1024" else WaveProblem(args.M)
 
 
 def config(M, desc, dt, precision, solver="gmres", gamma=0.5):
@@ -169,10 +279,8 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     M = args.M
-    desc, dt, theta = workload(M)
-    ex = W.WaveExact()
-    X, Y = W.grid_xy(desc)
-    zx, zy = W.boundary_xy(desc)
+    P = make_problem(args)
+    desc, dt = P.desc, P.dt
     n1 = M - 1
     stream = torch.cuda.current_stream()
 
@@ -195,12 +303,11 @@ def run_ours(args, rank, world, local_rank):
     K, Wm = args.steps, args.warmup
     n_total = Wm + K
     # boundary data for every step, resident on the device before timing
-    g_all = [cu(ex.u(zx, zy, (k + 2) * dt)) for k in range(n_total)]
+    g_all = [cu(P.g(k)) for k in range(n_total)]
 
     def new_state(domain):
-        st = kfbi.State(domain, kfbi.KFBI_WAVE)
-        st.init_wave(dt, theta, cu(ex.u(X, Y, 0.0)), cu(ex.lap(X, Y, 0.0)), cu(ex.u(X, Y, dt)),
-                     cu(ex.lap(X, Y, dt)))
+        st = kfbi.State(domain, P.equation(kfbi))
+        P.init(st, cu)
         return st
 
     # inside mask for the error norm, from the library's host-side plan
@@ -217,7 +324,7 @@ def run_ours(args, rank, world, local_rank):
                 e0 = torch.cuda.Event(enable_timing=True)
                 e1 = torch.cuda.Event(enable_timing=True)
                 e0.record(stream)
-            info = st.step_wave(g_all[k])
+            info = P.step(st, g_all[k])
             iters.append(info["iters"])
             if timed:
                 e1.record(stream)
@@ -265,14 +372,14 @@ def run_ours(args, rank, world, local_rank):
             "ms_per_step_instrumented": sum(lat_r) / K}
     st_r.close()
     t_dev = sum(lat) / 1e3
-    t_final = (Wm + K + 1) * dt
+    exact = torch.from_numpy(P.exact(Wm + K)).to(dev)
     u = st.get_u()
-    err = float((u - torch.from_numpy(ex.u(X, Y, t_final)).to(dev)).abs()[inside].max())
+    err = float((u - exact).abs()[inside].max())
     # per-class breakdown: one extra (untimed) step with every class timed
     st_b = new_state(dom)
     kfbi.kfbi_profile_reset()
     kfbi.kfbi_profile_enable(True)
-    st_b.step_wave(g_all[0])
+    P.step(st_b, g_all[0])
     kfbi.kfbi_profile_enable(False)
     breakdown = {kfbi.PROF_NAMES[c]: kfbi.kfbi_profile_read(c) for c in kfbi.PROF_NAMES}
     st_b.close()
@@ -280,15 +387,16 @@ def run_ours(args, rank, world, local_rank):
     # end to end through the public API with host buffers: H2D of the step's
     # boundary data, the step, D2H of the solution grid
     st2 = new_state(dom)
-    g_host = [torch.from_numpy(ex.u(zx, zy, (k + 2) * dt)).pin_memory() for k in range(K)]
-    u_host = torch.empty(n1 * n1, dtype=torch.float64).pin_memory()
-    g_dev = torch.empty(desc["nb"], dtype=torch.float64, device=dev)
-    u_dev = torch.empty(n1 * n1, dtype=torch.float64, device=dev)
+    cdt = torch.complex128 if P.cplx else torch.float64
+    g_host = [torch.from_numpy(P.g(k)).pin_memory() for k in range(K)]
+    u_host = torch.empty(n1 * n1, dtype=cdt).pin_memory()
+    g_dev = torch.empty(desc["nb"], dtype=cdt, device=dev)
+    u_dev = torch.empty(n1 * n1, dtype=cdt, device=dev)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for k in range(K):
         g_dev.copy_(g_host[k], non_blocking=True)
-        st2.step_wave(g_dev)
+        P.step(st2, g_dev)
         st2.get_u(u_dev)
         u_host.copy_(u_dev, non_blocking=True)
         torch.cuda.synchronize()
@@ -304,7 +412,7 @@ def run_ours(args, rank, world, local_rank):
         lat64 = []
         run_steps(st64, Wm, K, True, lat64)
         u64 = st64.get_u()
-        err64 = float((u64 - torch.from_numpy(ex.u(X, Y, t_final)).to(dev)).abs()[inside].max())
+        err64 = float((u64 - exact).abs()[inside].max())
         diff = float((u64 - u).abs()[inside].max())
         fp64 = {"value": M * M * K / (sum(lat64) / 1e3), "unit": UNIT,
                 "ms_per_step": sum(lat64) / K, "linf_vs_exact": err64,
@@ -316,7 +424,8 @@ def run_ours(args, rank, world, local_rank):
            "launches": n_launch, "prof": prof, "breakdown": breakdown, "clocks": clocks,
            "prec": prec, "note": note,
            "wall": wall, "fp64": fp64, "desc": desc, "dt": dt,
-           "h2d": desc["nb"] * 8, "d2h": n1 * n1 * 8}
+           "h2d": desc["nb"] * (16 if P.cplx else 8), "d2h": n1 * n1 * (16 if P.cplx else 8),
+           "problem": P}
     st.close()
     dom.close()
     return out
@@ -356,9 +465,12 @@ def roofline(res, M):
                 "avg_launch_us": avg_s * 1e6, "launches": n, "flops_per_launch": flops / n,
                 "timing": how}
     if res["prec"] == kfbi.KFBI_MIXED_FFT32:
-        # one pass reads every row of an FP32 plane and writes it transposed
-        # (the wave workload is real: one plane)
-        nbytes = 2.0 * M * M * 4
+        # one pass reads every row of an FP32 plane and writes it transposed;
+        # planes per launch (1 real, 2 complex) from the library's flop
+        # count, Mp rows of 5 M log2 M + 10 M flops per plane
+        lg = int(round(math.log2(M)))
+        planes = max(1, int(round(flops / n / (M * (5.0 * M * lg + 10.0 * M)))))
+        nbytes = planes * 2.0 * M * M * 4
         gbs = nbytes / avg_s / 1e9
         peak = peaks.get("hbm_gbs", 6800.0)
         return {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
@@ -537,22 +649,16 @@ def run_served(args):
 # ----------------------------------------------------------------------------
 
 
-def run_oracle(M, steps, budget_s=150.0):
-    import numpy as np
-
+def run_oracle(P, steps, budget_s=150.0):
+    """The oracle stepping the problem's first `steps` time steps (stops
+    after the step that crosses budget_s); returns (steps done, seconds)."""
     import oracle
-    from paper_2404_14864_gb300 import workloads as W
-    desc, dt, theta = workload(M)
-    d = oracle.make_domain(desc)
-    ex = W.WaveExact()
-    X, Y = W.grid_xy(desc)
-    zx, zy = W.boundary_xy(desc)
-    st = oracle.WaveStepper(d, dt, 1e-10)
-    st.init(ex.u(X, Y, 0.0), ex.lap(X, Y, 0.0), ex.u(X, Y, dt), ex.lap(X, Y, dt))
+    d = oracle.make_domain(P.desc)
+    st = P.oracle_stepper(oracle, d)
     done = 0
     t0 = time.perf_counter()
     for k in range(steps):
-        st.step(ex.u(zx, zy, (k + 2) * dt))
+        P.oracle_step(st, k)
         done += 1
         if time.perf_counter() - t0 > budget_s:
             break
@@ -566,24 +672,25 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     M = args.M
-    desc, dt, theta = workload(M)
+    P = make_problem(args)
 
     if args.impl == "reference":
         if rank != 0:
             return 0
         k = max(1, min(args.steps, 50))
-        run_oracle(M, 1, 1e9)  # one untimed warm-up step
-        done, t = run_oracle(M, k)
+        run_oracle(P, 1, 1e9)  # one untimed warm-up step
+        done, t = run_oracle(P, k)
         v = M * M * done / t
         cores = os.cpu_count()
         line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT,
                 "n_gpus": args.gpus, "steps": done, "warmup": 1, "ms_per_step": 1e3 * t / done,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
                 "data": "synthetic (manufactured solution)",
-                "config": config(M, desc, dt, "fp64 CPU oracle"),
+                "config": P.config("fp64 CPU oracle", args.solver, args.gamma),
                 "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-                                 "sample": "%d time steps of the %d^2 wave workload after one "
-                                           "untimed step (numpy float64 oracle)" % (done, M)},
+                                 "sample": "%d time steps of the %d^2 %s workload after one "
+                                           "untimed step (numpy float64 oracle)"
+                                           % (done, M, P.kind)},
                 "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}}
         print(json.dumps(line))
@@ -617,10 +724,10 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        done, t = run_oracle(M, args.cpu_steps)
+        done, t = run_oracle(res["problem"], args.cpu_steps)
         cpu = {"value": M * M * done / t, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-               "sample": "%d time steps of the %d^2 wave workload (numpy float64 oracle, "
-                         "BLAS threads = host cores)" % (done, M)}
+               "sample": "%d time steps of the %d^2 %s workload (numpy float64 oracle, "
+                         "BLAS threads = host cores)" % (done, M, res["problem"].kind)}
 
     if rank == 0:
         from paper_2404_14864_gb300 import kfbi
@@ -634,10 +741,10 @@ def main():
             "dtype": {kfbi.KFBI_FP64: "f64", kfbi.KFBI_MIXED_TF32: "tf32x3-f32acc+f64",
                       kfbi.KFBI_MIXED_FFT32: "fp32-fft+f64"}[res["prec"]],
             "data": "synthetic (manufactured solution)",
-            "config": config(M, desc, dt, {kfbi.KFBI_FP64: "fp64",
-                                           kfbi.KFBI_MIXED_TF32: "mixed-tf32x3",
-                                           kfbi.KFBI_MIXED_FFT32: "mixed-fp32-fft"}[res["prec"]],
-                             args.solver, args.gamma),
+            "config": res["problem"].config({kfbi.KFBI_FP64: "fp64",
+                                             kfbi.KFBI_MIXED_TF32: "mixed-tf32x3",
+                                             kfbi.KFBI_MIXED_FFT32: "mixed-fp32-fft"}[res["prec"]],
+                                            args.solver, args.gamma),
             "latency_ms": {"p50": p(0.5), "p99": p(0.99), "max": lat[-1]},
             "linf_vs_exact": res["err"],
             "%s_iters_per_step" % args.solver: res["iters"],

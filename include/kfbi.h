@@ -210,10 +210,15 @@ kfbi_status kfbi_step_heat(kfbi_domain* dom, kfbi_state* st, const double* g_nex
  * F^{n+2} = (kappa/theta) u^{n+1} - ((1-2theta)/theta) F^{n+1} - F^n. */
 kfbi_status kfbi_step_wave(kfbi_domain* dom, kfbi_state* st, const double* g_next_dev,
                            kfbi_solve_info* info, void* stream);
-/* One Strang step: u** = ((1 - i dt v/2)/(1 + i dt v/2)) u* (Eq. 3.10 with
- * w = 0; w != 0 returns KFBI_ERR_UNSUPPORTED), solve Eq. 3.12 for u^{n+1}
- * with data g_next_dev (complex128), then u* = 2 u^{n+1} - u**.
- * v_dev: (M-1)^2 doubles (the potential v). */
+/* One Strang step of -i u_t + Delta u + v u + w |u|^2 u = 0 (Eq. 2.2):
+ * the pointwise Crank-Nicolson step of Eq. 3.10,
+ * u** = ((1 - i a)/(1 + i a)) u* with a = (dt/2)(v + w |u*|^2) (the
+ * modulus-preserving root of Eq. 3.10, which the paper's Newton iteration
+ * reaches from u*; unique while dt |w| |u|^2 / 2 < 1), then Eq. 3.12 for
+ * u^{n+1} with data g_next_dev (complex128), then u* = 2 u^{n+1} - u**.
+ * v_dev: (M-1)^2 doubles (the potential v); w: real, finite (else
+ * KFBI_ERR_ARG).  Batches and the server step Schroedinger requests with
+ * w = 0. */
 kfbi_status kfbi_step_schrodinger(kfbi_domain* dom, kfbi_state* st, const double* v_dev,
                                   double w, const void* g_next_dev, kfbi_solve_info* info,
                                   void* stream);

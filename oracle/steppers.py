@@ -119,12 +119,38 @@ class SchrodingerStepper(_Base):
         self.ustar = u0 - 0.5j * self.tau * np.asarray(lap_u0, dtype=np.complex128)
         self.u = u0.copy()
 
-    def b_step(self, ustar, v, w=0.0):
-        """Pointwise Crank-Nicolson step of Eq. 3.10 for iu_t = (v + w|u|^2) u."""
-        if w != 0.0:
-            raise NotImplementedError("w != 0 needs the pointwise Newton solve")
-        a = 0.5j * self.tau * np.asarray(v)
-        return (1.0 - a) / (1.0 + a) * ustar
+    def b_step(self, ustar, v, w=0.0, tol=1e-15, maxit=50):
+        """Pointwise Crank-Nicolson step of Eq. 3.10 for iu_t = (v + w|u|^2) u.
+
+        With c = tau/2 the step is u + i c (v + w|u|^2) u = R,
+        R = u* - i c (v + w|u*|^2) u*.  For w = 0 it is linear:
+        u = (1 - i c v)/(1 + i c v) u*.  For w != 0 it is solved, as the
+        paper says, by Newton's method, here on the real 2x2 system in
+        (Re u, Im u) at every node, from u = u* until the update is below
+        tol |u| (quadratic convergence; maxit bounds it)."""
+        ustar = np.asarray(ustar, dtype=np.complex128)
+        v = np.asarray(v, dtype=np.float64)
+        c = 0.5 * self.tau
+        if w == 0.0:
+            a = 1j * c * v
+            return (1.0 - a) / (1.0 + a) * ustar
+        R = ustar - 1j * c * (v + w * np.abs(ustar) ** 2) * ustar
+        x, y = ustar.real.copy(), ustar.imag.copy()
+        for _ in range(maxit):
+            al = c * (v + w * (x * x + y * y))
+            # F(x, y) = (x - al y - Re R, y + al x - Im R), al = c (v + w (x^2 + y^2))
+            f1 = x - al * y - R.real
+            f2 = y + al * x - R.imag
+            dx_al, dy_al = 2.0 * c * w * x, 2.0 * c * w * y
+            j11, j12 = 1.0 - y * dx_al, -al - y * dy_al
+            j21, j22 = al + x * dx_al, 1.0 + x * dy_al
+            det = j11 * j22 - j12 * j21
+            d1 = (j22 * f1 - j12 * f2) / det
+            d2 = (j11 * f2 - j21 * f1) / det
+            x, y = x - d1, y - d2
+            if np.max(np.hypot(d1, d2) / np.maximum(np.hypot(x, y), 1e-300)) <= tol:
+                break
+        return x + 1j * y
 
     def step(self, g_next, v, w=0.0):
         uss = self.b_step(self.ustar, v, w)

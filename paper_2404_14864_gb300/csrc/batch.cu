@@ -50,6 +50,7 @@ struct GInst {
   const int* node_fidx;
   const double* node_fcoef;
   const double* lam64;
+  const float* lam32;
   // FP32 tables of the mixed path
   const float* alpha32;
   const float* beta32;
@@ -232,26 +233,27 @@ __global__ void gk_split64(const GInst* gi) {
   }
 }
 
+// Complex eigenvalue division on the TF32 pairs, in FP32 (k_eig_cplx32's
+// arithmetic): a pair holds 22 significant bits, which FP32 keeps.
 __global__ void gk_eig_cplx(const GInst* gi) {
   KFBI_PDL_ENTRY();
   const GInst& I = gi[blockIdx.y];
   ACTIVE_OR_RETURN(I);
   if (!I.C) return;
   const size_t plane = (size_t)I.Mp * I.Mp;
+  const float kre = (float)I.kre, kim = (float)I.kim, scale = (float)I.scale;
   INST_PLANE_LOOP(I) {
     const int a = (int)(idx / I.Mp), bcol = (int)(idx % I.Mp);
     if (a >= I.n1 || bcol >= I.n1) continue;
-    const double x = (double)I.T2h[idx] + (double)I.T2l[idx];
-    const double y = (double)I.T2h[plane + idx] + (double)I.T2l[plane + idx];
-    const double dr = I.lam64[a] + I.lam64[bcol] - I.kre;
-    const double den = I.scale / (dr * dr + I.kim * I.kim);
-    const double zr = (x * dr - y * I.kim) * den, zi = (x * I.kim + y * dr) * den;
-    float h = tf32r((float)zr);
+    float zr, zi;
+    eig_div_cplx32(I.T2h[idx] + I.T2l[idx], I.T2h[plane + idx] + I.T2l[plane + idx],
+                   (I.lam32[a] - kre) + I.lam32[bcol], kim, scale, zr, zi);
+    float h = tf32r(zr);
     I.T2h[idx] = h;
-    I.T2l[idx] = tf32r((float)(zr - (double)h));
-    h = tf32r((float)zi);
+    I.T2l[idx] = tf32r(zr - h);
+    h = tf32r(zi);
     I.T2h[plane + idx] = h;
-    I.T2l[plane + idx] = tf32r((float)(zi - (double)h));
+    I.T2l[plane + idx] = tf32r(zi - h);
   }
 }
 
@@ -1335,7 +1337,7 @@ void fill_instances(kfbi_batch* B, kfbi_state* const* states, const void* const*
     I.alpha = D->d_arm_alpha; I.beta = D->d_arm_beta; I.arm_fidx = D->d_arm_fidx;
     I.arm_fcoef = D->d_arm_fcoef; I.node_gidx = D->d_node_gidx; I.node_w = D->d_node_w;
     I.node_a = D->d_node_a; I.node_b = D->d_node_b; I.node_fidx = D->d_node_fidx;
-    I.node_fcoef = D->d_node_fcoef; I.lam64 = D->d_lam;
+    I.node_fcoef = D->d_node_fcoef; I.lam64 = D->d_lam; I.lam32 = T->lam;
     I.alpha32 = D->d_arm_alpha32; I.beta32 = D->d_arm_beta32; I.arm_fcoef32 = D->d_arm_fcoef32;
     I.node_w32 = D->d_node_w32; I.node_a32 = D->d_node_a32; I.node_b32 = D->d_node_b32;
     I.S32 = T->S32; I.row_start = T->row_start; I.node_col = T->node_col;

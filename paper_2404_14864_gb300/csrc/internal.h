@@ -151,6 +151,17 @@ __host__ __device__ inline float tf32_round(float x) {
 #endif
 }
 
+#ifdef __CUDACC__
+// Complex eigenvalue division of a box solve in FP32:
+// (x + i y) scale / (d - i kim) = (x + i y)(d + i kim) scale / (d^2 + kim^2).
+__device__ __forceinline__ void eig_div_cplx32(float x, float y, float d, float kim, float scale,
+                                               float& zr, float& zi) {
+  const float sc = __fdividef(scale, fmaf(d, d, kim * kim));
+  zr = (x * d - y * kim) * sc;
+  zi = (x * kim + y * d) * sc;
+}
+#endif
+
 struct TcDst;  // tensor-core DST engine (tc_dst.cu)
 
 // DST-I tables shared by every domain on the same grid (M, h), tables.cu:

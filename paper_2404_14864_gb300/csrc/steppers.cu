@@ -85,21 +85,27 @@ __global__ void k_make_ft(double* ft, const double* F, const uint8_t* mask, int 
   GRID_LOOP(Mp) { ft[idx] = mask[idx] ? -F[idx] : 0.0; }
 }
 
-// Pointwise Crank-Nicolson step of Eq. 3.10 with w = 0:
-// u** = (1 - i a)/(1 + i a) u*, a = dt v / 2; and f-tilde = -kappa u** on
-// Omega with kappa = i kim (Eq. 3.12: Delta u - kappa u = -kappa u**).
+// Pointwise Crank-Nicolson step of Eq. 3.10,
+// u + i (dt/2)(v + w|u|^2) u = u* - i (dt/2)(v + w|u*|^2) u*.  Its root keeps
+// the modulus (with |u| = |u*| both sides carry the same real factor
+// a = (dt/2)(v + w|u*|^2), and |1 + i a| = |1 - i a|), so the root the
+// paper's Newton iteration converges to from u* is
+// u** = (1 - i a)/(1 + i a) u*, in closed form; for w = 0 it is the linear
+// Cayley factor.  Then f-tilde = -kappa u** on Omega with kappa = i kim
+// (Eq. 3.12: Delta u - kappa u = -kappa u**).
 __global__ void k_schr_bstep(double* uss, double* ft, const double* ustar, const double* v,
-                             const uint8_t* mask, int n1, int Mp, double half_dt, double kim) {
+                             const uint8_t* mask, int n1, int Mp, double half_dt, double w,
+                             double kim) {
   KFBI_PDL_ENTRY();
   const size_t plane = (size_t)Mp * Mp;
   GRID_LOOP(Mp) {
     const int r = (int)(idx / Mp), c = (int)(idx % Mp);
     double xr = 0, xi = 0;
     if (r < n1 && c < n1) {
-      const double a = half_dt * v[(size_t)r * n1 + c];
+      const double sr = ustar[idx], si = ustar[plane + idx];
+      const double a = half_dt * (v[(size_t)r * n1 + c] + w * (sr * sr + si * si));
       const double den = 1.0 / (1.0 + a * a);
       const double pr = (1.0 - a * a) * den, pi = -2.0 * a * den;
-      const double sr = ustar[idx], si = ustar[plane + idx];
       xr = pr * sr - pi * si;
       xi = pr * si + pi * sr;
     }
@@ -424,15 +430,15 @@ kfbi_status kfbi_step_schrodinger(kfbi_domain* dom, kfbi_state* S, const double*
     if (dom) dom->err = "step needs the state's domain, v, g_next and an initialised state";
     return KFBI_ERR_ARG;
   }
-  if (w != 0.0) {
-    dom->err = "the nonlinear Strang B step (w != 0) is not built";
-    return KFBI_ERR_UNSUPPORTED;
+  if (!std::isfinite(w)) {
+    dom->err = "w must be finite";
+    return KFBI_ERR_ARG;
   }
   return guarded(dom, [&]() -> kfbi_status {
     cudaStream_t st = (cudaStream_t)stream;
     const size_t plane = (size_t)dom->Mp * dom->Mp;
     KFBI_LAUNCH_P(KFBI_PROF_GRID, k_schr_bstep, grid_for(plane, 256), 256, 0, st, S->d_aux, S->d_ft, S->d_F, v,
-                dom->d_mask, dom->n1, dom->Mp, 0.5 * S->dt, S->kim);
+                dom->d_mask, dom->n1, dom->Mp, 0.5 * S->dt, w, S->kim);
     KFBI_CHECK_LAUNCH();
     kfbi_status s = solve_step(dom, S, (const double*)g_next, true, info, st);
     if (s != KFBI_OK) return s;

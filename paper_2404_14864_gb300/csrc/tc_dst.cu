@@ -935,32 +935,62 @@ __global__ void __launch_bounds__(32 * GE_WARPS)
     out[(size_t)k * os + 1] = 0.0;
 }
 
-// Complex eigenvalue division on TF32 pairs (two planes), in FP64.
-__global__ void k_eig_split_cplx(float* __restrict__ hi, float* __restrict__ lo, size_t plane,
-                                 int Mp, int n1, const double* __restrict__ lam, double kre,
-                                 double kim, double scale, const double* stop) {
+// Complex eigenvalue division on FP32 planes: z *= scale / (lam[a] + lam[b] -
+// kappa) with kappa = kre + i kim, i.e. (x + i y)(d + i kim) scale /
+// (d^2 + kim^2), d = lam[a] + lam[b] - kre, in FP32.  FFT route (lo null):
+// z in hi, the arithmetic of the passes around it.  Tensor route: z = hi + lo
+// (a TF32 pair holds 22 significant bits, which FP32 keeps), the quotient is
+// split into a TF32 pair again; FP32 rounding (a few 2^-24) stays below the
+// pair's resolution.  One block per row a, float4 columns; padded rows and
+// columns are left as they are.
+__global__ void __launch_bounds__(256) k_eig_cplx32(float* __restrict__ hi, float* __restrict__ lo,
+                                                    size_t plane, int Mp, int n1,
+                                                    const float* __restrict__ lam, float kre,
+                                                    float kim, float scale, const double* stop) {
   KFBI_PDL_ENTRY();
   KFBI_STOP_RETURN(stop);
-  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < plane;
-       idx += (size_t)gridDim.x * blockDim.x) {
-    const int a = (int)(idx / Mp), b = (int)(idx % Mp);
-    if (a >= n1 || b >= n1) continue;
-    const double x = (double)hi[idx] + (lo ? (double)lo[idx] : 0.0);
-    const double y = (double)hi[plane + idx] + (lo ? (double)lo[plane + idx] : 0.0);
-    const double dr = lam[a] + lam[b] - kre;
-    const double den = scale / (dr * dr + kim * kim);
-    const double zr = (x * dr - y * kim) * den, zi = (x * kim + y * dr) * den;
-    if (!lo) {  // single FP32 planes (FFT passes)
-      hi[idx] = (float)zr;
-      hi[plane + idx] = (float)zi;
-      continue;
+  for (int a = blockIdx.x; a < n1; a += gridDim.x) {
+    const float la = lam[a] - kre;
+    const size_t row = (size_t)a * Mp;
+    float4* hr = reinterpret_cast<float4*>(hi + row);
+    float4* hq = reinterpret_cast<float4*>(hi + plane + row);
+    float4* lr = lo ? reinterpret_cast<float4*>(lo + row) : nullptr;
+    float4* lq = lo ? reinterpret_cast<float4*>(lo + plane + row) : nullptr;
+    for (int q = threadIdx.x; 4 * q < n1; q += blockDim.x) {
+      const float4 lb = *reinterpret_cast<const float4*>(lam + 4 * q);
+      float4 x = hr[q], y = hq[q];
+      float4 xl = make_float4(0.f, 0.f, 0.f, 0.f), yl = xl;
+      if (lo) {
+        xl = lr[q];
+        yl = lq[q];
+      }
+      float* xs = reinterpret_cast<float*>(&x);
+      float* ys = reinterpret_cast<float*>(&y);
+      float* xls = reinterpret_cast<float*>(&xl);
+      float* yls = reinterpret_cast<float*>(&yl);
+      const float* ls = reinterpret_cast<const float*>(&lb);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        if (4 * q + j >= n1) continue;
+        float zr, zi;
+        eig_div_cplx32(xs[j] + xls[j], ys[j] + yls[j], la + ls[j], kim, scale, zr, zi);
+        if (lo) {
+          xs[j] = tf32_round(zr);
+          xls[j] = tf32_round(zr - xs[j]);
+          ys[j] = tf32_round(zi);
+          yls[j] = tf32_round(zi - ys[j]);
+        } else {
+          xs[j] = zr;
+          ys[j] = zi;
+        }
+      }
+      hr[q] = x;
+      hq[q] = y;
+      if (lo) {
+        lr[q] = xl;
+        lq[q] = yl;
+      }
     }
-    float h = tf32_round((float)zr);
-    hi[idx] = h;
-    lo[idx] = tf32_round((float)(zr - (double)h));
-    h = tf32_round((float)zi);
-    hi[plane + idx] = h;
-    lo[plane + idx] = tf32_round((float)(zi - (double)h));
   }
 }
 
@@ -1366,9 +1396,8 @@ static void tc_box_solve(kfbi_domain* D, double kre, double kim, int P, cudaStre
     fft_pass(T, T->Rh, T->T1h, 0, 0.f, 0.f, P, nullptr, st);
     fft_pass(T, T->T1h, T->T2h, C ? 0 : 1, (float)kre, scale, P, nullptr, st);
     if (C)
-      KFBI_LAUNCH_P(KFBI_PROF_GRID, k_eig_split_cplx, grid_for(plane, 256), 256, 0, st, T->T2h,
-                    nullptr, plane, T->Mp, T->n1, D->d_lam, kre, kim, (2.0 / D->M) * (2.0 / D->M),
-                    nullptr);
+      KFBI_LAUNCH_P(KFBI_PROF_GRID, k_eig_cplx32, T->n1, 256, 0, st, T->T2h, (float*)nullptr, plane,
+                    T->Mp, T->n1, T->lam, (float)kre, (float)kim, scale, (const double*)nullptr);
     fft_pass(T, T->T2h, T->T1h, 0, 0.f, 0.f, P, nullptr, st);
     fft_pass(T, T->T1h, T->U, 0, 0.f, 0.f, P, nullptr, st);
     return;
@@ -1377,8 +1406,8 @@ static void tc_box_solve(kfbi_domain* D, double kre, double kim, int P, cudaStre
   launch_pass(T, pass_desc(T, kMapT1_hi, kMapT1_lo, T->T2h, T->T2l, C ? 0 : 1, P, (float)kre, scale),
               st);
   if (C)
-    KFBI_LAUNCH_P(KFBI_PROF_GRID, k_eig_split_cplx, grid_for(plane, 256), 256, 0, st, T->T2h,
-                  T->T2l, plane, T->Mp, T->n1, D->d_lam, kre, kim, (2.0 / D->M) * (2.0 / D->M), nullptr);
+    KFBI_LAUNCH_P(KFBI_PROF_GRID, k_eig_cplx32, T->n1, 256, 0, st, T->T2h, T->T2l, plane, T->Mp,
+                  T->n1, T->lam, (float)kre, (float)kim, scale, (const double*)nullptr);
   launch_pass(T, pass_desc(T, kMapT2_hi, kMapT2_lo, T->T1h, T->T1l, 0, P, 0.f, 0.f), st);
   launch_pass(T, pass_desc(T, kMapT1_hi, kMapT1_lo, T->U, nullptr, 2, P, 0.f, 0.f), st);
 }
@@ -1421,9 +1450,8 @@ static void tc_apply_sparse(kfbi_domain* D, double kre, double kim, const double
     fft_pass(T, nullptr, T->T1h, 0, 0.f, 0.f, P, T->stop, st, &sp);
     fft_pass(T, T->T1h, T->T2h, C ? 0 : 1, (float)kre, scale, P, T->stop, st);
     if (C)
-      KFBI_LAUNCH_P(KFBI_PROF_GRID, k_eig_split_cplx, grid_for(plane, 256), 256, 0, st, T->T2h,
-                    nullptr, plane, Mp, T->n1, D->d_lam, kre, kim, (2.0 / D->M) * (2.0 / D->M),
-                    T->stop);
+      KFBI_LAUNCH_P(KFBI_PROF_GRID, k_eig_cplx32, T->n1, 256, 0, st, T->T2h, (float*)nullptr, plane,
+                    Mp, T->n1, T->lam, (float)kre, (float)kim, scale, T->stop);
     fft_pass(T, T->T2h, T->U, 0, 0.f, 0.f, P, T->stop, st);
     if (C)
       KFBI_LAUNCH_P(KFBI_PROF_EXTRACT, k_gather_extract<true>, D->nb, 32 * GE_WARPS, 0, st, T->U, T->S32, Mp,
@@ -1455,8 +1483,8 @@ static void tc_apply_sparse(kfbi_domain* D, double kre, double kim, const double
   d2.stop = T->stop;
   launch_pass(T, d2, st);
   if (C)
-    KFBI_LAUNCH_P(KFBI_PROF_GRID, k_eig_split_cplx, grid_for(plane, 256), 256, 0, st, T->T2h,
-                  T->T2l, plane, Mp, T->n1, D->d_lam, kre, kim, (2.0 / D->M) * (2.0 / D->M), T->stop);
+    KFBI_LAUNCH_P(KFBI_PROF_GRID, k_eig_cplx32, T->n1, 256, 0, st, T->T2h, T->T2l, plane, Mp,
+                  T->n1, T->lam, (float)kre, (float)kim, scale, T->stop);
   PassDesc d3 = pass_desc(T, kMapT2_hi, kMapT2_lo, T->U, nullptr, 2, P, 0.f, 0.f, 0, -1, T->ct0,
                           T->nt3);
   d3.stop = T->stop;

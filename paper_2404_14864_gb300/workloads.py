@@ -107,6 +107,29 @@ class PlaneWaveExact:
         return -self.k2 * self.u(x, y, t)
 
 
+def ex5_star(c=0.2):
+    """The star of the paper's nonlinear Schroedinger example (Sec. 4, Ex. 5):
+    r = 1.5 ((1 - c) + c cos 3 theta) about the origin.  The paper does not
+    state c."""
+    return star(1.5 * (1.0 - c), 1.5 * c, 3, 0.5 * math.pi)
+
+
+class NonlinearSchrodingerExact:
+    """u = exp(i t) cos x cos y solves i u_t = Delta u + (v + w |u|^2) u with
+    w = 1 and v = 1 - cos^2 x cos^2 y (Sec. 4, Eqs. 4.3-4.4)."""
+
+    w = 1.0
+
+    def u(self, x, y, t):
+        return np.exp(1j * t) * np.cos(x) * np.cos(y)
+
+    def lap(self, x, y, t):
+        return -2.0 * self.u(x, y, t)
+
+    def v(self, x, y):
+        return 1.0 - (np.cos(x) * np.cos(y)) ** 2
+
+
 class GaussianPacket:
     """u0 = A exp(-|x - x0|^2 / (2 s^2)) exp(i k . x), normalised so that the
     discrete L2 norm over the grid is 1 (A computed by the caller)."""

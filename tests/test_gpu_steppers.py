@@ -95,7 +95,7 @@ def test_schrodinger_steps_match_oracle():
     assert rel_linf(host(st.get_phi()), orc.phi) <= 1e-9
 
 
-def test_nonlinear_b_step_is_reported_unsupported():
+def test_nonfinite_w_is_refused():
     desc = W.domain_desc(64, W.flower())
     dom = kfbi.Domain(desc)
     st = kfbi.State(dom, kfbi.KFBI_SCHRODINGER)
@@ -104,5 +104,5 @@ def test_nonlinear_b_step_is_reported_unsupported():
     st.init_schrodinger(0.01, dev(ex.u(X, Y, 0)), dev(ex.lap(X, Y, 0)))
     g = dev(np.zeros(desc["nb"], dtype=np.complex128))
     with pytest.raises(kfbi.KfbiError) as e:
-        st.step_schrodinger(dev(np.zeros_like(X)), g, w=1.0)
-    assert e.value.status == 8
+        st.step_schrodinger(dev(np.zeros_like(X)), g, w=float("nan"))
+    assert e.value.status == 1  # KFBI_ERR_ARG

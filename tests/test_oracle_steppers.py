@@ -123,3 +123,62 @@ def test_schrodinger_norm_conservation():
     z = (np.random.default_rng(1).standard_normal(50) + 1j) * 0.3
     vv = np.random.default_rng(2).uniform(0, 3, 50)
     assert np.allclose(np.abs(st.b_step(z, vv)), np.abs(z), atol=1e-15)
+
+
+def test_nonlinear_b_step_newton_root():
+    """Eq. 3.10 with w != 0, solved by Newton: the root satisfies the
+    printed equation, keeps |u| (the two sides of Eq. 3.10 then have equal
+    moduli), and so equals the closed form u* (1 - i b)/(1 + i b) with
+    b = tau/2 (v + w |u*|^2)."""
+    rng = np.random.default_rng(7)
+    z = (rng.standard_normal(400) + 1j * rng.standard_normal(400)) * 0.8
+    v = rng.uniform(-1.0, 3.0, 400)
+    d = oracle.make_domain(W.domain_desc(16, W.star()))
+    for tau, w in ((0.25, 1.0), (0.05, -2.0), (0.125, 3.0)):
+        st = oracle.SchrodingerStepper(d, tau)
+        u = st.b_step(z, v, w)
+        c = 0.5 * tau
+        lhs = u + 1j * c * (v + w * np.abs(u) ** 2) * u
+        rhs = z - 1j * c * (v + w * np.abs(z) ** 2) * z
+        assert np.abs(lhs - rhs).max() <= 1e-14 * np.abs(z).max()
+        assert np.allclose(np.abs(u), np.abs(z), rtol=1e-14, atol=0)
+        b = c * (v + w * np.abs(z) ** 2)
+        assert np.abs(u - z * (1 - 1j * b) / (1 + 1j * b)).max() <= 1e-14
+    # w = 0: the linear Cayley factor
+    st = oracle.SchrodingerStepper(d, 0.1)
+    assert np.allclose(st.b_step(z, v, 0.0), z * (1 - 0.05j * v) / (1 + 0.05j * v), rtol=1e-15)
+
+
+def _nls_err(M, c=0.2):
+    """The paper's nonlinear example (Sec. 4, Ex. 5): w = 1,
+    v = 1 - cos^2 x cos^2 y, u = exp(i t) cos x cos y, star
+    r = 1.5((1 - c) + c cos 3 theta), box [-pi, pi]^2, N_b = M,
+    tau = 8 / M (Table 4's time steps), T = 1."""
+    ex = W.NonlinearSchrodingerExact()
+    desc = W.domain_desc(M, W.ex5_star(c), lo=-math.pi, hi=math.pi)
+    d = oracle.make_domain(desc)
+    X, Y = W.grid_xy(desc)
+    zx, zy = W.boundary_xy(desc)
+    tau = 8.0 / M
+    n = int(round(1.0 / tau))
+    st = oracle.SchrodingerStepper(d, tau, 1e-11)
+    st.init(ex.u(X, Y, 0), ex.lap(X, Y, 0))
+    V = ex.v(X, Y)
+    for k in range(n):
+        U = st.step(ex.u(zx, zy, (k + 1) * tau), V, ex.w)
+    return np.abs(U - ex.u(X, Y, n * tau))[d.interior_inside()].max()
+
+
+def test_nonlinear_schrodinger_matches_paper_table4():
+    """The whole Strang step with the nonlinear B step against the errors the
+    paper prints for this example (Table 4, grids 32, 64, 128): the paper's
+    c is not stated; with c = 0.2 the errors agree within 10 % (they are
+    dominated by the time step: c in [0.1, 0.25] stays within 20 %)."""
+    paper = {}
+    for line in open(GOLDEN):
+        if line.startswith("table4"):
+            _, g, e = line.split()
+            paper[int(g)] = float(e)
+    for M in (32, 64, 128):
+        e = _nls_err(M)
+        assert abs(e / paper[M] - 1.0) < 0.1, (M, e, paper[M])
