@@ -17,7 +17,9 @@ for the heat, wave and Schroedinger equations on irregular domains"):
   division (Sec. 3.4.2), and boundary extraction by the 6x6 Taylor system
   (Eq. 3.36).  ``apply_operator`` chains them: it evaluates the interior
   limit u+ at the boundary nodes of the solution of the interface problem
-  (Eq. 3.30) with Phi = phi, Psi = psi, F = f-tilde.
+  (Eq. 3.30) with Phi = phi, Psi = psi, F = f-tilde; ``apply_neumann``
+  evaluates the interior normal derivative with Phi = 0, Psi = psi (the
+  Neumann BIE operator of Eq. 3.19).
 * ``richardson`` -- the Richardson iteration of Eq. 3.21
 * ``gmres``     -- restarted GMRES with modified Gram-Schmidt and Givens
   rotations for the Dirichlet BIE (Eq. 3.17) (Sec. 5 names GMRES as the
@@ -47,6 +49,7 @@ from .interface import (
     correction_rhs,
     extraction,
     extraction_stencil,
+    apply_neumann,
     apply_operator,
     interface_solve,
 )
@@ -57,6 +60,6 @@ __all__ = [
     "Domain", "PolarCurve", "EllipseCurve", "make_domain", "curve_from_desc",
     "box_solve", "dst_matrix", "eigenvalues", "lagrange6_weights",
     "density_derivatives", "jumps_at", "jump_matrix3", "correction_rhs",
-    "extraction", "extraction_stencil", "apply_operator", "interface_solve",
+    "extraction", "extraction_stencil", "apply_operator", "apply_neumann", "interface_solve",
     "gmres", "richardson", "HeatStepper", "WaveStepper", "SchrodingerStepper",
 ]

@@ -304,10 +304,13 @@ def node_f_gamma(dom, Ft):
     return Ft[sj[k, m] - 1, si[k, m] - 1]
 
 
-def extraction(dom, U, node_jumps):
+def extraction(dom, U, node_jumps, normal=False):
     """u+ at every boundary node from the 6x6 Taylor system of Eq. 3.36:
     U(p) + J(p) [p in Omega^c] = U+ + U+_x xi + U+_y eta + U+_xx xi^2/2
-    + U+_xy xi eta + U+_yy eta^2/2, (xi, eta) = p - z."""
+    + U+_xy xi eta + U+_yy eta^2/2, (xi, eta) = p - z.  With normal=True the
+    interior normal derivative d_n u+ = n_x U+_x + n_y U+_y, n = (tau2, -tau1)
+    the outward normal of Sec. 3.2.5 (the data the Neumann BIE, Eq. 3.19,
+    needs)."""
     si, sj = extraction_stencil(dom)
     dt = np.result_type(U, node_jumps)
     xi = dom.x[si] - dom.zx[:, None]          # (nb, 6)
@@ -318,7 +321,10 @@ def extraction(dom, U, node_jumps):
          + jm[..., 4] * xi * eta + 0.5 * jm[..., 5] * eta * eta)
     b = U[sj - 1, si - 1] + np.where(dom.inside[sj, si], 0.0, J)
     c = np.linalg.solve(A.astype(dt), b.astype(dt)[:, :, None])[:, :, 0]
-    return c[:, 0]
+    if not normal:
+        return c[:, 0]
+    t1, t2, _, _ = tangent_data(dom, dom.theta)
+    return t2 * c[:, 1] - t1 * c[:, 2]
 
 
 # ----------------------------------------------------------------------------
@@ -326,8 +332,9 @@ def extraction(dom, U, node_jumps):
 # ----------------------------------------------------------------------------
 
 
-def interface_solve(dom, kappa, phi, Ft=None, psi=None):
-    """Grid solution U of Eq. 3.30 and the extracted u+ at the boundary nodes.
+def interface_solve(dom, kappa, phi, Ft=None, psi=None, normal=False):
+    """Grid solution U of Eq. 3.30 and the extracted u+ (or, with normal=True,
+    d_n u+) at the boundary nodes.
 
     phi (nb,), psi (nb,) or None, Ft (M-1, M-1) f-tilde or None (zero);
     kappa real or complex.  Returns (u_plus (nb,), U (M-1, M-1))."""
@@ -347,9 +354,19 @@ def interface_solve(dom, kappa, phi, Ft=None, psi=None):
     # (c) jumps at the boundary nodes and extraction.
     nj = jumps_at(dom, None, phi, node_f_gamma(dom, Ft), kappa, psi,
                   node_k=np.arange(dom.nb))
-    return extraction(dom, U, nj), U
+    return extraction(dom, U, nj, normal), U
 
 
 def apply_operator(dom, kappa, phi, Ft=None, psi=None):
     """u+ at the boundary nodes (one application of the BIE operator)."""
     return interface_solve(dom, kappa, phi, Ft, psi)[0]
+
+
+def apply_neumann(dom, kappa, psi, Ft=None):
+    """d_n u+ at the boundary nodes of the interface solution with Phi = 0,
+    Psi = psi, F = Ft (Eq. 3.30).  With Ft = None this is the Neumann BIE
+    operator of Eq. 3.19: u = -V psi has [u_n] = psi (Sec. 3.2.3's table), so
+    its interior normal derivative is psi/2 - d_n(V psi), the principal value
+    plus half the jump; with psi = 0 it is d_n(Y f), the known term."""
+    psi = np.asarray(psi)
+    return interface_solve(dom, kappa, np.zeros(dom.nb, dtype=psi.dtype), Ft, psi, True)[0]
