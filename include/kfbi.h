@@ -160,6 +160,34 @@ kfbi_status kfbi_solve_density(kfbi_domain* dom, double kappa_re, double kappa_i
                                const void* b_dev, void* phi_dev, kfbi_solve_info* info,
                                void* stream);
 
+/* ---- Neumann BVP (Eqs. 3.19, 3.20, 3.22) ---------------------------------
+ * Delta u - kappa u = f in Omega, d_n u = g_N on Gamma (n the outward
+ * normal).  Float64 domains only: other precisions return
+ * KFBI_ERR_UNSUPPORTED.  The box condition is u = 0 on the box (the Green's
+ * function of the Dirichlet box; the solution in Omega does not depend on
+ * that choice). */
+
+/* out_dev[k] = d_n u+(z_k): interior normal derivative at boundary node k of
+ * the solution of the interface problem (Eq. 3.30) with [u] = 0,
+ * [u_n] = psi, F = f-tilde (f_dev may be NULL).  With f = 0 this is the
+ * Neumann BIE operator psi/2 - d_n (V psi) of Eq. 3.19 (u = -V psi).
+ * Layouts and types as kfbi_apply_operator.  Asynchronous on `stream`. */
+kfbi_status kfbi_apply_neumann(kfbi_domain* dom, double kappa_re, double kappa_im,
+                               const void* psi_dev, const void* f_dev, void* out_dev,
+                               void* stream);
+
+/* Solve the Neumann BVP: b = g_N - d_n (Y f)+, the BIE of Eq. 3.19 for psi
+ * with the domain's solver (GMRES or the Richardson iteration of Eq. 3.22),
+ * then u = Y f - V psi (Eq. 3.20) on the grid.
+ *   gn_dev     : n_boundary values of g_N (complex128 if kappa_im != 0).
+ *   f_dev      : (M-1)^2 grid of f or NULL (values outside Omega ignored).
+ *   psi_dev    : n_boundary, initial guess on entry, density on exit.
+ *   u_grid_dev : (M-1)^2 grid solution on exit (NULL: not formed).
+ * Synchronous.  KFBI_ERR_NOT_CONVERGED if gmres_maxit is reached. */
+kfbi_status kfbi_solve_neumann(kfbi_domain* dom, double kappa_re, double kappa_im,
+                               const void* gn_dev, const void* f_dev, void* psi_dev,
+                               void* u_grid_dev, kfbi_solve_info* info, void* stream);
+
 /* Allocation-free box solve, for callers that cannot allocate device memory
  * (code that runs where cudaMalloc is not allowed, e.g. inside a graph
  * capture it does not own, or a plugin whose host program owns every device
@@ -323,7 +351,11 @@ typedef enum {
   KFBI_PLAN_NODE_A = 18,     /* double[nb*6]: kappa-free density weights, nodes k-2..k+3 */
   KFBI_PLAN_NODE_B = 19,     /* double[nb*6]: density weights multiplying kappa */
   KFBI_PLAN_NODE_FIDX = 20,  /* int32[nb]: interior index of f at the node */
-  KFBI_PLAN_NODE_FCOEF = 21  /* double[nb]: its coefficient */
+  KFBI_PLAN_NODE_FCOEF = 21, /* double[nb]: its coefficient */
+  KFBI_PLAN_ARM_DELTA = 22,  /* double[n_arms*6]: weights of the Neumann density psi */
+  KFBI_PLAN_NODE_WN = 23,    /* double[nb*6]: normal-derivative extraction weights on U */
+  KFBI_PLAN_NODE_E = 24,     /* double[nb*6]: psi weights of d_n u+, nodes k-2..k+3 */
+  KFBI_PLAN_NODE_FCOEF_N = 25 /* double[nb]: coefficient of f (at NODE_FIDX) in d_n u+ */
 } kfbi_plan_field;
 
 kfbi_status kfbi_plan_create(const kfbi_domain_desc* desc, kfbi_plan** out);

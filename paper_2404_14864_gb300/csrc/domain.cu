@@ -98,7 +98,7 @@ __global__ void k_correct(double* __restrict__ R, size_t plane, const double* __
     double ar = 0.0, ai = 0.0, br = 0.0, bi = 0.0;
 #pragma unroll
     for (int m = 0; m < 6; ++m) {
-      const double al = alpha[m * n_arms + a], be = beta[m * n_arms + a];
+      const double al = alpha[m * n_arms + a], be = beta ? beta[m * n_arms + a] : 0.0;
       const double pr = phi[(size_t)k * ps];
       ar = fma(al, pr, ar);
       br = fma(be, pr, br);
@@ -220,7 +220,7 @@ __global__ void k_extract(const double* __restrict__ U, size_t plane, const doub
   if (kk < 0) kk += nb;
 #pragma unroll
   for (int j = 0; j < 6; ++j) {
-    const double a = A[j * nb + k], b = B[j * nb + k];
+    const double a = A[j * nb + k], b = B ? B[j * nb + k] : 0.0;
     const double pr = phi[(size_t)kk * ps];
     ar = fma(a, pr, ar);
     br = fma(b, pr, br);
@@ -287,7 +287,8 @@ static void free_domain(kfbi_domain* D) {
                   D->d_node_a, D->d_node_b, D->d_node_fidx, D->d_node_fcoef, D->d_arm_alpha32,
                   D->d_arm_beta32, D->d_arm_fcoef32, D->d_node_w32, D->d_node_a32,
                   D->d_node_b32, D->d_node_fcoef32, D->d_R, D->d_T, D->d_U,
-                  D->d_fpad, D->d_zero_nb};
+                  D->d_fpad, D->d_zero_nb, D->d_arm_delta, D->d_node_wn, D->d_node_e,
+                  D->d_node_fcoef_n};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete D;
@@ -341,6 +342,12 @@ static void upload_domain(kfbi_domain* D, const Plan& P) {
   D->d_node_b = dev_upload(D, nb_);
   D->d_node_fidx = dev_upload(D, to_padded(P.node_fidx, n1, Mp));
   D->d_node_fcoef = dev_upload(D, P.node_fcoef);
+  if (D->desc.precision == KFBI_FP64) {
+    D->d_arm_delta = dev_upload(D, transpose(P.arm_delta, na, 6));
+    D->d_node_wn = dev_upload(D, transpose(P.node_wn, nb, 6));
+    D->d_node_e = dev_upload(D, transpose(P.node_e, nb, 6));
+    D->d_node_fcoef_n = dev_upload(D, P.node_fcoef_n);
+  }
   if (is_mixed(D->desc.precision)) {
     D->d_arm_alpha32 = dev_upload(D, to_f32(alpha));
     D->d_arm_beta32 = dev_upload(D, to_f32(beta));
@@ -380,36 +387,44 @@ void correct_fp64(kfbi_domain* D, double kre, double kim, const double* phi, int
     KFBI_CUDA(cudaMemsetAsync(D->d_R, 0, 2 * plane * sizeof(double), st));
     D->rhs_sparse_planes = 2;
   }
+  // Neumann: the density is psi, weighted by arm_delta, with no kappa term
+  const double* al = D->neumann ? D->d_arm_delta : D->d_arm_alpha;
+  const double* be = D->neumann ? nullptr : D->d_arm_beta;
   if (D->n_irr > 0) {
     if (C)
       KFBI_LAUNCH_P(KFBI_PROF_CORRECT, k_correct<true>, (D->n_irr + 127) / 128, 128, 0, st, D->d_R, plane, ft,
-                  D->d_irr_off, D->d_arm_start, D->d_arm_k0, D->d_arm_alpha, D->d_arm_beta,
+                  D->d_irr_off, D->d_arm_start, D->d_arm_k0, al, be,
                   D->d_arm_fidx, D->d_arm_fcoef, D->n_irr, D->n_arms, D->nb, phi, ps, kre, kim);
     else
       KFBI_LAUNCH_P(KFBI_PROF_CORRECT, k_correct<false>, (D->n_irr + 127) / 128, 128, 0, st, D->d_R, plane, ft,
-                  D->d_irr_off, D->d_arm_start, D->d_arm_k0, D->d_arm_alpha, D->d_arm_beta,
+                  D->d_irr_off, D->d_arm_start, D->d_arm_k0, al, be,
                   D->d_arm_fidx, D->d_arm_fcoef, D->n_irr, D->n_arms, D->nb, phi, ps, kre, kim);
   }
   KFBI_CHECK_LAUNCH();
 }
 
-// FP64 extraction of u+ from the grid solution in D->d_U.
+// FP64 extraction of u+ (Neumann: d_n u+) from the grid solution in D->d_U.
 void extract_fp64(kfbi_domain* D, double kre, double kim, const double* phi, int ps,
                   const double* ft, double* out, int os, cudaStream_t st) {
   const size_t plane = (size_t)D->Mp * D->Mp;
+  const bool nm = D->neumann;
+  const double* w = nm ? D->d_node_wn : D->d_node_w;
+  const double* a = nm ? D->d_node_e : D->d_node_a;
+  const double* b = nm ? nullptr : D->d_node_b;
+  const double* fc = nm ? D->d_node_fcoef_n : D->d_node_fcoef;
   if (kim != 0.0)
     KFBI_LAUNCH_P(KFBI_PROF_EXTRACT, k_extract<true>, (D->nb + 127) / 128, 128, 0, st, D->d_U, plane, ft,
-                D->d_node_gidx, D->d_node_w, D->d_node_a, D->d_node_b, D->d_node_fidx,
-                D->d_node_fcoef, D->nb, phi, ps, kre, kim, out, os);
+                D->d_node_gidx, w, a, b, D->d_node_fidx, fc, D->nb, phi, ps, kre, kim, out, os);
   else
     KFBI_LAUNCH_P(KFBI_PROF_EXTRACT, k_extract<false>, (D->nb + 127) / 128, 128, 0, st, D->d_U, plane, ft,
-                D->d_node_gidx, D->d_node_w, D->d_node_a, D->d_node_b, D->d_node_fidx,
-                D->d_node_fcoef, D->nb, phi, ps, kre, kim, out, os);
+                D->d_node_gidx, w, a, b, D->d_node_fidx, fc, D->nb, phi, ps, kre, kim, out, os);
   KFBI_CHECK_LAUNCH();
 }
 
 void apply_internal(kfbi_domain* D, double kre, double kim, const double* phi, int ps,
                     const double* ft, double* out, int os, bool want_grid, cudaStream_t st) {
+  if (D->tc && D->neumann)
+    throw Status{KFBI_ERR_UNSUPPORTED, "the Neumann operator runs on KFBI_FP64 domains"};
   if (D->tc) {
     tc_apply(D, kre, kim, phi, ps, ft, out, os, want_grid, st);
     return;
@@ -495,6 +510,9 @@ long long domain_bytes_for(const Plan& P) {
                       3 * n1(P.node_w.size()) + n1(P.node_fcoef.size());
   b += sizeof(double) * dtab;
   if (mixed) b += sizeof(float) * dtab;
+  if (P.desc.precision == KFBI_FP64)  // Neumann tables
+    b += sizeof(double) * (n1(P.arm_delta.size()) + 2 * n1(P.node_wn.size()) +
+                           n1(P.node_fcoef_n.size()));
   b += sizeof(double) * (2 * plane * (mixed ? 3 : 4) + 2 * (size_t)P.nb);   // R, (T), U, fpad, zero_nb
   long long total = (long long)b + gmres_bytes(P.desc.gmres_restart, P.nb);
   if (mixed) total += tc_bytes_for(P, Mp);
@@ -660,11 +678,14 @@ long long kfbi_plan_size(const kfbi_plan* plan, int field) {
     case KFBI_PLAN_IRREGULAR: return P.n_irr();
     case KFBI_PLAN_N_ARMS: return P.n_arms();
     case KFBI_PLAN_ARM_NODE: case KFBI_PLAN_ARM_K0: return P.n_arms();
-    case KFBI_PLAN_ARM_ALPHA: case KFBI_PLAN_ARM_BETA: return (long long)P.n_arms() * 6;
+    case KFBI_PLAN_ARM_ALPHA: case KFBI_PLAN_ARM_BETA: case KFBI_PLAN_ARM_DELTA:
+      return (long long)P.n_arms() * 6;
     case KFBI_PLAN_ARM_FIDX: case KFBI_PLAN_ARM_FCOEF: return (long long)P.n_arms() * 2;
     case KFBI_PLAN_NODE_GIDX: case KFBI_PLAN_NODE_W: case KFBI_PLAN_NODE_A:
-    case KFBI_PLAN_NODE_B: return (long long)P.nb * 6;
-    case KFBI_PLAN_NODE_FIDX: case KFBI_PLAN_NODE_FCOEF: return P.nb;
+    case KFBI_PLAN_NODE_B: case KFBI_PLAN_NODE_WN: case KFBI_PLAN_NODE_E:
+      return (long long)P.nb * 6;
+    case KFBI_PLAN_NODE_FIDX: case KFBI_PLAN_NODE_FCOEF: case KFBI_PLAN_NODE_FCOEF_N:
+      return P.nb;
     default: return -1;
   }
 }
@@ -696,6 +717,10 @@ kfbi_status kfbi_plan_export(const kfbi_plan* plan, int field, void* dst) {
     case KFBI_PLAN_NODE_B: return cp(P.node_b);
     case KFBI_PLAN_NODE_FIDX: return cp(P.node_fidx);
     case KFBI_PLAN_NODE_FCOEF: return cp(P.node_fcoef);
+    case KFBI_PLAN_ARM_DELTA: return cp(P.arm_delta);
+    case KFBI_PLAN_NODE_WN: return cp(P.node_wn);
+    case KFBI_PLAN_NODE_E: return cp(P.node_e);
+    case KFBI_PLAN_NODE_FCOEF_N: return cp(P.node_fcoef_n);
     default: return KFBI_ERR_ARG;
   }
 }

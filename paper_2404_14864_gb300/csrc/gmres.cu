@@ -1483,3 +1483,93 @@ extern "C" kfbi_status kfbi_solve_density(kfbi_domain* dom, double kappa_re, dou
     return s;
   });
 }
+
+// ---- Neumann BVP (Eqs. 3.19, 3.20) ------------------------------------------
+
+namespace {
+// Switches the domain's operator to psi -> d_n u+ for the lifetime of a
+// Neumann entry point.
+struct NeumannScope {
+  kfbi_domain* D;
+  explicit NeumannScope(kfbi_domain* d) : D(d) { D->neumann = true; }
+  ~NeumannScope() { D->neumann = false; }
+};
+
+kfbi_status neumann_check(kfbi_domain* dom) {
+  if (dom->desc.precision != KFBI_FP64) {
+    dom->err = "the Neumann operator runs on KFBI_FP64 domains";
+    return KFBI_ERR_UNSUPPORTED;
+  }
+  return KFBI_OK;
+}
+}  // namespace
+
+extern "C" kfbi_status kfbi_apply_neumann(kfbi_domain* dom, double kappa_re, double kappa_im,
+                                          const void* psi_dev, const void* f_dev, void* out_dev,
+                                          void* stream) {
+  if (!dom) return KFBI_ERR_ARG;
+  if (!psi_dev || !out_dev) {
+    dom->err = "psi_dev and out_dev must be device pointers";
+    return KFBI_ERR_ARG;
+  }
+  kfbi_status c = neumann_check(dom);
+  if (c != KFBI_OK) return c;
+  return guarded(dom, [&]() -> kfbi_status {
+    NeumannScope ns(dom);
+    cudaStream_t st = (cudaStream_t)stream;
+    const bool C = kappa_im != 0.0;
+    const double* ft = nullptr;
+    if (f_dev) {
+      pad_mask(dom, (const double*)f_dev, dom->d_fpad, C, st);
+      ft = dom->d_fpad;
+    }
+    apply_internal(dom, kappa_re, kappa_im, (const double*)psi_dev, C ? 2 : 1, ft,
+                   (double*)out_dev, C ? 2 : 1, false, st);
+    return KFBI_OK;
+  });
+}
+
+extern "C" kfbi_status kfbi_solve_neumann(kfbi_domain* dom, double kappa_re, double kappa_im,
+                                          const void* gn_dev, const void* f_dev, void* psi_dev,
+                                          void* u_grid_dev, kfbi_solve_info* info,
+                                          void* stream) {
+  if (!dom) return KFBI_ERR_ARG;
+  if (!gn_dev || !psi_dev) {
+    dom->err = "gn_dev and psi_dev must be device pointers";
+    return KFBI_ERR_ARG;
+  }
+  kfbi_status c = neumann_check(dom);
+  if (c != KFBI_OK) return c;
+  return guarded(dom, [&]() -> kfbi_status {
+    NeumannScope ns(dom);
+    cudaStream_t st = (cudaStream_t)stream;
+    const int C = kappa_im != 0.0, nb = dom->nb;
+    const double* ft = nullptr;
+    if (f_dev) {
+      pad_mask(dom, (const double*)f_dev, dom->d_fpad, C, st);
+      ft = dom->d_fpad;
+    }
+    KFBI_LAUNCH(k_to_cplx, (nb + 255) / 256, 256, 0, st, (const double*)gn_dev, dom->d_B, nb, C);
+    KFBI_LAUNCH(k_to_cplx, (nb + 255) / 256, 256, 0, st, (const double*)psi_dev, dom->d_X, nb, C);
+    KFBI_CHECK_LAUNCH();
+    // b = g_N - d_n (Y f)+ : the known term of Eq. 3.19
+    const double* b = dom->d_B;
+    if (ft) {
+      apply_internal(dom, kappa_re, kappa_im, dom->d_zero_nb, 2, ft, dom->d_Dv, 2, false, st);
+      KFBI_LAUNCH_P(KFBI_PROF_KRYLOV, k_residual, 1, kThreads, 0, st, (const double2*)dom->d_B,
+                    (const double2*)dom->d_Dv, (double2*)dom->d_Rv, nb, dom->d_scal);
+      KFBI_CHECK_LAUNCH();
+      b = dom->d_Rv;
+    }
+    kfbi_status s = gmres_solve(dom, kappa_re, kappa_im, b, dom->d_X, false, info, st);
+    if (u_grid_dev && s == KFBI_OK) {
+      // u = Y f - V psi (Eq. 3.20): the interface solution with Psi = psi
+      apply_internal(dom, kappa_re, kappa_im, dom->d_X, 2, ft, nullptr, 2, true, st);
+      unpad(dom, dom->d_U, (double*)u_grid_dev, C, st);
+    }
+    KFBI_LAUNCH(k_from_cplx, (nb + 255) / 256, 256, 0, st, dom->d_X, (double*)psi_dev, nb, C);
+    KFBI_CHECK_LAUNCH();
+    KFBI_CUDA(cudaStreamSynchronize(st));
+    return s;
+  });
+}

@@ -208,6 +208,15 @@ struct kfbi_domain {
   double* d_node_b = nullptr;
   int* d_node_fidx = nullptr;
   double* d_node_fcoef = nullptr;
+  // Neumann tables (float64 domains): psi weights per arm, normal-derivative
+  // extraction weights, their psi and f terms
+  double* d_arm_delta = nullptr;
+  double* d_node_wn = nullptr;
+  double* d_node_e = nullptr;
+  double* d_node_fcoef_n = nullptr;
+  // set while a Neumann entry point runs: the operator of apply_internal is
+  // then psi -> d_n u+ (Phi = 0, Psi = psi) instead of phi -> u+
+  bool neumann = false;
   float* d_arm_alpha32 = nullptr;  // FP32 copies for the mixed path
   float* d_arm_beta32 = nullptr;
   float* d_arm_fcoef32 = nullptr;

@@ -290,7 +290,7 @@ kfbi_status build_plan(const kfbi_domain_desc& desc, Plan& P, std::string& err) 
   // correction arms: two per cut edge, grouped by node
   struct Arm {
     int node, k0;
-    double alpha[6], beta[6];
+    double alpha[6], beta[6], delta[6];
     int fidx[2];
     double fcoef[2];
   };
@@ -310,11 +310,12 @@ kfbi_status build_plan(const kfbi_domain_desc& desc, Plan& P, std::string& err) 
     density_weights(s, fr, P.dtheta, W0, As, Ass);
     const double ct = fr.t1p * fr.t1 + fr.t2p * fr.t2;
     const double cn = fr.t1p * fr.t2 - fr.t2p * fr.t1;
-    double td, Pw, Qw, Nw;
+    // along the cut direction d: td = t.e_d, nd = n.e_d with n = (t2, -t1)
+    double td, nd, Pw, Qw, Nw;
     if (dir == 0) {
-      td = fr.t1; Pw = fr.t1 * fr.t1 - fr.t2 * fr.t2; Qw = fr.t1 * fr.t2; Nw = fr.t2 * fr.t2;
+      td = fr.t1; nd = fr.t2; Pw = fr.t1 * fr.t1 - fr.t2 * fr.t2; Qw = fr.t1 * fr.t2; Nw = fr.t2 * fr.t2;
     } else {
-      td = fr.t2; Pw = fr.t2 * fr.t2 - fr.t1 * fr.t1; Qw = -fr.t1 * fr.t2; Nw = fr.t1 * fr.t1;
+      td = fr.t2; nd = -fr.t1; Pw = fr.t2 * fr.t2 - fr.t1 * fr.t1; Qw = -fr.t1 * fr.t2; Nw = fr.t1 * fr.t1;
     }
     // f at the intersection: linear extrapolation along the grid line from
     // the Omega-side endpoint pin and the next node inward.
@@ -341,6 +342,11 @@ kfbi_status build_plan(const kfbi_domain_desc& desc, Plan& P, std::string& err) 
         a.alpha[m] = sc * (W0[m] + d * td * As[m] +
                            hd2 * ((Ass[m] - ct * As[m]) * Pw + 2.0 * cn * As[m] * Qw));
         a.beta[m] = sc * hd2 * Nw * W0[m];
+        // psi part: [u] = 0, [u_d] = nd psi, and in the (t, n) frame
+        // H_tt = -cn psi, H_tn = psi_s - ct psi, H_nn = cn psi, so
+        // [u_dd] = -cn Pw psi + 2 Qw (psi_s - ct psi)
+        a.delta[m] = sc * (d * nd * W0[m] +
+                           hd2 * (-cn * Pw * W0[m] + 2.0 * Qw * (As[m] - ct * W0[m])));
       }
       const double gam = sc * hd2 * Nw;
       a.fidx[0] = (pj - 1) * n1 + (pi - 1);
@@ -363,6 +369,7 @@ kfbi_status build_plan(const kfbi_domain_desc& desc, Plan& P, std::string& err) 
   P.arm_k0.resize(na);
   P.arm_alpha.resize((size_t)na * 6);
   P.arm_beta.resize((size_t)na * 6);
+  P.arm_delta.resize((size_t)na * 6);
   P.arm_fidx.resize((size_t)na * 2);
   P.arm_fcoef.resize((size_t)na * 2);
   for (int a = 0; a < na; ++a) {
@@ -372,6 +379,7 @@ kfbi_status build_plan(const kfbi_domain_desc& desc, Plan& P, std::string& err) 
     for (int m = 0; m < 6; ++m) {
       P.arm_alpha[(size_t)a * 6 + m] = arms[a].alpha[m];
       P.arm_beta[(size_t)a * 6 + m] = arms[a].beta[m];
+      P.arm_delta[(size_t)a * 6 + m] = arms[a].delta[m];
     }
     for (int q2 = 0; q2 < 2; ++q2) {
       P.arm_fidx[(size_t)a * 2 + q2] = arms[a].fidx[q2];
@@ -387,6 +395,9 @@ kfbi_status build_plan(const kfbi_domain_desc& desc, Plan& P, std::string& err) 
   P.node_b.resize((size_t)nb * 6);
   P.node_fidx.resize(nb);
   P.node_fcoef.resize(nb);
+  P.node_wn.resize((size_t)nb * 6);
+  P.node_e.resize((size_t)nb * 6);
+  P.node_fcoef_n.resize(nb);
   for (int k = 0; k < nb; ++k) {
     const double zx = P.zx[k], zy = P.zy[k];
     const int i0 = (int)std::floor((zx - P.lo) / h + 0.5);
@@ -423,26 +434,31 @@ kfbi_status build_plan(const kfbi_domain_desc& desc, Plan& P, std::string& err) 
       err = "extraction stencil has no point in Omega";
       return KFBI_ERR_GEOMETRY;
     }
-    if (!gepp(A, rhs, 6)) {
+    // normal-derivative weights: the same system with right-hand side
+    // (t2 e_1 - t1 e_2) / h (the 1/h undoes the column scaling)
+    Frame fr = frame_at(cv, P.dtheta * (double)k);
+    const double t1 = fr.t1, t2 = fr.t2;
+    double An[36], rn[6] = {0.0, t2 / h, -t1 / h, 0.0, 0.0, 0.0};
+    std::memcpy(An, A, sizeof(A));
+    if (!gepp(A, rhs, 6) || !gepp(An, rn, 6)) {
       err = "singular extraction system";
       return KFBI_ERR_GEOMETRY;
     }
-    double G[6] = {0, 0, 0, 0, 0, 0};
+    double G[6] = {0, 0, 0, 0, 0, 0}, Gn[6] = {0, 0, 0, 0, 0, 0};
     for (int m = 0; m < 6; ++m) {
       P.node_w[(size_t)k * 6 + m] = rhs[m];
+      P.node_wn[(size_t)k * 6 + m] = rn[m];
       if (!P.in(si[m], sj[m])) {
-        G[0] += rhs[m];
-        G[1] += rhs[m] * xi[m];
-        G[2] += rhs[m] * eta[m];
-        G[3] += rhs[m] * 0.5 * xi[m] * xi[m];
-        G[4] += rhs[m] * xi[m] * eta[m];
-        G[5] += rhs[m] * 0.5 * eta[m] * eta[m];
+        const double tay[6] = {1.0, xi[m], eta[m], 0.5 * xi[m] * xi[m], xi[m] * eta[m],
+                               0.5 * eta[m] * eta[m]};
+        for (int c2 = 0; c2 < 6; ++c2) {
+          G[c2] += rhs[m] * tay[c2];
+          Gn[c2] += rn[m] * tay[c2];
+        }
       }
     }
-    Frame fr = frame_at(cv, P.dtheta * (double)k);
     double W0[6], As[6], Ass[6];
     density_weights(0.0, fr, P.dtheta, W0, As, Ass);
-    const double t1 = fr.t1, t2 = fr.t2;
     const double ct = fr.t1p * t1 + fr.t2p * t2;
     const double cn = fr.t1p * t2 - fr.t2p * t1;
     const double Mss = G[3] * (t1 * t1 - t2 * t2) + G[5] * (t2 * t2 - t1 * t1) + 2.0 * G[4] * t1 * t2;
@@ -455,6 +471,15 @@ kfbi_status build_plan(const kfbi_domain_desc& desc, Plan& P, std::string& err) 
     }
     P.node_fidx[k] = (sj[best] - 1) * n1 + (si[best] - 1);
     P.node_fcoef[k] = cR3;
+    // d_n u+ with Phi = 0, Psi = psi: jumps [u_x] = t2 psi, [u_y] = -t1 psi
+    // and, in the (t, n) frame, H_tt = -cn psi, H_tn = psi_s - ct psi,
+    // H_nn = f + cn psi, projected through the Omega^c rows (Gn)
+    const double Ktt = Gn[3] * t1 * t1 + Gn[4] * t1 * t2 + Gn[5] * t2 * t2;
+    const double Ktn = 2.0 * (Gn[3] - Gn[5]) * t1 * t2 + Gn[4] * (t2 * t2 - t1 * t1);
+    const double Knn = Gn[3] * t2 * t2 - Gn[4] * t1 * t2 + Gn[5] * t1 * t1;
+    const double cpsi = Gn[1] * t2 - Gn[2] * t1 - cn * Ktt - ct * Ktn + cn * Knn;
+    for (int m = 0; m < 6; ++m) P.node_e[(size_t)k * 6 + m] = cpsi * W0[m] + Ktn * As[m];
+    P.node_fcoef_n[k] = Knn;
   }
   return KFBI_OK;
 }

@@ -44,6 +44,9 @@ struct Plan {
   std::vector<double> arm_alpha, arm_beta;  // [a*6 + m]
   std::vector<int> arm_fidx;                // [a*2 + q], interior index
   std::vector<double> arm_fcoef;            // [a*2 + q]
+  // Neumann data (Psi = psi, Phi = 0): correction weights of psi at the
+  // arm's six density nodes (no kappa term: [u] = 0)
+  std::vector<double> arm_delta;  // [a*6 + m]
 
   // boundary-node extraction tables
   std::vector<int> node_gidx;     // [k*6 + m]
@@ -51,6 +54,10 @@ struct Plan {
   std::vector<double> node_a, node_b;  // [k*6 + j], density nodes k-2+j
   std::vector<int> node_fidx;     // [k]
   std::vector<double> node_fcoef; // [k]
+  // interior normal derivative d_n u+ (Neumann BIE, Eq. 3.19): stencil
+  // weights, psi weights at density nodes k-2+j, f coefficient
+  std::vector<double> node_wn, node_e;  // [k*6 + m], [k*6 + j]
+  std::vector<double> node_fcoef_n;     // [k]
 
   int n_irr() const { return (int)irr.size(); }
   int n_arms() const { return (int)arm_node.size(); }

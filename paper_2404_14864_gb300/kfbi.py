@@ -33,6 +33,8 @@ PLAN_FIELDS = {
     "arm_fcoef": (15, np.float64), "node_gidx": (16, np.int32), "node_w": (17, np.float64),
     "node_a": (18, np.float64), "node_b": (19, np.float64), "node_fidx": (20, np.int32),
     "node_fcoef": (21, np.float64),
+    "arm_delta": (22, np.float64), "node_wn": (23, np.float64), "node_e": (24, np.float64),
+    "node_fcoef_n": (25, np.float64),
 }
 
 
@@ -113,6 +115,9 @@ def lib():
         "kfbi_apply_operator": (S, [_VP, ctypes.c_double, ctypes.c_double, _VP, _VP, _VP, _VP]),
         "kfbi_interface_solve": (S, [_VP, ctypes.c_double, ctypes.c_double, _VP, _VP, _VP, _VP, _VP]),
         "kfbi_solve_density": (S, [_VP, ctypes.c_double, ctypes.c_double, _VP, _VP,
+                                   ctypes.POINTER(SolveInfo), _VP]),
+        "kfbi_apply_neumann": (S, [_VP, ctypes.c_double, ctypes.c_double, _VP, _VP, _VP, _VP]),
+        "kfbi_solve_neumann": (S, [_VP, ctypes.c_double, ctypes.c_double, _VP, _VP, _VP, _VP,
                                    ctypes.POINTER(SolveInfo), _VP]),
         "kfbi_state_create": (S, [_VP, ctypes.c_int, ctypes.POINTER(_VP)]),
         "kfbi_state_destroy": (None, [_VP]),
@@ -346,6 +351,26 @@ class Domain:
 
     def solve_density(self, kappa, b, phi, stream=None):
         return kfbi_solve_density(self.h, kappa, b, phi, stream)
+
+    def apply_neumann(self, kappa, psi, f=None, out=None, stream=None):
+        """d_n u+ of the interface solution with Psi = psi (Eq. 3.19's operator
+        for f = None)."""
+        import torch
+        if out is None:
+            out = torch.empty_like(psi)
+        k = complex(kappa)
+        _check(lib().kfbi_apply_neumann(self.h, k.real, k.imag, _ptr(psi), _ptr(f), _ptr(out),
+                                        _stream(stream)), self.h)
+        return out
+
+    def solve_neumann(self, kappa, gn, psi, f=None, u_grid=None, stream=None):
+        """Neumann BVP: psi (initial guess in, density out), optional grid u."""
+        k = complex(kappa)
+        info = SolveInfo()
+        _check(lib().kfbi_solve_neumann(self.h, k.real, k.imag, _ptr(gn), _ptr(f), _ptr(psi),
+                                        _ptr(u_grid), ctypes.byref(info), _stream(stream)),
+               self.h)
+        return info.as_dict()
 
 
 def table_cache_bytes():

@@ -140,6 +140,49 @@ def test_plan_tables_reproduce_oracle_correction_and_extraction(built, desc, kap
     assert np.abs(up_pl - up_or).max() <= 1e-11 * max(1.0, np.abs(up_or).max())
 
 
+@pytest.mark.parametrize("desc", DOMAINS, ids=lambda d: "%s-%d" % (d["curve"]["kind"], d["M"]))
+@pytest.mark.parametrize("kappa", [17.0, 40.0j])
+def test_plan_neumann_tables_reproduce_oracle(built, desc, kappa):
+    """Psi = psi, Phi = 0: the arm weights of psi give the oracle's corrected
+    right-hand side, and the normal-derivative tables its d_n u+ (Eq. 3.36
+    rows U_x, U_y with the psi and f jump terms)."""
+    p = kfbi.Plan(desc)
+    d = oracle.make_domain(desc)
+    rng = np.random.default_rng(5)
+    n1, nb = desc["M"] - 1, desc["nb"]
+    cplx = isinstance(kappa, complex)
+    psi = np.sin(2 * d.theta) + 0.4 * np.cos(5 * d.theta) + 0.1 * rng.standard_normal(nb)
+    X, Y = W.grid_xy(desc)
+    Ft = np.where(d.interior_inside(), np.sin(2 * X + 1) * np.cosh(Y) * 50.0, 0.0)
+    if cplx:
+        psi = psi + 0.5j * np.cos(3 * d.theta)
+        Ft = Ft * (1 - 0.5j)
+    zero = np.zeros(nb, dtype=psi.dtype)
+    ej = oracle.jumps_at(d, d.edge_theta, zero, edge_f_gamma(d, Ft), kappa, psi)
+    R_or = oracle.correction_rhs(d, Ft, ej)
+    irr = p.field("irregular")
+    node = p.field("arm_node"); k0 = p.field("arm_k0")
+    de = p.field("arm_delta").reshape(-1, 6)
+    fi = p.field("arm_fidx").reshape(-1, 2); fc = p.field("arm_fcoef").reshape(-1, 2)
+    idx = (k0[:, None] + np.arange(6)[None, :]) % nb
+    f = Ft.ravel()
+    contrib = (de * psi[idx]).sum(axis=1) + (fc * f[fi]).sum(axis=1)
+    acc = np.zeros(len(irr), dtype=R_or.dtype)
+    np.add.at(acc, node, contrib)
+    R_pl = Ft.ravel().astype(R_or.dtype).copy()
+    R_pl[irr] = f[irr] + acc
+    assert np.abs(R_pl.reshape(n1, n1) - R_or).max() <= 1e-12 * np.abs(R_or).max()
+    U = rng.standard_normal((n1, n1)) + (1j * rng.standard_normal((n1, n1)) if cplx else 0)
+    nj = oracle.jumps_at(d, None, zero, node_f_gamma(d, Ft), kappa, psi, node_k=np.arange(nb))
+    dn_or = oracle.extraction(d, U, nj, normal=True)
+    g = p.field("node_gidx").reshape(nb, 6)
+    wn = p.field("node_wn").reshape(nb, 6); e = p.field("node_e").reshape(nb, 6)
+    jdx = (np.arange(nb)[:, None] - 2 + np.arange(6)[None, :]) % nb
+    dn_pl = (wn * U.ravel()[g]).sum(1) + (e * psi[jdx]).sum(1) + \
+        p.field("node_fcoef_n") * f[p.field("node_fidx")]
+    assert np.abs(dn_pl - dn_or).max() <= 1e-10 * max(1.0, np.abs(dn_or).max())
+
+
 def test_plan_device_bytes_on_the_host(built):
     """The exact admission count is host-only: it grows with the padded grid
     and the equation's fields, and rejects bad arguments."""
