@@ -251,6 +251,14 @@ kfbi_status kfbi_step_schrodinger(kfbi_domain* dom, kfbi_state* st, const double
                                   double w, const void* g_next_dev, kfbi_solve_info* info,
                                   void* stream);
 
+/* Boundary condition of the state's steps: neumann = 0 (default) takes
+ * g_next as Dirichlet data u = g (Eq. 3.17), neumann = 1 as Neumann data
+ * d_n u = g with the outward normal (Eq. 3.19; the density is then psi and
+ * u = Y f - V psi, Eq. 3.20).  Resets the density to zero.  Neumann needs a
+ * KFBI_FP64 domain (else KFBI_ERR_UNSUPPORTED); batches and the server take
+ * Dirichlet states only. */
+kfbi_status kfbi_state_set_neumann(kfbi_state* st, int neumann);
+
 /* Copy the current field u^n (all (M-1)^2 nodes; values outside Omega are
  * the exterior part of the interface solution) or the current density. */
 kfbi_status kfbi_state_get_u(kfbi_state* st, void* u_out_dev, void* stream);

@@ -37,25 +37,30 @@ F^1 by initial boundary condition"):
 import numpy as np
 
 from .gmres import gmres, richardson
-from .interface import apply_operator, interface_solve
+from .interface import apply_neumann, apply_operator, interface_solve
 
 
 class _Base:
-    def __init__(self, dom, tau, tol=1e-10, restart=50, maxit=2000, solver="gmres", gamma=0.5):
+    def __init__(self, dom, tau, tol=1e-10, restart=50, maxit=2000, solver="gmres", gamma=0.5,
+                 bc="dirichlet"):
         self.dom, self.tau = dom, float(tau)
         self.tol, self.restart, self.maxit = tol, restart, maxit
         self.solver, self.gamma = solver, gamma
+        self.bc = bc
         self.mask = dom.interior_inside()
         self.phi = None
         self.iters = []
 
     def _solve(self, kappa, F, g):
-        """u^{n+1} on the grid for Delta u - kappa u = -F, u = g on Gamma."""
+        """u^{n+1} on the grid for Delta u - kappa u = -F with u = g on Gamma
+        (Eq. 3.17), or d_n u = g on Gamma when bc == "neumann" (Eq. 3.19,
+        u = Y f - V psi of Eq. 3.20; the density is then psi)."""
         dom = self.dom
         Ft = np.where(self.mask, -F, 0.0)
-        b = np.asarray(g) - apply_operator(dom, kappa, np.zeros(dom.nb, dtype=Ft.dtype), Ft)
+        op = apply_neumann if self.bc == "neumann" else apply_operator
+        b = np.asarray(g) - op(dom, kappa, np.zeros(dom.nb, dtype=Ft.dtype), Ft)
         x0 = self.phi if self.phi is not None else np.zeros(dom.nb, dtype=b.dtype)
-        A = lambda v: apply_operator(dom, kappa, v)
+        A = lambda v: op(dom, kappa, v)
         if self.solver == "richardson":
             phi, it, res, ok = richardson(A, b, x0, self.gamma, self.tol, self.maxit)
         else:
@@ -64,7 +69,10 @@ class _Base:
             raise RuntimeError("%s did not converge (res %.3e)" % (self.solver, res))
         self.phi = phi
         self.iters.append(it)
-        _, U = interface_solve(dom, kappa, phi, Ft)
+        if self.bc == "neumann":
+            _, U = interface_solve(dom, kappa, np.zeros(dom.nb, dtype=phi.dtype), Ft, phi)
+        else:
+            _, U = interface_solve(dom, kappa, phi, Ft)
         return U
 
 

@@ -1487,14 +1487,6 @@ extern "C" kfbi_status kfbi_solve_density(kfbi_domain* dom, double kappa_re, dou
 // ---- Neumann BVP (Eqs. 3.19, 3.20) ------------------------------------------
 
 namespace {
-// Switches the domain's operator to psi -> d_n u+ for the lifetime of a
-// Neumann entry point.
-struct NeumannScope {
-  kfbi_domain* D;
-  explicit NeumannScope(kfbi_domain* d) : D(d) { D->neumann = true; }
-  ~NeumannScope() { D->neumann = false; }
-};
-
 kfbi_status neumann_check(kfbi_domain* dom) {
   if (dom->desc.precision != KFBI_FP64) {
     dom->err = "the Neumann operator runs on KFBI_FP64 domains";

@@ -272,6 +272,7 @@ struct kfbi_state {
   double dt = 0, theta = 0.25, kre = 0, kim = 0;
   bool initialised = false;
   bool phi_zero = true;
+  bool neumann = false;  // boundary data are d_n u (Eq. 3.19), the density is psi
   double* d_u = nullptr;      // current field, padded planes
   double* d_F = nullptr;      // F^{n+1} (heat, wave) or u* (Schroedinger)
   double* d_Fprev = nullptr;  // F^n (wave)
@@ -303,6 +304,19 @@ void correct_fp64(kfbi_domain* D, double kre, double kim, const double* phi, int
                   const double* ft, cudaStream_t st);
 void extract_fp64(kfbi_domain* D, double kre, double kim, const double* phi, int ps,
                   const double* ft, double* out, int os, cudaStream_t st);
+// Switches a domain's operator to psi -> d_n u+ (the Neumann BIE of
+// Eq. 3.19) for its lifetime when `on`.
+struct NeumannScope {
+  kfbi_domain* D;
+  bool on;
+  explicit NeumannScope(kfbi_domain* d, bool o = true) : D(d), on(o) {
+    if (on) D->neumann = true;
+  }
+  ~NeumannScope() {
+    if (on) D->neumann = false;
+  }
+};
+
 // Run f (returning kfbi_status); convert exceptions into a status and keep
 // the message on the domain (or globally when D is null).
 template <class F>

@@ -198,6 +198,9 @@ __global__ void k_add_grid(double* __restrict__ U, const double* __restrict__ uf
 
 static kfbi_status solve_step(kfbi_domain* D, kfbi_state* S, const double* g, bool gC,
                               kfbi_solve_info* info, cudaStream_t st) {
+  // Neumann states: every application below is psi -> d_n u+ and the final
+  // grid is u = Y f - V psi (Eq. 3.20)
+  NeumannScope ns(D, S->neumann);
   const int nb = D->nb;
   const size_t pl = (size_t)S->planes * D->Mp * D->Mp;
   apply_accurate(D, S->kre, S->kim, D->d_zero_nb, 2, S->d_ft, S->d_ub, 2, st);
@@ -446,6 +449,22 @@ kfbi_status kfbi_step_schrodinger(kfbi_domain* dom, kfbi_state* S, const double*
                 S->d_aux, dom->Mp);
     KFBI_CHECK_LAUNCH();
     KFBI_CUDA(cudaStreamSynchronize(st));
+    return KFBI_OK;
+  });
+}
+
+kfbi_status kfbi_state_set_neumann(kfbi_state* S, int neumann) {
+  if (!S || !S->dom) return KFBI_ERR_ARG;
+  if (neumann && S->dom->desc.precision != KFBI_FP64) {
+    S->dom->err = "Neumann boundary data need a KFBI_FP64 domain";
+    return KFBI_ERR_UNSUPPORTED;
+  }
+  return guarded(S->dom, [&]() -> kfbi_status {
+    S->neumann = neumann != 0;
+    // the density changes meaning: start the next solve from zero
+    KFBI_CUDA(cudaMemset(S->d_phi, 0, 2 * (size_t)S->dom->nb * sizeof(double)));
+    S->phi_zero = true;
+    S->ax_valid = false;
     return KFBI_OK;
   });
 }

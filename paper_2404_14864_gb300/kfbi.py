@@ -120,6 +120,7 @@ def lib():
         "kfbi_solve_neumann": (S, [_VP, ctypes.c_double, ctypes.c_double, _VP, _VP, _VP, _VP,
                                    ctypes.POINTER(SolveInfo), _VP]),
         "kfbi_state_create": (S, [_VP, ctypes.c_int, ctypes.POINTER(_VP)]),
+        "kfbi_state_set_neumann": (S, [_VP, ctypes.c_int]),
         "kfbi_state_destroy": (None, [_VP]),
         "kfbi_state_init_heat": (S, [_VP, ctypes.c_double, _VP, _VP, _VP, _VP]),
         "kfbi_state_init_wave": (S, [_VP, ctypes.c_double, ctypes.c_double, _VP, _VP, _VP, _VP, _VP]),
@@ -428,6 +429,10 @@ class State:
         _check(lib().kfbi_step_schrodinger(self.dom.h, self.h, _ptr(v), float(w), _ptr(g_next),
                                            ctypes.byref(info), _stream(stream)), self.dom.h)
         return info.as_dict()
+
+    def set_neumann(self, on=True):
+        """Steps take Neumann data d_n u = g (float64 domains)."""
+        _check(lib().kfbi_state_set_neumann(self.h, 1 if on else 0), self.dom.h)
 
     def get_u(self, out=None, stream=None):
         import torch

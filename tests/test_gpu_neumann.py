@@ -145,3 +145,47 @@ def test_neumann_on_mixed_domains_is_refused(prec):
         dom.apply_neumann(10.0, psi)
     assert e.value.status == 8
     dom.close()
+
+
+def _heat_neumann_data(M):
+    """The paper's Neumann heat solution (Sec. 4, Ex. 2):
+    u = exp(-t) sin(0.6 x + 0.8 y), u_t = Delta u, on a star in
+    [-1.5, 1.5]^2, tau = 16 / M (its Table 2 steps)."""
+    desc = W.domain_desc(M, W.star(1.0, 0.2, 5), lo=-1.5, hi=1.5)
+    d = oracle.make_domain(desc)
+    X, Y = W.grid_xy(desc)
+    t1, t2, _, _ = oracle.interface.tangent_data(d, d.theta)
+    u = lambda t: math.exp(-t) * np.sin(0.6 * X + 0.8 * Y)
+    gN = lambda t: math.exp(-t) * np.cos(0.6 * d.zx + 0.8 * d.zy) * (0.6 * t2 - 0.8 * t1)
+    return desc, d, u, gN, 16.0 / M
+
+
+@pytest.mark.parametrize("M", [64, 128])
+def test_neumann_heat_steps_match_oracle(M):
+    desc, d, u, gN, tau = _heat_neumann_data(M)
+    dom = kfbi.Domain(desc, kfbi.KFBI_FP64, tol=1e-12, maxit=500)
+    st = kfbi.State(dom, kfbi.KFBI_HEAT)
+    st.set_neumann(True)
+    st.init_heat(tau, dev(u(0)), dev(-u(0)))
+    orc = oracle.HeatStepper(d, tau, 1e-12, bc="neumann")
+    orc.init(u(0), -u(0))
+    m = d.interior_inside()
+    n = int(round(1.0 / tau))
+    for k in range(n):
+        info = st.step_heat(dev(gN((k + 1) * tau)))
+        U = orc.step(gN((k + 1) * tau))
+        assert info["converged"]
+        assert rel_linf(host(st.get_u())[m], U[m]) <= 1e-10, k
+    e = np.abs(host(st.get_u()) - u(n * tau))[m].max()
+    assert e <= 1.01 * np.abs(U - u(n * tau))[m].max() + 1e-12
+    dom.close()
+
+
+def test_neumann_state_on_mixed_domain_is_refused():
+    desc = W.domain_desc(64, W.star())
+    dom = kfbi.Domain(desc, kfbi.KFBI_MIXED_FFT32)
+    st = kfbi.State(dom, kfbi.KFBI_HEAT)
+    with pytest.raises(kfbi.KfbiError) as e:
+        st.set_neumann(True)
+    assert e.value.status == 8
+    dom.close()
