@@ -162,10 +162,10 @@ kfbi_status kfbi_solve_density(kfbi_domain* dom, double kappa_re, double kappa_i
 
 /* ---- Neumann BVP (Eqs. 3.19, 3.20, 3.22) ---------------------------------
  * Delta u - kappa u = f in Omega, d_n u = g_N on Gamma (n the outward
- * normal).  Float64 domains only: other precisions return
- * KFBI_ERR_UNSUPPORTED.  The box condition is u = 0 on the box (the Green's
- * function of the Dirichlet box; the solution in Omega does not depend on
- * that choice). */
+ * normal), on domains of every precision (mixed domains iterate with the
+ * fast operator and refine with the float64 one, as for Dirichlet data).
+ * The box condition is u = 0 on the box (the Green's function of the
+ * Dirichlet box; the solution in Omega does not depend on that choice). */
 
 /* out_dev[k] = d_n u+(z_k): interior normal derivative at boundary node k of
  * the solution of the interface problem (Eq. 3.30) with [u] = 0,
@@ -254,9 +254,8 @@ kfbi_status kfbi_step_schrodinger(kfbi_domain* dom, kfbi_state* st, const double
 /* Boundary condition of the state's steps: neumann = 0 (default) takes
  * g_next as Dirichlet data u = g (Eq. 3.17), neumann = 1 as Neumann data
  * d_n u = g with the outward normal (Eq. 3.19; the density is then psi and
- * u = Y f - V psi, Eq. 3.20).  Resets the density to zero.  Neumann needs a
- * KFBI_FP64 domain (else KFBI_ERR_UNSUPPORTED); batches and the server take
- * Dirichlet states only. */
+ * u = Y f - V psi, Eq. 3.20).  Resets the density to zero.  Batches and
+ * the server take Dirichlet states only (KFBI_ERR_ARG). */
 kfbi_status kfbi_state_set_neumann(kfbi_state* st, int neumann);
 
 /* Copy the current field u^n (all (M-1)^2 nodes; values outside Omega are

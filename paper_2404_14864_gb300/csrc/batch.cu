@@ -1615,6 +1615,10 @@ kfbi_status batch_step(kfbi_batch* B, kfbi_state* const* states, const void* con
       B->err = "state i must be initialised on domain i and g_next[i] given";
       return KFBI_ERR_ARG;
     }
+    if (states[i]->neumann) {
+      B->err = "batches step Dirichlet states only";
+      return KFBI_ERR_ARG;
+    }
     if (states[i]->eq == KFBI_SCHRODINGER && (!src_or_v || !src_or_v[i])) {
       B->err = "Schroedinger instances need the potential v in src_or_v[i]";
       return KFBI_ERR_ARG;

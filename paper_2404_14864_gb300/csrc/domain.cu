@@ -288,7 +288,8 @@ static void free_domain(kfbi_domain* D) {
                   D->d_arm_beta32, D->d_arm_fcoef32, D->d_node_w32, D->d_node_a32,
                   D->d_node_b32, D->d_node_fcoef32, D->d_R, D->d_T, D->d_U,
                   D->d_fpad, D->d_zero_nb, D->d_arm_delta, D->d_node_wn, D->d_node_e,
-                  D->d_node_fcoef_n};
+                  D->d_node_fcoef_n, D->d_arm_delta32, D->d_node_wn32, D->d_node_e32,
+                  D->d_node_fcoef_n32, D->d_zero_arm32, D->d_zero_node32};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete D;
@@ -342,11 +343,21 @@ static void upload_domain(kfbi_domain* D, const Plan& P) {
   D->d_node_b = dev_upload(D, nb_);
   D->d_node_fidx = dev_upload(D, to_padded(P.node_fidx, n1, Mp));
   D->d_node_fcoef = dev_upload(D, P.node_fcoef);
-  if (D->desc.precision == KFBI_FP64) {
-    D->d_arm_delta = dev_upload(D, transpose(P.arm_delta, na, 6));
-    D->d_node_wn = dev_upload(D, transpose(P.node_wn, nb, 6));
-    D->d_node_e = dev_upload(D, transpose(P.node_e, nb, 6));
-    D->d_node_fcoef_n = dev_upload(D, P.node_fcoef_n);
+  // Neumann tables (the refined applications of mixed domains use the FP64
+  // ones too)
+  std::vector<double> delta = transpose(P.arm_delta, na, 6), nwn = transpose(P.node_wn, nb, 6),
+                      ne = transpose(P.node_e, nb, 6);
+  D->d_arm_delta = dev_upload(D, delta);
+  D->d_node_wn = dev_upload(D, nwn);
+  D->d_node_e = dev_upload(D, ne);
+  D->d_node_fcoef_n = dev_upload(D, P.node_fcoef_n);
+  if (is_mixed(D->desc.precision)) {
+    D->d_arm_delta32 = dev_upload(D, to_f32(delta));
+    D->d_node_wn32 = dev_upload(D, to_f32(nwn));
+    D->d_node_e32 = dev_upload(D, to_f32(ne));
+    D->d_node_fcoef_n32 = dev_upload(D, to_f32(P.node_fcoef_n));
+    D->d_zero_arm32 = dev_upload(D, std::vector<float>(delta.size(), 0.f));
+    D->d_zero_node32 = dev_upload(D, std::vector<float>(ne.size(), 0.f));
   }
   if (is_mixed(D->desc.precision)) {
     D->d_arm_alpha32 = dev_upload(D, to_f32(alpha));
@@ -423,8 +434,6 @@ void extract_fp64(kfbi_domain* D, double kre, double kim, const double* phi, int
 
 void apply_internal(kfbi_domain* D, double kre, double kim, const double* phi, int ps,
                     const double* ft, double* out, int os, bool want_grid, cudaStream_t st) {
-  if (D->tc && D->neumann)
-    throw Status{KFBI_ERR_UNSUPPORTED, "the Neumann operator runs on KFBI_FP64 domains"};
   if (D->tc) {
     tc_apply(D, kre, kim, phi, ps, ft, out, os, want_grid, st);
     return;
@@ -510,9 +519,11 @@ long long domain_bytes_for(const Plan& P) {
                       3 * n1(P.node_w.size()) + n1(P.node_fcoef.size());
   b += sizeof(double) * dtab;
   if (mixed) b += sizeof(float) * dtab;
-  if (P.desc.precision == KFBI_FP64)  // Neumann tables
-    b += sizeof(double) * (n1(P.arm_delta.size()) + 2 * n1(P.node_wn.size()) +
-                           n1(P.node_fcoef_n.size()));
+  // Neumann tables: FP64 always; FP32 copies and two zero tables if mixed
+  const size_t ntab = n1(P.arm_delta.size()) + 2 * n1(P.node_wn.size()) +
+                      n1(P.node_fcoef_n.size());
+  b += sizeof(double) * ntab;
+  if (mixed) b += sizeof(float) * (ntab + n1(P.arm_delta.size()) + n1(P.node_wn.size()));
   b += sizeof(double) * (2 * plane * (mixed ? 3 : 4) + 2 * (size_t)P.nb);   // R, (T), U, fpad, zero_nb
   long long total = (long long)b + gmres_bytes(P.desc.gmres_restart, P.nb);
   if (mixed) total += tc_bytes_for(P, Mp);

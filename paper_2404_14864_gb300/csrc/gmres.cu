@@ -1486,15 +1486,6 @@ extern "C" kfbi_status kfbi_solve_density(kfbi_domain* dom, double kappa_re, dou
 
 // ---- Neumann BVP (Eqs. 3.19, 3.20) ------------------------------------------
 
-namespace {
-kfbi_status neumann_check(kfbi_domain* dom) {
-  if (dom->desc.precision != KFBI_FP64) {
-    dom->err = "the Neumann operator runs on KFBI_FP64 domains";
-    return KFBI_ERR_UNSUPPORTED;
-  }
-  return KFBI_OK;
-}
-}  // namespace
 
 extern "C" kfbi_status kfbi_apply_neumann(kfbi_domain* dom, double kappa_re, double kappa_im,
                                           const void* psi_dev, const void* f_dev, void* out_dev,
@@ -1504,8 +1495,6 @@ extern "C" kfbi_status kfbi_apply_neumann(kfbi_domain* dom, double kappa_re, dou
     dom->err = "psi_dev and out_dev must be device pointers";
     return KFBI_ERR_ARG;
   }
-  kfbi_status c = neumann_check(dom);
-  if (c != KFBI_OK) return c;
   return guarded(dom, [&]() -> kfbi_status {
     NeumannScope ns(dom);
     cudaStream_t st = (cudaStream_t)stream;
@@ -1530,8 +1519,6 @@ extern "C" kfbi_status kfbi_solve_neumann(kfbi_domain* dom, double kappa_re, dou
     dom->err = "gn_dev and psi_dev must be device pointers";
     return KFBI_ERR_ARG;
   }
-  kfbi_status c = neumann_check(dom);
-  if (c != KFBI_OK) return c;
   return guarded(dom, [&]() -> kfbi_status {
     NeumannScope ns(dom);
     cudaStream_t st = (cudaStream_t)stream;
@@ -1544,19 +1531,20 @@ extern "C" kfbi_status kfbi_solve_neumann(kfbi_domain* dom, double kappa_re, dou
     KFBI_LAUNCH(k_to_cplx, (nb + 255) / 256, 256, 0, st, (const double*)gn_dev, dom->d_B, nb, C);
     KFBI_LAUNCH(k_to_cplx, (nb + 255) / 256, 256, 0, st, (const double*)psi_dev, dom->d_X, nb, C);
     KFBI_CHECK_LAUNCH();
-    // b = g_N - d_n (Y f)+ : the known term of Eq. 3.19
-    const double* b = dom->d_B;
+    // b = g_N - d_n (Y f)+ : the known term of Eq. 3.19, left in d_B (the
+    // refinement of mixed domains uses d_Rv and d_Dv as work space)
     if (ft) {
-      apply_internal(dom, kappa_re, kappa_im, dom->d_zero_nb, 2, ft, dom->d_Dv, 2, false, st);
+      apply_accurate(dom, kappa_re, kappa_im, dom->d_zero_nb, 2, ft, dom->d_Dv, 2, st);
       KFBI_LAUNCH_P(KFBI_PROF_KRYLOV, k_residual, 1, kThreads, 0, st, (const double2*)dom->d_B,
                     (const double2*)dom->d_Dv, (double2*)dom->d_Rv, nb, dom->d_scal);
       KFBI_CHECK_LAUNCH();
-      b = dom->d_Rv;
+      KFBI_CUDA(cudaMemcpyAsync(dom->d_B, dom->d_Rv, 2 * (size_t)nb * sizeof(double),
+                                cudaMemcpyDeviceToDevice, st));
     }
-    kfbi_status s = gmres_solve(dom, kappa_re, kappa_im, b, dom->d_X, false, info, st);
+    kfbi_status s = gmres_solve(dom, kappa_re, kappa_im, dom->d_B, dom->d_X, false, info, st);
     if (u_grid_dev && s == KFBI_OK) {
       // u = Y f - V psi (Eq. 3.20): the interface solution with Psi = psi
-      apply_internal(dom, kappa_re, kappa_im, dom->d_X, 2, ft, nullptr, 2, true, st);
+      apply_accurate(dom, kappa_re, kappa_im, dom->d_X, 2, ft, nullptr, 2, st);
       unpad(dom, dom->d_U, (double*)u_grid_dev, C, st);
     }
     KFBI_LAUNCH(k_from_cplx, (nb + 255) / 256, 256, 0, st, dom->d_X, (double*)psi_dev, nb, C);

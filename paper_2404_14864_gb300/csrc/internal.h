@@ -214,6 +214,14 @@ struct kfbi_domain {
   double* d_node_wn = nullptr;
   double* d_node_e = nullptr;
   double* d_node_fcoef_n = nullptr;
+  // their FP32 copies on mixed domains, and zero tables standing in for the
+  // kappa weights (the psi terms have none)
+  float* d_arm_delta32 = nullptr;
+  float* d_node_wn32 = nullptr;
+  float* d_node_e32 = nullptr;
+  float* d_node_fcoef_n32 = nullptr;
+  float* d_zero_arm32 = nullptr;
+  float* d_zero_node32 = nullptr;
   // set while a Neumann entry point runs: the operator of apply_internal is
   // then psi -> d_n u+ (Phi = 0, Psi = psi) instead of phi -> u+
   bool neumann = false;

@@ -455,10 +455,6 @@ kfbi_status kfbi_step_schrodinger(kfbi_domain* dom, kfbi_state* S, const double*
 
 kfbi_status kfbi_state_set_neumann(kfbi_state* S, int neumann) {
   if (!S || !S->dom) return KFBI_ERR_ARG;
-  if (neumann && S->dom->desc.precision != KFBI_FP64) {
-    S->dom->err = "Neumann boundary data need a KFBI_FP64 domain";
-    return KFBI_ERR_UNSUPPORTED;
-  }
   return guarded(S->dom, [&]() -> kfbi_status {
     S->neumann = neumann != 0;
     // the density changes meaning: start the next solve from zero

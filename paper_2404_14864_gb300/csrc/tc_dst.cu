@@ -1157,9 +1157,14 @@ TcDst* tc_create(kfbi_domain* D, const Plan& P) {
     KFBI_CUDA(cudaMemset(T->T1sh, 0, 2 * plane * sizeof(float)));
     KFBI_CUDA(cudaMemset(T->T1sl, 0, 2 * plane * sizeof(float)));
     float** bufs[] = {&T->Rh, &T->Rl, &T->T1h, &T->T1l, &T->T2h, &T->T2l, &T->U};
-    for (float** b : bufs) alloc(b, 2 * plane);
-    KFBI_CUDA(cudaMemset(T->Rh, 0, 2 * plane * sizeof(float)));
-    KFBI_CUDA(cudaMemset(T->Rl, 0, 2 * plane * sizeof(float)));
+    // zeroed once: the FFT passes write only the M - 1 data rows of their
+    // output planes, and the last pass and the stencil gather contract over
+    // all Mp entries of a row, so the padding rows must hold zeros (not
+    // whatever an earlier allocation left in recycled memory)
+    for (float** b : bufs) {
+      alloc(b, 2 * plane);
+      KFBI_CUDA(cudaMemset(*b, 0, 2 * plane * sizeof(float)));
+    }
     T->rhs_sparse_planes = 2;
     T->err = (int*)(D->d_scal + 6);
     KFBI_CUDA(cudaMemset(T->err, 0, sizeof(int)));
@@ -1419,9 +1424,24 @@ static void tc_box_solve(kfbi_domain* D, double kre, double kim, int P, cudaStre
 // the third computes only the rows the stencil needs, and the last pass is a
 // gather fused with the extraction.  Same discrete operator as the dense
 // route; only zero terms and unread outputs are skipped.
+// FP32 correction and extraction tables of the operator in use: phi -> u+
+// (Dirichlet) or, while a Neumann entry point runs, psi -> d_n u+ with zero
+// kappa weights.
+struct Tab32 {
+  const float *al, *be, *w, *a, *b, *fc;
+};
+static Tab32 tables32(const kfbi_domain* D) {
+  if (D->neumann)
+    return {D->d_arm_delta32, D->d_zero_arm32, D->d_node_wn32, D->d_node_e32, D->d_zero_node32,
+            D->d_node_fcoef_n32};
+  return {D->d_arm_alpha32, D->d_arm_beta32, D->d_node_w32, D->d_node_a32, D->d_node_b32,
+          D->d_node_fcoef32};
+}
+
 static void tc_apply_sparse(kfbi_domain* D, double kre, double kim, const double* phi, int ps,
                             double* out, int os, cudaStream_t st) {
   TcDst* T = D->tc;
+  const Tab32 tb = tables32(D);
   const bool C = kim != 0.0;
   const int P = C ? 2 : 1;
   const int Mp = T->Mp;
@@ -1437,8 +1457,8 @@ static void tc_apply_sparse(kfbi_domain* D, double kre, double kim, const double
     sp.nrows = T->nrows;
     sp.arm_start = D->d_arm_start;
     sp.arm_k0 = D->d_arm_k0;
-    sp.alpha = D->d_arm_alpha32;
-    sp.beta = D->d_arm_beta32;
+    sp.alpha = tb.al;
+    sp.beta = tb.be;
     sp.n_arms = D->n_arms;
     sp.nb = D->nb;
     sp.phi = phi;
@@ -1455,11 +1475,11 @@ static void tc_apply_sparse(kfbi_domain* D, double kre, double kim, const double
     fft_pass(T, T->T2h, T->U, 0, 0.f, 0.f, P, T->stop, st);
     if (C)
       KFBI_LAUNCH_P(KFBI_PROF_EXTRACT, k_gather_extract<true>, D->nb, 32 * GE_WARPS, 0, st, T->U, T->S32, Mp,
-                    plane, D->d_node_gidx, D->d_node_w32, D->d_node_a32, D->d_node_b32, D->nb, phi,
+                    plane, D->d_node_gidx, tb.w, tb.a, tb.b, D->nb, phi,
                     ps, (float)kre, (float)kim, out, os, T->stop);
     else
       KFBI_LAUNCH_P(KFBI_PROF_EXTRACT, k_gather_extract<false>, D->nb, 32 * GE_WARPS, 0, st, T->U, T->S32, Mp,
-                    plane, D->d_node_gidx, D->d_node_w32, D->d_node_a32, D->d_node_b32, D->nb, phi,
+                    plane, D->d_node_gidx, tb.w, tb.a, tb.b, D->nb, phi,
                     ps, (float)kre, (float)kim, out, os, T->stop);
     KFBI_CHECK_LAUNCH();
     return;
@@ -1467,12 +1487,12 @@ static void tc_apply_sparse(kfbi_domain* D, double kre, double kim, const double
   if (C)
     KFBI_LAUNCH_P(KFBI_PROF_CORRECT, k_correct32<true>, (D->n_irr + 127) / 128, 128, 0, st, T->Rh,
                   T->Rl, plane, nullptr, D->d_irr_off, D->d_arm_start, D->d_arm_k0,
-                  D->d_arm_alpha32, D->d_arm_beta32, D->d_arm_fidx, D->d_arm_fcoef32, D->n_irr,
+                  tb.al, tb.be, D->d_arm_fidx, D->d_arm_fcoef32, D->n_irr,
                   D->n_arms, D->nb, phi, ps, (float)kre, (float)kim, T->rv, T->stop);
   else
     KFBI_LAUNCH_P(KFBI_PROF_CORRECT, k_correct32<false>, (D->n_irr + 127) / 128, 128, 0, st, T->Rh,
                   T->Rl, plane, nullptr, D->d_irr_off, D->d_arm_start, D->d_arm_k0,
-                  D->d_arm_alpha32, D->d_arm_beta32, D->d_arm_fidx, D->d_arm_fcoef32, D->n_irr,
+                  tb.al, tb.be, D->d_arm_fidx, D->d_arm_fcoef32, D->n_irr,
                   D->n_arms, D->nb, phi, ps, (float)kre, (float)kim, T->rv, T->stop);
   KFBI_LAUNCH_P(KFBI_PROF_SPARSE, k_sparse_p1, dim3(Mp / 32, (T->nrows + 31) / 32), dim3(32, 8), 0, st,
                 T->rv, D->n_irr, T->row_start, T->node_col, T->rmin, T->nrows, T->S32, T->T1sh,
@@ -1491,11 +1511,11 @@ static void tc_apply_sparse(kfbi_domain* D, double kre, double kim, const double
   launch_pass(T, d3, st);
   if (C)
     KFBI_LAUNCH_P(KFBI_PROF_EXTRACT, k_gather_extract<true>, D->nb, 32 * GE_WARPS, 0, st, T->U, T->S32, Mp,
-                  plane, D->d_node_gidx, D->d_node_w32, D->d_node_a32, D->d_node_b32, D->nb, phi,
+                  plane, D->d_node_gidx, tb.w, tb.a, tb.b, D->nb, phi,
                   ps, (float)kre, (float)kim, out, os, T->stop);
   else
     KFBI_LAUNCH_P(KFBI_PROF_EXTRACT, k_gather_extract<false>, D->nb, 32 * GE_WARPS, 0, st, T->U, T->S32, Mp,
-                  plane, D->d_node_gidx, D->d_node_w32, D->d_node_a32, D->d_node_b32, D->nb, phi,
+                  plane, D->d_node_gidx, tb.w, tb.a, tb.b, D->nb, phi,
                   ps, (float)kre, (float)kim, out, os, T->stop);
   KFBI_CHECK_LAUNCH();
 }
@@ -1503,6 +1523,7 @@ static void tc_apply_sparse(kfbi_domain* D, double kre, double kim, const double
 void tc_apply(kfbi_domain* D, double kre, double kim, const double* phi, int ps, const double* ft,
               double* out, int os, bool want_grid, cudaStream_t st) {
   TcDst* T = D->tc;
+  const Tab32 tb = tables32(D);
   if (!ft && !want_grid && out && D->n_irr > 0) {
     tc_apply_sparse(D, kre, kim, phi, ps, out, os, st);
     return;
@@ -1524,25 +1545,25 @@ void tc_apply(kfbi_domain* D, double kre, double kim, const double* phi, int ps,
     if (C)
       KFBI_LAUNCH_P(KFBI_PROF_CORRECT, k_correct32<true>, (D->n_irr + 127) / 128, 128, 0, st,
                     T->Rh, T->fft ? nullptr : T->Rl, plane, ft, D->d_irr_off, D->d_arm_start, D->d_arm_k0,
-                    D->d_arm_alpha32, D->d_arm_beta32, D->d_arm_fidx, D->d_arm_fcoef32,
+                    tb.al, tb.be, D->d_arm_fidx, D->d_arm_fcoef32,
                     D->n_irr, D->n_arms, D->nb, phi, ps, (float)kre, (float)kim, nullptr, nullptr);
     else
       KFBI_LAUNCH_P(KFBI_PROF_CORRECT, k_correct32<false>, (D->n_irr + 127) / 128, 128, 0, st,
                     T->Rh, T->fft ? nullptr : T->Rl, plane, ft, D->d_irr_off, D->d_arm_start, D->d_arm_k0,
-                    D->d_arm_alpha32, D->d_arm_beta32, D->d_arm_fidx, D->d_arm_fcoef32,
+                    tb.al, tb.be, D->d_arm_fidx, D->d_arm_fcoef32,
                     D->n_irr, D->n_arms, D->nb, phi, ps, (float)kre, (float)kim, nullptr, nullptr);
   }
   tc_box_solve(D, kre, kim, P, st);
   if (out) {
     if (C)
       KFBI_LAUNCH_P(KFBI_PROF_EXTRACT, k_extract32<true>, (D->nb + 127) / 128, 128, 0, st, T->U,
-                    plane, ft, D->d_node_gidx, D->d_node_w32, D->d_node_a32, D->d_node_b32,
-                    D->d_node_fidx, D->d_node_fcoef32, D->nb, phi, ps, (float)kre, (float)kim,
+                    plane, ft, D->d_node_gidx, tb.w, tb.a, tb.b,
+                    D->d_node_fidx, tb.fc, D->nb, phi, ps, (float)kre, (float)kim,
                     out, os);
     else
       KFBI_LAUNCH_P(KFBI_PROF_EXTRACT, k_extract32<false>, (D->nb + 127) / 128, 128, 0, st, T->U,
-                    plane, ft, D->d_node_gidx, D->d_node_w32, D->d_node_a32, D->d_node_b32,
-                    D->d_node_fidx, D->d_node_fcoef32, D->nb, phi, ps, (float)kre, (float)kim,
+                    plane, ft, D->d_node_gidx, tb.w, tb.a, tb.b,
+                    D->d_node_fidx, tb.fc, D->nb, phi, ps, (float)kre, (float)kim,
                     out, os);
   }
   if (want_grid)
@@ -1571,15 +1592,21 @@ void tc_apply_accurate(kfbi_domain* D, double kre, double kim, const double* phi
   KFBI_LAUNCH_P(KFBI_PROF_GRID, k_f32_to_f64, grid_for(P * plane, 256), 256, 0, st, T->U, D->d_U,
                 P * plane);
   const double inv_h2 = 1.0 / (D->h * D->h);
-  if (C)
-    KFBI_LAUNCH_P(KFBI_PROF_GRID, k_resid_split<true>, grid_for(plane, 256), 256, 0, st, D->d_R,
-                  D->d_U, T->Rh, T->fft ? nullptr : T->Rl, Mp, T->n1, inv_h2, kre, kim);
-  else
-    KFBI_LAUNCH_P(KFBI_PROF_GRID, k_resid_split<false>, grid_for(plane, 256), 256, 0, st, D->d_R,
-                  D->d_U, T->Rh, T->fft ? nullptr : T->Rl, Mp, T->n1, inv_h2, kre, kim);
-  tc_box_solve(D, kre, kim, P, st);
-  KFBI_LAUNCH_P(KFBI_PROF_GRID, k_add_f32, grid_for(P * plane, 256), 256, 0, st, D->d_U, T->U,
-                P * plane);
+  // one refinement sweep leaves a relative grid error ~delta^2; the normal
+  // derivative of the Neumann operator amplifies grid errors by O(1/h), so
+  // its applications take a second sweep
+  const int sweeps = D->neumann ? 2 : 1;
+  for (int sw = 0; sw < sweeps; ++sw) {
+    if (C)
+      KFBI_LAUNCH_P(KFBI_PROF_GRID, k_resid_split<true>, grid_for(plane, 256), 256, 0, st, D->d_R,
+                    D->d_U, T->Rh, T->fft ? nullptr : T->Rl, Mp, T->n1, inv_h2, kre, kim);
+    else
+      KFBI_LAUNCH_P(KFBI_PROF_GRID, k_resid_split<false>, grid_for(plane, 256), 256, 0, st, D->d_R,
+                    D->d_U, T->Rh, T->fft ? nullptr : T->Rl, Mp, T->n1, inv_h2, kre, kim);
+    tc_box_solve(D, kre, kim, P, st);
+    KFBI_LAUNCH_P(KFBI_PROF_GRID, k_add_f32, grid_for(P * plane, 256), 256, 0, st, D->d_U, T->U,
+                  P * plane);
+  }
   if (out) extract_fp64(D, kre, kim, phi, ps, ft, out, os, st);
   KFBI_CHECK_LAUNCH();
 }
