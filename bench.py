@@ -26,6 +26,8 @@ import sys
 import threading
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -71,9 +73,10 @@ def parse():
     ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--cpu-steps", type=int, default=2)
     ap.add_argument("--workload", default="wave1024",
-                    choices=["wave1024", "nls1024", "batched", "served"],
-                    help="wave1024: theta = 1/4 wave (headline); nls1024: the paper's nonlinear "
-                         "Schroedinger example (w = 1) at --M; batched, served: configs 4, 5")
+                    choices=["wave1024", "heat1024-neumann", "nls1024", "batched", "served"],
+                    help="wave1024: theta = 1/4 wave (headline); heat1024-neumann: the paper's "
+                         "Neumann heat example at --M; nls1024: its nonlinear Schroedinger "
+                         "example (w = 1) at --M; batched, served: configs 4, 5")
     ap.add_argument("--batch", type=int, default=256)
     ap.add_argument("--requests", type=int, default=200)
     ap.add_argument("--max-resident", type=int, default=64)
@@ -192,8 +195,69 @@ class NlsProblem:
                 "box": [self.desc["lo"], self.desc["hi"]]}
 
 
+class HeatNeumannProblem:
+    """The paper's Neumann heat example (Sec. 4, Ex. 2) at grid M:
+    u = exp(-t) sin(0.6 x + 0.8 y), u_t = Delta u, d_n u given on Gamma, on
+    the star r = 1 + 0.2 sin 5 theta in [-1.5, 1.5]^2 (its heart curve is a
+    spline), N_b = M, dt = 16 / M (the time steps of its Table 2)."""
+
+    kind = "heat-neumann"
+    cplx = False
+
+    def __init__(self, M):
+        from paper_2404_14864_gb300 import workloads as W
+        self.M = M
+        self.desc = W.domain_desc(M, W.star(1.0, 0.2, 5), lo=-1.5, hi=1.5)
+        self.dt = 16.0 / M
+        self.X, self.Y = W.grid_xy(self.desc)
+        self.zx, self.zy = W.boundary_xy(self.desc)
+        self.nx, self.ny = W.boundary_normal(self.desc)
+
+    def equation(self, kfbi):
+        return kfbi.KFBI_HEAT
+
+    def _u(self, t):
+        return math.exp(-t) * np.sin(0.6 * self.X + 0.8 * self.Y)
+
+    def g(self, k):
+        t = (k + 1) * self.dt
+        c = math.exp(-t) * np.cos(0.6 * self.zx + 0.8 * self.zy)
+        return c * (0.6 * self.nx + 0.8 * self.ny)
+
+    def exact(self, n):
+        return self._u(n * self.dt)
+
+    def init(self, st, cu):
+        st.set_neumann(True)
+        st.init_heat(self.dt, cu(self._u(0.0)), cu(-self._u(0.0)))
+
+    def step(self, st, g_dev):
+        return st.step_heat(g_dev)
+
+    def oracle_stepper(self, oracle, d):
+        st = oracle.HeatStepper(d, self.dt, 1e-10, bc="neumann")
+        st.init(self._u(0.0), -self._u(0.0))
+        return st
+
+    def oracle_step(self, st, k):
+        st.step(self.g(k))
+
+    def config(self, precision, solver="gmres", gamma=0.5):
+        sv = ("gmres restart 50, tol 1e-10" if solver == "gmres"
+              else "richardson gamma %g, tol 1e-10" % gamma)
+        return {"workload": "heat-neumann-star-%d" % self.M, "M": self.M,
+                "unknowns": (self.M - 1) ** 2, "n_boundary": self.desc["nb"], "dt": "16/M",
+                "boundary": "neumann (Eq. 3.19)", "solver": sv, "precision": precision,
+                "l2": "flushed between timed steps (256 MiB write)",
+                "box": [self.desc["lo"], self.desc["hi"]]}
+
+
 def make_problem(args):
-    return NlsProblem(args.M) if args.workload == "nls1024" else WaveProblem(args.M)
+    if args.workload == "nls1024":
+        return NlsProblem(args.M)
+    if args.workload == "heat1024-neumann":
+        return HeatNeumannProblem(args.M)
+    return WaveProblem(args.M)
 
 
 def config(M, desc, dt, precision, solver="gmres", gamma=0.5):

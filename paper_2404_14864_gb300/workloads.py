@@ -65,6 +65,24 @@ def boundary_xy(desc):
     return c["cx"] + ca * u - sa * v, c["cy"] + sa * u + ca * v
 
 
+def boundary_normal(desc):
+    """Outward unit normal (n_x, n_y) = (y', -x') / |z'| at the boundary nodes
+    (the curves run counter-clockwise), for Neumann data d_n u = grad u . n."""
+    c = desc["curve"]
+    t = (2.0 * math.pi / desc["nb"]) * np.arange(desc["nb"])
+    if c["kind"] == "polar":
+        r = c["r0"] + c["eps"] * np.sin(c["k"] * t + c["phase"])
+        dr = c["eps"] * c["k"] * np.cos(c["k"] * t + c["phase"])
+        dx = dr * np.cos(t) - r * np.sin(t)
+        dy = dr * np.sin(t) + r * np.cos(t)
+    else:
+        ca, sa = math.cos(c["alpha"]), math.sin(c["alpha"])
+        du, dv = -c["a"] * np.sin(t), c["b"] * np.cos(t)
+        dx, dy = ca * du - sa * dv, sa * du + ca * dv
+    s = np.hypot(dx, dy)
+    return dy / s, -dx / s
+
+
 # ----------------------------------------------------------------------------
 # Manufactured solutions (value, Laplacian, source)
 # ----------------------------------------------------------------------------
@@ -88,6 +106,11 @@ class WaveExact:
 
     def u(self, x, y, t):
         return math.cos(SQRT2PI * t) * np.sin(math.pi * x) * np.sin(math.pi * y)
+
+    def grad(self, x, y, t):
+        c = math.cos(SQRT2PI * t) * math.pi
+        return (c * np.cos(math.pi * x) * np.sin(math.pi * y),
+                c * np.sin(math.pi * x) * np.cos(math.pi * y))
 
     def lap(self, x, y, t):
         return -2.0 * math.pi ** 2 * self.u(x, y, t)
