@@ -122,7 +122,7 @@ __global__ void __launch_bounds__(32 * RPB) k_dst_fft(const float* __restrict__ 
                                                       const float2* __restrict__ tw2M, int mode,
                                                       const float* __restrict__ lam, float kre,
                                                       float scale, const double* stop,
-                                                      const FftSparseRhs sp) {
+                                                      const FftSparseRhs sp, int r_lo, int bpp) {
   constexpr int M = 32 * N1;
   constexpr int T = 32 * RPB;  // threads
   extern __shared__ float4 smem4[];
@@ -162,8 +162,10 @@ __global__ void __launch_bounds__(32 * RPB) k_dst_fft(const float* __restrict__ 
   }
   KFBI_PDL_ENTRY();
   KFBI_STOP_RETURN(stop);
-  const int row0 = blockIdx.x * RPB;  // first row over all planes
-  const int p = row0 / Mp, rr0 = row0 - p * Mp;
+  // bpp blocks per plane cover rows r_lo .. r_lo + bpp RPB - 1 of each plane
+  const int p = blockIdx.x / bpp;
+  const int rr0 = r_lo + (blockIdx.x - p * bpp) * RPB;
+  const int row0 = p * Mp + rr0;  // first row over all planes
   if constexpr (SPARSE) {
     float* xrow = reinterpret_cast<float*>(s_ex + (size_t)warp * N1 * 33);
 #pragma unroll
@@ -304,14 +306,23 @@ static void launch_n1(const float* in, float* out, int Mp, int n1, const float2*
                       const float2* twB, const float2* tw2M, int mode, const float* lam, float kre,
                       float scale, int P, const double* stop, cudaStream_t st,
                       const FftSparseRhs* sp) {
-  const int blocks = P * Mp / RPB;
-  const double fl = fft_pass_flops(32 * N1, P * Mp);
-  if (sp)
-    KFBI_LAUNCH_PW(KFBI_PROF_DST, fl, (k_dst_fft<N1, true>), blocks, 32 * RPB, smem_bytes(32 * N1),
-                   st, in, out, Mp, n1, twM, twB, tw2M, mode, lam, kre, scale, stop, *sp);
+  // a sparse first pass transforms only the rows that can hold irregular
+  // nodes (whole RPB groups); the output columns of the other rows are zero
+  // in its dedicated buffer and stay so
+  int r_lo = 0, bpp = Mp / RPB;
+  if (sp) {
+    r_lo = sp->rmin / RPB * RPB;
+    bpp = (sp->rmin + sp->nrows - r_lo + RPB - 1) / RPB;
+  }
+  const int blocks = P * bpp;
+  const double fl = fft_pass_flops(32 * N1, blocks * RPB);
+  if (sp)  // timed with the sparse first passes, not the dense DST passes
+    KFBI_LAUNCH_PW(KFBI_PROF_SPARSE, fl, (k_dst_fft<N1, true>), blocks, 32 * RPB, smem_bytes(32 * N1),
+                   st, in, out, Mp, n1, twM, twB, tw2M, mode, lam, kre, scale, stop, *sp, r_lo, bpp);
   else
     KFBI_LAUNCH_PW(KFBI_PROF_DST, fl, (k_dst_fft<N1, false>), blocks, 32 * RPB, smem_bytes(32 * N1),
-                   st, in, out, Mp, n1, twM, twB, tw2M, mode, lam, kre, scale, stop, FftSparseRhs{});
+                   st, in, out, Mp, n1, twM, twB, tw2M, mode, lam, kre, scale, stop, FftSparseRhs{},
+                   r_lo, bpp);
 }
 
 }  // namespace ff

@@ -1467,8 +1467,11 @@ static void tc_apply_sparse(kfbi_domain* D, double kre, double kim, const double
     sp.kim = (float)kim;
     sp.cplx = C ? 1 : 0;
     const float scale = (float)((2.0 / D->M) * (2.0 / D->M));
-    fft_pass(T, nullptr, T->T1h, 0, 0.f, 0.f, P, T->stop, st, &sp);
-    fft_pass(T, T->T1h, T->T2h, C ? 0 : 1, (float)kre, scale, P, T->stop, st);
+    // the first pass writes only the columns of the irregular rows; T1sh
+    // (zeroed at creation, written by nothing else on an FFT domain) keeps
+    // zeros in the others
+    fft_pass(T, nullptr, T->T1sh, 0, 0.f, 0.f, P, T->stop, st, &sp);
+    fft_pass(T, T->T1sh, T->T2h, C ? 0 : 1, (float)kre, scale, P, T->stop, st);
     if (C)
       KFBI_LAUNCH_P(KFBI_PROF_GRID, k_eig_cplx32, T->n1, 256, 0, st, T->T2h, (float*)nullptr, plane,
                     Mp, T->n1, T->lam, (float)kre, (float)kim, scale, T->stop);
