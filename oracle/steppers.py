@@ -7,7 +7,7 @@ the boundary integral equation of Eq. 3.17:
 
   b = g - u+[phi = 0, f-tilde]          (Y f at the boundary nodes)
   (1/2 I + W) phi = b                    (GMRES, or the Richardson iteration
-                                          of Eq. 3.21; phi_0 = previous phi)
+                                          of Eq. 3.21; phi_0 = 2 phi^n - phi^(n-1))
   U = interface solution for (f-tilde, phi), u^{n+1} = U on Omega nodes.
 
 The right-hand side F is carried as its own variable (Eqs. 3.4 and the
@@ -49,6 +49,7 @@ class _Base:
         self.bc = bc
         self.mask = dom.interior_inside()
         self.phi = None
+        self.phi_prev = None
         self.iters = []
 
     def _solve(self, kappa, F, g):
@@ -59,7 +60,16 @@ class _Base:
         Ft = np.where(self.mask, -F, 0.0)
         op = apply_neumann if self.bc == "neumann" else apply_operator
         b = np.asarray(g) - op(dom, kappa, np.zeros(dom.nb, dtype=Ft.dtype), Ft)
-        x0 = self.phi if self.phi is not None else np.zeros(dom.nb, dtype=b.dtype)
+        # initial density: zero, the previous density, then the linear
+        # extrapolation in time 2 phi^n - phi^(n-1) (the paper leaves the
+        # initial value open)
+        if self.phi is None:
+            x0 = np.zeros(dom.nb, dtype=b.dtype)
+        elif self.phi_prev is None:
+            x0 = self.phi
+        else:
+            x0 = 2.0 * self.phi - self.phi_prev
+        self.phi_prev = self.phi
         A = lambda v: op(dom, kappa, v)
         if self.solver == "richardson":
             phi, it, res, ok = richardson(A, b, x0, self.gamma, self.tol, self.maxit)

@@ -1375,6 +1375,7 @@ kfbi_status batch_gmres(kfbi_batch* B, kfbi_solve_info* infos, cudaStream_t st) 
     xz[i] = B->states[i]->phi_zero ? 1 : 0;
     ax_ok[i] = !xz[i] && B->states[i]->ax_valid && B->states[i]->d_ax ? 1 : 0;
     B->states[i]->ax_valid = false;
+    B->states[i]->hist = false;  // batched steps keep no extrapolation history
   }
   // ||b||
   set_active(B, act, &xz, st);

@@ -293,6 +293,12 @@ struct kfbi_state {
   double* d_uf = nullptr;     // grid of the volume part, Y f-tilde (planes x Mp^2)
   double* d_ax = nullptr;     // A phi at the current phi (complex interleaved 2nb)
   bool ax_valid = false;
+  // the previous step's density (and, mixed, its A phi) for the linear
+  // extrapolation of the initial density in time
+  double* d_phi_prev = nullptr;
+  double* d_ax_prev = nullptr;
+  bool hist = false;           // d_phi_prev holds the previous converged density
+  bool ax_prev_valid = false;  // d_ax_prev holds A of it
   long long bytes = 0;
 };
 

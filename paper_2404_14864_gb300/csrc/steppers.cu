@@ -2,7 +2,8 @@
 //
 // Each step solves Delta u - kappa u = -F in Omega, u = g on Gamma through
 // the Dirichlet BIE: b = g - u+[0, f-tilde], GMRES for phi (initial guess
-// = previous phi), then one interface solve with (f-tilde, phi) whose grid
+// 2 phi^n - phi^(n-1), the previous density at the second step), then one
+// interface solve with (f-tilde, phi) whose grid
 // values in Omega are u^{n+1}.  The right-hand side F is carried as its own
 // variable (Eq. 3.4 for heat; the recurrence after Eq. 3.7 for the
 // theta-scheme; u* = 2u^{n+1} - u** for the Strang step, which is the
@@ -196,6 +197,27 @@ __global__ void k_add_grid(double* __restrict__ U, const double* __restrict__ uf
     U[i] += uf[i];
 }
 
+// History update and extrapolation of the initial density (complex
+// interleaved, 2 nb doubles): mode 1: x = 2 x - x_prev and x_prev = old x;
+// mode 0: x_prev = x; mode -1: nothing (a for the cached A phi).
+__global__ void k_extrap(double* __restrict__ x, double* __restrict__ xp, double* __restrict__ a,
+                         double* __restrict__ ap, int nb, int mode_x, int mode_a) {
+  KFBI_PDL_ENTRY();
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nb) return;
+  for (int c = 0; c < 2; ++c) {
+    const size_t i = 2 * (size_t)e + c;
+    const double t = x[i];
+    if (mode_x == 1) x[i] = 2.0 * t - xp[i];
+    xp[i] = t;
+    if (mode_a >= 0) {
+      const double u = a[i];
+      if (mode_a == 1) a[i] = 2.0 * u - ap[i];
+      ap[i] = u;
+    }
+  }
+}
+
 static kfbi_status solve_step(kfbi_domain* D, kfbi_state* S, const double* g, bool gC,
                               kfbi_solve_info* info, cudaStream_t st) {
   // Neumann states: every application below is psi -> d_n u+ and the final
@@ -212,7 +234,22 @@ static kfbi_status solve_step(kfbi_domain* D, kfbi_state* S, const double* g, bo
   KFBI_CHECK_LAUNCH();
   kfbi_solve_info loc{};
   bool grid_wx = false;
-  const bool have_ax = S->d_ax && S->ax_valid && !S->phi_zero;
+  // initial density: the previous one, or, once two converged densities
+  // exist, their linear extrapolation in time 2 phi^n - phi^(n-1) (on mixed
+  // domains the cached A phi is extrapolated with it, the operator being
+  // linear); the density entering this step becomes the history
+  bool have_ax = S->d_ax && S->ax_valid && !S->phi_zero;
+  if (!S->phi_zero) {
+    const int mphi = S->hist ? 1 : 0;
+    int max_ = -1;
+    if (S->d_ax && S->ax_valid) max_ = (S->hist && S->ax_prev_valid) ? 1 : 0;
+    KFBI_LAUNCH_P(KFBI_PROF_GRID, k_extrap, (nb + 255) / 256, 256, 0, st, S->d_phi, S->d_phi_prev,
+                  S->d_ax, S->d_ax_prev, nb, mphi, max_);
+    KFBI_CHECK_LAUNCH();
+    S->ax_prev_valid = max_ >= 0;
+    if (mphi == 1 && max_ != 1) have_ax = false;  // A x0 unknown: GMRES applies it
+    S->hist = true;
+  }
   S->ax_valid = false;
   kfbi_status s = gmres_solve(D, S->kre, S->kim, S->d_b, S->d_phi, S->phi_zero, &loc, st,
                               have_ax ? S->d_ax : nullptr, S->d_ax, &grid_wx);
@@ -263,9 +300,11 @@ kfbi_status kfbi_state_create(kfbi_domain* dom, int equation, kfbi_state** out) 
     alloc(&S->d_phi, nb2);
     alloc(&S->d_b, nb2);
     alloc(&S->d_ub, nb2);
+    alloc(&S->d_phi_prev, nb2);
     if (dom->tc) {
       alloc(&S->d_uf, plane);
       alloc(&S->d_ax, nb2);
+      alloc(&S->d_ax_prev, nb2);
     }
     KFBI_CUDA(cudaMemset(S->d_phi, 0, nb2 * sizeof(double)));
     return KFBI_OK;
@@ -283,8 +322,8 @@ long long kfbi_state_device_bytes(const kfbi_state* st) { return st ? st->bytes 
 void kfbi_state_destroy(kfbi_state* S) {
   if (!S) return;
   cudaDeviceSynchronize();
-  double* ptrs[] = {S->d_u,   S->d_F, S->d_Fprev, S->d_ft, S->d_aux,
-                    S->d_phi, S->d_b, S->d_ub,    S->d_uf, S->d_ax};
+  double* ptrs[] = {S->d_u,   S->d_F, S->d_Fprev, S->d_ft, S->d_aux,       S->d_phi,
+                    S->d_b,   S->d_ub, S->d_uf,   S->d_ax, S->d_phi_prev, S->d_ax_prev};
   for (double* p : ptrs)
     if (p) cudaFree(p);
   delete S;
@@ -320,6 +359,8 @@ kfbi_status kfbi_state_init_heat(kfbi_state* S, double dt, const double* u0, con
     KFBI_CUDA(cudaMemsetAsync(S->d_phi, 0, 2 * (size_t)D->nb * sizeof(double), st));
     S->phi_zero = true;
     S->ax_valid = false;
+    S->hist = false;
+    S->ax_prev_valid = false;
     S->initialised = true;
     return KFBI_OK;
   });
@@ -348,6 +389,8 @@ kfbi_status kfbi_state_init_wave(kfbi_state* S, double dt, double theta, const d
     KFBI_CUDA(cudaMemsetAsync(S->d_phi, 0, 2 * (size_t)D->nb * sizeof(double), st));
     S->phi_zero = true;
     S->ax_valid = false;
+    S->hist = false;
+    S->ax_prev_valid = false;
     S->initialised = true;
     return KFBI_OK;
   });
@@ -374,6 +417,8 @@ kfbi_status kfbi_state_init_schrodinger(kfbi_state* S, double dt, const void* u0
     KFBI_CUDA(cudaMemsetAsync(S->d_phi, 0, 2 * (size_t)D->nb * sizeof(double), st));
     S->phi_zero = true;
     S->ax_valid = false;
+    S->hist = false;
+    S->ax_prev_valid = false;
     S->initialised = true;
     return KFBI_OK;
   });
@@ -461,6 +506,8 @@ kfbi_status kfbi_state_set_neumann(kfbi_state* S, int neumann) {
     KFBI_CUDA(cudaMemset(S->d_phi, 0, 2 * (size_t)S->dom->nb * sizeof(double)));
     S->phi_zero = true;
     S->ax_valid = false;
+    S->hist = false;
+    S->ax_prev_valid = false;
     return KFBI_OK;
   });
 }
@@ -492,7 +539,7 @@ long long state_bytes_for(int Mp, int nb, int equation, bool mixed) {
   const int planes = equation == KFBI_SCHRODINGER ? 2 : 1;
   const size_t plane = (size_t)Mp * Mp * planes;
   const int fields = 3 + (equation != KFBI_HEAT ? 1 : 0) + (mixed ? 1 : 0);
-  const int vectors = 3 + (mixed ? 1 : 0);
+  const int vectors = 4 + (mixed ? 2 : 0);  // phi, b, ub, phi_prev (+ ax, ax_prev)
   return (long long)((fields * plane + vectors * 2 * (size_t)nb) * sizeof(double));
 }
 
