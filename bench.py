@@ -500,6 +500,10 @@ def run_ours(args, rank, world, local_rank):
 # ncu --set full capture of the timed step).  Reset to None whenever
 # k_tc_pass changes until it is captured again.
 TC_PASS_TRAFFIC_1024 = 16.845824e6 + 0.0
+# DRAM bytes per dense FFT32 pass at the 1024^2 wave workload (one real
+# plane): dram__bytes rate x duration of the dense k_dst_fft launches in one
+# ncu capture of the current kernel.  None whenever k_dst_fft changes.
+FFT_PASS_TRAFFIC_1024 = 4.26e6
 
 
 def roofline(res, M):
@@ -539,8 +543,9 @@ def roofline(res, M):
         nbytes = rows * 2.0 * M * 4
         gbs = nbytes / avg_s / 1e9
         peak = peaks.get("hbm_gbs", 6800.0)
+        traffic = FFT_PASS_TRAFFIC_1024 if (M == 1024 and abs(rows - M) < 0.5) else None
         return {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
-                "traffic": None, "traffic_unit": "bytes per launch",
+                "traffic": traffic, "traffic_unit": "bytes per launch",
                 "kernel": "k_dst_fft (FP32 FFT DST-I pass)",
                 "peak_source": "of measured: STREAM-style copy (hbm_gbs)",
                 "algorithmic_bytes_per_launch": nbytes, "avg_launch_us": avg_s * 1e6,
