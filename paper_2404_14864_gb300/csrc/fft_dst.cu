@@ -173,11 +173,16 @@ __global__ void __launch_bounds__(32 * RPB) k_dst_fft(const float* __restrict__ 
     __syncwarp();
     const int rl = rr0 + warp - sp.rmin;  // row within the irregular rows
     if (rl >= 0 && rl < sp.nrows) {
-      const int ne = sp.row_start[rl + 1];
-      for (int n = sp.row_start[rl] + lane; n < ne; n += 32) {
-        float sr = 0.f, si = 0.f;
-        const int a1 = sp.arm_start[n + 1];
-        for (int a = sp.arm_start[n]; a < a1; ++a) {
+      // lanes take the row's correction arms (grouped by node, nodes by
+      // column), each one arm with its six density terms; a segmented sum
+      // over lanes in a fixed order adds the arms of a node
+      const int a0 = sp.arm_start[sp.row_start[rl]], a1 = sp.arm_start[sp.row_start[rl + 1]];
+      for (int ab = a0; ab < a1; ab += 32) {
+        const int a = ab + lane;
+        float v = 0.f;
+        int col = -1 - lane;  // distinct keys for idle lanes
+        if (a < a1) {
+          col = sp.arm_col[a];
           int k = sp.arm_k0[a];
           float ar = 0.f, ai = 0.f, br = 0.f, bi = 0.f;
 #pragma unroll
@@ -193,13 +198,22 @@ __global__ void __launch_bounds__(32 * RPB) k_dst_fft(const float* __restrict__ 
             }
             k = (k + 1 == sp.nb) ? 0 : k + 1;
           }
-          sr += ar + sp.kre * br;
+          float sr = ar + sp.kre * br, si = 0.f;
           if (sp.cplx) {
             sr -= sp.kim * bi;
-            si += ai + sp.kre * bi + sp.kim * br;
+            si = ai + sp.kre * bi + sp.kim * br;
           }
+          v = p == 0 ? sr : si;
         }
-        xrow[sp.node_col[n]] = p == 0 ? sr : si;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const float t = __shfl_up_sync(0xffffffffu, v, o);
+          const int kc = __shfl_up_sync(0xffffffffu, col, o);
+          if (lane >= o && kc == col) v += t;
+        }
+        const int next = __shfl_down_sync(0xffffffffu, col, 1);
+        if (a < a1 && (lane == 31 || next != col)) xrow[col] += v;
+        __syncwarp();
       }
     }
   } else

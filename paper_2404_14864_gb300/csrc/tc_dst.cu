@@ -1188,6 +1188,13 @@ TcDst* tc_create(kfbi_domain* D, const Plan& P) {
       T->bytes += (long long)((rs.size() + col.size()) * sizeof(int));
       KFBI_CUDA(cudaMemcpy(T->row_start, rs.data(), rs.size() * sizeof(int), cudaMemcpyHostToDevice));
       KFBI_CUDA(cudaMemcpy(T->node_col, col.data(), col.size() * sizeof(int), cudaMemcpyHostToDevice));
+      if (D->desc.precision == KFBI_MIXED_FFT32) {
+        std::vector<int> ac(std::max(1, P.n_arms()), 0);
+        for (int a = 0; a < P.n_arms(); ++a) ac[a] = P.irr[P.arm_node[a]] % n1;
+        KFBI_CUDA(cudaMalloc(&T->arm_col, ac.size() * sizeof(int)));
+        T->bytes += (long long)(ac.size() * sizeof(int));
+        KFBI_CUDA(cudaMemcpy(T->arm_col, ac.data(), ac.size() * sizeof(int), cudaMemcpyHostToDevice));
+      }
       T->kb0 = T->rmin / BK;
       T->nk2 = rmax / BK + 1 - T->kb0;
       int imin = n1, imax = 0;
@@ -1281,6 +1288,7 @@ void tc_destroy(TcDst* T) {
     if (p) cudaFree(p);
   if (T->row_start) cudaFree(T->row_start);
   if (T->node_col) cudaFree(T->node_col);
+  if (T->arm_col) cudaFree(T->arm_col);
   if (T->d_maps) cudaFree(T->d_maps);
   if (T->twM) cudaFree(T->twM);
   if (T->twB) cudaFree(T->twB);
@@ -1299,7 +1307,10 @@ long long tc_bytes_for(const Plan& P, int Mp) {
     const int rows = P.irr.back() / P.n1 - P.irr.front() / P.n1 + 1;
     b += (long long)((rows + 1 + P.n_irr()) * sizeof(int));
   }
-  if (P.desc.precision == KFBI_MIXED_FFT32) b += 3LL * P.M * (long long)sizeof(float2);
+  if (P.desc.precision == KFBI_MIXED_FFT32) {
+    b += 3LL * P.M * (long long)sizeof(float2);
+    if (P.n_irr() > 0) b += (long long)(std::max(1, P.n_arms()) * sizeof(int));  // arm_col
+  }
   return b + (long long)(kNumMaps * sizeof(CUtensorMap));
 }
 
@@ -1453,6 +1464,7 @@ static void tc_apply_sparse(kfbi_domain* D, double kre, double kim, const double
     FftSparseRhs sp;
     sp.row_start = T->row_start;
     sp.node_col = T->node_col;
+    sp.arm_col = T->arm_col;
     sp.rmin = T->rmin;
     sp.nrows = T->nrows;
     sp.arm_start = D->d_arm_start;

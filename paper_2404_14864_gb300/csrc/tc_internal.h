@@ -73,6 +73,7 @@ struct TcDst {
   // sparse route for right-hand sides supported on the irregular nodes
   float *T1sh = nullptr, *T1sl = nullptr, *rv = nullptr;
   int *row_start = nullptr, *node_col = nullptr;
+  int* arm_col = nullptr;  // FFT domains: grid column of each arm's irregular node
   int rmin = 0, nrows = 0, kb0 = 0, nk2 = 0, ct0 = 0, nt3 = 0;
   CUtensorMap mT1s_hi, mT1s_lo;
   // device copies of the tensor maps, in kMap* order
@@ -104,6 +105,7 @@ struct TcDst {
 struct FftSparseRhs {
   const int* row_start;
   const int* node_col;
+  const int* arm_col;  // column of each arm's node (arms grouped by node, nodes by row)
   int rmin, nrows;
   const int* arm_start;
   const int* arm_k0;
