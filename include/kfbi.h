@@ -258,6 +258,17 @@ kfbi_status kfbi_step_schrodinger(kfbi_domain* dom, kfbi_state* st, const double
  * the server take Dirichlet states only (KFBI_ERR_ARG). */
 kfbi_status kfbi_state_set_neumann(kfbi_state* st, int neumann);
 
+/* Checkpoint and resume: the state's time-level data (fields, densities,
+ * extrapolation history, superposition caches, step parameters) as one
+ * host blob of kfbi_state_blob_bytes bytes (caller-owned host memory).
+ * Importing into a state of the same equation on a domain with the same
+ * description continues the run bit for bit.  Both synchronous; import
+ * returns KFBI_ERR_ARG for a blob of another equation, grid, node count or
+ * domain precision. */
+long long kfbi_state_blob_bytes(const kfbi_state* st);
+kfbi_status kfbi_state_export(kfbi_state* st, void* host_buf, long long bytes);
+kfbi_status kfbi_state_import(kfbi_state* st, const void* host_buf, long long bytes);
+
 /* Copy the current field u^n (all (M-1)^2 nodes; values outside Omega are
  * the exterior part of the interface solution) or the current density. */
 kfbi_status kfbi_state_get_u(kfbi_state* st, void* u_out_dev, void* stream);

@@ -10,6 +10,8 @@
 // backward-Euler identity Delta u^{n+1} = kappa (u^{n+1} - u**)).
 // All grid kernels are elementwise over the padded planes, in float64.
 #include <cmath>
+#include <cstring>
+#include <vector>
 
 #include "internal.h"
 
@@ -271,6 +273,29 @@ static kfbi_status solve_step(kfbi_domain* D, kfbi_state* S, const double* g, bo
 
 using namespace kfbi;
 
+namespace {
+struct StateBlobHeader {
+  char magic[8];  // "KFBIST1\0"
+  int eq, planes, Mp, nb;
+  int initialised, phi_zero, neumann, hist, ax_valid, ax_prev_valid, has_ax;
+  double dt, theta, kre, kim;
+};
+
+// (device pointer, doubles) of every array the blob carries, in order
+std::vector<std::pair<double*, size_t>> state_arrays(kfbi_state* S) {
+  const size_t plane = (size_t)S->planes * S->dom->Mp * S->dom->Mp;
+  const size_t nb2 = 2 * (size_t)S->dom->nb;
+  std::vector<std::pair<double*, size_t>> a = {{S->d_u, plane}, {S->d_F, plane},
+                                               {S->d_phi, nb2}, {S->d_phi_prev, nb2}};
+  if (S->d_Fprev) a.push_back({S->d_Fprev, plane});
+  if (S->d_ax) {
+    a.push_back({S->d_ax, nb2});
+    a.push_back({S->d_ax_prev, nb2});
+  }
+  return a;
+}
+}  // namespace
+
 extern "C" {
 
 kfbi_status kfbi_state_create(kfbi_domain* dom, int equation, kfbi_state** out) {
@@ -516,6 +541,88 @@ kfbi_status kfbi_state_get_u(kfbi_state* S, void* u_out, void* stream) {
   if (!S || !S->dom || !u_out) return KFBI_ERR_ARG;
   return guarded(S->dom, [&]() -> kfbi_status {
     unpad(S->dom, S->d_u, (double*)u_out, S->planes == 2, (cudaStream_t)stream);
+    return KFBI_OK;
+  });
+}
+
+// ---- checkpoint: the state's time-level data as one host blob -------------
+
+
+long long kfbi_state_blob_bytes(const kfbi_state* S) {
+  if (!S || !S->dom) return -1;
+  size_t n = sizeof(StateBlobHeader);
+  for (auto& a : state_arrays(const_cast<kfbi_state*>(S))) n += a.second * sizeof(double);
+  return (long long)n;
+}
+
+kfbi_status kfbi_state_export(kfbi_state* S, void* host_buf, long long bytes) {
+  if (!S || !S->dom || !host_buf) return KFBI_ERR_ARG;
+  if (bytes < kfbi_state_blob_bytes(S)) {
+    S->dom->err = "state blob buffer too small (kfbi_state_blob_bytes)";
+    return KFBI_ERR_ARG;
+  }
+  return guarded(S->dom, [&]() -> kfbi_status {
+    StateBlobHeader h{};
+    std::memcpy(h.magic, "KFBIST1", 8);
+    h.eq = S->eq;
+    h.planes = S->planes;
+    h.Mp = S->dom->Mp;
+    h.nb = S->dom->nb;
+    h.initialised = S->initialised;
+    h.phi_zero = S->phi_zero;
+    h.neumann = S->neumann;
+    h.hist = S->hist;
+    h.ax_valid = S->ax_valid;
+    h.ax_prev_valid = S->ax_prev_valid;
+    h.has_ax = S->d_ax != nullptr;
+    h.dt = S->dt;
+    h.theta = S->theta;
+    h.kre = S->kre;
+    h.kim = S->kim;
+    char* out = (char*)host_buf;
+    std::memcpy(out, &h, sizeof(h));
+    out += sizeof(h);
+    KFBI_CUDA(cudaDeviceSynchronize());
+    for (auto& a : state_arrays(S)) {
+      KFBI_CUDA(cudaMemcpy(out, a.first, a.second * sizeof(double), cudaMemcpyDeviceToHost));
+      out += a.second * sizeof(double);
+    }
+    return KFBI_OK;
+  });
+}
+
+kfbi_status kfbi_state_import(kfbi_state* S, const void* host_buf, long long bytes) {
+  if (!S || !S->dom || !host_buf) return KFBI_ERR_ARG;
+  if (bytes < (long long)sizeof(StateBlobHeader)) {
+    S->dom->err = "state blob too short";
+    return KFBI_ERR_ARG;
+  }
+  StateBlobHeader h;
+  std::memcpy(&h, host_buf, sizeof(h));
+  if (std::memcmp(h.magic, "KFBIST1", 8) != 0 || h.eq != S->eq || h.planes != S->planes ||
+      h.Mp != S->dom->Mp || h.nb != S->dom->nb || h.has_ax != (S->d_ax != nullptr) ||
+      bytes < kfbi_state_blob_bytes(S)) {
+    S->dom->err = "state blob does not match this state (equation, grid, boundary nodes or "
+                  "domain precision)";
+    return KFBI_ERR_ARG;
+  }
+  return guarded(S->dom, [&]() -> kfbi_status {
+    const char* in = (const char*)host_buf + sizeof(h);
+    KFBI_CUDA(cudaDeviceSynchronize());
+    for (auto& a : state_arrays(S)) {
+      KFBI_CUDA(cudaMemcpy(a.first, in, a.second * sizeof(double), cudaMemcpyHostToDevice));
+      in += a.second * sizeof(double);
+    }
+    S->initialised = h.initialised != 0;
+    S->phi_zero = h.phi_zero != 0;
+    S->neumann = h.neumann != 0;
+    S->hist = h.hist != 0;
+    S->ax_valid = h.ax_valid != 0;
+    S->ax_prev_valid = h.ax_prev_valid != 0;
+    S->dt = h.dt;
+    S->theta = h.theta;
+    S->kre = h.kre;
+    S->kim = h.kim;
     return KFBI_OK;
   });
 }

@@ -121,6 +121,9 @@ def lib():
                                    ctypes.POINTER(SolveInfo), _VP]),
         "kfbi_state_create": (S, [_VP, ctypes.c_int, ctypes.POINTER(_VP)]),
         "kfbi_state_set_neumann": (S, [_VP, ctypes.c_int]),
+        "kfbi_state_blob_bytes": (ctypes.c_longlong, [_VP]),
+        "kfbi_state_export": (S, [_VP, _VP, ctypes.c_longlong]),
+        "kfbi_state_import": (S, [_VP, _VP, ctypes.c_longlong]),
         "kfbi_state_destroy": (None, [_VP]),
         "kfbi_state_init_heat": (S, [_VP, ctypes.c_double, _VP, _VP, _VP, _VP]),
         "kfbi_state_init_wave": (S, [_VP, ctypes.c_double, ctypes.c_double, _VP, _VP, _VP, _VP, _VP]),
@@ -429,6 +432,18 @@ class State:
         _check(lib().kfbi_step_schrodinger(self.dom.h, self.h, _ptr(v), float(w), _ptr(g_next),
                                            ctypes.byref(info), _stream(stream)), self.dom.h)
         return info.as_dict()
+
+    def export(self):
+        """Checkpoint: the state's time-level data as bytes."""
+        n = int(lib().kfbi_state_blob_bytes(self.h))
+        buf = ctypes.create_string_buffer(n)
+        _check(lib().kfbi_state_export(self.h, buf, n), self.dom.h)
+        return buf.raw
+
+    def import_(self, blob):
+        """Resume from bytes written by export()."""
+        buf = ctypes.create_string_buffer(bytes(blob), len(blob))
+        _check(lib().kfbi_state_import(self.h, buf, len(blob)), self.dom.h)
 
     def set_neumann(self, on=True):
         """Steps take Neumann data d_n u = g (float64 domains)."""
