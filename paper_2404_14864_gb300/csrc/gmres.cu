@@ -741,21 +741,26 @@ __global__ void __launch_bounds__(CLT) k_arnoldi_cl(double2* __restrict__ V, int
   asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 
-// x += V[:, :k] y with R y = g: one warp per CTA solves the triangle
-// (row sums across lanes), then the CTA updates its slice.
+// x += V[:, :k] y with R y = g: the CTA stages the triangle of R in shared
+// memory, one warp solves it (row sums across lanes), then the CTA updates
+// its slice.
 __global__ void __launch_bounds__(GT) k_update_grid(const double2* __restrict__ V, int nb, int k,
                                                     const double2* H, const double2* g, int m,
                                                     double2* __restrict__ x, int slice) {
   KFBI_PDL_ENTRY();
   __shared__ double2 y[64];
+  __shared__ double2 R[64 * 65 / 2];  // R[l (l + 1) / 2 + i] = H(i, l), i <= l < k <= 64
   const int b = blockIdx.x;
   const int e0 = b * slice, e1 = min(nb, e0 + slice);
+  for (int l = 0; l < k; ++l)
+    for (int i = threadIdx.x; i <= l; i += GT) R[l * (l + 1) / 2 + i] = H[(size_t)l * (m + 1) + i];
+  __syncthreads();
   if (threadIdx.x < 32) {
     const int lane = threadIdx.x;
     for (int i = k - 1; i >= 0; --i) {
       double2 s = make_double2(0.0, 0.0);
       for (int l = i + 1 + lane; l < k; l += 32) {
-        const double2 t = cmul(H[(size_t)l * (m + 1) + i], y[l]);
+        const double2 t = cmul(R[l * (l + 1) / 2 + i], y[l]);
         s.x += t.x;
         s.y += t.y;
       }
@@ -765,9 +770,9 @@ __global__ void __launch_bounds__(GT) k_update_grid(const double2* __restrict__ 
       }
       if (lane == 0) {
         const double2 r = make_double2(g[i].x - s.x, g[i].y - s.y);
-        const double2 d = H[(size_t)i * (m + 1) + i];
-        const double dd = d.x * d.x + d.y * d.y;
-        y[i] = make_double2((r.x * d.x + r.y * d.y) / dd, (r.y * d.x - r.x * d.y) / dd);
+        const double2 d = R[i * (i + 1) / 2 + i];
+        const double inv = 1.0 / (d.x * d.x + d.y * d.y);
+        y[i] = make_double2((r.x * d.x + r.y * d.y) * inv, (r.y * d.x - r.x * d.y) * inv);
       }
       __syncwarp();
     }
