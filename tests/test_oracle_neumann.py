@@ -116,3 +116,29 @@ def test_neumann_heat_stepper_converges():
     e = [_heat_neumann_err(M) for M in (32, 64, 128)]
     assert e[0] / e[1] > 3.0 and e[1] / e[2] > 3.0, e
     assert e[2] < 2.2e-3, e
+
+
+def test_neumann_bvp_complex_kappa_converges():
+    """Complex kappa (the Schroedinger steps' kappa = 2i/tau is complex):
+    u = (1 + 0.5i) sin(0.6 x + 0.8 y), kappa = 10 + 20i."""
+    kappa = 10.0 + 20.0j
+    e = []
+    for M in (32, 64, 128):
+        desc = W.domain_desc(M, W.star())
+        d = oracle.make_domain(desc)
+        X, Y = W.grid_xy(desc)
+        m = d.interior_inside()
+        c = 1.0 + 0.5j
+        u = c * np.sin(0.6 * X + 0.8 * Y)
+        Ft = np.where(m, -(1.0 + kappa) * u, 0.0)
+        t1, t2, _, _ = oracle.interface.tangent_data(d, d.theta)
+        cz = c * np.cos(0.6 * d.zx + 0.8 * d.zy)
+        gN = 0.6 * cz * t2 - 0.8 * cz * t1
+        b = gN - oracle.apply_neumann(d, kappa, np.zeros(d.nb, dtype=complex), Ft)
+        psi, it, res, ok = oracle.gmres(lambda v: oracle.apply_neumann(d, kappa, v), b, None,
+                                        1e-12, 50, 500)
+        assert ok
+        _, U = oracle.interface_solve(d, kappa, np.zeros(d.nb, dtype=complex), Ft, psi)
+        e.append(np.abs(U - u)[m].max())
+    assert e[0] / e[1] > 2.5 and e[1] / e[2] > 1.5, e
+    assert e[2] < 2e-3, e
