@@ -1401,7 +1401,14 @@ kfbi_status gmres_solve(kfbi_domain* D, double kre, double kim, const double* b,
       status = KFBI_ERR_NONFINITE;
       break;
     }
-    if (bnorm == 0.0 || rn <= tol * bnorm) {
+    if (bnorm == 0.0) {  // b = 0: x = 0, whatever the initial guess
+      KFBI_CUDA(cudaMemsetAsync(x, 0, 2 * (size_t)nb * sizeof(double), st));
+      fresh = false;
+      rn = 0.0;
+      conv = true;
+      break;
+    }
+    if (rn <= tol * bnorm) {
       conv = true;
       break;
     }

@@ -253,3 +253,30 @@ def test_batches_refuse_neumann_states():
     assert e.value.status == 1
     b.close()
     dom.close()
+
+
+def test_neumann_zero_data_gives_zero_density():
+    desc = W.domain_desc(64, W.star())
+    dom = kfbi.Domain(desc, kfbi.KFBI_MIXED_FFT32, tol=1e-10)
+    psi = dev(np.full(desc["nb"], 0.3))  # a nonzero initial guess
+    info = dom.solve_neumann(10.0, dev(np.zeros(desc["nb"])), psi)
+    assert info["converged"] and info["iters"] == 0
+    assert not np.any(host(psi))
+    dom.close()
+
+
+@pytest.mark.parametrize("prec", [kfbi.KFBI_FP64, kfbi.KFBI_MIXED_FFT32], ids=["fp64", "fft32"])
+def test_neumann_richardson_on_every_precision(prec):
+    kappa = 10.0
+    desc, d, u, f, gN = _bvp(64, kappa)
+    m = d.interior_inside()
+    Ft = np.where(m, f, 0.0)
+    b = gN - oracle.apply_neumann(d, kappa, np.zeros(d.nb), Ft)
+    x_g, _, _, _ = oracle.gmres(lambda v: oracle.apply_neumann(d, kappa, v), b, None, 1e-13,
+                                50, 500)
+    dom = kfbi.Domain(desc, prec, tol=1e-10, maxit=5000, solver=kfbi.KFBI_RICHARDSON, gamma=1.2)
+    psi = dev(np.zeros(d.nb))
+    info = dom.solve_neumann(kappa, dev(gN), psi, dev(f))
+    assert info["converged"]
+    assert rel_linf(host(psi), x_g) <= 1e-8
+    dom.close()

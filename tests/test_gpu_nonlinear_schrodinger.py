@@ -100,3 +100,28 @@ def test_nls_w_zero_is_the_linear_step():
     m = d.interior_inside()
     assert rel_linf(host(st.get_u())[m], U[m]) <= 1e-10
     dom.close()
+
+
+def test_nls_focusing_w_negative_matches_oracle():
+    """w = -1 (focusing) on the same data: the closed-form root on the GPU
+    and the oracle's Newton iteration give the same steps (no exact solution
+    is needed for parity)."""
+    ex = W.NonlinearSchrodingerExact()
+    desc = W.domain_desc(64, W.ex5_star(0.2), lo=-math.pi, hi=math.pi)
+    d = oracle.make_domain(desc)
+    X, Y = W.grid_xy(desc)
+    zx, zy = W.boundary_xy(desc)
+    tau = 0.125
+    V = ex.v(X, Y)
+    dom = kfbi.Domain(desc, kfbi.KFBI_FP64, tol=1e-12)
+    st = kfbi.State(dom, kfbi.KFBI_SCHRODINGER)
+    st.init_schrodinger(tau, dev(ex.u(X, Y, 0)), dev(ex.lap(X, Y, 0)))
+    orc = oracle.SchrodingerStepper(d, tau, 1e-12)
+    orc.init(ex.u(X, Y, 0), ex.lap(X, Y, 0))
+    for k in range(3):
+        g = ex.u(zx, zy, (k + 1) * tau)
+        st.step_schrodinger(dev(V), dev(g), w=-1.0)
+        U = orc.step(g, V, -1.0)
+    m = d.interior_inside()
+    assert rel_linf(host(st.get_u())[m], U[m]) <= 1e-10
+    dom.close()
