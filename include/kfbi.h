@@ -245,8 +245,8 @@ kfbi_status kfbi_step_wave(kfbi_domain* dom, kfbi_state* st, const double* g_nex
  * reaches from u*; unique while dt |w| |u|^2 / 2 < 1), then Eq. 3.12 for
  * u^{n+1} with data g_next_dev (complex128), then u* = 2 u^{n+1} - u**.
  * v_dev: (M-1)^2 doubles (the potential v); w: real, finite (else
- * KFBI_ERR_ARG).  Batches and the server step Schroedinger requests with
- * w = 0. */
+ * KFBI_ERR_ARG).  Batched steps take each state's kfbi_state_set_w; the
+ * server steps Schroedinger requests with w = 0. */
 kfbi_status kfbi_step_schrodinger(kfbi_domain* dom, kfbi_state* st, const double* v_dev,
                                   double w, const void* g_next_dev, kfbi_solve_info* info,
                                   void* stream);
@@ -257,6 +257,12 @@ kfbi_status kfbi_step_schrodinger(kfbi_domain* dom, kfbi_state* st, const double
  * u = Y f - V psi, Eq. 3.20).  Resets the density to zero.  Batches and
  * the server take Dirichlet states only (KFBI_ERR_ARG). */
 kfbi_status kfbi_state_set_neumann(kfbi_state* st, int neumann);
+
+/* Nonlinear coefficient w of a Schroedinger state's batched steps
+ * (kfbi_batch_step takes no w; single steps pass theirs to
+ * kfbi_step_schrodinger).  Default 0; KFBI_ERR_ARG for another equation or
+ * a non-finite w. */
+kfbi_status kfbi_state_set_w(kfbi_state* st, double w);
 
 /* Checkpoint and resume: the state's time-level data (fields, densities,
  * extrapolation history, superposition caches, step parameters) as one

@@ -34,6 +34,7 @@ struct GInst {
   int Mp, n1, nb, n_irr, n_arms, M, m, C, eq;
   int rmin, nrows;
   double h, kre, kim, scale, dt, theta;
+  double w;  // Schroedinger: nonlinear coefficient of the B step (Eq. 3.10)
   // FP64 domain tables
   const uint8_t* mask;
   const int* irr_off;
@@ -130,10 +131,11 @@ __global__ void gk_make_ft(const GInst* gi) {
     const int r = (int)(idx / I.Mp), c = (int)(idx % I.Mp);
     double xr = 0, xi = 0;
     if (r < I.n1 && c < I.n1) {
-      const double a = half_dt * I.src[(size_t)r * I.n1 + c];
+      // the modulus-preserving root of Eq. 3.10 (as k_schr_bstep)
+      const double sr = I.F[idx], si = I.F[plane + idx];
+      const double a = half_dt * (I.src[(size_t)r * I.n1 + c] + I.w * (sr * sr + si * si));
       const double den = 1.0 / (1.0 + a * a);
       const double pr = (1.0 - a * a) * den, pi = -2.0 * a * den;
-      const double sr = I.F[idx], si = I.F[plane + idx];
       xr = pr * sr - pi * si;
       xi = pr * si + pi * sr;
     }
@@ -1332,7 +1334,7 @@ void fill_instances(kfbi_batch* B, kfbi_state* const* states, const void* const*
     I.M = D->M; I.m = D->restart; I.C = S->kim != 0.0; I.eq = S->eq;
     I.rmin = T->rmin; I.nrows = T->nrows;
     I.h = D->h; I.kre = S->kre; I.kim = S->kim; I.scale = (2.0 / D->M) * (2.0 / D->M);
-    I.dt = S->dt; I.theta = S->theta;
+    I.dt = S->dt; I.theta = S->theta; I.w = S->w;
     I.mask = D->d_mask; I.irr_off = D->d_irr_off; I.arm_start = D->d_arm_start; I.arm_k0 = D->d_arm_k0;
     I.alpha = D->d_arm_alpha; I.beta = D->d_arm_beta; I.arm_fidx = D->d_arm_fidx;
     I.arm_fcoef = D->d_arm_fcoef; I.node_gidx = D->d_node_gidx; I.node_w = D->d_node_w;

@@ -281,6 +281,7 @@ struct kfbi_state {
   bool initialised = false;
   bool phi_zero = true;
   bool neumann = false;  // boundary data are d_n u (Eq. 3.19), the density is psi
+  double w = 0.0;        // nonlinear Schroedinger coefficient of batched steps
   double* d_u = nullptr;      // current field, padded planes
   double* d_F = nullptr;      // F^{n+1} (heat, wave) or u* (Schroedinger)
   double* d_Fprev = nullptr;  // F^n (wave)

@@ -523,6 +523,16 @@ kfbi_status kfbi_step_schrodinger(kfbi_domain* dom, kfbi_state* S, const double*
   });
 }
 
+kfbi_status kfbi_state_set_w(kfbi_state* S, double w) {
+  if (!S || !S->dom) return KFBI_ERR_ARG;
+  if (S->eq != KFBI_SCHRODINGER || !std::isfinite(w)) {
+    S->dom->err = "w needs a Schroedinger state and a finite value";
+    return KFBI_ERR_ARG;
+  }
+  S->w = w;
+  return KFBI_OK;
+}
+
 kfbi_status kfbi_state_set_neumann(kfbi_state* S, int neumann) {
   if (!S || !S->dom) return KFBI_ERR_ARG;
   return guarded(S->dom, [&]() -> kfbi_status {

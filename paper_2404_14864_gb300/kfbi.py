@@ -121,6 +121,7 @@ def lib():
                                    ctypes.POINTER(SolveInfo), _VP]),
         "kfbi_state_create": (S, [_VP, ctypes.c_int, ctypes.POINTER(_VP)]),
         "kfbi_state_set_neumann": (S, [_VP, ctypes.c_int]),
+        "kfbi_state_set_w": (S, [_VP, ctypes.c_double]),
         "kfbi_state_blob_bytes": (ctypes.c_longlong, [_VP]),
         "kfbi_state_export": (S, [_VP, _VP, ctypes.c_longlong]),
         "kfbi_state_import": (S, [_VP, _VP, ctypes.c_longlong]),
@@ -444,6 +445,10 @@ class State:
         """Resume from bytes written by export()."""
         buf = ctypes.create_string_buffer(bytes(blob), len(blob))
         _check(lib().kfbi_state_import(self.h, buf, len(blob)), self.dom.h)
+
+    def set_w(self, w):
+        """Nonlinear coefficient of this Schroedinger state's batched steps."""
+        _check(lib().kfbi_state_set_w(self.h, float(w)), self.dom.h)
 
     def set_neumann(self, on=True):
         """Steps take Neumann data d_n u = g (float64 domains)."""

@@ -120,3 +120,40 @@ def test_batch_matches_oracle_for_one_instance():
         U = orc.step(ex.u(r.zx, r.zy, t1), ex.src(r.X, r.Y, t1) + ex.src(r.X, r.Y, t1 + r.tau))
     m = d.interior_inside()
     assert rel_linf(host(states[0].get_u())[m], U[m]) <= 1e-8
+
+
+def test_batch_nonlinear_schrodinger_equals_single_steps():
+    """w = 1 (the paper's nonlinear example) through kfbi_state_set_w in a
+    batch with a linear instance: each equals its domain stepped alone."""
+    ex = W.NonlinearSchrodingerExact()
+    desc = W.domain_desc(64, W.ex5_star(0.2), lo=-math.pi, hi=math.pi)
+    X, Y = W.grid_xy(desc)
+    zx, zy = W.boundary_xy(desc)
+    tau = 0.125
+    V = dev(ex.v(X, Y))
+    lin = _Run("schr", W.domain_desc(128, W.flower()))
+
+    def nl_state(dom):
+        st = kfbi.State(dom, kfbi.KFBI_SCHRODINGER)
+        st.init_schrodinger(tau, dev(ex.u(X, Y, 0)), dev(ex.lap(X, Y, 0)))
+        return st
+
+    doms = [kfbi.Domain(desc, kfbi.KFBI_MIXED_TF32, tol=1e-12, maxit=800),
+            kfbi.Domain(lin.desc, kfbi.KFBI_MIXED_TF32, tol=1e-12, maxit=800)]
+    states = [nl_state(doms[0]), lin.make_state(doms[1])]
+    states[0].set_w(ex.w)
+    batch = kfbi.Batch(doms)
+    for k in range(3):
+        g1, v1 = lin.inputs(k)
+        infos = batch.step(states, [dev(ex.u(zx, zy, (k + 1) * tau)), g1], [V, v1])
+        assert all(i["converged"] for i in infos)
+    d1 = kfbi.Domain(desc, kfbi.KFBI_MIXED_TF32, tol=1e-12, maxit=800)
+    s1 = nl_state(d1)
+    for k in range(3):
+        s1.step_schrodinger(V, dev(ex.u(zx, zy, (k + 1) * tau)), w=ex.w)
+    assert rel_linf(host(states[0].get_u()), host(s1.get_u())) <= 1e-10
+    with pytest.raises(kfbi.KfbiError):
+        states[0].set_w(float("inf"))
+    batch.close()
+    for d in doms + [d1]:
+        d.close()
