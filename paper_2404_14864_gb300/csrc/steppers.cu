@@ -278,7 +278,7 @@ struct StateBlobHeader {
   char magic[8];  // "KFBIST1\0"
   int eq, planes, Mp, nb;
   int initialised, phi_zero, neumann, hist, ax_valid, ax_prev_valid, has_ax;
-  double dt, theta, kre, kim;
+  double dt, theta, kre, kim, w;
 };
 
 // (device pointer, doubles) of every array the blob carries, in order
@@ -589,6 +589,7 @@ kfbi_status kfbi_state_export(kfbi_state* S, void* host_buf, long long bytes) {
     h.theta = S->theta;
     h.kre = S->kre;
     h.kim = S->kim;
+    h.w = S->w;
     char* out = (char*)host_buf;
     std::memcpy(out, &h, sizeof(h));
     out += sizeof(h);
@@ -633,6 +634,7 @@ kfbi_status kfbi_state_import(kfbi_state* S, const void* host_buf, long long byt
     S->theta = h.theta;
     S->kre = h.kre;
     S->kim = h.kim;
+    S->w = h.w;
     return KFBI_OK;
   });
 }
