@@ -45,3 +45,18 @@ def test_problem_is_a_consistent_manufactured_solution(workload, M, steps, bound
     assert err2 < err, (err, err2)
     cfg = P.config("fp64")
     assert cfg["M"] == M and cfg["workload"].endswith(str(M))
+
+
+@pytest.mark.parametrize("curve", ["ellipse", "star", "flower"])
+def test_boundary_normal_is_the_outward_unit_normal(curve):
+    from paper_2404_14864_gb300 import workloads as W
+    c = {"ellipse": W.ellipse(), "star": W.star(), "flower": W.flower()}[curve]
+    desc = W.domain_desc(64, c)
+    d = oracle.make_domain(desc)
+    t1, t2, _, _ = oracle.interface.tangent_data(d, d.theta)
+    nx, ny = W.boundary_normal(desc)
+    assert np.abs(np.hypot(nx, ny) - 1.0).max() < 1e-14
+    assert np.abs(nx - t2).max() < 1e-13 and np.abs(ny + t1).max() < 1e-13
+    # outward: a small step along n leaves the domain
+    zx, zy = W.boundary_xy(desc)
+    assert np.all(d.curve.level(zx + 1e-3 * nx, zy + 1e-3 * ny) > 0)
