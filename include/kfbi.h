@@ -199,9 +199,11 @@ kfbi_status kfbi_solve_neumann(kfbi_domain* dom, double kappa_re, double kappa_i
  *                    layout, device memory owned by the caller.
  * Work space is a static device array of 2.5 MiB that every GPU loading the
  * library holds until exit, so M - 1 <= 256; larger M returns KFBI_ERR_ARG.
- * The first call on a device looks up the array's address (call it once
- * before any stream capture); all calls share the array, so calls that
- * overlap on the GPU race.  Allocates nothing; asynchronous on `stream`. */
+ * The first call in a device's context looks up the array's address (call
+ * it once before any stream capture); after cudaDeviceReset, or from
+ * another context, the next call looks it up again.  All calls share the
+ * array, so calls that overlap on the GPU race.  Allocates nothing;
+ * asynchronous on `stream`. */
 kfbi_status kfbi_box_solve_noalloc(int M, double box_lo, double box_hi, double kappa_re,
                                    double kappa_im, const void* rhs_dev, void* u_dev,
                                    void* stream);

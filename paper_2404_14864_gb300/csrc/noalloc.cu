@@ -12,11 +12,16 @@
 // The scratch array is file-scope device memory: every GPU that loads the
 // library holds it (about 2.5 MiB) until the process exits.  Host code
 // cannot use the array's name as a device address, so the address is
-// looked up once per device with cudaGetSymbolAddress (the first call on a
-// device does this, so that first call should come before any stream
-// capture).  All calls share the one array and it keeps the last call's
+// looked up with cudaGetSymbolAddress the first time a call runs in a
+// device's context (so that first call should come before any stream
+// capture).  The cached address is keyed on the current CUDA context: after
+// cudaDeviceReset, or in another context on the same device, the module is
+// loaded again, the array may sit elsewhere, and the next call looks the
+// address up again.  All calls share the one array and it keeps the last call's
 // contents; every region the solve reads is rewritten by each call, and
 // calls that overlap on the GPU (two streams at once) race on it.
+#include <cuda.h>
+
 #include <cmath>
 #include <mutex>
 
@@ -34,6 +39,8 @@ static __device__ __align__(256) double g_scratch[kScratchDoubles];
 
 constexpr int kMaxDevices = 64;
 static std::mutex g_mu;
+// per device: the context the address was looked up in, and the address
+static CUcontext g_ctx[kMaxDevices] = {nullptr};
 static double* g_addr[kMaxDevices] = {nullptr};
 
 // S[a][i] = sin(pi a i / M) (a*i reduced mod 2M), zero padded; lambda_a.
@@ -95,8 +102,25 @@ __global__ void k_na_unpad(const double* src, double* dst, int n1, int Mp, int C
   }
 }
 
-// Device address of the scratch array on the current device (looked up on
-// the first call per device).
+// cuCtxGetCurrent through the runtime's driver entry point (the library
+// does not link the driver library directly).
+typedef CUresult (*CtxGetCurrentFn)(CUcontext*);
+static CtxGetCurrentFn ctx_get_current() {
+  static std::once_flag once;
+  static CtxGetCurrentFn fn = nullptr;
+  std::call_once(once, []() {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 4000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (CtxGetCurrentFn)p;
+  });
+  return fn;
+}
+
+// Device address of the scratch array in the current context (looked up on
+// the first call in each context of a device).
 static double* scratch_address(std::string& err) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -109,14 +133,29 @@ static double* scratch_address(std::string& err) {
     return nullptr;
   }
   std::lock_guard<std::mutex> lk(g_mu);
-  if (!g_addr[dev]) {
+  // a context that differs from the cached one means the module (and the
+  // array) may have been loaded again; with no context current yet, the
+  // runtime lookup below makes the device's primary context current
+  CtxGetCurrentFn get = ctx_get_current();
+  if (!get) {
+    err = "cuCtxGetCurrent is not available";
+    return nullptr;
+  }
+  CUcontext ctx = nullptr;
+  if (get(&ctx) != CUDA_SUCCESS) ctx = nullptr;
+  if (!ctx || !g_addr[dev] || g_ctx[dev] != ctx) {
     void* p = nullptr;
     e = cudaGetSymbolAddress(&p, g_scratch);
     if (e != cudaSuccess) {
       err = std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e);
       return nullptr;
     }
+    if (!ctx && (get(&ctx) != CUDA_SUCCESS || !ctx)) {
+      err = "no current CUDA context";
+      return nullptr;
+    }
     g_addr[dev] = (double*)p;
+    g_ctx[dev] = ctx;
   }
   return g_addr[dev];
 }

@@ -275,7 +275,7 @@ using namespace kfbi;
 
 namespace {
 struct StateBlobHeader {
-  char magic[8];  // "KFBIST1\0"
+  char magic[8];  // "KFBIST2\0" (2: the header carries w)
   int eq, planes, Mp, nb;
   int initialised, phi_zero, neumann, hist, ax_valid, ax_prev_valid, has_ax;
   double dt, theta, kre, kim, w;
@@ -573,7 +573,7 @@ kfbi_status kfbi_state_export(kfbi_state* S, void* host_buf, long long bytes) {
   }
   return guarded(S->dom, [&]() -> kfbi_status {
     StateBlobHeader h{};
-    std::memcpy(h.magic, "KFBIST1", 8);
+    std::memcpy(h.magic, "KFBIST2", 8);
     h.eq = S->eq;
     h.planes = S->planes;
     h.Mp = S->dom->Mp;
@@ -610,7 +610,7 @@ kfbi_status kfbi_state_import(kfbi_state* S, const void* host_buf, long long byt
   }
   StateBlobHeader h;
   std::memcpy(&h, host_buf, sizeof(h));
-  if (std::memcmp(h.magic, "KFBIST1", 8) != 0 || h.eq != S->eq || h.planes != S->planes ||
+  if (std::memcmp(h.magic, "KFBIST2", 8) != 0 || h.eq != S->eq || h.planes != S->planes ||
       h.Mp != S->dom->Mp || h.nb != S->dom->nb || h.has_ax != (S->d_ax != nullptr) ||
       bytes < kfbi_state_blob_bytes(S)) {
     S->dom->err = "state blob does not match this state (equation, grid, boundary nodes or "

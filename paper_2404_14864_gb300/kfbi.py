@@ -17,6 +17,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libkfbi.so")
 
 KFBI_OK = 0
+(KFBI_ERR_ARG, KFBI_ERR_GEOMETRY, KFBI_ERR_OOM, KFBI_ERR_NOT_CONVERGED, KFBI_ERR_NONFINITE,
+ KFBI_ERR_TIMEOUT, KFBI_ERR_CUDA, KFBI_ERR_UNSUPPORTED) = range(1, 9)
 STATUS_NAMES = {0: "KFBI_OK", 1: "KFBI_ERR_ARG", 2: "KFBI_ERR_GEOMETRY", 3: "KFBI_ERR_OOM",
                 4: "KFBI_ERR_NOT_CONVERGED", 5: "KFBI_ERR_NONFINITE", 6: "KFBI_ERR_TIMEOUT",
                 7: "KFBI_ERR_CUDA", 8: "KFBI_ERR_UNSUPPORTED"}
@@ -306,8 +308,21 @@ def kfbi_solve_density(h, kappa, b, phi, stream=None):
 
 
 def kfbi_box_solve_noalloc(M, box_lo, box_hi, kappa, rhs, u, stream=None):
-    """Box solve with no device allocation (static scratch, M - 1 <= 256)."""
+    """Box solve with no device allocation (static scratch, M - 1 <= 256).
+    rhs and u: contiguous CUDA tensors of (M - 1)^2 values, complex128 when
+    kappa has an imaginary part and float64 otherwise."""
+    import torch
     k = complex(kappa)
+    want = torch.complex128 if k.imag != 0.0 else torch.float64
+    n = (int(M) - 1) ** 2 if int(M) >= 2 else 0
+    for name, t in (("rhs", rhs), ("u", u)):
+        if t is None or not t.is_cuda or not t.is_contiguous():
+            raise KfbiError(KFBI_ERR_ARG, "%s must be a contiguous CUDA tensor" % name)
+        if t.dtype != want:
+            raise KfbiError(KFBI_ERR_ARG, "%s must be %s for kappa = %r" % (name, want, kappa))
+        if t.numel() != n:
+            raise KfbiError(KFBI_ERR_ARG, "%s must hold (M - 1)^2 = %d values, not %d"
+                            % (name, n, t.numel()))
     _check(lib().kfbi_box_solve_noalloc(int(M), float(box_lo), float(box_hi), k.real, k.imag,
                                         _ptr(rhs), _ptr(u), _stream(stream)))
 

@@ -73,3 +73,51 @@ def test_blob_of_another_state_is_refused():
         st.import_(blob[:100])
     other.close()
     dom.close()
+
+
+def test_resumed_nonlinear_schrodinger_batch_is_bitwise_identical():
+    """A w = 1 Schroedinger state (the paper's Ex. 5) stepped in a batch,
+    exported after 2 of 4 steps and imported into a fresh state on a fresh
+    domain, continues bit for bit: the blob carries w (set by
+    kfbi_state_set_w, which batched steps use)."""
+    import math
+    ex = W.NonlinearSchrodingerExact()
+    desc = W.domain_desc(64, W.ex5_star(0.2), lo=-math.pi, hi=math.pi)
+    X, Y = W.grid_xy(desc)
+    zx, zy = W.boundary_xy(desc)
+    tau = 0.125
+    V = dev(ex.v(X, Y))
+    g = [dev(ex.u(zx, zy, (k + 1) * tau)) for k in range(4)]
+
+    def fresh():
+        dom = kfbi.Domain(desc, kfbi.KFBI_MIXED_TF32, tol=1e-12, maxit=800)
+        st = kfbi.State(dom, kfbi.KFBI_SCHRODINGER)
+        st.init_schrodinger(tau, dev(ex.u(X, Y, 0)), dev(ex.lap(X, Y, 0)))
+        return dom, st, kfbi.Batch([dom])
+
+    dom, st, b = fresh()
+    st.set_w(ex.w)
+    for k in range(4):
+        b.step([st], [g[k]], [V])
+    u_ref = host(st.get_u())
+    b.close()
+    dom.close()
+    dom1, st1, b1 = fresh()
+    st1.set_w(ex.w)
+    for k in range(2):
+        b1.step([st1], [g[k]], [V])
+    blob = st1.export()
+    b1.close()
+    dom1.close()
+    dom2, st2, b2 = fresh()   # w is not set here: it comes with the blob
+    st2.import_(blob)
+    for k in range(2, 4):
+        b2.step([st2], [g[k]], [V])
+    assert np.array_equal(host(st2.get_u()), u_ref)
+    # the same run without w differs: the blob's w was used
+    dom3, st3, b3 = fresh()
+    for k in range(4):
+        b3.step([st3], [g[k]], [V])
+    assert not np.array_equal(host(st3.get_u()), u_ref)
+    for o in (b2, dom2, b3, dom3):
+        o.close()

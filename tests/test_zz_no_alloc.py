@@ -5,13 +5,17 @@ Its output must equal the grid solution of the existing entry point
 kfbi_interface_solve when that call's corrections vanish: density zero and
 a source that is zero on every irregular node and on the nodes its
 extrapolation of f reads, so the corrected right-hand side is the source
-itself.  Two calls in a row (real, then complex kappa) are checked, and an
-oversized grid is rejected.  This file is collected last on purpose.
+itself.  Two calls in a row (real, then complex kappa) are checked.  It is
+also compared with the oracle's box solve (the DST-I formula of Eq. 3.31
+written out in float64) at the smallest and the largest grid it takes and on
+a stream of its own, and grids outside 2 <= M <= 257 and wrongly typed
+tensors are rejected.  This file is collected last on purpose.
 """
 
 import numpy as np
 import pytest
 
+import oracle
 from paper_2404_14864_gb300 import kfbi, workloads as W
 from gpu_util import dev, ensure_built, host, rel_linf
 
@@ -52,10 +56,45 @@ def test_box_solve_noalloc_matches_interface_solve_twice():
     dom.close()
 
 
-def test_box_solve_noalloc_rejects_oversized_grid():
+@pytest.mark.parametrize("M", [2, 3, 130, 257])
+def test_box_solve_noalloc_matches_oracle_on_own_stream(M):
+    """Against the oracle's box solve, on a non-default stream: M = 2 (one
+    unknown, padded to 128) through M = 257 (the largest padded size, 256)."""
+    import torch
+    ensure_built()
+    rng = np.random.default_rng(M)
+    lo, hi = -1.0, 1.0
+    h = (hi - lo) / M
+    n1 = M - 1
+    st = torch.cuda.Stream()
+    for kappa in (2.0 / h, 3.0 + 2.0j / h):
+        cplx = isinstance(kappa, complex)
+        R = rng.standard_normal((n1, n1))
+        if cplx:
+            R = R + 1j * rng.standard_normal((n1, n1))
+        ref = oracle.box_solve(R, kappa, M, h)
+        f = dev(R.reshape(-1))
+        u = dev(np.zeros(n1 * n1, dtype=R.dtype))
+        torch.cuda.synchronize()
+        with torch.cuda.stream(st):
+            kfbi.kfbi_box_solve_noalloc(M, lo, hi, kappa, f, u, stream=st)
+        st.synchronize()
+        assert rel_linf(host(u).reshape(n1, n1), ref) <= TOL
+
+
+def test_box_solve_noalloc_rejects_bad_sizes_and_types():
     ensure_built()
     import torch
     f = torch.zeros(300 * 300, dtype=torch.float64, device="cuda")
     with pytest.raises(kfbi.KfbiError) as e:
         kfbi.kfbi_box_solve_noalloc(301, -1.0, 1.0, 10.0, f, f)
-    assert e.value.status == 1
+    assert e.value.status == kfbi.KFBI_ERR_ARG
+    one = torch.zeros(0, dtype=torch.float64, device="cuda")
+    with pytest.raises(kfbi.KfbiError) as e:
+        kfbi.kfbi_box_solve_noalloc(1, -1.0, 1.0, 10.0, one, one)
+    assert e.value.status == kfbi.KFBI_ERR_ARG
+    g = torch.zeros(15 * 15, dtype=torch.float64, device="cuda")
+    with pytest.raises(kfbi.KfbiError):   # complex kappa needs complex128 data
+        kfbi.kfbi_box_solve_noalloc(16, -1.0, 1.0, 1.0 + 2.0j, g, g)
+    with pytest.raises(kfbi.KfbiError):   # too few values
+        kfbi.kfbi_box_solve_noalloc(17, -1.0, 1.0, 10.0, g, g)
