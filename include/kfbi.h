@@ -60,12 +60,12 @@ typedef enum {
   KFBI_MIXED_TF32 = 1,  /* DST on tcgen05 tensor cores, TF32 split in 3
                            passes with FP32 accumulation; correction and
                            extraction in FP32; GMRES in FP64 */
-  KFBI_MIXED_FFT32 = 2  /* DST-I by FP32 FFT on the CUDA cores (M a power
-                           of two, 64 <= M <= 1024; otherwise
-                           KFBI_ERR_UNSUPPORTED at creation); correction,
-                           extraction, GMRES and refinement as
-                           KFBI_MIXED_TF32.  Single domains only: batches and
-                           the server take KFBI_MIXED_TF32 domains */
+  KFBI_MIXED_FFT32 = 2  /* DST-I by FP32 FFT on the CUDA cores (M = 32 N1,
+                           N1 in {2, 4, 6, 8, 12, 16, 24, 32, 48, 64}, i.e.
+                           64 <= M <= 2048 with M / 32 a power of two or
+                           three times one; otherwise KFBI_ERR_UNSUPPORTED at
+                           creation); correction, extraction, GMRES and
+                           refinement as KFBI_MIXED_TF32 */
 } kfbi_precision;
 
 typedef enum {
@@ -284,14 +284,17 @@ kfbi_status kfbi_state_get_phi(kfbi_state* st, void* phi_out_dev, void* stream);
 
 /* ---- batched time steps ------------------------------------------------- */
 
-/* A batch groups n KFBI_MIXED_TF32 domains of one device (any sizes and
- * curves, same gmres_restart) so that one time step of all of them runs as
- * grouped launches: the tcgen05 DST passes of every instance are one
- * persistent launch over all instances' tiles, every other kernel takes the
- * instance from its grid, and one lockstep GMRES iteration of the whole
+/* A batch groups n mixed-precision domains of one device (KFBI_MIXED_TF32
+ * and KFBI_MIXED_FFT32 in any mix; any sizes and curves, same
+ * gmres_restart) so that one time step of all of them runs as grouped
+ * launches (Sec. 3.4.2's box solve and Procedure 2's operator application
+ * for many instances at once): the tcgen05 DST passes of every TF32
+ * instance are one persistent launch over all their tiles, the FFT passes
+ * of the FFT32 instances one launch per grid size, every other kernel takes
+ * the instance from its grid, and one lockstep GMRES iteration of the whole
  * batch is a CUDA graph replayed until every instance has converged.  The
- * first step binds the states, runs the autotuner (tile order of the
- * grouped passes, timed with CUDA events) and captures the graph.
+ * first step binds the states, runs the autotuner (below) and captures the
+ * graph.
  * An instance's result does not depend on what it is batched with (same
  * bits alone or in any mix); against kfbi_step_* on its own domain it agrees
  * to the GMRES tolerance (reduction orders differ).
@@ -308,10 +311,41 @@ void kfbi_batch_destroy(kfbi_batch* batch);
 kfbi_status kfbi_batch_step(kfbi_batch* batch, kfbi_state* const* states,
                             const void* const* g_next_dev, const double* const* src_or_v_dev,
                             kfbi_solve_info* infos, void* stream);
-/* Autotuner result: chosen tile order (0 as given, 1 largest instances
- * first) and the measured microseconds of the grouped fast passes for each. */
+/* Autotuner result for the TF32 instances: chosen tile order (0 as given,
+ * 1 largest instances first) and the measured microseconds of the grouped
+ * fast passes for the first candidate of each order. */
 kfbi_status kfbi_batch_tuning(const kfbi_batch* batch, int* tile_order, double* us_natural,
                               double* us_largest_first);
+/* One autotuned group.  The autotuner times each candidate launch shape of
+ * a group on the group's fast application (the passes one GMRES iteration
+ * runs; CUDA events, one warm-up and three timed repetitions) and keeps the
+ * fastest:
+ *   engine 1: the FFT32 instances of grid size M; candidates: rows (warps)
+ *             per block of the FFT passes, param[c][0] in {8, 4};
+ *   engine 0: all TF32 instances; candidates: param[c][0] tile order (0 as
+ *             given, 1 largest first), param[c][1] persistent CTAs of the
+ *             tensor passes (one per SM, or half as many).
+ * No candidate changes the arithmetic of a tile or a row, so an instance's
+ * bits do not depend on the choice (split K, which would, follows the tile
+ * count: CTA pairs when a pass's tiles fill at most half of the SMs).
+ * FFT choices are cached per M and kept across rebinds; a grid size new to
+ * the batch is tuned at its first step. */
+typedef struct {
+  int engine;        /* 0 TF32 tensor passes, 1 FFT passes */
+  int M;             /* grid size of an FFT group (0 for TF32) */
+  int instances;     /* instances in the group */
+  int n_candidates;  /* candidates considered (at most 4) */
+  int chosen;        /* index of the kept candidate */
+  int param[4][2];   /* the candidates' launch parameters (see above) */
+  double us[4];      /* measured microseconds per candidate (0 when forced) */
+} kfbi_batch_tuning_t;
+int kfbi_batch_tuning_count(const kfbi_batch* batch);
+kfbi_status kfbi_batch_tuning_get(const kfbi_batch* batch, int i, kfbi_batch_tuning_t* out);
+/* candidate >= 0: skip the timing and use candidate (modulo each group's
+ * candidate count) in every group from the next step on, so that every
+ * configuration can be checked; -1 restores the autotuner.  KFBI_ERR_ARG
+ * for candidate < -1. */
+kfbi_status kfbi_batch_force_candidate(kfbi_batch* batch, int candidate);
 const char* kfbi_batch_last_error(const kfbi_batch* batch);
 
 /* ---- inspection and diagnostics ----------------------------------------- */
@@ -352,6 +386,11 @@ kfbi_status kfbi_profile_read(int cls, long long* launches, double* total_ms);
  * the classes whose launches count them (KFBI_PROF_DST: the executed dense
  * products of each pass, three TF32 products per pass on a mixed domain). */
 kfbi_status kfbi_profile_work(int cls, double* flops);
+/* Algorithmic bytes the recorded launches of a class move (counted by the
+ * launches that declare them: the FFT DST passes count the rows they read
+ * and write, 4 (M - 1) bytes per row each way; a first pass built from the
+ * irregular nodes counts only its writes). */
+kfbi_status kfbi_profile_bytes(int cls, double* bytes);
 
 /* Host-only plan: the geometry and coefficient tables kfbi_create_domain
  * uploads, built without touching the GPU, for inspection and tests. */
@@ -435,7 +474,9 @@ typedef struct {
 } kfbi_server_desc;
 
 typedef struct {
-  kfbi_domain_desc domain; /* precision KFBI_MIXED_TF32, gmres_restart = the server's */
+  kfbi_domain_desc domain; /* precision KFBI_MIXED_TF32 or KFBI_MIXED_FFT32 (M with an FFT
+                              pass, else KFBI_ERR_UNSUPPORTED at submission);
+                              gmres_restart = the server's */
   int equation;            /* kfbi_equation */
   int steps;               /* time steps, >= 1 */
   double dt;               /* time step */

@@ -19,7 +19,12 @@ INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(BUILD, "libkfbi.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC]
+# -ffp-contract=off: host arithmetic (geometry, tables) rounds every
+# operation as written, so the plan is the same on x86-64 and aarch64 (GCC
+# fuses a * b + c into one FMA by default where the ISA has it, which moved
+# near-tie node classifications on aarch64 hosts).
+COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
+          "-I" + INCLUDE, "-I" + CSRC]
 
 
 def _nvcc():

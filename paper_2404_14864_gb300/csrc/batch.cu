@@ -18,6 +18,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <map>
 #include <numeric>
 #include <vector>
 
@@ -32,6 +33,7 @@ using tc::PassDesc;
 // Everything a grouped kernel needs about one instance.
 struct GInst {
   int Mp, n1, nb, n_irr, n_arms, M, m, C, eq;
+  int fft;  // KFBI_MIXED_FFT32 instance: FFT passes on single FP32 planes (Rh, T1h, T2h, U32)
   int rmin, nrows;
   double h, kre, kim, scale, dt, theta;
   double w;  // Schroedinger: nonlinear coefficient of the B step (Eq. 3.10)
@@ -67,6 +69,7 @@ struct GInst {
   double* U64;
   float* Rh;
   float* Rl;
+  float* T1h;
   float* T2h;
   float* T2l;
   float* U32;
@@ -228,6 +231,10 @@ __global__ void gk_split64(const GInst* gi) {
     for (int p = 0; p < P; ++p) {
       const size_t i = p * plane + idx;
       const double x = I.R64[i];
+      if (I.fft) {  // FFT passes read one FP32 plane
+        I.Rh[i] = (float)x;
+        continue;
+      }
       const float h = tf32r((float)x);
       I.Rh[i] = h;
       I.Rl[i] = tf32r((float)(x - (double)h));
@@ -241,7 +248,7 @@ __global__ void gk_eig_cplx(const GInst* gi) {
   KFBI_PDL_ENTRY();
   const GInst& I = gi[blockIdx.y];
   ACTIVE_OR_RETURN(I);
-  if (!I.C) return;
+  if (!I.C || I.fft) return;  // the FFT solve pass divides by the eigenvalues itself
   const size_t plane = (size_t)I.Mp * I.Mp;
   const float kre = (float)I.kre, kim = (float)I.kim, scale = (float)I.scale;
   INST_PLANE_LOOP(I) {
@@ -295,6 +302,10 @@ __global__ void gk_resid_split(const GInst* gi) {
           Lu += (p == 0) ? I.kim * uo : -I.kim * uo;
         }
         res = I.R64[p * plane + idx] - Lu;
+      }
+      if (I.fft) {
+        I.Rh[p * plane + idx] = (float)res;
+        continue;
       }
       const float h = tf32r((float)res);
       I.Rh[p * plane + idx] = h;
@@ -374,6 +385,7 @@ __global__ void gk_correct32_rv(const GInst* gi, const int* dj) {
   KFBI_PDL_ENTRY();
   const GInst& I = gi[blockIdx.y];
   ACTIVE_OR_RETURN(I);
+  if (I.fft) return;  // FFT instances build these rows inside their first pass
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= I.n_irr) return;
   const double* phi = (const double*)(I.V + (size_t)(*dj) * I.nb);
@@ -413,6 +425,7 @@ __global__ void __launch_bounds__(256) gk_sparse_p1(const GInst* gi) {
   KFBI_PDL_ENTRY();
   const GInst& I = gi[blockIdx.z];
   ACTIVE_OR_RETURN(I);
+  if (I.fft) return;
   const int Mp = I.Mp;
   const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
   if (c0 >= Mp || r0 >= I.nrows) return;
@@ -449,6 +462,8 @@ __global__ void __launch_bounds__(256) gk_sparse_p1(const GInst* gi) {
 }
 
 // Gather of the stencil values and extraction (as k_gather_extract) into W.
+// TF32 instances leave the last pass's input with rows = x indices; FFT
+// instances (solve pass written transposed) with rows = y indices.
 __global__ void __launch_bounds__(192) gk_gather_extract(const GInst* gi, const int* dj) {
   KFBI_PDL_ENTRY();
   const GInst& I = gi[blockIdx.y];
@@ -464,8 +479,8 @@ __global__ void __launch_bounds__(192) gk_gather_extract(const GInst* gi, const 
   {
     const int off = I.node_gidx[warp * nb + k];
     const int jr = off / Mp, ic = off - jr * Mp;
-    const float* t0 = I.U32 + (size_t)ic * Mp;
-    const float* sr = I.S32 + (size_t)jr * Mp;
+    const float* t0 = I.U32 + (size_t)(I.fft ? jr : ic) * Mp;
+    const float* sr = I.S32 + (size_t)(I.fft ? ic : jr) * Mp;
     float s0 = 0.f, s1 = 0.f;
     for (int a = lane; a < Mp; a += 32) {
       const float sv = sr[a];
@@ -1026,10 +1041,30 @@ struct kfbi_batch {
   double pass_work[kPassKinds] = {0};  // tensor flops of a pass over all instances
   int max_n_irr = 1, max_nb = 1, max_Mp = 128, max_nrows = 1, max_planes_blocks = 1;
   bool bound = false;
+  // FFT32 instances: per pass kind one grouped launch per distinct M
+  enum { kFftDense1, kFftSolve, kFftFinal, kFftSparse1, kFftSolveS, kFftKinds };
+  struct FftPassGroup {
+    int M = 0, nblocks = 0, rpb = 8;
+    bool sparse = false;
+    size_t smem = 0;
+    double flops = 0.0, bytes = 0.0;
+    FftDesc* d_desc = nullptr;
+    int2* d_blk = nullptr;
+    int cap_desc = 0, cap_blk = 0;
+  };
+  std::vector<FftPassGroup> fg[kFftKinds];
+  std::vector<int> fft_ms;     // distinct M of the FFT instances
+  std::vector<int> fft_rpb;    // rows per block of each M's passes
+  std::map<int, int> rpb_of_M;  // autotuned rows per block, kept across rebinds
+  std::vector<kfbi_batch_tuning_t> tuning;  // one record per tuned group
+  int force = -1;               // >= 0: use this candidate everywhere, no timing
+  std::vector<long long> fft_sig;  // launch shapes baked into the captured graph
+  int n_fft = 0, n_tc = 0;
   // autotuned launch shape of the grouped passes (CTAs per SM multiple,
   // tile order) and the CUDA graph of one lockstep GMRES iteration
   int tile_order = 0;  // 0: instances in given order, 1: largest first
   int splitk = 0;      // grouped passes: 0 from the tile count, 1, or 2 (CTA pairs)
+  int cta_cap = 0;     // persistent CTAs of a pass without pairs: 0 one per SM, else this many
   bool tuned = false;  // the autotuner ran (its choice is kept across rebinds)
   cudaGraphExec_t iter_graph = nullptr;
   cudaStream_t graph_stream = nullptr;
@@ -1043,13 +1078,22 @@ namespace {
 
 dim3 inst_grid(int nblocks_x, int n) { return dim3((unsigned)std::max(1, nblocks_x), (unsigned)n); }
 
+void build_fft_passes(kfbi_batch* B);
+
 void build_passes(kfbi_batch* B) {
-  // per-instance descriptors for the dense and sparse passes (kappa fixed by the states)
+  build_fft_passes(B);
+  // per-instance descriptors for the dense and sparse tensor passes of the
+  // TF32 instances (kappa fixed by the states)
+  std::vector<int> tci;
+  for (int i = 0; i < B->n; ++i)
+    if (!B->h_inst[i].fft) tci.push_back(i);
+  B->n_tc = (int)tci.size();
   for (int kind = 0; kind < kfbi_batch::kPassKinds; ++kind) {
-    std::vector<PassDesc> ds(B->n);
-    std::vector<int> pref(B->n + 1, 0);
-    for (int ii = 0; ii < B->n; ++ii) {
-      const int i = ii;  // tile order is applied by the permutation below
+    const int nt = B->n_tc;
+    std::vector<PassDesc> ds(nt);
+    std::vector<int> pref(nt + 1, 0);
+    for (int ii = 0; ii < nt; ++ii) {
+      const int i = tci[ii];  // tile order is applied by the permutation below
       kfbi_domain* D = B->doms[i];
       TcDst* T = D->tc;
       const GInst& I = B->h_inst[i];
@@ -1093,39 +1137,175 @@ void build_passes(kfbi_batch* B) {
       }
       d.o_hi = tc_out_map(T, d.out_hi);
       d.o_lo = d.out_lo ? tc_out_map(T, d.out_lo) : nullptr;
-      ds[i] = d;
+      ds[ii] = d;
     }
     // tile order: optionally largest instances first (longest-processing-time
     // first keeps the persistent CTAs balanced)
-    std::vector<int> order(B->n);
+    std::vector<int> order(nt);
     std::iota(order.begin(), order.end(), 0);
     if (B->tile_order == 1)
       std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
         return (long long)ds[a].nk * ds[a].nct * ds[a].nrt > (long long)ds[b].nk * ds[b].nct * ds[b].nrt;
       });
-    std::vector<PassDesc> ordered(B->n);
-    for (int ii = 0; ii < B->n; ++ii) {
+    std::vector<PassDesc> ordered(nt);
+    for (int ii = 0; ii < nt; ++ii) {
       ordered[ii] = ds[order[ii]];
       pref[ii + 1] = pref[ii] + ordered[ii].nct * ordered[ii].nrt;
     }
-    B->total[kind] = pref[B->n];
+    B->total[kind] = pref[nt];
     B->pass_work[kind] = 0.0;
-    for (int ii = 0; ii < B->n; ++ii) B->pass_work[kind] += tc::pass_flops(ordered[ii]);
-    KFBI_CUDA(cudaMemcpy(B->d_pass[kind], ordered.data(), sizeof(PassDesc) * B->n, cudaMemcpyHostToDevice));
-    KFBI_CUDA(cudaMemcpy(B->d_prefix[kind], pref.data(), sizeof(int) * (B->n + 1), cudaMemcpyHostToDevice));
+    for (int ii = 0; ii < nt; ++ii) B->pass_work[kind] += tc::pass_flops(ordered[ii]);
+    if (nt > 0) {
+      KFBI_CUDA(cudaMemcpy(B->d_pass[kind], ordered.data(), sizeof(PassDesc) * nt, cudaMemcpyHostToDevice));
+      KFBI_CUDA(cudaMemcpy(B->d_prefix[kind], pref.data(), sizeof(int) * (nt + 1), cudaMemcpyHostToDevice));
+    }
   }
 }
 
+// Descriptors and block maps of the FFT instances' grouped passes: for each
+// pass kind, one group per distinct M (one launch each), blocks of every
+// instance of that size in instance order.  A change of launch shape (block
+// count, rows per block, shared memory) invalidates the captured iteration
+// graph.
+void build_fft_passes(kfbi_batch* B) {
+  std::vector<int> ms;
+  for (int i = 0; i < B->n; ++i)
+    if (B->h_inst[i].fft) ms.push_back(B->h_inst[i].M);
+  std::sort(ms.begin(), ms.end());
+  ms.erase(std::unique(ms.begin(), ms.end()), ms.end());
+  B->fft_ms = ms;
+  B->fft_rpb.assign(ms.size(), 8);
+  for (size_t gi = 0; gi < ms.size(); ++gi) {
+    auto it = B->rpb_of_M.find(ms[gi]);
+    // untuned: 8 rows per block where a complex solve still fits, else 4
+    B->fft_rpb[gi] = it != B->rpb_of_M.end() ? it->second : (fft_rpb_fits(ms[gi], 8, 2) ? 8 : 4);
+  }
+  B->n_fft = 0;
+  for (int i = 0; i < B->n; ++i) B->n_fft += B->h_inst[i].fft ? 1 : 0;
+  std::vector<long long> sig;
+  for (int kind = 0; kind < kfbi_batch::kFftKinds; ++kind) {
+    auto& groups = B->fg[kind];
+    groups.resize(ms.size());
+    for (size_t gi = 0; gi < ms.size(); ++gi) {
+      kfbi_batch::FftPassGroup& g = groups[gi];
+      g.M = ms[gi];
+      g.sparse = kind == kfbi_batch::kFftSparse1;
+      int rpb = B->fft_rpb[gi];
+      std::vector<FftDesc> ds;
+      std::vector<int2> blk;
+      double flops = 0.0, bytes = 0.0;
+      int pw_max = 1;
+      for (int i = 0; i < B->n; ++i) {
+        const GInst& I = B->h_inst[i];
+        if (!I.fft || I.M != g.M) continue;
+        kfbi_domain* D = B->doms[i];
+        TcDst* T = D->tc;
+        const int P = I.C ? 2 : 1;
+        const float kre = (float)I.kre, kim = (float)I.kim, scale = (float)I.scale;
+        FftDesc d{};
+        switch (kind) {
+          case kfbi_batch::kFftDense1:
+            d = fft_desc(T, T->Rh, T->T1h, P, false, 0.f, 0.f, 0.f, nullptr, nullptr, rpb);
+            break;
+          case kfbi_batch::kFftSolve:
+            d = fft_desc(T, T->T1h, T->T2h, P, true, kre, kim, scale, nullptr, nullptr, rpb);
+            break;
+          case kfbi_batch::kFftFinal:
+            d = fft_desc(T, T->T2h, T->U, P, false, 0.f, 0.f, 0.f, nullptr, nullptr, rpb);
+            d.transpose = 0;
+            break;
+          case kfbi_batch::kFftSparse1: {
+            FftSparseRhs sp{};
+            sp.row_start = T->row_start;
+            sp.node_col = T->node_col;
+            sp.arm_col = T->arm_col;
+            sp.rmin = T->rmin;
+            sp.nrows = T->nrows;
+            sp.arm_start = D->d_arm_start;
+            sp.arm_k0 = D->d_arm_k0;
+            sp.alpha = D->d_arm_alpha32;
+            sp.beta = D->d_arm_beta32;
+            sp.n_arms = D->n_arms;
+            sp.nb = D->nb;
+            sp.phi = (const double*)I.V;  // V[*dj]: the Arnoldi vector of the iteration
+            sp.ps = 2;
+            sp.kre = kre;
+            sp.kim = kim;
+            sp.cplx = I.C;
+            sp.dj = B->d_j;
+            sp.dj_stride = 2LL * I.nb;
+            d = fft_desc(T, nullptr, T->T1sh, P, false, 0.f, 0.f, 0.f, nullptr, &sp, rpb);
+            break;
+          }
+          default:  // kFftSolveS
+            d = fft_desc(T, T->T1sh, T->U, P, true, kre, kim, scale, nullptr, nullptr, rpb);
+            break;
+        }
+        d.active = B->d_flags + 4 * i;
+        const int li = (int)ds.size();
+        for (int b = 0; b < fft_blocks(d); ++b) blk.push_back(make_int2(li, b));
+        flops += fft_desc_flops(d, rpb);
+        bytes += fft_desc_bytes(d, rpb);
+        pw_max = std::max(pw_max, d.pw);
+        ds.push_back(d);
+      }
+      g.rpb = rpb;
+      g.nblocks = (int)blk.size();
+      g.smem = fft_smem(g.M, rpb, pw_max);
+      g.flops = flops;
+      g.bytes = bytes;
+      if ((int)ds.size() > g.cap_desc) {
+        if (g.d_desc) KFBI_CUDA(cudaFree(g.d_desc));
+        KFBI_CUDA(cudaMalloc(&g.d_desc, ds.size() * sizeof(FftDesc)));
+        g.cap_desc = (int)ds.size();
+      }
+      if ((int)blk.size() > g.cap_blk) {
+        if (g.d_blk) KFBI_CUDA(cudaFree(g.d_blk));
+        KFBI_CUDA(cudaMalloc(&g.d_blk, blk.size() * sizeof(int2)));
+        g.cap_blk = (int)blk.size();
+      }
+      if (!ds.empty())
+        KFBI_CUDA(cudaMemcpy(g.d_desc, ds.data(), ds.size() * sizeof(FftDesc), cudaMemcpyHostToDevice));
+      if (!blk.empty())
+        KFBI_CUDA(cudaMemcpy(g.d_blk, blk.data(), blk.size() * sizeof(int2), cudaMemcpyHostToDevice));
+      sig.insert(sig.end(), {(long long)g.M, (long long)g.nblocks, (long long)g.rpb, (long long)g.smem,
+                             (long long)(uintptr_t)g.d_desc, (long long)(uintptr_t)g.d_blk});
+    }
+  }
+  if (sig != B->fft_sig) {
+    B->fft_sig = sig;
+    if (B->iter_graph) {
+      KFBI_CUDA(cudaGraphExecDestroy(B->iter_graph));
+      B->iter_graph = nullptr;
+    }
+  }
+}
+
+void fft_group_launch(const kfbi_batch::FftPassGroup& g, int kind, cudaStream_t st) {
+  if (g.nblocks == 0) return;
+  FftGroup ga{};
+  ga.descs = g.d_desc;
+  ga.blk = g.d_blk;
+  ga.rpb = g.rpb;
+  fft_launch(ga, g.M, g.sparse, g.nblocks, g.smem,
+             kind == kfbi_batch::kFftSparse1 ? KFBI_PROF_SPARSE : KFBI_PROF_DST, g.flops, g.bytes, st);
+}
+
+void fft_grouped(kfbi_batch* B, int kind, cudaStream_t st) {
+  for (const kfbi_batch::FftPassGroup& g : B->fg[kind]) fft_group_launch(g, kind, st);
+}
+
 void grouped_pass(kfbi_batch* B, int kind, cudaStream_t st) {
+  if (B->n_tc == 0) return;
   GroupArgs ga;
   ga.descs = B->d_pass[kind];
   ga.prefix = B->d_prefix[kind];
-  ga.n_inst = B->n;
+  ga.n_inst = B->n_tc;
   ga.total = B->total[kind];
   ga.one = PassDesc{};
   ga.err = B->doms[0]->tc->err;
   ga.splitk = B->splitk;
-  tc::launch_tc_pass(ga, B->nsm, B->pass_work[kind], st);
+  tc::launch_tc_pass(ga, B->nsm, B->pass_work[kind], st, B->cta_cap);
 }
 
 int plane_blocks(kfbi_batch* B) { return B->max_planes_blocks; }
@@ -1140,11 +1320,18 @@ void batch_accurate(kfbi_batch* B, int which, int with_ft, int target, cudaStrea
                 B->d_inst, which, with_ft, (const int*)nullptr);
   KFBI_LAUNCH_P(KFBI_PROF_GRID, gk_split64, inst_grid(pb, n), 256, 0, st, B->d_inst);
   for (int sweep = 0; sweep < 2; ++sweep) {
-    grouped_pass(B, kfbi_batch::kDense1, st);
-    grouped_pass(B, kfbi_batch::kDense2, st);
-    KFBI_LAUNCH_P(KFBI_PROF_GRID, gk_eig_cplx, inst_grid(pb, n), 256, 0, st, B->d_inst);
-    grouped_pass(B, kfbi_batch::kDense3, st);
-    grouped_pass(B, kfbi_batch::kDense4, st);
+    if (B->n_tc > 0) {
+      grouped_pass(B, kfbi_batch::kDense1, st);
+      grouped_pass(B, kfbi_batch::kDense2, st);
+      KFBI_LAUNCH_P(KFBI_PROF_GRID, gk_eig_cplx, inst_grid(pb, n), 256, 0, st, B->d_inst);
+      grouped_pass(B, kfbi_batch::kDense3, st);
+      grouped_pass(B, kfbi_batch::kDense4, st);
+    }
+    if (B->n_fft > 0) {
+      fft_grouped(B, kfbi_batch::kFftDense1, st);
+      fft_grouped(B, kfbi_batch::kFftSolve, st);
+      fft_grouped(B, kfbi_batch::kFftFinal, st);
+    }
     if (sweep == 0) {
       KFBI_LAUNCH_P(KFBI_PROF_GRID, gk_f32_to_f64, inst_grid(pb, n), 256, 0, st, B->d_inst);
       KFBI_LAUNCH_P(KFBI_PROF_GRID, gk_resid_split, inst_grid(pb, n), 256, 0, st, B->d_inst);
@@ -1157,18 +1344,33 @@ void batch_accurate(kfbi_batch* B, int which, int with_ft, int target, cudaStrea
   KFBI_CHECK_LAUNCH();
 }
 
+// W = A_fast V[j] for every active instance: the sparse route (TF32
+// instances: correction values, CUDA-core first pass, two restricted tensor
+// passes; FFT instances: first pass built from the arms, solve pass), then
+// the gather at the stencil points with the extraction.
+void fast_apply(kfbi_batch* B, cudaStream_t st) {
+  const int n = B->n;
+  if (B->n_tc > 0) {
+    KFBI_LAUNCH_P(KFBI_PROF_CORRECT, gk_correct32_rv, inst_grid((B->max_n_irr + 127) / 128, n), 128, 0,
+                  st, B->d_inst, (const int*)B->d_j);
+    KFBI_LAUNCH_P(KFBI_PROF_SPARSE, gk_sparse_p1, dim3(B->max_Mp / 32, (B->max_nrows + 31) / 32, n),
+                  dim3(32, 8), 0, st, B->d_inst);
+    grouped_pass(B, kfbi_batch::kSparse2, st);
+    KFBI_LAUNCH_P(KFBI_PROF_GRID, gk_eig_cplx, inst_grid(plane_blocks(B), n), 256, 0, st, B->d_inst);
+    grouped_pass(B, kfbi_batch::kSparse3, st);
+  }
+  if (B->n_fft > 0) {
+    fft_grouped(B, kfbi_batch::kFftSparse1, st);
+    fft_grouped(B, kfbi_batch::kFftSolveS, st);
+  }
+  KFBI_LAUNCH_P(KFBI_PROF_EXTRACT, gk_gather_extract, inst_grid(B->max_nb, n), 192, 0, st, B->d_inst,
+                (const int*)B->d_j);
+}
+
 // one lockstep GMRES iteration: W = A_fast V[j], CGS2 Arnoldi, j += 1
 void batch_iteration(kfbi_batch* B, cudaStream_t st) {
   const int n = B->n;
-  KFBI_LAUNCH_P(KFBI_PROF_CORRECT, gk_correct32_rv, inst_grid((B->max_n_irr + 127) / 128, n), 128, 0,
-                st, B->d_inst, (const int*)B->d_j);
-  KFBI_LAUNCH_P(KFBI_PROF_SPARSE, gk_sparse_p1, dim3(B->max_Mp / 32, (B->max_nrows + 31) / 32, n),
-                dim3(32, 8), 0, st, B->d_inst);
-  grouped_pass(B, kfbi_batch::kSparse2, st);
-  KFBI_LAUNCH_P(KFBI_PROF_GRID, gk_eig_cplx, inst_grid(plane_blocks(B), n), 256, 0, st, B->d_inst);
-  grouped_pass(B, kfbi_batch::kSparse3, st);
-  KFBI_LAUNCH_P(KFBI_PROF_EXTRACT, gk_gather_extract, inst_grid(B->max_nb, n), 192, 0, st, B->d_inst,
-                (const int*)B->d_j);
+  fast_apply(B, st);
   KFBI_LAUNCH_P(KFBI_PROF_KRYLOV, gk_cgs_dots, inst_grid(GMAX, n), GT, 0, st, B->d_inst,
                 (const int*)B->d_j);
   KFBI_LAUNCH_P(KFBI_PROF_KRYLOV, gk_cgs_update, inst_grid(GMAX, n), GT, 0, st, B->d_inst,
@@ -1255,8 +1457,8 @@ void batch_bind(kfbi_batch* B, kfbi_domain* const* domains, int n) {
     if (!domains[i] || !domains[i]->tc || domains[i]->n_irr == 0 ||
         domains[i]->restart != domains[0]->restart || domains[i]->desc.solver != KFBI_GMRES)
       throw Status{KFBI_ERR_ARG,
-                   "every domain of a batch must be KFBI_MIXED_TF32 with an interface, the "
-                   "GMRES solver and the same gmres_restart"};
+                   "every domain of a batch must be KFBI_MIXED_TF32 or KFBI_MIXED_FFT32 with an "
+                   "interface, the GMRES solver and the same gmres_restart"};
   batch_reserve(B, n);
   if (B->iter_graph) {
     KFBI_CUDA(cudaGraphExecDestroy(B->iter_graph));
@@ -1306,6 +1508,11 @@ void kfbi_batch_destroy(kfbi_batch* B) {
     if (B->d_pass[k]) cudaFree(B->d_pass[k]);
     if (B->d_prefix[k]) cudaFree(B->d_prefix[k]);
   }
+  for (int k = 0; k < kfbi_batch::kFftKinds; ++k)
+    for (auto& g : B->fg[k]) {
+      if (g.d_desc) cudaFree(g.d_desc);
+      if (g.d_blk) cudaFree(g.d_blk);
+    }
   void* ps[] = {B->d_inst, B->d_flags, B->d_j, B->d_sel, B->d_scal_all, B->d_tol};
   for (void* p : ps)
     if (p) cudaFree(p);
@@ -1331,6 +1538,7 @@ void fill_instances(kfbi_batch* B, kfbi_state* const* states, const void* const*
     TcDst* T = D->tc;
     GInst I{};
     I.Mp = D->Mp; I.n1 = D->n1; I.nb = D->nb; I.n_irr = D->n_irr; I.n_arms = D->n_arms;
+    I.fft = T->fft ? 1 : 0; I.T1h = T->T1h;
     I.M = D->M; I.m = D->restart; I.C = S->kim != 0.0; I.eq = S->eq;
     I.rmin = T->rmin; I.nrows = T->nrows;
     I.h = D->h; I.kre = S->kre; I.kim = S->kim; I.scale = (2.0 / D->M) * (2.0 / D->M);
@@ -1454,15 +1662,7 @@ kfbi_status batch_gmres(kfbi_batch* B, kfbi_solve_info* infos, cudaStream_t st) 
         // restart: W = A_fast Dv (Dv staged in V[0]) then r = Rv - W
         KFBI_CUDA(cudaMemsetAsync(B->d_j, 0, sizeof(int), st));
         KFBI_LAUNCH_P(KFBI_PROF_KRYLOV, gk_dv_to_v0, inst_grid(8, n), 256, 0, st, B->d_inst);
-        KFBI_LAUNCH_P(KFBI_PROF_CORRECT, gk_correct32_rv, inst_grid((B->max_n_irr + 127) / 128, n), 128, 0,
-                      st, B->d_inst, (const int*)B->d_j);
-        KFBI_LAUNCH_P(KFBI_PROF_SPARSE, gk_sparse_p1, dim3(B->max_Mp / 32, (B->max_nrows + 31) / 32, n),
-                      dim3(32, 8), 0, st, B->d_inst);
-        grouped_pass(B, kfbi_batch::kSparse2, st);
-        KFBI_LAUNCH_P(KFBI_PROF_GRID, gk_eig_cplx, inst_grid(plane_blocks(B), n), 256, 0, st, B->d_inst);
-        grouped_pass(B, kfbi_batch::kSparse3, st);
-        KFBI_LAUNCH_P(KFBI_PROF_EXTRACT, gk_gather_extract, inst_grid(B->max_nb, n), 192, 0, st,
-                      B->d_inst, (const int*)B->d_j);
+        fast_apply(B, st);
       }
       KFBI_LAUNCH_P(KFBI_PROF_KRYLOV, gk_restart, inst_grid(1, n), 1024, 0, st, B->d_inst,
                     first_cycle ? 0 : 1);
@@ -1573,33 +1773,125 @@ void capture_iteration(kfbi_batch* B) {
   g_launches.fetch_sub(B->launches);
 }
 
-// Autotuner: time the grouped fast application with the two tile orders
-// (instances as given, largest first) and keep the faster one.
+// Autotuner.  The candidates of each group are timed on the group's fast
+// application (the passes a GMRES iteration runs) with CUDA events: one
+// warm-up and three timed repetitions, the fastest kept.
+//  - FFT instances, one group per grid size M: rows (warps) per block of the
+//    FFT passes, 8 or 4 (4 only where a complex solve does not fit 8); the
+//    choice is cached per M and kept across rebinds.
+//  - TF32 instances (all sizes in one persistent launch per pass): tile
+//    order (instances as given, or largest first) x persistent CTAs (one per
+//    SM, or half as many taking twice the tiles each).  Split K stays with
+//    the tile-count rule of launch_tc_pass: CTA pairs change the order in
+//    which a tile's K range is summed, and a timed choice could then give an
+//    instance other bits in another batch.  Every candidate of both engines
+//    leaves each tile's and each row's arithmetic unchanged.
+// B->force >= 0 skips the timing and takes that candidate (modulo the
+// group's candidate count) for every group, so every configuration can be
+// checked for correctness.
+double time_ms(cudaEvent_t e0, cudaEvent_t e1) {
+  float ms = 0.f;
+  KFBI_CUDA(cudaEventSynchronize(e1));
+  KFBI_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+  return ms;
+}
+
 void autotune(kfbi_batch* B, cudaStream_t st) {
   cudaEvent_t e0, e1;
   KFBI_CUDA(cudaEventCreate(&e0));
   KFBI_CUDA(cudaEventCreate(&e1));
   std::vector<int> all(B->n, 1), zero(B->n, 0);
-  for (int order = 0; order < 2; ++order) {
-    B->tile_order = order;
-    build_passes(B);
-    set_active(B, all, &zero, st);
-    KFBI_CUDA(cudaMemsetAsync(B->d_j, 0, sizeof(int), st));
-    // one warm-up and three timed passes over the two grouped fast passes
-    grouped_pass(B, kfbi_batch::kSparse2, st);
-    KFBI_CUDA(cudaEventRecord(e0, st));
-    for (int r = 0; r < 3; ++r) {
-      grouped_pass(B, kfbi_batch::kSparse2, st);
-      grouped_pass(B, kfbi_batch::kSparse3, st);
-    }
-    KFBI_CUDA(cudaEventRecord(e1, st));
-    KFBI_CUDA(cudaEventSynchronize(e1));
-    float ms = 0.f;
-    KFBI_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-    B->tuned_us[order] = 1e3 * ms / 3.0;
-  }
-  B->tile_order = B->tuned_us[1] < B->tuned_us[0] ? 1 : 0;
+  B->tuning.clear();
+  const bool prof = g_prof_on;
+  g_prof_on = false;  // tuning launches are not part of any profile
   build_passes(B);
+  set_active(B, all, &zero, st);
+  KFBI_CUDA(cudaMemsetAsync(B->d_j, 0, sizeof(int), st));
+  // FFT groups
+  for (size_t gi = 0; gi < B->fft_ms.size(); ++gi) {
+    const int M = B->fft_ms[gi];
+    kfbi_batch_tuning_t rec{};
+    rec.engine = 1;
+    rec.M = M;
+    for (int i = 0; i < B->n; ++i) rec.instances += B->h_inst[i].fft && B->h_inst[i].M == M ? 1 : 0;
+    const int cand[2] = {8, 4};
+    for (int c = 0; c < 2; ++c) {
+      // a complex solve needs room for both planes' rows
+      if (!fft_rpb_fits(M, cand[c], 2)) continue;
+      rec.param[rec.n_candidates][0] = cand[c];
+      rec.us[rec.n_candidates] = 0.0;
+      ++rec.n_candidates;
+    }
+    if (B->force >= 0) {
+      rec.chosen = B->force % rec.n_candidates;
+    } else {
+      for (int c = 0; c < rec.n_candidates; ++c) {
+        B->rpb_of_M[M] = rec.param[c][0];
+        build_fft_passes(B);
+        const auto& g1 = B->fg[kfbi_batch::kFftSparse1][gi];
+        const auto& g2 = B->fg[kfbi_batch::kFftSolveS][gi];
+        fft_group_launch(g1, kfbi_batch::kFftSparse1, st);
+        fft_group_launch(g2, kfbi_batch::kFftSolveS, st);
+        KFBI_CUDA(cudaEventRecord(e0, st));
+        for (int r = 0; r < 3; ++r) {
+          fft_group_launch(g1, kfbi_batch::kFftSparse1, st);
+          fft_group_launch(g2, kfbi_batch::kFftSolveS, st);
+        }
+        KFBI_CUDA(cudaEventRecord(e1, st));
+        rec.us[c] = 1e3 * time_ms(e0, e1) / 3.0;
+      }
+      rec.chosen = 0;
+      for (int c = 1; c < rec.n_candidates; ++c)
+        if (rec.us[c] < rec.us[rec.chosen]) rec.chosen = c;
+    }
+    B->rpb_of_M[M] = rec.param[rec.chosen][0];
+    B->tuning.push_back(rec);
+  }
+  // TF32 instances
+  if (B->n_tc > 0) {
+    kfbi_batch_tuning_t rec{};
+    rec.engine = 0;
+    rec.M = 0;
+    rec.instances = B->n_tc;
+    for (int order = 0; order < 2; ++order)
+      for (int half = 0; half < 2; ++half) {
+        rec.param[rec.n_candidates][0] = order;
+        rec.param[rec.n_candidates][1] = half ? B->nsm / 2 : B->nsm;
+        ++rec.n_candidates;
+      }
+    if (B->force >= 0) {
+      rec.chosen = B->force % rec.n_candidates;
+    } else {
+      for (int c = 0; c < rec.n_candidates; ++c) {
+        B->tile_order = rec.param[c][0];
+        B->cta_cap = rec.param[c][1];
+        build_passes(B);
+        grouped_pass(B, kfbi_batch::kSparse2, st);
+        KFBI_CUDA(cudaEventRecord(e0, st));
+        for (int r = 0; r < 3; ++r) {
+          grouped_pass(B, kfbi_batch::kSparse2, st);
+          grouped_pass(B, kfbi_batch::kSparse3, st);
+        }
+        KFBI_CUDA(cudaEventRecord(e1, st));
+        rec.us[c] = 1e3 * time_ms(e0, e1) / 3.0;
+      }
+      rec.chosen = 0;
+      for (int c = 1; c < rec.n_candidates; ++c)
+        if (rec.us[c] < rec.us[rec.chosen]) rec.chosen = c;
+    }
+    B->tile_order = rec.param[rec.chosen][0];
+    B->cta_cap = rec.param[rec.chosen][1];
+    B->tuned_us[0] = rec.us[0];
+    B->tuned_us[1] = rec.n_candidates > 1 ? rec.us[rec.n_candidates / 2] : 0.0;
+    B->tuning.push_back(rec);
+  }
+  g_prof_on = prof;
+  build_passes(B);
+  // launch shapes baked into the captured iteration may have changed
+  if (B->iter_graph) {
+    KFBI_CUDA(cudaGraphExecDestroy(B->iter_graph));
+    B->iter_graph = nullptr;
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
 }
@@ -1630,18 +1922,25 @@ kfbi_status batch_step(kfbi_batch* B, kfbi_state* const* states, const void* con
   kfbi_status s = guarded(nullptr, [&]() -> kfbi_status {
     B->states.assign(states, states + B->n);
     fill_instances(B, states, g_next, src_or_v, src_scale);
-    if (!B->bound) {
-      if (!B->tuned) {
+    if (!B->bound || !B->tuned) {
+      // tune what has no choice yet: the TF32 instances once, and each FFT
+      // grid size the first time it appears (choices are kept across
+      // rebinds)
+      bool need = !B->tuned;
+      for (int i = 0; i < B->n && !need; ++i)
+        need = B->h_inst[i].fft && !B->rpb_of_M.count(B->h_inst[i].M);
+      if (need) {
         autotune(B, st);
         B->tuned = true;
       } else {
         build_passes(B);
       }
-      capture_iteration(B);
       B->bound = true;
     } else {
       build_passes(B);
     }
+    // (re)capture when the launch shapes changed or the batch was rebound
+    capture_iteration(B);
     const int n = B->n;
     std::vector<int> all(n, 1);
     set_active(B, all, nullptr, st);
@@ -1697,6 +1996,22 @@ kfbi_status kfbi_batch_tuning(const kfbi_batch* B, int* tile_order, double* us_n
   if (tile_order) *tile_order = B->tile_order;
   if (us_natural) *us_natural = B->tuned_us[0];
   if (us_largest_first) *us_largest_first = B->tuned_us[1];
+  return KFBI_OK;
+}
+
+int kfbi_batch_tuning_count(const kfbi_batch* B) { return B ? (int)B->tuning.size() : 0; }
+
+kfbi_status kfbi_batch_tuning_get(const kfbi_batch* B, int i, kfbi_batch_tuning_t* out) {
+  if (!B || !out || i < 0 || i >= (int)B->tuning.size()) return KFBI_ERR_ARG;
+  *out = B->tuning[i];
+  return KFBI_OK;
+}
+
+kfbi_status kfbi_batch_force_candidate(kfbi_batch* B, int candidate) {
+  if (!B || candidate < -1) return KFBI_ERR_ARG;
+  B->force = candidate;
+  B->tuned = false;  // the next step tunes (or applies the forced candidate) again
+  B->rpb_of_M.clear();
   return KFBI_OK;
 }
 

@@ -2,10 +2,20 @@
 // Sec. 3.4.2 (arXiv 2404.14864) with each one-dimensional sine transform
 // computed by an FP32 FFT on the CUDA cores instead of a dense product.
 //
-// One pass transforms every row of an Mp x Mp plane and writes the result
-// transposed, like a dense pass: out[p][c][r] = sum_n sin(pi (c+1) n / M)
-// in[p][r][n-1], c = 0 .. M-2 (rows c >= M-1 of the output are never
-// written and stay zero).  Two passes give S A S.
+// A transform pass takes every row of P planes of Mp x Mp floats and writes
+// the sine transform transposed, out[p][c][r] = sum_n sin(pi (c+1) n / M)
+// in[p][r][n-1], c = 0 .. M-2 (output rows c >= M-1 are never written and
+// stay zero), or in place of the row (out[p][r][c]).  The box solve
+// S (S R S / (lambda_a + lambda_b - kappa)) S of Sec. 3.4.2 needs three
+// passes, not four: after the first pass (along x, written transposed) a
+// row of the plane holds one x-frequency b and all y samples, and the
+// y-transform, the division by lambda_a + lambda_b - kappa and the inverse
+// y-transform all run along that row.  The middle pass therefore does
+// forward DST, division and inverse DST per row (for complex kappa a warp
+// holds the row of both planes) and writes transposed; a row of its output
+// holds one y index and all x frequencies, so the third pass transforms
+// along x and writes its rows in place: the solution comes out in the
+// layout of the right-hand side (row = y, column = x).
 //
 // DST-I through a complex FFT of length M.  With x_n = in[r][n-1]
 // (n = 1 .. M-1), let y be the odd extension of length 2M (y_0 = y_M = 0,
@@ -17,27 +27,36 @@
 //
 // FFT_M, M = 32 N1 (four-step factorisation n = 32 n1 + n2, k = k1 + N1 k2):
 // lane n2 holds z_{32 n1 + n2} for all n1 and does an N1-point DFT in
-// registers; the result is multiplied by W_M^{n2 k1} and transposed through
-// shared memory; lane k1 then does the 32-point DFT over n2 and holds
-// Z_{k1 + N1 k2}.  In-register DFTs are radix-2 with twiddles from a shared
-// table of W_M^j (exact powers computed on the host in float64).
+// registers (mixed radix: one radix-3 step when 3 divides N1, radix-2
+// otherwise, every register index a compile-time constant); the result is
+// multiplied by W_M^{n2 k1} and transposed through shared memory; lane k1
+// (and k1 + 32 when N1 > 32) then does the 32-point DFT over n2 and
+// untangles the DST values from Z_k and Z_{M-k} (held by lanes k1 and
+// N1 - k1, exchanged by warp shuffles; for N1 > 32 through shared memory in
+// natural order).  Twiddles are exact powers computed on the
+// host in float64 and rounded.  Supported: M = 32 N1 with N1 in
+// {2, 4, 6, 8, 12, 16, 24, 32, 48, 64}, i.e. M = 64 .. 2048 with M / 32 a
+// power of two or three times one.
 //
-// One warp per row, RPB rows per block; the block stages its rows' results
-// and writes the transposed output as RPB-float runs.  Pass 2 of a box solve
-// (real kappa) applies the eigenvalue division as it stages.
+// One warp per row (and per plane of a complex solve), RPB rows per block
+// (4 or 8, chosen at launch).  One kernel per N1; a block of a grouped launch
+// may belong to any instance of that size: a per-block map gives its
+// instance descriptor.
+#include <algorithm>
+#include <cmath>
 #include <cstdint>
+#include <mutex>
 
 #include "tc_internal.h"
 
 namespace kfbi {
 namespace ff {
-using kfbi::FftSparseRhs;
-
-constexpr int RPB = 8;  // rows (warps) per block
 
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
   return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
 
 __host__ __device__ constexpr int bitrev(int i, int bits) {
   int r = 0;
@@ -47,8 +66,7 @@ __host__ __device__ constexpr int bitrev(int i, int bits) {
 
 __host__ __device__ constexpr int log2i(int n) { return n <= 1 ? 0 : 1 + log2i(n >> 1); }
 
-// t[i] = a[bitrev(i)] with every index a compile-time constant (a loop
-// would leave the permutation to the optimiser and the arrays in memory).
+// t[i] = a[bitrev(i)] with every index a compile-time constant.
 template <int N, int I = 0>
 __device__ __forceinline__ void bitrev_copy(float2 (&t)[N], const float2 (&a)[N]) {
   if constexpr (I < N) {
@@ -58,10 +76,10 @@ __device__ __forceinline__ void bitrev_copy(float2 (&t)[N], const float2 (&a)[N]
   }
 }
 
-// Butterflies of stage LEN (LEN / 2 apart), then the next stage; one
-// template instance per stage keeps every register index a constant.
-template <int N, int LEN>
-__device__ __forceinline__ void dft_stages(float2 (&t)[N], const float2* tw, int stride) {
+// Radix-2 butterflies of stage LEN (LEN / 2 apart), then the next stage.
+// tw[j] = W_M^j and N * S = M, so W_LEN^j = tw[j * (N / LEN) * S].
+template <int N, int S, int LEN>
+__device__ __forceinline__ void r2_stages(float2 (&t)[N], const float2* tw) {
   if constexpr (LEN <= N) {
 #pragma unroll
     for (int i = 0; i < N; i += LEN) {
@@ -72,25 +90,56 @@ __device__ __forceinline__ void dft_stages(float2 (&t)[N], const float2* tw, int
         // W^0 = 1 and W_LEN^{LEN/4} = -i need no multiplication
         const float2 v = j == 0 ? x
                          : (4 * j == LEN ? make_float2(x.y, -x.x)
-                                         : cmul(x, tw[j * (N / LEN) * stride]));
-        t[i + j] = make_float2(u.x + v.x, u.y + v.y);
-        t[i + j + LEN / 2] = make_float2(u.x - v.x, u.y - v.y);
+                                         : cmul(x, tw[j * (N / LEN) * S]));
+        t[i + j] = cadd(u, v);
+        t[i + j + LEN / 2] = csub(u, v);
       }
     }
-    dft_stages<N, LEN * 2>(t, tw, stride);
+    r2_stages<N, S, LEN * 2>(t, tw);
   }
 }
 
-// In-place radix-2 decimation-in-time DFT of N values in registers;
-// tw[j * stride] = exp(-2 pi i j / (N * stride)), so W_len^j is
-// tw[j * (N / len) * stride].
-template <int N>
-__device__ __forceinline__ void dft_reg(float2 (&a)[N], const float2* tw, int stride) {
-  float2 t[N];
-  bitrev_copy<N>(t, a);
-  dft_stages<N, 2>(t, tw, stride);
+// In-place DFT of N register values, X_k = sum_n a_n W_N^{nk}, natural
+// order in and out; W_N^j = tw[j S] (N S = M).  N = 2^a or 3 * 2^a.
+template <int N, int S>
+__device__ __forceinline__ void dft(float2 (&a)[N], const float2* tw) {
+  if constexpr (N == 1) {
+    return;
+  } else if constexpr (N % 3 == 0) {
+    // decimation in time by 3: three interleaved DFTs of length L, then
+    // twiddles W_N^{k}, W_N^{2k} and a 3-point DFT per k
+    constexpr int L = N / 3;
+    float2 s0[L], s1[L], s2[L];
 #pragma unroll
-  for (int i = 0; i < N; ++i) a[i] = t[i];
+    for (int l = 0; l < L; ++l) {
+      s0[l] = a[3 * l];
+      s1[l] = a[3 * l + 1];
+      s2[l] = a[3 * l + 2];
+    }
+    dft<L, 3 * S>(s0, tw);
+    dft<L, 3 * S>(s1, tw);
+    dft<L, 3 * S>(s2, tw);
+    constexpr float kS3 = 0.866025403784438646763723170752936183f;  // sin(pi / 3)
+#pragma unroll
+    for (int k = 0; k < L; ++k) {
+      const float2 t0 = s0[k];
+      const float2 t1 = k == 0 ? s1[k] : cmul(s1[k], tw[k * S]);
+      const float2 t2 = k == 0 ? s2[k] : cmul(s2[k], tw[2 * k * S]);
+      const float2 sm = cadd(t1, t2), df = csub(t1, t2);
+      const float2 m = make_float2(t0.x - 0.5f * sm.x, t0.y - 0.5f * sm.y);
+      // W_3 = -1/2 - i sqrt(3)/2: X_{k+L} = m - i (sqrt3/2) df, X_{k+2L} = m + i (sqrt3/2) df
+      const float2 r = make_float2(kS3 * df.y, -kS3 * df.x);
+      a[k] = cadd(t0, sm);
+      a[k + L] = cadd(m, r);
+      a[k + 2 * L] = csub(m, r);
+    }
+  } else {
+    float2 t[N];
+    bitrev_copy<N>(t, a);
+    r2_stages<N, S, 2>(t, tw);
+#pragma unroll
+    for (int i = 0; i < N; ++i) a[i] = t[i];
+  }
 }
 
 // Element y_n of the odd extension of row xr (x_n at xr[n-1]).
@@ -99,151 +148,14 @@ __device__ __forceinline__ float yodd(const float* xr, int n, int M) {
   return n < M ? xr[n - 1] : -xr[2 * M - n - 1];
 }
 
-// Shared memory of one block (floats): twiddle tables W_M^j, W_M^{n2 k1}
-// by [k1][n2], exp(-i pi k/M) (2M each), eigenvalues M, and per warp an
-// N1 x 33 complex transpose buffer that first holds the warp's input row;
-// once every warp has finished its transposes the buffers hold the staged
-// output, (M - 1) x (RPB + 1) floats.
-constexpr size_t smem_bytes(int M) {
-  return sizeof(float) * ((size_t)6 * M + M + (size_t)RPB * (M / 32) * 33 * 2);
-}
-static_assert((1024 - 1) * (RPB + 1) <= RPB * 32 * 33 * 2, "staged output fits the transposes");
-
-// mode 0: plain transform; mode 1: eigenvalue division of the box solve,
-// out *= scale / (lam[r] + lam[c] - kre) for r < n1, 0 for padded rows r.
-// SPARSE: the input plane is not read; each warp builds its row from the
-// corrected values of the row's irregular nodes (the right-hand side of a
-// fast application is zero elsewhere), with the arithmetic of k_correct32.
-template <int N1, bool SPARSE>
-__global__ void __launch_bounds__(32 * RPB) k_dst_fft(const float* __restrict__ in,
-                                                      float* __restrict__ out, int Mp, int n1,
-                                                      const float2* __restrict__ twM,
-                                                      const float2* __restrict__ twB,
-                                                      const float2* __restrict__ tw2M, int mode,
-                                                      const float* __restrict__ lam, float kre,
-                                                      float scale, const double* stop,
-                                                      const FftSparseRhs sp, int r_lo, int bpp) {
+// In-place DST-I of the row held in buf (as floats: buf[n-1] = x_n on
+// entry, buf[c] = DST_{c+1} on exit, c = 0 .. M-2).  buf holds N1 x 33
+// float2; lanes of the warp call it together.
+template <int N1>
+__device__ __forceinline__ void row_dst(float2* buf, int lane, const float2* s_tw,
+                                        const float2* s_twb, const float2* s_tw2) {
   constexpr int M = 32 * N1;
-  constexpr int T = 32 * RPB;  // threads
-  extern __shared__ float4 smem4[];
-  float2* s_tw = reinterpret_cast<float2*>(smem4);  // [M] W_M^j
-  float2* s_twb = s_tw + M;                         // [N1][32] W_M^{n2 k1}
-  float2* s_tw2 = s_twb + M;                        // [M] exp(-i pi k / M)
-  float* s_lam = reinterpret_cast<float*>(s_tw2 + M);  // [M]
-  float2* s_ex = reinterpret_cast<float2*>(s_lam + M);   // [RPB][N1][33]
-  float* s_out = reinterpret_cast<float*>(s_ex);         // [M - 1][RPB + 1], after the transposes
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  // the tables are written once at domain set-up: load them before waiting
-  // for the previous kernel (every load issued before any is used)
-  {
-    constexpr int NT = (M + T - 1) / T;
-    float2 v0[NT], v1[NT], v2[NT];
-    float v3[NT];
-#pragma unroll
-    for (int q = 0; q < NT; ++q) {
-      const int i = threadIdx.x + q * T;
-      if (i < M) {
-        v0[q] = twM[i];
-        v1[q] = twB[i];
-        v2[q] = tw2M[i];
-        v3[q] = mode == 1 && i < n1 ? lam[i] : 0.f;
-      }
-    }
-#pragma unroll
-    for (int q = 0; q < NT; ++q) {
-      const int i = threadIdx.x + q * T;
-      if (i < M) {
-        s_tw[i] = v0[q];
-        s_twb[i] = v1[q];
-        s_tw2[i] = v2[q];
-        s_lam[i] = v3[q];
-      }
-    }
-  }
-  KFBI_PDL_ENTRY();
-  KFBI_STOP_RETURN(stop);
-  // bpp blocks per plane cover rows r_lo .. r_lo + bpp RPB - 1 of each plane
-  const int p = blockIdx.x / bpp;
-  const int rr0 = r_lo + (blockIdx.x - p * bpp) * RPB;
-  const int row0 = p * Mp + rr0;  // first row over all planes
-  if constexpr (SPARSE) {
-    float* xrow = reinterpret_cast<float*>(s_ex + (size_t)warp * N1 * 33);
-#pragma unroll
-    for (int q = 0; q < M / 32; ++q) xrow[lane + 32 * q] = 0.f;
-    __syncwarp();
-    const int rl = rr0 + warp - sp.rmin;  // row within the irregular rows
-    if (rl >= 0 && rl < sp.nrows) {
-      // lanes take the row's correction arms (grouped by node, nodes by
-      // column), each one arm with its six density terms; a segmented sum
-      // over lanes in a fixed order adds the arms of a node
-      const int a0 = sp.arm_start[sp.row_start[rl]], a1 = sp.arm_start[sp.row_start[rl + 1]];
-      for (int ab = a0; ab < a1; ab += 32) {
-        const int a = ab + lane;
-        float v = 0.f;
-        int col = -1 - lane;  // distinct keys for idle lanes
-        if (a < a1) {
-          col = sp.arm_col[a];
-          int k = sp.arm_k0[a];
-          float ar = 0.f, ai = 0.f, br = 0.f, bi = 0.f;
-#pragma unroll
-          for (int m = 0; m < 6; ++m) {
-            const float al = sp.alpha[m * sp.n_arms + a], be = sp.beta[m * sp.n_arms + a];
-            const float pr = (float)sp.phi[(size_t)k * sp.ps];
-            ar = fmaf(al, pr, ar);
-            br = fmaf(be, pr, br);
-            if (sp.cplx) {
-              const float pi = (float)sp.phi[(size_t)k * sp.ps + 1];
-              ai = fmaf(al, pi, ai);
-              bi = fmaf(be, pi, bi);
-            }
-            k = (k + 1 == sp.nb) ? 0 : k + 1;
-          }
-          float sr = ar + sp.kre * br, si = 0.f;
-          if (sp.cplx) {
-            sr -= sp.kim * bi;
-            si = ai + sp.kre * bi + sp.kim * br;
-          }
-          v = p == 0 ? sr : si;
-        }
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          const float t = __shfl_up_sync(0xffffffffu, v, o);
-          const int kc = __shfl_up_sync(0xffffffffu, col, o);
-          if (lane >= o && kc == col) v += t;
-        }
-        const int next = __shfl_down_sync(0xffffffffu, col, 1);
-        if (a < a1 && (lane == 31 || next != col)) xrow[col] += v;
-        __syncwarp();
-      }
-    }
-  } else
-  // the block's RPB input rows (M floats each) into the warps' transpose
-  // buffers: all loads first, then all stores
-  {
-    const float* src = in + (size_t)row0 * Mp;
-    constexpr int NV = RPB * (M / 4) / T;  // float4 per thread (M >= 128)
-    constexpr int NVQ = NV > 0 ? NV : 1;
-    float4 v[NVQ];
-#pragma unroll
-    for (int q = 0; q < NVQ; ++q) {
-      const int i = threadIdx.x + q * T;
-      if (i < RPB * (M / 4)) {
-        const int rw = i / (M / 4), cq = i - rw * (M / 4);
-        v[q] = *reinterpret_cast<const float4*>(src + (size_t)rw * Mp + 4 * cq);
-      }
-    }
-#pragma unroll
-    for (int q = 0; q < NVQ; ++q) {
-      const int i = threadIdx.x + q * T;
-      if (i < RPB * (M / 4)) {
-        const int rw = i / (M / 4), cq = i - rw * (M / 4);
-        *reinterpret_cast<float4*>(reinterpret_cast<float*>(s_ex + (size_t)rw * N1 * 33) + 4 * cq) = v[q];
-      }
-    }
-  }
-  __syncthreads();
-  float2* ex = s_ex + (size_t)warp * N1 * 33;
-  const float* xr = reinterpret_cast<const float*>(ex);
+  float* xr = reinterpret_cast<float*>(buf);
   // step 1: N1-point DFTs over n1 of z_{32 n1 + lane}, then W_M^{lane k1}
   float2 a[N1];
 #pragma unroll
@@ -251,130 +163,420 @@ __global__ void __launch_bounds__(32 * RPB) k_dst_fft(const float* __restrict__ 
     const int m = 32 * q + lane;
     a[q] = make_float2(yodd(xr, 2 * m, M), yodd(xr, 2 * m + 1, M));
   }
-  dft_reg<N1>(a, s_tw, 32);
+  dft<N1, 32>(a, s_tw);
   __syncwarp();  // every lane has read its part of the row before the transpose overwrites it
 #pragma unroll
-  for (int k1 = 0; k1 < N1; ++k1) ex[k1 * 33 + lane] = cmul(a[k1], s_twb[k1 * 32 + lane]);
+  for (int k1 = 0; k1 < N1; ++k1) buf[k1 * 33 + lane] = cmul(a[k1], s_twb[k1 * 32 + lane]);
   __syncwarp();
-  // step 3: lane k1 < N1 does the 32-point DFT over n2
-  float2 b[32];
-  if (lane < N1) {
+  // step 2: lane k1 (and k1 + 32) does the 32-point DFT over n2
+  constexpr int NQ = (N1 + 31) / 32;
+  float2 b[NQ][32];
 #pragma unroll
-    for (int n2 = 0; n2 < 32; ++n2) b[n2] = ex[lane * 33 + n2];
-    dft_reg<32>(b, s_tw, N1);
+  for (int t = 0; t < NQ; ++t) {
+    const int k1 = lane + 32 * t;
+    if (k1 < N1) {
+#pragma unroll
+      for (int n2 = 0; n2 < 32; ++n2) b[t][n2] = buf[k1 * 33 + n2];
+      dft<32, N1>(b[t], s_tw);
+    } else {
+#pragma unroll
+      for (int n2 = 0; n2 < 32; ++n2) b[t][n2] = make_float2(0.f, 0.f);
+    }
+  }
+  __syncwarp();
+  // DST_k = -Im(E_k + exp(-i pi k / M) O_k) / 2 from Z_k and Z_{M-k}
+  if constexpr (N1 <= 32) {
+    // lane k1 < N1 holds Z_{k1 + N1 k2} in b[0][k2]; Z_{M-k} is b[0][31 - k2]
+    // of lane N1 - k1 (lane 0: its own b[0][(32 - k2) % 32])
+    const int partner = lane == 0 ? 0 : N1 - lane;
+#pragma unroll
+    for (int k2 = 0; k2 < 32; ++k2) {
+      float2 zc;
+      zc.x = __shfl_sync(0xffffffffu, b[0][31 - k2].x, partner);
+      zc.y = __shfl_sync(0xffffffffu, b[0][31 - k2].y, partner);
+      if (lane == 0) zc = b[0][(32 - k2) & 31];
+      // straight-line body (only the store is predicated) so the unrolled
+      // iterations overlap
+      const int k = lane + N1 * k2;
+      const float2 zk = b[0][k2];
+      const float ey = 0.5f * (zk.y - zc.y);
+      const float ox = 0.5f * (zk.y + zc.y), oy = -0.5f * (zk.x - zc.x);
+      const float2 w = s_tw2[k < M ? k : 0];
+      const float v = -0.5f * (ey + w.x * oy + w.y * ox);
+      if (lane < N1 && k != 0) xr[k - 1] = v;
+    }
   } else {
+    // Z in natural order through the buffer (M float2 fit in N1 x 33)
 #pragma unroll
-    for (int n2 = 0; n2 < 32; ++n2) b[n2] = make_float2(0.f, 0.f);
+    for (int t = 0; t < NQ; ++t) {
+      const int k1 = lane + 32 * t;
+      if (k1 < N1) {
+#pragma unroll
+        for (int k2 = 0; k2 < 32; ++k2) buf[k1 + N1 * k2] = b[t][k2];
+      }
+    }
+    __syncwarp();
+    float v[N1];
+#pragma unroll
+    for (int q = 0; q < N1; ++q) {
+      const int k = lane + 32 * q;
+      const float2 zk = buf[k];
+      const float2 zc = buf[k == 0 ? 0 : M - k];
+      const float ey = 0.5f * (zk.y - zc.y);
+      const float ox = 0.5f * (zk.y + zc.y), oy = -0.5f * (zk.x - zc.x);
+      const float2 w = s_tw2[k];
+      v[q] = -0.5f * (ey + w.x * oy + w.y * ox);
+    }
+    __syncwarp();  // all Z read before the row overwrites them
+#pragma unroll
+    for (int q = 0; q < N1; ++q) {
+      const int k = lane + 32 * q;
+      if (k > 0) xr[k - 1] = v[q];
+    }
   }
-  // every warp is done with its transpose buffer: the staged output may
-  // overwrite them
-  __syncthreads();
-  // DST_k = -Im(E_k + exp(-i pi k / M) O_k) / 2 for k = lane + N1 k2
-  // (lanes < N1 hold Z_k in b[k2]); Z_{M-k} is b[31 - k2] of lane N1 - lane,
-  // or, for lane 0, its own b[(32 - k2) % 32].  Output row c = k - 1.
+  __syncwarp();
+}
+
+constexpr size_t buf_floats(int N1) { return (size_t)N1 * 33 * 2; }
+
+// Shared memory of one block (bytes): twiddle tables W_M^j, W_M^{n2 k1} at
+// [k1][n2] and exp(-i pi k / M) (M float2 each), eigenvalues (M floats),
+// and one N1 x 33 complex row buffer per warp and plane.
+constexpr size_t smem_for(int N1, int rpb, int pw) {
+  return sizeof(float) * ((size_t)7 * 32 * N1 + (size_t)rpb * pw * buf_floats(N1));
+}
+
+template <int N1, bool SPARSE>
+__device__ __forceinline__ void body(const FftDesc& d, int lb, int rpb, float* smem) {
+  constexpr int M = 32 * N1;
+  const int T = 32 * rpb;
+  float2* s_tw = reinterpret_cast<float2*>(smem);  // [M] W_M^j
+  float2* s_twb = s_tw + M;                         // [N1][32] W_M^{n2 k1}
+  float2* s_tw2 = s_twb + M;                        // [M] exp(-i pi k / M)
+  float* s_lam = reinterpret_cast<float*>(s_tw2 + M);  // [M]
+  float2* s_buf = reinterpret_cast<float2*>(s_lam + M);  // [rpb][pw][N1 * 33]
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const bool solve = d.solve != 0;
+  const int pw = d.pw;
+  // the tables are written once at domain set-up: load them before waiting
+  // for the previous kernel
+  for (int i = threadIdx.x; i < M; i += T) {
+    s_tw[i] = d.twM[i];
+    s_twb[i] = d.twB[i];
+    s_tw2[i] = d.tw2M[i];
+    s_lam[i] = solve && i < d.n1 ? d.lam[i] : 0.f;
+  }
+  KFBI_PDL_ENTRY();
+  KFBI_STOP_RETURN(d.stop);
+  if (d.active && *d.active == 0) return;
+  // lb = (plane group) * rblocks + row block
+  const int pg = lb / d.rblocks;
+  const int rr0 = d.r_lo + (lb - pg * d.rblocks) * rpb;
   const int r = rr0 + warp;  // data row within the plane
-  const float lam_r = r < n1 ? s_lam[r] : 0.f;
-  const int partner = lane == 0 ? 0 : N1 - lane;
+  const size_t plane = (size_t)d.Mp * d.Mp;
+  for (int pl = 0; pl < pw; ++pl) {
+    const int p = pg + pl;  // plane
+    float2* buf = s_buf + (size_t)(warp * pw + pl) * N1 * 33;
+    float* xrow = reinterpret_cast<float*>(buf);
+    if constexpr (SPARSE) {
+      const FftSparseRhs& sp = d.sp;
+      const double* phi = sp.phi + (sp.dj ? (size_t)(*sp.dj) * sp.dj_stride : 0);
 #pragma unroll
-  for (int k2 = 0; k2 < 32; ++k2) {
-    float2 zc;
-    zc.x = __shfl_sync(0xffffffffu, b[31 - k2].x, partner);
-    zc.y = __shfl_sync(0xffffffffu, b[31 - k2].y, partner);
-    if (lane == 0) zc = b[(32 - k2) & 31];
-    // straight-line body (only the store is predicated) so the unrolled
-    // iterations overlap
-    const int k = (lane + N1 * k2) & (M - 1);
-    const float2 zk = b[k2];
-    const float ey = 0.5f * (zk.y - zc.y);
-    const float ox = 0.5f * (zk.y + zc.y), oy = -0.5f * (zk.x - zc.x);
-    const float2 w = s_tw2[k];
-    float v = -0.5f * (ey + w.x * oy + w.y * ox);
-    const int c = k - 1;
-    if (mode == 1) v = r < n1 ? v * __fdividef(scale, lam_r + s_lam[c < 0 ? 0 : c] - kre) : 0.f;
-    if (lane < N1 && k != 0) s_out[c * (RPB + 1) + warp] = v;
+      for (int q = 0; q < N1; ++q) xrow[lane + 32 * q] = 0.f;
+      __syncwarp();
+      const int rl = r - sp.rmin;  // row within the irregular rows
+      if (rl >= 0 && rl < sp.nrows) {
+        // lanes take the row's correction arms (grouped by node, nodes by
+        // column), each one arm with its six density terms; a segmented sum
+        // over lanes in a fixed order adds the arms of a node
+        const int a0 = sp.arm_start[sp.row_start[rl]], a1 = sp.arm_start[sp.row_start[rl + 1]];
+        for (int ab = a0; ab < a1; ab += 32) {
+          const int a = ab + lane;
+          float val = 0.f;
+          int col = -1 - lane;  // distinct keys for idle lanes
+          if (a < a1) {
+            col = sp.arm_col[a];
+            int k = sp.arm_k0[a];
+            float ar = 0.f, ai = 0.f, br = 0.f, bi = 0.f;
+#pragma unroll
+            for (int m = 0; m < 6; ++m) {
+              const float al = sp.alpha[m * sp.n_arms + a], be = sp.beta[m * sp.n_arms + a];
+              const float pr = (float)phi[(size_t)k * sp.ps];
+              ar = fmaf(al, pr, ar);
+              br = fmaf(be, pr, br);
+              if (sp.cplx) {
+                const float pi = (float)phi[(size_t)k * sp.ps + 1];
+                ai = fmaf(al, pi, ai);
+                bi = fmaf(be, pi, bi);
+              }
+              k = (k + 1 == sp.nb) ? 0 : k + 1;
+            }
+            float sr = ar + sp.kre * br, si = 0.f;
+            if (sp.cplx) {
+              sr -= sp.kim * bi;
+              si = ai + sp.kre * bi + sp.kim * br;
+            }
+            val = p == 0 ? sr : si;
+          }
+#pragma unroll
+          for (int o = 1; o < 32; o <<= 1) {
+            const float t = __shfl_up_sync(0xffffffffu, val, o);
+            const int kc = __shfl_up_sync(0xffffffffu, col, o);
+            if (lane >= o && kc == col) val += t;
+          }
+          const int next = __shfl_down_sync(0xffffffffu, col, 1);
+          if (a < a1 && (lane == 31 || next != col)) xrow[col] += val;
+          __syncwarp();
+        }
+      }
+    } else if (r < d.n1) {
+      // the row (M floats from a 16-byte aligned start): all loads first
+      const float4* src = reinterpret_cast<const float4*>(d.in + p * plane + (size_t)r * d.Mp);
+      constexpr int NV = (M / 4 + 31) / 32;
+      float4 x[NV];
+#pragma unroll
+      for (int q = 0; q < NV; ++q) {
+        const int i = lane + 32 * q;
+        if (i < M / 4) x[q] = src[i];
+      }
+#pragma unroll
+      for (int q = 0; q < NV; ++q) {
+        const int i = lane + 32 * q;
+        if (i < M / 4) reinterpret_cast<float4*>(xrow)[i] = x[q];
+      }
+    } else {
+      // padding rows transform to zero
+#pragma unroll
+      for (int q = 0; q < N1; ++q) xrow[lane + 32 * q] = 0.f;
+    }
+  }
+  __syncthreads();  // tables (and rows) visible
+  // forward transform of each plane's row; a solve divides by
+  // lambda_r + lambda_c - kappa and transforms back.  The loops are kept
+  // rolled so the kernel holds one copy of the transform's code (two
+  // inlined copies overflowed the instruction cache)
+  const int nphase = solve ? 2 : 1;
+#pragma unroll 1
+  for (int ph = 0; ph < nphase; ++ph) {
+#pragma unroll 1
+    for (int pl = 0; pl < pw; ++pl)
+      row_dst<N1>(s_buf + (size_t)(warp * pw + pl) * N1 * 33, lane, s_tw, s_twb, s_tw2);
+    if (ph + 1 < nphase) {
+      __syncwarp();
+      float* x0 = reinterpret_cast<float*>(s_buf + (size_t)(warp * pw) * N1 * 33);
+      const float lam_r = r < d.n1 ? s_lam[r] : 0.f;
+      if (pw == 2) {
+        float* x1 = reinterpret_cast<float*>(s_buf + (size_t)(warp * pw + 1) * N1 * 33);
+        for (int c = lane; c < M - 1; c += 32) {
+          float zr = 0.f, zi = 0.f;
+          if (r < d.n1) eig_div_cplx32(x0[c], x1[c], lam_r + s_lam[c] - d.kre, d.kim, d.scale, zr, zi);
+          x0[c] = zr;
+          x1[c] = zi;
+        }
+      } else {
+        for (int c = lane; c < M - 1; c += 32)
+          x0[c] = r < d.n1 ? x0[c] * __fdividef(d.scale, lam_r + s_lam[c] - d.kre) : 0.f;
+      }
+      __syncwarp();
+    }
+  }
+  if (!d.transpose) {
+    // the last pass of a box solve: each warp writes its row as it is
+    // (M floats, the slot of index M - 1 zero)
+    __syncwarp();
+    for (int pl = 0; pl < pw; ++pl) {
+      float* xr = reinterpret_cast<float*>(s_buf + (size_t)(warp * pw + pl) * N1 * 33);
+      if (lane == 0) xr[M - 1] = 0.f;
+      __syncwarp();
+      if (r < d.n1) {
+        float4* dst = reinterpret_cast<float4*>(d.out + (pg + pl) * plane + (size_t)r * d.Mp);
+        for (int i = lane; i < M / 4; i += 32) dst[i] = reinterpret_cast<const float4*>(xr)[i];
+      }
+    }
+    return;
   }
   __syncthreads();
-  float* dst = out + (size_t)p * Mp * Mp + rr0;
-  constexpr int NW = ((M - 1) * (RPB / 4) + T - 1) / T;
+  // transposed write: for each output row c the block's rpb rows are one
+  // contiguous run of rpb floats (float4 pieces read from four warps' rows)
+  const int nq = rpb / 4;
+  for (int pl = 0; pl < pw; ++pl) {
+    float* dst = d.out + (pg + pl) * plane + rr0;
+    for (int i = threadIdx.x; i < (M - 1) * nq; i += T) {
+      const int c = i / nq, h = i - c * nq;
+      float o[4];
 #pragma unroll
-  for (int q = 0; q < NW; ++q) {
-    const int i = threadIdx.x + q * T;
-    if (i < (M - 1) * (RPB / 4)) {
-      const int c = i / (RPB / 4), h = i - c * (RPB / 4);
-      const float* sv = s_out + c * (RPB + 1) + 4 * h;
-      *reinterpret_cast<float4*>(dst + (size_t)c * Mp + 4 * h) = make_float4(sv[0], sv[1], sv[2], sv[3]);
+      for (int j = 0; j < 4; ++j)
+        o[j] = reinterpret_cast<const float*>(s_buf + (size_t)((4 * h + j) * pw + pl) * N1 * 33)[c];
+      *reinterpret_cast<float4*>(dst + (size_t)c * d.Mp + 4 * h) = make_float4(o[0], o[1], o[2], o[3]);
     }
   }
 }
 
-template <int N1>
-static void set_smem_attr() {
-  KFBI_CUDA(cudaFuncSetAttribute(k_dst_fft<N1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem_bytes(32 * N1)));
-  KFBI_CUDA(cudaFuncSetAttribute(k_dst_fft<N1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem_bytes(32 * N1)));
-}
-
-template <int N1>
-static void launch_n1(const float* in, float* out, int Mp, int n1, const float2* twM,
-                      const float2* twB, const float2* tw2M, int mode, const float* lam, float kre,
-                      float scale, int P, const double* stop, cudaStream_t st,
-                      const FftSparseRhs* sp) {
-  // a sparse first pass transforms only the rows that can hold irregular
-  // nodes (whole RPB groups); the output columns of the other rows are zero
-  // in its dedicated buffer and stay so
-  int r_lo = 0, bpp = Mp / RPB;
-  if (sp) {
-    r_lo = sp->rmin / RPB * RPB;
-    bpp = (sp->rmin + sp->nrows - r_lo + RPB - 1) / RPB;
+// One kernel per transform length (every block of a launch has the same N1;
+// a grouped launch over instances of several sizes is one launch per size).
+template <int N1, bool SPARSE>
+__global__ void __launch_bounds__(256) k_dst_fft(const __grid_constant__ FftGroup g) {
+  extern __shared__ float4 smem4[];
+  float* smem = reinterpret_cast<float*>(smem4);
+  // a private copy of the descriptor: its fields stay in registers instead
+  // of being reloaded through a pointer after every shared-memory store
+  FftDesc d;
+  int lb = blockIdx.x;
+  if (g.descs) {
+    const int2 m = g.blk[blockIdx.x];
+    d = g.descs[m.x];
+    lb = m.y;
+  } else {
+    d = g.one;
   }
-  const int blocks = P * bpp;
-  const double fl = fft_pass_flops(32 * N1, blocks * RPB);
-  if (sp)  // timed with the sparse first passes, not the dense DST passes
-    KFBI_LAUNCH_PW(KFBI_PROF_SPARSE, fl, (k_dst_fft<N1, true>), blocks, 32 * RPB, smem_bytes(32 * N1),
-                   st, in, out, Mp, n1, twM, twB, tw2M, mode, lam, kre, scale, stop, *sp, r_lo, bpp);
-  else
-    KFBI_LAUNCH_PW(KFBI_PROF_DST, fl, (k_dst_fft<N1, false>), blocks, 32 * RPB, smem_bytes(32 * N1),
-                   st, in, out, Mp, n1, twM, twB, tw2M, mode, lam, kre, scale, stop, FftSparseRhs{},
-                   r_lo, bpp);
+  body<N1, SPARSE>(d, lb, g.rpb, smem);
 }
 
 }  // namespace ff
 
-// Flops of one pass as executed: per row one complex FFT of length M
+// ---- host side --------------------------------------------------------------
+
+bool fft_supported(int M) {
+  if (M % 32 != 0) return false;
+  switch (M / 32) {
+    case 2: case 4: case 6: case 8: case 12: case 16: case 24: case 32: case 48: case 64:
+      return true;
+    default:
+      return false;
+  }
+}
+
+size_t fft_smem(int M, int rpb, int pw) { return ff::smem_for(M / 32, rpb, pw); }
+
+bool fft_rpb_fits(int M, int rpb, int pw) { return fft_smem(M, rpb, pw) <= (size_t)kMaxSmemOptin; }
+
+// Flops of one row transform as executed: one complex FFT of length M
 // (5 M log2 M) and the O(M) untangling (about 10 M).
-double fft_pass_flops(int M, int rows) {
-  int lg = 0;
-  while ((1 << lg) < M) ++lg;
-  return (double)rows * (5.0 * M * lg + 10.0 * M);
+double fft_pass_flops(int M, int rows) { return (double)rows * (5.0 * M * std::log2((double)M) + 10.0 * M); }
+
+template <int N1>
+static void set_attr() {
+  KFBI_CUDA(cudaFuncSetAttribute(ff::k_dst_fft<N1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 kMaxSmemOptin));
+  KFBI_CUDA(cudaFuncSetAttribute(ff::k_dst_fft<N1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 kMaxSmemOptin));
 }
 
-bool fft_supported(int M) { return M >= 64 && M <= 1024 && (M & (M - 1)) == 0; }
-
-size_t fft_smem_bytes(int M) { return ff::smem_bytes(M); }
-
-void fft_prepare(int M) {
-  switch (M) {
-    case 64: ff::set_smem_attr<2>(); break;
-    case 128: ff::set_smem_attr<4>(); break;
-    case 256: ff::set_smem_attr<8>(); break;
-    case 512: ff::set_smem_attr<16>(); break;
-    case 1024: ff::set_smem_attr<32>(); break;
-    default: throw Status{KFBI_ERR_UNSUPPORTED, "FFT passes need M = 64 .. 1024, a power of two"};
+template <int N1>
+static void launch_n1(const FftGroup& g, bool sparse, int nblocks, size_t smem, int prof_class,
+                      double flops, double bytes, cudaStream_t st) {
+  void* tok = g_prof_on ? prof_begin(prof_class, st) : nullptr;
+  if (sparse)
+    launch_kernel(ff::k_dst_fft<N1, true>, nblocks, 32 * g.rpb, smem, st, g);
+  else
+    launch_kernel(ff::k_dst_fft<N1, false>, nblocks, 32 * g.rpb, smem, st, g);
+  if (tok) {
+    prof_end(tok, st);
+    prof_add_work(tok, flops);
+    prof_add_bytes(tok, bytes);
   }
+  g_launches.fetch_add(1, std::memory_order_relaxed);
 }
 
-void fft_pass(const TcDst* T, const float* in, float* out, int mode, float kre, float scale, int P,
-              const double* stop, cudaStream_t st, const FftSparseRhs* sp) {
+void fft_prepare_all() {
+  static std::once_flag once;
+  std::call_once(once, []() {
+    set_attr<2>(); set_attr<4>(); set_attr<6>(); set_attr<8>(); set_attr<12>();
+    set_attr<16>(); set_attr<24>(); set_attr<32>(); set_attr<48>(); set_attr<64>();
+  });
+}
+
+FftDesc fft_desc(const TcDst* T, const float* in, float* out, int P, bool solve, float kre,
+                 float kim, float scale, const double* stop, const FftSparseRhs* sp, int rpb) {
+  FftDesc d{};
   const int M = T->n1 + 1;
-  switch (M) {
-    case 64: ff::launch_n1<2>(in, out, T->Mp, T->n1, T->twM, T->twB, T->tw2M, mode, T->lam, kre, scale, P, stop, st, sp); break;
-    case 128: ff::launch_n1<4>(in, out, T->Mp, T->n1, T->twM, T->twB, T->tw2M, mode, T->lam, kre, scale, P, stop, st, sp); break;
-    case 256: ff::launch_n1<8>(in, out, T->Mp, T->n1, T->twM, T->twB, T->tw2M, mode, T->lam, kre, scale, P, stop, st, sp); break;
-    case 512: ff::launch_n1<16>(in, out, T->Mp, T->n1, T->twM, T->twB, T->tw2M, mode, T->lam, kre, scale, P, stop, st, sp); break;
-    case 1024: ff::launch_n1<32>(in, out, T->Mp, T->n1, T->twM, T->twB, T->tw2M, mode, T->lam, kre, scale, P, stop, st, sp); break;
-    default: throw Status{KFBI_ERR_UNSUPPORTED, "FFT passes need M = 64 .. 1024, a power of two"};
+  d.in = in;
+  d.out = out;
+  d.twM = T->twM;
+  d.twB = T->twB;
+  d.tw2M = T->tw2M;
+  d.lam = T->lam;
+  d.N1 = M / 32;
+  d.Mp = T->Mp;
+  d.n1 = T->n1;
+  d.solve = solve ? 1 : 0;
+  d.transpose = 1;
+  d.pw = solve && P == 2 ? 2 : 1;
+  d.kre = kre;
+  d.kim = kim;
+  d.scale = scale;
+  d.stop = stop;
+  d.active = nullptr;
+  d.r_lo = 0;
+  int rows = T->n1;
+  if (sp) {
+    d.sparse = 1;
+    d.sp = *sp;
+    d.r_lo = sp->rmin / rpb * rpb;
+    rows = sp->rmin + sp->nrows - d.r_lo;
   }
+  d.rblocks = (rows + rpb - 1) / rpb;
+  d.pgroups = P / d.pw;
+  return d;
+}
+
+int fft_blocks(const FftDesc& d) { return d.pgroups * d.rblocks; }
+
+double fft_desc_bytes(const FftDesc& d, int rpb) {
+  const int M = 32 * d.N1;
+  const int rows = std::max(0, std::min(d.r_lo + d.rblocks * rpb, d.n1) - d.r_lo);
+  const double per_row = 4.0 * (M - 1) * (d.sparse ? 1 : 2);  // read (unless built) + write
+  return (double)rows * d.pgroups * d.pw * per_row;
+}
+
+double fft_desc_flops(const FftDesc& d, int rpb) {
+  const int M = 32 * d.N1;
+  return fft_pass_flops(M, fft_blocks(d) * rpb * d.pw * (d.solve ? 2 : 1));
+}
+
+void fft_launch(const FftGroup& g, int M, bool sparse, int nblocks, size_t smem, int prof_class,
+                double flops, double bytes, cudaStream_t st) {
+  fft_prepare_all();
+  if (nblocks <= 0) return;
+  switch (M / 32) {
+    case 2: launch_n1<2>(g, sparse, nblocks, smem, prof_class, flops, bytes, st); break;
+    case 4: launch_n1<4>(g, sparse, nblocks, smem, prof_class, flops, bytes, st); break;
+    case 6: launch_n1<6>(g, sparse, nblocks, smem, prof_class, flops, bytes, st); break;
+    case 8: launch_n1<8>(g, sparse, nblocks, smem, prof_class, flops, bytes, st); break;
+    case 12: launch_n1<12>(g, sparse, nblocks, smem, prof_class, flops, bytes, st); break;
+    case 16: launch_n1<16>(g, sparse, nblocks, smem, prof_class, flops, bytes, st); break;
+    case 24: launch_n1<24>(g, sparse, nblocks, smem, prof_class, flops, bytes, st); break;
+    case 32: launch_n1<32>(g, sparse, nblocks, smem, prof_class, flops, bytes, st); break;
+    case 48: launch_n1<48>(g, sparse, nblocks, smem, prof_class, flops, bytes, st); break;
+    case 64: launch_n1<64>(g, sparse, nblocks, smem, prof_class, flops, bytes, st); break;
+    default: throw Status{KFBI_ERR_UNSUPPORTED, "no FFT pass for this M"};
+  }
+}
+
+static void launch_one(const TcDst* T, const FftDesc& d, int prof_class, cudaStream_t st) {
+  const int M = T->n1 + 1;
+  int rpb = T->fft_rpb;
+  FftGroup g{};
+  g.descs = nullptr;
+  g.blk = nullptr;
+  g.one = d;
+  g.rpb = rpb;
+  fft_launch(g, M, d.sparse != 0, fft_blocks(d), fft_smem(M, rpb, d.pw), prof_class,
+             fft_desc_flops(d, rpb), fft_desc_bytes(d, rpb), st);
+}
+
+void fft_pass(const TcDst* T, const float* in, float* out, int P, const double* stop,
+              cudaStream_t st, const FftSparseRhs* sp, bool transpose) {
+  FftDesc d = fft_desc(T, in, out, P, false, 0.f, 0.f, 0.f, stop, sp, T->fft_rpb);
+  d.transpose = transpose ? 1 : 0;
+  // a sparse first pass is timed with the sparse passes, not the dense DST passes
+  launch_one(T, d, sp ? KFBI_PROF_SPARSE : KFBI_PROF_DST, st);
+}
+
+void fft_solve(const TcDst* T, const float* in, float* out, int P, float kre, float kim,
+               float scale, const double* stop, cudaStream_t st) {
+  const FftDesc d = fft_desc(T, in, out, P, true, kre, kim, scale, stop, nullptr, T->fft_rpb);
+  launch_one(T, d, KFBI_PROF_DST, st);
 }
 
 }  // namespace kfbi

@@ -27,6 +27,7 @@ extern unsigned g_prof_mask;
 void* prof_begin(int cls, cudaStream_t st);
 void prof_end(void* tok, cudaStream_t st);
 void prof_add_work(void* tok, double work);
+void prof_add_bytes(void* tok, double bytes);
 
 // Programmatic dependent launch.  Every library kernel is launched with
 // programmatic stream serialization (unless KFBI_PDL=0), so it can be

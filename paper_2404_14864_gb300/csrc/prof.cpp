@@ -21,7 +21,8 @@ namespace {
 struct Rec {
   int cls;
   cudaEvent_t a, b;
-  double work;  // floating-point operations the launch issues (0 if not counted)
+  double work;   // floating-point operations the launch issues (0 if not counted)
+  double bytes;  // algorithmic bytes the launch moves (0 if not counted)
 };
 std::mutex mu;
 std::vector<Rec> recs;
@@ -42,7 +43,7 @@ cudaEvent_t take() {
 void* prof_begin(int cls, cudaStream_t st) {
   if (!((g_prof_mask >> cls) & 1u)) return nullptr;
   std::lock_guard<std::mutex> lk(mu);
-  Rec r{cls, take(), take(), 0.0};
+  Rec r{cls, take(), take(), 0.0, 0.0};
   if (!r.a || !r.b) return nullptr;
   cudaEventRecord(r.a, st);
   recs.push_back(r);
@@ -61,6 +62,13 @@ void prof_add_work(void* tok, double work) {
   std::lock_guard<std::mutex> lk(mu);
   size_t i = (size_t)tok - 1;
   if (i < recs.size()) recs[i].work += work;
+}
+
+void prof_add_bytes(void* tok, double bytes) {
+  if (!tok) return;
+  std::lock_guard<std::mutex> lk(mu);
+  size_t i = (size_t)tok - 1;
+  if (i < recs.size()) recs[i].bytes += bytes;
 }
 
 }  // namespace kfbi
@@ -109,6 +117,16 @@ kfbi_status kfbi_profile_work(int cls, double* flops) {
   for (auto& r : recs)
     if (r.cls == cls) w += r.work;
   *flops = w;
+  return KFBI_OK;
+}
+
+kfbi_status kfbi_profile_bytes(int cls, double* bytes) {
+  if (!bytes || cls < 0 || cls >= KFBI_PROF_NCLASS) return KFBI_ERR_ARG;
+  std::lock_guard<std::mutex> lk(mu);
+  double b = 0.0;
+  for (auto& r : recs)
+    if (r.cls == cls) b += r.bytes;
+  *bytes = b;
   return KFBI_OK;
 }
 

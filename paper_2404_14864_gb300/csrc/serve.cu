@@ -31,7 +31,7 @@
 #include <thread>
 #include <vector>
 
-#include "internal.h"
+#include "tc_internal.h"
 
 using namespace kfbi;
 
@@ -500,8 +500,11 @@ int lane_of(const kfbi_server* S, const kfbi_domain_desc& d) {
 
 kfbi_status check_request(const kfbi_server* S, const kfbi_request* r, std::string& why) {
   if (!r) return why = "request is NULL", KFBI_ERR_ARG;
-  if (r->domain.precision != KFBI_MIXED_TF32)
-    return why = "served requests run on KFBI_MIXED_TF32 domains", KFBI_ERR_ARG;
+  if (r->domain.precision != KFBI_MIXED_TF32 && r->domain.precision != KFBI_MIXED_FFT32)
+    return why = "served requests run on KFBI_MIXED_TF32 or KFBI_MIXED_FFT32 domains", KFBI_ERR_ARG;
+  if (r->domain.precision == KFBI_MIXED_FFT32 && !fft_supported(r->domain.M))
+    return why = "no FFT pass for this grid size (KFBI_MIXED_FFT32 needs M = 32 N1)",
+           KFBI_ERR_UNSUPPORTED;
   if (r->domain.gmres_restart != S->desc.gmres_restart)
     return why = "the request's gmres_restart must equal the server's", KFBI_ERR_ARG;
   if (r->domain.gmres_maxit < 1 || !(r->domain.gmres_tol > 0.0))

@@ -808,7 +808,9 @@ __global__ void __launch_bounds__(256) k_sparse_p1(const float* __restrict__ rv,
 }
 
 // Last pass restricted to the extraction stencil, fused with Eq. 3.36:
-// U(j', i') = sum_a T3[i'][a] S[j'][a] at the six stencil points of node k,
+// U(j', i') = sum_a T3[i'][a] S[j'][a] at the six stencil points of node k
+// (TY: T3 rows are y indices, U(j', i') = sum_b T3[j'][b] S[i'][b], the
+// layout the FFT solve pass leaves),
 // then u+ as in k_extract32.  One block of GE_WARPS warps per node: the six
 // points lie in a 3 x 3 window of grid rows j and columns i, so the block
 // streams three rows of T3 and three rows of S (float4, each warp a
@@ -817,7 +819,7 @@ __global__ void __launch_bounds__(256) k_sparse_p1(const float* __restrict__ rv,
 // node with a full dot product each read twice the rows, 48 MB per
 // application at 1024^2; one warp per node left too few warps in flight.)
 constexpr int GE_WARPS = 4;
-template <bool C>
+template <bool C, bool TY>
 __global__ void __launch_bounds__(32 * GE_WARPS)
     k_gather_extract(const float* __restrict__ T3, const float* __restrict__ S32, int Mp,
                      size_t plane, const int* __restrict__ gidx, const float* __restrict__ w,
@@ -846,10 +848,11 @@ __global__ void __launch_bounds__(32 * GE_WARPS)
   for (int d = 0; d < 3; ++d) {
     // rows past the plane are clamped; their sums are never picked
     const int ii = min(ilo + d, Mp - 1), jj = min(jlo + d, Mp - 1);
+    const int tt = TY ? jj : ii, ss = TY ? ii : jj;
 #pragma unroll
     for (int q = 0; q < NP; ++q)
-      tr[q][d] = reinterpret_cast<const float4*>(T3 + q * plane + (size_t)ii * Mp);
-    srow[d] = reinterpret_cast<const float4*>(S32 + (size_t)jj * Mp);
+      tr[q][d] = reinterpret_cast<const float4*>(T3 + q * plane + (size_t)tt * Mp);
+    srow[d] = reinterpret_cast<const float4*>(S32 + (size_t)ss * Mp);
   }
   float acc[NP][3][3];
 #pragma unroll
@@ -872,11 +875,13 @@ __global__ void __launch_bounds__(32 * GE_WARPS)
       for (int dj = 0; dj < 3; ++dj)
 #pragma unroll
         for (int di = 0; di < 3; ++di) {
+          // window point (row jlo + dj, column ilo + di)
+          const float4 tv = t[q][TY ? dj : di], s4 = sv[TY ? di : dj];
           float x = acc[q][dj][di];
-          x = fmaf(t[q][di].x, sv[dj].x, x);
-          x = fmaf(t[q][di].y, sv[dj].y, x);
-          x = fmaf(t[q][di].z, sv[dj].z, x);
-          x = fmaf(t[q][di].w, sv[dj].w, x);
+          x = fmaf(tv.x, s4.x, x);
+          x = fmaf(tv.y, s4.y, x);
+          x = fmaf(tv.z, s4.z, x);
+          x = fmaf(tv.w, s4.w, x);
           acc[q][dj][di] = x;
         }
   }
@@ -1250,7 +1255,9 @@ TcDst* tc_create(kfbi_domain* D, const Plan& P) {
                                    SMEM_BYTES));
     if (D->desc.precision == KFBI_MIXED_FFT32) {
       const int M = D->M;
-      if (!fft_supported(M)) throw Status{KFBI_ERR_UNSUPPORTED, "FFT passes need M = 64 .. 1024, a power of two"};
+      if (!fft_supported(M))
+        throw Status{KFBI_ERR_UNSUPPORTED,
+                     "FFT passes need M = 32 N1, N1 in {2, 4, 6, 8, 12, 16, 24, 32, 48, 64}"};
       // W_M^j and exp(-i pi j / M), j < M, in float64 then rounded
       // (the exponent n2 k1 is reduced mod M before the angle is formed)
       std::vector<float2> tw(M), twb(M), tw2(M);
@@ -1270,8 +1277,9 @@ TcDst* tc_create(kfbi_domain* D, const Plan& P) {
       KFBI_CUDA(cudaMemcpy(T->twM, tw.data(), M * sizeof(float2), cudaMemcpyHostToDevice));
       KFBI_CUDA(cudaMemcpy(T->twB, twb.data(), M * sizeof(float2), cudaMemcpyHostToDevice));
       KFBI_CUDA(cudaMemcpy(T->tw2M, tw2.data(), M * sizeof(float2), cudaMemcpyHostToDevice));
-      fft_prepare(M);
+      fft_prepare_all();
       T->fft = true;
+      T->fft_rpb = M >= 2048 ? 4 : 8;
     }
     KFBI_CUDA(cudaDeviceGetAttribute(&T->nsm, cudaDevAttrMultiProcessorCount, D->device));
   } catch (...) {
@@ -1359,12 +1367,16 @@ double tc::pass_flops(const PassDesc& d) {
   return 3.0 * 2.0 * BC * BR * BK * (double)d.nrt * d.nct * d.nk;
 }
 
-void tc::launch_tc_pass(GroupArgs ga, int nsm, double work, cudaStream_t st) {
+void tc::launch_tc_pass(GroupArgs ga, int nsm, double work, cudaStream_t st, int max_ctas) {
   // CTA pairs only when every pair owns exactly one tile (the pair
   // exchange reuses the idle stage ring)
   if (ga.splitk < 1 || (ga.splitk == 2 && 2 * ga.total > nsm)) ga.splitk = 2 * ga.total <= nsm ? 2 : 1;
   const int pairs = ga.splitk == 2;
-  const int grid = pairs ? 2 * std::min(ga.total, nsm / 2) : std::min(ga.total, nsm);
+  // persistent CTAs without pairs: one per SM, or max_ctas (> 0) when the
+  // autotuner caps them (each CTA then takes more tiles; the per-tile
+  // arithmetic is the same)
+  const int cap = max_ctas > 0 ? std::min(max_ctas, nsm) : nsm;
+  const int grid = pairs ? 2 * std::min(ga.total, nsm / 2) : std::min(ga.total, cap);
   if (grid <= 0) return;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)grid, 1, 1);
@@ -1409,13 +1421,11 @@ static void tc_box_solve(kfbi_domain* D, double kre, double kim, int P, cudaStre
   const bool C = kim != 0.0;
   const float scale = (float)((2.0 / D->M) * (2.0 / D->M));
   if (T->fft) {
-    fft_pass(T, T->Rh, T->T1h, 0, 0.f, 0.f, P, nullptr, st);
-    fft_pass(T, T->T1h, T->T2h, C ? 0 : 1, (float)kre, scale, P, nullptr, st);
-    if (C)
-      KFBI_LAUNCH_P(KFBI_PROF_GRID, k_eig_cplx32, T->n1, 256, 0, st, T->T2h, (float*)nullptr, plane,
-                    T->Mp, T->n1, T->lam, (float)kre, (float)kim, scale, (const double*)nullptr);
-    fft_pass(T, T->T2h, T->T1h, 0, 0.f, 0.f, P, nullptr, st);
-    fft_pass(T, T->T1h, T->U, 0, 0.f, 0.f, P, nullptr, st);
+    // transform along x (written transposed); along y: transform, divide
+    // by the eigenvalues, transform back (one pass); transform along x
+    fft_pass(T, T->Rh, T->T1h, P, nullptr, st);
+    fft_solve(T, T->T1h, T->T2h, P, (float)kre, (float)kim, scale, nullptr, st);
+    fft_pass(T, T->T2h, T->U, P, nullptr, st, nullptr, false);
     return;
   }
   launch_pass(T, pass_desc(T, kMapR_hi, kMapR_lo, T->T1h, T->T1l, 0, P, 0.f, 0.f), st);
@@ -1478,22 +1488,20 @@ static void tc_apply_sparse(kfbi_domain* D, double kre, double kim, const double
     sp.kre = (float)kre;
     sp.kim = (float)kim;
     sp.cplx = C ? 1 : 0;
+    sp.dj = nullptr;
+    sp.dj_stride = 0;
     const float scale = (float)((2.0 / D->M) * (2.0 / D->M));
     // the first pass writes only the columns of the irregular rows; T1sh
     // (zeroed at creation, written by nothing else on an FFT domain) keeps
     // zeros in the others
-    fft_pass(T, nullptr, T->T1sh, 0, 0.f, 0.f, P, T->stop, st, &sp);
-    fft_pass(T, T->T1sh, T->T2h, C ? 0 : 1, (float)kre, scale, P, T->stop, st);
+    fft_pass(T, nullptr, T->T1sh, P, T->stop, st, &sp);
+    fft_solve(T, T->T1sh, T->U, P, (float)kre, (float)kim, scale, T->stop, st);
     if (C)
-      KFBI_LAUNCH_P(KFBI_PROF_GRID, k_eig_cplx32, T->n1, 256, 0, st, T->T2h, (float*)nullptr, plane,
-                    Mp, T->n1, T->lam, (float)kre, (float)kim, scale, T->stop);
-    fft_pass(T, T->T2h, T->U, 0, 0.f, 0.f, P, T->stop, st);
-    if (C)
-      KFBI_LAUNCH_P(KFBI_PROF_EXTRACT, k_gather_extract<true>, D->nb, 32 * GE_WARPS, 0, st, T->U, T->S32, Mp,
+      KFBI_LAUNCH_P(KFBI_PROF_EXTRACT, (k_gather_extract<true, true>), D->nb, 32 * GE_WARPS, 0, st, T->U, T->S32, Mp,
                     plane, D->d_node_gidx, tb.w, tb.a, tb.b, D->nb, phi,
                     ps, (float)kre, (float)kim, out, os, T->stop);
     else
-      KFBI_LAUNCH_P(KFBI_PROF_EXTRACT, k_gather_extract<false>, D->nb, 32 * GE_WARPS, 0, st, T->U, T->S32, Mp,
+      KFBI_LAUNCH_P(KFBI_PROF_EXTRACT, (k_gather_extract<false, true>), D->nb, 32 * GE_WARPS, 0, st, T->U, T->S32, Mp,
                     plane, D->d_node_gidx, tb.w, tb.a, tb.b, D->nb, phi,
                     ps, (float)kre, (float)kim, out, os, T->stop);
     KFBI_CHECK_LAUNCH();
@@ -1525,11 +1533,11 @@ static void tc_apply_sparse(kfbi_domain* D, double kre, double kim, const double
   d3.stop = T->stop;
   launch_pass(T, d3, st);
   if (C)
-    KFBI_LAUNCH_P(KFBI_PROF_EXTRACT, k_gather_extract<true>, D->nb, 32 * GE_WARPS, 0, st, T->U, T->S32, Mp,
+    KFBI_LAUNCH_P(KFBI_PROF_EXTRACT, (k_gather_extract<true, false>), D->nb, 32 * GE_WARPS, 0, st, T->U, T->S32, Mp,
                   plane, D->d_node_gidx, tb.w, tb.a, tb.b, D->nb, phi,
                   ps, (float)kre, (float)kim, out, os, T->stop);
   else
-    KFBI_LAUNCH_P(KFBI_PROF_EXTRACT, k_gather_extract<false>, D->nb, 32 * GE_WARPS, 0, st, T->U, T->S32, Mp,
+    KFBI_LAUNCH_P(KFBI_PROF_EXTRACT, (k_gather_extract<false, false>), D->nb, 32 * GE_WARPS, 0, st, T->U, T->S32, Mp,
                   plane, D->d_node_gidx, tb.w, tb.a, tb.b, D->nb, phi,
                   ps, (float)kre, (float)kim, out, os, T->stop);
   KFBI_CHECK_LAUNCH();

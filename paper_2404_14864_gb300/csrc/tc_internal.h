@@ -52,8 +52,9 @@ struct GroupArgs {
 
 __global__ void k_tc_pass(const __grid_constant__ GroupArgs ga);
 // Launch one pass (ga.splitk < 1: chosen from the tile count; CTA pairs
-// when the tiles fill at most half of the SMs).  work: flops for profiling.
-void launch_tc_pass(GroupArgs ga, int nsm, double work, cudaStream_t st);
+// when the tiles fill at most half of the SMs).  work: flops for profiling;
+// max_ctas > 0 caps the persistent grid of a pass without pairs.
+void launch_tc_pass(GroupArgs ga, int nsm, double work, cudaStream_t st, int max_ctas = 0);
 // Tensor flops of one pass of an instance (all its tiles and K-blocks).
 double pass_flops(const PassDesc& d);
 extern const int kPassThreads;
@@ -96,6 +97,7 @@ struct TcDst {
   float2* twM = nullptr;
   float2* twB = nullptr;
   float2* tw2M = nullptr;
+  int fft_rpb = 8;  // rows (warps) per block of this domain's FFT passes (4 or 8)
 };
 
 
@@ -116,18 +118,68 @@ struct FftSparseRhs {
   int ps;
   float kre, kim;
   int cplx;
+  // batched GMRES: the density is V[*dj], phi + (*dj) * dj_stride doubles
+  const int* dj;
+  long long dj_stride;
+};
+
+// Largest dynamic shared memory a block may opt into (227 KiB).
+constexpr int kMaxSmemOptin = 232448;
+
+// One instance's share of an FFT pass (fft_dst.cu).  Rows r_lo ..
+// r_lo + rblocks * rpb - 1 of each plane group; rows >= n1 are zero rows.
+struct FftDesc {
+  const float* in;  // P planes of Mp x Mp (unused when sparse)
+  float* out;       // P planes, written transposed
+  const float2* twM;
+  const float2* twB;
+  const float2* tw2M;
+  const float* lam;
+  int N1, Mp, n1;
+  int solve;    // 0: transform; 1: transform, divide by lambda_r + lambda_c - kappa, transform
+  int pw;       // planes per warp: 2 for a solve with complex kappa, else 1
+  int pgroups;  // plane groups (blocks per row block): P / pw
+  int sparse;   // rows built from the corrected irregular nodes (sp)
+  int transpose;  // 1: out[p][c][r] (transposed), 0: out[p][r][c] (rows in place)
+  float kre, kim, scale;
+  int r_lo, rblocks;
+  const int* active;   // instance flag (nullptr: always)
+  const double* stop;  // as KFBI_STOP_RETURN
+  FftSparseRhs sp;
+};
+
+// A launch: one descriptor by value (descs == nullptr), or descriptor
+// array and per-block (instance, block within instance) map.
+struct FftGroup {
+  const FftDesc* descs;
+  const int2* blk;
+  FftDesc one;
+  int rpb;
 };
 
 // FP32 FFT passes (fft_dst.cu).  fft_pass transforms every row of P planes
-// of `in` and writes out transposed (mode 1: eigenvalue division of the box
-// solve); with sp the rows are built from the corrected irregular nodes
-// instead of read from `in`; stop as KFBI_STOP_RETURN.
+// of `in` and writes out transposed (or, transpose false, each row in
+// place); with sp the rows are built from the
+// corrected irregular nodes instead of read from `in`.  fft_solve is the
+// middle pass of a box solve: per row forward DST, division by
+// lambda_r + lambda_c - kappa (times scale), inverse DST, written transposed.
+// stop as KFBI_STOP_RETURN.
 bool fft_supported(int M);
-size_t fft_smem_bytes(int M);
-void fft_prepare(int M);
+size_t fft_smem(int M, int rpb, int pw);
+bool fft_rpb_fits(int M, int rpb, int pw);
 double fft_pass_flops(int M, int rows);
-void fft_pass(const TcDst* T, const float* in, float* out, int mode, float kre, float scale, int P,
-              const double* stop, cudaStream_t st, const FftSparseRhs* sp = nullptr);
+void fft_prepare_all();
+FftDesc fft_desc(const TcDst* T, const float* in, float* out, int P, bool solve, float kre,
+                 float kim, float scale, const double* stop, const FftSparseRhs* sp, int rpb);
+int fft_blocks(const FftDesc& d);
+double fft_desc_flops(const FftDesc& d, int rpb);
+double fft_desc_bytes(const FftDesc& d, int rpb);
+void fft_launch(const FftGroup& g, int M, bool sparse, int nblocks, size_t smem, int prof_class,
+                double flops, double bytes, cudaStream_t st);
+void fft_pass(const TcDst* T, const float* in, float* out, int P, const double* stop,
+              cudaStream_t st, const FftSparseRhs* sp = nullptr, bool transpose = true);
+void fft_solve(const TcDst* T, const float* in, float* out, int P, float kre, float kim,
+               float scale, const double* stop, cudaStream_t st);
 
 // Device tensor map of one of the domain's pass output planes (T1, T2 pairs
 // or U); throws for any other pointer.

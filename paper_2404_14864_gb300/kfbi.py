@@ -98,6 +98,24 @@ class ServerStats(ctypes.Structure):
 
 REQ_QUEUED, REQ_RESIDENT, REQ_DONE, REQ_FAILED = 0, 1, 2, 3
 
+
+class BatchTuning(ctypes.Structure):
+    _fields_ = [("engine", ctypes.c_int), ("M", ctypes.c_int), ("instances", ctypes.c_int),
+                ("n_candidates", ctypes.c_int), ("chosen", ctypes.c_int),
+                ("param", (ctypes.c_int * 2) * 4), ("us", ctypes.c_double * 4)]
+
+    def as_dict(self):
+        n = int(self.n_candidates)
+        if self.engine == 1:
+            cands = [{"rows_per_block": int(self.param[c][0]), "us": float(self.us[c])}
+                     for c in range(n)]
+        else:
+            cands = [{"tile_order": int(self.param[c][0]), "ctas": int(self.param[c][1]),
+                      "us": float(self.us[c])} for c in range(n)]
+        return {"engine": "fft32" if self.engine == 1 else "tf32", "M": int(self.M),
+                "instances": int(self.instances), "chosen": int(self.chosen),
+                "candidates": cands}
+
 _lib = None
 _VP = ctypes.c_void_p
 
@@ -148,6 +166,7 @@ def lib():
         "kfbi_profile_read": (S, [ctypes.c_int, ctypes.POINTER(ctypes.c_longlong),
                                   ctypes.POINTER(ctypes.c_double)]),
         "kfbi_profile_work": (S, [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
+        "kfbi_profile_bytes": (S, [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
         "kfbi_box_solve_noalloc": (S, [ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                        ctypes.c_double, ctypes.c_double, _VP, _VP, _VP]),
         "kfbi_batch_create": (S, [ctypes.POINTER(_VP), ctypes.c_int, _VP, ctypes.POINTER(_VP)]),
@@ -157,6 +176,9 @@ def lib():
         "kfbi_batch_tuning": (S, [_VP, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double),
                                   ctypes.POINTER(ctypes.c_double)]),
         "kfbi_batch_last_error": (ctypes.c_char_p, [_VP]),
+        "kfbi_batch_tuning_count": (ctypes.c_int, [_VP]),
+        "kfbi_batch_tuning_get": (S, [_VP, ctypes.c_int, ctypes.POINTER(BatchTuning)]),
+        "kfbi_batch_force_candidate": (S, [_VP, ctypes.c_int]),
         "kfbi_plan_create": (S, [ctypes.POINTER(DomainDesc), ctypes.POINTER(_VP)]),
         "kfbi_plan_destroy": (None, [_VP]),
         "kfbi_plan_size": (ctypes.c_longlong, [_VP, ctypes.c_int]),
@@ -272,6 +294,13 @@ def kfbi_profile_work(cls):
     return float(w.value)
 
 
+def kfbi_profile_bytes(cls):
+    """Algorithmic bytes moved by the recorded launches of a class."""
+    w = ctypes.c_double()
+    _check(lib().kfbi_profile_bytes(int(cls), ctypes.byref(w)))
+    return float(w.value)
+
+
 # ----------------------------------------------------------------------------
 # C-ABI entry points with the same names
 # ----------------------------------------------------------------------------
@@ -305,6 +334,13 @@ def kfbi_solve_density(h, kappa, b, phi, stream=None):
     _check(lib().kfbi_solve_density(h, k.real, k.imag, _ptr(b), _ptr(phi), ctypes.byref(info),
                                     _stream(stream)), h)
     return info.as_dict()
+
+
+def fft_supported(M):
+    """Whether KFBI_MIXED_FFT32 has a transform for grid size M (M = 32 N1,
+    N1 in {2, 4, 6, 8, 12, 16, 24, 32, 48, 64})."""
+    M = int(M)
+    return M % 32 == 0 and M // 32 in (2, 4, 6, 8, 12, 16, 24, 32, 48, 64)
 
 
 def kfbi_box_solve_noalloc(M, box_lo, box_hi, kappa, rhs, u, stream=None):
@@ -528,12 +564,20 @@ class Batch:
         return [infos[i].as_dict() for i in range(n)]
 
     def tuning(self):
-        o = ctypes.c_int()
-        a = ctypes.c_double()
-        b = ctypes.c_double()
-        _check(lib().kfbi_batch_tuning(self.h, ctypes.byref(o), ctypes.byref(a), ctypes.byref(b)))
-        return {"tile_order": int(o.value), "us_natural": float(a.value),
-                "us_largest_first": float(b.value)}
+        """The autotuner's records: one per FFT grid size and one for the TF32
+        instances (candidates, their measured microseconds, the kept one)."""
+        L = lib()
+        out = []
+        for i in range(L.kfbi_batch_tuning_count(self.h)):
+            t = BatchTuning()
+            _check(L.kfbi_batch_tuning_get(self.h, i, ctypes.byref(t)))
+            out.append(t.as_dict())
+        return out
+
+    def force_candidate(self, candidate):
+        """Use candidate (modulo each group's count) everywhere from the next
+        step on, without timing; -1 restores the autotuner."""
+        _check(lib().kfbi_batch_force_candidate(self.h, int(candidate)))
 
 
 class Server:
@@ -570,8 +614,9 @@ class Server:
 
     def submit(self, desc_dict, equation, steps, dt, arrival, u0, lap_u0, g, theta=0.25, u1=None,
                lap_u1=None, src_init=None, src_profile=None, src_coef=None, potential=None,
-               tol=1e-10, maxit=2000):
-        """Queue a request (grids (M-1, M-1); g (steps, nb)); returns its id."""
+               tol=1e-10, maxit=2000, precision=KFBI_MIXED_TF32):
+        """Queue a request (grids (M-1, M-1); g (steps, nb)); returns its id.
+        precision: KFBI_MIXED_TF32 or KFBI_MIXED_FFT32 (sizes with an FFT pass)."""
         cplx = equation == KFBI_SCHRODINGER
         gt = np.complex128 if cplx else np.float64
 
@@ -589,7 +634,7 @@ class Server:
         def p(a):
             return None if a is None else ctypes.c_void_p(a.ctypes.data)
 
-        r = Request(make_desc(desc_dict, KFBI_MIXED_TF32, self.restart, tol, maxit), int(equation),
+        r = Request(make_desc(desc_dict, int(precision), self.restart, tol, maxit), int(equation),
                     int(steps), float(dt), float(theta), float(arrival), p(keep["u0"]),
                     p(keep["lap_u0"]), p(keep["u1"]), p(keep["lap_u1"]), p(keep["g"]),
                     p(keep["src_init"]), p(keep["src_profile"]), p(keep["src_coef"]),

@@ -1,9 +1,12 @@
 """GPU tests of the batched path (kfbi_batch_step): instances of uneven
 size, curve and equation advance together in grouped launches (one
-persistent tcgen05 launch over all instances' tiles per pass, a CUDA graph
-per lockstep GMRES iteration).  Each instance must agree with the same
-domain stepped alone to 1e-10 relative (both solve the BIE to GMRES
-tolerance 1e-12; observed ~2e-12) and match the oracle."""
+persistent tcgen05 launch over all TF32 instances' tiles per pass, one FFT
+launch per grid size for the FFT32 instances, a CUDA graph per lockstep
+GMRES iteration).  Each instance must agree with the same domain stepped
+alone to 1e-10 relative (both solve the BIE to GMRES tolerance 1e-12;
+observed ~2e-12) and match the oracle's steps to 1e-8 (the mixed step bound
+of the single-domain tests), with every configuration the autotuner can
+choose."""
 
 import math
 
@@ -79,11 +82,20 @@ class _Run:
         return st.step_schrodinger(s, g)
 
 
-def test_batch_steps_equal_single_instance_steps():
+def _prec(engine, desc):
+    """The engine's precision, TF32 where the FFT pass has no transform of
+    that size (an "fft32" batch then mixes both engines)."""
+    if engine == "fft32" and kfbi.fft_supported(desc["M"]):
+        return kfbi.KFBI_MIXED_FFT32
+    return kfbi.KFBI_MIXED_TF32
+
+
+@pytest.mark.parametrize("engine", ["tf32", "fft32"])
+def test_batch_steps_equal_single_instance_steps(engine):
     runs = [_Run(k, d) for k, d in _instances()]
     steps = 3
     # batched
-    doms = [kfbi.Domain(r.desc, kfbi.KFBI_MIXED_TF32, tol=1e-12, maxit=800) for r in runs]
+    doms = [kfbi.Domain(r.desc, _prec(engine, r.desc), tol=1e-12, maxit=800) for r in runs]
     states = [r.make_state(d) for r, d in zip(runs, doms)]
     batch = kfbi.Batch(doms)
     for k in range(steps):
@@ -93,33 +105,99 @@ def test_batch_steps_equal_single_instance_steps():
     ub = [host(s.get_u()) for s in states]
     # alone
     for r, u_b in zip(runs, ub):
-        d1 = kfbi.Domain(r.desc, kfbi.KFBI_MIXED_TF32, tol=1e-12, maxit=800)
+        d1 = kfbi.Domain(r.desc, _prec(engine, r.desc), tol=1e-12, maxit=800)
         s1 = r.make_state(d1)
         for k in range(steps):
             r.step_alone(s1, k)
         u1 = host(s1.get_u())
         assert rel_linf(u_b, u1) <= 1e-10, r.desc["M"]
+    # the autotuner timed every candidate of every group and kept the fastest
     t = batch.tuning()
-    assert t["tile_order"] in (0, 1) and t["us_natural"] > 0
+    engines = {x["engine"] for x in t}
+    assert "tf32" in engines
+    if engine == "fft32":
+        fft_ms = sorted(x["M"] for x in t if x["engine"] == "fft32")
+        assert fft_ms == sorted({r.desc["M"] for r in runs if r.desc["M"] != 96})
+    for x in t:
+        us = [c["us"] for c in x["candidates"]]
+        assert len(us) >= 1 and all(u > 0 for u in us)
+        assert us[x["chosen"]] == min(us)
 
 
-def test_batch_matches_oracle_for_one_instance():
-    r = _Run("heat", W.domain_desc(128, W.star()))
-    r2 = _Run("wave", W.domain_desc(96, W.ellipse()))
-    doms = [kfbi.Domain(x.desc, kfbi.KFBI_MIXED_TF32, tol=1e-12, maxit=800) for x in (r, r2)]
-    states = [x.make_state(d) for x, d in zip((r, r2), doms)]
-    batch = kfbi.Batch(doms)
+def _oracle_stepper(r):
+    """The oracle's stepper for a run, initialised as make_state does."""
     d = oracle.make_domain(r.desc)
-    orc = oracle.HeatStepper(d, r.tau, 1e-12)
-    ex = r.ex
-    orc.init(ex.u(r.X, r.Y, 0), ex.lap(r.X, r.Y, 0), ex.src(r.X, r.Y, 0) + ex.src(r.X, r.Y, r.tau))
-    for k in range(2):
-        ins = [x.inputs(k) for x in (r, r2)]
-        batch.step(states, [g for g, _ in ins], [s for _, s in ins])
-        t1 = (k + 1) * r.tau
-        U = orc.step(ex.u(r.zx, r.zy, t1), ex.src(r.X, r.Y, t1) + ex.src(r.X, r.Y, t1 + r.tau))
-    m = d.interior_inside()
-    assert rel_linf(host(states[0].get_u())[m], U[m]) <= 1e-8
+    X, Y, ex, tau = r.X, r.Y, r.ex, r.tau
+    if r.kind == "heat":
+        st = oracle.HeatStepper(d, tau, 1e-12)
+        st.init(ex.u(X, Y, 0), ex.lap(X, Y, 0), ex.src(X, Y, 0) + ex.src(X, Y, tau))
+    elif r.kind == "wave":
+        st = oracle.WaveStepper(d, tau, 1e-12)
+        st.init(ex.u(X, Y, 0), ex.lap(X, Y, 0), ex.u(X, Y, tau), ex.lap(X, Y, tau))
+    else:
+        st = oracle.SchrodingerStepper(d, tau, 1e-12)
+        st.init(ex.u(X, Y, 0), ex.lap(X, Y, 0))
+    return d, st
+
+
+def _oracle_step(r, st, k):
+    X, Y, ex, tau = r.X, r.Y, r.ex, r.tau
+    if r.kind == "heat":
+        t1 = (k + 1) * tau
+        return st.step(ex.u(r.zx, r.zy, t1), ex.src(X, Y, t1) + ex.src(X, Y, t1 + tau))
+    if r.kind == "wave":
+        return st.step(ex.u(r.zx, r.zy, (k + 2) * tau))
+    return st.step(ex.u(r.zx, r.zy, (k + 1) * tau), np.zeros_like(X))
+
+
+def _check_batch_against_oracle(runs, engine, steps, force=None, fields=False):
+    doms = [kfbi.Domain(x.desc, _prec(engine, x.desc), tol=1e-12, maxit=800) for x in runs]
+    states = [x.make_state(d) for x, d in zip(runs, doms)]
+    batch = kfbi.Batch(doms)
+    if force is not None:
+        batch.force_candidate(force)
+    orcs = [_oracle_stepper(x) for x in runs]
+    for k in range(steps):
+        ins = [x.inputs(k) for x in runs]
+        infos = batch.step(states, [g for g, _ in ins], [s for _, s in ins])
+        assert all(i["converged"] for i in infos)
+        Us = [_oracle_step(x, st, k) for x, (_, st) in zip(runs, orcs)]
+    # every instance, not only the first
+    for x, st, (d, _), U in zip(runs, states, orcs, Us):
+        m = d.interior_inside()
+        assert rel_linf(host(st.get_u())[m], U[m]) <= 1e-8, (x.kind, x.desc["M"])
+    tun = batch.tuning()
+    us = [host(st.get_u()) for st in states]
+    batch.close()
+    for d in doms:
+        d.close()
+    return (tun, us) if fields else tun
+
+
+@pytest.mark.parametrize("engine", ["tf32", "fft32"])
+def test_batch_matches_oracle_for_every_instance(engine):
+    runs = [_Run("heat", W.domain_desc(128, W.star())), _Run("wave", W.domain_desc(96, W.ellipse())),
+            _Run("schr", W.domain_desc(64, W.flower())), _Run("heat", W.domain_desc(192, W.ellipse()))]
+    _check_batch_against_oracle(runs, engine, 2)
+
+
+def test_batch_every_autotuner_candidate_matches_oracle():
+    """Each launch configuration the autotuner may pick (rows per block of
+    the FFT passes; tile order and persistent CTAs of the tensor passes),
+    forced in turn, gives the oracle's steps: FFT instances of two sizes
+    (one complex) and TF32 instances in one batch.  No candidate changes a
+    tile's or a row's arithmetic, so all give the same bits."""
+    runs = [_Run("heat", W.domain_desc(128, W.star())), _Run("schr", W.domain_desc(192, W.flower())),
+            _Run("wave", W.domain_desc(96, W.ellipse())), _Run("heat", W.domain_desc(130, W.star()))]
+    fields = []
+    for candidate in range(4):
+        tun, us = _check_batch_against_oracle(runs, "fft32", 2, force=candidate, fields=True)
+        assert {x["engine"] for x in tun} == {"fft32", "tf32"}
+        for x in tun:
+            assert x["chosen"] == candidate % len(x["candidates"])
+        fields.append(us)
+    for us in fields[1:]:
+        assert all(np.array_equal(a, b) for a, b in zip(us, fields[0]))
 
 
 def test_batch_nonlinear_schrodinger_equals_single_steps():

@@ -3,14 +3,18 @@ CUDA cores; correction, extraction, GMRES and refinement as for
 KFBI_MIXED_TF32) against the float64 oracle.
 
 Stated bound for the fast operator: 2e-5 relative L-infinity, the same as
-the TF32 path.  Arithmetic behind it: each pass is a complex FFT of length
-M in FP32 (log2 M radix-2 stages, twiddles correctly rounded from float64:
-a few units of 2^-24 per stage, ~1.3e-7 of the largest output measured on
-the host prototype at M = 1024) plus an O(1)-operation untangling; four
-passes, the FP32 eigenvalue division and the FP32 correction and
-extraction stay well below 1e-5.  Steps use the refined (accurate) operator
-and must match the oracle to 1e-8, with the error against the exact
-solution at most 1.1x the float64 path's.
+the TF32 path.  Arithmetic behind it: each row transform is a complex FFT
+of length M in FP32 (log2 M radix-2 stages, or one radix-3 stage and
+radix-2 stages, twiddles correctly rounded from float64: a few units of
+2^-24 per stage, ~1.3e-7 of the largest output measured on the host
+prototype at M = 1024) plus an O(1)-operation untangling; four row
+transforms (the middle two in one pass), the FP32 eigenvalue division and
+the FP32 correction and extraction stay well below 1e-5.  Sizes: powers of
+two and three times powers of two from 64 to 2048, each several 128-wide
+tiles with a ragged tail (M - 1 unknowns per row on Mp padded columns).
+Steps use the refined (accurate) operator and must match the oracle to
+1e-8, with the error against the exact solution at most 1.1x the float64
+path's.
 """
 
 import numpy as np
@@ -27,7 +31,10 @@ FFT = kfbi.KFBI_MIXED_FFT32
 
 CASES = [
     ("star-64", W.domain_desc(64, W.star())),
+    ("star-192", W.domain_desc(192, W.star())),
     ("ellipse-256", W.domain_desc(256, W.ellipse())),
+    ("flower-384", W.domain_desc(384, W.flower())),
+    ("flower-768", W.domain_desc(768, W.flower())),
     ("ellipse-1024", W.domain_desc(1024, W.ellipse())),
 ]
 
@@ -141,7 +148,7 @@ def _run_wave(desc, prec, steps):
     return host(st.get_u()), ex.u(X, Y, (steps + 1) * tau), tau
 
 
-@pytest.mark.parametrize("M", [128, 1024])
+@pytest.mark.parametrize("M", [128, 192, 1024])
 def test_fft_wave_steps(M):
     desc = W.domain_desc(M, W.ellipse())
     d = oracle.make_domain(desc)
@@ -197,7 +204,20 @@ def test_fft_solve_density_refined(kappa):
     assert rel_linf(host(phi), x_or) <= STEP_BOUND
 
 
-@pytest.mark.parametrize("M", [96, 130, 2048])
+def test_fft_operator_2048():
+    """The largest transform (M = 2048, N1 = 64: two 32-point DFTs per lane),
+    real and complex kappa, against the oracle."""
+    desc = W.domain_desc(2048, W.ellipse())
+    h = (desc["hi"] - desc["lo"]) / desc["M"]
+    dom = kfbi.Domain(desc, FFT)
+    for kappa in (2.0 / h, 2.0j / (0.5 * h)):
+        d, phi, f = _inputs(desc, isinstance(kappa, complex))
+        a = host(dom.apply_operator(kappa, dev(phi)))
+        assert rel_linf(a, oracle.apply_operator(d, kappa, phi)) <= BOUND
+    dom.close()
+
+
+@pytest.mark.parametrize("M", [96, 130, 160, 4096])
 def test_fft_unsupported_sizes_are_refused(M):
     desc = W.domain_desc(M, W.star())
     with pytest.raises(kfbi.KfbiError) as e:

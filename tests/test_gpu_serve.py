@@ -4,8 +4,9 @@ heat, wave and Schroedinger requests of uneven size.
 - A request's final field is the same, bit for bit, when it runs alone and
   when it shares every tick with other requests that come and go.
 - A served request agrees with the single-domain steppers to 1e-10 relative
-  (both solve the BIE to GMRES tolerance 1e-12), and a served heat request
-  matches the oracle's steps to the mixed path's step bound (1e-8).
+  (both solve the BIE to GMRES tolerance 1e-12), and served heat, wave and
+  Schroedinger requests match the oracle's steps to the mixed path's step
+  bound (1e-8), on KFBI_MIXED_TF32 and KFBI_MIXED_FFT32 domains alike.
 - Admission: at most max_resident requests are on the device; a request
   that does not fit the memory budget waits (first come first served) until
   an earlier one retires; one larger than the whole budget fails alone.
@@ -30,13 +31,23 @@ def _lib():
     ensure_built()
 
 
-def _submit(srv, kind, desc, steps, arrival, inputs=None):
+PRECS = {"tf32": kfbi.KFBI_MIXED_TF32, "fft32": kfbi.KFBI_MIXED_FFT32}
+
+
+def _prec(name, desc):
+    """FFT32 where the grid has an FFT pass (an "fft32" mix then holds both engines)."""
+    if name == "fft32" and not kfbi.fft_supported(desc["M"]):
+        return kfbi.KFBI_MIXED_TF32
+    return PRECS[name]
+
+
+def _submit(srv, kind, desc, steps, arrival, inputs=None, prec="tf32"):
     x = inputs or W.request_inputs(kind, desc, steps)
     return srv.submit(desc, x["equation"], steps, x["dt"], arrival, x["u0"], x["lap_u0"], x["g"],
                       theta=x.get("theta", 0.25), u1=x.get("u1"), lap_u1=x.get("lap_u1"),
                       src_init=x.get("src_init"), src_profile=x.get("src_profile"),
                       src_coef=x.get("src_coef"), potential=x.get("potential"), tol=TOL,
-                      maxit=800)
+                      maxit=800, precision=_prec(prec, desc))
 
 
 def _mix():
@@ -62,10 +73,11 @@ def _drain(srv, n, max_ticks=200):
     raise AssertionError("requests did not finish")
 
 
-def test_served_result_is_the_same_alone_and_in_the_mix():
+@pytest.mark.parametrize("prec", ["tf32", "fft32"])
+def test_served_result_is_the_same_alone_and_in_the_mix(prec):
     mix = _mix()
     srv = kfbi.Server(max_resident=3, plan_threads=0, restart=50)
-    ids = [_submit(srv, k, d, s, a) for k, d, s, a in mix]
+    ids = [_submit(srv, k, d, s, a, prec=prec) for k, d, s, a in mix]
     seen = _drain(srv, len(ids))
     assert max(seen) == 3  # the slot limit was reached: requests overlapped
     mixed = []
@@ -79,25 +91,26 @@ def test_served_result_is_the_same_alone_and_in_the_mix():
     srv.close()
     for (k, d, s, a), u_mix in zip(mix, mixed):
         alone = kfbi.Server(max_resident=1, plan_threads=0, restart=50)
-        j = _submit(alone, k, d, s, 0.0)
+        j = _submit(alone, k, d, s, 0.0, prec=prec)
         _drain(alone, 1)
         u_alone = alone.result(j)
         assert np.array_equal(u_alone, u_mix), (k, d["M"], rel_linf(u_mix, u_alone))
         alone.close()
 
 
-def test_served_request_agrees_with_single_domain_steppers():
+@pytest.mark.parametrize("prec", ["tf32", "fft32"])
+def test_served_request_agrees_with_single_domain_steppers(prec):
     rng = np.random.Generator(np.random.PCG64(5))
     for kind in ("heat", "wave", "schrodinger"):
         desc = W.domain_desc(128, W.random_star(rng))
         steps = 3
         x = W.request_inputs(kind, desc, steps)
         srv = kfbi.Server(max_resident=2, plan_threads=1, restart=50)
-        i = _submit(srv, kind, desc, steps, 0.0, x)
+        i = _submit(srv, kind, desc, steps, 0.0, x, prec=prec)
         _drain(srv, 1)
         u_srv = srv.result(i)
         srv.close()
-        dom = kfbi.Domain(desc, kfbi.KFBI_MIXED_TF32, restart=50, tol=TOL, maxit=800)
+        dom = kfbi.Domain(desc, _prec(prec, desc), restart=50, tol=TOL, maxit=800)
         st = kfbi.State(dom, x["equation"])
         if kind == "heat":
             st.init_heat(x["dt"], dev(x["u0"]), dev(x["lap_u0"]), dev(x["src_init"]))
@@ -117,21 +130,38 @@ def test_served_request_agrees_with_single_domain_steppers():
         assert rel_linf(u_srv, u1) <= 1e-10, kind
 
 
-def test_served_heat_request_matches_oracle():
-    desc = W.domain_desc(128, W.star())
-    steps = 2
-    x = W.request_inputs("heat", desc, steps)
+@pytest.mark.parametrize("prec", ["tf32", "fft32"])
+def test_served_requests_match_oracle(prec):
+    """Heat, wave and Schroedinger requests served together (one tick steps
+    all three) against the oracle's steppers on the same inputs."""
+    rng = np.random.Generator(np.random.PCG64(17))
+    reqs = [("heat", W.domain_desc(128, W.star()), 2), ("wave", W.domain_desc(192, W.ellipse()), 2),
+            ("schrodinger", W.domain_desc(64, W.random_star(rng)), 3)]
+    xs = [W.request_inputs(k, d, n) for k, d, n in reqs]
     srv = kfbi.Server(max_resident=4, plan_threads=0, restart=50)
-    i = _submit(srv, "heat", desc, steps, 0.0, x)
-    _drain(srv, 1)
-    u = srv.result(i)
-    d = oracle.make_domain(desc)
-    orc = oracle.HeatStepper(d, x["dt"], 1e-12)
-    orc.init(x["u0"], x["lap_u0"], x["src_init"])
-    for n in range(steps):
-        U = orc.step(x["g"][n], x["src_coef"][n] * x["src_profile"])
-    m = d.interior_inside()
-    assert rel_linf(u[m], U[m]) <= 1e-8
+    ids = [_submit(srv, k, d, n, 0.0, x, prec=prec) for (k, d, n), x in zip(reqs, xs)]
+    _drain(srv, len(ids))
+    for (kind, desc, steps), x, i in zip(reqs, xs, ids):
+        u = srv.result(i)
+        d = oracle.make_domain(desc)
+        if kind == "heat":
+            orc = oracle.HeatStepper(d, x["dt"], 1e-12)
+            orc.init(x["u0"], x["lap_u0"], x["src_init"])
+            for n in range(steps):
+                U = orc.step(x["g"][n], x["src_coef"][n] * x["src_profile"])
+        elif kind == "wave":
+            orc = oracle.WaveStepper(d, x["dt"], 1e-12)
+            orc.init(x["u0"], x["lap_u0"], x["u1"], x["lap_u1"], theta=x["theta"])
+            for n in range(steps):
+                U = orc.step(x["g"][n])
+        else:
+            orc = oracle.SchrodingerStepper(d, x["dt"], 1e-12)
+            orc.init(x["u0"], x["lap_u0"])
+            for n in range(steps):
+                U = orc.step(x["g"][n], x["potential"])
+        m = d.interior_inside()
+        assert rel_linf(u[m], U[m]) <= 1e-8, (kind, desc["M"])
+    srv.close()
 
 
 def test_admission_by_slots_memory_and_fifo():
