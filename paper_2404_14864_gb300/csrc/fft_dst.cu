@@ -38,8 +38,10 @@
 // {2, 4, 6, 8, 12, 16, 24, 32, 48, 64}, i.e. M = 64 .. 2048 with M / 32 a
 // power of two or three times one.
 //
-// One warp per row (and per plane of a complex solve), RPB rows per block
-// (4 or 8, chosen at launch).  One kernel per N1; a block of a grouped launch
+// One warp per row (and per plane of a complex solve) for N1 >= 32; for
+// smaller N1 a warp carries floor(32 / N1) rows so that every lane works in
+// the 32-point DFTs and the untangling.  RPB warps per block (4 or 8, chosen
+// at launch).  One kernel per N1; a block of a grouped launch
 // may belong to any instance of that size: a per-block map gives its
 // instance descriptor.
 #include <algorithm>
@@ -148,72 +150,93 @@ __device__ __forceinline__ float yodd(const float* xr, int n, int M) {
   return n < M ? xr[n - 1] : -xr[2 * M - n - 1];
 }
 
-// In-place DST-I of the row held in buf (as floats: buf[n-1] = x_n on
-// entry, buf[c] = DST_{c+1} on exit, c = 0 .. M-2).  buf holds N1 x 33
-// float2; lanes of the warp call it together.
+// Rows per warp: for N1 < 32 the 32-point DFTs of one row occupy only N1
+// lanes, so a warp carries R = floor(32 / N1) rows and lane L works on row
+// L / N1 in the second step (every lane busy for N1 = 2, 4, 8, 16).
+__host__ __device__ constexpr int rows_per_warp(int N1) { return N1 >= 32 ? 1 : 32 / N1; }
+
+// In-place DST-I of the R rows of a warp: row rho held in buf + rho stride
+// (as floats: buf[n-1] = x_n on entry, buf[c] = DST_{c+1} on exit,
+// c = 0 .. M-2).  Each row buffer holds N1 x 33 float2; the lanes of the
+// warp call it together.
 template <int N1>
-__device__ __forceinline__ void row_dst(float2* buf, int lane, const float2* s_tw,
-                                        const float2* s_twb, const float2* s_tw2) {
+__device__ __forceinline__ void rows_dst(float2* buf, size_t stride, int lane, const float2* s_tw,
+                                         const float2* s_twb, const float2* s_tw2) {
   constexpr int M = 32 * N1;
-  float* xr = reinterpret_cast<float*>(buf);
-  // step 1: N1-point DFTs over n1 of z_{32 n1 + lane}, then W_M^{lane k1}
-  float2 a[N1];
+  constexpr int R = rows_per_warp(N1);
+  // step 1 (each row): N1-point DFTs over n1 of z_{32 n1 + lane}, then
+  // W_M^{lane k1}, written transposed into the row's buffer
 #pragma unroll
-  for (int q = 0; q < N1; ++q) {
-    const int m = 32 * q + lane;
-    a[q] = make_float2(yodd(xr, 2 * m, M), yodd(xr, 2 * m + 1, M));
+  for (int rho = 0; rho < R; ++rho) {
+    float2* b_ = buf + rho * stride;
+    const float* xr = reinterpret_cast<const float*>(b_);
+    float2 a[N1];
+#pragma unroll
+    for (int q = 0; q < N1; ++q) {
+      const int m = 32 * q + lane;
+      a[q] = make_float2(yodd(xr, 2 * m, M), yodd(xr, 2 * m + 1, M));
+    }
+    dft<N1, 32>(a, s_tw);
+    __syncwarp();  // every lane has read its part of the row before the transpose overwrites it
+#pragma unroll
+    for (int k1 = 0; k1 < N1; ++k1) b_[k1 * 33 + lane] = cmul(a[k1], s_twb[k1 * 32 + lane]);
   }
-  dft<N1, 32>(a, s_tw);
-  __syncwarp();  // every lane has read its part of the row before the transpose overwrites it
-#pragma unroll
-  for (int k1 = 0; k1 < N1; ++k1) buf[k1 * 33 + lane] = cmul(a[k1], s_twb[k1 * 32 + lane]);
   __syncwarp();
-  // step 2: lane k1 (and k1 + 32) does the 32-point DFT over n2
-  constexpr int NQ = (N1 + 31) / 32;
-  float2 b[NQ][32];
+  if constexpr (N1 <= 32) {
+    // step 2: lane L = rho N1 + k1 does the 32-point DFT over n2 of row rho
+    const int rho = lane / N1, k1 = lane - rho * N1;
+    const bool act = rho < R;
+    float2* b_ = buf + (act ? rho : 0) * stride;
+    float* xr = reinterpret_cast<float*>(b_);
+    float2 b[32];
+    if (act) {
 #pragma unroll
-  for (int t = 0; t < NQ; ++t) {
-    const int k1 = lane + 32 * t;
-    if (k1 < N1) {
-#pragma unroll
-      for (int n2 = 0; n2 < 32; ++n2) b[t][n2] = buf[k1 * 33 + n2];
-      dft<32, N1>(b[t], s_tw);
+      for (int n2 = 0; n2 < 32; ++n2) b[n2] = b_[k1 * 33 + n2];
+      dft<32, N1>(b, s_tw);
     } else {
 #pragma unroll
-      for (int n2 = 0; n2 < 32; ++n2) b[t][n2] = make_float2(0.f, 0.f);
+      for (int n2 = 0; n2 < 32; ++n2) b[n2] = make_float2(0.f, 0.f);
     }
-  }
-  __syncwarp();
-  // DST_k = -Im(E_k + exp(-i pi k / M) O_k) / 2 from Z_k and Z_{M-k}
-  if constexpr (N1 <= 32) {
-    // lane k1 < N1 holds Z_{k1 + N1 k2} in b[0][k2]; Z_{M-k} is b[0][31 - k2]
-    // of lane N1 - k1 (lane 0: its own b[0][(32 - k2) % 32])
-    const int partner = lane == 0 ? 0 : N1 - lane;
+    __syncwarp();
+    // DST_k = -Im(E_k + exp(-i pi k / M) O_k) / 2 from Z_k and Z_{M-k}: lane
+    // rho N1 + k1 holds Z_{k1 + N1 k2} of its row in b[k2]; Z_{M-k} is
+    // b[31 - k2] of lane rho N1 + N1 - k1 (k1 = 0: its own b[(32 - k2) % 32])
+    const int partner = act ? rho * N1 + (k1 == 0 ? 0 : N1 - k1) : lane;
 #pragma unroll
     for (int k2 = 0; k2 < 32; ++k2) {
       float2 zc;
-      zc.x = __shfl_sync(0xffffffffu, b[0][31 - k2].x, partner);
-      zc.y = __shfl_sync(0xffffffffu, b[0][31 - k2].y, partner);
-      if (lane == 0) zc = b[0][(32 - k2) & 31];
+      zc.x = __shfl_sync(0xffffffffu, b[31 - k2].x, partner);
+      zc.y = __shfl_sync(0xffffffffu, b[31 - k2].y, partner);
+      if (k1 == 0) zc = b[(32 - k2) & 31];
       // straight-line body (only the store is predicated) so the unrolled
       // iterations overlap
-      const int k = lane + N1 * k2;
-      const float2 zk = b[0][k2];
+      const int k = k1 + N1 * k2;
+      const float2 zk = b[k2];
       const float ey = 0.5f * (zk.y - zc.y);
       const float ox = 0.5f * (zk.y + zc.y), oy = -0.5f * (zk.x - zc.x);
       const float2 w = s_tw2[k < M ? k : 0];
       const float v = -0.5f * (ey + w.x * oy + w.y * ox);
-      if (lane < N1 && k != 0) xr[k - 1] = v;
+      if (act && k != 0) xr[k - 1] = v;
     }
   } else {
-    // Z in natural order through the buffer (M float2 fit in N1 x 33)
+    // one row (R = 1): lane k1 and k1 + 32 do the 32-point DFTs over n2,
+    // then Z in natural order through the buffer (M float2 fit in N1 x 33)
+    constexpr int NQ = N1 / 32;
+    float* xr = reinterpret_cast<float*>(buf);
+    float2 b[NQ][32];
 #pragma unroll
     for (int t = 0; t < NQ; ++t) {
       const int k1 = lane + 32 * t;
-      if (k1 < N1) {
 #pragma unroll
-        for (int k2 = 0; k2 < 32; ++k2) buf[k1 + N1 * k2] = b[t][k2];
-      }
+      for (int n2 = 0; n2 < 32; ++n2) b[t][n2] = buf[k1 * 33 + n2];
+      dft<32, N1>(b[t], s_tw);
+    }
+    __syncwarp();
+#pragma unroll
+    for (int t = 0; t < NQ; ++t) {
+      const int k1 = lane + 32 * t;
+#pragma unroll
+      for (int k2 = 0; k2 < 32; ++k2) buf[k1 + N1 * k2] = b[t][k2];
     }
     __syncwarp();
     float v[N1];
@@ -241,23 +264,27 @@ constexpr size_t buf_floats(int N1) { return (size_t)N1 * 33 * 2; }
 
 // Shared memory of one block (bytes): twiddle tables W_M^j, W_M^{n2 k1} at
 // [k1][n2] and exp(-i pi k / M) (M float2 each), eigenvalues (M floats),
-// and one N1 x 33 complex row buffer per warp and plane.
+// and one N1 x 33 complex row buffer per row slot (rpb warps x R rows) and
+// plane.
 constexpr size_t smem_for(int N1, int rpb, int pw) {
-  return sizeof(float) * ((size_t)7 * 32 * N1 + (size_t)rpb * pw * buf_floats(N1));
+  return sizeof(float) *
+         ((size_t)7 * 32 * N1 + (size_t)rpb * rows_per_warp(N1) * pw * buf_floats(N1));
 }
 
 template <int N1, bool SPARSE>
 __device__ __forceinline__ void body(const FftDesc& d, int lb, int rpb, float* smem) {
   constexpr int M = 32 * N1;
+  constexpr int R = rows_per_warp(N1);
   const int T = 32 * rpb;
   float2* s_tw = reinterpret_cast<float2*>(smem);  // [M] W_M^j
   float2* s_twb = s_tw + M;                         // [N1][32] W_M^{n2 k1}
   float2* s_tw2 = s_twb + M;                        // [M] exp(-i pi k / M)
   float* s_lam = reinterpret_cast<float*>(s_tw2 + M);  // [M]
-  float2* s_buf = reinterpret_cast<float2*>(s_lam + M);  // [rpb][pw][N1 * 33]
+  float2* s_buf = reinterpret_cast<float2*>(s_lam + M);  // [rpb R slots][pw][N1 * 33]
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const bool solve = d.solve != 0;
   const int pw = d.pw;
+  const size_t bstride = (size_t)N1 * 33;  // float2 per row buffer
   // the tables are written once at domain set-up: load them before waiting
   // for the previous kernel
   for (int i = threadIdx.x; i < M; i += T) {
@@ -269,89 +296,93 @@ __device__ __forceinline__ void body(const FftDesc& d, int lb, int rpb, float* s
   KFBI_PDL_ENTRY();
   KFBI_STOP_RETURN(d.stop);
   if (d.active && *d.active == 0) return;
-  // lb = (plane group) * rblocks + row block
+  // lb = (plane group) * rblocks + row block; slot s = warp R + rho holds
+  // data row rr0 + s
   const int pg = lb / d.rblocks;
-  const int rr0 = d.r_lo + (lb - pg * d.rblocks) * rpb;
-  const int r = rr0 + warp;  // data row within the plane
+  const int rr0 = d.r_lo + (lb - pg * d.rblocks) * rpb * R;
   const size_t plane = (size_t)d.Mp * d.Mp;
-  for (int pl = 0; pl < pw; ++pl) {
-    const int p = pg + pl;  // plane
-    float2* buf = s_buf + (size_t)(warp * pw + pl) * N1 * 33;
-    float* xrow = reinterpret_cast<float*>(buf);
-    if constexpr (SPARSE) {
-      const FftSparseRhs& sp = d.sp;
-      const double* phi = sp.phi + (sp.dj ? (size_t)(*sp.dj) * sp.dj_stride : 0);
+  for (int rho = 0; rho < R; ++rho) {
+    const int sl = warp * R + rho;
+    const int r = rr0 + sl;  // data row within the plane
+    for (int pl = 0; pl < pw; ++pl) {
+      const int p = pg + pl;  // plane
+      float2* buf = s_buf + (size_t)(sl * pw + pl) * bstride;
+      float* xrow = reinterpret_cast<float*>(buf);
+      if constexpr (SPARSE) {
+        const FftSparseRhs& sp = d.sp;
+        const double* phi = sp.phi + (sp.dj ? (size_t)(*sp.dj) * sp.dj_stride : 0);
 #pragma unroll
-      for (int q = 0; q < N1; ++q) xrow[lane + 32 * q] = 0.f;
-      __syncwarp();
-      const int rl = r - sp.rmin;  // row within the irregular rows
-      if (rl >= 0 && rl < sp.nrows) {
-        // lanes take the row's correction arms (grouped by node, nodes by
-        // column), each one arm with its six density terms; a segmented sum
-        // over lanes in a fixed order adds the arms of a node
-        const int a0 = sp.arm_start[sp.row_start[rl]], a1 = sp.arm_start[sp.row_start[rl + 1]];
-        for (int ab = a0; ab < a1; ab += 32) {
-          const int a = ab + lane;
-          float val = 0.f;
-          int col = -1 - lane;  // distinct keys for idle lanes
-          if (a < a1) {
-            col = sp.arm_col[a];
-            int k = sp.arm_k0[a];
-            float ar = 0.f, ai = 0.f, br = 0.f, bi = 0.f;
+        for (int q = 0; q < N1; ++q) xrow[lane + 32 * q] = 0.f;
+        __syncwarp();
+        const int rl = r - sp.rmin;  // row within the irregular rows
+        if (rl >= 0 && rl < sp.nrows) {
+          // lanes take the row's correction arms (grouped by node, nodes by
+          // column), each one arm with its six density terms; a segmented
+          // sum over lanes in a fixed order adds the arms of a node
+          const int a0 = sp.arm_start[sp.row_start[rl]], a1 = sp.arm_start[sp.row_start[rl + 1]];
+          for (int ab = a0; ab < a1; ab += 32) {
+            const int a = ab + lane;
+            float val = 0.f;
+            int col = -1 - lane;  // distinct keys for idle lanes
+            if (a < a1) {
+              col = sp.arm_col[a];
+              int k = sp.arm_k0[a];
+              float ar = 0.f, ai = 0.f, br = 0.f, bi = 0.f;
 #pragma unroll
-            for (int m = 0; m < 6; ++m) {
-              const float al = sp.alpha[m * sp.n_arms + a], be = sp.beta[m * sp.n_arms + a];
-              const float pr = (float)phi[(size_t)k * sp.ps];
-              ar = fmaf(al, pr, ar);
-              br = fmaf(be, pr, br);
-              if (sp.cplx) {
-                const float pi = (float)phi[(size_t)k * sp.ps + 1];
-                ai = fmaf(al, pi, ai);
-                bi = fmaf(be, pi, bi);
+              for (int m = 0; m < 6; ++m) {
+                const float al = sp.alpha[m * sp.n_arms + a], be = sp.beta[m * sp.n_arms + a];
+                const float pr = (float)phi[(size_t)k * sp.ps];
+                ar = fmaf(al, pr, ar);
+                br = fmaf(be, pr, br);
+                if (sp.cplx) {
+                  const float pi = (float)phi[(size_t)k * sp.ps + 1];
+                  ai = fmaf(al, pi, ai);
+                  bi = fmaf(be, pi, bi);
+                }
+                k = (k + 1 == sp.nb) ? 0 : k + 1;
               }
-              k = (k + 1 == sp.nb) ? 0 : k + 1;
+              float sr = ar + sp.kre * br, si = 0.f;
+              if (sp.cplx) {
+                sr -= sp.kim * bi;
+                si = ai + sp.kre * bi + sp.kim * br;
+              }
+              val = p == 0 ? sr : si;
             }
-            float sr = ar + sp.kre * br, si = 0.f;
-            if (sp.cplx) {
-              sr -= sp.kim * bi;
-              si = ai + sp.kre * bi + sp.kim * br;
-            }
-            val = p == 0 ? sr : si;
-          }
 #pragma unroll
-          for (int o = 1; o < 32; o <<= 1) {
-            const float t = __shfl_up_sync(0xffffffffu, val, o);
-            const int kc = __shfl_up_sync(0xffffffffu, col, o);
-            if (lane >= o && kc == col) val += t;
+            for (int o = 1; o < 32; o <<= 1) {
+              const float t = __shfl_up_sync(0xffffffffu, val, o);
+              const int kc = __shfl_up_sync(0xffffffffu, col, o);
+              if (lane >= o && kc == col) val += t;
+            }
+            const int next = __shfl_down_sync(0xffffffffu, col, 1);
+            if (a < a1 && (lane == 31 || next != col)) xrow[col] += val;
+            __syncwarp();
           }
-          const int next = __shfl_down_sync(0xffffffffu, col, 1);
-          if (a < a1 && (lane == 31 || next != col)) xrow[col] += val;
-          __syncwarp();
         }
-      }
-    } else if (r < d.n1) {
-      // the row (M floats from a 16-byte aligned start): all loads first
-      const float4* src = reinterpret_cast<const float4*>(d.in + p * plane + (size_t)r * d.Mp);
-      constexpr int NV = (M / 4 + 31) / 32;
-      float4 x[NV];
+      } else if (r < d.n1) {
+        // the row (M floats from a 16-byte aligned start): all loads first
+        const float4* src = reinterpret_cast<const float4*>(d.in + p * plane + (size_t)r * d.Mp);
+        constexpr int NV = (M / 4 + 31) / 32;
+        float4 x[NV];
 #pragma unroll
-      for (int q = 0; q < NV; ++q) {
-        const int i = lane + 32 * q;
-        if (i < M / 4) x[q] = src[i];
-      }
+        for (int q = 0; q < NV; ++q) {
+          const int i = lane + 32 * q;
+          if (i < M / 4) x[q] = src[i];
+        }
 #pragma unroll
-      for (int q = 0; q < NV; ++q) {
-        const int i = lane + 32 * q;
-        if (i < M / 4) reinterpret_cast<float4*>(xrow)[i] = x[q];
-      }
-    } else {
-      // padding rows transform to zero
+        for (int q = 0; q < NV; ++q) {
+          const int i = lane + 32 * q;
+          if (i < M / 4) reinterpret_cast<float4*>(xrow)[i] = x[q];
+        }
+      } else {
+        // padding rows transform to zero
 #pragma unroll
-      for (int q = 0; q < N1; ++q) xrow[lane + 32 * q] = 0.f;
+        for (int q = 0; q < N1; ++q) xrow[lane + 32 * q] = 0.f;
+      }
     }
   }
   __syncthreads();  // tables (and rows) visible
-  // forward transform of each plane's row; a solve divides by
+  // forward transform of each plane's rows; a solve divides by
   // lambda_r + lambda_c - kappa and transforms back.  The loops are kept
   // rolled so the kernel holds one copy of the transform's code (two
   // inlined copies overflowed the instruction cache)
@@ -360,45 +391,55 @@ __device__ __forceinline__ void body(const FftDesc& d, int lb, int rpb, float* s
   for (int ph = 0; ph < nphase; ++ph) {
 #pragma unroll 1
     for (int pl = 0; pl < pw; ++pl)
-      row_dst<N1>(s_buf + (size_t)(warp * pw + pl) * N1 * 33, lane, s_tw, s_twb, s_tw2);
+      rows_dst<N1>(s_buf + (size_t)(warp * R * pw + pl) * bstride, pw * bstride, lane, s_tw, s_twb,
+                   s_tw2);
     if (ph + 1 < nphase) {
       __syncwarp();
-      float* x0 = reinterpret_cast<float*>(s_buf + (size_t)(warp * pw) * N1 * 33);
-      const float lam_r = r < d.n1 ? s_lam[r] : 0.f;
-      if (pw == 2) {
-        float* x1 = reinterpret_cast<float*>(s_buf + (size_t)(warp * pw + 1) * N1 * 33);
-        for (int c = lane; c < M - 1; c += 32) {
-          float zr = 0.f, zi = 0.f;
-          if (r < d.n1) eig_div_cplx32(x0[c], x1[c], lam_r + s_lam[c] - d.kre, d.kim, d.scale, zr, zi);
-          x0[c] = zr;
-          x1[c] = zi;
+      for (int rho = 0; rho < R; ++rho) {
+        const int sl = warp * R + rho;
+        const int r = rr0 + sl;
+        float* x0 = reinterpret_cast<float*>(s_buf + (size_t)(sl * pw) * bstride);
+        const float lam_r = r < d.n1 ? s_lam[r] : 0.f;
+        if (pw == 2) {
+          float* x1 = reinterpret_cast<float*>(s_buf + (size_t)(sl * pw + 1) * bstride);
+          for (int c = lane; c < M - 1; c += 32) {
+            float zr = 0.f, zi = 0.f;
+            if (r < d.n1)
+              eig_div_cplx32(x0[c], x1[c], lam_r + s_lam[c] - d.kre, d.kim, d.scale, zr, zi);
+            x0[c] = zr;
+            x1[c] = zi;
+          }
+        } else {
+          for (int c = lane; c < M - 1; c += 32)
+            x0[c] = r < d.n1 ? x0[c] * __fdividef(d.scale, lam_r + s_lam[c] - d.kre) : 0.f;
         }
-      } else {
-        for (int c = lane; c < M - 1; c += 32)
-          x0[c] = r < d.n1 ? x0[c] * __fdividef(d.scale, lam_r + s_lam[c] - d.kre) : 0.f;
       }
       __syncwarp();
     }
   }
   if (!d.transpose) {
-    // the last pass of a box solve: each warp writes its row as it is
+    // the last pass of a box solve: each warp writes its rows as they are
     // (M floats, the slot of index M - 1 zero)
     __syncwarp();
-    for (int pl = 0; pl < pw; ++pl) {
-      float* xr = reinterpret_cast<float*>(s_buf + (size_t)(warp * pw + pl) * N1 * 33);
-      if (lane == 0) xr[M - 1] = 0.f;
-      __syncwarp();
-      if (r < d.n1) {
-        float4* dst = reinterpret_cast<float4*>(d.out + (pg + pl) * plane + (size_t)r * d.Mp);
-        for (int i = lane; i < M / 4; i += 32) dst[i] = reinterpret_cast<const float4*>(xr)[i];
+    for (int rho = 0; rho < R; ++rho) {
+      const int sl = warp * R + rho;
+      const int r = rr0 + sl;
+      for (int pl = 0; pl < pw; ++pl) {
+        float* xr = reinterpret_cast<float*>(s_buf + (size_t)(sl * pw + pl) * bstride);
+        if (lane == 0) xr[M - 1] = 0.f;
+        __syncwarp();
+        if (r < d.n1) {
+          float4* dst = reinterpret_cast<float4*>(d.out + (pg + pl) * plane + (size_t)r * d.Mp);
+          for (int i = lane; i < M / 4; i += 32) dst[i] = reinterpret_cast<const float4*>(xr)[i];
+        }
       }
     }
     return;
   }
   __syncthreads();
-  // transposed write: for each output row c the block's rpb rows are one
-  // contiguous run of rpb floats (float4 pieces read from four warps' rows)
-  const int nq = rpb / 4;
+  // transposed write: for each output row c the block's rpb R rows are one
+  // contiguous run of rpb R floats (float4 pieces read from four slots' rows)
+  const int nq = rpb * R / 4;
   for (int pl = 0; pl < pw; ++pl) {
     float* dst = d.out + (pg + pl) * plane + rr0;
     for (int i = threadIdx.x; i < (M - 1) * nq; i += T) {
@@ -406,7 +447,7 @@ __device__ __forceinline__ void body(const FftDesc& d, int lb, int rpb, float* s
       float o[4];
 #pragma unroll
       for (int j = 0; j < 4; ++j)
-        o[j] = reinterpret_cast<const float*>(s_buf + (size_t)((4 * h + j) * pw + pl) * N1 * 33)[c];
+        o[j] = reinterpret_cast<const float*>(s_buf + (size_t)((4 * h + j) * pw + pl) * bstride)[c];
       *reinterpret_cast<float4*>(dst + (size_t)c * d.Mp + 4 * h) = make_float4(o[0], o[1], o[2], o[3]);
     }
   }
@@ -490,6 +531,7 @@ FftDesc fft_desc(const TcDst* T, const float* in, float* out, int P, bool solve,
                  float kim, float scale, const double* stop, const FftSparseRhs* sp, int rpb) {
   FftDesc d{};
   const int M = T->n1 + 1;
+  const int R = ff::rows_per_warp(M / 32);  // rows per warp: a block covers rpb R rows
   d.in = in;
   d.out = out;
   d.twM = T->twM;
@@ -512,10 +554,10 @@ FftDesc fft_desc(const TcDst* T, const float* in, float* out, int P, bool solve,
   if (sp) {
     d.sparse = 1;
     d.sp = *sp;
-    d.r_lo = sp->rmin / rpb * rpb;
+    d.r_lo = sp->rmin / (rpb * R) * (rpb * R);
     rows = sp->rmin + sp->nrows - d.r_lo;
   }
-  d.rblocks = (rows + rpb - 1) / rpb;
+  d.rblocks = (rows + rpb * R - 1) / (rpb * R);
   d.pgroups = P / d.pw;
   return d;
 }
@@ -524,14 +566,15 @@ int fft_blocks(const FftDesc& d) { return d.pgroups * d.rblocks; }
 
 double fft_desc_bytes(const FftDesc& d, int rpb) {
   const int M = 32 * d.N1;
-  const int rows = std::max(0, std::min(d.r_lo + d.rblocks * rpb, d.n1) - d.r_lo);
+  const int rows =
+      std::max(0, std::min(d.r_lo + d.rblocks * rpb * ff::rows_per_warp(d.N1), d.n1) - d.r_lo);
   const double per_row = 4.0 * (M - 1) * (d.sparse ? 1 : 2);  // read (unless built) + write
   return (double)rows * d.pgroups * d.pw * per_row;
 }
 
 double fft_desc_flops(const FftDesc& d, int rpb) {
   const int M = 32 * d.N1;
-  return fft_pass_flops(M, fft_blocks(d) * rpb * d.pw * (d.solve ? 2 : 1));
+  return fft_pass_flops(M, fft_blocks(d) * rpb * ff::rows_per_warp(d.N1) * d.pw * (d.solve ? 2 : 1));
 }
 
 void fft_launch(const FftGroup& g, int M, bool sparse, int nblocks, size_t smem, int prof_class,

@@ -11,6 +11,8 @@
 // rotated residual |g_{j+1}| as the convergence estimate.  All of it runs
 // in one CTA per kernel: the vectors are a few thousand entries.
 #include <algorithm>
+#include <atomic>
+#include <chrono>
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -67,10 +69,25 @@ __global__ void __launch_bounds__(kThreads) k_bnorm(const double2* __restrict__ 
 }
 
 // r = b - Ax (Ax may be null for x = 0); V0 = r / beta; g = (beta, 0, ...).
+// The eight scalars and then, after a system-scope fence, their sequence
+// number, written to host-mapped memory (slot seq & 1 of mbox) that the host
+// polls: no copy or event in the stream, whose kernels would otherwise lose
+// the programmatic-launch overlap at every scalar read.  One thread; mbox
+// null: nothing.
+__device__ __forceinline__ void mbox_post(const double* scal, double* mbox, long long seq) {
+  if (!mbox) return;
+  volatile double* slot = mbox + 16 * (seq & 1);
+#pragma unroll
+  for (int i = 0; i < 8; ++i) slot[i] = scal[i];
+  __threadfence_system();
+  reinterpret_cast<volatile long long*>(slot)[8] = seq;
+}
+
 __global__ void __launch_bounds__(kThreads) k_restart(const double2* __restrict__ b,
                                                        const double2* __restrict__ Ax,
                                                        double2* __restrict__ V0, double2* g,
-                                                       int m, int nb, double* scal) {
+                                                       int m, int nb, double* scal, double* mbox,
+                                                       long long seq) {
   KFBI_PDL_ENTRY();
   __shared__ double red[32];
   double s = 0.0;
@@ -94,6 +111,7 @@ __global__ void __launch_bounds__(kThreads) k_restart(const double2* __restrict_
   if (threadIdx.x == 0) {
     scal[1] = beta;
     scal[2] = !isfinite(beta) ? 2.0 : (beta <= scal[3] * scal[0] ? 1.0 : 0.0);
+    mbox_post(scal, mbox, seq);
   }
 }
 
@@ -626,7 +644,7 @@ template <bool C>
 __global__ void __launch_bounds__(CLT) k_arnoldi_cl(double2* __restrict__ V, int nb, int j,
                                                     double2* __restrict__ w, double2* H, double* cs,
                                                     double2* sn, double2* g, int m, double* scal,
-                                                    int cached) {
+                                                    int cached, double* mbox, long long seq) {
   KFBI_PDL_ENTRY();
   // a step queued ahead of an earlier step that converged does nothing
   // (every CTA of the cluster reads the same flag and returns together)
@@ -725,7 +743,10 @@ __global__ void __launch_bounds__(CLT) k_arnoldi_cl(double2* __restrict__ V, int
       gcol[i] = make_double2(h1[i].x + h2[i].x, h1[i].y + h2[i].y);
     __syncthreads();
     if (threadIdx.x < 32) rotate_column_warp<C>(gcol, j, gcs, gsn, threadIdx.x);
-    if (threadIdx.x == 0) givens_new<C>(gcol, j, hn, gcs, gsn, gg, scal);
+    if (threadIdx.x == 0) {
+      givens_new<C>(gcol, j, hn, gcs, gsn, gg, scal);
+      mbox_post(scal, mbox, seq);
+    }
     __syncthreads();
     double2* col = H + (size_t)j * (m + 1);
     for (int i = threadIdx.x; i <= j + 1; i += CLT) {
@@ -834,9 +855,10 @@ void gmres_alloc(kfbi_domain* D) {
   KFBI_CUDA(cudaMemset(D->d_scal, 0, 8 * sizeof(double)));
   KFBI_CUDA(cudaMallocHost(&D->h_scal, 8 * sizeof(double)));
   std::memset(D->h_scal, 0, 8 * sizeof(double));
-  KFBI_CUDA(cudaMallocHost(&D->h_ring, 16 * sizeof(double)));
-  std::memset(D->h_ring, 0, 16 * sizeof(double));
-  for (cudaEvent_t& e : D->ev_ring) KFBI_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  KFBI_CUDA(cudaHostAlloc(&D->h_mbox, 32 * sizeof(double), cudaHostAllocMapped));
+  std::memset(D->h_mbox, 0, 32 * sizeof(double));
+  KFBI_CUDA(cudaHostGetDevicePointer((void**)&D->d_mbox, D->h_mbox, 0));
+  D->mbox_seq = 0;
 }
 
 void gmres_free(kfbi_domain* D) {
@@ -846,17 +868,41 @@ void gmres_free(kfbi_domain* D) {
     if (p) cudaFree(p);
   if (D->h_scal) cudaFreeHost(D->h_scal);
   D->h_scal = nullptr;
-  if (D->h_ring) cudaFreeHost(D->h_ring);
-  D->h_ring = nullptr;
-  for (cudaEvent_t& e : D->ev_ring) {
-    if (e) cudaEventDestroy(e);
-    e = nullptr;
-  }
+  if (D->h_mbox) cudaFreeHost(D->h_mbox);
+  D->h_mbox = nullptr;
+  D->d_mbox = nullptr;
 }
 
 static void read_scalars(kfbi_domain* D, cudaStream_t st) {
   KFBI_CUDA(cudaMemcpyAsync(D->h_scal, D->d_scal, 8 * sizeof(double), cudaMemcpyDeviceToHost, st));
   KFBI_CUDA(cudaStreamSynchronize(st));
+  check_device_flags(D);
+}
+
+// Next sequence number of the scalar mailbox (never 0, the initial content).
+static long long next_post(kfbi_domain* D) { return ++D->mbox_seq; }
+
+// The scalars a kernel posted with sequence number q (mbox_post): poll the
+// mapped slot; should the stream drain without that post (a kernel that
+// returned early), fall back to copying the scalars after the stream.
+static void wait_post(kfbi_domain* D, long long q, cudaStream_t st) {
+  volatile double* slot = D->h_mbox + 16 * (q & 1);
+  volatile long long* seq = reinterpret_cast<volatile long long*>(slot + 8);
+  const auto t0 = std::chrono::steady_clock::now();
+  for (long long spins = 1; *seq != q; ++spins) {
+    if ((spins & 255) != 0) continue;
+    const cudaError_t e = cudaStreamQuery(st);
+    if (e == cudaSuccess) {
+      if (*seq == q) break;
+      read_scalars(D, st);
+      return;
+    }
+    if (e != cudaErrorNotReady) KFBI_CUDA(e);
+    if (std::chrono::steady_clock::now() - t0 > std::chrono::seconds(60))
+      throw Status{KFBI_ERR_TIMEOUT, "no GMRES scalars within 60 s"};
+  }
+  std::atomic_thread_fence(std::memory_order_acquire);
+  for (int i = 0; i < 8; ++i) D->h_scal[i] = slot[i];
   check_device_flags(D);
 }
 
@@ -914,7 +960,8 @@ static int arnoldi_cluster_size() {
   return cl;
 }
 
-static void arnoldi_step_cluster(kfbi_domain* D, bool C, int j, int CL, cudaStream_t st) {
+static void arnoldi_step_cluster(kfbi_domain* D, bool C, int j, int CL, cudaStream_t st,
+                                 long long post = 0) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(CL, 1, 1);
   cfg.blockDim = dim3(CLT, 1, 1);
@@ -934,22 +981,23 @@ static void arnoldi_step_cluster(kfbi_domain* D, bool C, int j, int CL, cudaStre
   double2* V = (double2*)D->d_V;
   double2* w = (double2*)D->d_W;
   void* tok = g_prof_on ? prof_begin(KFBI_PROF_KRYLOV, st) : nullptr;
+  double* mbox = post > 0 ? D->d_mbox : nullptr;
   if (C)
     KFBI_CUDA(cudaLaunchKernelEx(&cfg, k_arnoldi_cl<true>, V, D->nb, j, w, (double2*)D->d_H, D->d_cs,
                                  (double2*)D->d_sn, (double2*)D->d_g, D->restart, D->d_scal,
-                                 cached));
+                                 cached, mbox, post));
   else
     KFBI_CUDA(cudaLaunchKernelEx(&cfg, k_arnoldi_cl<false>, V, D->nb, j, w, (double2*)D->d_H,
                                  D->d_cs, (double2*)D->d_sn, (double2*)D->d_g, D->restart,
-                                 D->d_scal, cached));
+                                 D->d_scal, cached, mbox, post));
   if (tok) prof_end(tok, st);
   g_launches.fetch_add(1, std::memory_order_relaxed);
 }
 
-static void arnoldi_step(kfbi_domain* D, bool C, int j, cudaStream_t st) {
+static void arnoldi_step(kfbi_domain* D, bool C, int j, cudaStream_t st, long long post = 0) {
   const int CL = arnoldi_cluster_size();
   if (CL > 0) {
-    arnoldi_step_cluster(D, C, j, CL, st);
+    arnoldi_step_cluster(D, C, j, CL, st, post);
     return;
   }
   const int nb = D->nb, m = D->restart;
@@ -999,9 +1047,11 @@ struct StopScope {
 // stream before the host reads iteration j's residual, so the GPU does not
 // wait for the host between iterations; the exception is an iteration that
 // the residual history predicts to be the last one (the previous residual
-// times the previous reduction ratio within 3x of the target).  The scalars of each step are
-// copied into a two-slot pinned ring behind an event; the host reads slot s
-// before it queues snapshot s + 2.  When iteration j converged, the queued
+// times the previous reduction ratio within 3x of the target).  The restart
+// and Arnoldi kernels post their scalars to a two-slot host-mapped mailbox
+// (mbox_post), so no copy or event sits between the kernels of consecutive
+// iterations; the host polls post q before it queues the kernel that posts
+// q + 2 into the same slot.  When iteration j converged, the queued
 // iteration j + 1 finds the convergence flag set and its kernels return at
 // once; it would only have written H column j + 1, g[j + 1 .. j + 2] and
 // V[j + 2], none of which the update with k = j + 1 reads.
@@ -1016,24 +1066,14 @@ static kfbi_status gmres_core(kfbi_domain* D, double kre, double kim, const doub
   double2* g = (double2*)D->d_g;
   const bool ahead = D->tc && D->n_irr > 0 && arnoldi_cluster_size() > 0;
   StopScope scope(D, ahead);
-  long long seq = 0;  // scalar snapshots queued
-  auto snapshot = [&]() {
-    const int s = (int)(seq & 1);
-    KFBI_CUDA(cudaMemcpyAsync(D->h_ring + 8 * s, D->d_scal, 8 * sizeof(double),
-                              cudaMemcpyDeviceToHost, st));
-    KFBI_CUDA(cudaEventRecord(D->ev_ring[s], st));
-    return seq++;
-  };
-  auto read_snapshot = [&](long long q) {
-    const int s = (int)(q & 1);
-    KFBI_CUDA(cudaEventSynchronize(D->ev_ring[s]));
-    std::memcpy(D->h_scal, D->h_ring + 8 * s, 8 * sizeof(double));
-    check_device_flags(D);
-  };
+  // with lookahead the restart and Arnoldi kernels post their scalars to the
+  // mapped mailbox (sequence numbers qj[j] for iteration j)
+  std::vector<long long> qj(m + 1, 0);
   auto iterate = [&](int j) {
     apply_internal(D, kre, kim, (const double*)(V + (size_t)j * nb), 2, nullptr, D->d_W, 2,
                    false, st);
-    arnoldi_step(D, C, j, st);
+    qj[j] = ahead ? next_post(D) : 0;
+    arnoldi_step(D, C, j, st, qj[j]);
   };
   KFBI_LAUNCH_P(KFBI_PROF_KRYLOV, k_bnorm, 1, kThreads, 0, st, (const double2*)b, nb, D->d_scal, tol);
   int it = 0;
@@ -1043,17 +1083,13 @@ static kfbi_status gmres_core(kfbi_domain* D, double kre, double kim, const doub
   for (;;) {
     const bool skip_ax = first && x_zero;
     if (!skip_ax) apply_internal(D, kre, kim, x, 2, nullptr, D->d_W, 2, false, st);
+    const long long q0 = ahead ? next_post(D) : 0;
     KFBI_LAUNCH_P(KFBI_PROF_KRYLOV, k_restart, 1, kThreads, 0, st, (const double2*)b, skip_ax ? nullptr : W, V, g, m,
-                nb, D->d_scal);
+                nb, D->d_scal, ahead ? D->d_mbox : nullptr, q0);
     KFBI_CHECK_LAUNCH();
-    long long s0 = 0;  // snapshot of the restart; iteration j's is s0 + 1 + j
     if (ahead) {
-      s0 = snapshot();
-      if (it < maxit) {
-        iterate(0);
-        snapshot();
-      }
-      read_snapshot(s0);
+      if (it < maxit) iterate(0);
+      wait_post(D, q0, st);
     } else {
       read_scalars(D, st);
     }
@@ -1073,7 +1109,6 @@ static kfbi_status gmres_core(kfbi_domain* D, double kre, double kim, const doub
       if (ahead) {
         if (queued < j) {
           iterate(j);
-          snapshot();
           queued = j;
         }
         // queue j + 1 before reading j, unless j is expected to converge:
@@ -1084,10 +1119,9 @@ static kfbi_status gmres_core(kfbi_domain* D, double kre, double kim, const doub
         const bool likely_last = res2 > 0.0 && res1 * (res1 / res2) <= 3.0 * target;
         if (j + 1 < m && it + 2 <= maxit && !likely_last) {
           iterate(j + 1);
-          snapshot();
           queued = j + 1;
         }
-        read_snapshot(s0 + 1 + j);
+        wait_post(D, qj[j], st);
         res2 = res1;
         res1 = D->h_scal[1];
       } else {
@@ -1107,7 +1141,9 @@ static kfbi_status gmres_core(kfbi_domain* D, double kre, double kim, const doub
     }
     if (D->h_scal[2] != 0.0 || it >= maxit) break;
   }
-  KFBI_CUDA(cudaStreamSynchronize(st));
+  // the scalars already came from the mailbox; without it, the last read
+  // is still in flight behind the update
+  if (!ahead) KFBI_CUDA(cudaStreamSynchronize(st));
   const double bn = D->h_scal[0] > 0.0 ? D->h_scal[0] : 1.0;
   if (info) {
     info->iters = it;
@@ -1130,7 +1166,7 @@ namespace gm {
 __global__ void __launch_bounds__(kThreads) k_residual(const double2* __restrict__ b,
                                                         const double2* __restrict__ Ax,
                                                         double2* __restrict__ r, int nb,
-                                                        double* scal) {
+                                                        double* scal, double* mbox, long long seq) {
   KFBI_PDL_ENTRY();
   __shared__ double red[32];
   double s = 0.0;
@@ -1144,7 +1180,10 @@ __global__ void __launch_bounds__(kThreads) k_residual(const double2* __restrict
     s += v.x * v.x + v.y * v.y;
   }
   s = block_sum(s, red);
-  if (threadIdx.x == 0) scal[1] = sqrt(s);
+  if (threadIdx.x == 0) {
+    scal[1] = sqrt(s);
+    mbox_post(scal, mbox, seq);
+  }
 }
 
 __global__ void k_axpy(double2* __restrict__ x, const double2* __restrict__ d, int nb) {
@@ -1390,10 +1429,11 @@ kfbi_status gmres_solve(kfbi_domain* D, double kre, double kim, const double* b,
         fresh = true;
       }
     }
+    const long long q = next_post(D);
     KFBI_LAUNCH_P(KFBI_PROF_KRYLOV, k_residual, 1, kThreads, 0, st, (const double2*)b,
-                  (const double2*)ax, (double2*)D->d_Rv, nb, D->d_scal);
+                  (const double2*)ax, (double2*)D->d_Rv, nb, D->d_scal, D->d_mbox, q);
     KFBI_CHECK_LAUNCH();
-    read_scalars(D, st);
+    wait_post(D, q, st);
     if (sweep == 0) bnorm = D->h_scal[0];
     rn = D->h_scal[1];
     if (!std::isfinite(rn)) {
@@ -1548,7 +1588,8 @@ extern "C" kfbi_status kfbi_solve_neumann(kfbi_domain* dom, double kappa_re, dou
     if (ft) {
       apply_accurate(dom, kappa_re, kappa_im, dom->d_zero_nb, 2, ft, dom->d_Dv, 2, st);
       KFBI_LAUNCH_P(KFBI_PROF_KRYLOV, k_residual, 1, kThreads, 0, st, (const double2*)dom->d_B,
-                    (const double2*)dom->d_Dv, (double2*)dom->d_Rv, nb, dom->d_scal);
+                    (const double2*)dom->d_Dv, (double2*)dom->d_Rv, nb, dom->d_scal,
+                    (double*)nullptr, 0LL);
       KFBI_CHECK_LAUNCH();
       KFBI_CUDA(cudaMemcpyAsync(dom->d_B, dom->d_Rv, 2 * (size_t)nb * sizeof(double),
                                 cudaMemcpyDeviceToDevice, st));

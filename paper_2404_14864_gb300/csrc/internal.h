@@ -264,8 +264,12 @@ struct kfbi_domain {
   double* h_scal = nullptr; // pinned mirror
   // GMRES lookahead: pinned snapshots of d_scal (two slots, in stream
   // order) and the events that mark them
-  double* h_ring = nullptr;
-  cudaEvent_t ev_ring[2] = {nullptr, nullptr};
+  // scalar mailbox: host-mapped memory the GMRES kernels post their scalars
+  // to (2 slots of 16 doubles: 8 scalars, then the sequence number), polled
+  // by the host instead of a copy in the stream
+  double* h_mbox = nullptr;
+  double* d_mbox = nullptr;
+  long long mbox_seq = 0;
   // residual reduction per Richardson step seen at kappa = (rich_kre,
   // rich_kim) in the last solve (0: none yet); sizes the first run of steps
   double rich_rate = 0.0, rich_kre = 0.0, rich_kim = 0.0;
