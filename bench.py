@@ -552,7 +552,7 @@ TC_PASS_TRAFFIC_1024 = 16.845824e6 + 0.0
 # plane): dram__bytes_read.sum + dram__bytes_write.sum averaged over the
 # captured k_dst_fft launches of the current kernel.  None whenever
 # k_dst_fft changes until it is captured again.
-FFT_PASS_TRAFFIC_1024 = None
+FFT_PASS_TRAFFIC_1024 = 4.265e6
 
 
 def load_peaks():

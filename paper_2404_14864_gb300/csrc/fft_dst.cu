@@ -417,6 +417,8 @@ __device__ __forceinline__ void body(const FftDesc& d, int lb, int rpb, float* s
       __syncwarp();
     }
   }
+  // the transforms are done: the next kernel may launch during the writes
+  KFBI_PDL_TRIGGER();
   if (!d.transpose) {
     // the last pass of a box solve: each warp writes its rows as they are
     // (M floats, the slot of index M - 1 zero)
@@ -596,9 +598,8 @@ void fft_launch(const FftGroup& g, int M, bool sparse, int nblocks, size_t smem,
   }
 }
 
-static void launch_one(const TcDst* T, const FftDesc& d, int prof_class, cudaStream_t st) {
+static void launch_one(const TcDst* T, const FftDesc& d, int prof_class, cudaStream_t st, int rpb) {
   const int M = T->n1 + 1;
-  int rpb = T->fft_rpb;
   FftGroup g{};
   g.descs = nullptr;
   g.blk = nullptr;
@@ -609,17 +610,20 @@ static void launch_one(const TcDst* T, const FftDesc& d, int prof_class, cudaStr
 }
 
 void fft_pass(const TcDst* T, const float* in, float* out, int P, const double* stop,
-              cudaStream_t st, const FftSparseRhs* sp, bool transpose) {
-  FftDesc d = fft_desc(T, in, out, P, false, 0.f, 0.f, 0.f, stop, sp, T->fft_rpb);
+              cudaStream_t st, const FftSparseRhs* sp, bool transpose, int rpb) {
+  if (rpb <= 0) rpb = sp ? T->fft_rpb_sparse : T->fft_rpb;
+  FftDesc d = fft_desc(T, in, out, P, false, 0.f, 0.f, 0.f, stop, sp, rpb);
   d.transpose = transpose ? 1 : 0;
   // a sparse first pass is timed with the sparse passes, not the dense DST passes
-  launch_one(T, d, sp ? KFBI_PROF_SPARSE : KFBI_PROF_DST, st);
+  launch_one(T, d, sp ? KFBI_PROF_SPARSE : KFBI_PROF_DST, st, rpb);
 }
 
 void fft_solve(const TcDst* T, const float* in, float* out, int P, float kre, float kim,
-               float scale, const double* stop, cudaStream_t st) {
-  const FftDesc d = fft_desc(T, in, out, P, true, kre, kim, scale, stop, nullptr, T->fft_rpb);
-  launch_one(T, d, KFBI_PROF_DST, st);
+               float scale, const double* stop, cudaStream_t st, int rpb) {
+  if (rpb <= 0) rpb = T->fft_rpb_solve;
+  if (!fft_rpb_fits(T->n1 + 1, rpb, P == 2 ? 2 : 1)) rpb = 4;
+  const FftDesc d = fft_desc(T, in, out, P, true, kre, kim, scale, stop, nullptr, rpb);
+  launch_one(T, d, KFBI_PROF_DST, st, rpb);
 }
 
 }  // namespace kfbi

@@ -1415,6 +1415,8 @@ static void launch_pass(TcDst* T, const PassDesc& d, cudaStream_t st) {
 
 // Four TF32x3 passes: (Rh, Rl) -> U (fp32 planes), eigenvalue division after
 // the forward transform.
+static void fft_tune(kfbi_domain* D, cudaStream_t st);
+
 static void tc_box_solve(kfbi_domain* D, double kre, double kim, int P, cudaStream_t st) {
   TcDst* T = D->tc;
   const size_t plane = (size_t)T->Mp * T->Mp;
@@ -1423,6 +1425,7 @@ static void tc_box_solve(kfbi_domain* D, double kre, double kim, int P, cudaStre
   if (T->fft) {
     // transform along x (written transposed); along y: transform, divide
     // by the eigenvalues, transform back (one pass); transform along x
+    fft_tune(D, st);
     fft_pass(T, T->Rh, T->T1h, P, nullptr, st);
     fft_solve(T, T->T1h, T->T2h, P, (float)kre, (float)kim, scale, nullptr, st);
     fft_pass(T, T->T2h, T->U, P, nullptr, st, nullptr, false);
@@ -1459,6 +1462,72 @@ static Tab32 tables32(const kfbi_domain* D) {
           D->d_node_fcoef32};
 }
 
+// Right-hand side of an FFT first pass built from the irregular nodes.
+static FftSparseRhs fft_sparse_rhs(const kfbi_domain* D, const Tab32& tb, const double* phi, int ps,
+                                   double kre, double kim) {
+  const TcDst* T = D->tc;
+  FftSparseRhs sp;
+  sp.row_start = T->row_start;
+  sp.node_col = T->node_col;
+  sp.arm_col = T->arm_col;
+  sp.rmin = T->rmin;
+  sp.nrows = T->nrows;
+  sp.arm_start = D->d_arm_start;
+  sp.arm_k0 = D->d_arm_k0;
+  sp.alpha = tb.al;
+  sp.beta = tb.be;
+  sp.n_arms = D->n_arms;
+  sp.nb = D->nb;
+  sp.phi = phi;
+  sp.ps = ps;
+  sp.kre = (float)kre;
+  sp.kim = (float)kim;
+  sp.cplx = kim != 0.0 ? 1 : 0;
+  sp.dj = nullptr;
+  sp.dj_stride = 0;
+  return sp;
+}
+
+// First FFT application of a single domain: each pass kind (sparse first
+// pass, solve pass, plain pass) is timed with 8 and 4 warps per block on
+// this domain's own work planes (CUDA events, one warm-up, three timed
+// repetitions) and the faster is kept.  The results do not depend on the
+// choice, only the launch shape does; batches tune their own groups.
+static void fft_tune(kfbi_domain* D, cudaStream_t st) {
+  TcDst* T = D->tc;
+  if (T->fft_tuned) return;
+  T->fft_tuned = true;
+  const bool prof = g_prof_on;
+  g_prof_on = false;
+  cudaEvent_t e0, e1;
+  KFBI_CUDA(cudaEventCreate(&e0));
+  KFBI_CUDA(cudaEventCreate(&e1));
+  const FftSparseRhs sp = fft_sparse_rhs(D, tables32(D), D->d_zero_nb, 2, 1.0, 0.0);
+  const float scale = (float)((2.0 / D->M) * (2.0 / D->M));
+  auto timed = [&](auto&& launch) {
+    launch();
+    KFBI_CUDA(cudaEventRecord(e0, st));
+    for (int r = 0; r < 3; ++r) launch();
+    KFBI_CUDA(cudaEventRecord(e1, st));
+    KFBI_CUDA(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    KFBI_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    return ms;
+  };
+  float best[3] = {1e30f, 1e30f, 1e30f};
+  for (int c : {8, 4}) {
+    const float t0 = timed([&]() { fft_pass(T, nullptr, T->T1sh, 1, nullptr, st, &sp, true, c); });
+    const float t1 = timed([&]() { fft_solve(T, T->T1sh, T->U, 1, 1.f, 0.f, scale, nullptr, st, c); });
+    const float t2 = timed([&]() { fft_pass(T, T->Rh, T->T1h, 1, nullptr, st, nullptr, true, c); });
+    if (t0 < best[0]) { best[0] = t0; T->fft_rpb_sparse = c; }
+    if (t1 < best[1]) { best[1] = t1; T->fft_rpb_solve = c; }
+    if (t2 < best[2]) { best[2] = t2; T->fft_rpb = c; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  g_prof_on = prof;
+}
+
 static void tc_apply_sparse(kfbi_domain* D, double kre, double kim, const double* phi, int ps,
                             double* out, int os, cudaStream_t st) {
   TcDst* T = D->tc;
@@ -1470,26 +1539,9 @@ static void tc_apply_sparse(kfbi_domain* D, double kre, double kim, const double
   if (T->fft) {
     // FFT passes cost the same for any right-hand side: the first pass
     // builds its rows from the corrected irregular nodes (no plane is read),
-    // then two full passes and the last pass at the stencil points only
-    FftSparseRhs sp;
-    sp.row_start = T->row_start;
-    sp.node_col = T->node_col;
-    sp.arm_col = T->arm_col;
-    sp.rmin = T->rmin;
-    sp.nrows = T->nrows;
-    sp.arm_start = D->d_arm_start;
-    sp.arm_k0 = D->d_arm_k0;
-    sp.alpha = tb.al;
-    sp.beta = tb.be;
-    sp.n_arms = D->n_arms;
-    sp.nb = D->nb;
-    sp.phi = phi;
-    sp.ps = ps;
-    sp.kre = (float)kre;
-    sp.kim = (float)kim;
-    sp.cplx = C ? 1 : 0;
-    sp.dj = nullptr;
-    sp.dj_stride = 0;
+    // then the solve pass and the last pass at the stencil points only
+    fft_tune(D, st);
+    const FftSparseRhs sp = fft_sparse_rhs(D, tb, phi, ps, kre, kim);
     const float scale = (float)((2.0 / D->M) * (2.0 / D->M));
     // the first pass writes only the columns of the irregular rows; T1sh
     // (zeroed at creation, written by nothing else on an FFT domain) keeps

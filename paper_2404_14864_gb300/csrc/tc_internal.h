@@ -97,7 +97,10 @@ struct TcDst {
   float2* twM = nullptr;
   float2* twB = nullptr;
   float2* tw2M = nullptr;
-  int fft_rpb = 8;  // rows (warps) per block of this domain's FFT passes (4 or 8)
+  int fft_rpb = 8;  // warps per block of this domain's plain FFT passes (4 or 8)
+  int fft_rpb_sparse = 8;  // ... of its sparse first pass
+  int fft_rpb_solve = 8;   // ... of its solve pass
+  bool fft_tuned = false;  // the three were timed on this domain (first application)
 };
 
 
@@ -176,10 +179,12 @@ double fft_desc_flops(const FftDesc& d, int rpb);
 double fft_desc_bytes(const FftDesc& d, int rpb);
 void fft_launch(const FftGroup& g, int M, bool sparse, int nblocks, size_t smem, int prof_class,
                 double flops, double bytes, cudaStream_t st);
+// rpb <= 0: the domain's tuned warps per block for the pass.
 void fft_pass(const TcDst* T, const float* in, float* out, int P, const double* stop,
-              cudaStream_t st, const FftSparseRhs* sp = nullptr, bool transpose = true);
+              cudaStream_t st, const FftSparseRhs* sp = nullptr, bool transpose = true,
+              int rpb = 0);
 void fft_solve(const TcDst* T, const float* in, float* out, int P, float kre, float kim,
-               float scale, const double* stop, cudaStream_t st);
+               float scale, const double* stop, cudaStream_t st, int rpb = 0);
 
 // Device tensor map of one of the domain's pass output planes (T1, T2 pairs
 // or U); throws for any other pointer.
