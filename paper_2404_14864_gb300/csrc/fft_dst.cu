@@ -417,8 +417,6 @@ __device__ __forceinline__ void body(const FftDesc& d, int lb, int rpb, float* s
       __syncwarp();
     }
   }
-  // the transforms are done: the next kernel may launch during the writes
-  KFBI_PDL_TRIGGER();
   if (!d.transpose) {
     // the last pass of a box solve: each warp writes its rows as they are
     // (M floats, the slot of index M - 1 zero)

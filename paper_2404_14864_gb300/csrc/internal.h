@@ -42,13 +42,6 @@ void prof_add_bytes(void* tok, double bytes);
 extern bool g_pdl;
 #define KFBI_PDL_ENTRY() asm volatile("griddepcontrol.wait;" ::: "memory")
 
-// Late trigger: lets the next kernel in the stream launch (and run its code
-// before its own KFBI_PDL_ENTRY) while this one writes its results; the
-// next kernel still waits for this one's completion and memory at its
-// KFBI_PDL_ENTRY.  Used after the compute phase, not at entry (an entry
-// trigger put the next kernel's blocks on the SMs this one was using).
-#define KFBI_PDL_TRIGGER() asm volatile("griddepcontrol.launch_dependents;" ::: "memory")
-
 // Early exit of a kernel of a speculatively queued GMRES iteration: stop
 // points at the solver's convergence flag (nonzero once an earlier
 // iteration converged or failed); nullptr never stops.  Read after
