@@ -678,14 +678,23 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_pass(const __grid_constant__ 
 // ---------------------------------------------------------------------------
 
 // FP64 planes -> TF32 pairs (hi = tf32(x), lo = tf32(x - hi)).
+// fp32_lo: FFT domains, whose passes read the FP32 plane hi alone: lo gets
+// the FP32 remainder x - hi (the pair keeps ~48 bits of x for the
+// double-float refinement residual, k_resid_u32).
 __global__ void k_split64(const double* __restrict__ src, float* __restrict__ hi,
-                          float* __restrict__ lo, size_t n) {
+                          float* __restrict__ lo, size_t n, int fp32_lo) {
   KFBI_PDL_ENTRY();
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
        i += (size_t)gridDim.x * blockDim.x) {
     const double x = src[i];
     if (!lo) {  // single FP32 plane (FFT passes)
       hi[i] = (float)x;
+      continue;
+    }
+    if (fp32_lo) {
+      const float h = (float)x;
+      hi[i] = h;
+      lo[i] = (float)(x - (double)h);
       continue;
     }
     const float h = tf32_round((float)x);
@@ -1095,6 +1104,91 @@ __global__ void k_resid_split(const double* __restrict__ R, const double* __rest
       const float h = tf32_round((float)res);
       hi[p * plane + idx] = h;
       lo[p * plane + idx] = tf32_round((float)(res - (double)h));
+    }
+  }
+}
+
+// Error-free transformations on FP32 (Knuth's TwoSum; TwoProduct by FMA).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+__device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
+  p = a * b;
+  e = fmaf(a, b, -p);
+}
+
+// The residual of the first refinement sweep on an FFT domain, from the
+// FP32 solution of the first box solve: r = R - (D_xx + D_yy - kappa) u with
+// u = U32 (every neighbour an FP32 number), in double-float arithmetic on
+// the FP32 pipe: the five-point sum accumulated by TwoSum with its rounding
+// errors kept (hi + lo, ~2^-48 of the terms), 1/h^2 and kappa as FP32 pairs
+// (split on the host), the products by TwoProduct, R as the FP32 pair
+// (Rh, Rl) that k_split64 wrote, and R - Lu gathered by TwoSum before the
+// final rounding: r keeps ~2^-48 of |R| while it is ~1e-6 |R| itself (the
+// float64 stencil of k_resid_split gives the same r to FP32 rounding, with
+// float64 operations that GB300 issues at a small fraction of the FP32
+// rate).  Overwrites Rh with r (each thread reads its own point first) and
+// writes U64 = U32, the start of the refined grid.
+template <bool C>
+__global__ void __launch_bounds__(256) k_resid_u32(float* __restrict__ Rh,
+                                                   const float* __restrict__ Rl,
+                                                   const float* __restrict__ U32,
+                                                   double* __restrict__ U64, int Mp, int n1,
+                                                   float ih_hi, float ih_lo, float kr_hi,
+                                                   float kr_lo, float ki_hi, float ki_lo) {
+  KFBI_PDL_ENTRY();
+  const size_t plane = (size_t)Mp * Mp;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < plane;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    const int r = (int)(idx / Mp), c = (int)(idx - (size_t)r * Mp);
+    const bool in = r < n1 && c < n1;
+#pragma unroll
+    for (int p = 0; p < (C ? 2 : 1); ++p) {
+      const float* Up = U32 + p * plane;
+      const float u = in ? Up[idx] : 0.f;
+      float res = 0.f;
+      if (in) {
+        const float e = c + 1 < n1 ? Up[idx + 1] : 0.f;
+        const float w = c > 0 ? Up[idx - 1] : 0.f;
+        const float nn = r + 1 < n1 ? Up[idx + Mp] : 0.f;
+        const float so = r > 0 ? Up[idx - Mp] : 0.f;
+        // S = e + w + n + s - 4u as hi + lo
+        float sh = -4.f * u, sl = 0.f, t;
+        two_sum(sh, e, sh, t);
+        sl += t;
+        two_sum(sh, w, sh, t);
+        sl += t;
+        two_sum(sh, nn, sh, t);
+        sl += t;
+        two_sum(sh, so, sh, t);
+        sl += t;
+        // Lu = S / h^2 - kappa u (+- kim u_other): leading products exact
+        float p1, e1, p2, e2;
+        two_prod(sh, ih_hi, p1, e1);
+        two_prod(kr_hi, u, p2, e2);
+        float tail = e1 + fmaf(sh, ih_lo, sl * ih_hi) - e2 - kr_lo * u;
+        float lu_hi, t2;
+        two_sum(p1, -p2, lu_hi, t2);
+        tail += t2;
+        if (C) {
+          const float uo = U32[(1 - p) * plane + idx];
+          float p3, e3;
+          two_prod(ki_hi, uo, p3, e3);
+          const float sg = p == 0 ? 1.f : -1.f;
+          float t3;
+          two_sum(lu_hi, sg * p3, lu_hi, t3);
+          tail += t3 + sg * (e3 + ki_lo * uo);
+        }
+        // res = R - Lu
+        const float R_hi = Rh[p * plane + idx], R_lo = Rl[p * plane + idx];
+        float d, t4;
+        two_sum(R_hi, -lu_hi, d, t4);
+        res = d + ((t4 + R_lo) - tail);
+      }
+      U64[p * plane + idx] = (double)u;
+      Rh[p * plane + idx] = res;
     }
   }
 }
@@ -1609,7 +1703,7 @@ void tc_apply(kfbi_domain* D, double kre, double kim, const double* phi, int ps,
   const size_t plane = (size_t)Mp * Mp;
   if (ft) {
     KFBI_LAUNCH_P(KFBI_PROF_GRID, k_split64, grid_for(P * plane, 256), 256, 0, st, ft, T->Rh,
-                  T->fft ? nullptr : T->Rl, P * plane);
+                  T->fft ? nullptr : T->Rl, P * plane, 0);
     T->rhs_sparse_planes = 0;
   } else if (T->rhs_sparse_planes < P) {
     KFBI_CUDA(cudaMemsetAsync(T->Rh, 0, 2 * plane * sizeof(float), st));
@@ -1660,24 +1754,44 @@ void tc_apply_accurate(kfbi_domain* D, double kre, double kim, const double* phi
   const int Mp = T->Mp;
   const size_t plane = (size_t)Mp * Mp;
   correct_fp64(D, kre, kim, phi, ps, ft, st);  // D->d_R: FP64 corrected RHS
-  KFBI_LAUNCH_P(KFBI_PROF_GRID, k_split64, grid_for(P * plane, 256), 256, 0, st, D->d_R, T->Rh,
-                T->fft ? nullptr : T->Rl, P * plane);
+  // FFT domains keep the FP32 remainder of R in the (otherwise unused) lo
+  // planes for the double-float residual
+  KFBI_LAUNCH_P(KFBI_PROF_GRID, k_split64, grid_for(P * plane, 256), 256, 0, st, D->d_R, T->Rh, T->Rl,
+                P * plane, T->fft ? 1 : 0);
   T->rhs_sparse_planes = 0;
   tc_box_solve(D, kre, kim, P, st);
-  KFBI_LAUNCH_P(KFBI_PROF_GRID, k_f32_to_f64, grid_for(P * plane, 256), 256, 0, st, T->U, D->d_U,
-                P * plane);
+  if (!T->fft)
+    KFBI_LAUNCH_P(KFBI_PROF_GRID, k_f32_to_f64, grid_for(P * plane, 256), 256, 0, st, T->U, D->d_U,
+                  P * plane);
   const double inv_h2 = 1.0 / (D->h * D->h);
   // one refinement sweep leaves a relative grid error ~delta^2; the normal
   // derivative of the Neumann operator amplifies grid errors by O(1/h), so
-  // its applications take a second sweep
+  // its applications take a second sweep.  The first sweep's residual is
+  // formed from the FP32 solution in double-float arithmetic (and starts
+  // the FP64 grid); a second sweep's grid is no longer FP32, so its
+  // residual is the float64 stencil
   const int sweeps = D->neumann ? 2 : 1;
+  const float ih_hi = (float)inv_h2, ih_lo = (float)(inv_h2 - (double)ih_hi);
+  const float kr_hi = (float)kre, kr_lo = (float)(kre - (double)kr_hi);
+  const float ki_hi = (float)kim, ki_lo = (float)(kim - (double)ki_hi);
   for (int sw = 0; sw < sweeps; ++sw) {
-    if (C)
+    float* rl = T->fft ? nullptr : T->Rl;
+    if (sw == 0 && T->fft) {
+      if (C)
+        KFBI_LAUNCH_P(KFBI_PROF_GRID, k_resid_u32<true>, grid_for(plane, 256), 256, 0, st, T->Rh,
+                      (const float*)T->Rl, (const float*)T->U, D->d_U, Mp, T->n1, ih_hi, ih_lo,
+                      kr_hi, kr_lo, ki_hi, ki_lo);
+      else
+        KFBI_LAUNCH_P(KFBI_PROF_GRID, k_resid_u32<false>, grid_for(plane, 256), 256, 0, st, T->Rh,
+                      (const float*)T->Rl, (const float*)T->U, D->d_U, Mp, T->n1, ih_hi, ih_lo,
+                      kr_hi, kr_lo, ki_hi, ki_lo);
+    } else if (C) {
       KFBI_LAUNCH_P(KFBI_PROF_GRID, k_resid_split<true>, grid_for(plane, 256), 256, 0, st, D->d_R,
-                    D->d_U, T->Rh, T->fft ? nullptr : T->Rl, Mp, T->n1, inv_h2, kre, kim);
-    else
+                    D->d_U, T->Rh, rl, Mp, T->n1, inv_h2, kre, kim);
+    } else {
       KFBI_LAUNCH_P(KFBI_PROF_GRID, k_resid_split<false>, grid_for(plane, 256), 256, 0, st, D->d_R,
-                    D->d_U, T->Rh, T->fft ? nullptr : T->Rl, Mp, T->n1, inv_h2, kre, kim);
+                    D->d_U, T->Rh, rl, Mp, T->n1, inv_h2, kre, kim);
+    }
     tc_box_solve(D, kre, kim, P, st);
     KFBI_LAUNCH_P(KFBI_PROF_GRID, k_add_f32, grid_for(P * plane, 256), 256, 0, st, D->d_U, T->U,
                   P * plane);
