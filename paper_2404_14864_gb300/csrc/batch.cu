@@ -16,6 +16,8 @@
 // single-instance path the kernels differ in reduction order, and results
 // agree to the GMRES tolerance.
 #include <algorithm>
+#include <atomic>
+#include <chrono>
 #include <cmath>
 #include <cstring>
 #include <map>
@@ -586,6 +588,33 @@ __global__ void gk_gather_scal(const GInst* gi, double* out) {
   if (threadIdx.x < 8) out[8 * blockIdx.x + threadIdx.x] = I.scal[threadIdx.x];
 }
 
+// All instances' scalars (8 doubles each) and flags (4 ints each) posted to
+// host-mapped memory, then, after a system-scope fence, the post's
+// sequence number (one more than the last, from a device counter, so that
+// posts inside a replayed graph number themselves): slot seq & 1 of mbox,
+// scalars at [0, 8 cap), flags from double 8 cap, the sequence number in
+// the slot's last double.  The host polls the number instead of copying the
+// state back behind a synchronisation.  One block.
+__global__ void __launch_bounds__(256) gk_post(const GInst* gi, int n, double* mbox, int slot_stride,
+                                              int cap, long long* ctr) {
+  KFBI_PDL_ENTRY();
+  __shared__ long long s_seq;
+  if (threadIdx.x == 0) s_seq = ++(*ctr);
+  __syncthreads();
+  volatile double* slot = mbox + (s_seq & 1) * (size_t)slot_stride;
+  volatile int* fl = reinterpret_cast<volatile int*>(slot + 8 * (size_t)cap);
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const GInst& I = gi[i];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) slot[8 * i + k] = I.scal[k];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) fl[4 * i + k] = I.flags[k];
+  }
+  __threadfence_system();
+  __syncthreads();
+  if (threadIdx.x == 0) reinterpret_cast<volatile long long*>(slot + slot_stride - 1)[0] = s_seq;
+}
+
 __global__ void gk_set_tol(const GInst* gi, const double* tol, const int* sel) {
   KFBI_PDL_ENTRY();
   const GInst& I = gi[blockIdx.x];
@@ -1033,6 +1062,12 @@ struct kfbi_batch {
   double* d_tol = nullptr;      // n inner tolerances
   double* h_scal = nullptr;     // pinned: 8 doubles per instance
   int* h_flags = nullptr;       // pinned: 4 ints per instance
+  // state mailbox (gk_post): two host-mapped slots of 12 cap + 16 doubles,
+  // the device's post counter and its host mirror
+  double* h_mbox = nullptr;
+  double* d_mbox = nullptr;
+  long long* d_postctr = nullptr;
+  long long host_posts = 0;
   // grouped pass descriptors and tile prefixes, per pass kind
   enum { kDense1, kDense2, kDense3, kDense4, kSparse2, kSparse3, kPassKinds };
   PassDesc* d_pass[kPassKinds] = {nullptr};
@@ -1367,7 +1402,15 @@ void fast_apply(kfbi_batch* B, cudaStream_t st) {
                 (const int*)B->d_j);
 }
 
-// one lockstep GMRES iteration: W = A_fast V[j], CGS2 Arnoldi, j += 1
+// The state post kernel alone (inside a captured iteration the host counts
+// the posts per replay).
+void launch_post(kfbi_batch* B, cudaStream_t st) {
+  KFBI_LAUNCH(gk_post, 1, 256, 0, st, (const GInst*)B->d_inst, B->n, B->d_mbox,
+              (int)(12 * (size_t)B->cap + 16), B->cap, B->d_postctr);
+}
+
+// one lockstep GMRES iteration: W = A_fast V[j], CGS2 Arnoldi, j += 1, and
+// the post of every instance's state
 void batch_iteration(kfbi_batch* B, cudaStream_t st) {
   const int n = B->n;
   fast_apply(B, st);
@@ -1380,21 +1423,44 @@ void batch_iteration(kfbi_batch* B, cudaStream_t st) {
   KFBI_LAUNCH_P(KFBI_PROF_KRYLOV, gk_cgs_finalize, inst_grid(GMAX, n), GT, 0, st, B->d_inst,
                 (const int*)B->d_j);
   KFBI_LAUNCH_P(KFBI_PROF_KRYLOV, gk_bump, 1, 32, 0, st, B->d_j);
+  launch_post(B, st);
   KFBI_CHECK_LAUNCH();
 }
 
-void read_state(kfbi_batch* B, cudaStream_t st) {
-  KFBI_LAUNCH(gk_gather_scal, B->n, 32, 0, st, B->d_inst, B->d_scal_all);
-  KFBI_CUDA(cudaMemcpyAsync(B->h_scal, B->d_scal_all, 8 * B->n * sizeof(double),
-                            cudaMemcpyDeviceToHost, st));
-  KFBI_CUDA(cudaMemcpyAsync(B->h_flags, B->d_flags, 4 * B->n * sizeof(int), cudaMemcpyDeviceToHost, st));
-  KFBI_CUDA(cudaStreamSynchronize(st));
-  for (int i = 0; i < B->n; ++i) {
+// Queue a state post (gk_post); returns the sequence number it will carry.
+long long post_state(kfbi_batch* B, cudaStream_t st) {
+  launch_post(B, st);
+  return ++B->host_posts;
+}
+
+// Wait for post q and copy its scalars and flags into h_scal / h_flags.
+void wait_state(kfbi_batch* B, long long q, cudaStream_t st) {
+  const size_t stride = 12 * (size_t)B->cap + 16;
+  volatile double* slot = B->h_mbox + (q & 1) * stride;
+  volatile long long* seq = reinterpret_cast<volatile long long*>(slot + stride - 1);
+  const auto t0 = std::chrono::steady_clock::now();
+  for (long long spins = 1; *seq != q; ++spins) {
+    if ((spins & 255) != 0) continue;
+    const cudaError_t e = cudaStreamQuery(st);
+    if (e != cudaSuccess && e != cudaErrorNotReady) KFBI_CUDA(e);
+    if (e == cudaSuccess && *seq != q)
+      throw Status{KFBI_ERR_CUDA, "batch state post missing after the stream drained"};
+    if (std::chrono::steady_clock::now() - t0 > std::chrono::seconds(60))
+      throw Status{KFBI_ERR_TIMEOUT, "no batch state within 60 s"};
+  }
+  std::atomic_thread_fence(std::memory_order_acquire);
+  const int n = B->n;
+  for (int i = 0; i < 8 * n; ++i) B->h_scal[i] = slot[i];
+  const volatile int* fl = reinterpret_cast<const volatile int*>(slot + 8 * (size_t)B->cap);
+  for (int i = 0; i < 4 * n; ++i) B->h_flags[i] = fl[i];
+  for (int i = 0; i < n; ++i) {
     int f = 0;
     std::memcpy(&f, B->h_scal + 8 * i + 6, sizeof(int));
     if (f) throw Status{KFBI_ERR_TIMEOUT, "a tensor-core DST pass gave up waiting on its pipeline"};
   }
 }
+
+void read_state(kfbi_batch* B, cudaStream_t st) { wait_state(B, post_state(B, st), st); }
 
 void set_active(kfbi_batch* B, const std::vector<int>& act, const std::vector<int>* xz, cudaStream_t st) {
   std::vector<int> buf(act);
@@ -1420,8 +1486,10 @@ void batch_reserve(kfbi_batch* B, int n) {
   }
   if (B->h_scal) cudaFreeHost(B->h_scal);
   if (B->h_flags) cudaFreeHost(B->h_flags);
+  if (B->h_mbox) cudaFreeHost(B->h_mbox);
   B->d_inst = nullptr; B->d_flags = nullptr; B->d_sel = nullptr; B->d_scal_all = nullptr;
-  B->d_tol = nullptr; B->h_scal = nullptr; B->h_flags = nullptr;
+  B->d_tol = nullptr; B->h_scal = nullptr; B->h_flags = nullptr; B->h_mbox = nullptr;
+  B->d_mbox = nullptr;
   const int c = std::max(n, 2 * B->cap);
   B->cap = 0;
   KFBI_CUDA(cudaMalloc(&B->d_inst, sizeof(GInst) * c));
@@ -1432,6 +1500,12 @@ void batch_reserve(kfbi_batch* B, int n) {
   KFBI_CUDA(cudaMalloc(&B->d_tol, sizeof(double) * c));
   KFBI_CUDA(cudaMallocHost(&B->h_scal, sizeof(double) * 8 * c));
   KFBI_CUDA(cudaMallocHost(&B->h_flags, sizeof(int) * 4 * c));
+  {
+    const size_t bytes = 2 * (12 * (size_t)c + 16) * sizeof(double);
+    KFBI_CUDA(cudaHostAlloc(&B->h_mbox, bytes, cudaHostAllocMapped));
+    std::memset(B->h_mbox, 0, bytes);
+    KFBI_CUDA(cudaHostGetDevicePointer((void**)&B->d_mbox, B->h_mbox, 0));
+  }
   for (int k = 0; k < kfbi_batch::kPassKinds; ++k) {
     KFBI_CUDA(cudaMalloc(&B->d_pass[k], sizeof(PassDesc) * c));
     KFBI_CUDA(cudaMalloc(&B->d_prefix[k], sizeof(int) * (c + 1)));
@@ -1448,6 +1522,9 @@ kfbi_batch* batch_new() {
   KFBI_CUDA(cudaGetDevice(&B->device));
   KFBI_CUDA(cudaDeviceGetAttribute(&B->nsm, cudaDevAttrMultiProcessorCount, B->device));
   KFBI_CUDA(cudaMalloc(&B->d_j, sizeof(int)));
+  KFBI_CUDA(cudaMalloc(&B->d_postctr, sizeof(long long)));
+  KFBI_CUDA(cudaMemset(B->d_postctr, 0, sizeof(long long)));
+  B->host_posts = 0;
   return B;
 }
 
@@ -1518,6 +1595,8 @@ void kfbi_batch_destroy(kfbi_batch* B) {
     if (p) cudaFree(p);
   if (B->h_scal) cudaFreeHost(B->h_scal);
   if (B->h_flags) cudaFreeHost(B->h_flags);
+  if (B->h_mbox) cudaFreeHost(B->h_mbox);
+  if (B->d_postctr) cudaFree(B->d_postctr);
   delete B;
 }
 
@@ -1678,14 +1757,26 @@ kfbi_status batch_gmres(kfbi_batch* B, kfbi_solve_info* infos, cudaStream_t st) 
       bool any_left = false;
       for (int i = 0; i < n; ++i) any_left |= inner[i] != 0;
       if (!any_left) break;
-      for (int j = 0; j < m; ++j) {
-        // instances whose restart length is shorter stop at their m
+      // iteration j + 1 is queued before the host reads iteration j's posted
+      // state, so the GPU does not wait for the host between iterations;
+      // instances that converged at j are inactive on the device and skip
+      // j + 1, and when all have, the queued iteration's kernels only return
+      std::vector<long long> qj(m + 1, 0);
+      int queued = -1;
+      auto queue = [&](int j) {
         if (B->iter_graph) {
           KFBI_CUDA(cudaGraphLaunch(B->iter_graph, st));
           g_launches.fetch_add(B->launches);
-        } else
+        } else {
           batch_iteration(B, st);
-        read_state(B, st);
+        }
+        qj[j] = ++B->host_posts;  // the iteration ends with one state post
+        queued = j;
+      };
+      for (int j = 0; j < m; ++j) {
+        if (queued < j) queue(j);
+        if (j + 1 < m) queue(j + 1);
+        wait_state(B, qj[j], st);
         bool still = false;
         for (int i = 0; i < n; ++i) {
           if (!inner[i]) continue;
@@ -1942,6 +2033,15 @@ kfbi_status batch_step(kfbi_batch* B, kfbi_state* const* states, const void* con
     // (re)capture when the launch shapes changed or the batch was rebound
     capture_iteration(B);
     const int n = B->n;
+    // the state posts of this step count from 1 again (the previous step
+    // ended with the stream synchronised, so no post is in flight)
+    {
+      const size_t stride = 12 * (size_t)B->cap + 16;
+      for (int sl = 0; sl < 2; ++sl)
+        reinterpret_cast<volatile long long*>(B->h_mbox + sl * stride + stride - 1)[0] = 0;
+      KFBI_CUDA(cudaMemsetAsync(B->d_postctr, 0, sizeof(long long), st));
+      B->host_posts = 0;
+    }
     std::vector<int> all(n, 1);
     set_active(B, all, nullptr, st);
     KFBI_LAUNCH_P(KFBI_PROF_GRID, gk_make_ft, inst_grid(plane_blocks(B), n), 256, 0, st, B->d_inst);
