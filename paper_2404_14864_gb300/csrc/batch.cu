@@ -36,6 +36,9 @@ using tc::PassDesc;
 struct GInst {
   int Mp, n1, nb, n_irr, n_arms, M, m, C, eq;
   int fft;  // KFBI_MIXED_FFT32 instance: FFT passes on single FP32 planes (Rh, T1h, T2h, U32)
+  // FP32 pairs of 1/h^2, Re kappa, Im kappa (the double-float residual of
+  // FFT instances; split on the host)
+  float ih_hi, ih_lo, kr_hi, kr_lo, ki_hi, ki_lo;
   int rmin, nrows;
   double h, kre, kim, scale, dt, theta;
   double w;  // Schroedinger: nonlinear coefficient of the B step (Eq. 3.10)
@@ -133,7 +136,7 @@ __global__ void gk_make_ft(const GInst* gi) {
   }
   const double half_dt = 0.5 * I.dt, kim = I.kim;
   INST_PLANE_LOOP(I) {
-    const int r = (int)(idx / I.Mp), c = (int)(idx % I.Mp);
+    const int r = (int)((unsigned)idx / (unsigned)I.Mp), c = (int)idx - r * I.Mp;
     double xr = 0, xi = 0;
     if (r < I.n1 && c < I.n1) {
       // the modulus-preserving root of Eq. 3.10 (as k_schr_bstep)
@@ -233,8 +236,10 @@ __global__ void gk_split64(const GInst* gi) {
     for (int p = 0; p < P; ++p) {
       const size_t i = p * plane + idx;
       const double x = I.R64[i];
-      if (I.fft) {  // FFT passes read one FP32 plane
-        I.Rh[i] = (float)x;
+      if (I.fft) {  // FFT passes read the FP32 plane Rh; Rl keeps the remainder
+        const float h = (float)x;
+        I.Rh[i] = h;
+        I.Rl[i] = (float)(x - (double)h);
         continue;
       }
       const float h = tf32r((float)x);
@@ -254,7 +259,7 @@ __global__ void gk_eig_cplx(const GInst* gi) {
   const size_t plane = (size_t)I.Mp * I.Mp;
   const float kre = (float)I.kre, kim = (float)I.kim, scale = (float)I.scale;
   INST_PLANE_LOOP(I) {
-    const int a = (int)(idx / I.Mp), bcol = (int)(idx % I.Mp);
+    const int a = (int)((unsigned)idx / (unsigned)I.Mp), bcol = (int)idx - a * I.Mp;
     if (a >= I.n1 || bcol >= I.n1) continue;
     float zr, zi;
     eig_div_cplx32(I.T2h[idx] + I.T2l[idx], I.T2h[plane + idx] + I.T2l[plane + idx],
@@ -272,6 +277,7 @@ __global__ void gk_f32_to_f64(const GInst* gi) {
   KFBI_PDL_ENTRY();
   const GInst& I = gi[blockIdx.y];
   ACTIVE_OR_RETURN(I);
+  if (I.fft) return;  // gk_resid_u32 starts the FP64 grid of FFT instances
   const size_t plane = (size_t)I.Mp * I.Mp;
   const int P = I.C ? 2 : 1;
   INST_PLANE_LOOP(I) {
@@ -279,16 +285,86 @@ __global__ void gk_f32_to_f64(const GInst* gi) {
   }
 }
 
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+__device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
+  p = a * b;
+  e = fmaf(a, b, -p);
+}
+
+// Residual of the refinement for FFT instances (as k_resid_u32): from the
+// FP32 grid U32 and the FP32 pair (Rh, Rl) of R in double-float arithmetic,
+// r into Rh, and U64 = U32.
+__global__ void gk_resid_u32(const GInst* gi) {
+  KFBI_PDL_ENTRY();
+  const GInst& I = gi[blockIdx.y];
+  ACTIVE_OR_RETURN(I);
+  if (!I.fft) return;
+  const size_t plane = (size_t)I.Mp * I.Mp;
+  const int Mp = I.Mp, n1 = I.n1;
+  const bool C = I.C != 0;
+  INST_PLANE_LOOP(I) {
+    const int r = (int)((unsigned)idx / (unsigned)Mp), c = (int)idx - r * Mp;
+    const bool in = r < n1 && c < n1;
+    for (int p = 0; p < (C ? 2 : 1); ++p) {
+      const float* Up = I.U32 + p * plane;
+      const float u = in ? Up[idx] : 0.f;
+      float res = 0.f;
+      if (in) {
+        const float e = c + 1 < n1 ? Up[idx + 1] : 0.f;
+        const float w = c > 0 ? Up[idx - 1] : 0.f;
+        const float nn = r + 1 < n1 ? Up[idx + Mp] : 0.f;
+        const float so = r > 0 ? Up[idx - Mp] : 0.f;
+        float sh = -4.f * u, sl = 0.f, t;
+        two_sum(sh, e, sh, t);
+        sl += t;
+        two_sum(sh, w, sh, t);
+        sl += t;
+        two_sum(sh, nn, sh, t);
+        sl += t;
+        two_sum(sh, so, sh, t);
+        sl += t;
+        float p1, e1, p2, e2;
+        two_prod(sh, I.ih_hi, p1, e1);
+        two_prod(I.kr_hi, u, p2, e2);
+        float tail = e1 + fmaf(sh, I.ih_lo, sl * I.ih_hi) - e2 - I.kr_lo * u;
+        float lu_hi, t2;
+        two_sum(p1, -p2, lu_hi, t2);
+        tail += t2;
+        if (C) {
+          const float uo = I.U32[(1 - p) * plane + idx];
+          float p3, e3;
+          two_prod(I.ki_hi, uo, p3, e3);
+          const float sg = p == 0 ? 1.f : -1.f;
+          float t3;
+          two_sum(lu_hi, sg * p3, lu_hi, t3);
+          tail += t3 + sg * (e3 + I.ki_lo * uo);
+        }
+        const float R_hi = I.Rh[p * plane + idx], R_lo = I.Rl[p * plane + idx];
+        float d, t4;
+        two_sum(R_hi, -lu_hi, d, t4);
+        res = d + ((t4 + R_lo) - tail);
+      }
+      I.U64[p * plane + idx] = (double)u;
+      I.Rh[p * plane + idx] = res;
+    }
+  }
+}
+
 __global__ void gk_resid_split(const GInst* gi) {
   KFBI_PDL_ENTRY();
   const GInst& I = gi[blockIdx.y];
   ACTIVE_OR_RETURN(I);
+  if (I.fft) return;  // gk_resid_u32
   const size_t plane = (size_t)I.Mp * I.Mp;
   const int Mp = I.Mp, n1 = I.n1;
   const double inv_h2 = 1.0 / (I.h * I.h);
   const bool C = I.C != 0;
   INST_PLANE_LOOP(I) {
-    const int r = (int)(idx / Mp), c = (int)(idx % Mp);
+    const int r = (int)((unsigned)idx / (unsigned)Mp), c = (int)idx - r * Mp;
     for (int p = 0; p < (C ? 2 : 1); ++p) {
       double res = 0.0;
       if (r < n1 && c < n1) {
@@ -465,66 +541,139 @@ __global__ void __launch_bounds__(256) gk_sparse_p1(const GInst* gi) {
 
 // Gather of the stencil values and extraction (as k_gather_extract) into W.
 // TF32 instances leave the last pass's input with rows = x indices; FFT
-// instances (solve pass written transposed) with rows = y indices.
-__global__ void __launch_bounds__(192) gk_gather_extract(const GInst* gi, const int* dj) {
-  KFBI_PDL_ENTRY();
-  const GInst& I = gi[blockIdx.y];
-  ACTIVE_OR_RETURN(I);
-  const int k = blockIdx.x;
-  const int nb = I.nb;
-  if (k >= nb) return;
-  __shared__ float Ush[6][2];
+// instances (solve pass written transposed) with rows = y indices.  The six
+// stencil points of a node lie in a 3 x 3 window of grid rows and columns:
+// the node's warp streams the window's three grid rows and three S rows
+// (float4) and forms the nine window sums.  One warp per node: a batch holds
+// tens of thousands of nodes, and a block per node (as the single-domain
+// kernel, where a grid has about a thousand) kept too few nodes in flight.
+constexpr int GB_NODES = 4;  // nodes (warps) per block
+
+template <bool C, bool TY>
+__device__ __forceinline__ void gather_window(const GInst& I, int lane, int jlo, int ilo,
+                                              float* win) {
+  constexpr int NP = C ? 2 : 1;
   const int Mp = I.Mp;
   const size_t plane = (size_t)Mp * Mp;
-  const bool C = I.C != 0;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  {
-    const int off = I.node_gidx[warp * nb + k];
-    const int jr = off / Mp, ic = off - jr * Mp;
-    const float* t0 = I.U32 + (size_t)(I.fft ? jr : ic) * Mp;
-    const float* sr = I.S32 + (size_t)(I.fft ? ic : jr) * Mp;
-    float s0 = 0.f, s1 = 0.f;
-    for (int a = lane; a < Mp; a += 32) {
-      const float sv = sr[a];
-      s0 = fmaf(t0[a], sv, s0);
-      if (C) s1 = fmaf(t0[plane + a], sv, s1);
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-      s0 += __shfl_xor_sync(0xffffffffu, s0, o);
-      if (C) s1 += __shfl_xor_sync(0xffffffffu, s1, o);
-    }
-    if (lane == 0) {
-      Ush[warp][0] = s0;
-      Ush[warp][1] = s1;
-    }
+  const float4* tr[NP][3];
+  const float4* srow[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    // rows past the plane are clamped; their sums are never picked
+    const int ii = min(ilo + d, Mp - 1), jj = min(jlo + d, Mp - 1);
+    const int tt = TY ? jj : ii, ss = TY ? ii : jj;
+#pragma unroll
+    for (int q = 0; q < NP; ++q)
+      tr[q][d] = reinterpret_cast<const float4*>(I.U32 + q * plane + (size_t)tt * Mp);
+    srow[d] = reinterpret_cast<const float4*>(I.S32 + (size_t)ss * Mp);
   }
-  __syncthreads();
-  if (threadIdx.x != 0) return;
-  const double* phi = (const double*)(I.V + (size_t)(*dj) * nb);
+  float acc[NP][3][3];
+#pragma unroll
+  for (int q = 0; q < NP; ++q)
+#pragma unroll
+    for (int dj = 0; dj < 3; ++dj)
+#pragma unroll
+      for (int di = 0; di < 3; ++di) acc[q][dj][di] = 0.f;
+#pragma unroll 1
+  for (int a4 = lane; a4 < Mp / 4; a4 += 32) {
+    float4 t[NP][3], sv[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+#pragma unroll
+      for (int q = 0; q < NP; ++q) t[q][d] = tr[q][d][a4];
+      sv[d] = srow[d][a4];
+    }
+#pragma unroll
+    for (int q = 0; q < NP; ++q)
+#pragma unroll
+      for (int dj = 0; dj < 3; ++dj)
+#pragma unroll
+        for (int di = 0; di < 3; ++di) {
+          // window point (row jlo + dj, column ilo + di)
+          const float4 tv = t[q][TY ? dj : di], s4 = sv[TY ? di : dj];
+          float x = acc[q][dj][di];
+          x = fmaf(tv.x, s4.x, x);
+          x = fmaf(tv.y, s4.y, x);
+          x = fmaf(tv.z, s4.z, x);
+          x = fmaf(tv.w, s4.w, x);
+          acc[q][dj][di] = x;
+        }
+  }
+#pragma unroll
+  for (int q = 0; q < NP; ++q)
+#pragma unroll
+    for (int dj = 0; dj < 3; ++dj)
+#pragma unroll
+      for (int di = 0; di < 3; ++di) {
+        float x = acc[q][dj][di];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        if (lane == 0) win[q * 9 + dj * 3 + di] = x;
+      }
+  __syncwarp();
+}
+
+// One kernel per value type (the complex window holds twice the registers);
+// instances of the other type return at once.  Lane m < 6 fetches stencil
+// point m's offset and extraction operands before the rows stream in.
+template <bool C>
+__global__ void __launch_bounds__(32 * GB_NODES) gk_gather_extract(const GInst* gi, const int* dj) {
+  KFBI_PDL_ENTRY();
+  const GInst& I = gi[blockIdx.y];
+  if ((I.C != 0) != C) return;
+  ACTIVE_OR_RETURN(I);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int k = blockIdx.x * GB_NODES + warp;
+  const int nb = I.nb;
+  if (k >= nb) return;  // the whole warp
+  __shared__ float win[GB_NODES][2 * 9];
+  const int Mp = I.Mp;
+  int jl = Mp, il = Mp;
+  float wm = 0.f, am = 0.f, bm = 0.f, pr = 0.f, pi = 0.f;
+  if (lane < 6) {
+    const int off = I.node_gidx[lane * nb + k];
+    jl = off / Mp;
+    il = off - jl * Mp;
+    wm = I.node_w32[lane * nb + k];
+    am = I.node_a32[lane * nb + k];
+    bm = I.node_b32[lane * nb + k];
+    int kk = (k - 2 + lane) % nb;
+    if (kk < 0) kk += nb;
+    const double* phi = (const double*)(I.V + (size_t)(*dj) * nb);
+    pr = (float)phi[(size_t)kk * 2];
+    if (C) pi = (float)phi[(size_t)kk * 2 + 1];
+  }
+  // window origin: the least row and column over lanes 0-5
+  int jlo = jl, ilo = il;
+#pragma unroll
+  for (int o = 4; o > 0; o >>= 1) {
+    jlo = min(jlo, __shfl_xor_sync(0xffffffffu, jlo, o));
+    ilo = min(ilo, __shfl_xor_sync(0xffffffffu, ilo, o));
+  }
+  jlo = __shfl_sync(0xffffffffu, jlo, 0);
+  ilo = __shfl_sync(0xffffffffu, ilo, 0);
+  if (I.fft) gather_window<C, true>(I, lane, jlo, ilo, win[warp]);
+  else gather_window<C, false>(I, lane, jlo, ilo, win[warp]);
   const float kre = (float)I.kre, kim = (float)I.kim;
-  float sr = 0.f, si = 0.f;
+  float sr = 0.f, si = 0.f, ar = 0.f, ai = 0.f, br = 0.f, bi = 0.f;
 #pragma unroll
   for (int m = 0; m < 6; ++m) {
-    const float wm = I.node_w32[m * nb + k];
-    sr = fmaf(wm, Ush[m][0], sr);
-    if (C) si = fmaf(wm, Ush[m][1], si);
-  }
-  float ar = 0.f, ai = 0.f, br = 0.f, bi = 0.f;
-  int kk = k - 2;
-  if (kk < 0) kk += nb;
-#pragma unroll
-  for (int j = 0; j < 6; ++j) {
-    const float a = I.node_a32[j * nb + k], b = I.node_b32[j * nb + k];
-    const float pr = (float)phi[(size_t)kk * 2];
-    ar = fmaf(a, pr, ar);
-    br = fmaf(b, pr, br);
+    const int w_at = (__shfl_sync(0xffffffffu, jl, m) - jlo) * 3 + __shfl_sync(0xffffffffu, il, m) - ilo;
+    const float w_ = __shfl_sync(0xffffffffu, wm, m);
+    const float a_ = __shfl_sync(0xffffffffu, am, m);
+    const float b_ = __shfl_sync(0xffffffffu, bm, m);
+    const float pr_ = __shfl_sync(0xffffffffu, pr, m);
+    const float pi_ = C ? __shfl_sync(0xffffffffu, pi, m) : 0.f;
+    sr = fmaf(w_, win[warp][w_at], sr);
+    if (C) si = fmaf(w_, win[warp][9 + w_at], si);
+    ar = fmaf(a_, pr_, ar);
+    br = fmaf(b_, pr_, br);
     if (C) {
-      const float pi = (float)phi[(size_t)kk * 2 + 1];
-      ai = fmaf(a, pi, ai);
-      bi = fmaf(b, pi, bi);
+      ai = fmaf(a_, pi_, ai);
+      bi = fmaf(b_, pi_, bi);
     }
-    kk = (kk + 1 == nb) ? 0 : kk + 1;
   }
+  if (lane != 0) return;
   sr += ar + kre * br;
   if (C) {
     sr -= kim * bi;
@@ -993,7 +1142,7 @@ __global__ void gk_step_update(const GInst* gi) {
   if (I.eq == KFBI_HEAT) {
     const double four_dt = 4.0 / I.dt;
     INST_PLANE_LOOP(I) {
-      const int r = (int)(idx / I.Mp), c = (int)(idx % I.Mp);
+      const int r = (int)((unsigned)idx / (unsigned)I.Mp), c = (int)idx - r * I.Mp;
       const double uu = I.U64[idx];
       double f = four_dt * uu - I.F[idx];
       if (I.src && r < I.n1 && c < I.n1) f += I.src_scale * I.src[(size_t)r * I.n1 + c];
@@ -1094,7 +1243,8 @@ struct kfbi_batch {
   std::vector<kfbi_batch_tuning_t> tuning;  // one record per tuned group
   int force = -1;               // >= 0: use this candidate everywhere, no timing
   std::vector<long long> fft_sig;  // launch shapes baked into the captured graph
-  int n_fft = 0, n_tc = 0;
+  int n_fft = 0, n_tc = 0, n_cplx = 0;  // instance counts (FFT32, TF32, complex)
+  int gather_mask = 0;                   // gather kernels in the captured iteration
   // autotuned launch shape of the grouped passes (CTAs per SM multiple,
   // tile order) and the CUDA graph of one lockstep GMRES iteration
   int tile_order = 0;  // 0: instances in given order, 1: largest first
@@ -1368,8 +1518,12 @@ void batch_accurate(kfbi_batch* B, int which, int with_ft, int target, cudaStrea
       fft_grouped(B, kfbi_batch::kFftFinal, st);
     }
     if (sweep == 0) {
-      KFBI_LAUNCH_P(KFBI_PROF_GRID, gk_f32_to_f64, inst_grid(pb, n), 256, 0, st, B->d_inst);
-      KFBI_LAUNCH_P(KFBI_PROF_GRID, gk_resid_split, inst_grid(pb, n), 256, 0, st, B->d_inst);
+      if (B->n_tc > 0) {
+        KFBI_LAUNCH_P(KFBI_PROF_GRID, gk_f32_to_f64, inst_grid(pb, n), 256, 0, st, B->d_inst);
+        KFBI_LAUNCH_P(KFBI_PROF_GRID, gk_resid_split, inst_grid(pb, n), 256, 0, st, B->d_inst);
+      }
+      if (B->n_fft > 0)
+        KFBI_LAUNCH_P(KFBI_PROF_GRID, gk_resid_u32, inst_grid(pb, n), 256, 0, st, B->d_inst);
     } else {
       KFBI_LAUNCH_P(KFBI_PROF_GRID, gk_add_f32, inst_grid(pb, n), 256, 0, st, B->d_inst);
     }
@@ -1398,8 +1552,13 @@ void fast_apply(kfbi_batch* B, cudaStream_t st) {
     fft_grouped(B, kfbi_batch::kFftSparse1, st);
     fft_grouped(B, kfbi_batch::kFftSolveS, st);
   }
-  KFBI_LAUNCH_P(KFBI_PROF_EXTRACT, gk_gather_extract, inst_grid(B->max_nb, n), 192, 0, st, B->d_inst,
-                (const int*)B->d_j);
+  const dim3 gg = inst_grid((B->max_nb + GB_NODES - 1) / GB_NODES, n);
+  if (B->n_cplx < n)
+    KFBI_LAUNCH_P(KFBI_PROF_EXTRACT, gk_gather_extract<false>, gg, 32 * GB_NODES, 0, st, B->d_inst,
+                  (const int*)B->d_j);
+  if (B->n_cplx > 0)
+    KFBI_LAUNCH_P(KFBI_PROF_EXTRACT, gk_gather_extract<true>, gg, 32 * GB_NODES, 0, st, B->d_inst,
+                  (const int*)B->d_j);
 }
 
 // The state post kernel alone (inside a captured iteration the host counts
@@ -1552,7 +1711,12 @@ void batch_bind(kfbi_batch* B, kfbi_domain* const* domains, int n) {
     B->max_Mp = std::max(B->max_Mp, D->Mp);
     B->max_nrows = std::max(B->max_nrows, D->tc->nrows);
   }
-  B->max_planes_blocks = std::min(1024, (B->max_Mp * B->max_Mp + 255) / 256);
+  // grid-stride plane kernels: up to 8 points per thread on the largest
+  // plane, at least 8 blocks per SM over the batch (one block per 256 points
+  // left most blocks of a mixed-size batch with nothing to do)
+  const int full = (B->max_Mp * B->max_Mp + 255) / 256;
+  int pb = std::max((full + 7) / 8, (B->nsm * 8 + n - 1) / n);
+  B->max_planes_blocks = std::max(1, std::min({pb, full, 1024}));
 }
 
 }  // namespace kfbi
@@ -1611,13 +1775,21 @@ namespace {
 void fill_instances(kfbi_batch* B, kfbi_state* const* states, const void* const* g_next,
                     const double* const* src, const double* src_scale) {
   B->h_inst.resize(B->n);
+  B->n_cplx = 0;
   for (int i = 0; i < B->n; ++i) {
     kfbi_domain* D = B->doms[i];
     kfbi_state* S = states[i];
+    B->n_cplx += S->kim != 0.0 ? 1 : 0;
     TcDst* T = D->tc;
     GInst I{};
     I.Mp = D->Mp; I.n1 = D->n1; I.nb = D->nb; I.n_irr = D->n_irr; I.n_arms = D->n_arms;
     I.fft = T->fft ? 1 : 0; I.T1h = T->T1h;
+    {
+      const double ih2 = 1.0 / (D->h * D->h);
+      I.ih_hi = (float)ih2; I.ih_lo = (float)(ih2 - (double)I.ih_hi);
+      I.kr_hi = (float)S->kre; I.kr_lo = (float)(S->kre - (double)I.kr_hi);
+      I.ki_hi = (float)S->kim; I.ki_lo = (float)(S->kim - (double)I.ki_hi);
+    }
     I.M = D->M; I.m = D->restart; I.C = S->kim != 0.0; I.eq = S->eq;
     I.rmin = T->rmin; I.nrows = T->nrows;
     I.h = D->h; I.kre = S->kre; I.kim = S->kim; I.scale = (2.0 / D->M) * (2.0 / D->M);
@@ -1646,6 +1818,15 @@ void fill_instances(kfbi_batch* B, kfbi_state* const* states, const void* const*
     B->h_inst[i] = I;
   }
   KFBI_CUDA(cudaMemcpy(B->d_inst, B->h_inst.data(), sizeof(GInst) * B->n, cudaMemcpyHostToDevice));
+  // the captured iteration launches the real and/or the complex gather
+  const int gmask = (B->n_cplx < B->n ? 1 : 0) | (B->n_cplx > 0 ? 2 : 0);
+  if (gmask != B->gather_mask) {
+    B->gather_mask = gmask;
+    if (B->iter_graph) {
+      KFBI_CUDA(cudaGraphExecDestroy(B->iter_graph));
+      B->iter_graph = nullptr;
+    }
+  }
 }
 
 // Refinement GMRES for every instance, lockstep (see gmres_solve).  An
