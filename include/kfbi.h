@@ -392,6 +392,16 @@ kfbi_status kfbi_profile_work(int cls, double* flops);
  * irregular nodes counts only its writes). */
 kfbi_status kfbi_profile_bytes(int cls, double* bytes);
 
+/* Self-check of the FP32 <-> FP64 conversions the refinement kernels do on
+ * the integer and FP32 pipes (the GPU's FP64 pipe is narrow): on the current
+ * device, n seeded bit patterns (doubles of every exponent, rounding ties
+ * and carries; floats of every exponent) are converted both ways and by the
+ * hardware conversions, and *mismatches receives the number of results whose
+ * bits differ (0 expected).  Synchronous on `stream` (NULL: the legacy
+ * default stream).  KFBI_ERR_ARG for n < 1 or a NULL mismatches pointer. */
+kfbi_status kfbi_check_conversions(unsigned long long seed, long long n, long long* mismatches,
+                                   void* stream);
+
 /* Host-only plan: the geometry and coefficient tables kfbi_create_domain
  * uploads, built without touching the GPU, for inspection and tests. */
 typedef enum {

@@ -39,6 +39,10 @@ struct GInst {
   // FP32 pairs of 1/h^2, Re kappa, Im kappa (the double-float residual of
   // FFT instances; split on the host)
   float ih_hi, ih_lo, kr_hi, kr_lo, ki_hi, ki_lo;
+  // FFT instances: the FP32 pair of f-tilde, split once per step (held in
+  // the TF32 low planes, which the FFT passes leave unused)
+  float* fth;
+  float* ftl;
   int rmin, nrows;
   double h, kre, kim, scale, dt, theta;
   double w;  // Schroedinger: nonlinear coefficient of the B step (Eq. 3.10)
@@ -131,7 +135,11 @@ __global__ void gk_make_ft(const GInst* gi) {
   const GInst& I = gi[blockIdx.y];
   const size_t plane = (size_t)I.Mp * I.Mp;
   if (I.eq != KFBI_SCHRODINGER) {
-    INST_PLANE_LOOP(I) { I.ft[idx] = I.mask[idx] ? -I.F[idx] : 0.0; }
+    INST_PLANE_LOOP(I) {
+      const double v = I.mask[idx] ? -I.F[idx] : 0.0;
+      I.ft[idx] = v;
+      if (I.fft) split_f64(v, I.fth[idx], I.ftl[idx]);
+    }
     return;
   }
   const double half_dt = 0.5 * I.dt, kim = I.kim;
@@ -150,18 +158,34 @@ __global__ void gk_make_ft(const GInst* gi) {
     I.aux[idx] = xr;
     I.aux[plane + idx] = xi;
     const bool in = I.mask[idx] != 0;
-    I.ft[idx] = in ? kim * xi : 0.0;
-    I.ft[plane + idx] = in ? -kim * xr : 0.0;
+    const double vr = in ? kim * xi : 0.0, vi = in ? -kim * xr : 0.0;
+    I.ft[idx] = vr;
+    I.ft[plane + idx] = vi;
+    if (I.fft) {
+      split_f64(vr, I.fth[idx], I.ftl[idx]);
+      split_f64(vi, I.fth[plane + idx], I.ftl[plane + idx]);
+    }
   }
 }
 
-// R64 = f-tilde (with_ft) or 0 over the instance's planes.
+// R64 = f-tilde (with_ft) or 0 over the instance's planes; FFT instances
+// take the FP32 pair (Rh, Rl) straight from the split of f-tilde.
 __global__ void gk_base_rhs(const GInst* gi, int with_ft) {
   KFBI_PDL_ENTRY();
   const GInst& I = gi[blockIdx.y];
   ACTIVE_OR_RETURN(I);
   const size_t plane = (size_t)I.Mp * I.Mp;
   const int P = I.C ? 2 : 1;
+  if (I.fft) {
+    INST_PLANE_LOOP(I) {
+      for (int p = 0; p < P; ++p) {
+        const size_t i = p * plane + idx;
+        I.Rh[i] = with_ft ? I.fth[i] : 0.f;
+        I.Rl[i] = with_ft ? I.ftl[i] : 0.f;
+      }
+    }
+    return;
+  }
   INST_PLANE_LOOP(I) {
     for (int p = 0; p < P; ++p) I.R64[p * plane + idx] = with_ft ? I.ft[p * plane + idx] : 0.0;
   }
@@ -220,28 +244,30 @@ __global__ void gk_correct64(const GInst* gi, int which, int with_ft, const int*
       if (C) si += c0 * ft[plane + f0] + c1 * ft[plane + f1];
     }
   }
+  if (I.fft) {  // the FP32 pair the FFT passes and the residual read
+    split_f64(sr, I.Rh[off], I.Rl[off]);
+    if (C) split_f64(si, I.Rh[plane + off], I.Rl[plane + off]);
+    return;
+  }
   I.R64[off] = sr;
   if (C) I.R64[plane + off] = si;
 }
 
 __device__ __forceinline__ float tf32r(float x) { return tf32_round(x); }
 
+// TF32 pair of R64 (FFT instances have their pair from gk_base_rhs and
+// gk_correct64)
 __global__ void gk_split64(const GInst* gi) {
   KFBI_PDL_ENTRY();
   const GInst& I = gi[blockIdx.y];
   ACTIVE_OR_RETURN(I);
+  if (I.fft) return;
   const size_t plane = (size_t)I.Mp * I.Mp;
   const int P = I.C ? 2 : 1;
   INST_PLANE_LOOP(I) {
     for (int p = 0; p < P; ++p) {
       const size_t i = p * plane + idx;
       const double x = I.R64[i];
-      if (I.fft) {  // FFT passes read the FP32 plane Rh; Rl keeps the remainder
-        const float h = (float)x;
-        I.Rh[i] = h;
-        I.Rl[i] = (float)(x - (double)h);
-        continue;
-      }
       const float h = tf32r((float)x);
       I.Rh[i] = h;
       I.Rl[i] = tf32r((float)(x - (double)h));
@@ -281,7 +307,7 @@ __global__ void gk_f32_to_f64(const GInst* gi) {
   const size_t plane = (size_t)I.Mp * I.Mp;
   const int P = I.C ? 2 : 1;
   INST_PLANE_LOOP(I) {
-    for (int p = 0; p < P; ++p) I.U64[p * plane + idx] = (double)I.U32[p * plane + idx];
+    for (int p = 0; p < P; ++p) I.U64[p * plane + idx] = f32_to_f64(I.U32[p * plane + idx]);
   }
 }
 
@@ -348,7 +374,7 @@ __global__ void gk_resid_u32(const GInst* gi) {
         two_sum(R_hi, -lu_hi, d, t4);
         res = d + ((t4 + R_lo) - tail);
       }
-      I.U64[p * plane + idx] = (double)u;
+      I.U64[p * plane + idx] = f32_to_f64(u);
       I.Rh[p * plane + idx] = res;
     }
   }
@@ -399,7 +425,7 @@ __global__ void gk_add_f32(const GInst* gi) {
   const size_t plane = (size_t)I.Mp * I.Mp;
   const int P = I.C ? 2 : 1;
   INST_PLANE_LOOP(I) {
-    for (int p = 0; p < P; ++p) I.U64[p * plane + idx] += (double)I.U32[p * plane + idx];
+    for (int p = 0; p < P; ++p) I.U64[p * plane + idx] += f32_to_f64(I.U32[p * plane + idx]);
   }
 }
 
@@ -1503,7 +1529,7 @@ void batch_accurate(kfbi_batch* B, int which, int with_ft, int target, cudaStrea
   KFBI_LAUNCH_P(KFBI_PROF_GRID, gk_base_rhs, inst_grid(pb, n), 256, 0, st, B->d_inst, with_ft);
   KFBI_LAUNCH_P(KFBI_PROF_CORRECT, gk_correct64, inst_grid((B->max_n_irr + 127) / 128, n), 128, 0, st,
                 B->d_inst, which, with_ft, (const int*)nullptr);
-  KFBI_LAUNCH_P(KFBI_PROF_GRID, gk_split64, inst_grid(pb, n), 256, 0, st, B->d_inst);
+  if (B->n_tc > 0) KFBI_LAUNCH_P(KFBI_PROF_GRID, gk_split64, inst_grid(pb, n), 256, 0, st, B->d_inst);
   for (int sweep = 0; sweep < 2; ++sweep) {
     if (B->n_tc > 0) {
       grouped_pass(B, kfbi_batch::kDense1, st);
@@ -1803,6 +1829,7 @@ void fill_instances(kfbi_batch* B, kfbi_state* const* states, const void* const*
     I.node_w32 = D->d_node_w32; I.node_a32 = D->d_node_a32; I.node_b32 = D->d_node_b32;
     I.S32 = T->S32; I.row_start = T->row_start; I.node_col = T->node_col;
     I.R64 = D->d_R; I.U64 = D->d_U; I.Rh = T->Rh; I.Rl = T->Rl; I.T2h = T->T2h; I.T2l = T->T2l;
+    I.fth = T->T1l; I.ftl = T->T2l;
     I.U32 = T->U; I.T1sh = T->T1sh; I.T1sl = T->T1sl; I.rv = T->rv;
     I.V = (double2*)D->d_V; I.W = (double2*)D->d_W; I.H = (double2*)D->d_H; I.cs = D->d_cs;
     I.sn = (double2*)D->d_sn; I.g = (double2*)D->d_g; I.hcol = (double2*)D->d_hcol;

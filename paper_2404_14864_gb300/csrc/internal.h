@@ -153,6 +153,79 @@ __host__ __device__ inline float tf32_round(float x) {
 }
 
 #ifdef __CUDACC__
+// FP32 <-> FP64 conversions on the integer and FP32 pipes.  GB300 runs FP64
+// conversions on its narrow FP64 pipe (about two operations per clock per
+// SM), which bounds the plane kernels of the refinement.  Both functions
+// return exactly what the hardware conversions return (round to nearest,
+// ties to even); inputs outside the exponent ranges they handle (zeros and
+// tiny, huge or non-finite values) take the hardware conversion.
+
+// The hardware split, out of line: inlined, the compiler predicates it into
+// the fast path, where it still occupies the FP64 pipe.
+static __device__ __noinline__ float2 split_f64_hw(double x) {
+  const float h = (float)x;
+  return make_float2(h, (float)(x - (double)h));
+}
+
+// float -> double, exact for every finite x (a NaN gives a NaN): the
+// exponent rebiased from 127 to 1023, a subnormal normalised by its leading
+// zeros, infinities and NaNs mapped to exponent 2047.
+__device__ __forceinline__ double f32_to_f64(float x) {
+  const uint32_t u = __float_as_uint(x);
+  const uint32_t e = (u >> 23) & 0xffu, m = u & 0x7fffffu;
+  uint32_t de = e + 896u;
+  unsigned long long dm = (unsigned long long)m << 29;
+  if (e == 0u) {
+    // 0 or m 2^-149: the top bit of m at position p = 31 - clz(m) gives
+    // exponent p - 149 (biased p + 874), the bits below it the fraction
+    const int p = 31 - __clz((int)m);
+    de = m ? (uint32_t)(p + 874) : 0u;
+    dm = m ? (((unsigned long long)m << (52 - p)) & 0xfffffffffffffull) : 0ull;
+  } else if (e == 0xffu) {
+    de = 0x7ffu;
+  }
+  const unsigned long long b = ((unsigned long long)(u & 0x80000000u) << 32) |
+                               ((unsigned long long)de << 52) | dm;
+  return __longlong_as_double((long long)b);
+}
+
+// x = hi + lo + O(2^-48 |x|): hi = (float)x, lo = (float)(x - (double)hi).
+// For 949 <= biased exponent <= 1149 (2^-74 <= |x| < 2^127): hi keeps the
+// top 24 significand bits, rounded on the 29 bits below them; x - hi is that
+// remainder r (|r| <= 2^28) times 2^(e - 1075), converted to FP32 in one
+// rounding as two exact 14-bit halves joined by an FMA.
+__device__ __forceinline__ void split_f64(double x, float& hi, float& lo) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const uint32_t w = (uint32_t)(b >> 32);
+  const int e = (int)((w >> 20) & 0x7ffu);
+  if (e < 949 || e > 1149) {
+    if ((b << 1) == 0ull) {  // +-0 (the plane padding)
+      hi = __uint_as_float(w);
+      lo = 0.f;
+      return;
+    }
+    const float2 v = split_f64_hw(x);
+    hi = v.x;
+    lo = v.y;
+    return;
+  }
+  const uint32_t s = w & 0x80000000u;
+  uint32_t f = s | ((uint32_t)(e - 896) << 23) | (uint32_t)((b >> 29) & 0x7fffffu);
+  int r = (int)(b & 0x1fffffffu);
+  if (r > 0x10000000 || (r == 0x10000000 && (f & 1u))) {
+    f += 1u;  // a carry out of the significand raises the exponent: still exact
+    r -= 0x20000000;
+  }
+  hi = __uint_as_float(f);
+  const uint32_t ar = (uint32_t)(r < 0 ? -r : r);
+  const float fh = __uint_as_float(0x4b000000u | (ar >> 14)) - 8388608.f;
+  const float fl = __uint_as_float(0x4b000000u | (ar & 0x3fffu)) - 8388608.f;
+  const float v = fmaf(fh, 16384.f, fl) * __uint_as_float((uint32_t)(e - 948) << 23);
+  // sign of x - hi: sign of x, flipped where hi rounded away from zero (an
+  // exact split leaves +0, as the hardware subtraction does)
+  lo = (ar != 0u && (s != 0) != (r < 0)) ? -v : v;
+}
+
 // Complex eigenvalue division of a box solve in FP32:
 // (x + i y) scale / (d - i kim) = (x + i y)(d + i kim) scale / (d^2 + kim^2).
 __device__ __forceinline__ void eig_div_cplx32(float x, float y, float d, float kim, float scale,

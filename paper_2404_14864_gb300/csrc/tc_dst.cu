@@ -687,14 +687,11 @@ __global__ void k_split64(const double* __restrict__ src, float* __restrict__ hi
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
        i += (size_t)gridDim.x * blockDim.x) {
     const double x = src[i];
-    if (!lo) {  // single FP32 plane (FFT passes)
-      hi[i] = (float)x;
-      continue;
-    }
-    if (fp32_lo) {
-      const float h = (float)x;
+    if (!lo || fp32_lo) {  // FP32 plane(s) of the FFT passes
+      float h, l;
+      split_f64(x, h, l);
       hi[i] = h;
-      lo[i] = (float)(x - (double)h);
+      if (lo) lo[i] = l;
       continue;
     }
     const float h = tf32_round((float)x);
@@ -1065,7 +1062,7 @@ __global__ void k_f32_to_f64(const float* __restrict__ src, double* __restrict__
   KFBI_PDL_ENTRY();
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
        i += (size_t)gridDim.x * blockDim.x)
-    dst[i] = (double)src[i];
+    dst[i] = f32_to_f64(src[i]);
 }
 
 // Residual of the five-point system in FP64 for the iterative refinement of
@@ -1187,7 +1184,7 @@ __global__ void __launch_bounds__(256) k_resid_u32(float* __restrict__ Rh,
         two_sum(R_hi, -lu_hi, d, t4);
         res = d + ((t4 + R_lo) - tail);
       }
-      U64[p * plane + idx] = (double)u;
+      U64[p * plane + idx] = f32_to_f64(u);
       Rh[p * plane + idx] = res;
     }
   }
@@ -1197,7 +1194,7 @@ __global__ void k_add_f32(double* __restrict__ dst, const float* __restrict__ sr
   KFBI_PDL_ENTRY();
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
        i += (size_t)gridDim.x * blockDim.x)
-    dst[i] += (double)src[i];
+    dst[i] += f32_to_f64(src[i]);
 }
 
 const int kPassThreads = THREADS;
@@ -1801,3 +1798,80 @@ void tc_apply_accurate(kfbi_domain* D, double kre, double kim, const double* phi
 }
 
 }  // namespace kfbi
+
+// ---- self-check of the integer-pipe conversions ----------------------------
+
+namespace kfbi {
+namespace {
+
+__device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
+  // splitmix64 finaliser
+  z += 0x9e3779b97f4a7c15ull;
+  z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+  z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+  return z ^ (z >> 31);
+}
+
+__global__ void k_check_conversions(unsigned long long seed, long long n,
+                                    unsigned long long* bad) {
+  unsigned long long local = 0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const unsigned long long z = mix64(seed ^ mix64((unsigned long long)i));
+    unsigned long long b = z;
+    const unsigned long long sign = z & 0x8000000000000000ull;
+    switch (i & 3) {
+      case 0: break;  // any bit pattern
+      case 1:         // exponents around the handled range
+        b = sign | ((unsigned long long)(900 + (z >> 40) % 300) << 52) | (z & 0xfffffffffffffull);
+        break;
+      case 2:  // rounding ties: the 29 bits below the FP32 significand are 1000...0
+        b = sign | ((unsigned long long)(940 + (z >> 40) % 220) << 52) |
+            (z & 0xfffffe0000000ull) | 0x10000000ull;
+        break;
+      default:  // all-ones significand: the rounding carries into the exponent
+        b = sign | ((unsigned long long)(940 + (z >> 40) % 220) << 52) |
+            (0xfffffe0000000ull | ((z >> 11) & 0x1fffffffull));
+        break;
+    }
+    const double x = __longlong_as_double((long long)b);
+    float hi, lo;
+    split_f64(x, hi, lo);
+    const float h_ref = (float)x;
+    const float l_ref = (float)(x - (double)h_ref);
+    if (h_ref != h_ref) {
+      local += hi == hi;
+    } else {
+      local += __float_as_uint(hi) != __float_as_uint(h_ref);
+      local += __float_as_uint(lo) != __float_as_uint(l_ref);
+    }
+    const float f = __uint_as_float((uint32_t)(z >> 17));
+    const double d = f32_to_f64(f), d_ref = (double)f;
+    if (d_ref != d_ref) local += d == d;  // a NaN must stay a NaN (payloads may differ)
+    else local += __double_as_longlong(d) != __double_as_longlong(d_ref);
+  }
+  if (local) atomicAdd(bad, local);
+}
+
+}  // namespace
+}  // namespace kfbi
+
+extern "C" kfbi_status kfbi_check_conversions(unsigned long long seed, long long n,
+                                              long long* mismatches, void* stream) {
+  if (!mismatches || n < 1) return KFBI_ERR_ARG;
+  return kfbi::guarded(nullptr, [&]() -> kfbi_status {
+    cudaStream_t st = (cudaStream_t)stream;
+    unsigned long long* d_bad = nullptr;
+    KFBI_CUDA(cudaMallocAsync(&d_bad, sizeof(unsigned long long), st));
+    KFBI_CUDA(cudaMemsetAsync(d_bad, 0, sizeof(unsigned long long), st));
+    const long long blocks = std::min<long long>((n + 255) / 256, 4096);
+    kfbi::k_check_conversions<<<(unsigned)blocks, 256, 0, st>>>(seed, n, d_bad);
+    KFBI_CHECK_LAUNCH();
+    unsigned long long h_bad = 0;
+    KFBI_CUDA(cudaMemcpyAsync(&h_bad, d_bad, sizeof(h_bad), cudaMemcpyDeviceToHost, st));
+    KFBI_CUDA(cudaFreeAsync(d_bad, st));
+    KFBI_CUDA(cudaStreamSynchronize(st));
+    *mismatches = (long long)h_bad;
+    return KFBI_OK;
+  });
+}

@@ -167,6 +167,8 @@ def lib():
                                   ctypes.POINTER(ctypes.c_double)]),
         "kfbi_profile_work": (S, [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
         "kfbi_profile_bytes": (S, [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
+        "kfbi_check_conversions": (S, [ctypes.c_ulonglong, ctypes.c_longlong,
+                                       ctypes.POINTER(ctypes.c_longlong), ctypes.c_void_p]),
         "kfbi_box_solve_noalloc": (S, [ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                        ctypes.c_double, ctypes.c_double, _VP, _VP, _VP]),
         "kfbi_batch_create": (S, [ctypes.POINTER(_VP), ctypes.c_int, _VP, ctypes.POINTER(_VP)]),
@@ -299,6 +301,14 @@ def kfbi_profile_bytes(cls):
     w = ctypes.c_double()
     _check(lib().kfbi_profile_bytes(int(cls), ctypes.byref(w)))
     return float(w.value)
+
+
+def kfbi_check_conversions(seed, n, stream=None):
+    """Bit mismatches of the integer-pipe FP32/FP64 conversions against the
+    hardware ones over n seeded patterns (0 expected)."""
+    m = ctypes.c_longlong()
+    _check(lib().kfbi_check_conversions(int(seed), int(n), ctypes.byref(m), _stream(stream)))
+    return int(m.value)
 
 
 # ----------------------------------------------------------------------------
