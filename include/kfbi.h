@@ -402,6 +402,16 @@ kfbi_status kfbi_profile_bytes(int cls, double* bytes);
 kfbi_status kfbi_check_conversions(unsigned long long seed, long long n, long long* mismatches,
                                    void* stream);
 
+/* Self-check of the bounded device-side waits (the tensor-core passes'
+ * pipeline waits give up after a cycle limit, record the failure in the
+ * domain's error word, and the call returns KFBI_ERR_TIMEOUT): one block
+ * waits, with the same wait routine and a limit of `seconds`, on an mbarrier
+ * that nothing completes.  Returns KFBI_ERR_TIMEOUT when the wait gave up as
+ * designed (the expected result; the device stays usable), KFBI_OK if the
+ * wait completed, KFBI_ERR_ARG unless 0 < seconds <= 1.  Synchronous on
+ * `stream`. */
+kfbi_status kfbi_check_wait_timeout(double seconds, void* stream);
+
 /* Host-only plan: the geometry and coefficient tables kfbi_create_domain
  * uploads, built without touching the GPU, for inspection and tests. */
 typedef enum {

@@ -124,6 +124,33 @@ __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
   for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x;                         \
        idx < (size_t)(I).Mp * (I).Mp; idx += (size_t)gridDim.x * blockDim.x)
 
+// Grid-stride over the padded plane in quads: four consecutive points of one
+// grid row (Mp is a multiple of 128), moved with 16-byte vector accesses so
+// that each thread keeps four points' loads in flight (one point per
+// iteration left these kernels waiting on memory latency at a third of the
+// HBM bandwidth).
+#define INST_QUAD_LOOP(I)                                                                  \
+  for (size_t idx = 4 * (blockIdx.x * (size_t)blockDim.x + threadIdx.x);                   \
+       idx < (size_t)(I).Mp * (I).Mp; idx += 4 * (size_t)gridDim.x * blockDim.x)
+
+struct Quad {
+  double v[4];
+};
+__device__ __forceinline__ Quad ldq(const double* p) {
+  const double2 a = reinterpret_cast<const double2*>(p)[0];
+  const double2 b = reinterpret_cast<const double2*>(p)[1];
+  return Quad{{a.x, a.y, b.x, b.y}};
+}
+__device__ __forceinline__ void stq(double* p, const Quad& q) {
+  reinterpret_cast<double2*>(p)[0] = make_double2(q.v[0], q.v[1]);
+  reinterpret_cast<double2*>(p)[1] = make_double2(q.v[2], q.v[3]);
+}
+__device__ __forceinline__ float4 ldf4(const float* p) { return *reinterpret_cast<const float4*>(p); }
+__device__ __forceinline__ void stf4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
+__device__ __forceinline__ float f4at(const float4& v, int k) {
+  return k == 0 ? v.x : k == 1 ? v.y : k == 2 ? v.z : v.w;
+}
+
 #define ACTIVE_OR_RETURN(I) \
   if ((I).flags[0] == 0) return;
 
@@ -135,10 +162,21 @@ __global__ void gk_make_ft(const GInst* gi) {
   const GInst& I = gi[blockIdx.y];
   const size_t plane = (size_t)I.Mp * I.Mp;
   if (I.eq != KFBI_SCHRODINGER) {
-    INST_PLANE_LOOP(I) {
-      const double v = I.mask[idx] ? -I.F[idx] : 0.0;
-      I.ft[idx] = v;
-      if (I.fft) split_f64(v, I.fth[idx], I.ftl[idx]);
+    INST_QUAD_LOOP(I) {
+      const uchar4 mk = *reinterpret_cast<const uchar4*>(I.mask + idx);
+      const Quad f = ldq(I.F + idx);
+      const Quad v{{mk.x ? -f.v[0] : 0.0, mk.y ? -f.v[1] : 0.0, mk.z ? -f.v[2] : 0.0,
+                    mk.w ? -f.v[3] : 0.0}};
+      stq(I.ft + idx, v);
+      if (I.fft) {
+        float4 h, l;
+        split_f64(v.v[0], h.x, l.x);
+        split_f64(v.v[1], h.y, l.y);
+        split_f64(v.v[2], h.z, l.z);
+        split_f64(v.v[3], h.w, l.w);
+        stf4(I.fth + idx, h);
+        stf4(I.ftl + idx, l);
+      }
     }
     return;
   }
@@ -176,18 +214,22 @@ __global__ void gk_base_rhs(const GInst* gi, int with_ft) {
   ACTIVE_OR_RETURN(I);
   const size_t plane = (size_t)I.Mp * I.Mp;
   const int P = I.C ? 2 : 1;
+  const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
   if (I.fft) {
-    INST_PLANE_LOOP(I) {
+    INST_QUAD_LOOP(I) {
       for (int p = 0; p < P; ++p) {
         const size_t i = p * plane + idx;
-        I.Rh[i] = with_ft ? I.fth[i] : 0.f;
-        I.Rl[i] = with_ft ? I.ftl[i] : 0.f;
+        stf4(I.Rh + i, with_ft ? ldf4(I.fth + i) : z4);
+        stf4(I.Rl + i, with_ft ? ldf4(I.ftl + i) : z4);
       }
     }
     return;
   }
-  INST_PLANE_LOOP(I) {
-    for (int p = 0; p < P; ++p) I.R64[p * plane + idx] = with_ft ? I.ft[p * plane + idx] : 0.0;
+  INST_QUAD_LOOP(I) {
+    for (int p = 0; p < P; ++p) {
+      const size_t i = p * plane + idx;
+      stq(I.R64 + i, with_ft ? ldq(I.ft + i) : Quad{{0.0, 0.0, 0.0, 0.0}});
+    }
   }
 }
 
@@ -321,63 +363,93 @@ __device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
   e = fmaf(a, b, -p);
 }
 
+// r = R - L u at one point, in double-float arithmetic from FP32 values:
+// u and its four neighbours, uo the other plane's u (complex: L couples the
+// planes through +-Im kappa, sg = +1 for the real plane, -1 for the
+// imaginary one), (R_hi, R_lo) the FP32 pair of R.
+template <bool C>
+__device__ __forceinline__ float resid_df(const GInst& I, float u, float e, float w, float nn,
+                                          float so, float uo, float sg, float R_hi, float R_lo) {
+  float sh = -4.f * u, sl = 0.f, t;
+  two_sum(sh, e, sh, t);
+  sl += t;
+  two_sum(sh, w, sh, t);
+  sl += t;
+  two_sum(sh, nn, sh, t);
+  sl += t;
+  two_sum(sh, so, sh, t);
+  sl += t;
+  float p1, e1, p2, e2;
+  two_prod(sh, I.ih_hi, p1, e1);
+  two_prod(I.kr_hi, u, p2, e2);
+  float tail = e1 + fmaf(sh, I.ih_lo, sl * I.ih_hi) - e2 - I.kr_lo * u;
+  float lu_hi, t2;
+  two_sum(p1, -p2, lu_hi, t2);
+  tail += t2;
+  if (C) {
+    float p3, e3;
+    two_prod(I.ki_hi, uo, p3, e3);
+    float t3;
+    two_sum(lu_hi, sg * p3, lu_hi, t3);
+    tail += t3 + sg * (e3 + I.ki_lo * uo);
+  }
+  float d, t4;
+  two_sum(R_hi, -lu_hi, d, t4);
+  return d + ((t4 + R_lo) - tail);
+}
+
+template <bool C>
+__device__ __forceinline__ void resid_u32_quads(const GInst& I) {
+  const size_t plane = (size_t)I.Mp * I.Mp;
+  const int Mp = I.Mp, n1 = I.n1;
+  const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+  INST_QUAD_LOOP(I) {
+    const int r = (int)((unsigned)idx / (unsigned)Mp), c0 = (int)idx - r * Mp;
+    const bool live = r < n1 && c0 < n1;
+#pragma unroll
+    for (int p = 0; p < (C ? 2 : 1); ++p) {
+      const float* Up = I.U32 + p * plane;
+      float4 res = z4, uq = z4;
+      if (live) {
+        uq = ldf4(Up + idx);
+        const float4 un = r + 1 < n1 ? ldf4(Up + idx + Mp) : z4;
+        const float4 us = r > 0 ? ldf4(Up + idx - Mp) : z4;
+        const float uw = c0 > 0 ? Up[idx - 1] : 0.f;
+        const float ue = c0 + 4 < n1 ? Up[idx + 4] : 0.f;
+        const float4 uo = C ? ldf4(I.U32 + (1 - p) * plane + idx) : z4;
+        const float4 rh = ldf4(I.Rh + p * plane + idx), rl = ldf4(I.Rl + p * plane + idx);
+        float o[4], uu[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const int c = c0 + k;
+          const float u = c < n1 ? f4at(uq, k) : 0.f;
+          const float e = c + 1 < n1 ? (k < 3 ? f4at(uq, k + 1) : ue) : 0.f;
+          const float w = c > 0 ? (k > 0 ? f4at(uq, k - 1) : uw) : 0.f;
+          uu[k] = u;
+          o[k] = c < n1 ? resid_df<C>(I, u, e, w, f4at(un, k), f4at(us, k), f4at(uo, k),
+                                      p == 0 ? 1.f : -1.f, f4at(rh, k), f4at(rl, k))
+                        : 0.f;
+        }
+        res = make_float4(o[0], o[1], o[2], o[3]);
+        uq = make_float4(uu[0], uu[1], uu[2], uu[3]);
+      }
+      stq(I.U64 + p * plane + idx, Quad{{f32_to_f64(uq.x), f32_to_f64(uq.y), f32_to_f64(uq.z),
+                                         f32_to_f64(uq.w)}});
+      stf4(I.Rh + p * plane + idx, res);
+    }
+  }
+}
+
 // Residual of the refinement for FFT instances (as k_resid_u32): from the
 // FP32 grid U32 and the FP32 pair (Rh, Rl) of R in double-float arithmetic,
-// r into Rh, and U64 = U32.
+// r into Rh, and U64 = U32 (0 outside the n1 x n1 block).
 __global__ void gk_resid_u32(const GInst* gi) {
   KFBI_PDL_ENTRY();
   const GInst& I = gi[blockIdx.y];
   ACTIVE_OR_RETURN(I);
   if (!I.fft) return;
-  const size_t plane = (size_t)I.Mp * I.Mp;
-  const int Mp = I.Mp, n1 = I.n1;
-  const bool C = I.C != 0;
-  INST_PLANE_LOOP(I) {
-    const int r = (int)((unsigned)idx / (unsigned)Mp), c = (int)idx - r * Mp;
-    const bool in = r < n1 && c < n1;
-    for (int p = 0; p < (C ? 2 : 1); ++p) {
-      const float* Up = I.U32 + p * plane;
-      const float u = in ? Up[idx] : 0.f;
-      float res = 0.f;
-      if (in) {
-        const float e = c + 1 < n1 ? Up[idx + 1] : 0.f;
-        const float w = c > 0 ? Up[idx - 1] : 0.f;
-        const float nn = r + 1 < n1 ? Up[idx + Mp] : 0.f;
-        const float so = r > 0 ? Up[idx - Mp] : 0.f;
-        float sh = -4.f * u, sl = 0.f, t;
-        two_sum(sh, e, sh, t);
-        sl += t;
-        two_sum(sh, w, sh, t);
-        sl += t;
-        two_sum(sh, nn, sh, t);
-        sl += t;
-        two_sum(sh, so, sh, t);
-        sl += t;
-        float p1, e1, p2, e2;
-        two_prod(sh, I.ih_hi, p1, e1);
-        two_prod(I.kr_hi, u, p2, e2);
-        float tail = e1 + fmaf(sh, I.ih_lo, sl * I.ih_hi) - e2 - I.kr_lo * u;
-        float lu_hi, t2;
-        two_sum(p1, -p2, lu_hi, t2);
-        tail += t2;
-        if (C) {
-          const float uo = I.U32[(1 - p) * plane + idx];
-          float p3, e3;
-          two_prod(I.ki_hi, uo, p3, e3);
-          const float sg = p == 0 ? 1.f : -1.f;
-          float t3;
-          two_sum(lu_hi, sg * p3, lu_hi, t3);
-          tail += t3 + sg * (e3 + I.ki_lo * uo);
-        }
-        const float R_hi = I.Rh[p * plane + idx], R_lo = I.Rl[p * plane + idx];
-        float d, t4;
-        two_sum(R_hi, -lu_hi, d, t4);
-        res = d + ((t4 + R_lo) - tail);
-      }
-      I.U64[p * plane + idx] = f32_to_f64(u);
-      I.Rh[p * plane + idx] = res;
-    }
-  }
+  if (I.C) resid_u32_quads<true>(I);
+  else resid_u32_quads<false>(I);
 }
 
 __global__ void gk_resid_split(const GInst* gi) {
@@ -424,8 +496,17 @@ __global__ void gk_add_f32(const GInst* gi) {
   ACTIVE_OR_RETURN(I);
   const size_t plane = (size_t)I.Mp * I.Mp;
   const int P = I.C ? 2 : 1;
-  INST_PLANE_LOOP(I) {
-    for (int p = 0; p < P; ++p) I.U64[p * plane + idx] += f32_to_f64(I.U32[p * plane + idx]);
+  INST_QUAD_LOOP(I) {
+    for (int p = 0; p < P; ++p) {
+      const size_t i = p * plane + idx;
+      const float4 d = ldf4(I.U32 + i);
+      Quad u = ldq(I.U64 + i);
+      u.v[0] += f32_to_f64(d.x);
+      u.v[1] += f32_to_f64(d.y);
+      u.v[2] += f32_to_f64(d.z);
+      u.v[3] += f32_to_f64(d.w);
+      stq(I.U64 + i, u);
+    }
   }
 }
 
@@ -833,8 +914,8 @@ __global__ void gk_keep_uf(const GInst* gi) {
   ACTIVE_OR_RETURN(I);
   const size_t plane = (size_t)I.Mp * I.Mp;
   const int P = I.C ? 2 : 1;
-  INST_PLANE_LOOP(I) {
-    for (int p = 0; p < P; ++p) I.uf[p * plane + idx] = I.U64[p * plane + idx];
+  INST_QUAD_LOOP(I) {
+    for (int p = 0; p < P; ++p) stq(I.uf + p * plane + idx, ldq(I.U64 + p * plane + idx));
   }
 }
 
@@ -844,8 +925,15 @@ __global__ void gk_add_uf(const GInst* gi) {
   ACTIVE_OR_RETURN(I);
   const size_t plane = (size_t)I.Mp * I.Mp;
   const int P = I.C ? 2 : 1;
-  INST_PLANE_LOOP(I) {
-    for (int p = 0; p < P; ++p) I.U64[p * plane + idx] += I.uf[p * plane + idx];
+  INST_QUAD_LOOP(I) {
+    for (int p = 0; p < P; ++p) {
+      const size_t i = p * plane + idx;
+      Quad u = ldq(I.U64 + i);
+      const Quad f = ldq(I.uf + i);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) u.v[k] += f.v[k];
+      stq(I.U64 + i, u);
+    }
   }
 }
 
@@ -1084,6 +1172,143 @@ __global__ void __launch_bounds__(GT) gk_cgs_finalize(const GInst* gi, const int
   }
 }
 
+// One CGS2 Arnoldi step of an instance in one block (the batch holds many
+// small instances: the four-kernel form above spent most of its time in
+// cross-block partial sums and launch latency).  W is staged in shared
+// memory; each warp forms the dots of one basis vector at a time; the
+// Hessenberg column, the earlier rotations and the right-hand side g are
+// rotated in shared memory by one thread.  Same arithmetic as
+// gk_cgs_dots/update/finalize up to the order of the partial sums.
+constexpr int AT = 512;
+constexpr int kArnoldiMaxNb = 8192;  // W in shared memory: 128 KiB
+
+template <bool C>
+__global__ void __launch_bounds__(AT) gk_arnoldi(const GInst* gi, const int* dj) {
+  KFBI_PDL_ENTRY();
+  const GInst& I = gi[blockIdx.x];
+  if ((I.C != 0) != C) return;
+  ACTIVE_OR_RETURN(I);
+  extern __shared__ double2 Ws[];  // nb
+  __shared__ double2 h[2][GMAX + 1];
+  __shared__ double2 sn_s[GMAX];
+  __shared__ double cs_s[GMAX];
+  __shared__ double red[AT / 32];
+  const int j = *dj, nb = I.nb, m = I.m;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int e = threadIdx.x; e < nb; e += AT) Ws[e] = I.W[e];
+  for (int i = threadIdx.x; i < j; i += AT) {
+    cs_s[i] = I.cs[i];
+    sn_s[i] = I.sn[i];
+  }
+  __syncthreads();
+  for (int pass = 0; pass < 2; ++pass) {
+    // h_i = V_i^H W
+    for (int i = warp; i <= j; i += AT / 32) {
+      const double2* v = I.V + (size_t)i * nb;
+      double sx = 0.0, sy = 0.0;
+      for (int e = lane; e < nb; e += 32) {
+        const double2 x = v[e], y = Ws[e];
+        if (C) {
+          sx += x.x * y.x + x.y * y.y;
+          sy += x.x * y.y - x.y * y.x;
+        } else {
+          sx += x.x * y.x;
+        }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        sx += __shfl_xor_sync(0xffffffffu, sx, o);
+        if (C) sy += __shfl_xor_sync(0xffffffffu, sy, o);
+      }
+      if (lane == 0) h[pass][i] = make_double2(sx, sy);
+    }
+    __syncthreads();
+    // W -= V h
+    for (int e = threadIdx.x; e < nb; e += AT) {
+      double2 acc = Ws[e];
+      for (int i = 0; i <= j; ++i) {
+        const double2 v = I.V[(size_t)i * nb + e], hi = h[pass][i];
+        if (C) {
+          acc.x -= hi.x * v.x - hi.y * v.y;
+          acc.y -= hi.x * v.y + hi.y * v.x;
+        } else {
+          acc.x -= hi.x * v.x;
+        }
+      }
+      Ws[e] = acc;
+    }
+    __syncthreads();
+  }
+  // h_{j+1,j} = ||W||, V_{j+1} = W / h_{j+1,j}
+  double s = 0.0;
+  for (int e = threadIdx.x; e < nb; e += AT) s += Ws[e].x * Ws[e].x + (C ? Ws[e].y * Ws[e].y : 0.0);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) red[warp] = s;
+  __syncthreads();
+  if (warp == 0) {
+    double t = lane < AT / 32 ? red[lane] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (lane == 0) red[0] = sqrt(t);
+  }
+  __syncthreads();
+  const double hn = red[0];
+  const double inv = hn > 0.0 ? 1.0 / hn : 0.0;
+  double2* vn = I.V + (size_t)(j + 1) * nb;
+  for (int e = threadIdx.x; e < nb; e += AT) vn[e] = make_double2(Ws[e].x * inv, Ws[e].y * inv);
+  // Hessenberg column j: CGS2 sum, earlier rotations, new rotation, g
+  double2* col = h[0];
+  for (int i = threadIdx.x; i <= j; i += AT)
+    col[i] = make_double2(h[0][i].x + h[1][i].x, h[0][i].y + h[1][i].y);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    col[j + 1] = make_double2(hn, 0.0);
+    for (int i = 0; i < j; ++i) {
+      const double c = cs_s[i];
+      const double2 sv = sn_s[i], a = col[i], bb = col[i + 1];
+      const double2 t = cmul(sv, bb);
+      const double2 u = cmul(make_double2(sv.x, -sv.y), a);
+      col[i] = make_double2(c * a.x + t.x, c * a.y + t.y);
+      col[i + 1] = make_double2(-u.x + c * bb.x, -u.y + c * bb.y);
+    }
+    const double2 a = col[j];
+    const double bre = col[j + 1].x;
+    double c;
+    double2 sv;
+    const double aa = hypot(a.x, a.y);
+    if (bre == 0.0) {
+      c = 1.0;
+      sv = make_double2(0.0, 0.0);
+    } else if (aa == 0.0) {
+      c = 0.0;
+      sv = make_double2(1.0, 0.0);
+    } else {
+      const double den = hypot(aa, bre);
+      c = aa / den;
+      sv = make_double2(a.x / aa * bre / den, a.y / aa * bre / den);
+    }
+    I.cs[j] = c;
+    I.sn[j] = sv;
+    col[j] = make_double2(c * a.x + sv.x * bre, c * a.y + sv.y * bre);
+    col[j + 1] = make_double2(0.0, 0.0);
+    const double2 gj = I.g[j];
+    const double2 u = cmul(make_double2(sv.x, -sv.y), gj);
+    I.g[j + 1] = make_double2(-u.x, -u.y);
+    I.g[j] = make_double2(c * gj.x, c * gj.y);
+    const double res = hypot(u.x, u.y);
+    I.scal[1] = res;
+    const double st = !isfinite(res) ? 2.0 : ((res <= I.scal[3] * I.scal[0] || hn == 0.0) ? 1.0 : 0.0);
+    I.scal[2] = st;
+    I.flags[1] = j + 1;
+  }
+  __syncthreads();
+  double2* Hc = I.H + (size_t)j * (m + 1);
+  for (int i = threadIdx.x; i <= j + 1; i += AT) Hc[i] = col[i];
+  // the stop flag last: no other thread of this block reads flags[0] again
+  if (threadIdx.x == 0 && I.scal[2] != 0.0) I.flags[0] = 0;
+}
+
 // Dv += V y (k = flags[1] iterations); runs for every instance with k > 0.
 __global__ void __launch_bounds__(GT) gk_update(const GInst* gi) {
   KFBI_PDL_ENTRY();
@@ -1167,29 +1392,40 @@ __global__ void gk_step_update(const GInst* gi) {
   const size_t plane = (size_t)I.Mp * I.Mp;
   if (I.eq == KFBI_HEAT) {
     const double four_dt = 4.0 / I.dt;
-    INST_PLANE_LOOP(I) {
-      const int r = (int)((unsigned)idx / (unsigned)I.Mp), c = (int)idx - r * I.Mp;
-      const double uu = I.U64[idx];
-      double f = four_dt * uu - I.F[idx];
-      if (I.src && r < I.n1 && c < I.n1) f += I.src_scale * I.src[(size_t)r * I.n1 + c];
-      I.u[idx] = uu;
-      I.F[idx] = f;
+    INST_QUAD_LOOP(I) {
+      const int r = (int)((unsigned)idx / (unsigned)I.Mp), c0 = (int)idx - r * I.Mp;
+      const Quad uu = ldq(I.U64 + idx), F = ldq(I.F + idx);
+      Quad f;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        f.v[k] = four_dt * uu.v[k] - F.v[k];
+        if (I.src && r < I.n1 && c0 + k < I.n1)
+          f.v[k] += I.src_scale * I.src[(size_t)r * I.n1 + c0 + k];
+      }
+      stq(I.u + idx, uu);
+      stq(I.F + idx, f);
     }
   } else if (I.eq == KFBI_WAVE) {
     const double k_theta = I.kre / I.theta, c1 = (1.0 - 2.0 * I.theta) / I.theta;
-    INST_PLANE_LOOP(I) {
-      const double uu = I.U64[idx], f = I.F[idx];
-      const double fn = k_theta * uu - c1 * f - I.Fprev[idx];
-      I.Fprev[idx] = f;
-      I.F[idx] = fn;
-      I.u[idx] = uu;
+    INST_QUAD_LOOP(I) {
+      const Quad uu = ldq(I.U64 + idx), f = ldq(I.F + idx), fp = ldq(I.Fprev + idx);
+      Quad fn;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) fn.v[k] = k_theta * uu.v[k] - c1 * f.v[k] - fp.v[k];
+      stq(I.Fprev + idx, f);
+      stq(I.F + idx, fn);
+      stq(I.u + idx, uu);
     }
   } else {
-    INST_PLANE_LOOP(I) {
+    INST_QUAD_LOOP(I) {
       for (int p = 0; p < 2; ++p) {
         const size_t q = p * plane + idx;
-        I.u[q] = I.U64[q];
-        I.F[q] = 2.0 * I.U64[q] - I.aux[q];
+        const Quad uu = ldq(I.U64 + q), ax = ldq(I.aux + q);
+        Quad f;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) f.v[k] = 2.0 * uu.v[k] - ax.v[k];
+        stq(I.u + q, uu);
+        stq(I.F + q, f);
       }
     }
   }
@@ -1599,14 +1835,25 @@ void launch_post(kfbi_batch* B, cudaStream_t st) {
 void batch_iteration(kfbi_batch* B, cudaStream_t st) {
   const int n = B->n;
   fast_apply(B, st);
-  KFBI_LAUNCH_P(KFBI_PROF_KRYLOV, gk_cgs_dots, inst_grid(GMAX, n), GT, 0, st, B->d_inst,
-                (const int*)B->d_j);
-  KFBI_LAUNCH_P(KFBI_PROF_KRYLOV, gk_cgs_update, inst_grid(GMAX, n), GT, 0, st, B->d_inst,
-                (const int*)B->d_j, 1, 0);
-  KFBI_LAUNCH_P(KFBI_PROF_KRYLOV, gk_cgs_update, inst_grid(GMAX, n), GT, 0, st, B->d_inst,
-                (const int*)B->d_j, 0, 1);
-  KFBI_LAUNCH_P(KFBI_PROF_KRYLOV, gk_cgs_finalize, inst_grid(GMAX, n), GT, 0, st, B->d_inst,
-                (const int*)B->d_j);
+  if (B->max_nb <= kArnoldiMaxNb) {
+    // one block per instance
+    const size_t smem = (size_t)B->max_nb * sizeof(double2);
+    if (B->n_cplx < n)
+      KFBI_LAUNCH_P(KFBI_PROF_KRYLOV, gk_arnoldi<false>, n, AT, smem, st, B->d_inst,
+                    (const int*)B->d_j);
+    if (B->n_cplx > 0)
+      KFBI_LAUNCH_P(KFBI_PROF_KRYLOV, gk_arnoldi<true>, n, AT, smem, st, B->d_inst,
+                    (const int*)B->d_j);
+  } else {
+    KFBI_LAUNCH_P(KFBI_PROF_KRYLOV, gk_cgs_dots, inst_grid(GMAX, n), GT, 0, st, B->d_inst,
+                  (const int*)B->d_j);
+    KFBI_LAUNCH_P(KFBI_PROF_KRYLOV, gk_cgs_update, inst_grid(GMAX, n), GT, 0, st, B->d_inst,
+                  (const int*)B->d_j, 1, 0);
+    KFBI_LAUNCH_P(KFBI_PROF_KRYLOV, gk_cgs_update, inst_grid(GMAX, n), GT, 0, st, B->d_inst,
+                  (const int*)B->d_j, 0, 1);
+    KFBI_LAUNCH_P(KFBI_PROF_KRYLOV, gk_cgs_finalize, inst_grid(GMAX, n), GT, 0, st, B->d_inst,
+                  (const int*)B->d_j);
+  }
   KFBI_LAUNCH_P(KFBI_PROF_KRYLOV, gk_bump, 1, 32, 0, st, B->d_j);
   launch_post(B, st);
   KFBI_CHECK_LAUNCH();
@@ -1743,6 +1990,11 @@ void batch_bind(kfbi_batch* B, kfbi_domain* const* domains, int n) {
   const int full = (B->max_Mp * B->max_Mp + 255) / 256;
   int pb = std::max((full + 7) / 8, (B->nsm * 8 + n - 1) / n);
   B->max_planes_blocks = std::max(1, std::min({pb, full, 1024}));
+  if (B->max_nb <= kArnoldiMaxNb) {
+    const int smem = (int)(B->max_nb * sizeof(double2));
+    KFBI_CUDA(cudaFuncSetAttribute(gk_arnoldi<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    KFBI_CUDA(cudaFuncSetAttribute(gk_arnoldi<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  }
 }
 
 }  // namespace kfbi

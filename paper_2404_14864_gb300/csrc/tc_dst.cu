@@ -128,12 +128,17 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
-// Bounded wait on an mbarrier phase; false after WAIT_LIMIT cycles.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+// Bounded wait on an mbarrier phase; false after `limit` cycles.
+__device__ __forceinline__ bool mbar_wait_for(uint64_t* bar, uint32_t parity, long long limit) {
   const long long t0 = clock64();
   while (!mbar_try_wait(bar, parity))
-    if (clock64() - t0 > WAIT_LIMIT) return false;
+    if (clock64() - t0 > limit) return false;
   return true;
+}
+
+// The pipeline waits of the passes: false after WAIT_LIMIT cycles.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  return mbar_wait_for(bar, parity, WAIT_LIMIT);
 }
 
 // Wait that also acquires writes other CTAs of the cluster released to
@@ -1855,6 +1860,45 @@ __global__ void k_check_conversions(unsigned long long seed, long long n,
 
 }  // namespace
 }  // namespace kfbi
+
+namespace kfbi {
+namespace {
+
+// A wait that must give up: an mbarrier expecting one arrival that never
+// comes, waited on with the passes' bounded wait, which then records the
+// failure in the error word as a pass does.
+__global__ void k_wait_selftest(long long limit, int* err) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) mbar_init(&bar, 1);
+  __syncthreads();
+  if (threadIdx.x == 0 && !mbar_wait_for(&bar, 0u, limit)) atomicOr(err, 64);
+}
+
+}  // namespace
+}  // namespace kfbi
+
+extern "C" kfbi_status kfbi_check_wait_timeout(double seconds, void* stream) {
+  if (!(seconds > 0.0 && seconds <= 1.0)) return KFBI_ERR_ARG;
+  return kfbi::guarded(nullptr, [&]() -> kfbi_status {
+    cudaStream_t st = (cudaStream_t)stream;
+    int dev = 0, khz = 0;
+    KFBI_CUDA(cudaGetDevice(&dev));
+    KFBI_CUDA(cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev));
+    const long long limit = (long long)(seconds * 1e3 * (double)khz);
+    int* d_err = nullptr;
+    KFBI_CUDA(cudaMallocAsync(&d_err, sizeof(int), st));
+    KFBI_CUDA(cudaMemsetAsync(d_err, 0, sizeof(int), st));
+    kfbi::k_wait_selftest<<<1, 32, 0, st>>>(limit, d_err);
+    KFBI_CHECK_LAUNCH();
+    int h_err = 0;
+    KFBI_CUDA(cudaMemcpyAsync(&h_err, d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    KFBI_CUDA(cudaFreeAsync(d_err, st));
+    KFBI_CUDA(cudaStreamSynchronize(st));
+    if (h_err != 0)
+      throw kfbi::Status{KFBI_ERR_TIMEOUT, "bounded wait gave up (flags " + std::to_string(h_err) + ")"};
+    return KFBI_OK;
+  });
+}
 
 extern "C" kfbi_status kfbi_check_conversions(unsigned long long seed, long long n,
                                               long long* mismatches, void* stream) {

@@ -169,6 +169,7 @@ def lib():
         "kfbi_profile_bytes": (S, [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
         "kfbi_check_conversions": (S, [ctypes.c_ulonglong, ctypes.c_longlong,
                                        ctypes.POINTER(ctypes.c_longlong), ctypes.c_void_p]),
+        "kfbi_check_wait_timeout": (S, [ctypes.c_double, ctypes.c_void_p]),
         "kfbi_box_solve_noalloc": (S, [ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                        ctypes.c_double, ctypes.c_double, _VP, _VP, _VP]),
         "kfbi_batch_create": (S, [ctypes.POINTER(_VP), ctypes.c_int, _VP, ctypes.POINTER(_VP)]),
@@ -309,6 +310,11 @@ def kfbi_check_conversions(seed, n, stream=None):
     m = ctypes.c_longlong()
     _check(lib().kfbi_check_conversions(int(seed), int(n), ctypes.byref(m), _stream(stream)))
     return int(m.value)
+
+
+def kfbi_check_wait_timeout(seconds, stream=None):
+    """Status of the bounded-wait self-check (KFBI_ERR_TIMEOUT expected)."""
+    return int(lib().kfbi_check_wait_timeout(float(seconds), _stream(stream)))
 
 
 # ----------------------------------------------------------------------------
