@@ -474,6 +474,12 @@ void tc_apply(kfbi_domain* D, double kre, double kim, const double* phi, int phi
               const double* ft, double* out, int out_stride, bool want_grid, cudaStream_t st);
 void tc_apply_accurate(kfbi_domain* D, double kre, double kim, const double* phi, int phi_stride,
                        const double* ft, double* out, int out_stride, cudaStream_t st);
+// Accurate application at phi = phi_prev + d from the grid of an accurate
+// application at phi_prev (in D->d_U, no volume source) and one FP32 box
+// solve of the correction d; the result's error is that of a box solve
+// without refinement, relative to |A d|.
+void tc_apply_correction(kfbi_domain* D, double kre, double kim, const double* d, const double* phi,
+                         int phi_stride, double* out, int out_stride, cudaStream_t st);
 long long tc_bytes(const TcDst* tc);
 // Exact device bytes of what the allocation routines take for a plan: the
 // tensor-core buffers, the GMRES workspace, a whole domain (not counting the

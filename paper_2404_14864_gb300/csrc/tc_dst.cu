@@ -1802,6 +1802,29 @@ void tc_apply_accurate(kfbi_domain* D, double kre, double kim, const double* phi
   KFBI_CHECK_LAUNCH();
 }
 
+// Application at phi = phi_prev + d for a small correction d, given the
+// grid of an accurate application at phi_prev in D->d_U (no volume
+// source): the grid is affine in the density, so W phi = W phi_prev + W d,
+// and W d needs only one FP32 box solve (no refinement sweep) because its
+// error scales with |d|.  D->d_U becomes W phi and out the FP64 extraction
+// at phi from that grid.
+void tc_apply_correction(kfbi_domain* D, double kre, double kim, const double* d, const double* phi,
+                         int ps, double* out, int os, cudaStream_t st) {
+  TcDst* T = D->tc;
+  const bool C = kim != 0.0;
+  const int P = C ? 2 : 1;
+  const size_t plane = (size_t)T->Mp * T->Mp;
+  correct_fp64(D, kre, kim, d, ps, nullptr, st);
+  KFBI_LAUNCH_P(KFBI_PROF_GRID, k_split64, grid_for(P * plane, 256), 256, 0, st, D->d_R, T->Rh,
+                T->fft ? nullptr : T->Rl, P * plane, 0);
+  T->rhs_sparse_planes = 0;
+  tc_box_solve(D, kre, kim, P, st);
+  KFBI_LAUNCH_P(KFBI_PROF_GRID, k_add_f32, grid_for(P * plane, 256), 256, 0, st, D->d_U, T->U,
+                P * plane);
+  if (out) extract_fp64(D, kre, kim, phi, ps, nullptr, out, os, st);
+  KFBI_CHECK_LAUNCH();
+}
+
 }  // namespace kfbi
 
 // ---- self-check of the integer-pipe conversions ----------------------------
