@@ -238,6 +238,7 @@ __global__ void gk_base_rhs(const GInst* gi, int with_ft) {
 __device__ __forceinline__ const double* density_of(const GInst& I, int which, int j) {
   if (which == 0) return nullptr;
   if (which == 1) return (const double*)I.x;
+  if (which == 3) return (const double*)I.Dv;
   return (const double*)(I.V + (size_t)j * I.nb);
 }
 
@@ -1355,7 +1356,8 @@ __global__ void __launch_bounds__(GT) gk_update(const GInst* gi) {
   }
 }
 
-// x += Dv; Dv = 0
+// x += Dv (Dv stays: the next check may apply it alone; every inner solve
+// starts from gk_zero_dv)
 __global__ void gk_axpy(const GInst* gi, const int* sel) {
   KFBI_PDL_ENTRY();
   const GInst& I = gi[blockIdx.y];
@@ -1363,7 +1365,6 @@ __global__ void gk_axpy(const GInst* gi, const int* sel) {
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < I.nb; e += gridDim.x * blockDim.x) {
     I.x[e].x += I.Dv[e].x;
     I.x[e].y += I.Dv[e].y;
-    I.Dv[e] = make_double2(0.0, 0.0);
   }
 }
 
@@ -1795,6 +1796,35 @@ void batch_accurate(kfbi_batch* B, int which, int with_ft, int target, cudaStrea
   KFBI_CHECK_LAUNCH();
 }
 
+// Application at x = x_prev + Dv for the active instances, from the grid of
+// an accurate application at x_prev in U64 (as tc_apply_correction): one
+// unrefined box solve of the correction Dv added to U64, then the FP64
+// extraction at x into Ax.
+void batch_correction(kfbi_batch* B, cudaStream_t st) {
+  const int n = B->n;
+  const int pb = plane_blocks(B);
+  KFBI_LAUNCH_P(KFBI_PROF_GRID, gk_base_rhs, inst_grid(pb, n), 256, 0, st, B->d_inst, 0);
+  KFBI_LAUNCH_P(KFBI_PROF_CORRECT, gk_correct64, inst_grid((B->max_n_irr + 127) / 128, n), 128, 0, st,
+                B->d_inst, 3, 0, (const int*)nullptr);
+  if (B->n_tc > 0) {
+    KFBI_LAUNCH_P(KFBI_PROF_GRID, gk_split64, inst_grid(pb, n), 256, 0, st, B->d_inst);
+    grouped_pass(B, kfbi_batch::kDense1, st);
+    grouped_pass(B, kfbi_batch::kDense2, st);
+    KFBI_LAUNCH_P(KFBI_PROF_GRID, gk_eig_cplx, inst_grid(pb, n), 256, 0, st, B->d_inst);
+    grouped_pass(B, kfbi_batch::kDense3, st);
+    grouped_pass(B, kfbi_batch::kDense4, st);
+  }
+  if (B->n_fft > 0) {
+    fft_grouped(B, kfbi_batch::kFftDense1, st);
+    fft_grouped(B, kfbi_batch::kFftSolve, st);
+    fft_grouped(B, kfbi_batch::kFftFinal, st);
+  }
+  KFBI_LAUNCH_P(KFBI_PROF_GRID, gk_add_f32, inst_grid(pb, n), 256, 0, st, B->d_inst);
+  KFBI_LAUNCH_P(KFBI_PROF_EXTRACT, gk_extract64, inst_grid((B->max_nb + 127) / 128, n), 128, 0, st,
+                B->d_inst, 1, 0, 1);
+  KFBI_CHECK_LAUNCH();
+}
+
 // W = A_fast V[j] for every active instance: the sparse route (TF32
 // instances: correction values, CUDA-core first pass, two restricted tensor
 // passes; FFT instances: first pass built from the arms, solve pass), then
@@ -2119,6 +2149,11 @@ kfbi_status batch_gmres(kfbi_batch* B, kfbi_solve_info* infos, cudaStream_t st) 
   std::vector<int> act(n, 1), xz(n), conv(n, 0), iters(n, 0), apps(n, 0), bad(n, 0);
   std::vector<int> ax_ok(n), fresh(n, 0);
   std::vector<double> bnorm(n, 0.0), rn(n, 0.0);
+  // small final corrections (as gmres_solve): r_prev the residual the last
+  // correction was solved for, err the bound on |A x - Ax| left by
+  // correction applications since the last refined one
+  const double kFastRelLinf = 2e-5;
+  std::vector<double> r_prev(n, 0.0), err(n, 0.0);
   B->grid_wx.assign(n, 0);
   for (int i = 0; i < n; ++i) {
     xz[i] = B->states[i]->phi_zero ? 1 : 0;
@@ -2137,15 +2172,21 @@ kfbi_status batch_gmres(kfbi_batch* B, kfbi_solve_info* infos, cudaStream_t st) 
     // first sweep an instance whose A phi is cached (its phi is the
     // previous step's converged phi) copies it instead
     set_active(B, act, &xz, st);
-    std::vector<int> need(n), cached(n);
-    bool any_acc = false, any_cached = false;
+    std::vector<int> need(n), cached(n), corr(n);
+    bool any_acc = false, any_cached = false, any_corr = false;
     for (int i = 0; i < n; ++i) {
       const bool has = act[i] && !xz[i];
       cached[i] = has && sweep == 0 && ax_ok[i];
-      need[i] = has && !cached[i];
-      fresh[i] = need[i];
+      const double tol = B->doms[i]->desc.gmres_tol;
+      const double e = err[i] + 2.0 * kFastRelLinf * std::sqrt((double)B->doms[i]->nb) * r_prev[i];
+      corr[i] = has && sweep > 0 && fresh[i] && !B->doms[i]->neumann && e <= 0.1 * tol * bnorm[i];
+      need[i] = has && !cached[i] && !corr[i];
+      if (corr[i]) err[i] = e;
+      else if (has) err[i] = 0.0;
+      fresh[i] = need[i] || corr[i];
       any_acc |= need[i] != 0;
       any_cached |= cached[i] != 0;
+      any_corr |= corr[i] != 0;
     }
     if (any_cached) {
       set_active(B, cached, nullptr, st);
@@ -2157,7 +2198,12 @@ kfbi_status batch_gmres(kfbi_batch* B, kfbi_solve_info* infos, cudaStream_t st) 
       batch_accurate(B, 1, 0, 1, st);
       for (int i = 0; i < n; ++i) apps[i] += need[i];
     }
-    if (any_cached || any_acc) set_active(B, act, &xz, st);
+    if (any_corr) {
+      set_active(B, corr, nullptr, st);
+      batch_correction(B, st);
+      for (int i = 0; i < n; ++i) apps[i] += corr[i];
+    }
+    if (any_cached || any_acc || any_corr) set_active(B, act, &xz, st);
     KFBI_LAUNCH_P(KFBI_PROF_KRYLOV, gk_residual, inst_grid(1, n), 1024, 0, st, B->d_inst);
     read_state(B, st);
     bool any = false;
@@ -2171,12 +2217,14 @@ kfbi_status batch_gmres(kfbi_batch* B, kfbi_solve_info* infos, cudaStream_t st) 
         continue;
       }
       const double tol = B->doms[i]->desc.gmres_tol;
-      if (bnorm[i] == 0.0 || rn[i] <= tol * bnorm[i] || iters[i] >= B->doms[i]->desc.gmres_maxit) {
-        conv[i] = rn[i] <= tol * bnorm[i] || bnorm[i] == 0.0;
+      const bool ok = rn[i] + err[i] <= tol * bnorm[i];
+      if (bnorm[i] == 0.0 || ok || iters[i] >= B->doms[i]->desc.gmres_maxit) {
+        conv[i] = ok || bnorm[i] == 0.0;
         B->grid_wx[i] = conv[i] && fresh[i];
         act[i] = 0;
         continue;
       }
+      r_prev[i] = rn[i];
       inner_tol[i] = std::max(0.5 * tol * bnorm[i] / rn[i], kInnerFloor);
       any = true;
     }
