@@ -21,6 +21,7 @@
 #include <cmath>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <numeric>
 #include <vector>
 
@@ -1319,15 +1320,26 @@ __global__ void __launch_bounds__(GT) gk_update(const GInst* gi) {
   const int G = grid_g(I.nb);
   if ((int)blockIdx.x >= G) return;
   const int m = I.m;
-  __shared__ double2 y[64];
+  __shared__ double2 y[64], gs[64];
+  __shared__ double2 R[64 * 65 / 2];  // R[l (l + 1) / 2 + i] = H(i, l), i <= l < k
   int e0, e1;
   slice_of(I.nb, blockIdx.x, G, e0, e1);
+  // the triangle and g in one round of independent loads (the solve below
+  // is a serial chain and must not wait on global memory)
+  for (int t = threadIdx.x; t < k * (k + 1) / 2; t += GT) {
+    int l = (int)((sqrtf(8.f * (float)t + 1.f) - 1.f) * 0.5f);
+    while (l * (l + 1) / 2 > t) --l;
+    while ((l + 1) * (l + 2) / 2 <= t) ++l;
+    R[t] = I.H[(size_t)l * (m + 1) + (t - l * (l + 1) / 2)];
+  }
+  for (int i = threadIdx.x; i < k; i += GT) gs[i] = I.g[i];
+  __syncthreads();
   if (threadIdx.x < 32) {
     const int lane = threadIdx.x;
     for (int i = k - 1; i >= 0; --i) {
       double2 s = make_double2(0.0, 0.0);
       for (int l = i + 1 + lane; l < k; l += 32) {
-        const double2 t = cmul(I.H[(size_t)l * (m + 1) + i], y[l]);
+        const double2 t = cmul(R[l * (l + 1) / 2 + i], y[l]);
         s.x += t.x;
         s.y += t.y;
       }
@@ -1336,8 +1348,8 @@ __global__ void __launch_bounds__(GT) gk_update(const GInst* gi) {
         s.y += __shfl_xor_sync(0xffffffffu, s.y, o);
       }
       if (lane == 0) {
-        const double2 r = make_double2(I.g[i].x - s.x, I.g[i].y - s.y);
-        const double2 d = I.H[(size_t)i * (m + 1) + i];
+        const double2 r = make_double2(gs[i].x - s.x, gs[i].y - s.y);
+        const double2 d = R[i * (i + 1) / 2 + i];
         const double dd = d.x * d.x + d.y * d.y;
         y[i] = make_double2((r.x * d.x + r.y * d.y) / dd, (r.y * d.x - r.x * d.y) / dd);
       }
@@ -2020,11 +2032,14 @@ void batch_bind(kfbi_batch* B, kfbi_domain* const* domains, int n) {
   const int full = (B->max_Mp * B->max_Mp + 255) / 256;
   int pb = std::max((full + 7) / 8, (B->nsm * 8 + n - 1) / n);
   B->max_planes_blocks = std::max(1, std::min({pb, full, 1024}));
-  if (B->max_nb <= kArnoldiMaxNb) {
-    const int smem = (int)(B->max_nb * sizeof(double2));
+  // the limit is a property of the kernel, shared by every batch (and
+  // server lane): set once, to the largest staging any batch uses
+  static std::once_flag arnoldi_attr;
+  std::call_once(arnoldi_attr, []() {
+    const int smem = (int)(kArnoldiMaxNb * sizeof(double2));
     KFBI_CUDA(cudaFuncSetAttribute(gk_arnoldi<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     KFBI_CUDA(cudaFuncSetAttribute(gk_arnoldi<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-  }
+  });
 }
 
 }  // namespace kfbi

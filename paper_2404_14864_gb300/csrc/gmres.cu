@@ -769,12 +769,19 @@ __global__ void __launch_bounds__(GT) k_update_grid(const double2* __restrict__ 
                                                     const double2* H, const double2* g, int m,
                                                     double2* __restrict__ x, int slice) {
   KFBI_PDL_ENTRY();
-  __shared__ double2 y[64];
+  __shared__ double2 y[64], gs[64];
   __shared__ double2 R[64 * 65 / 2];  // R[l (l + 1) / 2 + i] = H(i, l), i <= l < k <= 64
   const int b = blockIdx.x;
   const int e0 = b * slice, e1 = min(nb, e0 + slice);
-  for (int l = 0; l < k; ++l)
-    for (int i = threadIdx.x; i <= l; i += GT) R[l * (l + 1) / 2 + i] = H[(size_t)l * (m + 1) + i];
+  // the triangle and g in one round of independent loads (the solve below
+  // is a serial chain and must not wait on global memory)
+  for (int t = threadIdx.x; t < k * (k + 1) / 2; t += GT) {
+    int l = (int)((sqrtf(8.f * (float)t + 1.f) - 1.f) * 0.5f);
+    while (l * (l + 1) / 2 > t) --l;
+    while ((l + 1) * (l + 2) / 2 <= t) ++l;
+    R[t] = H[(size_t)l * (m + 1) + (t - l * (l + 1) / 2)];
+  }
+  for (int i = threadIdx.x; i < k; i += GT) gs[i] = g[i];
   __syncthreads();
   if (threadIdx.x < 32) {
     const int lane = threadIdx.x;
@@ -790,7 +797,7 @@ __global__ void __launch_bounds__(GT) k_update_grid(const double2* __restrict__ 
         s.y += __shfl_xor_sync(0xffffffffu, s.y, o);
       }
       if (lane == 0) {
-        const double2 r = make_double2(g[i].x - s.x, g[i].y - s.y);
+        const double2 r = make_double2(gs[i].x - s.x, gs[i].y - s.y);
         const double2 d = R[i * (i + 1) / 2 + i];
         const double inv = 1.0 / (d.x * d.x + d.y * d.y);
         y[i] = make_double2((r.x * d.x + r.y * d.y) * inv, (r.y * d.x - r.x * d.y) * inv);
