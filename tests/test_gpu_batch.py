@@ -235,3 +235,22 @@ def test_batch_nonlinear_schrodinger_equals_single_steps():
     batch.close()
     for d in doms + [d1]:
         d.close()
+
+
+def test_batches_of_different_sizes_step_in_any_order():
+    """Kernel limits that depend on a batch's sizes (the Arnoldi step stages
+    a whole boundary vector in shared memory) belong to the kernel, not to
+    the batch: a large batch still steps after a small one was bound."""
+    rng = np.random.Generator(np.random.PCG64(11))
+    big = _Run("heat", W.domain_desc(1024, W.random_star(rng)))
+    small = _Run("heat", W.domain_desc(128, W.random_star(rng)))
+    d_big = kfbi.Domain(big.desc, kfbi.KFBI_MIXED_FFT32, tol=1e-10, maxit=800)
+    d_small = kfbi.Domain(small.desc, kfbi.KFBI_MIXED_FFT32, tol=1e-10, maxit=800)
+    s_big, s_small = big.make_state(d_big), small.make_state(d_small)
+    b_big = kfbi.Batch([d_big])
+    b_small = kfbi.Batch([d_small])
+    for k in range(2):
+        g, s = small.inputs(k)
+        assert all(i["converged"] for i in b_small.step([s_small], [g], [s]))
+        g, s = big.inputs(k)
+        assert all(i["converged"] for i in b_big.step([s_big], [g], [s]))
