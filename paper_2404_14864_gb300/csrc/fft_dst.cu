@@ -287,11 +287,34 @@ __device__ __forceinline__ void body(const FftDesc& d, int lb, int rpb, float* s
   const size_t bstride = (size_t)N1 * 33;  // float2 per row buffer
   // the tables are written once at domain set-up: load them before waiting
   // for the previous kernel
-  for (int i = threadIdx.x; i < M; i += T) {
-    s_tw[i] = d.twM[i];
-    s_twb[i] = d.twB[i];
-    s_tw2[i] = d.tw2M[i];
-    s_lam[i] = solve && i < d.n1 ? d.lam[i] : 0.f;
+  {
+    // four rounds of loads in flight per thread (read-only path), then the
+    // stores: one round trip for the tables instead of one per round
+    constexpr int CH = 4;
+    for (int i0 = threadIdx.x; i0 < M; i0 += CH * T) {
+      float2 a[CH], b[CH], c[CH];
+      float l[CH];
+#pragma unroll
+      for (int q = 0; q < CH; ++q) {
+        const int i = i0 + q * T;
+        if (i < M) {
+          a[q] = __ldg(d.twM + i);
+          b[q] = __ldg(d.twB + i);
+          c[q] = __ldg(d.tw2M + i);
+          l[q] = solve && i < d.n1 ? __ldg(d.lam + i) : 0.f;
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < CH; ++q) {
+        const int i = i0 + q * T;
+        if (i < M) {
+          s_tw[i] = a[q];
+          s_twb[i] = b[q];
+          s_tw2[i] = c[q];
+          s_lam[i] = l[q];
+        }
+      }
+    }
   }
   KFBI_PDL_ENTRY();
   KFBI_STOP_RETURN(d.stop);
