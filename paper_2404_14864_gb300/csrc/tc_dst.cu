@@ -686,22 +686,38 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_pass(const __grid_constant__ 
 // fp32_lo: FFT domains, whose passes read the FP32 plane hi alone: lo gets
 // the FP32 remainder x - hi (the pair keeps ~48 bits of x for the
 // double-float refinement residual, k_resid_u32).
+// Plane kernels in quads: four consecutive elements per thread and 16-byte
+// accesses (n is a multiple of 4: planes are Mp x Mp with Mp a multiple of
+// 128), so each thread keeps four elements' loads in flight.
+#define QUAD_LOOP(q, n)                                                           \
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < (n) / 4;     \
+       q += (size_t)gridDim.x * blockDim.x)
+
+__device__ __forceinline__ void split_one(double x, bool fp32_pair, float& h, float& l) {
+  if (fp32_pair) {
+    split_f64(x, h, l);
+    return;
+  }
+  h = tf32_round((float)x);
+  l = tf32_round((float)(x - (double)h));
+}
+
 __global__ void k_split64(const double* __restrict__ src, float* __restrict__ hi,
                           float* __restrict__ lo, size_t n, int fp32_lo) {
   KFBI_PDL_ENTRY();
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
-       i += (size_t)gridDim.x * blockDim.x) {
-    const double x = src[i];
-    if (!lo || fp32_lo) {  // FP32 plane(s) of the FFT passes
-      float h, l;
-      split_f64(x, h, l);
-      hi[i] = h;
-      if (lo) lo[i] = l;
-      continue;
-    }
-    const float h = tf32_round((float)x);
-    hi[i] = h;
-    lo[i] = tf32_round((float)(x - (double)h));
+  // FP32 plane(s) of the FFT passes (hi alone, or hi with its FP32
+  // remainder), else a TF32 pair
+  const bool f32 = !lo || fp32_lo;
+  QUAD_LOOP(q, n) {
+    const double2 a = reinterpret_cast<const double2*>(src)[2 * q];
+    const double2 b = reinterpret_cast<const double2*>(src)[2 * q + 1];
+    float4 h, l;
+    split_one(a.x, f32, h.x, l.x);
+    split_one(a.y, f32, h.y, l.y);
+    split_one(b.x, f32, h.z, l.z);
+    split_one(b.y, f32, h.w, l.w);
+    reinterpret_cast<float4*>(hi)[q] = h;
+    if (lo) reinterpret_cast<float4*>(lo)[q] = l;
   }
 }
 
@@ -1065,9 +1081,11 @@ __global__ void k_extract32(const float* __restrict__ U, size_t plane,
 
 __global__ void k_f32_to_f64(const float* __restrict__ src, double* __restrict__ dst, size_t n) {
   KFBI_PDL_ENTRY();
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
-       i += (size_t)gridDim.x * blockDim.x)
-    dst[i] = f32_to_f64(src[i]);
+  QUAD_LOOP(q, n) {
+    const float4 v = reinterpret_cast<const float4*>(src)[q];
+    reinterpret_cast<double2*>(dst)[2 * q] = make_double2(f32_to_f64(v.x), f32_to_f64(v.y));
+    reinterpret_cast<double2*>(dst)[2 * q + 1] = make_double2(f32_to_f64(v.z), f32_to_f64(v.w));
+  }
 }
 
 // Residual of the five-point system in FP64 for the iterative refinement of
@@ -1131,8 +1149,55 @@ __device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
 // final rounding: r keeps ~2^-48 of |R| while it is ~1e-6 |R| itself (the
 // float64 stencil of k_resid_split gives the same r to FP32 rounding, with
 // float64 operations that GB300 issues at a small fraction of the FP32
-// rate).  Overwrites Rh with r (each thread reads its own point first) and
+// rate).  Overwrites Rh with r (each thread reads its own points first) and
 // writes U64 = U32, the start of the refined grid.
+//
+// r = R - L u at one point in double-float arithmetic from FP32 values: u,
+// its four neighbours, uo the other plane's u (complex: L couples the planes
+// through +-Im kappa, sg = +1 for the real plane, -1 for the imaginary one),
+// (R_hi, R_lo) the FP32 pair of R.
+template <bool C>
+__device__ __forceinline__ float resid_point(float u, float e, float w, float nn, float so, float uo,
+                                             float sg, float R_hi, float R_lo, float ih_hi,
+                                             float ih_lo, float kr_hi, float kr_lo, float ki_hi,
+                                             float ki_lo) {
+  // S = e + w + n + s - 4u as hi + lo
+  float sh = -4.f * u, sl = 0.f, t;
+  two_sum(sh, e, sh, t);
+  sl += t;
+  two_sum(sh, w, sh, t);
+  sl += t;
+  two_sum(sh, nn, sh, t);
+  sl += t;
+  two_sum(sh, so, sh, t);
+  sl += t;
+  // Lu = S / h^2 - kappa u (+- kim u_other): leading products exact
+  float p1, e1, p2, e2;
+  two_prod(sh, ih_hi, p1, e1);
+  two_prod(kr_hi, u, p2, e2);
+  float tail = e1 + fmaf(sh, ih_lo, sl * ih_hi) - e2 - kr_lo * u;
+  float lu_hi, t2;
+  two_sum(p1, -p2, lu_hi, t2);
+  tail += t2;
+  if (C) {
+    float p3, e3;
+    two_prod(ki_hi, uo, p3, e3);
+    float t3;
+    two_sum(lu_hi, sg * p3, lu_hi, t3);
+    tail += t3 + sg * (e3 + ki_lo * uo);
+  }
+  // res = R - Lu
+  float d, t4;
+  two_sum(R_hi, -lu_hi, d, t4);
+  return d + ((t4 + R_lo) - tail);
+}
+
+__device__ __forceinline__ float f4k(const float4& v, int k) {
+  return k == 0 ? v.x : k == 1 ? v.y : k == 2 ? v.z : v.w;
+}
+
+// The kernel: four consecutive points of a row per thread; U64 = 0 and r = 0
+// outside the n1 x n1 block.
 template <bool C>
 __global__ void __launch_bounds__(256) k_resid_u32(float* __restrict__ Rh,
                                                    const float* __restrict__ Rl,
@@ -1142,64 +1207,62 @@ __global__ void __launch_bounds__(256) k_resid_u32(float* __restrict__ Rh,
                                                    float kr_lo, float ki_hi, float ki_lo) {
   KFBI_PDL_ENTRY();
   const size_t plane = (size_t)Mp * Mp;
-  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < plane;
-       idx += (size_t)gridDim.x * blockDim.x) {
-    const int r = (int)(idx / Mp), c = (int)(idx - (size_t)r * Mp);
-    const bool in = r < n1 && c < n1;
+  const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+  QUAD_LOOP(q, plane) {
+    const size_t idx = 4 * q;
+    const int r = (int)((unsigned)idx / (unsigned)Mp), c0 = (int)idx - r * Mp;
+    const bool live = r < n1 && c0 < n1;
 #pragma unroll
     for (int p = 0; p < (C ? 2 : 1); ++p) {
       const float* Up = U32 + p * plane;
-      const float u = in ? Up[idx] : 0.f;
-      float res = 0.f;
-      if (in) {
-        const float e = c + 1 < n1 ? Up[idx + 1] : 0.f;
-        const float w = c > 0 ? Up[idx - 1] : 0.f;
-        const float nn = r + 1 < n1 ? Up[idx + Mp] : 0.f;
-        const float so = r > 0 ? Up[idx - Mp] : 0.f;
-        // S = e + w + n + s - 4u as hi + lo
-        float sh = -4.f * u, sl = 0.f, t;
-        two_sum(sh, e, sh, t);
-        sl += t;
-        two_sum(sh, w, sh, t);
-        sl += t;
-        two_sum(sh, nn, sh, t);
-        sl += t;
-        two_sum(sh, so, sh, t);
-        sl += t;
-        // Lu = S / h^2 - kappa u (+- kim u_other): leading products exact
-        float p1, e1, p2, e2;
-        two_prod(sh, ih_hi, p1, e1);
-        two_prod(kr_hi, u, p2, e2);
-        float tail = e1 + fmaf(sh, ih_lo, sl * ih_hi) - e2 - kr_lo * u;
-        float lu_hi, t2;
-        two_sum(p1, -p2, lu_hi, t2);
-        tail += t2;
-        if (C) {
-          const float uo = U32[(1 - p) * plane + idx];
-          float p3, e3;
-          two_prod(ki_hi, uo, p3, e3);
-          const float sg = p == 0 ? 1.f : -1.f;
-          float t3;
-          two_sum(lu_hi, sg * p3, lu_hi, t3);
-          tail += t3 + sg * (e3 + ki_lo * uo);
+      float4 res = z4, uq = z4;
+      if (live) {
+        uq = *reinterpret_cast<const float4*>(Up + idx);
+        const float4 un = r + 1 < n1 ? *reinterpret_cast<const float4*>(Up + idx + Mp) : z4;
+        const float4 us = r > 0 ? *reinterpret_cast<const float4*>(Up + idx - Mp) : z4;
+        const float uw = c0 > 0 ? Up[idx - 1] : 0.f;
+        const float ue = c0 + 4 < n1 ? Up[idx + 4] : 0.f;
+        const float4 uo = C ? *reinterpret_cast<const float4*>(U32 + (1 - p) * plane + idx) : z4;
+        const float4 rh = *reinterpret_cast<const float4*>(Rh + p * plane + idx);
+        const float4 rl = *reinterpret_cast<const float4*>(Rl + p * plane + idx);
+        float o[4], uu[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const int c = c0 + k;
+          const float u = c < n1 ? f4k(uq, k) : 0.f;
+          const float e = c + 1 < n1 ? (k < 3 ? f4k(uq, k + 1) : ue) : 0.f;
+          const float w = c > 0 ? (k > 0 ? f4k(uq, k - 1) : uw) : 0.f;
+          uu[k] = u;
+          o[k] = c < n1 ? resid_point<C>(u, e, w, f4k(un, k), f4k(us, k), f4k(uo, k),
+                                         p == 0 ? 1.f : -1.f, f4k(rh, k), f4k(rl, k), ih_hi,
+                                         ih_lo, kr_hi, kr_lo, ki_hi, ki_lo)
+                        : 0.f;
         }
-        // res = R - Lu
-        const float R_hi = Rh[p * plane + idx], R_lo = Rl[p * plane + idx];
-        float d, t4;
-        two_sum(R_hi, -lu_hi, d, t4);
-        res = d + ((t4 + R_lo) - tail);
+        res = make_float4(o[0], o[1], o[2], o[3]);
+        uq = make_float4(uu[0], uu[1], uu[2], uu[3]);
       }
-      U64[p * plane + idx] = f32_to_f64(u);
-      Rh[p * plane + idx] = res;
+      reinterpret_cast<double2*>(U64 + p * plane + idx)[0] =
+          make_double2(f32_to_f64(uq.x), f32_to_f64(uq.y));
+      reinterpret_cast<double2*>(U64 + p * plane + idx)[1] =
+          make_double2(f32_to_f64(uq.z), f32_to_f64(uq.w));
+      *reinterpret_cast<float4*>(Rh + p * plane + idx) = res;
     }
   }
 }
 
 __global__ void k_add_f32(double* __restrict__ dst, const float* __restrict__ src, size_t n) {
   KFBI_PDL_ENTRY();
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
-       i += (size_t)gridDim.x * blockDim.x)
-    dst[i] += f32_to_f64(src[i]);
+  QUAD_LOOP(q, n) {
+    const float4 v = reinterpret_cast<const float4*>(src)[q];
+    double2 a = reinterpret_cast<const double2*>(dst)[2 * q];
+    double2 b = reinterpret_cast<const double2*>(dst)[2 * q + 1];
+    a.x += f32_to_f64(v.x);
+    a.y += f32_to_f64(v.y);
+    b.x += f32_to_f64(v.z);
+    b.y += f32_to_f64(v.w);
+    reinterpret_cast<double2*>(dst)[2 * q] = a;
+    reinterpret_cast<double2*>(dst)[2 * q + 1] = b;
+  }
 }
 
 const int kPassThreads = THREADS;
@@ -1704,7 +1767,7 @@ void tc_apply(kfbi_domain* D, double kre, double kim, const double* phi, int ps,
   const int Mp = T->Mp;
   const size_t plane = (size_t)Mp * Mp;
   if (ft) {
-    KFBI_LAUNCH_P(KFBI_PROF_GRID, k_split64, grid_for(P * plane, 256), 256, 0, st, ft, T->Rh,
+    KFBI_LAUNCH_P(KFBI_PROF_GRID, k_split64, grid_for(P * plane / 4, 256), 256, 0, st, ft, T->Rh,
                   T->fft ? nullptr : T->Rl, P * plane, 0);
     T->rhs_sparse_planes = 0;
   } else if (T->rhs_sparse_planes < P) {
@@ -1738,7 +1801,7 @@ void tc_apply(kfbi_domain* D, double kre, double kim, const double* phi, int ps,
                     out, os);
   }
   if (want_grid)
-    KFBI_LAUNCH_P(KFBI_PROF_GRID, k_f32_to_f64, grid_for(P * plane, 256), 256, 0, st, T->U,
+    KFBI_LAUNCH_P(KFBI_PROF_GRID, k_f32_to_f64, grid_for(P * plane / 4, 256), 256, 0, st, T->U,
                   D->d_U, P * plane);
   KFBI_CHECK_LAUNCH();
 }
@@ -1758,12 +1821,12 @@ void tc_apply_accurate(kfbi_domain* D, double kre, double kim, const double* phi
   correct_fp64(D, kre, kim, phi, ps, ft, st);  // D->d_R: FP64 corrected RHS
   // FFT domains keep the FP32 remainder of R in the (otherwise unused) lo
   // planes for the double-float residual
-  KFBI_LAUNCH_P(KFBI_PROF_GRID, k_split64, grid_for(P * plane, 256), 256, 0, st, D->d_R, T->Rh, T->Rl,
+  KFBI_LAUNCH_P(KFBI_PROF_GRID, k_split64, grid_for(P * plane / 4, 256), 256, 0, st, D->d_R, T->Rh, T->Rl,
                 P * plane, T->fft ? 1 : 0);
   T->rhs_sparse_planes = 0;
   tc_box_solve(D, kre, kim, P, st);
   if (!T->fft)
-    KFBI_LAUNCH_P(KFBI_PROF_GRID, k_f32_to_f64, grid_for(P * plane, 256), 256, 0, st, T->U, D->d_U,
+    KFBI_LAUNCH_P(KFBI_PROF_GRID, k_f32_to_f64, grid_for(P * plane / 4, 256), 256, 0, st, T->U, D->d_U,
                   P * plane);
   const double inv_h2 = 1.0 / (D->h * D->h);
   // one refinement sweep leaves a relative grid error ~delta^2; the normal
@@ -1780,11 +1843,11 @@ void tc_apply_accurate(kfbi_domain* D, double kre, double kim, const double* phi
     float* rl = T->fft ? nullptr : T->Rl;
     if (sw == 0 && T->fft) {
       if (C)
-        KFBI_LAUNCH_P(KFBI_PROF_GRID, k_resid_u32<true>, grid_for(plane, 256), 256, 0, st, T->Rh,
+        KFBI_LAUNCH_P(KFBI_PROF_GRID, k_resid_u32<true>, grid_for(plane / 4, 256), 256, 0, st, T->Rh,
                       (const float*)T->Rl, (const float*)T->U, D->d_U, Mp, T->n1, ih_hi, ih_lo,
                       kr_hi, kr_lo, ki_hi, ki_lo);
       else
-        KFBI_LAUNCH_P(KFBI_PROF_GRID, k_resid_u32<false>, grid_for(plane, 256), 256, 0, st, T->Rh,
+        KFBI_LAUNCH_P(KFBI_PROF_GRID, k_resid_u32<false>, grid_for(plane / 4, 256), 256, 0, st, T->Rh,
                       (const float*)T->Rl, (const float*)T->U, D->d_U, Mp, T->n1, ih_hi, ih_lo,
                       kr_hi, kr_lo, ki_hi, ki_lo);
     } else if (C) {
@@ -1795,7 +1858,7 @@ void tc_apply_accurate(kfbi_domain* D, double kre, double kim, const double* phi
                     D->d_U, T->Rh, rl, Mp, T->n1, inv_h2, kre, kim);
     }
     tc_box_solve(D, kre, kim, P, st);
-    KFBI_LAUNCH_P(KFBI_PROF_GRID, k_add_f32, grid_for(P * plane, 256), 256, 0, st, D->d_U, T->U,
+    KFBI_LAUNCH_P(KFBI_PROF_GRID, k_add_f32, grid_for(P * plane / 4, 256), 256, 0, st, D->d_U, T->U,
                   P * plane);
   }
   if (out) extract_fp64(D, kre, kim, phi, ps, ft, out, os, st);
@@ -1815,11 +1878,11 @@ void tc_apply_correction(kfbi_domain* D, double kre, double kim, const double* d
   const int P = C ? 2 : 1;
   const size_t plane = (size_t)T->Mp * T->Mp;
   correct_fp64(D, kre, kim, d, ps, nullptr, st);
-  KFBI_LAUNCH_P(KFBI_PROF_GRID, k_split64, grid_for(P * plane, 256), 256, 0, st, D->d_R, T->Rh,
+  KFBI_LAUNCH_P(KFBI_PROF_GRID, k_split64, grid_for(P * plane / 4, 256), 256, 0, st, D->d_R, T->Rh,
                 T->fft ? nullptr : T->Rl, P * plane, 0);
   T->rhs_sparse_planes = 0;
   tc_box_solve(D, kre, kim, P, st);
-  KFBI_LAUNCH_P(KFBI_PROF_GRID, k_add_f32, grid_for(P * plane, 256), 256, 0, st, D->d_U, T->U,
+  KFBI_LAUNCH_P(KFBI_PROF_GRID, k_add_f32, grid_for(P * plane / 4, 256), 256, 0, st, D->d_U, T->U,
                 P * plane);
   if (out) extract_fp64(D, kre, kim, phi, ps, nullptr, out, os, st);
   KFBI_CHECK_LAUNCH();
