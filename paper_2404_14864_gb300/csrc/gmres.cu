@@ -83,39 +83,78 @@ __device__ __forceinline__ void mbox_post(const double* scal, double* mbox, long
   reinterpret_cast<volatile long long*>(slot)[8] = seq;
 }
 
+// kRegPT elements of r per thread stay in registers between the norm and the
+// scaling (nb <= kRegPT * kThreads); larger nb reads V0 back.
+constexpr int kRegPT = 4;
+
 __global__ void __launch_bounds__(kThreads) k_restart(const double2* __restrict__ b,
                                                        const double2* __restrict__ Ax,
                                                        double2* __restrict__ V0, double2* g,
                                                        int m, int nb, double* scal, double* mbox,
-                                                       long long seq) {
+                                                       long long seq, double tol_x0) {
   KFBI_PDL_ENTRY();
   __shared__ double red[32];
+  // x = 0 (Ax null) with tol_x0 >= 0: beta is ||b|| itself, so the start of
+  // the solve writes scal[0] = ||b|| and scal[3] = tol here (no k_bnorm)
+  const bool own_norm = !Ax && tol_x0 >= 0.0;
+  const double s0 = own_norm ? 0.0 : scal[0], s3 = own_norm ? tol_x0 : scal[3];
   double s = 0.0;
-  for (int e = threadIdx.x; e < nb; e += kThreads) {
-    double2 r = b[e];
-    if (Ax) {
-      r.x -= Ax[e].x;
-      r.y -= Ax[e].y;
+  double2 rr[kRegPT];
+  const bool in_regs = nb <= kRegPT * kThreads;
+  if (in_regs) {
+#pragma unroll
+    for (int k = 0; k < kRegPT; ++k) {
+      const int e = threadIdx.x + k * kThreads;
+      double2 r = make_double2(0.0, 0.0);
+      if (e < nb) {
+        r = b[e];
+        if (Ax) {
+          const double2 a = Ax[e];
+          r.x -= a.x;
+          r.y -= a.y;
+        }
+      }
+      rr[k] = r;
+      s += r.x * r.x + r.y * r.y;
     }
-    V0[e] = r;
-    s += r.x * r.x + r.y * r.y;
+  } else {
+    for (int e = threadIdx.x; e < nb; e += kThreads) {
+      double2 r = b[e];
+      if (Ax) {
+        r.x -= Ax[e].x;
+        r.y -= Ax[e].y;
+      }
+      V0[e] = r;
+      s += r.x * r.x + r.y * r.y;
+    }
   }
   s = block_sum(s, red);
   const double beta = sqrt(s);
   const double inv = beta > 0.0 ? 1.0 / beta : 0.0;
-  for (int e = threadIdx.x; e < nb; e += kThreads) {
-    V0[e].x *= inv;
-    V0[e].y *= inv;
+  if (in_regs) {
+#pragma unroll
+    for (int k = 0; k < kRegPT; ++k) {
+      const int e = threadIdx.x + k * kThreads;
+      if (e < nb) V0[e] = make_double2(rr[k].x * inv, rr[k].y * inv);
+    }
+  } else {
+    for (int e = threadIdx.x; e < nb; e += kThreads) {
+      V0[e].x *= inv;
+      V0[e].y *= inv;
+    }
   }
   if (threadIdx.x <= m) g[threadIdx.x] = make_double2(threadIdx.x == 0 ? beta : 0.0, 0.0);
   if (threadIdx.x == 0) {
+    const double bn = own_norm ? beta : s0;
+    if (own_norm) {
+      scal[0] = bn;
+      scal[3] = s3;
+    }
     scal[1] = beta;
-    scal[2] = !isfinite(beta) ? 2.0 : (beta <= scal[3] * scal[0] ? 1.0 : 0.0);
+    scal[2] = !isfinite(beta) ? 2.0 : (beta <= s3 * bn ? 1.0 : 0.0);
     mbox_post(scal, mbox, seq);
   }
 }
-
-
 
 // ---- multi-CTA CGS2 Arnoldi ------------------------------------------------
 // GB300 keeps a small fraction of FP64 throughput per SM, so one Arnoldi
@@ -1082,7 +1121,9 @@ static kfbi_status gmres_core(kfbi_domain* D, double kre, double kim, const doub
     qj[j] = ahead ? next_post(D) : 0;
     arnoldi_step(D, C, j, st, qj[j]);
   };
-  KFBI_LAUNCH_P(KFBI_PROF_KRYLOV, k_bnorm, 1, kThreads, 0, st, (const double2*)b, nb, D->d_scal, tol);
+  // from x = 0 the first restart takes ||b|| itself
+  if (!x_zero)
+    KFBI_LAUNCH_P(KFBI_PROF_KRYLOV, k_bnorm, 1, kThreads, 0, st, (const double2*)b, nb, D->d_scal, tol);
   int it = 0;
   bool first = true;
   kfbi_status status = KFBI_OK;
@@ -1092,7 +1133,7 @@ static kfbi_status gmres_core(kfbi_domain* D, double kre, double kim, const doub
     if (!skip_ax) apply_internal(D, kre, kim, x, 2, nullptr, D->d_W, 2, false, st);
     const long long q0 = ahead ? next_post(D) : 0;
     KFBI_LAUNCH_P(KFBI_PROF_KRYLOV, k_restart, 1, kThreads, 0, st, (const double2*)b, skip_ax ? nullptr : W, V, g, m,
-                nb, D->d_scal, ahead ? D->d_mbox : nullptr, q0);
+                nb, D->d_scal, ahead ? D->d_mbox : nullptr, q0, skip_ax ? tol : -1.0);
     KFBI_CHECK_LAUNCH();
     if (ahead) {
       if (it < maxit) iterate(0);
