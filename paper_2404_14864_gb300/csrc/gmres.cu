@@ -1545,7 +1545,6 @@ kfbi_status gmres_solve(kfbi_domain* D, double kre, double kim, const double* b,
                               cudaMemcpyDeviceToDevice, st));
     if (grid_wx) *grid_wx = true;
   }
-  KFBI_CUDA(cudaStreamSynchronize(st));
   if (info) {
     info->iters = it;
     info->applications = apps;
@@ -1556,6 +1555,10 @@ kfbi_status gmres_solve(kfbi_domain* D, double kre, double kim, const double* b,
     D->err = "GMRES with refinement reached gmres_maxit";
     status = KFBI_ERR_NOT_CONVERGED;
   }
+  // every scalar the host needed came through the mailbox; on success the
+  // caller's remaining kernels queue behind the solve and the caller
+  // synchronises once at its end, on failure the stream is drained here
+  if (status != KFBI_OK) KFBI_CUDA(cudaStreamSynchronize(st));
   return status;
 }
 
