@@ -65,6 +65,7 @@ __global__ void __launch_bounds__(kThreads) k_bnorm(const double2* __restrict__ 
   if (threadIdx.x == 0) {
     scal[0] = sqrt(s);
     scal[3] = tol;
+    scal[7] = scal[0];  // kept for the refinement (inner solves reuse scal[0])
   }
 }
 
@@ -152,6 +153,78 @@ __global__ void __launch_bounds__(kThreads) k_restart(const double2* __restrict_
     }
     scal[1] = beta;
     scal[2] = !isfinite(beta) ? 2.0 : (beta <= s3 * bn ? 1.0 : 0.0);
+    mbox_post(scal, mbox, seq);
+  }
+}
+
+// The refinement's residual check and the start of its inner solve in one
+// kernel: r = b - Ax into Rv, ||r|| into scal[1], and (as k_restart from
+// x = 0 on Rv) V0 = r / ||r||, g = (||r||, 0, ...), with the inner tolerance
+// max(0.5 tol ||b|| / ||r||, floor) formed here from ||b|| in scal[7].
+// When ||r|| <= tol ||b|| (or is not finite) the GMRES status scal[2] is set
+// (1, 2), so an iteration queued behind this kernel returns at once.
+__global__ void __launch_bounds__(kThreads) k_residual_restart(const double2* __restrict__ b,
+                                                                const double2* __restrict__ Ax,
+                                                                double2* __restrict__ Rv,
+                                                                double2* __restrict__ V0,
+                                                                double2* g, int m, int nb,
+                                                                double* scal, double* mbox,
+                                                                long long seq, double tol,
+                                                                double floor_) {
+  KFBI_PDL_ENTRY();
+  __shared__ double red[32];
+  double s = 0.0;
+  double2 rr[kRegPT];
+  const bool in_regs = nb <= kRegPT * kThreads;
+  if (in_regs) {
+#pragma unroll
+    for (int k = 0; k < kRegPT; ++k) {
+      const int e = threadIdx.x + k * kThreads;
+      double2 r = make_double2(0.0, 0.0);
+      if (e < nb) {
+        r = b[e];
+        if (Ax) {
+          const double2 a = Ax[e];
+          r.x -= a.x;
+          r.y -= a.y;
+        }
+        Rv[e] = r;
+      }
+      rr[k] = r;
+      s += r.x * r.x + r.y * r.y;
+    }
+  } else {
+    for (int e = threadIdx.x; e < nb; e += kThreads) {
+      double2 r = b[e];
+      if (Ax) {
+        r.x -= Ax[e].x;
+        r.y -= Ax[e].y;
+      }
+      Rv[e] = r;
+      s += r.x * r.x + r.y * r.y;
+    }
+  }
+  s = block_sum(s, red);
+  const double beta = sqrt(s);
+  const double inv = beta > 0.0 ? 1.0 / beta : 0.0;
+  if (in_regs) {
+#pragma unroll
+    for (int k = 0; k < kRegPT; ++k) {
+      const int e = threadIdx.x + k * kThreads;
+      if (e < nb) V0[e] = make_double2(rr[k].x * inv, rr[k].y * inv);
+    }
+  } else {
+    for (int e = threadIdx.x; e < nb; e += kThreads)
+      V0[e] = make_double2(Rv[e].x * inv, Rv[e].y * inv);
+  }
+  if (threadIdx.x <= m) g[threadIdx.x] = make_double2(threadIdx.x == 0 ? beta : 0.0, 0.0);
+  if (threadIdx.x == 0) {
+    const double bn = scal[7];
+    const double st = !isfinite(beta) ? 2.0 : (beta <= tol * bn ? 1.0 : 0.0);
+    scal[0] = beta;
+    scal[1] = beta;
+    scal[2] = st;
+    scal[3] = st == 0.0 ? fmax(0.5 * tol * bn / beta, floor_) : 1.0;
     mbox_post(scal, mbox, seq);
   }
 }
@@ -1101,9 +1174,16 @@ struct StopScope {
 // iteration j + 1 finds the convergence flag set and its kernels return at
 // once; it would only have written H column j + 1, g[j + 1 .. j + 2] and
 // V[j + 2], none of which the update with k = j + 1 reads.
+// A first cycle already in the stream (the refinement queues it behind its
+// residual check, k_residual_restart): the restart's post and iteration 0's.
+struct Prestart {
+  long long q0;
+  long long qj0;
+};
+
 static kfbi_status gmres_core(kfbi_domain* D, double kre, double kim, const double* b, double* x,
                               bool x_zero, double tol, int maxit, kfbi_solve_info* info,
-                              cudaStream_t st) {
+                              cudaStream_t st, const Prestart* pre = nullptr) {
   const int m = D->restart, nb = D->nb;
   const bool C = kim != 0.0;
   double2* V = (double2*)D->d_V;
@@ -1122,7 +1202,7 @@ static kfbi_status gmres_core(kfbi_domain* D, double kre, double kim, const doub
     arnoldi_step(D, C, j, st, qj[j]);
   };
   // from x = 0 the first restart takes ||b|| itself
-  if (!x_zero)
+  if (!x_zero && !pre)
     KFBI_LAUNCH_P(KFBI_PROF_KRYLOV, k_bnorm, 1, kThreads, 0, st, (const double2*)b, nb, D->d_scal, tol);
   int it = 0;
   bool first = true;
@@ -1130,13 +1210,20 @@ static kfbi_status gmres_core(kfbi_domain* D, double kre, double kim, const doub
   if (info) *info = kfbi_solve_info{0, 0.0, 0, 0};
   for (;;) {
     const bool skip_ax = first && x_zero;
-    if (!skip_ax) apply_internal(D, kre, kim, x, 2, nullptr, D->d_W, 2, false, st);
-    const long long q0 = ahead ? next_post(D) : 0;
-    KFBI_LAUNCH_P(KFBI_PROF_KRYLOV, k_restart, 1, kThreads, 0, st, (const double2*)b, skip_ax ? nullptr : W, V, g, m,
-                nb, D->d_scal, ahead ? D->d_mbox : nullptr, q0, skip_ax ? tol : -1.0);
-    KFBI_CHECK_LAUNCH();
+    const bool queued_first = first && pre && ahead;
+    long long q0 = 0;
+    if (queued_first) {
+      q0 = pre->q0;
+      qj[0] = pre->qj0;
+    } else {
+      if (!skip_ax) apply_internal(D, kre, kim, x, 2, nullptr, D->d_W, 2, false, st);
+      q0 = ahead ? next_post(D) : 0;
+      KFBI_LAUNCH_P(KFBI_PROF_KRYLOV, k_restart, 1, kThreads, 0, st, (const double2*)b, skip_ax ? nullptr : W, V, g, m,
+                  nb, D->d_scal, ahead ? D->d_mbox : nullptr, q0, skip_ax ? tol : -1.0);
+      KFBI_CHECK_LAUNCH();
+    }
     if (ahead) {
-      if (it < maxit) iterate(0);
+      if (it < maxit && !queued_first) iterate(0);
       wait_post(D, q0, st);
     } else {
       read_scalars(D, st);
@@ -1430,10 +1517,10 @@ static kfbi_status richardson_core(kfbi_domain* D, double kre, double kim, const
 // Inner solver of the domain (kfbi_solver).
 static kfbi_status inner_solve(kfbi_domain* D, double kre, double kim, const double* b, double* x,
                                bool x_zero, double tol, int maxit, kfbi_solve_info* info,
-                               cudaStream_t st) {
+                               cudaStream_t st, const Prestart* pre = nullptr) {
   if (D->desc.solver == KFBI_RICHARDSON)
     return richardson_core(D, kre, kim, b, x, x_zero, tol, maxit, info, st);
-  return gmres_core(D, kre, kim, b, x, x_zero, tol, maxit, info, st);
+  return gmres_core(D, kre, kim, b, x, x_zero, tol, maxit, info, st, pre);
 }
 
 // Relative tolerance below which the inner solves of the refinement do not
@@ -1476,6 +1563,9 @@ kfbi_status gmres_solve(kfbi_domain* D, double kre, double kim, const double* b,
   // only d (tc_apply_correction); the residual test then subtracts that
   // bound, so the refined result still meets the tolerance.
   const double fast_rel = kFastRelLinf * std::sqrt((double)nb);
+  // the inner solver queues ahead through the mailbox (gmres_core's lookahead)
+  const bool lookahead = D->desc.solver != KFBI_RICHARDSON && D->n_irr > 0 &&
+                         arnoldi_cluster_size() > 0;
   double r_prev = 0.0;     // residual the last correction was solved for
   double err_bound = 0.0;  // bound on |A x - d_Ax| (corrections since the last full application)
   for (int sweep = 0; sweep < 8; ++sweep) {
@@ -1500,12 +1590,33 @@ kfbi_status gmres_solve(kfbi_domain* D, double kre, double kim, const double* b,
         err_bound = 0.0;
       }
     }
-    const long long q = next_post(D);
-    KFBI_LAUNCH_P(KFBI_PROF_KRYLOV, k_residual, 1, kThreads, 0, st, (const double2*)b,
-                  (const double2*)ax, (double2*)D->d_Rv, nb, D->d_scal, D->d_mbox, q);
-    KFBI_CHECK_LAUNCH();
+    // With the GMRES inner solver on the mailbox path, the residual check
+    // also starts the inner solve (k_residual_restart) and its first
+    // iteration is queued before the host reads the residual: if the check
+    // converged, that iteration finds the GMRES status set and returns.
+    const bool spec = lookahead && it < maxit;
+    Prestart pre{};
+    long long q = 0;
+    if (spec) {
+      KFBI_CUDA(cudaMemsetAsync(D->d_Dv, 0, 2 * (size_t)nb * sizeof(double), st));
+      q = next_post(D);
+      KFBI_LAUNCH_P(KFBI_PROF_KRYLOV, k_residual_restart, 1, kThreads, 0, st, (const double2*)b,
+                    (const double2*)ax, (double2*)D->d_Rv, (double2*)D->d_V, (double2*)D->d_g,
+                    D->restart, nb, D->d_scal, D->d_mbox, q, tol, kInnerFloor);
+      KFBI_CHECK_LAUNCH();
+      StopScope scope(D, true);
+      apply_internal(D, kre, kim, D->d_V, 2, nullptr, D->d_W, 2, false, st);
+      pre.q0 = q;
+      pre.qj0 = next_post(D);
+      arnoldi_step(D, kim != 0.0, 0, st, pre.qj0);
+    } else {
+      q = next_post(D);
+      KFBI_LAUNCH_P(KFBI_PROF_KRYLOV, k_residual, 1, kThreads, 0, st, (const double2*)b,
+                    (const double2*)ax, (double2*)D->d_Rv, nb, D->d_scal, D->d_mbox, q);
+      KFBI_CHECK_LAUNCH();
+    }
     wait_post(D, q, st);
-    if (sweep == 0) bnorm = D->h_scal[0];
+    if (sweep == 0) bnorm = D->h_scal[spec ? 7 : 0];
     rn = D->h_scal[1];
     if (!std::isfinite(rn)) {
       D->err = "non-finite density residual";
@@ -1526,10 +1637,10 @@ kfbi_status gmres_solve(kfbi_domain* D, double kre, double kim, const double* b,
     if (it >= maxit) break;
     r_prev = rn;
     const double inner_tol = std::max(0.5 * tol * bnorm / rn, kInnerFloor);
-    KFBI_CUDA(cudaMemsetAsync(D->d_Dv, 0, 2 * (size_t)nb * sizeof(double), st));
+    if (!spec) KFBI_CUDA(cudaMemsetAsync(D->d_Dv, 0, 2 * (size_t)nb * sizeof(double), st));
     kfbi_solve_info in{};
-    kfbi_status s =
-        inner_solve(D, kre, kim, D->d_Rv, D->d_Dv, true, inner_tol, maxit - it, &in, st);
+    kfbi_status s = inner_solve(D, kre, kim, D->d_Rv, D->d_Dv, true, inner_tol, maxit - it, &in,
+                                st, spec ? &pre : nullptr);
     it += in.iters;
     apps += in.applications;
     if (s == KFBI_ERR_NONFINITE) {
