@@ -969,8 +969,14 @@ __global__ void __launch_bounds__(1024) gk_restart(const GInst* gi, int with_ax)
     s += r.x * r.x + r.y * r.y;
   }
   s = block_sum(s, red);
-  const double beta = sqrt(s);
-  const double inv = beta > 0.0 ? 1.0 / beta : 0.0;
+  // the square root and the reciprocal once, not in every thread
+  __shared__ double s_beta, s_inv;
+  if (threadIdx.x == 0) {
+    s_beta = sqrt(s);
+    s_inv = s_beta > 0.0 ? 1.0 / s_beta : 0.0;
+  }
+  __syncthreads();
+  const double beta = s_beta, inv = s_inv;
   for (int e = threadIdx.x; e < I.nb; e += 1024) {
     I.V[e].x *= inv;
     I.V[e].y *= inv;
@@ -1113,7 +1119,7 @@ __global__ void __launch_bounds__(GT) gk_cgs_finalize(const GInst* gi, const int
   if ((int)blockIdx.x >= G) return;
   const int j = *dj;
   const int m = I.m;
-  __shared__ double nrm;
+  __shared__ double nrm, nrm_inv;
   int e0, e1;
   slice_of(I.nb, blockIdx.x, G, e0, e1);
   if (threadIdx.x < 32) {
@@ -1121,11 +1127,14 @@ __global__ void __launch_bounds__(GT) gk_cgs_finalize(const GInst* gi, const int
     double s = 0.0;
     for (int q = lane; q < G; q += 32) s += I.part[q].x;
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) nrm = sqrt(s);
+    if (lane == 0) {
+      nrm = sqrt(s);
+      nrm_inv = nrm > 0.0 ? 1.0 / nrm : 0.0;
+    }
   }
   __syncthreads();
   const double hn = nrm;
-  const double inv = hn > 0.0 ? 1.0 / hn : 0.0;
+  const double inv = nrm_inv;
   double2* vn = I.V + (size_t)(j + 1) * I.nb;
   for (int e = e0 + threadIdx.x; e < e1; e += GT)
     vn[e] = make_double2(I.W[e].x * inv, I.W[e].y * inv);
@@ -1252,11 +1261,14 @@ __global__ void __launch_bounds__(AT) gk_arnoldi(const GInst* gi, const int* dj)
     double t = lane < AT / 32 ? red[lane] : 0.0;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-    if (lane == 0) red[0] = sqrt(t);
+    if (lane == 0) {
+      red[0] = sqrt(t);
+      red[1] = red[0] > 0.0 ? 1.0 / red[0] : 0.0;
+    }
   }
   __syncthreads();
   const double hn = red[0];
-  const double inv = hn > 0.0 ? 1.0 / hn : 0.0;
+  const double inv = red[1];
   double2* vn = I.V + (size_t)(j + 1) * nb;
   for (int e = threadIdx.x; e < nb; e += AT) vn[e] = make_double2(Ws[e].x * inv, Ws[e].y * inv);
   // Hessenberg column j: CGS2 sum, earlier rotations, new rotation, g

@@ -130,8 +130,15 @@ __global__ void __launch_bounds__(kThreads) k_restart(const double2* __restrict_
     }
   }
   s = block_sum(s, red);
-  const double beta = sqrt(s);
-  const double inv = beta > 0.0 ? 1.0 / beta : 0.0;
+  // the square root and the reciprocal once (FP64 sequences every thread
+  // would otherwise run on GB300's narrow FP64 pipe)
+  __shared__ double s_beta, s_inv;
+  if (threadIdx.x == 0) {
+    s_beta = sqrt(s);
+    s_inv = s_beta > 0.0 ? 1.0 / s_beta : 0.0;
+  }
+  __syncthreads();
+  const double beta = s_beta, inv = s_inv;
   if (in_regs) {
 #pragma unroll
     for (int k = 0; k < kRegPT; ++k) {
@@ -205,8 +212,15 @@ __global__ void __launch_bounds__(kThreads) k_residual_restart(const double2* __
     }
   }
   s = block_sum(s, red);
-  const double beta = sqrt(s);
-  const double inv = beta > 0.0 ? 1.0 / beta : 0.0;
+  // the square root and the reciprocal once (FP64 sequences every thread
+  // would otherwise run on GB300's narrow FP64 pipe)
+  __shared__ double s_beta, s_inv;
+  if (threadIdx.x == 0) {
+    s_beta = sqrt(s);
+    s_inv = s_beta > 0.0 ? 1.0 / s_beta : 0.0;
+  }
+  __syncthreads();
+  const double beta = s_beta, inv = s_inv;
   if (in_regs) {
 #pragma unroll
     for (int k = 0; k < kRegPT; ++k) {
@@ -472,11 +486,14 @@ __global__ void __launch_bounds__(GT) k_cgs_finalize(double2* __restrict__ V, in
     double s = 0.0;
     for (int q = lane; q < G; q += 32) s += part[q].x;
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) nrm[0] = make_double2(sqrt(s), 0.0);
+    if (lane == 0) {
+      const double h = sqrt(s);
+      nrm[0] = make_double2(h, h > 0.0 ? 1.0 / h : 0.0);
+    }
   }
   __syncthreads();
   const double hn = nrm[0].x;
-  const double inv = hn > 0.0 ? 1.0 / hn : 0.0;
+  const double inv = nrm[0].y;
   double2* vn = V + (size_t)(j + 1) * nb;
   for (int e = e0 + threadIdx.x; e < e1; e += GT) vn[e] = make_double2(w[e].x * inv, w[e].y * inv);
   if (b == 0 && threadIdx.x == 0) {
@@ -768,7 +785,7 @@ __global__ void __launch_bounds__(CLT) k_arnoldi_cl(double2* __restrict__ V, int
   __shared__ double2 pa[65], pb[65], h1[65], h2[65], tmp[CLT], gcol[66], gsn[65], gg[66];
   __shared__ double gcs[65];
   __shared__ double pn[CLT / 32];
-  __shared__ double pnorm, s_hn;
+  __shared__ double pnorm, s_hn, s_inv;
   const int slice = (nb + CL - 1) / CL;
   const int e0 = min(nb, rank * slice), e1 = min(nb, e0 + slice), ns = e1 - e0;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -838,14 +855,17 @@ __global__ void __launch_bounds__(CLT) k_arnoldi_cl(double2* __restrict__ V, int
       const double o = __shfl_down_sync(0xffffffffu, v, w2);
       if ((lane & (2 * w2 - 1)) == 0) v += o;
     }
-    if (lane == 0) s_hn = sqrt(v);
+    if (lane == 0) {
+      s_hn = sqrt(v);
+      s_inv = s_hn > 0.0 ? 1.0 / s_hn : 0.0;
+    }
   }
   __syncthreads();
   // that was the last read of a peer's shared memory: arrive on the
   // cluster barrier now, wait for the peers only before leaving
   asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
   const double hn = s_hn;
-  const double inv = hn > 0.0 ? 1.0 / hn : 0.0;
+  const double inv = s_inv;
   double2* vn = V + (size_t)(j + 1) * nb + e0;
   for (int e = threadIdx.x; e < ns; e += CLT) vn[e] = make_double2(ws[e].x * inv, ws[e].y * inv);
   if (rank == 0) {
