@@ -500,7 +500,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_pass(const __grid_constant__ 
       const int ngroups = ((rank ? d->nk - kh : kh) + KPA - 1) / KPA;
       for (int gi = 0; gi < ngroups; ++gi, ++g) {
         const int b = g % NACC;
-        // one lane waits, the warp follows its verdict (tcgen05.ld needs the
+        // one lane waits, the warp follows its result (tcgen05.ld needs the
         // whole warp converged)
         int got = 1;
         if (lane == 0)
