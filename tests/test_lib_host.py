@@ -253,3 +253,13 @@ def test_binding_wrappers_expose_the_entry_points():
         for n in names:
             assert callable(getattr(cls, n, None)), (cls.__name__, n)
     assert callable(kfbi.table_cache_bytes)
+
+
+def test_self_checks_refuse_bad_arguments_without_touching_the_gpu(built):
+    """The device self-checks validate their arguments before any CUDA call."""
+    import ctypes
+    m = ctypes.c_longlong(-1)
+    assert built.kfbi_check_conversions(0, 0, ctypes.byref(m), None) == kfbi.KFBI_ERR_ARG
+    assert built.kfbi_check_conversions(0, 16, None, None) == kfbi.KFBI_ERR_ARG
+    for seconds in (0.0, -1.0, 1.5, float("nan")):
+        assert built.kfbi_check_wait_timeout(seconds, None) == kfbi.KFBI_ERR_ARG
