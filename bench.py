@@ -1347,6 +1347,10 @@ def main():
             "roofline": roofline(res, M),
             "kernel_time_ms_one_step": {k: {"launches": v[0], "ms": v[1]}
                                         for k, v in res["breakdown"].items()},
+            "kernel_time_note": ("one extra untimed step with a CUDA event pair around every "
+                                 "launch: the events serialise the programmatic dependent "
+                                 "launches, so the classes add up to more than ms_per_step; "
+                                 "read them as shares"),
             "gpu_launches": res["launches"],
             "clocks": res["clocks"],
             "e2e": {"value": replica_value(world, M * M * K, t_e2e), "unit": UNIT,
